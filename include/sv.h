@@ -1,0 +1,141 @@
+/*
+ * sv.h -- C ABI of the B300 sparse truncated state-vector library (libsv.so).
+ *
+ * The method (arXiv 2607.07816, "A Sparse and Truncated State Vector
+ * Simulator for Peaked Circuits"):
+ *   - the state stores only nonzero amplitudes, each with its basis state as a
+ *     64-bit key (Sec. II, Sec. V); qubit i is bit i of the key; n <= 64
+ *     (Sec. V);
+ *   - a gate is a 2^m x 2^m unitary on m qubits applied to every group of
+ *     basis states that differ only in those m bits (Eq. 3 and its
+ *     generalisation in Sec. IV-A); contributions to one new basis state are
+ *     summed (the segmented sum of Sec. IV-A) and exact zeros are dropped;
+ *   - truncation keeps the largest-probability terms: p-mass first, then
+ *     top-k, then renormalisation (Sec. III, Sec. IV-B);
+ *   - the result read back is the most probable basis state (Sec. V).
+ *
+ * All compute runs in CUDA kernels on the handle's stream; the state stays
+ * device-resident between calls.
+ *
+ * Conventions shared by every entry point:
+ *   - Gate local index: r = sum_t bit(key, qubits[t]) << t (qubits[0] is the
+ *     least significant bit).  U is row-major U[r_out][r_in], 2*4^m doubles
+ *     interleaved (re, im).
+ *   - Canonical order of terms: probability descending, then key ascending.
+ *     prob = fma(re, re, im*im) in double (complex64 components widened).
+ *   - Probability masses are exact sums of floor(prob * 2^120) held as
+ *     128-bit integers, converted to double with round-to-nearest-even.
+ *   - Ownership: every input buffer is read before the call returns; the
+ *     caller may free it afterwards.  Output buffers belong to the caller.
+ *   - Errors: every call returns an sv_status.  Arguments are validated on
+ *     the host (SV_E_ARG).  Device-side failures (a bounded wait that ran
+ *     out) are recorded on the handle and returned by the call that observes
+ *     them; the handle then refuses further work with SV_E_STATE.
+ *     sv_last_error() describes the last failure.
+ *   - Threads: a handle must not be used by two host threads at once.
+ */
+#ifndef SV_H_
+#define SV_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sv_state sv_state; /* opaque; owned by the caller until sv_destroy */
+
+typedef enum {
+  SV_OK = 0,
+  SV_E_ARG = -1,          /* invalid argument (checked on the host) */
+  SV_E_NOMEM = -2,        /* device allocation failed */
+  SV_E_CUDA = -3,         /* a CUDA runtime call failed */
+  SV_E_NOT_UNITARY = -4,  /* max |U^dagger U - I| above 1e-10 */
+  SV_E_TIMEOUT = -5,      /* a bounded device-side wait ran out */
+  SV_E_STATE = -6         /* handle unusable, or state empty / mass overflow */
+} sv_status;
+
+typedef enum { SV_C128 = 0, SV_C64 = 1 } sv_prec;
+
+/* Device memory provider.  alloc returns device memory of at least `bytes`
+ * bytes aligned to 256 bytes, or NULL on failure; free releases it.  A NULL
+ * allocator pointer selects cudaMalloc / cudaFree. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* ctx);
+  void (*free)(void* ptr, void* ctx);
+  void* ctx;
+} sv_allocator;
+
+/* Create the state |0...0> (a single term, Sec. I) on n qubits (1..64),
+ * complex128 amplitudes, the legacy default stream and cudaMalloc.
+ * K >= 1 is the top-k limit, 0 < p <= 1 the p-mass threshold of Sec. III
+ * (p >= 1 disables the p-mass cut). */
+sv_status sv_create(int n, uint64_t K, double p, sv_state** out);
+
+/* As sv_create with an amplitude precision (sv_prec), a cudaStream_t (NULL =
+ * legacy default stream) and an allocator (NULL = cudaMalloc). */
+sv_status sv_create_ex(int n, uint64_t K, double p, int prec, void* cuda_stream,
+                       const sv_allocator* alloc, sv_state** out);
+
+/* Free the handle and its device memory.  Accepts NULL. */
+sv_status sv_destroy(sv_state* s);
+
+/* Apply a 2^m x 2^m unitary (1 <= m <= 4) to the m distinct qubits
+ * qubits[0..m-1] (Eq. 3, Sec. IV-A).  Never truncates.  U must be finite
+ * and unitary within 1e-10 (SV_E_NOT_UNITARY otherwise).  Enqueued on the
+ * handle's stream; the call waits for the new term count. */
+sv_status sv_apply_gate(sv_state* s, int m, const int* qubits, const double* U);
+
+/* Truncate by the rule of Sec. III: p-mass cut c_p (smallest prefix of the
+ * canonical order whose mass reaches p * total), then c = min(c_p, K); if
+ * c < N the first c terms are kept and scaled by 1/sqrt(kept mass).
+ * kept (nullable) receives c; retained_fraction (nullable) receives
+ * kept mass / total mass (1 when nothing was cut).  Synchronises. */
+sv_status sv_truncate(sv_state* s, uint64_t* kept, double* retained_fraction);
+
+/* Most probable basis state in canonical order (Sec. V).  Synchronises;
+ * 16 bytes come back to the host.  SV_E_STATE if the state is empty. */
+sv_status sv_peak(sv_state* s, uint64_t* key, double* prob);
+
+/* Keys and probabilities in canonical order into host buffers of `cap`
+ * entries; writes min(cap, N) entries and sets *count = N.  Either buffer
+ * may be NULL.  Synchronises. */
+sv_status sv_probs(sv_state* s, uint64_t* keys, double* probs, uint64_t cap, uint64_t* count);
+
+/* Current number of terms. */
+sv_status sv_num_terms(sv_state* s, uint64_t* N);
+
+/* Product of the retained fractions of every truncation so far: the
+ * fidelity estimate of Sec. III. */
+sv_status sv_retained_mass(sv_state* s, double* F);
+
+/* Keys and amplitudes (interleaved re, im as doubles) in canonical order
+ * into host buffers of `cap` entries; writes min(cap, N), *count = N. */
+sv_status sv_export(sv_state* s, uint64_t* keys, double* amps, uint64_t cap, uint64_t* count);
+
+/* Replace the state with N host terms (checkpoint / test hook).  Keys must
+ * be distinct and below 2^n (SV_E_ARG otherwise); zero amplitudes are not
+ * stored; complex64 handles round each component to float. */
+sv_status sv_load(sv_state* s, const uint64_t* keys, const double* amps, uint64_t N);
+
+/* Human-readable description of the last failure on this handle (never
+ * NULL; empty when there was none). */
+const char* sv_last_error(const sv_state* s);
+
+/* Statistics of the last sv_apply_gate / sv_truncate (for benchmarking):
+ * terms before the gate, candidates after it, terms kept by the last
+ * truncation, radix-sort passes run, select levels run, and the total and
+ * kept probability masses of the last truncation. */
+typedef struct {
+  uint64_t n_in, n_pre, n_kept;
+  uint32_t sort_passes;
+  uint32_t select_levels;
+  double total_mass, kept_mass;
+} sv_stats;
+sv_status sv_last_stats(const sv_state* s, sv_stats* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SV_H_ */

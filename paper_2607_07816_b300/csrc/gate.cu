@@ -1,0 +1,236 @@
+// Gate application: key transform, partner-group heads, per-group mat-vec.
+//
+// Sec. IV-A: every amplitude meets the column of U selected by its bits on
+// the gate qubits; all amplitudes whose basis states agree outside those bits
+// form one group, whose 2^m outputs are y[r'] = sum_r U[r'][r] x[r] (Eq. 3
+// generalised).  Here the group is made contiguous by sorting on the key with
+// the gate bits moved to the bottom (sk = squeeze(key) << m | r), so a group
+// is a run of equal sk >> m with its members in ascending r.  One thread then
+// computes one output (group, r') in registers, and zero outputs are dropped
+// while the survivors are compacted in (group, r') order.
+#include "internal.h"
+#include "tile.cuh"
+
+namespace sv {
+
+struct KeyParams {
+  uint64_t qmask;
+  int m;
+  int q[4];
+  int qs[4];
+};
+
+__global__ void __launch_bounds__(256) k_gate_keys(const uint64_t* __restrict__ keys, uint64_t n,
+                                                   KeyParams kp, uint64_t* __restrict__ sk,
+                                                   uint32_t* __restrict__ sidx,
+                                                   uint32_t* __restrict__ hist, int passes) {
+  __shared__ uint32_t sh[MAX_PASSES][RADIX];
+  for (int i = threadIdx.x; i < MAX_PASSES * RADIX; i += blockDim.x) (&sh[0][0])[i] = 0;
+  __syncthreads();
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t key = keys[i];
+    uint32_t r = 0;
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      if (t < kp.m) r |= (uint32_t)((key >> kp.q[t]) & 1ull) << t;
+    uint64_t s = (squeeze_out(key, kp.qs, kp.m) << kp.m) | r;
+    sk[i] = s;
+    sidx[i] = (uint32_t)i;
+    for (int p = 0; p < passes; ++p) atomicAdd(&sh[p][(s >> (RADIX_BITS * p)) & (RADIX - 1)], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < passes * RADIX; i += blockDim.x) {
+    uint32_t c = (&sh[0][0])[i];
+    if (c) atomicAdd(&hist[i], c);
+  }
+}
+
+void launch_gate_keys(const uint64_t* keys, uint64_t n, const GateParams& gp, uint64_t* sk,
+                      uint32_t* sidx, uint32_t* hist, int passes, cudaStream_t st) {
+  KeyParams kp;
+  kp.qmask = gp.qmask;
+  kp.m = gp.m;
+  for (int t = 0; t < 4; ++t) {
+    kp.q[t] = gp.q[t];
+    kp.qs[t] = gp.qs[t];
+  }
+  cudaMemsetAsync(hist, 0, sizeof(uint32_t) * MAX_PASSES * RADIX, st);
+  if (n == 0) return;
+  uint64_t blocks = (n + 255) / 256;
+  if (blocks > 148 * 8) blocks = 148 * 8;
+  k_gate_keys<<<(unsigned)blocks, 256, 0, st>>>(keys, n, kp, sk, sidx, hist, passes);
+}
+
+// ------------------------------------------------------------------ heads
+constexpr int HEAD_BLOCK = 256, HEAD_ITEMS = 8;
+
+__global__ void __launch_bounds__(HEAD_BLOCK) k_group_heads(const uint64_t* __restrict__ sk, uint64_t n,
+                                                            int m, uint32_t* __restrict__ heads,
+                                                            uint64_t* lookback, Ctl* ctl) {
+  typedef TileLayout<HEAD_BLOCK, HEAD_ITEMS> L;
+  __shared__ CompactShared<HEAD_BLOCK> cs;
+  __shared__ uint64_t s_tile;
+  const uint64_t tiles = (n + L::TILE - 1) / L::TILE;
+  while (true) {
+    if (threadIdx.x == 0) s_tile = atomicAdd((unsigned long long*)&ctl->tile_counter[0], 1ull);
+    __syncthreads();
+    const uint64_t tile = s_tile;
+    if (tile >= tiles) break;
+    const uint64_t base = tile * L::TILE;
+    bool flag[HEAD_ITEMS];
+    uint32_t pos[HEAD_ITEMS];
+#pragma unroll
+    for (int j = 0; j < HEAD_ITEMS; ++j) {
+      uint64_t i = L::index(base, j);
+      bool f = false;
+      if (i < n) f = (i == 0) || ((sk[i] >> m) != (sk[i - 1] >> m));
+      flag[j] = f;
+    }
+    tile_compact<HEAD_BLOCK, HEAD_ITEMS>(flag, pos, cs, lookback, tile, &ctl->err);
+#pragma unroll
+    for (int j = 0; j < HEAD_ITEMS; ++j)
+      if (flag[j]) heads[cs.tile_base_out + pos[j]] = (uint32_t)L::index(base, j);
+    if (tile == tiles - 1 && threadIdx.x == 0) ctl->count[0] = cs.tile_base_out + cs.tile_total;
+    __syncthreads();
+  }
+}
+
+void launch_group_heads(const uint64_t* sk, uint64_t n, int m, uint32_t* heads, uint64_t* lookback,
+                        Ctl* ctl, cudaStream_t st) {
+  uint64_t tiles = (n + HEAD_BLOCK * HEAD_ITEMS - 1) / (HEAD_BLOCK * HEAD_ITEMS);
+  cudaMemsetAsync(lookback, 0, sizeof(uint64_t) * (tiles + 1), st);
+  cudaMemsetAsync(&ctl->tile_counter[0], 0, sizeof(uint64_t), st);
+  cudaMemsetAsync(&ctl->count[0], 0, sizeof(uint64_t), st);
+  if (n == 0) return;
+  uint64_t grid = tiles < 148 * 4 ? tiles : 148 * 4;
+  k_group_heads<<<(unsigned)grid, HEAD_BLOCK, 0, st>>>(sk, n, m, heads, lookback, ctl);
+}
+
+// ------------------------------------------------------------------ apply
+template <typename Real>
+struct Cplx;
+template <>
+struct Cplx<double> {
+  typedef double2 T;
+};
+template <>
+struct Cplx<float> {
+  typedef float2 T;
+};
+
+__device__ __forceinline__ double fma_r(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fma_r(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+constexpr int APPLY_BLOCK = 256, APPLY_ITEMS = 4;
+
+template <typename Real>
+__global__ void __launch_bounds__(APPLY_BLOCK) k_gate_apply(
+    const uint64_t* __restrict__ sk, const uint32_t* __restrict__ sidx, uint64_t n,
+    const uint32_t* __restrict__ heads, const typename Cplx<Real>::T* __restrict__ amps_in,
+    const GateParams gp, uint64_t* __restrict__ keys_out, typename Cplx<Real>::T* __restrict__ amps_out,
+    uint64_t* __restrict__ probs_out, uint64_t* lookback, Ctl* ctl) {
+  typedef TileLayout<APPLY_BLOCK, APPLY_ITEMS> L;
+  typedef typename Cplx<Real>::T C2;
+  __shared__ Real sU[512];
+  __shared__ uint32_t s_re_nz[16], s_im_nz[16];
+  __shared__ CompactShared<APPLY_BLOCK> cs;
+  __shared__ uint64_t s_tile;
+  const int m = gp.m, d = 1 << m;
+  for (int i = threadIdx.x; i < 2 * d * d; i += APPLY_BLOCK) sU[i] = (Real)gp.U[i];
+  if (threadIdx.x < 16) {
+    s_re_nz[threadIdx.x] = gp.re_nz[threadIdx.x];
+    s_im_nz[threadIdx.x] = gp.im_nz[threadIdx.x];
+  }
+  const uint64_t G = ctl->count[0];
+  const uint64_t S = G << m;
+  const uint64_t tiles = (S + L::TILE - 1) / L::TILE;
+  const uint32_t dmask = (uint32_t)d - 1u;
+  while (true) {
+    if (threadIdx.x == 0) s_tile = atomicAdd((unsigned long long*)&ctl->tile_counter[1], 1ull);
+    __syncthreads();
+    const uint64_t tile = s_tile;
+    if (tile >= tiles) break;
+    const uint64_t base = tile * L::TILE;
+    bool flag[APPLY_ITEMS];
+    uint32_t pos[APPLY_ITEMS];
+    Real yr[APPLY_ITEMS], yi[APPLY_ITEMS];
+    uint64_t ykey[APPLY_ITEMS];
+#pragma unroll
+    for (int j = 0; j < APPLY_ITEMS; ++j) {
+      uint64_t slot = L::index(base, j);
+      Real re = (Real)0, im = (Real)0;
+      uint64_t key = 0;
+      if (slot < S) {
+        uint64_t g = slot >> m;
+        uint32_t ro = (uint32_t)slot & dmask;
+        uint64_t h = heads[g];
+        uint64_t e = (g + 1 < G) ? (uint64_t)heads[g + 1] : n;
+        uint32_t present = 0;
+        for (uint64_t i = h; i < e; ++i) present |= 1u << (uint32_t)(sk[i] & dmask);
+        uint32_t rnz = s_re_nz[ro] & present, inz = s_im_nz[ro] & present;
+        uint32_t cols = rnz | inz;
+        while (cols) {
+          int r = __ffs(cols) - 1;
+          cols &= cols - 1u;
+          uint64_t i = h + __popc(present & ((1u << r) - 1u));
+          C2 x = amps_in[sidx[i]];
+          Real ur = sU[2 * (ro * d + r)], ui = sU[2 * (ro * d + r) + 1];
+          if ((rnz >> r) & 1u) {
+            re = fma_r(ur, x.x, re);
+            im = fma_r(ur, x.y, im);
+          }
+          if ((inz >> r) & 1u) {
+            re = fma_r(-ui, x.y, re);
+            im = fma_r(ui, x.x, im);
+          }
+        }
+        key = spread_in(sk[h] >> m, gp.qs, m);
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          if (t < m) key |= (uint64_t)((ro >> t) & 1u) << gp.q[t];
+      }
+      yr[j] = re;
+      yi[j] = im;
+      ykey[j] = key;
+      flag[j] = (slot < S) && !(re == (Real)0 && im == (Real)0);
+    }
+    tile_compact<APPLY_BLOCK, APPLY_ITEMS>(flag, pos, cs, lookback, tile, &ctl->err);
+#pragma unroll
+    for (int j = 0; j < APPLY_ITEMS; ++j) {
+      if (flag[j]) {
+        uint64_t o = cs.tile_base_out + pos[j];
+        keys_out[o] = ykey[j];
+        C2 y;
+        y.x = yr[j];
+        y.y = yi[j];
+        amps_out[o] = y;
+        probs_out[o] = (uint64_t)__double_as_longlong(prob_of((double)yr[j], (double)yi[j]));
+      }
+    }
+    if (tile == tiles - 1 && threadIdx.x == 0) ctl->count[1] = cs.tile_base_out + cs.tile_total;
+    __syncthreads();
+  }
+}
+
+void launch_gate_apply(int prec, const uint64_t* sk, const uint32_t* sidx, uint64_t n,
+                       const uint32_t* heads, const void* amps_in, const GateParams& gp,
+                       uint64_t* keys_out, void* amps_out, uint64_t* probs_out, uint64_t* lookback,
+                       Ctl* ctl, cudaStream_t st, uint64_t max_tiles) {
+  cudaMemsetAsync(lookback, 0, sizeof(uint64_t) * (max_tiles + 1), st);
+  cudaMemsetAsync(&ctl->tile_counter[1], 0, sizeof(uint64_t), st);
+  cudaMemsetAsync(&ctl->count[1], 0, sizeof(uint64_t), st);
+  if (n == 0) return;
+  uint64_t grid = max_tiles < 148 * 4 ? max_tiles : 148 * 4;
+  if (grid == 0) grid = 1;
+  if (prec == 0)
+    k_gate_apply<double><<<(unsigned)grid, APPLY_BLOCK, 0, st>>>(
+        sk, sidx, n, heads, (const double2*)amps_in, gp, keys_out, (double2*)amps_out, probs_out,
+        lookback, ctl);
+  else
+    k_gate_apply<float><<<(unsigned)grid, APPLY_BLOCK, 0, st>>>(
+        sk, sidx, n, heads, (const float2*)amps_in, gp, keys_out, (float2*)amps_out, probs_out,
+        lookback, ctl);
+}
+
+}  // namespace sv

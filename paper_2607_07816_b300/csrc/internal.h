@@ -1,0 +1,110 @@
+// Internal launch interfaces between the translation units of libsv.so.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace sv {
+
+constexpr int RADIX_BITS = 8;
+constexpr int RADIX = 1 << RADIX_BITS;
+constexpr int MAX_PASSES = 8;
+constexpr int SORT_THREADS = 256;
+constexpr int SORT_ITEMS = 16;
+constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;
+
+// Scratch used by one LSD radix sort.
+struct SortScratch {
+  uint32_t* hist;        // [MAX_PASSES][RADIX] device digit counts
+  uint32_t* hist_host;   // pinned mirror of hist
+  uint64_t* lookback;    // [tiles][RADIX] look-back descriptors for one pass
+  uint64_t lookback_tiles;
+  uint64_t* tile_counter;
+  uint32_t* err;
+};
+
+inline uint64_t sort_tiles(uint64_t n) { return (n + SORT_TILE - 1) / SORT_TILE; }
+
+// Histogram of every 8-bit digit of k[0..n) over the low nbits bits.
+void launch_digit_hist(const uint64_t* k, uint64_t n, int nbits, uint32_t* hist, cudaStream_t st);
+
+// Stable LSD radix sort of (k, v) pairs on bits [0, nbits) of k, with the
+// digit histograms already in scratch.hist (and its host mirror when
+// hist_on_host).  Passes whose digit is constant over all keys are skipped.
+// The result lands in (kA, vA) when the return value is 0, in (kB, vB)
+// when it is 1.  *passes_run receives the number of scatter passes.
+int radix_sort_pairs(uint64_t* kA, uint32_t* vA, uint64_t* kB, uint32_t* vB, uint64_t n, int nbits,
+                     const SortScratch& sc, cudaStream_t st, int* passes_run, cudaError_t* cerr);
+
+// Gate parameters passed by value to the gate kernels.
+struct GateParams {
+  uint64_t qmask;
+  uint64_t n_mask;
+  int m;
+  int q[4];            // gate qubits in the caller's order (bit t of r)
+  int qs[4];           // the same qubits in ascending order
+  uint32_t re_nz[16];  // bit r set when Re U[r_out][r] != 0
+  uint32_t im_nz[16];  // bit r set when Im U[r_out][r] != 0
+  double U[512];       // U[r_out][r] as (re, im), row-major
+};
+
+void launch_gate_keys(const uint64_t* keys, uint64_t n, const GateParams& gp, uint64_t* sk,
+                      uint32_t* sv_out, uint32_t* hist, int passes, cudaStream_t st);
+
+// Mark partner-group heads of the grouped sequence and compact their
+// positions; the group count lands in ctl->count[0].
+void launch_group_heads(const uint64_t* sk, uint64_t n, int m, uint32_t* heads, uint64_t* lookback,
+                        Ctl* ctl, cudaStream_t st);
+
+// Per-group mat-vec + zero drop; writes candidates and their probabilities,
+// the candidate count lands in ctl->count[1].
+void launch_gate_apply(int prec, const uint64_t* sk, const uint32_t* sidx, uint64_t n,
+                       const uint32_t* heads, const void* amps_in, const GateParams& gp,
+                       uint64_t* keys_out, void* amps_out, uint64_t* probs_out, uint64_t* lookback,
+                       Ctl* ctl, cudaStream_t st, uint64_t max_tiles);
+
+// Truncation select.
+constexpr int SEL_BITS = 11;
+constexpr int SEL_BINS = 1 << SEL_BITS;
+constexpr int FINISH_CAP = 4096;
+
+struct SelectScratch {
+  uint32_t* hist_count;   // [SEL_BINS]
+  uint64_t* hist_mass;    // [SEL_BINS][2] (hi, lo)
+  uint64_t* buf;          // [FINISH_CAP][2] composite (hi = ~pbits, lo = key)
+};
+
+// Initialise the select: mode 0 = by mass (target from p and the total
+// mass, computed in the first level), 1 = by count (target = rank).
+void launch_select_init(Ctl* ctl, int mode, uint64_t count_target, cudaStream_t st);
+void launch_select_hist(const uint64_t* probs, const uint64_t* keys, uint64_t n, Ctl* ctl,
+                        const SelectScratch& ss, cudaStream_t st);
+void launch_select_pick(Ctl* ctl, const SelectScratch& ss, double p, cudaStream_t st);
+void launch_select_compact(const uint64_t* probs, const uint64_t* keys, uint64_t n, Ctl* ctl,
+                           const SelectScratch& ss, cudaStream_t st);
+void launch_select_finish(Ctl* ctl, const SelectScratch& ss, double p, cudaStream_t st);
+// Keep the terms not after the cut in canonical order, scale them by
+// ctl->scale and recompute their probabilities; count in ctl->count[2].
+void launch_truncate_compact(int prec, const uint64_t* keys, const void* amps, const uint64_t* probs,
+                             uint64_t n, uint64_t* keys_out, void* amps_out, uint64_t* probs_out,
+                             uint64_t* lookback, Ctl* ctl, cudaStream_t st);
+void launch_set_scale(Ctl* ctl, cudaStream_t st);
+
+// Readout.
+void launch_peak(const uint64_t* probs, const uint64_t* keys, uint64_t n, Ctl* ctl, cudaStream_t st);
+void launch_iota(uint32_t* v, uint64_t n, cudaStream_t st);
+void launch_not_bits_gather(const uint64_t* probs, const uint32_t* idx, uint64_t n, uint64_t* out,
+                            cudaStream_t st);
+void launch_gather_terms(int prec, const uint32_t* idx, uint64_t n, const uint64_t* keys,
+                         const void* amps, const uint64_t* probs, uint64_t* keys_out,
+                         double* amps_out, uint64_t* probs_out, cudaStream_t st);
+// Load: amplitudes from double pairs (rounded to float for complex64),
+// zeros dropped, duplicates flagged (input sorted by key); probabilities
+// computed.  Count in ctl->count[2], duplicates in ctl->count[3].
+void launch_load_compact(int prec, const uint64_t* sorted_keys, const uint32_t* idx, uint64_t n,
+                         const double* amps_in, uint64_t* keys_out, void* amps_out,
+                         uint64_t* probs_out, uint64_t* lookback, Ctl* ctl, cudaStream_t st);
+
+}  // namespace sv

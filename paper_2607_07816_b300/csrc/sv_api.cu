@@ -1,0 +1,634 @@
+// C ABI of libsv.so (declared in include/sv.h): the state engine that
+// sequences the kernels of one gate application, one truncation and the
+// readouts on the handle's stream.
+//
+// Per gate (Sec. IV-A): key transform + digit histograms -> LSD radix sort
+// on (bits outside the gate, then the gate bits) -> partner-group heads ->
+// per-group mat-vec with zero drop and ordered compaction.
+// Per truncation (Sec. III, Sec. IV-B): radix select of the cut on the
+// canonical composite by mass (p) and/or by count (K) -> renormalising
+// compaction.  Readout (Sec. V): argmax in canonical order.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "internal.h"
+#include "sv.h"
+
+using namespace sv;
+
+struct sv_state {
+  int n = 0;
+  uint64_t K = 0;
+  double p = 1.0;
+  int prec = 0;
+  cudaStream_t st = nullptr;
+  sv_allocator alloc{};
+  bool custom_alloc = false;
+  size_t amp_bytes = 16;
+
+  uint64_t N = 0;
+  uint64_t cap = 0;
+  uint64_t* keys[2] = {nullptr, nullptr};
+  void* amps[2] = {nullptr, nullptr};
+  uint64_t* probs[2] = {nullptr, nullptr};
+  int cur = 0;
+
+  uint64_t sort_cap = 0;
+  uint64_t* sk[2] = {nullptr, nullptr};
+  uint32_t* sidx[2] = {nullptr, nullptr};
+  uint32_t* heads = nullptr;
+  uint64_t lb_entries = 0;
+  uint64_t* lookback = nullptr;
+
+  uint32_t* hist = nullptr;
+  uint32_t* hist_host = nullptr;
+  uint64_t* tile_counter = nullptr;
+  SelectScratch ss{};
+  Ctl* ctl = nullptr;
+  Ctl* ctl_host = nullptr;
+
+  double F = 1.0;
+  std::string err;
+  bool broken = false;
+  sv_stats stats{};
+};
+
+namespace {
+
+constexpr uint64_t MAX_TERMS = (1ull << 32) - 1;  // 32-bit term indices in the sort payload
+
+void* dev_alloc(sv_state* s, size_t bytes) {
+  if (bytes == 0) bytes = 256;
+  if (s->custom_alloc) return s->alloc.alloc(bytes, s->alloc.ctx);
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void dev_free(sv_state* s, void* p) {
+  if (!p) return;
+  if (s->custom_alloc)
+    s->alloc.free(p, s->alloc.ctx);
+  else
+    cudaFree(p);
+}
+
+sv_status fail(sv_state* s, sv_status code, const std::string& msg) {
+  s->err = msg;
+  return code;
+}
+
+sv_status cuda_check(sv_state* s, cudaError_t e, const char* where) {
+  if (e == cudaSuccess) return SV_OK;
+  s->broken = true;
+  return fail(s, SV_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+// Wait for the stream and read the control block; device error bits make
+// the handle unusable.
+sv_status sync_ctl(sv_state* s, const char* where) {
+  cudaError_t e = cudaMemcpyAsync(s->ctl_host, s->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  sv_status rc = cuda_check(s, e, where);
+  if (rc != SV_OK) return rc;
+  if (s->ctl_host->err & ERR_TIMEOUT) {
+    s->broken = true;
+    return fail(s, SV_E_TIMEOUT, std::string(where) + ": a bounded device wait ran out");
+  }
+  if (s->ctl_host->err & ERR_MASS) {
+    s->broken = true;
+    return fail(s, SV_E_STATE, std::string(where) + ": probability mass out of fixed-point range");
+  }
+  return SV_OK;
+}
+
+sv_status ensure_lookback(sv_state* s, uint64_t entries) {
+  if (entries <= s->lb_entries) return SV_OK;
+  uint64_t want = entries + entries / 2 + 1024;
+  uint64_t* p = (uint64_t*)dev_alloc(s, want * sizeof(uint64_t));
+  if (!p) return fail(s, SV_E_NOMEM, "look-back buffer allocation failed");
+  dev_free(s, s->lookback);
+  s->lookback = p;
+  s->lb_entries = want;
+  return SV_OK;
+}
+
+// State buffers (both halves) hold at least `need` terms; the current
+// state is preserved.
+sv_status ensure_state_cap(sv_state* s, uint64_t need) {
+  if (need <= s->cap) return SV_OK;
+  uint64_t cap = s->cap * 2 > need ? s->cap * 2 : need;
+  if (cap < 4096) cap = 4096;
+  uint64_t* k[2];
+  void* a[2];
+  uint64_t* pr[2];
+  for (int i = 0; i < 2; ++i) {
+    k[i] = (uint64_t*)dev_alloc(s, cap * 8);
+    a[i] = dev_alloc(s, cap * s->amp_bytes);
+    pr[i] = (uint64_t*)dev_alloc(s, cap * 8);
+    if (!k[i] || !a[i] || !pr[i]) {
+      for (int j = 0; j <= i; ++j) {
+        dev_free(s, k[j]);
+        dev_free(s, a[j]);
+        dev_free(s, pr[j]);
+      }
+      return fail(s, SV_E_NOMEM, "state buffer allocation failed");
+    }
+  }
+  if (s->N) {
+    cudaMemcpyAsync(k[0], s->keys[s->cur], s->N * 8, cudaMemcpyDeviceToDevice, s->st);
+    cudaMemcpyAsync(a[0], s->amps[s->cur], s->N * s->amp_bytes, cudaMemcpyDeviceToDevice, s->st);
+    cudaMemcpyAsync(pr[0], s->probs[s->cur], s->N * 8, cudaMemcpyDeviceToDevice, s->st);
+  }
+  sv_status rc = cuda_check(s, cudaStreamSynchronize(s->st), "state growth");
+  for (int i = 0; i < 2; ++i) {
+    dev_free(s, s->keys[i]);
+    dev_free(s, s->amps[i]);
+    dev_free(s, s->probs[i]);
+    s->keys[i] = k[i];
+    s->amps[i] = a[i];
+    s->probs[i] = pr[i];
+  }
+  s->cur = 0;
+  s->cap = cap;
+  return rc;
+}
+
+sv_status ensure_sort_cap(sv_state* s, uint64_t need) {
+  if (need > s->sort_cap) {
+    uint64_t cap = s->sort_cap * 2 > need ? s->sort_cap * 2 : need;
+    if (cap < 4096) cap = 4096;
+    for (int i = 0; i < 2; ++i) {
+      dev_free(s, s->sk[i]);
+      dev_free(s, s->sidx[i]);
+      s->sk[i] = (uint64_t*)dev_alloc(s, cap * 8);
+      s->sidx[i] = (uint32_t*)dev_alloc(s, cap * 4);
+    }
+    dev_free(s, s->heads);
+    s->heads = (uint32_t*)dev_alloc(s, cap * 4);
+    if (!s->sk[0] || !s->sk[1] || !s->sidx[0] || !s->sidx[1] || !s->heads) {
+      s->sort_cap = 0;
+      return fail(s, SV_E_NOMEM, "sort buffer allocation failed");
+    }
+    s->sort_cap = cap;
+  }
+  return ensure_lookback(s, sort_tiles(need) * RADIX + 16);
+}
+
+SortScratch sort_scratch(sv_state* s) {
+  SortScratch sc;
+  sc.hist = s->hist;
+  sc.hist_host = s->hist_host;
+  sc.lookback = s->lookback;
+  sc.lookback_tiles = s->lb_entries / RADIX;
+  sc.tile_counter = s->tile_counter;
+  sc.err = &s->ctl->err;
+  return sc;
+}
+
+// Sort (sk[0], sidx[0]) on nbits bits; histograms are computed first unless
+// hist_ready.  Returns the buffer index holding the result.
+sv_status sort_pairs(sv_state* s, uint64_t n, int nbits, bool hist_ready, int* which, int* passes) {
+  if (!hist_ready) launch_digit_hist(s->sk[0], n, nbits, s->hist, s->st);
+  cudaMemcpyAsync(s->hist_host, s->hist, sizeof(uint32_t) * MAX_PASSES * RADIX, cudaMemcpyDeviceToHost,
+                  s->st);
+  sv_status rc = cuda_check(s, cudaStreamSynchronize(s->st), "digit histogram");
+  if (rc != SV_OK) return rc;
+  cudaError_t e;
+  *which = radix_sort_pairs(s->sk[0], s->sidx[0], s->sk[1], s->sidx[1], n, nbits, sort_scratch(s),
+                            s->st, passes, &e);
+  return cuda_check(s, e, "radix sort");
+}
+
+// Canonical order (probability descending, key ascending) of the current
+// state: the permutation ends in sidx[*which].
+sv_status canonical_perm(sv_state* s, int* which) {
+  uint64_t N = s->N;
+  sv_status rc = ensure_sort_cap(s, N);
+  if (rc != SV_OK) return rc;
+  launch_iota(s->sidx[0], N, s->st);
+  cudaMemcpyAsync(s->sk[0], s->keys[s->cur], N * 8, cudaMemcpyDeviceToDevice, s->st);
+  int w = 0, passes = 0;
+  rc = sort_pairs(s, N, s->n, false, &w, &passes);
+  if (rc != SV_OK) return rc;
+  // second, stable sort by ~prob_bits (ascending = probability descending)
+  launch_not_bits_gather(s->probs[s->cur], s->sidx[w], N, s->sk[1 - w], s->st);
+  launch_digit_hist(s->sk[1 - w], N, 63, s->hist, s->st);
+  cudaMemcpyAsync(s->hist_host, s->hist, sizeof(uint32_t) * MAX_PASSES * RADIX, cudaMemcpyDeviceToHost,
+                  s->st);
+  rc = cuda_check(s, cudaStreamSynchronize(s->st), "digit histogram");
+  if (rc != SV_OK) return rc;
+  cudaError_t e;
+  int w2 = radix_sort_pairs(s->sk[1 - w], s->sidx[w], s->sk[w], s->sidx[1 - w], N, 63,
+                            sort_scratch(s), s->st, &passes, &e);
+  rc = cuda_check(s, e, "radix sort");
+  if (rc != SV_OK) return rc;
+  // radix_sort_pairs returns 0 for (kA, vA) = (sk[1-w], sidx[w]) and 1 for (sk[w], sidx[1-w])
+  *which = (w2 == 0) ? w : 1 - w;
+  return SV_OK;
+}
+
+bool is_unitary(int m, const double* U) {
+  const int d = 1 << m;
+  for (int i = 0; i < 2 * d * d; ++i)
+    if (!std::isfinite(U[i])) return false;
+  double worst = 0.0;
+  for (int a = 0; a < d; ++a)
+    for (int b = 0; b < d; ++b) {
+      double re = 0.0, im = 0.0;  // (U^dagger U)[a][b] = sum_r conj(U[r][a]) U[r][b]
+      for (int r = 0; r < d; ++r) {
+        double ar = U[2 * (r * d + a)], ai = U[2 * (r * d + a) + 1];
+        double br = U[2 * (r * d + b)], bi = U[2 * (r * d + b) + 1];
+        re += ar * br + ai * bi;
+        im += ar * bi - ai * br;
+      }
+      if (a == b) re -= 1.0;
+      double v = std::fabs(re) > std::fabs(im) ? std::fabs(re) : std::fabs(im);
+      worst = v > worst ? v : worst;
+    }
+  return worst <= 1e-10;
+}
+
+double u128_to_double(uint64_t hi, uint64_t lo) {
+  unsigned __int128 v = ((unsigned __int128)hi << 64) | lo;
+  return std::ldexp((double)v, -120);
+}
+
+#define SV_GUARD(s)                                                    \
+  do {                                                                 \
+    if (!(s)) return SV_E_ARG;                                         \
+    if ((s)->broken) return fail((s), SV_E_STATE, "handle unusable after an earlier failure: " + (s)->err); \
+  } while (0)
+
+}  // namespace
+
+extern "C" {
+
+sv_status sv_create_ex(int n, uint64_t K, double p, int prec, void* cuda_stream,
+                       const sv_allocator* alloc, sv_state** out) {
+  if (!out) return SV_E_ARG;
+  *out = nullptr;
+  if (n < 1 || n > 64 || K < 1 || !(p > 0.0) || !(p <= 1.0) || (prec != SV_C128 && prec != SV_C64))
+    return SV_E_ARG;
+  if (alloc && (!alloc->alloc || !alloc->free)) return SV_E_ARG;
+  sv_state* s = new sv_state();
+  s->n = n;
+  s->K = K;
+  s->p = p;
+  s->prec = prec;
+  s->st = (cudaStream_t)cuda_stream;
+  s->amp_bytes = prec == SV_C128 ? 16 : 8;
+  if (alloc) {
+    s->alloc = *alloc;
+    s->custom_alloc = true;
+  }
+  sv_status rc = SV_OK;
+  s->hist = (uint32_t*)dev_alloc(s, sizeof(uint32_t) * MAX_PASSES * RADIX);
+  s->tile_counter = (uint64_t*)dev_alloc(s, 256);
+  s->ctl = (Ctl*)dev_alloc(s, sizeof(Ctl));
+  s->ss.hist_count = (uint32_t*)dev_alloc(s, sizeof(uint32_t) * SEL_BINS);
+  s->ss.hist_mass = (uint64_t*)dev_alloc(s, sizeof(uint64_t) * 2 * SEL_BINS);
+  s->ss.buf = (uint64_t*)dev_alloc(s, sizeof(uint64_t) * 2 * FINISH_CAP);
+  if (!s->hist || !s->tile_counter || !s->ctl || !s->ss.hist_count || !s->ss.hist_mass || !s->ss.buf)
+    rc = SV_E_NOMEM;
+  if (rc == SV_OK && (cudaMallocHost(&s->hist_host, sizeof(uint32_t) * MAX_PASSES * RADIX) != cudaSuccess ||
+                      cudaMallocHost(&s->ctl_host, sizeof(Ctl)) != cudaSuccess))
+    rc = SV_E_CUDA;
+  if (rc == SV_OK) rc = ensure_state_cap(s, 4096);
+  if (rc == SV_OK) rc = ensure_sort_cap(s, 4096);
+  if (rc == SV_OK) {
+    cudaMemsetAsync(s->ctl, 0, sizeof(Ctl), s->st);
+    const uint64_t zero_key = 0;
+    const double one[2] = {1.0, 0.0};
+    const float onef[2] = {1.0f, 0.0f};
+    const uint64_t one_bits = 0x3ff0000000000000ull;  // prob of 1+0i
+    cudaMemcpyAsync(s->keys[0], &zero_key, 8, cudaMemcpyHostToDevice, s->st);
+    cudaMemcpyAsync(s->amps[0], prec == SV_C128 ? (const void*)one : (const void*)onef, s->amp_bytes,
+                    cudaMemcpyHostToDevice, s->st);
+    cudaMemcpyAsync(s->probs[0], &one_bits, 8, cudaMemcpyHostToDevice, s->st);
+    rc = cuda_check(s, cudaStreamSynchronize(s->st), "sv_create");
+    s->N = 1;
+    s->cur = 0;
+  }
+  if (rc != SV_OK) {
+    sv_destroy(s);
+    return rc;
+  }
+  *out = s;
+  return SV_OK;
+}
+
+sv_status sv_create(int n, uint64_t K, double p, sv_state** out) {
+  return sv_create_ex(n, K, p, SV_C128, nullptr, nullptr, out);
+}
+
+sv_status sv_destroy(sv_state* s) {
+  if (!s) return SV_OK;
+  if (s->st) cudaStreamSynchronize(s->st);
+  else cudaDeviceSynchronize();
+  for (int i = 0; i < 2; ++i) {
+    dev_free(s, s->keys[i]);
+    dev_free(s, s->amps[i]);
+    dev_free(s, s->probs[i]);
+    dev_free(s, s->sk[i]);
+    dev_free(s, s->sidx[i]);
+  }
+  dev_free(s, s->heads);
+  dev_free(s, s->lookback);
+  dev_free(s, s->hist);
+  dev_free(s, s->tile_counter);
+  dev_free(s, s->ctl);
+  dev_free(s, s->ss.hist_count);
+  dev_free(s, s->ss.hist_mass);
+  dev_free(s, s->ss.buf);
+  if (s->hist_host) cudaFreeHost(s->hist_host);
+  if (s->ctl_host) cudaFreeHost(s->ctl_host);
+  delete s;
+  return SV_OK;
+}
+
+sv_status sv_apply_gate(sv_state* s, int m, const int* qubits, const double* U) {
+  SV_GUARD(s);
+  if (m < 1 || m > 4 || !qubits || !U) return fail(s, SV_E_ARG, "sv_apply_gate: bad m or null pointer");
+  GateParams gp;
+  std::memset(&gp, 0, sizeof(gp));
+  gp.m = m;
+  gp.n_mask = s->n == 64 ? ~0ull : ((1ull << s->n) - 1);
+  for (int t = 0; t < m; ++t) {
+    if (qubits[t] < 0 || qubits[t] >= s->n) return fail(s, SV_E_ARG, "sv_apply_gate: qubit out of range");
+    if (gp.qmask & (1ull << qubits[t])) return fail(s, SV_E_ARG, "sv_apply_gate: repeated qubit");
+    gp.qmask |= 1ull << qubits[t];
+    gp.q[t] = qubits[t];
+    gp.qs[t] = qubits[t];
+  }
+  for (int a = 0; a < m; ++a)  // ascending copy
+    for (int b = a + 1; b < m; ++b)
+      if (gp.qs[b] < gp.qs[a]) {
+        int t = gp.qs[a];
+        gp.qs[a] = gp.qs[b];
+        gp.qs[b] = t;
+      }
+  if (!is_unitary(m, U)) return fail(s, SV_E_NOT_UNITARY, "sv_apply_gate: U is not unitary within 1e-10");
+  const int d = 1 << m;
+  for (int ro = 0; ro < d; ++ro)
+    for (int r = 0; r < d; ++r) {
+      double ur = U[2 * (ro * d + r)], ui = U[2 * (ro * d + r) + 1];
+      gp.U[2 * (ro * d + r)] = ur;
+      gp.U[2 * (ro * d + r) + 1] = ui;
+      // complex64: the zero pattern is that of the float-rounded entries
+      bool rz = s->prec == SV_C128 ? ur != 0.0 : (float)ur != 0.0f;
+      bool iz = s->prec == SV_C128 ? ui != 0.0 : (float)ui != 0.0f;
+      if (rz) gp.re_nz[ro] |= 1u << r;
+      if (iz) gp.im_nz[ro] |= 1u << r;
+    }
+  const uint64_t N = s->N;
+  s->stats.n_in = N;
+  s->stats.sort_passes = 0;
+  if (N == 0) {
+    s->stats.n_pre = 0;
+    return SV_OK;
+  }
+  if (N > MAX_TERMS || (N << m) > MAX_TERMS * 16ull)
+    return fail(s, SV_E_ARG, "sv_apply_gate: state too large for 32-bit term indices");
+  sv_status rc = ensure_state_cap(s, N << m);
+  if (rc == SV_OK) rc = ensure_sort_cap(s, N);
+  const uint64_t apply_tiles = ((N << m) + 1023) / 1024 + 1;
+  if (rc == SV_OK) rc = ensure_lookback(s, apply_tiles + 16);
+  if (rc != SV_OK) return rc;
+  const int passes = (s->n + RADIX_BITS - 1) / RADIX_BITS;
+  launch_gate_keys(s->keys[s->cur], N, gp, s->sk[0], s->sidx[0], s->hist, passes, s->st);
+  int w = 0, run = 0;
+  rc = sort_pairs(s, N, s->n, true, &w, &run);
+  if (rc != SV_OK) return rc;
+  s->stats.sort_passes = (uint32_t)run;
+  const int alt = 1 - s->cur;
+  launch_group_heads(s->sk[w], N, m, s->heads, s->lookback, s->ctl, s->st);
+  launch_gate_apply(s->prec, s->sk[w], s->sidx[w], N, s->heads, s->amps[s->cur], gp, s->keys[alt],
+                    s->amps[alt], s->probs[alt], s->lookback, s->ctl, s->st, apply_tiles);
+  rc = sync_ctl(s, "sv_apply_gate");
+  if (rc != SV_OK) return rc;
+  s->cur = alt;
+  s->N = s->ctl_host->count[1];
+  s->stats.n_pre = s->N;
+  return SV_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Radix select of the cut; leaves the result in s->ctl_host.
+sv_status run_select(sv_state* s, int mode, uint64_t count_target, uint32_t* levels) {
+  const uint64_t N = s->N;
+  launch_select_init(s->ctl, mode, count_target, s->st);
+  for (int level = 0; level < 16; ++level) {
+    launch_select_hist(s->probs[s->cur], s->keys[s->cur], N, s->ctl, s->ss, s->st);
+    launch_select_pick(s->ctl, s->ss, s->p, s->st);
+    ++*levels;
+    sv_status rc = sync_ctl(s, "truncation select");
+    if (rc != SV_OK) return rc;
+    if (s->ctl_host->sel_done) return SV_OK;
+    if (s->ctl_host->sel_bin_count <= (uint64_t)FINISH_CAP) {
+      launch_select_compact(s->probs[s->cur], s->keys[s->cur], N, s->ctl, s->ss, s->st);
+      launch_select_finish(s->ctl, s->ss, s->p, s->st);
+      rc = sync_ctl(s, "truncation select");
+      if (rc != SV_OK) return rc;
+      if (!s->ctl_host->sel_done) {
+        s->broken = true;
+        return fail(s, SV_E_STATE, "truncation select did not resolve");
+      }
+      return SV_OK;
+    }
+  }
+  s->broken = true;
+  return fail(s, SV_E_STATE, "truncation select did not resolve");
+}
+
+}  // namespace
+
+extern "C" {
+
+sv_status sv_truncate(sv_state* s, uint64_t* kept, double* retained_fraction) {
+  SV_GUARD(s);
+  const uint64_t N = s->N;
+  s->stats.select_levels = 0;
+  s->stats.n_kept = N;
+  s->stats.total_mass = s->stats.kept_mass = 0.0;
+  const bool need_p = s->p < 1.0, need_k = N > s->K;
+  double f = 1.0;
+  if (N > 0 && (need_p || need_k)) {
+    uint64_t c = N;
+    bool have_cut = false;
+    sv_status rc;
+    if (need_p) {
+      rc = run_select(s, 0, 0, &s->stats.select_levels);
+      if (rc != SV_OK) return rc;
+      if (s->ctl_host->sel_done == 1) {
+        c = s->ctl_host->cut_count;
+        have_cut = true;
+      }
+    }
+    if (c > s->K) {
+      rc = run_select(s, 1, s->K, &s->stats.select_levels);
+      if (rc != SV_OK) return rc;
+      if (s->ctl_host->sel_done != 1) {
+        s->broken = true;
+        return fail(s, SV_E_STATE, "top-k select found no cut");
+      }
+      c = s->ctl_host->cut_count;
+      have_cut = true;
+    }
+    double SN = u128_to_double(s->ctl_host->total_mass_hi, s->ctl_host->total_mass_lo);
+    s->stats.total_mass = SN;
+    s->stats.kept_mass = SN;
+    if (have_cut && c < N) {
+      const int alt = 1 - s->cur;
+      rc = ensure_lookback(s, (N + 1023) / 1024 + 16);
+      if (rc != SV_OK) return rc;
+      launch_set_scale(s->ctl, s->st);
+      launch_truncate_compact(s->prec, s->keys[s->cur], s->amps[s->cur], s->probs[s->cur], N,
+                              s->keys[alt], s->amps[alt], s->probs[alt], s->lookback, s->ctl, s->st);
+      rc = sync_ctl(s, "sv_truncate");
+      if (rc != SV_OK) return rc;
+      if (s->ctl_host->count[2] != c) {
+        s->broken = true;
+        return fail(s, SV_E_STATE, "truncation kept an unexpected number of terms");
+      }
+      double Sc = u128_to_double(s->ctl_host->cut_mass_hi, s->ctl_host->cut_mass_lo);
+      f = Sc / SN;
+      s->F = s->F * f;
+      s->cur = alt;
+      s->N = c;
+      s->stats.kept_mass = Sc;
+    }
+  }
+  s->stats.n_kept = s->N;
+  if (kept) *kept = s->N;
+  if (retained_fraction) *retained_fraction = f;
+  return SV_OK;
+}
+
+sv_status sv_peak(sv_state* s, uint64_t* key, double* prob) {
+  SV_GUARD(s);
+  if (!key || !prob) return fail(s, SV_E_ARG, "sv_peak: null output");
+  if (s->N == 0) return fail(s, SV_E_STATE, "sv_peak: empty state");
+  launch_peak(s->probs[s->cur], s->keys[s->cur], s->N, s->ctl, s->st);
+  sv_status rc = sync_ctl(s, "sv_peak");
+  if (rc != SV_OK) return rc;
+  *key = s->ctl_host->peak_z_lo;
+  uint64_t b = s->ctl_host->peak_z_hi;
+  std::memcpy(prob, &b, 8);
+  return SV_OK;
+}
+
+sv_status sv_num_terms(sv_state* s, uint64_t* N) {
+  SV_GUARD(s);
+  if (!N) return SV_E_ARG;
+  *N = s->N;
+  return SV_OK;
+}
+
+sv_status sv_retained_mass(sv_state* s, double* F) {
+  SV_GUARD(s);
+  if (!F) return SV_E_ARG;
+  *F = s->F;
+  return SV_OK;
+}
+
+static sv_status dump(sv_state* s, uint64_t* keys, double* amps, double* probs, uint64_t cap,
+                      uint64_t* count) {
+  SV_GUARD(s);
+  if (!count) return fail(s, SV_E_ARG, "null count");
+  const uint64_t N = s->N;
+  *count = N;
+  const uint64_t w = cap < N ? cap : N;
+  if (w == 0) return SV_OK;
+  int which = 0;
+  sv_status rc = canonical_perm(s, &which);
+  if (rc != SV_OK) return rc;
+  uint64_t* dk = nullptr;
+  double* da = nullptr;
+  uint64_t* dp = nullptr;
+  const int alt = 1 - s->cur;
+  if (keys) dk = s->keys[alt];
+  if (probs) dp = s->probs[alt];
+  void* tmp = nullptr;
+  if (amps) {
+    tmp = dev_alloc(s, w * 16);
+    if (!tmp) return fail(s, SV_E_NOMEM, "export buffer allocation failed");
+    da = (double*)tmp;
+  }
+  launch_gather_terms(s->prec, s->sidx[which], w, s->keys[s->cur], s->amps[s->cur], s->probs[s->cur],
+                      dk, da, dp, s->st);
+  if (dk) cudaMemcpyAsync(keys, dk, w * 8, cudaMemcpyDeviceToHost, s->st);
+  if (dp) cudaMemcpyAsync(probs, dp, w * 8, cudaMemcpyDeviceToHost, s->st);
+  if (da) cudaMemcpyAsync(amps, da, w * 16, cudaMemcpyDeviceToHost, s->st);
+  rc = cuda_check(s, cudaStreamSynchronize(s->st), "export");
+  if (tmp) dev_free(s, tmp);
+  return rc;
+}
+
+sv_status sv_probs(sv_state* s, uint64_t* keys, double* probs, uint64_t cap, uint64_t* count) {
+  return dump(s, keys, nullptr, probs, cap, count);
+}
+
+sv_status sv_export(sv_state* s, uint64_t* keys, double* amps, uint64_t cap, uint64_t* count) {
+  return dump(s, keys, amps, nullptr, cap, count);
+}
+
+sv_status sv_load(sv_state* s, const uint64_t* keys, const double* amps, uint64_t N) {
+  SV_GUARD(s);
+  if (N > 0 && (!keys || !amps)) return fail(s, SV_E_ARG, "sv_load: null input");
+  if (N > MAX_TERMS) return fail(s, SV_E_ARG, "sv_load: too many terms");
+  if (s->n < 64)
+    for (uint64_t i = 0; i < N; ++i)
+      if (keys[i] >> s->n) return fail(s, SV_E_ARG, "sv_load: key outside n bits");
+  sv_status rc = ensure_state_cap(s, N);
+  if (rc == SV_OK) rc = ensure_sort_cap(s, N);
+  if (rc == SV_OK) rc = ensure_lookback(s, (N + 1023) / 1024 + 16);
+  if (rc != SV_OK) return rc;
+  if (N == 0) {
+    s->N = 0;
+    return SV_OK;
+  }
+  double* tmp = (double*)dev_alloc(s, N * 16);
+  if (!tmp) return fail(s, SV_E_NOMEM, "sv_load: staging allocation failed");
+  cudaMemcpyAsync(s->sk[0], keys, N * 8, cudaMemcpyHostToDevice, s->st);
+  cudaMemcpyAsync(tmp, amps, N * 16, cudaMemcpyHostToDevice, s->st);
+  launch_iota(s->sidx[0], N, s->st);
+  int w = 0, passes = 0;
+  rc = sort_pairs(s, N, s->n, false, &w, &passes);
+  if (rc != SV_OK) {
+    dev_free(s, tmp);
+    return rc;
+  }
+  const int alt = 1 - s->cur;
+  launch_load_compact(s->prec, s->sk[w], s->sidx[w], N, tmp, s->keys[alt], s->amps[alt], s->probs[alt],
+                      s->lookback, s->ctl, s->st);
+  rc = sync_ctl(s, "sv_load");
+  dev_free(s, tmp);
+  if (rc != SV_OK) return rc;
+  if (s->ctl_host->count[3] != 0) return fail(s, SV_E_ARG, "sv_load: duplicate keys");
+  s->cur = alt;
+  s->N = s->ctl_host->count[2];
+  return SV_OK;
+}
+
+const char* sv_last_error(const sv_state* s) {
+  if (!s) return "null handle";
+  return s->err.c_str();
+}
+
+sv_status sv_last_stats(const sv_state* s, sv_stats* out) {
+  if (!s || !out) return SV_E_ARG;
+  *out = s->stats;
+  return SV_OK;
+}
+
+}  // extern "C"

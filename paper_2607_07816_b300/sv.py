@@ -1,0 +1,249 @@
+"""Thin Python binding of libsv.so (C ABI in include/sv.h).
+
+Argument marshalling only: every step of gate application, truncation and
+readout runs in the library's CUDA kernels.  The module-level functions carry
+the C names (``sv_create``, ``sv_apply_gate``, ...); ``SparseState`` wraps a
+handle for convenience.  There is no fallback: if the library cannot be
+loaded, or no CUDA device is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+SV_OK, SV_E_ARG, SV_E_NOMEM, SV_E_CUDA, SV_E_NOT_UNITARY, SV_E_TIMEOUT, SV_E_STATE = 0, -1, -2, -3, -4, -5, -6
+SV_C128, SV_C64 = 0, 1
+_STATUS = {0: "SV_OK", -1: "SV_E_ARG", -2: "SV_E_NOMEM", -3: "SV_E_CUDA", -4: "SV_E_NOT_UNITARY",
+           -5: "SV_E_TIMEOUT", -6: "SV_E_STATE"}
+
+EXPORTED = ["sv_create", "sv_create_ex", "sv_destroy", "sv_apply_gate", "sv_truncate", "sv_peak",
+            "sv_probs", "sv_num_terms", "sv_retained_mass", "sv_export", "sv_load", "sv_last_error",
+            "sv_last_stats"]
+
+
+class SVError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class sv_allocator(ctypes.Structure):
+    _fields_ = [("alloc", ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)),
+                ("free", ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)),
+                ("ctx", ctypes.c_void_p)]
+
+
+class sv_stats(ctypes.Structure):
+    _fields_ = [("n_in", ctypes.c_uint64), ("n_pre", ctypes.c_uint64), ("n_kept", ctypes.c_uint64),
+                ("sort_passes", ctypes.c_uint32), ("select_levels", ctypes.c_uint32),
+                ("total_mass", ctypes.c_double), ("kept_mass", ctypes.c_double)]
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libsv.so from the package directory (building it when absent)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise OSError(f"libsv.so not found at {path}")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    P, u64, i32, dbl, vp = ctypes.POINTER, ctypes.c_uint64, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+    lib.sv_create.restype = i32
+    lib.sv_create.argtypes = [i32, u64, dbl, P(vp)]
+    lib.sv_create_ex.restype = i32
+    lib.sv_create_ex.argtypes = [i32, u64, dbl, i32, vp, P(sv_allocator), P(vp)]
+    lib.sv_destroy.restype = i32
+    lib.sv_destroy.argtypes = [vp]
+    lib.sv_apply_gate.restype = i32
+    lib.sv_apply_gate.argtypes = [vp, i32, P(ctypes.c_int), P(dbl)]
+    lib.sv_truncate.restype = i32
+    lib.sv_truncate.argtypes = [vp, P(u64), P(dbl)]
+    lib.sv_peak.restype = i32
+    lib.sv_peak.argtypes = [vp, P(u64), P(dbl)]
+    lib.sv_probs.restype = i32
+    lib.sv_probs.argtypes = [vp, vp, vp, u64, P(u64)]
+    lib.sv_num_terms.restype = i32
+    lib.sv_num_terms.argtypes = [vp, P(u64)]
+    lib.sv_retained_mass.restype = i32
+    lib.sv_retained_mass.argtypes = [vp, P(dbl)]
+    lib.sv_export.restype = i32
+    lib.sv_export.argtypes = [vp, vp, vp, u64, P(u64)]
+    lib.sv_load.restype = i32
+    lib.sv_load.argtypes = [vp, vp, vp, u64]
+    lib.sv_last_error.restype = ctypes.c_char_p
+    lib.sv_last_error.argtypes = [vp]
+    lib.sv_last_stats.restype = i32
+    lib.sv_last_stats.argtypes = [vp, P(sv_stats)]
+    _lib = lib
+    return lib
+
+
+def _check(h, rc: int) -> None:
+    if rc != SV_OK:
+        msg = _lib.sv_last_error(h).decode() if h else ""
+        raise SVError(rc, msg)
+
+
+def _u_buffer(u) -> np.ndarray:
+    u = np.ascontiguousarray(np.asarray(u, dtype=np.complex128))
+    return np.ascontiguousarray(u.view(np.float64).reshape(-1))
+
+
+# ------------------------------------------------ C-named thin wrappers
+def sv_create(n: int, K: int, p: float) -> int:
+    lib = load_library()
+    h = ctypes.c_void_p()
+    _check(None, lib.sv_create(n, ctypes.c_uint64(K), p, ctypes.byref(h)))
+    return h.value
+
+
+def sv_create_ex(n: int, K: int, p: float, prec: int = SV_C128, stream: int = 0) -> int:
+    lib = load_library()
+    h = ctypes.c_void_p()
+    _check(None, lib.sv_create_ex(n, ctypes.c_uint64(K), p, prec, ctypes.c_void_p(stream), None,
+                                  ctypes.byref(h)))
+    return h.value
+
+
+def sv_destroy(h: int) -> None:
+    _check(h, load_library().sv_destroy(ctypes.c_void_p(h)))
+
+
+def sv_apply_gate(h: int, qubits: Sequence[int], u) -> None:
+    lib = load_library()
+    m = len(qubits)
+    q = (ctypes.c_int * m)(*[int(x) for x in qubits])
+    ub = _u_buffer(u)
+    _check(h, lib.sv_apply_gate(ctypes.c_void_p(h), m, q, ub.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+
+
+def sv_truncate(h: int):
+    kept, f = ctypes.c_uint64(), ctypes.c_double()
+    _check(h, load_library().sv_truncate(ctypes.c_void_p(h), ctypes.byref(kept), ctypes.byref(f)))
+    return kept.value, f.value
+
+
+def sv_peak(h: int):
+    k, p = ctypes.c_uint64(), ctypes.c_double()
+    _check(h, load_library().sv_peak(ctypes.c_void_p(h), ctypes.byref(k), ctypes.byref(p)))
+    return k.value, p.value
+
+
+def sv_num_terms(h: int) -> int:
+    n = ctypes.c_uint64()
+    _check(h, load_library().sv_num_terms(ctypes.c_void_p(h), ctypes.byref(n)))
+    return n.value
+
+
+def sv_retained_mass(h: int) -> float:
+    f = ctypes.c_double()
+    _check(h, load_library().sv_retained_mass(ctypes.c_void_p(h), ctypes.byref(f)))
+    return f.value
+
+
+def sv_probs(h: int, cap: Optional[int] = None):
+    n = sv_num_terms(h) if cap is None else cap
+    keys = np.zeros(n, dtype=np.uint64)
+    probs = np.zeros(n, dtype=np.float64)
+    cnt = ctypes.c_uint64()
+    _check(h, load_library().sv_probs(ctypes.c_void_p(h), keys.ctypes.data, probs.ctypes.data,
+                                      ctypes.c_uint64(n), ctypes.byref(cnt)))
+    w = min(n, cnt.value)
+    return keys[:w], probs[:w]
+
+
+def sv_export(h: int):
+    n = sv_num_terms(h)
+    keys = np.zeros(n, dtype=np.uint64)
+    amps = np.zeros(2 * n, dtype=np.float64)
+    cnt = ctypes.c_uint64()
+    _check(h, load_library().sv_export(ctypes.c_void_p(h), keys.ctypes.data, amps.ctypes.data,
+                                       ctypes.c_uint64(n), ctypes.byref(cnt)))
+    return keys, amps.view(np.complex128)
+
+
+def sv_load(h: int, keys, amps) -> None:
+    keys = np.ascontiguousarray(keys, dtype=np.uint64)
+    a = np.ascontiguousarray(np.asarray(amps, dtype=np.complex128)).view(np.float64)
+    _check(h, load_library().sv_load(ctypes.c_void_p(h), keys.ctypes.data, a.ctypes.data,
+                                     ctypes.c_uint64(len(keys))))
+
+
+def sv_last_error(h: int) -> str:
+    return load_library().sv_last_error(ctypes.c_void_p(h)).decode()
+
+
+def sv_last_stats(h: int) -> dict:
+    st = sv_stats()
+    _check(h, load_library().sv_last_stats(ctypes.c_void_p(h), ctypes.byref(st)))
+    return {f: getattr(st, f) for f, _ in sv_stats._fields_}
+
+
+# ------------------------------------------------ convenience wrapper
+class SparseState:
+    """A device-resident sparse state: keys u64, amplitudes complex128
+    (``prec=SV_C128``) or complex64 with FP64 mass (``prec=SV_C64``)."""
+
+    def __init__(self, n: int, K: int = 1 << 62, p: float = 1.0, prec: int = SV_C128, stream: int = 0):
+        self.n, self.K, self.p, self.prec = n, int(K), float(p), prec
+        self.h = sv_create_ex(n, int(K), float(p), prec, stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            sv_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def apply_gate(self, qubits, u):
+        sv_apply_gate(self.h, qubits, u)
+
+    def truncate(self):
+        return sv_truncate(self.h)
+
+    def peak(self):
+        return sv_peak(self.h)
+
+    def num_terms(self) -> int:
+        return sv_num_terms(self.h)
+
+    def retained_mass(self) -> float:
+        return sv_retained_mass(self.h)
+
+    def probs(self):
+        return sv_probs(self.h)
+
+    def export(self):
+        return sv_export(self.h)
+
+    def load(self, keys, amps):
+        sv_load(self.h, keys, amps)
+
+    def stats(self) -> dict:
+        return sv_last_stats(self.h)
+
+    def run(self, gates, truncate: bool = True):
+        for (q, u) in gates:
+            self.apply_gate(q, u)
+            if truncate:
+                self.truncate()
+        return self

@@ -1,0 +1,195 @@
+"""CUDA path (through the C ABI) against the CPU oracle, element by element.
+
+With the same operation order on both sides (fused multiply-adds in
+ascending input order, exact fixed-point masses, correctly rounded sqrt and
+division), the kept key sets and the amplitudes are expected to be identical,
+so these tests compare exactly.  They cover several tiles with ragged tails,
+every gate width m = 1..4, exact ties in probability, p-cuts landing on a
+prefix sum, top-k and p-mass together, and both precisions.
+"""
+import numpy as np
+import pytest
+
+from paper_2607_07816_b300 import circuits as C
+from tests.parity import assert_states_equal, run_both
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sv():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2607_07816_b300 import sv as _sv
+    _sv.load_library()
+    return _sv
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_exact_mirror_n12(sv, oracle_mod, prec):
+    c = C.exact_mirror_n12()
+    g = sv.SparseState(c.n, c.K, c.p, prec=prec)
+    o = oracle_mod.Oracle(c.n, c.K, c.p, prec=prec)
+    run_both(c.gates, g, o)
+    key, pr = g.peak()
+    assert key == c.hidden
+    assert pr > 1.0 - (1e-12 if prec == 0 else 1e-5)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_random_gates_topk_and_pmass(sv, oracle_mod, seed):
+    rng = np.random.default_rng(500 + seed)
+    n = int(rng.integers(6, 21))
+    K = int(rng.choice([7, 100, 1000, 5000, 1 << 20]))
+    p = float(rng.choice([1.0, 0.999, 0.95, 0.5]))
+    prec = int(seed % 2)
+    gates = []
+    for _ in range(24):
+        m = int(rng.integers(1, min(4, n) + 1))
+        kind = str(rng.choice(["haar", "haar", "mcx", "h"]))
+        gates.append(C.random_gate(n, m, rng, kind))
+    g = sv.SparseState(n, K, p, prec=prec)
+    o = oracle_mod.Oracle(n, K, p, prec=prec)
+    run_both(gates, g, o)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_ragged_multi_tile_states(sv, oracle_mod, prec):
+    """Loaded states of 1..~70k terms on 30 qubits: many sort and
+    compaction tiles, ragged tails, all gate widths."""
+    rng = np.random.default_rng(77 + prec)
+    for count in [1, 2, 1023, 4097, 9000, 70001]:
+        n = 30
+        keys, amps = C.random_state(n, count, rng)
+        K = max(1, count // 3)
+        g = sv.SparseState(n, K, 0.97, prec=prec)
+        o = oracle_mod.Oracle(n, K, 0.97, prec=prec)
+        g.load(keys, amps)
+        o.load(keys, amps)
+        assert_states_equal(g, o, what=f"load {count}")
+        gates = [C.random_gate(n, m, rng, "haar") for m in (1, 2, 3, 4)]
+        run_both(gates, g, o)
+
+
+def test_equal_probabilities_cut_by_key(sv, oracle_mod):
+    n = 12
+    for K in [1, 5, 1000, 4095]:
+        g = sv.SparseState(n, K, 1.0)
+        o = oracle_mod.Oracle(n, K, 1.0)
+        gates = [((i,), C.mat_h()) for i in range(n)]
+        for (q, u) in gates:
+            g.apply_gate(q, u)
+            o.apply_gate(q, u)
+        assert g.num_terms() == 1 << n
+        assert g.truncate() == o.truncate()
+        assert_states_equal(g, o, what=f"K={K}")
+
+
+def test_p_cut_on_exact_prefix_and_forced_ties(sv, oracle_mod):
+    keys = np.array([5, 9, 2, 7, 11, 3], dtype=np.uint64)
+    amps = np.array([0.5 + 0.5j, 0.5, 0.25 + 0.25j, -0.25 + 0.25j, 0.0625, 0.0625j])
+    for p in [0.75, 0.75 + 1e-12, 0.5, 0.875, 0.999, 1e-300]:
+        for K in [1, 3, 100]:
+            g = sv.SparseState(4, K, p)
+            o = oracle_mod.Oracle(4, K, p)
+            g.load(keys, amps)
+            o.load(keys, amps)
+            assert g.truncate() == o.truncate(), (p, K)
+            assert_states_equal(g, o, what=f"p={p} K={K}")
+
+
+def test_tied_random_states(sv, oracle_mod):
+    rng = np.random.default_rng(11)
+    for trial in range(6):
+        keys, amps = C.random_state(24, 20000, rng, ties=True)
+        K = int(rng.integers(1, 20000))
+        p = float(rng.uniform(0.3, 1.0))
+        g = sv.SparseState(24, K, p)
+        o = oracle_mod.Oracle(24, K, p)
+        g.load(keys, amps)
+        o.load(keys, amps)
+        assert g.truncate() == o.truncate()
+        assert_states_equal(g, o, what=f"trial {trial}")
+
+
+def test_structured_gates_keep_count(sv, oracle_mod):
+    rng = np.random.default_rng(5)
+    keys, amps = C.random_state(20, 3000, rng)
+    g = sv.SparseState(20)
+    g.load(keys, amps)
+    for m in (2, 3, 4):
+        for _ in range(3):
+            qs = tuple(int(x) for x in rng.choice(20, size=m, replace=False))
+            g.apply_gate(qs, C.mat_mcx(m))
+            assert g.num_terms() == 3000
+    g.apply_gate((0, 19), C.mat_cz())
+    assert g.num_terms() == 3000
+
+
+def test_random_mix_circuit_n60(sv, oracle_mod):
+    c = C.random_mix_circuit(60, 60, seed=9, sigma=0.05, K=2000, p=0.9999)
+    for prec in (0, 1):
+        g = sv.SparseState(c.n, c.K, c.p, prec=prec)
+        o = oracle_mod.Oracle(c.n, c.K, c.p, prec=prec)
+        run_both(c.gates, g, o, check_every=False)
+
+
+def test_brickwork_n40_reduced_K(sv, oracle_mod):
+    c = C.brickwork_n40(layers=3, K=1 << 12)
+    g = sv.SparseState(c.n, c.K, c.p)
+    o = oracle_mod.Oracle(c.n, c.K, c.p)
+    run_both(c.gates, g, o, check_every=False)
+
+
+def test_complex64_close_to_complex128(sv, oracle_mod):
+    c = C.brickwork_circuit(16, 4, seed=3, sigma=0.05, K=1 << 10, p=1.0)
+    g64 = sv.SparseState(c.n, c.K, c.p, prec=1)
+    o128 = oracle_mod.Oracle(c.n, c.K, c.p, prec=0)
+    g64.run(c.gates)
+    o128.run(c.gates)
+    assert g64.peak()[0] == o128.peak()[0]
+    gk, ga = g64.export()
+    ok, oa, _ = o128.export()
+    common, gi, oi = np.intersect1d(gk, ok, return_indices=True)
+    assert len(common) > 0.9 * len(ok)
+    assert np.max(np.abs(ga[gi] - oa[oi])) <= 2e-6
+
+
+def test_argument_errors(sv):
+    g = sv.SparseState(5)
+    with pytest.raises(sv.SVError) as e:
+        g.apply_gate((0, 0), np.eye(4))
+    assert e.value.status == sv.SV_E_ARG
+    with pytest.raises(sv.SVError) as e:
+        g.apply_gate((7,), np.eye(2))
+    assert e.value.status == sv.SV_E_ARG
+    with pytest.raises(sv.SVError) as e:
+        g.apply_gate((1,), np.array([[1, 1], [0, 1]]))
+    assert e.value.status == sv.SV_E_NOT_UNITARY
+    with pytest.raises(sv.SVError) as e:
+        g.load(np.array([1, 1], dtype=np.uint64), np.array([0.6, 0.8]))
+    assert e.value.status == sv.SV_E_ARG
+    with pytest.raises(sv.SVError) as e:
+        g.load(np.array([32], dtype=np.uint64), np.array([1.0]))
+    assert e.value.status == sv.SV_E_ARG
+    # the handle is still usable after rejected arguments
+    g.apply_gate((1,), C.mat_h())
+    assert g.num_terms() == 2
+
+
+def test_probs_dump_and_export_roundtrip(sv, oracle_mod):
+    rng = np.random.default_rng(3)
+    keys, amps = C.random_state(33, 5000, rng, ties=True)
+    g = sv.SparseState(33, prec=0)
+    o = oracle_mod.Oracle(33)
+    g.load(keys, amps)
+    o.load(keys, amps)
+    pk, pp = g.probs()
+    ok, _, op = o.export()
+    assert np.array_equal(pk, ok)
+    assert np.array_equal(pp, op)
+    ek, ea = g.export()
+    g2 = sv.SparseState(33)
+    g2.load(ek, ea)
+    assert_states_equal(g2, o, what="reload")
