@@ -1,0 +1,421 @@
+#!/usr/bin/env python
+"""Benchmark: sparse-gate terms/s and HBM / FP64 roofline fraction.
+
+Workload: the n=40 brickwork peaked circuit (8 layers of Haar SU(4) on
+neighbouring pairs, the perturbed mirror with theta ~ N(0, 0.05), X on the
+hidden string), top-K truncation to K = 2^24 terms after every gate, p = 1.
+One step = apply the next gate + truncate + read the peak, on the state
+already at K terms (the whole hot path: key transform, grouping sort, group
+mat-vec with zero drop, select, renormalising compaction, argmax).
+
+value   : sum of input terms over the timed steps / device time of the steps
+          (CUDA events on the library's stream; state resident in HBM and
+          larger than L2, so no flush is needed).
+e2e     : the same metric for the whole circuit run through the C ABI from
+          the host (create, every gate with its matrix copied from host
+          memory, every truncation, the peak read back), host wall clock.
+roofline: the dominant kernel's algorithmic bytes (or FP64 flops) per launch
+          over its CUDA-event launch time, against MEASURED_PEAKS.json.
+
+--impl reference times the CPU oracle (test infrastructure, the only
+reference that exists for this paper) on a bounded sample of the workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_QUBITS, K_TERMS, LAYERS, SEED = 40, 1 << 24, 8, 1002
+SM_COUNT, FP64_FMA_PER_SM_CLK = 148, 2      # B300 FP64: 2 DFMA / SM / clock (probe: 0.56 TFMA/s @ 1.94 GHz)
+WORKLOAD = "n40 brickwork Haar-SU(4) x8 + perturbed mirror + X^s, top-K 2^24 per gate, p=1"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="c128", choices=["c128", "c64"])
+    ap.add_argument("--K", type=int, default=K_TERMS)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-c64", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "src": "measured", "sm_max_mhz": float(d.get("sm_max_mhz", 2032))}
+    return {"hbm_gbs": 6400.0, "src": "fallback", "sm_max_mhz": 2032.0}
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"sv_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ roofline
+def phase_model(ph: str, totals: dict, prec: str, passes: int):
+    """Algorithmic bytes and FP64 flops of one phase over the timed steps.
+    S_a = amplitude bytes; per term: key 8 B, probability 8 B."""
+    sa = 16 if prec == "c128" else 8
+    n_in, n_pre, n_kept = totals["n_in"], totals["n_pre"], totals["n_kept"]
+    if ph == "sort":     # each pass reads and writes (sort key 8 B + index 4 B)
+        return {"bytes": passes * 24 * n_in, "flops": 0.0}
+    if ph == "keys":     # read key, write sort key + index
+        return {"bytes": 20 * n_in, "flops": 0.0}
+    if ph == "apply":    # read sorted key + index + amplitude per input; write key+amp+prob per candidate
+        return {"bytes": (12 + sa) * n_in + (16 + sa) * n_pre, "flops": totals["dfma"] * 2.0}
+    if ph == "select":   # each histogram level reads the probabilities
+        return {"bytes": 8 * n_pre * max(1, totals["select_levels"]) / max(1, totals["steps"]), "flops": 0.0}
+    if ph == "compact":  # read prob (+ key, amp of kept); write kept key, amp, prob
+        return {"bytes": 8 * n_pre + (8 + sa) * n_kept + (16 + sa) * n_kept, "flops": 0.0}
+    if ph == "peak":
+        return {"bytes": 8 * n_kept, "flops": 0.0}
+    if ph == "heads":
+        return {"bytes": 8 * n_in, "flops": 0.0}
+    return {"bytes": 0.0, "flops": 0.0}
+
+
+def dense_dfma_per_gate(m: int, n_in: int) -> float:
+    # every input term meets 2^m outputs, 4 fused multiply-adds each, plus
+    # the probability (2 ops) of every candidate (counted by the caller)
+    return n_in * (1 << m) * 4.0
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+    from paper_2607_07816_b300 import circuits as C
+    from paper_2607_07816_b300 import sv
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    sv.load_library()
+    peaks = measured_peaks()
+
+    def run_prec(prec_name, K, steps, warmup, sample_clocks):
+        prec = sv.SV_C128 if prec_name == "c128" else sv.SV_C64
+        circ = C.brickwork_n40(seed=SEED + rank, layers=LAYERS, K=K)
+        gates = circ.gates
+        st = sv.SparseState(circ.n, K, 1.0, prec=prec, stream=stream.cuda_stream)
+        gi = 0
+        # ramp: run until the state is at K terms
+        while gi < len(gates) and st.num_terms() < K:
+            q, u = gates[gi]
+            st.apply_gate(q, u)
+            st.truncate()
+            gi += 1
+        for _ in range(warmup):
+            q, u = gates[gi % len(gates)]
+            st.apply_gate(q, u)
+            st.truncate()
+            st.peak()
+            gi += 1
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
+        st.set_timing(True)
+        totals = {"n_in": 0, "n_pre": 0, "n_kept": 0, "dfma": 0.0, "select_levels": 0, "steps": steps,
+                  "sort_passes": 0}
+        clocks = ClockSampler(dev.index) if sample_clocks else None
+        if clocks:
+            clocks.start()
+            time.sleep(0.3)
+        l0 = sv.sv_launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(steps):
+            q, u = gates[gi % len(gates)]
+            gi += 1
+            st.apply_gate(q, u)
+            s1 = st.stats()
+            st.truncate()
+            s2 = st.stats()
+            st.peak()
+            totals["n_in"] += s1["n_in"]
+            totals["n_pre"] += s1["n_pre"]
+            totals["n_kept"] += s2["n_kept"]
+            totals["sort_passes"] += s1["sort_passes"]
+            totals["select_levels"] += s2["select_levels"]
+            totals["dfma"] += dense_dfma_per_gate(len(q), s1["n_in"]) + 2.0 * s1["n_pre"] + 2.0 * s2["n_kept"]
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        launches = sv.sv_launch_count() - l0
+        ms = e0.elapsed_time(e1)
+        clk = clocks.stop() if clocks else None
+        phases = st.phase_times()
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        peak = st.peak()
+        st.close()
+        return {"ms": ms, "totals": totals, "phases": phases, "launches": launches, "clocks": clk,
+                "peak": peak, "hidden": circ.hidden}
+
+    main = run_prec(args.prec, args.K, args.steps, args.warmup, sample_clocks=True)
+    res = {"main": main}
+    if not args.no_c64 and args.prec == "c128":
+        res["c64"] = run_prec("c64", args.K, args.steps, args.warmup, sample_clocks=False)
+    if not args.no_e2e:
+        res["e2e"] = run_e2e(args, rank, dev, stream)
+    return res, peaks
+
+
+def run_e2e(args, rank, dev, stream):
+    import numpy as np
+    import torch
+    from paper_2607_07816_b300 import circuits as C
+    from paper_2607_07816_b300 import sv
+
+    circ = C.brickwork_n40(seed=SEED + rank, layers=LAYERS, K=args.K)
+    prec = sv.SV_C128 if args.prec == "c128" else sv.SV_C64
+    # host-resident inputs: the gate matrices in pinned host memory
+    pinned = [(q, torch.from_numpy(np.ascontiguousarray(u)).pin_memory().numpy()) for (q, u) in circ.gates]
+    torch.cuda.synchronize(dev)
+    h0, d0 = sv.sv_transfer_bytes()
+    t0 = time.perf_counter()
+    st = sv.SparseState(circ.n, args.K, 1.0, prec=prec, stream=stream.cuda_stream)
+    n_in = 0
+    for (q, u) in pinned:
+        n_in += st.num_terms()
+        st.apply_gate(q, u)
+        st.truncate()
+    key, pr = st.peak()
+    st.close()
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - t0
+    h1, d1 = sv.sv_transfer_bytes()
+    g = len(pinned)
+    return {"value": n_in / wall, "unit": "terms/s", "h2d_bytes_per_step": int((h1 - h0) / g),
+            "d2h_bytes_per_step": int((d1 - d0) / g), "wall_s": wall, "gates": g,
+            "peak_is_hidden": bool(key == circ.hidden), "peak_prob": pr}
+
+
+def roofline(main, prec, peaks):
+    tot = main["totals"]
+    phases = main["phases"]
+    dom = max((p for p in phases if p != "other"), key=lambda p: phases[p][0])
+    ms, launches = phases[dom]
+    per_launch_s = ms / 1e3 / max(1, launches)
+    passes = tot["sort_passes"] / max(1, tot["steps"])
+    model = phase_model(dom, tot, prec, passes if dom == "sort" else 1)
+    if dom == "sort":
+        bytes_per_launch = 24.0 * tot["n_in"] / max(1, tot["steps"])   # one pass over N_in
+    else:
+        bytes_per_launch = model["bytes"] / max(1, launches)
+    gbs = bytes_per_launch / per_launch_s / 1e9
+    hbm_frac = gbs / peaks["hbm_gbs"]
+    out = {"kernel": dom, "bound": "hbm", "achieved": round(gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+           "frac": round(hbm_frac, 4), "traffic": traffic_for(dom, bytes_per_launch),
+           "peak_src": f"{peaks['src']} copy bandwidth", "launch_ms": round(per_launch_s * 1e3, 4),
+           "launches": launches}
+    if model["flops"] > 0:
+        fp64_peak = SM_COUNT * FP64_FMA_PER_SM_CLK * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
+        tflops = model["flops"] / max(1, launches) / per_launch_s / 1e12
+        if tflops / fp64_peak > hbm_frac:
+            out.update({"bound": "alu", "achieved": round(tflops, 4), "peak": round(fp64_peak, 4),
+                        "unit": "TFLOP/s", "frac": round(tflops / fp64_peak, 4),
+                        "peak_src": "FP64 pipe: 148 SMs x 2 DFMA/clk x 2 flop x max SM clock",
+                        "hbm_frac": round(hbm_frac, 4)})
+    return out
+
+
+def traffic_for(kernel, alg_bytes):
+    """DRAM bytes per launch from the committed ncu summary, when it was
+    taken on the current kernel sources (else null)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path))
+        from paper_2607_07816_b300 import build as B
+        if d.get("source_hash") != B.source_hash():
+            return None
+        ent = d["kernels"].get(kernel)
+        if not ent:
+            return None
+        return ent["dram_bytes_per_unit"] * ent["units_per_launch_full"]
+    except Exception:
+        return None
+
+
+def gate_bytes_method(tot, prec):
+    sa = 16 if prec == "c128" else 8
+    S = 8 + sa
+    b = 2 * S * tot["n_in"] + S * (tot["n_in"] + tot["n_pre"]) + 8 * tot["n_pre"] + S * (tot["n_pre"] + tot["n_kept"])
+    strict = S * (tot["n_in"] + tot["n_kept"])
+    return b, strict
+
+
+# ------------------------------------------------------------------ CPU / reference arm
+def oracle_sample(seconds: float, K_cap: int, max_gates: int = 10 ** 9):
+    """The oracle as it stands, single-threaded, on the same circuit from
+    |0...0>, gate after gate until `seconds` of CPU work have elapsed."""
+    import oracle
+    from paper_2607_07816_b300 import circuits as C
+    circ = C.brickwork_n40(seed=SEED, layers=LAYERS, K=K_cap)
+    o = oracle.Oracle(circ.n, K_cap, 1.0)
+    n_in, g = 0, 0
+    t0 = time.perf_counter()
+    last = 0.0
+    while g < min(len(circ.gates), max_gates):
+        # stop before a gate that would overrun the budget (each brickwork
+        # gate can multiply the term count by 4 until K is reached)
+        if g > 0 and time.perf_counter() - t0 + 4.5 * last > seconds:
+            break
+        tg = time.perf_counter()
+        q, u = circ.gates[g]
+        n_in += o.num_terms()
+        o.apply_gate(q, u)
+        o.truncate()
+        o.peak()
+        g += 1
+        last = time.perf_counter() - tg
+    dt = time.perf_counter() - t0
+    return {"value": n_in / dt, "unit": "terms/s", "cores": 1, "kind": "oracle",
+            "sample": f"{WORKLOAD.split(',')[0]}: gates 1..{g} from |0>, K capped at {K_cap}, "
+                      f"{n_in} input terms in {dt:.1f} s (single-threaded C++ std::map oracle)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    import oracle  # noqa: F401  (builds the oracle if needed)
+    per = []
+    total_terms, total_t = 0, 0.0
+    for i in range(args.warmup + args.steps):
+        s = oracle_sample(seconds=1.0, K_cap=1 << 14, max_gates=40)
+        if i >= args.warmup:
+            per.append(s)
+    vals = [p["value"] for p in per]
+    v = statistics.mean(vals)
+    line = {"metric": "sparse-gate terms/s", "value": v, "unit": "terms/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "n": N_QUBITS, "K": args.K, "p": 1.0, "prec": "c128"},
+            "cpu_baseline": {"value": v, "unit": "terms/s", "cores": 1, "kind": "oracle",
+                             "sample": "each step: " + per[0]["sample"]},
+            "e2e": {"value": v, "unit": "terms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    return line
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+        if line is not None:
+            print(json.dumps(line))
+        return
+    import torch
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    res, peaks = run_ours(args, rank, world)
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    main_r = res["main"]
+    tot = main_r["totals"]
+    ms = main_r["ms"]
+    value = tot["n_in"] * world / (ms / 1e3)
+    bm, bstrict = gate_bytes_method(tot, args.prec)
+    bw = peaks["hbm_gbs"] * 1e9
+    line = {
+        "metric": "sparse-gate terms/s", "value": value, "unit": "terms/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.prec == "c128" else "f32",
+        "data": "synthetic (seeded Haar brickwork mirror circuit)",
+        "config": {"workload": WORKLOAD, "n": N_QUBITS, "K": args.K, "p": 1.0, "prec": args.prec,
+                   "layers": LAYERS, "seed": SEED, "l2": "state larger than L2 (no flush needed)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": roofline(main_r, args.prec, peaks),
+        "gate_roofline": {"B_method_frac": round(bm / (ms / 1e3) / bw, 4),
+                          "B_strict_frac": round(bstrict / (ms / 1e3) / bw, 4),
+                          "peak_gbs": peaks["hbm_gbs"]},
+        "phases_ms": {k: round(v[0], 3) for k, v in main_r["phases"].items()},
+        "phase_launches": {k: v[1] for k, v in main_r["phases"].items()},
+        "gpu_launches": main_r["launches"],
+        "clocks": main_r["clocks"],
+        "peak_key": main_r["peak"][0],
+        "totals": {k: (int(v) if isinstance(v, (int, float)) and k != "dfma" else v) for k, v in tot.items()},
+    }
+    if "c64" in res:
+        c = res["c64"]
+        ct = c["totals"]
+        cb, _ = gate_bytes_method(ct, "c64")
+        line["c64"] = {"value": ct["n_in"] / (c["ms"] / 1e3), "unit": "terms/s", "ms_per_step": c["ms"] / args.steps,
+                       "B_method_frac": round(cb / (c["ms"] / 1e3) / bw, 4),
+                       "roofline": roofline(c, "c64", peaks),
+                       "phases_ms": {k: round(v[0], 3) for k, v in c["phases"].items()}}
+    if "e2e" in res:
+        line["e2e"] = res["e2e"]
+    if not args.no_cpu and world == 1:
+        line["cpu_baseline"] = oracle_sample(seconds=15.0, K_cap=args.K)
+        line["cpu_baseline"]["cores"] = 1
+    print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

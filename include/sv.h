@@ -135,6 +135,24 @@ typedef struct {
 } sv_stats;
 sv_status sv_last_stats(const sv_state* s, sv_stats* out);
 
+/* Phase timing for benchmarking.  With timing on, CUDA events recorded on
+ * the handle's stream bracket each phase and the elapsed device times are
+ * accumulated.  sv_set_timing also resets the accumulators.  Phases, in
+ * order: 0 gate key transform + digit histograms, 1 radix-sort passes,
+ * 2 partner-group heads, 3 group mat-vec, 4 truncation select, 5 truncation
+ * compaction, 6 peak, 7 other (readout, load).  ms and launches (nullable)
+ * receive SV_NUM_PHASES entries: milliseconds and kernel launches. */
+#define SV_NUM_PHASES 8
+sv_status sv_set_timing(sv_state* s, int enable);
+sv_status sv_phase_times(const sv_state* s, double* ms, uint64_t* launches);
+
+/* Number of CUDA kernels this library has launched in this process. */
+uint64_t sv_launch_count(void);
+
+/* Bytes this library has moved host->device (copies and gate parameters)
+ * and device->host (copies) in this process.  Either pointer may be NULL. */
+void sv_transfer_bytes(uint64_t* h2d, uint64_t* d2h);
+
 #ifdef __cplusplus
 }
 #endif

@@ -8,6 +8,7 @@
 // Per truncation (Sec. III, Sec. IV-B): radix select of the cut on the
 // canonical composite by mass (p) and/or by count (K) -> renormalising
 // compaction.  Readout (Sec. V): argmax in canonical order.
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -17,6 +18,12 @@
 #include "sv.h"
 
 using namespace sv;
+
+// Phases timed with CUDA events when timing is on (sv_set_timing).
+enum Phase { PH_KEYS = 0, PH_SORT, PH_HEADS, PH_APPLY, PH_SELECT, PH_COMPACT, PH_PEAK, PH_OTHER, PH_COUNT };
+
+static std::atomic<uint64_t> g_launches{0};
+static std::atomic<uint64_t> g_h2d{0}, g_d2h{0};  // bytes crossing PCIe (copies and gate parameters)
 
 struct sv_state {
   int n = 0;
@@ -53,6 +60,13 @@ struct sv_state {
   std::string err;
   bool broken = false;
   sv_stats stats{};
+
+  bool timing = false;
+  cudaEvent_t ev_beg[PH_COUNT] = {};
+  cudaEvent_t ev_end[PH_COUNT] = {};
+  bool ph_pending[PH_COUNT] = {};
+  double ph_ms[PH_COUNT] = {};
+  uint64_t ph_launches[PH_COUNT] = {};
 };
 
 namespace {
@@ -78,6 +92,34 @@ void dev_free(sv_state* s, void* p) {
     cudaFree(p);
 }
 
+void ph_begin(sv_state* s, int ph) {
+  if (s->timing) cudaEventRecord(s->ev_beg[ph], s->st);
+}
+
+void ph_end(sv_state* s, int ph) {
+  if (s->timing) {
+    cudaEventRecord(s->ev_end[ph], s->st);
+    s->ph_pending[ph] = true;
+  }
+}
+
+// After a stream synchronisation: fold finished phase intervals in.
+void ph_collect(sv_state* s) {
+  if (!s->timing) return;
+  for (int ph = 0; ph < PH_COUNT; ++ph) {
+    if (!s->ph_pending[ph]) continue;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, s->ev_beg[ph], s->ev_end[ph]) == cudaSuccess) s->ph_ms[ph] += ms;
+    s->ph_pending[ph] = false;
+  }
+  cudaGetLastError();
+}
+
+void launched(sv_state* s, int ph, uint64_t k) {
+  s->ph_launches[ph] += k;
+  g_launches += k;
+}
+
 sv_status fail(sv_state* s, sv_status code, const std::string& msg) {
   s->err = msg;
   return code;
@@ -93,10 +135,12 @@ sv_status cuda_check(sv_state* s, cudaError_t e, const char* where) {
 // the handle unusable.
 sv_status sync_ctl(sv_state* s, const char* where) {
   cudaError_t e = cudaMemcpyAsync(s->ctl_host, s->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s->st);
+  g_d2h += sizeof(Ctl);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
   if (e == cudaSuccess) e = cudaGetLastError();
   sv_status rc = cuda_check(s, e, where);
   if (rc != SV_OK) return rc;
+  ph_collect(s);
   if (s->ctl_host->err & ERR_TIMEOUT) {
     s->broken = true;
     return fail(s, SV_E_TIMEOUT, std::string(where) + ": a bounded device wait ran out");
@@ -195,14 +239,22 @@ SortScratch sort_scratch(sv_state* s) {
 // Sort (sk[0], sidx[0]) on nbits bits; histograms are computed first unless
 // hist_ready.  Returns the buffer index holding the result.
 sv_status sort_pairs(sv_state* s, uint64_t n, int nbits, bool hist_ready, int* which, int* passes) {
-  if (!hist_ready) launch_digit_hist(s->sk[0], n, nbits, s->hist, s->st);
+  if (!hist_ready) {
+    launch_digit_hist(s->sk[0], n, nbits, s->hist, s->st);
+    launched(s, PH_OTHER, n ? 1 : 0);
+  }
   cudaMemcpyAsync(s->hist_host, s->hist, sizeof(uint32_t) * MAX_PASSES * RADIX, cudaMemcpyDeviceToHost,
                   s->st);
+  g_d2h += sizeof(uint32_t) * MAX_PASSES * RADIX;
   sv_status rc = cuda_check(s, cudaStreamSynchronize(s->st), "digit histogram");
   if (rc != SV_OK) return rc;
+  ph_collect(s);
   cudaError_t e;
+  ph_begin(s, PH_SORT);
   *which = radix_sort_pairs(s->sk[0], s->sidx[0], s->sk[1], s->sidx[1], n, nbits, sort_scratch(s),
                             s->st, passes, &e);
+  ph_end(s, PH_SORT);
+  launched(s, PH_SORT, (uint64_t)*passes);
   return cuda_check(s, e, "radix sort");
 }
 
@@ -213,6 +265,7 @@ sv_status canonical_perm(sv_state* s, int* which) {
   sv_status rc = ensure_sort_cap(s, N);
   if (rc != SV_OK) return rc;
   launch_iota(s->sidx[0], N, s->st);
+  launched(s, PH_OTHER, 1);
   cudaMemcpyAsync(s->sk[0], s->keys[s->cur], N * 8, cudaMemcpyDeviceToDevice, s->st);
   int w = 0, passes = 0;
   rc = sort_pairs(s, N, s->n, false, &w, &passes);
@@ -220,6 +273,7 @@ sv_status canonical_perm(sv_state* s, int* which) {
   // second, stable sort by ~prob_bits (ascending = probability descending)
   launch_not_bits_gather(s->probs[s->cur], s->sidx[w], N, s->sk[1 - w], s->st);
   launch_digit_hist(s->sk[1 - w], N, 63, s->hist, s->st);
+  launched(s, PH_OTHER, 2);
   cudaMemcpyAsync(s->hist_host, s->hist, sizeof(uint32_t) * MAX_PASSES * RADIX, cudaMemcpyDeviceToHost,
                   s->st);
   rc = cuda_check(s, cudaStreamSynchronize(s->st), "digit histogram");
@@ -227,6 +281,7 @@ sv_status canonical_perm(sv_state* s, int* which) {
   cudaError_t e;
   int w2 = radix_sort_pairs(s->sk[1 - w], s->sidx[w], s->sk[w], s->sidx[1 - w], N, 63,
                             sort_scratch(s), s->st, &passes, &e);
+  launched(s, PH_OTHER, (uint64_t)passes);
   rc = cuda_check(s, e, "radix sort");
   if (rc != SV_OK) return rc;
   // radix_sort_pairs returns 0 for (kA, vA) = (sk[1-w], sidx[w]) and 1 for (sk[w], sidx[1-w])
@@ -347,6 +402,10 @@ sv_status sv_destroy(sv_state* s) {
   dev_free(s, s->ss.hist_count);
   dev_free(s, s->ss.hist_mass);
   dev_free(s, s->ss.buf);
+  for (int ph = 0; ph < PH_COUNT; ++ph) {
+    if (s->ev_beg[ph]) cudaEventDestroy(s->ev_beg[ph]);
+    if (s->ev_end[ph]) cudaEventDestroy(s->ev_end[ph]);
+  }
   if (s->hist_host) cudaFreeHost(s->hist_host);
   if (s->ctl_host) cudaFreeHost(s->ctl_host);
   delete s;
@@ -402,15 +461,25 @@ sv_status sv_apply_gate(sv_state* s, int m, const int* qubits, const double* U) 
   if (rc == SV_OK) rc = ensure_lookback(s, apply_tiles + 16);
   if (rc != SV_OK) return rc;
   const int passes = (s->n + RADIX_BITS - 1) / RADIX_BITS;
+  ph_begin(s, PH_KEYS);
   launch_gate_keys(s->keys[s->cur], N, gp, s->sk[0], s->sidx[0], s->hist, passes, s->st);
+  ph_end(s, PH_KEYS);
+  g_h2d += sizeof(GateParams);
+  launched(s, PH_KEYS, 1);
   int w = 0, run = 0;
   rc = sort_pairs(s, N, s->n, true, &w, &run);
   if (rc != SV_OK) return rc;
   s->stats.sort_passes = (uint32_t)run;
   const int alt = 1 - s->cur;
+  ph_begin(s, PH_HEADS);
   launch_group_heads(s->sk[w], N, m, s->heads, s->lookback, s->ctl, s->st);
+  ph_end(s, PH_HEADS);
+  ph_begin(s, PH_APPLY);
   launch_gate_apply(s->prec, s->sk[w], s->sidx[w], N, s->heads, s->amps[s->cur], gp, s->keys[alt],
                     s->amps[alt], s->probs[alt], s->lookback, s->ctl, s->st, apply_tiles);
+  ph_end(s, PH_APPLY);
+  launched(s, PH_HEADS, 1);
+  launched(s, PH_APPLY, 1);
   rc = sync_ctl(s, "sv_apply_gate");
   if (rc != SV_OK) return rc;
   s->cur = alt;
@@ -427,16 +496,23 @@ namespace {
 sv_status run_select(sv_state* s, int mode, uint64_t count_target, uint32_t* levels) {
   const uint64_t N = s->N;
   launch_select_init(s->ctl, mode, count_target, s->st);
+  launched(s, PH_SELECT, 1);
   for (int level = 0; level < 16; ++level) {
+    ph_begin(s, PH_SELECT);
     launch_select_hist(s->probs[s->cur], s->keys[s->cur], N, s->ctl, s->ss, s->st);
     launch_select_pick(s->ctl, s->ss, s->p, s->st);
+    ph_end(s, PH_SELECT);
+    launched(s, PH_SELECT, 2);
     ++*levels;
     sv_status rc = sync_ctl(s, "truncation select");
     if (rc != SV_OK) return rc;
     if (s->ctl_host->sel_done) return SV_OK;
     if (s->ctl_host->sel_bin_count <= (uint64_t)FINISH_CAP) {
+      ph_begin(s, PH_SELECT);
       launch_select_compact(s->probs[s->cur], s->keys[s->cur], N, s->ctl, s->ss, s->st);
       launch_select_finish(s->ctl, s->ss, s->p, s->st);
+      ph_end(s, PH_SELECT);
+      launched(s, PH_SELECT, 2);
       rc = sync_ctl(s, "truncation select");
       if (rc != SV_OK) return rc;
       if (!s->ctl_host->sel_done) {
@@ -491,9 +567,12 @@ sv_status sv_truncate(sv_state* s, uint64_t* kept, double* retained_fraction) {
       const int alt = 1 - s->cur;
       rc = ensure_lookback(s, (N + 1023) / 1024 + 16);
       if (rc != SV_OK) return rc;
+      ph_begin(s, PH_COMPACT);
       launch_set_scale(s->ctl, s->st);
       launch_truncate_compact(s->prec, s->keys[s->cur], s->amps[s->cur], s->probs[s->cur], N,
                               s->keys[alt], s->amps[alt], s->probs[alt], s->lookback, s->ctl, s->st);
+      ph_end(s, PH_COMPACT);
+      launched(s, PH_COMPACT, 2);
       rc = sync_ctl(s, "sv_truncate");
       if (rc != SV_OK) return rc;
       if (s->ctl_host->count[2] != c) {
@@ -518,7 +597,10 @@ sv_status sv_peak(sv_state* s, uint64_t* key, double* prob) {
   SV_GUARD(s);
   if (!key || !prob) return fail(s, SV_E_ARG, "sv_peak: null output");
   if (s->N == 0) return fail(s, SV_E_STATE, "sv_peak: empty state");
+  ph_begin(s, PH_PEAK);
   launch_peak(s->probs[s->cur], s->keys[s->cur], s->N, s->ctl, s->st);
+  ph_end(s, PH_PEAK);
+  launched(s, PH_PEAK, 2);
   sv_status rc = sync_ctl(s, "sv_peak");
   if (rc != SV_OK) return rc;
   *key = s->ctl_host->peak_z_lo;
@@ -566,6 +648,8 @@ static sv_status dump(sv_state* s, uint64_t* keys, double* amps, double* probs, 
   }
   launch_gather_terms(s->prec, s->sidx[which], w, s->keys[s->cur], s->amps[s->cur], s->probs[s->cur],
                       dk, da, dp, s->st);
+  launched(s, PH_OTHER, 1);
+  g_d2h += w * ((dk ? 8 : 0) + (dp ? 8 : 0) + (da ? 16 : 0));
   if (dk) cudaMemcpyAsync(keys, dk, w * 8, cudaMemcpyDeviceToHost, s->st);
   if (dp) cudaMemcpyAsync(probs, dp, w * 8, cudaMemcpyDeviceToHost, s->st);
   if (da) cudaMemcpyAsync(amps, da, w * 16, cudaMemcpyDeviceToHost, s->st);
@@ -599,9 +683,11 @@ sv_status sv_load(sv_state* s, const uint64_t* keys, const double* amps, uint64_
   }
   double* tmp = (double*)dev_alloc(s, N * 16);
   if (!tmp) return fail(s, SV_E_NOMEM, "sv_load: staging allocation failed");
+  g_h2d += N * 24;
   cudaMemcpyAsync(s->sk[0], keys, N * 8, cudaMemcpyHostToDevice, s->st);
   cudaMemcpyAsync(tmp, amps, N * 16, cudaMemcpyHostToDevice, s->st);
   launch_iota(s->sidx[0], N, s->st);
+  launched(s, PH_OTHER, 1);
   int w = 0, passes = 0;
   rc = sort_pairs(s, N, s->n, false, &w, &passes);
   if (rc != SV_OK) {
@@ -611,6 +697,7 @@ sv_status sv_load(sv_state* s, const uint64_t* keys, const double* amps, uint64_
   const int alt = 1 - s->cur;
   launch_load_compact(s->prec, s->sk[w], s->sidx[w], N, tmp, s->keys[alt], s->amps[alt], s->probs[alt],
                       s->lookback, s->ctl, s->st);
+  launched(s, PH_OTHER, 1);
   rc = sync_ctl(s, "sv_load");
   dev_free(s, tmp);
   if (rc != SV_OK) return rc;
@@ -629,6 +716,39 @@ sv_status sv_last_stats(const sv_state* s, sv_stats* out) {
   if (!s || !out) return SV_E_ARG;
   *out = s->stats;
   return SV_OK;
+}
+
+sv_status sv_set_timing(sv_state* s, int enable) {
+  if (!s) return SV_E_ARG;
+  if (enable && !s->ev_beg[0]) {
+    for (int ph = 0; ph < PH_COUNT; ++ph) {
+      if (cudaEventCreate(&s->ev_beg[ph]) != cudaSuccess || cudaEventCreate(&s->ev_end[ph]) != cudaSuccess)
+        return fail(s, SV_E_CUDA, "sv_set_timing: event creation failed");
+    }
+  }
+  s->timing = enable != 0;
+  for (int ph = 0; ph < PH_COUNT; ++ph) {
+    s->ph_ms[ph] = 0.0;
+    s->ph_launches[ph] = 0;
+    s->ph_pending[ph] = false;
+  }
+  return SV_OK;
+}
+
+sv_status sv_phase_times(const sv_state* s, double* ms, uint64_t* launches) {
+  if (!s) return SV_E_ARG;
+  for (int ph = 0; ph < PH_COUNT; ++ph) {
+    if (ms) ms[ph] = s->ph_ms[ph];
+    if (launches) launches[ph] = s->ph_launches[ph];
+  }
+  return SV_OK;
+}
+
+uint64_t sv_launch_count(void) { return g_launches.load(); }
+
+void sv_transfer_bytes(uint64_t* h2d, uint64_t* d2h) {
+  if (h2d) *h2d = g_h2d.load();
+  if (d2h) *d2h = g_d2h.load();
 }
 
 }  // extern "C"

@@ -23,7 +23,8 @@ _STATUS = {0: "SV_OK", -1: "SV_E_ARG", -2: "SV_E_NOMEM", -3: "SV_E_CUDA", -4: "S
 
 EXPORTED = ["sv_create", "sv_create_ex", "sv_destroy", "sv_apply_gate", "sv_truncate", "sv_peak",
             "sv_probs", "sv_num_terms", "sv_retained_mass", "sv_export", "sv_load", "sv_last_error",
-            "sv_last_stats"]
+            "sv_last_stats", "sv_set_timing", "sv_phase_times", "sv_launch_count", "sv_transfer_bytes"]
+PHASES = ["keys", "sort", "heads", "apply", "select", "compact", "peak", "other"]
 
 
 class SVError(RuntimeError):
@@ -89,6 +90,14 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.sv_last_error.argtypes = [vp]
     lib.sv_last_stats.restype = i32
     lib.sv_last_stats.argtypes = [vp, P(sv_stats)]
+    lib.sv_set_timing.restype = i32
+    lib.sv_set_timing.argtypes = [vp, i32]
+    lib.sv_phase_times.restype = i32
+    lib.sv_phase_times.argtypes = [vp, P(dbl), P(u64)]
+    lib.sv_launch_count.restype = u64
+    lib.sv_launch_count.argtypes = []
+    lib.sv_transfer_bytes.restype = None
+    lib.sv_transfer_bytes.argtypes = [P(u64), P(u64)]
     _lib = lib
     return lib
 
@@ -194,6 +203,27 @@ def sv_last_stats(h: int) -> dict:
     return {f: getattr(st, f) for f, _ in sv_stats._fields_}
 
 
+def sv_set_timing(h: int, enable: bool) -> None:
+    _check(h, load_library().sv_set_timing(ctypes.c_void_p(h), int(bool(enable))))
+
+
+def sv_phase_times(h: int) -> dict:
+    ms = (ctypes.c_double * len(PHASES))()
+    ln = (ctypes.c_uint64 * len(PHASES))()
+    _check(h, load_library().sv_phase_times(ctypes.c_void_p(h), ms, ln))
+    return {name: (ms[i], int(ln[i])) for i, name in enumerate(PHASES)}
+
+
+def sv_launch_count() -> int:
+    return int(load_library().sv_launch_count())
+
+
+def sv_transfer_bytes():
+    a, b = ctypes.c_uint64(), ctypes.c_uint64()
+    load_library().sv_transfer_bytes(ctypes.byref(a), ctypes.byref(b))
+    return a.value, b.value
+
+
 # ------------------------------------------------ convenience wrapper
 class SparseState:
     """A device-resident sparse state: keys u64, amplitudes complex128
@@ -240,6 +270,12 @@ class SparseState:
 
     def stats(self) -> dict:
         return sv_last_stats(self.h)
+
+    def set_timing(self, enable: bool = True) -> None:
+        sv_set_timing(self.h, enable)
+
+    def phase_times(self) -> dict:
+        return sv_phase_times(self.h)
 
     def run(self, gates, truncate: bool = True):
         for (q, u) in gates:
