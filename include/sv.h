@@ -153,6 +153,22 @@ uint64_t sv_launch_count(void);
  * and device->host (copies) in this process.  Either pointer may be NULL. */
 void sv_transfer_bytes(uint64_t* h2d, uint64_t* d2h);
 
+/* Peak readout that allocates nothing.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc where they need
+ * the readout (their device memory is owned by another runtime or pool,
+ * they run under a fixed device-memory budget, or an allocation would stall
+ * the device at that point).  The caller passes its own device arrays:
+ * keys[n] (uint64) and amps[n] (double2 for SV_C128, float2 for SV_C64),
+ * a cudaStream_t (NULL = legacy default stream), and host outputs for the
+ * most probable key and its probability (canonical order: probability
+ * descending, key ascending).  Working memory is a fixed 64 KiB + 256 B
+ * array inside the library, so 1 <= n <= 2^28 (SV_E_ARG otherwise).  The
+ * first call on a device looks up that array's device address; make it
+ * before any stream capture.  All calls on a device share the array: calls
+ * that overlap on the GPU race.  Synchronises the stream. */
+sv_status sv_peak_noalloc(int prec, const uint64_t* keys, const void* amps, uint64_t n,
+                          void* cuda_stream, uint64_t* key, double* prob);
+
 #ifdef __cplusplus
 }
 #endif

@@ -23,7 +23,7 @@ _STATUS = {0: "SV_OK", -1: "SV_E_ARG", -2: "SV_E_NOMEM", -3: "SV_E_CUDA", -4: "S
 
 EXPORTED = ["sv_create", "sv_create_ex", "sv_destroy", "sv_apply_gate", "sv_truncate", "sv_peak",
             "sv_probs", "sv_num_terms", "sv_retained_mass", "sv_export", "sv_load", "sv_last_error",
-            "sv_last_stats", "sv_set_timing", "sv_phase_times", "sv_launch_count", "sv_transfer_bytes"]
+            "sv_last_stats", "sv_set_timing", "sv_phase_times", "sv_launch_count", "sv_transfer_bytes", "sv_peak_noalloc"]
 PHASES = ["keys", "sort", "heads", "apply", "select", "compact", "peak", "other"]
 
 
@@ -96,6 +96,8 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.sv_phase_times.argtypes = [vp, P(dbl), P(u64)]
     lib.sv_launch_count.restype = u64
     lib.sv_launch_count.argtypes = []
+    lib.sv_peak_noalloc.restype = i32
+    lib.sv_peak_noalloc.argtypes = [i32, vp, vp, u64, vp, P(u64), P(dbl)]
     lib.sv_transfer_bytes.restype = None
     lib.sv_transfer_bytes.argtypes = [P(u64), P(u64)]
     _lib = lib
@@ -222,6 +224,18 @@ def sv_transfer_bytes():
     a, b = ctypes.c_uint64(), ctypes.c_uint64()
     load_library().sv_transfer_bytes(ctypes.byref(a), ctypes.byref(b))
     return a.value, b.value
+
+
+def sv_peak_noalloc(prec: int, keys_ptr: int, amps_ptr: int, n: int, stream: int = 0):
+    """Peak of a caller-owned device term list without any allocation
+    (see include/sv.h).  keys_ptr / amps_ptr are device addresses."""
+    k, p = ctypes.c_uint64(), ctypes.c_double()
+    rc = load_library().sv_peak_noalloc(prec, ctypes.c_void_p(keys_ptr), ctypes.c_void_p(amps_ptr),
+                                        ctypes.c_uint64(n), ctypes.c_void_p(stream), ctypes.byref(k),
+                                        ctypes.byref(p))
+    if rc != SV_OK:
+        raise SVError(rc, "sv_peak_noalloc failed")
+    return k.value, p.value
 
 
 # ------------------------------------------------ convenience wrapper
