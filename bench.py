@@ -117,8 +117,10 @@ def phase_model(ph: str, totals: dict, prec: str, passes: int):
         return {"bytes": 20 * n_in, "flops": 0.0}
     if ph == "apply":    # read sorted key + index + amplitude per input; write key+amp+prob per candidate
         return {"bytes": (12 + sa) * n_in + (16 + sa) * n_pre, "flops": totals["dfma"] * 2.0}
-    if ph == "select":   # each histogram level reads the probabilities
-        return {"bytes": 8 * n_pre * max(1, totals["select_levels"]) / max(1, totals["steps"]), "flops": 0.0}
+    if ph == "window":   # one streaming pass over the probabilities (+ window keys)
+        return {"bytes": 8 * n_pre, "flops": 0.0}
+    if ph == "select":   # histogram levels over the window terms
+        return {"bytes": 16 * totals.get("window_terms", 0), "flops": 0.0}
     if ph == "compact":  # read prob (+ key, amp of kept); write kept key, amp, prob
         return {"bytes": 8 * n_pre + (8 + sa) * n_kept + (16 + sa) * n_kept, "flops": 0.0}
     if ph == "peak":
@@ -170,7 +172,7 @@ def run_ours(args, rank, world):
             torch.distributed.barrier()
         st.set_timing(True)
         totals = {"n_in": 0, "n_pre": 0, "n_kept": 0, "dfma": 0.0, "select_levels": 0, "steps": steps,
-                  "sort_passes": 0}
+                  "sort_passes": 0, "window_hits": 0, "window_terms": 0}
         clocks = ClockSampler(dev.index) if sample_clocks else None
         if clocks:
             clocks.start()
@@ -192,6 +194,8 @@ def run_ours(args, rank, world):
             totals["n_kept"] += s2["n_kept"]
             totals["sort_passes"] += s1["sort_passes"]
             totals["select_levels"] += s2["select_levels"]
+            totals["window_hits"] += s2["window_hits"]
+            totals["window_terms"] += s2["window_terms"]
             totals["dfma"] += dense_dfma_per_gate(len(q), s1["n_in"]) + 2.0 * s1["n_pre"] + 2.0 * s2["n_kept"]
         e1.record(stream)
         torch.cuda.synchronize(dev)

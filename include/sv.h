@@ -125,13 +125,17 @@ const char* sv_last_error(const sv_state* s);
 
 /* Statistics of the last sv_apply_gate / sv_truncate (for benchmarking):
  * terms before the gate, candidates after it, terms kept by the last
- * truncation, radix-sort passes run, select levels run, and the total and
- * kept probability masses of the last truncation. */
+ * truncation, radix-sort passes run, select levels run, the total and kept
+ * probability masses of the last truncation, how many of its selects ran on
+ * the sampled window (window_hits) and the window size of the last one. */
 typedef struct {
   uint64_t n_in, n_pre, n_kept;
   uint32_t sort_passes;
   uint32_t select_levels;
   double total_mass, kept_mass;
+  uint32_t window_hits;
+  uint32_t pad;
+  uint64_t window_terms;
 } sv_stats;
 sv_status sv_last_stats(const sv_state* s, sv_stats* out);
 
@@ -139,10 +143,11 @@ sv_status sv_last_stats(const sv_state* s, sv_stats* out);
  * the handle's stream bracket each phase and the elapsed device times are
  * accumulated.  sv_set_timing also resets the accumulators.  Phases, in
  * order: 0 gate key transform + digit histograms, 1 radix-sort passes,
- * 2 partner-group heads, 3 group mat-vec, 4 truncation select, 5 truncation
- * compaction, 6 peak, 7 other (readout, load).  ms and launches (nullable)
- * receive SV_NUM_PHASES entries: milliseconds and kernel launches. */
-#define SV_NUM_PHASES 8
+ * 2 partner-group heads, 3 group mat-vec, 4 truncation select levels,
+ * 5 truncation compaction, 6 peak, 7 other (readout, load), 8 truncation
+ * sample window pass.  ms and launches (nullable) receive SV_NUM_PHASES
+ * entries: milliseconds and kernel launches. */
+#define SV_NUM_PHASES 9
 sv_status sv_set_timing(sv_state* s, int enable);
 sv_status sv_phase_times(const sv_state* s, double* ms, uint64_t* launches);
 

@@ -11,6 +11,7 @@ typedef unsigned __int128 u128;
 // error bits recorded in the device control block
 constexpr uint32_t ERR_TIMEOUT = 1u;   // a bounded spin-wait gave up
 constexpr uint32_t ERR_MASS = 2u;      // a probability too large for the fixed-point mass
+constexpr uint32_t ERR_INVARIANT = 4u; // duplicate keys reached a gate (groups larger than 2^m)
 
 // Bounded waits: a decoupled look-back poll gives up after this many polls
 // (with exponential __nanosleep back-off capped at 256 ns: about a second).
@@ -44,6 +45,14 @@ struct Ctl {
   double scale;                            // 1/sqrt(double(S_c))
   uint64_t peak_z_hi, peak_z_lo;           // canonical composite of the peak
   uint64_t compact_n;                      // entries in the select buffer
+  // sample-estimated window of the cut (truncation)
+  uint64_t win_hi, win_lo;                 // window = probabilities in [lo, hi] (bit patterns)
+  uint64_t win_n;                          // terms gathered into the window buffer
+  uint64_t above_count;                    // terms with probability > hi
+  uint64_t above_mass_hi, above_mass_lo;
+  uint64_t win_mass_hi, win_mass_lo;
+  uint32_t use_window;                     // 1: select over the window, 0: over all terms
+  uint32_t pad1;
 };
 
 __device__ __forceinline__ uint64_t ld_acquire(const uint64_t* p) {
@@ -91,6 +100,51 @@ __device__ __forceinline__ uint64_t lookback_exclusive(uint64_t* lb, uint32_t st
     --t;
   }
   st_release(lb + tile * stride, LB_INC | (excl + agg));
+  return excl;
+}
+
+// Warp-cooperative decoupled look-back over a single chain: all 32 lanes of
+// one warp call it.  The warp polls a window of 32 predecessor descriptors at
+// once, waits until every descriptor from the nearest inclusive prefix up to
+// the tile is published, sums them with a warp reduction and moves the window
+// back when the window holds no inclusive prefix.  Same contract and bounded
+// wait as lookback_exclusive; every lane returns the exclusive prefix.
+__device__ __forceinline__ uint64_t lookback_exclusive_warp(uint64_t* lb, uint64_t tile, uint64_t agg,
+                                                            uint32_t* err) {
+  const int lane = threadIdx.x & 31;
+  if (tile == 0) {
+    if (lane == 0) st_release(lb, LB_INC | agg);
+    return 0;
+  }
+  if (lane == 0) st_release(lb + tile, LB_AGG | agg);
+  uint64_t excl = 0;
+  int64_t end = (int64_t)tile;  // window covers [end - 32, end)
+  uint32_t spins = 0, ns = 8;
+  while (true) {
+    const int64_t t = end - 32 + lane;
+    const uint64_t v = t >= 0 ? ld_acquire(lb + t) : LB_INC;  // before tile 0: an inclusive zero
+    const uint32_t st = (uint32_t)(v >> 62);
+    const uint32_t inc = __ballot_sync(0xffffffffu, st == 2u);
+    const uint32_t notready = __ballot_sync(0xffffffffu, st == 0u);
+    const int hi = inc ? 31 - __clz((int)inc) : 0;  // nearest inclusive prefix in the window
+    const uint32_t need = inc ? (0xffffffffu << hi) : 0xffffffffu;
+    if (notready & need) {
+      if (++spins > SPIN_LIMIT) {
+        if (lane == 0) atomicOr(err, ERR_TIMEOUT);
+        break;
+      }
+      __nanosleep(ns);
+      if (ns < 256) ns <<= 1;
+      continue;
+    }
+    uint64_t x = (lane >= hi) ? (v & LB_VAL) : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, (unsigned long long)x, o);
+    excl += x;
+    if (inc) break;
+    end -= 32;
+  }
+  if (lane == 0) st_release(lb + tile, LB_INC | (excl + agg));
   return excl;
 }
 

@@ -63,7 +63,7 @@ void launch_gate_keys(const uint64_t* keys, uint64_t n, const GateParams& gp, ui
 }
 
 // ------------------------------------------------------------------ heads
-constexpr int HEAD_BLOCK = 256, HEAD_ITEMS = 8;
+constexpr int HEAD_BLOCK = 256, HEAD_ITEMS = 16;
 
 __global__ void __launch_bounds__(HEAD_BLOCK) k_group_heads(const uint64_t* __restrict__ sk, uint64_t n,
                                                             int m, uint32_t* __restrict__ heads,
@@ -122,8 +122,23 @@ struct Cplx<float> {
 __device__ __forceinline__ double fma_r(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ float fma_r(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 
-constexpr int APPLY_BLOCK = 256, APPLY_ITEMS = 4;
+constexpr int APPLY_BLOCK = 256, APPLY_ITEMS = 8;
+constexpr int APPLY_TILE = APPLY_BLOCK * APPLY_ITEMS;  // output slots per tile (multiple of 16)
 
+template <typename Real>
+struct ApplySmem {
+  typedef typename Cplx<Real>::T C2;
+  C2 x[APPLY_TILE];                    // gathered member amplitudes
+  uint8_t r[APPLY_TILE];               // member local index
+  uint32_t head[APPLY_TILE / 2 + 1];   // member offsets of the tile's groups
+  uint64_t rest[APPLY_TILE / 2];       // squeezed key of each group
+};
+
+// One tile = APPLY_TILE consecutive output slots (group g, output r'), i.e.
+// APPLY_TILE / 2^m whole groups.  Phase 1 stages the groups' members (their
+// r and gathered amplitudes) in shared memory with independent loads;
+// phase 2 computes one output per slot from shared memory; phase 3 drops
+// zero outputs and writes the survivors in slot order.
 template <typename Real>
 __global__ void __launch_bounds__(APPLY_BLOCK) k_gate_apply(
     const uint64_t* __restrict__ sk, const uint32_t* __restrict__ sidx, uint64_t n,
@@ -132,6 +147,8 @@ __global__ void __launch_bounds__(APPLY_BLOCK) k_gate_apply(
     uint64_t* __restrict__ probs_out, uint64_t* lookback, Ctl* ctl) {
   typedef TileLayout<APPLY_BLOCK, APPLY_ITEMS> L;
   typedef typename Cplx<Real>::T C2;
+  extern __shared__ __align__(16) uint8_t s_dyn[];
+  ApplySmem<Real>& sm = *reinterpret_cast<ApplySmem<Real>*>(s_dyn);
   __shared__ Real sU[512];
   __shared__ uint32_t s_re_nz[16], s_im_nz[16];
   __shared__ CompactShared<APPLY_BLOCK> cs;
@@ -144,38 +161,62 @@ __global__ void __launch_bounds__(APPLY_BLOCK) k_gate_apply(
   }
   const uint64_t G = ctl->count[0];
   const uint64_t S = G << m;
-  const uint64_t tiles = (S + L::TILE - 1) / L::TILE;
+  const uint64_t tiles = (S + APPLY_TILE - 1) / APPLY_TILE;
   const uint32_t dmask = (uint32_t)d - 1u;
+  const uint32_t groups_per_tile = (uint32_t)APPLY_TILE >> m;
   while (true) {
     if (threadIdx.x == 0) s_tile = atomicAdd((unsigned long long*)&ctl->tile_counter[1], 1ull);
     __syncthreads();
     const uint64_t tile = s_tile;
     if (tile >= tiles) break;
-    const uint64_t base = tile * L::TILE;
+    const uint64_t base = tile * APPLY_TILE;
+    // ---- phase 1: stage
+    const uint64_t g0 = base >> m;
+    const uint64_t g1 = g0 + groups_per_tile < G ? g0 + groups_per_tile : G;
+    const uint32_t ng = (uint32_t)(g1 - g0);
+    const uint64_t mbase = heads[g0];
+    const uint64_t mend = g1 < G ? (uint64_t)heads[g1] : n;
+    uint32_t nm = (uint32_t)(mend - mbase);
+    if (nm > APPLY_TILE) {  // only possible with duplicate keys: refuse instead of overrunning
+      if (threadIdx.x == 0) atomicOr(&ctl->err, ERR_INVARIANT);
+      nm = APPLY_TILE;
+    }
+    for (uint32_t k = threadIdx.x; k < ng; k += APPLY_BLOCK) {
+      uint64_t h = heads[g0 + k];
+      sm.head[k] = (uint32_t)(h - mbase);
+      sm.rest[k] = sk[h] >> m;
+    }
+    if (threadIdx.x == 0) sm.head[ng] = nm;
+    for (uint32_t k = threadIdx.x; k < nm; k += APPLY_BLOCK) {
+      uint64_t i = mbase + k;
+      sm.r[k] = (uint8_t)(sk[i] & dmask);
+      sm.x[k] = amps_in[sidx[i]];
+    }
+    __syncthreads();
+    // ---- phase 2: one output per slot
     bool flag[APPLY_ITEMS];
     uint32_t pos[APPLY_ITEMS];
     Real yr[APPLY_ITEMS], yi[APPLY_ITEMS];
     uint64_t ykey[APPLY_ITEMS];
 #pragma unroll
     for (int j = 0; j < APPLY_ITEMS; ++j) {
-      uint64_t slot = L::index(base, j);
+      const uint64_t slot = L::index(base, j);
       Real re = (Real)0, im = (Real)0;
       uint64_t key = 0;
       if (slot < S) {
-        uint64_t g = slot >> m;
-        uint32_t ro = (uint32_t)slot & dmask;
-        uint64_t h = heads[g];
-        uint64_t e = (g + 1 < G) ? (uint64_t)heads[g + 1] : n;
+        const uint32_t ls = (uint32_t)(slot - base);
+        const uint32_t gl = ls >> m;
+        const uint32_t ro = ls & dmask;
+        const uint32_t h = min(sm.head[gl], nm), e = min(sm.head[gl + 1], nm);
         uint32_t present = 0;
-        for (uint64_t i = h; i < e; ++i) present |= 1u << (uint32_t)(sk[i] & dmask);
-        uint32_t rnz = s_re_nz[ro] & present, inz = s_im_nz[ro] & present;
+        for (uint32_t k = h; k < e; ++k) present |= 1u << sm.r[k];
+        const uint32_t rnz = s_re_nz[ro] & present, inz = s_im_nz[ro] & present;
         uint32_t cols = rnz | inz;
         while (cols) {
-          int r = __ffs(cols) - 1;
+          const int r = __ffs(cols) - 1;
           cols &= cols - 1u;
-          uint64_t i = h + __popc(present & ((1u << r) - 1u));
-          C2 x = amps_in[sidx[i]];
-          Real ur = sU[2 * (ro * d + r)], ui = sU[2 * (ro * d + r) + 1];
+          const C2 x = sm.x[h + __popc(present & ((1u << r) - 1u))];
+          const Real ur = sU[2 * (ro * d + r)], ui = sU[2 * (ro * d + r) + 1];
           if ((rnz >> r) & 1u) {
             re = fma_r(ur, x.x, re);
             im = fma_r(ur, x.y, im);
@@ -185,7 +226,7 @@ __global__ void __launch_bounds__(APPLY_BLOCK) k_gate_apply(
             im = fma_r(ui, x.x, im);
           }
         }
-        key = spread_in(sk[h] >> m, gp.qs, m);
+        key = spread_in(sm.rest[gl], gp.qs, m);
 #pragma unroll
         for (int t = 0; t < 4; ++t)
           if (t < m) key |= (uint64_t)((ro >> t) & 1u) << gp.q[t];
@@ -195,11 +236,12 @@ __global__ void __launch_bounds__(APPLY_BLOCK) k_gate_apply(
       ykey[j] = key;
       flag[j] = (slot < S) && !(re == (Real)0 && im == (Real)0);
     }
+    // ---- phase 3: drop zeros, write in slot order
     tile_compact<APPLY_BLOCK, APPLY_ITEMS>(flag, pos, cs, lookback, tile, &ctl->err);
 #pragma unroll
     for (int j = 0; j < APPLY_ITEMS; ++j) {
       if (flag[j]) {
-        uint64_t o = cs.tile_base_out + pos[j];
+        const uint64_t o = cs.tile_base_out + pos[j];
         keys_out[o] = ykey[j];
         C2 y;
         y.x = yr[j];
@@ -221,14 +263,22 @@ void launch_gate_apply(int prec, const uint64_t* sk, const uint32_t* sidx, uint6
   cudaMemsetAsync(&ctl->tile_counter[1], 0, sizeof(uint64_t), st);
   cudaMemsetAsync(&ctl->count[1], 0, sizeof(uint64_t), st);
   if (n == 0) return;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_gate_apply<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(ApplySmem<double>));
+    cudaFuncSetAttribute(k_gate_apply<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(ApplySmem<float>));
+    attr_set = true;
+  }
   uint64_t grid = max_tiles < 148 * 4 ? max_tiles : 148 * 4;
   if (grid == 0) grid = 1;
   if (prec == 0)
-    k_gate_apply<double><<<(unsigned)grid, APPLY_BLOCK, 0, st>>>(
+    k_gate_apply<double><<<(unsigned)grid, APPLY_BLOCK, sizeof(ApplySmem<double>), st>>>(
         sk, sidx, n, heads, (const double2*)amps_in, gp, keys_out, (double2*)amps_out, probs_out,
         lookback, ctl);
   else
-    k_gate_apply<float><<<(unsigned)grid, APPLY_BLOCK, 0, st>>>(
+    k_gate_apply<float><<<(unsigned)grid, APPLY_BLOCK, sizeof(ApplySmem<float>), st>>>(
         sk, sidx, n, heads, (const float2*)amps_in, gp, keys_out, (float2*)amps_out, probs_out,
         lookback, ctl);
 }

@@ -11,8 +11,8 @@ namespace sv {
 constexpr int RADIX_BITS = 8;
 constexpr int RADIX = 1 << RADIX_BITS;
 constexpr int MAX_PASSES = 8;
-constexpr int SORT_THREADS = 256;
-constexpr int SORT_ITEMS = 16;
+constexpr int SORT_THREADS = 512;
+constexpr int SORT_ITEMS = 8;
 constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;
 
 // Scratch used by one LSD radix sort.
@@ -74,11 +74,30 @@ struct SelectScratch {
   uint32_t* hist_count;   // [SEL_BINS]
   uint64_t* hist_mass;    // [SEL_BINS][2] (hi, lo)
   uint64_t* buf;          // [FINISH_CAP][2] composite (hi = ~pbits, lo = key)
+  uint64_t* win_p;        // [win_cap] probability bits of the window terms
+  uint64_t* win_k;        // [win_cap] keys of the window terms
+  uint32_t* win_i;        // [win_cap] positions of the window terms
+  uint64_t win_cap;
+  uint32_t* tile_keep;    // [window tiles] kept terms per tile
+  uint64_t* tile_off;     // [window tiles] output offset per tile
+  uint64_t tiles_cap;
 };
 
-// Initialise the select: mode 0 = by mass (target from p and the total
-// mass, computed in the first level), 1 = by count (target = rank).
-void launch_select_init(Ctl* ctl, int mode, uint64_t count_target, cudaStream_t st);
+// Number of tiles of the window pass (and of the windowed compaction).
+uint64_t window_tiles(uint64_t n);
+// After a select on the window: per-tile kept counts, their scan (total in
+// ctl->count[2]) and the lookback-free renormalising compaction.
+void launch_truncate_windowed(int prec, const uint64_t* keys, const void* amps, const uint64_t* probs,
+                              uint64_t n, uint64_t* keys_out, void* amps_out, uint64_t* probs_out,
+                              const SelectScratch& ss, Ctl* ctl, cudaStream_t st);
+
+// Sample-estimated window, one streaming pass (exact total mass, count and
+// mass above the window, window terms gathered) and the choice of the list
+// the radix select runs on (ctl->use_window); sets the select state.
+void launch_select_window(const uint64_t* probs, const uint64_t* keys, uint64_t n, Ctl* ctl,
+                          const SelectScratch& ss, int mode, uint64_t count_target, double p,
+                          cudaStream_t st);
+
 void launch_select_hist(const uint64_t* probs, const uint64_t* keys, uint64_t n, Ctl* ctl,
                         const SelectScratch& ss, cudaStream_t st);
 void launch_select_pick(Ctl* ctl, const SelectScratch& ss, double p, cudaStream_t st);

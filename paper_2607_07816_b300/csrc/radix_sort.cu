@@ -40,8 +40,10 @@ void launch_digit_hist(const uint64_t* k, uint64_t n, int nbits, uint32_t* hist,
   k_digit_hist<<<(unsigned)blocks, 256, 0, st>>>(k, n, passes, hist);
 }
 
-// Exclusive scan of the 256 digit counts of one pass, by a 256-thread block.
-__device__ __forceinline__ uint32_t block_exclusive_scan_256(uint32_t v, uint32_t* warp_tot) {
+// Exclusive scan of one value per thread over the block (values of threads
+// that have none are 0); all BLOCK threads call it.
+template <int BLOCK>
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* warp_tot) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t x = v;
 #pragma unroll
@@ -57,6 +59,12 @@ __device__ __forceinline__ uint32_t block_exclusive_scan_256(uint32_t v, uint32_
   return base + x - v;
 }
 
+// One pass of the LSD sort over the 8-bit digit at `shift`.  Warp w of the
+// tile owns elements [w*32*ITEMS, (w+1)*32*ITEMS) (lane-interleaved), so the
+// warp-local ranks (match_any + a per-warp counter per digit) follow the
+// input order and the sort is stable.  Threads 0..255 then own one digit
+// each: exclusive offsets across warps, the tile-local digit offsets, and
+// the decoupled look-back over earlier tiles for the digit's global base.
 template <int BLOCK, int ITEMS>
 __global__ void __launch_bounds__(BLOCK) k_onesweep(const uint64_t* __restrict__ kin,
                                                    const uint32_t* __restrict__ vin,
@@ -65,7 +73,7 @@ __global__ void __launch_bounds__(BLOCK) k_onesweep(const uint64_t* __restrict__
                                                    int shift, const uint32_t* __restrict__ hist,
                                                    uint64_t* lookback, uint64_t* tile_counter,
                                                    uint32_t* err) {
-  static_assert(BLOCK == RADIX, "one thread per digit");
+  static_assert(BLOCK >= RADIX, "one thread per digit");
   constexpr int TILE = BLOCK * ITEMS;
   constexpr int WARPS = BLOCK / 32;
   extern __shared__ __align__(16) uint8_t s_dyn[];
@@ -78,9 +86,10 @@ __global__ void __launch_bounds__(BLOCK) k_onesweep(const uint64_t* __restrict__
   __shared__ uint64_t s_tile;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool digit_thread = tid < RADIX;
   if (tid == 0) s_tile = atomicAdd((unsigned long long*)tile_counter, 1ull);
   for (int i = tid; i < WARPS * RADIX; i += BLOCK) (&s_whist[0][0])[i] = 0;
-  uint32_t digit_base = block_exclusive_scan_256(hist[tid], s_wtot);  // includes syncs
+  const uint32_t digit_base = block_exclusive_scan<BLOCK>(digit_thread ? hist[tid] : 0u, s_wtot);
   const uint64_t tile = s_tile;
   const uint64_t base = tile * TILE;
 
@@ -109,18 +118,21 @@ __global__ void __launch_bounds__(BLOCK) k_onesweep(const uint64_t* __restrict__
     __syncwarp();
   }
   __syncthreads();
-  // per digit: exclusive offsets across warps and the tile count
   uint32_t cnt = 0;
+  if (digit_thread) {
 #pragma unroll
-  for (int w = 0; w < WARPS; ++w) {
-    uint32_t c = s_whist[w][tid];
-    s_whist[w][tid] = cnt;
-    cnt += c;
+    for (int w = 0; w < WARPS; ++w) {
+      uint32_t c = s_whist[w][tid];
+      s_whist[w][tid] = cnt;
+      cnt += c;
+    }
   }
-  uint32_t local = block_exclusive_scan_256(cnt, s_wtot);
-  s_local[tid] = local;
-  uint64_t excl = lookback_exclusive(lookback + tid, RADIX, tile, cnt, err);
-  s_global[tid] = digit_base + excl;
+  const uint32_t local = block_exclusive_scan<BLOCK>(cnt, s_wtot);
+  if (digit_thread) {
+    s_local[tid] = local;
+    uint64_t excl = lookback_exclusive(lookback + tid, RADIX, tile, cnt, err);
+    s_global[tid] = digit_base + excl;
+  }
   __syncthreads();
 #pragma unroll
   for (int i = 0; i < ITEMS; ++i) {

@@ -20,7 +20,7 @@
 using namespace sv;
 
 // Phases timed with CUDA events when timing is on (sv_set_timing).
-enum Phase { PH_KEYS = 0, PH_SORT, PH_HEADS, PH_APPLY, PH_SELECT, PH_COMPACT, PH_PEAK, PH_OTHER, PH_COUNT };
+enum Phase { PH_KEYS = 0, PH_SORT, PH_HEADS, PH_APPLY, PH_SELECT, PH_COMPACT, PH_PEAK, PH_OTHER, PH_WINDOW, PH_COUNT };
 
 static std::atomic<uint64_t> g_launches{0};
 static std::atomic<uint64_t> g_h2d{0}, g_d2h{0};  // bytes crossing PCIe (copies and gate parameters)
@@ -144,6 +144,10 @@ sv_status sync_ctl(sv_state* s, const char* where) {
   if (s->ctl_host->err & ERR_TIMEOUT) {
     s->broken = true;
     return fail(s, SV_E_TIMEOUT, std::string(where) + ": a bounded device wait ran out");
+  }
+  if (s->ctl_host->err & ERR_INVARIANT) {
+    s->broken = true;
+    return fail(s, SV_E_STATE, std::string(where) + ": duplicate keys in the state");
   }
   if (s->ctl_host->err & ERR_MASS) {
     s->broken = true;
@@ -457,7 +461,7 @@ sv_status sv_apply_gate(sv_state* s, int m, const int* qubits, const double* U) 
     return fail(s, SV_E_ARG, "sv_apply_gate: state too large for 32-bit term indices");
   sv_status rc = ensure_state_cap(s, N << m);
   if (rc == SV_OK) rc = ensure_sort_cap(s, N);
-  const uint64_t apply_tiles = ((N << m) + 1023) / 1024 + 1;
+  const uint64_t apply_tiles = ((N << m) + 2047) / 2048 + 1;
   if (rc == SV_OK) rc = ensure_lookback(s, apply_tiles + 16);
   if (rc != SV_OK) return rc;
   const int passes = (s->n + RADIX_BITS - 1) / RADIX_BITS;
@@ -492,24 +496,77 @@ sv_status sv_apply_gate(sv_state* s, int m, const int* qubits, const double* U) 
 
 namespace {
 
-// Radix select of the cut; leaves the result in s->ctl_host.
+// Window buffer for the truncation select: room for N/6 + 65536 terms.
+sv_status ensure_window_cap(sv_state* s, uint64_t N) {
+  uint64_t need = N / 6 + 65536;
+  if (need > s->ss.win_cap) {
+    uint64_t cap = need + need / 2;
+    dev_free(s, s->ss.win_p);
+    dev_free(s, s->ss.win_k);
+    dev_free(s, s->ss.win_i);
+    s->ss.win_p = (uint64_t*)dev_alloc(s, cap * 8);
+    s->ss.win_k = (uint64_t*)dev_alloc(s, cap * 8);
+    s->ss.win_i = (uint32_t*)dev_alloc(s, cap * 4);
+    if (!s->ss.win_p || !s->ss.win_k || !s->ss.win_i) {
+      s->ss.win_cap = 0;
+      return fail(s, SV_E_NOMEM, "select window allocation failed");
+    }
+    s->ss.win_cap = cap;
+  }
+  uint64_t tiles = window_tiles(N) + 1;
+  if (tiles > s->ss.tiles_cap) {
+    uint64_t cap = tiles + tiles / 2 + 64;
+    dev_free(s, s->ss.tile_keep);
+    dev_free(s, s->ss.tile_off);
+    s->ss.tile_keep = (uint32_t*)dev_alloc(s, cap * 4);
+    s->ss.tile_off = (uint64_t*)dev_alloc(s, cap * 8);
+    if (!s->ss.tile_keep || !s->ss.tile_off) {
+      s->ss.tiles_cap = 0;
+      return fail(s, SV_E_NOMEM, "select tile table allocation failed");
+    }
+    s->ss.tiles_cap = cap;
+  }
+  return SV_OK;
+}
+
+// Exact cut by count (mode 1, rank count_target) or by mass (mode 0, p of
+// the total): sample window + one streaming pass, then radix-select levels on
+// the window (or on all terms when the window misses).  The result is left
+// in s->ctl_host.
 sv_status run_select(sv_state* s, int mode, uint64_t count_target, uint32_t* levels) {
   const uint64_t N = s->N;
-  launch_select_init(s->ctl, mode, count_target, s->st);
-  launched(s, PH_SELECT, 1);
+  sv_status rc = ensure_window_cap(s, N);
+  if (rc != SV_OK) return rc;
+  ph_begin(s, PH_WINDOW);
+  launch_select_window(s->probs[s->cur], s->keys[s->cur], N, s->ctl, s->ss, mode, count_target, s->p,
+                       s->st);
+  ph_end(s, PH_WINDOW);
+  launched(s, PH_WINDOW, 3);
+  rc = sync_ctl(s, "truncation select");
+  if (rc != SV_OK) return rc;
+  const bool win = s->ctl_host->use_window != 0;
+  s->stats.window_terms = s->ctl_host->win_n;
+  s->stats.window_hits += win ? 1 : 0;
+  const uint64_t* lp = win ? s->ss.win_p : s->probs[s->cur];
+  const uint64_t* lk = win ? s->ss.win_k : s->keys[s->cur];
+  const uint64_t ln = win ? s->ctl_host->win_n : N;
+  bool small = win && ln <= (uint64_t)FINISH_CAP;
   for (int level = 0; level < 16; ++level) {
-    ph_begin(s, PH_SELECT);
-    launch_select_hist(s->probs[s->cur], s->keys[s->cur], N, s->ctl, s->ss, s->st);
-    launch_select_pick(s->ctl, s->ss, s->p, s->st);
-    ph_end(s, PH_SELECT);
-    launched(s, PH_SELECT, 2);
-    ++*levels;
-    sv_status rc = sync_ctl(s, "truncation select");
-    if (rc != SV_OK) return rc;
-    if (s->ctl_host->sel_done) return SV_OK;
-    if (s->ctl_host->sel_bin_count <= (uint64_t)FINISH_CAP) {
+    if (!small) {
       ph_begin(s, PH_SELECT);
-      launch_select_compact(s->probs[s->cur], s->keys[s->cur], N, s->ctl, s->ss, s->st);
+      launch_select_hist(lp, lk, ln, s->ctl, s->ss, s->st);
+      launch_select_pick(s->ctl, s->ss, s->p, s->st);
+      ph_end(s, PH_SELECT);
+      launched(s, PH_SELECT, 2);
+      ++*levels;
+      rc = sync_ctl(s, "truncation select");
+      if (rc != SV_OK) return rc;
+      if (s->ctl_host->sel_done) return SV_OK;
+      small = s->ctl_host->sel_bin_count <= (uint64_t)FINISH_CAP;
+    }
+    if (small) {
+      ph_begin(s, PH_SELECT);
+      launch_select_compact(lp, lk, ln, s->ctl, s->ss, s->st);
       launch_select_finish(s->ctl, s->ss, s->p, s->st);
       ph_end(s, PH_SELECT);
       launched(s, PH_SELECT, 2);
@@ -534,6 +591,8 @@ sv_status sv_truncate(sv_state* s, uint64_t* kept, double* retained_fraction) {
   SV_GUARD(s);
   const uint64_t N = s->N;
   s->stats.select_levels = 0;
+  s->stats.window_hits = 0;
+  s->stats.window_terms = 0;
   s->stats.n_kept = N;
   s->stats.total_mass = s->stats.kept_mass = 0.0;
   const bool need_p = s->p < 1.0, need_k = N > s->K;
@@ -568,11 +627,17 @@ sv_status sv_truncate(sv_state* s, uint64_t* kept, double* retained_fraction) {
       rc = ensure_lookback(s, (N + 1023) / 1024 + 16);
       if (rc != SV_OK) return rc;
       ph_begin(s, PH_COMPACT);
-      launch_set_scale(s->ctl, s->st);
-      launch_truncate_compact(s->prec, s->keys[s->cur], s->amps[s->cur], s->probs[s->cur], N,
-                              s->keys[alt], s->amps[alt], s->probs[alt], s->lookback, s->ctl, s->st);
+      if (s->ctl_host->use_window) {
+        launch_truncate_windowed(s->prec, s->keys[s->cur], s->amps[s->cur], s->probs[s->cur], N,
+                                 s->keys[alt], s->amps[alt], s->probs[alt], s->ss, s->ctl, s->st);
+        launched(s, PH_COMPACT, 4);
+      } else {
+        launch_set_scale(s->ctl, s->st);
+        launch_truncate_compact(s->prec, s->keys[s->cur], s->amps[s->cur], s->probs[s->cur], N,
+                                s->keys[alt], s->amps[alt], s->probs[alt], s->lookback, s->ctl, s->st);
+        launched(s, PH_COMPACT, 2);
+      }
       ph_end(s, PH_COMPACT);
-      launched(s, PH_COMPACT, 2);
       rc = sync_ctl(s, "sv_truncate");
       if (rc != SV_OK) return rc;
       if (s->ctl_host->count[2] != c) {

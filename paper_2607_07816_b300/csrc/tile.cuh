@@ -29,6 +29,39 @@ struct CompactShared {
   uint64_t tile_base_out;
 };
 
+// flags[j] -> positions pos[j] among the tile's kept elements (input order)
+// and cs.tile_total; no cross-tile communication.  All threads must call it.
+template <int BLOCK, int ITEMS>
+__device__ __forceinline__ void tile_local_positions(const bool (&flags)[ITEMS], uint32_t (&pos)[ITEMS],
+                                                     CompactShared<BLOCK>& cs) {
+  constexpr int WARPS = BLOCK / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t lt = (1u << lane) - 1u;
+  uint32_t run = 0;
+#pragma unroll
+  for (int j = 0; j < ITEMS; ++j) {
+    uint32_t b = __ballot_sync(0xffffffffu, flags[j]);
+    pos[j] = run + __popc(b & lt);
+    run += __popc(b);
+  }
+  if (lane == 0) cs.warp_excl[warp] = run;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t v = lane < WARPS ? cs.warp_excl[lane] : 0u;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane < WARPS) cs.warp_excl[lane] = x - v;
+    if (lane == 31) cs.tile_total = x;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < ITEMS; ++j) pos[j] += cs.warp_excl[warp];
+}
+
 // flags[j] -> local positions pos[j] within the tile; after the call
 // cs.tile_base_out holds the global output offset of this tile and
 // cs.tile_total its number of kept elements.  All threads must call it.
@@ -58,9 +91,10 @@ __device__ __forceinline__ void tile_compact(const bool (&flags)[ITEMS], uint32_
     }
     if (lane < WARPS) cs.warp_excl[lane] = x - v;
     uint32_t total = __shfl_sync(0xffffffffu, x, 31);
+    uint64_t base = lookback_exclusive_warp(lookback, tile, total, err);
     if (lane == 0) {
       cs.tile_total = total;
-      cs.tile_base_out = lookback_exclusive(lookback, 1, tile, total, err);
+      cs.tile_base_out = base;
     }
   }
   __syncthreads();

@@ -33,27 +33,6 @@ __device__ __forceinline__ bool z_matches(uint64_t hi, uint64_t lo, uint64_t ph,
   return ((lo ^ pl) >> (128 - bits)) == 0;
 }
 
-// ---------------------------------------------------------------- init
-__global__ void k_select_init(Ctl* ctl, int mode, uint64_t count_target) {
-  ctl->sel_prefix_hi = 1ull << 63;  // ~sign bit of a non-negative double
-  ctl->sel_prefix_lo = 0;
-  ctl->sel_bits = 1;
-  ctl->sel_mode = (uint32_t)mode;
-  ctl->sel_done = 0;
-  ctl->sel_compact = 0;
-  ctl->sel_target_hi = 0;
-  ctl->sel_target_lo = count_target;
-  ctl->sel_before_count = 0;
-  ctl->sel_before_mass_hi = 0;
-  ctl->sel_before_mass_lo = 0;
-  ctl->sel_bin_count = 0;
-  ctl->compact_n = 0;
-}
-
-void launch_select_init(Ctl* ctl, int mode, uint64_t count_target, cudaStream_t st) {
-  k_select_init<<<1, 1, 0, st>>>(ctl, mode, count_target);
-}
-
 // ---------------------------------------------------------------- histogram
 __device__ __forceinline__ void sel_digit(int bits, int* D, int* shift) {
   int d = 128 - bits;
@@ -66,12 +45,46 @@ __device__ __forceinline__ uint32_t z_digit(uint64_t hi, uint64_t lo, int shift,
   return (uint32_t)(z >> shift) & ((1u << D) - 1u);
 }
 
+// Adds one element per lane to the shared histograms.  Lanes with the same
+// digit are merged first (__match_any_sync): the lowest lane of each group
+// adds the group's count and mass, so a hot bin takes one atomic per warp
+// instead of one per element.  All lanes of a bin share the probability's
+// exponent (the exponent is fixed before any other bits), so the group mass
+// is the exact sum of the mantissas times a common power of two; the
+// mantissa sum is formed by three 18-bit chunked warp reductions (no chunk
+// sum can exceed 32 bits).  Probabilities below 2^-68, whose fixed-point
+// value is a truncated shift, and those of 2 or more (whose group sum could
+// exceed 128 bits) are added one by one.
+__device__ __forceinline__ void warp_hist_add(bool active, uint32_t dg, uint64_t pb, uint32_t* cnt,
+                                              uint64_t* mass, uint32_t* err) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t key = active ? dg : 0xffffffffu;
+  const uint32_t peers = __match_any_sync(0xffffffffu, key);
+  const uint32_t e = (uint32_t)(pb >> 52) & 0x7ffu;
+  const int sh = (int)e - 955;
+  const bool exact_shift = active && e != 0 && sh >= 0 && sh <= 68;
+  uint64_t mant = exact_shift ? ((pb & ((1ull << 52) - 1)) | (1ull << 52)) : 0ull;
+  const uint32_t s0 = __reduce_add_sync(peers, (uint32_t)(mant & 0x3ffffull));
+  const uint32_t s1 = __reduce_add_sync(peers, (uint32_t)((mant >> 18) & 0x3ffffull));
+  const uint32_t s2 = __reduce_add_sync(peers, (uint32_t)(mant >> 36));
+  if (!active) return;
+  if (lane == (uint32_t)(__ffs(peers) - 1)) {
+    atomicAdd(&cnt[dg], (uint32_t)__popc(peers));
+    const uint64_t msum = (uint64_t)s0 + ((uint64_t)s1 << 18) + ((uint64_t)s2 << 36);
+    if (msum) atomic_add_u128(&mass[2 * dg], &mass[2 * dg + 1], ((u128)msum) << sh);
+  }
+  if (active && !exact_shift && e != 0) {  // tiny (or above 2) probability: added alone
+    u128 v = fx_from_bits(pb, err);
+    if (v) atomic_add_u128(&mass[2 * dg], &mass[2 * dg + 1], v);
+  }
+}
+
 __global__ void __launch_bounds__(256) k_select_hist(const uint64_t* __restrict__ probs,
                                                      const uint64_t* __restrict__ keys, uint64_t n,
                                                      Ctl* ctl, uint32_t* __restrict__ g_cnt,
                                                      uint64_t* __restrict__ g_mass) {
   __shared__ uint32_t s_cnt[SEL_BINS];
-  __shared__ uint64_t s_mass[SEL_BINS][2];
+  __shared__ uint64_t s_mass[2 * SEL_BINS];
   if (ctl->sel_done) return;
   const int bits = (int)ctl->sel_bits;
   const uint64_t ph = ctl->sel_prefix_hi, pl = ctl->sel_prefix_lo;
@@ -80,25 +93,27 @@ __global__ void __launch_bounds__(256) k_select_hist(const uint64_t* __restrict_
   const bool need_lo = bits > 64 || shift < 64;
   for (int i = threadIdx.x; i < SEL_BINS; i += blockDim.x) {
     s_cnt[i] = 0;
-    s_mass[i][0] = s_mass[i][1] = 0;
+    s_mass[2 * i] = s_mass[2 * i + 1] = 0;
   }
   __syncthreads();
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
-       i += (uint64_t)gridDim.x * blockDim.x) {
-    uint64_t pb = probs[i];
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  // whole warps iterate together (the warp reductions need all 32 lanes)
+  const uint64_t nround = (n + stride - 1) / stride * stride;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nround; i += stride) {
+    bool active = i < n;
+    uint64_t pb = active ? probs[i] : 0ull;
     uint64_t hi = ~pb;
-    if (bits <= 64 && bits > 0 && ((hi ^ ph) >> (64 - bits)) != 0) continue;
-    uint64_t lo = need_lo ? keys[i] : 0ull;
-    if (bits > 64 && !z_matches(hi, lo, ph, pl, bits)) continue;
-    uint32_t dg = z_digit(hi, lo, shift, D);
-    atomicAdd(&s_cnt[dg], 1u);
-    atomic_add_u128(&s_mass[dg][0], &s_mass[dg][1], fx_from_bits(pb, &ctl->err));
+    if (active && bits <= 64 && ((hi ^ ph) >> (64 - bits)) != 0) active = false;
+    uint64_t lo = (active && need_lo) ? keys[i] : 0ull;
+    if (active && bits > 64 && !z_matches(hi, lo, ph, pl, bits)) active = false;
+    uint32_t dg = active ? z_digit(hi, lo, shift, D) : 0u;
+    warp_hist_add(active, dg, pb, s_cnt, s_mass, &ctl->err);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < (1 << D); i += blockDim.x) {
     if (s_cnt[i]) {
       atomicAdd(&g_cnt[i], s_cnt[i]);
-      atomic_add_u128(&g_mass[2 * i], &g_mass[2 * i + 1], make_u128(s_mass[i][0], s_mass[i][1]));
+      atomic_add_u128(&g_mass[2 * i], &g_mass[2 * i + 1], make_u128(s_mass[2 * i], s_mass[2 * i + 1]));
     }
   }
 }
@@ -108,9 +123,383 @@ void launch_select_hist(const uint64_t* probs, const uint64_t* keys, uint64_t n,
   cudaMemsetAsync(ss.hist_count, 0, sizeof(uint32_t) * SEL_BINS, st);
   cudaMemsetAsync(ss.hist_mass, 0, sizeof(uint64_t) * 2 * SEL_BINS, st);
   if (n == 0) return;
-  uint64_t blocks = (n + 255) / 256;
+  // each block flushes up to 3 * SEL_BINS global atomics: give every block a
+  // large share of the list
+  uint64_t blocks = (n + 8191) / 8192;
   if (blocks > 148 * 4) blocks = 148 * 4;
   k_select_hist<<<(unsigned)blocks, 256, 0, st>>>(probs, keys, n, ctl, ss.hist_count, ss.hist_mass);
+}
+
+// ---------------------------------------------------------------- sample window
+// The cut is located from a sample first: SAMPLE_N probabilities at evenly
+// spaced positions are sorted in shared memory, the sample rank of the cut is
+// estimated (count: K * SAMPLE_N / N; mass: the sample prefix whose mass
+// fraction reaches p) and a window of +-4 binomial standard deviations (+16)
+// around it is turned into a probability interval [lo, hi].  One streaming
+// pass then sums the exact fixed-point mass of all terms, counts and sums the
+// terms above hi, and gathers the terms inside [lo, hi].  If the window
+// provably holds the cut, the radix select runs on the window only; else it
+// runs on all terms.  The sample only steers the work: the cut found is the
+// exact one either way.
+constexpr int SAMPLE_N = 8192;
+constexpr int SAMPLE_THREADS = 1024;
+
+// LSD radix sort (4 passes of 8 bits) of SAMPLE_N 32-bit keys in shared
+// memory by one 1024-thread block.  Warp w owns keys [w*256, (w+1)*256)
+// lane-interleaved; ranks come from __match_any_sync and per-warp digit
+// counters, so each pass is stable.  The result ends in `a`.
+__device__ void block_sort_samples(uint32_t* a, uint32_t* tmp, uint32_t* whist /* [32][256] */,
+                                   uint32_t* dsum /* [256] */, uint32_t* wtot /* [32] */) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t lt = (1u << lane) - 1u;
+  constexpr int ITEMS = SAMPLE_N / SAMPLE_THREADS;  // 8
+  for (int pass = 0; pass < 4; ++pass) {
+    const int shift = 8 * pass;
+    uint32_t k[ITEMS], d[ITEMS], rk[ITEMS];
+    for (int i = lane; i < 256; i += 32) whist[warp * 256 + i] = 0;
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+      k[i] = a[warp * 256 + i * 32 + lane];
+      d[i] = (k[i] >> shift) & 255u;
+    }
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+      uint32_t peers = __match_any_sync(0xffffffffu, d[i]);
+      int leader = __ffs(peers) - 1;
+      uint32_t old = 0;
+      if (lane == leader) {
+        old = whist[warp * 256 + d[i]];
+        whist[warp * 256 + d[i]] = old + __popc(peers);
+      }
+      rk[i] = __shfl_sync(0xffffffffu, old, leader) + __popc(peers & lt);
+      __syncwarp();
+    }
+    __syncthreads();
+    uint32_t tot = 0;
+    if (tid < 256) {
+      for (int w = 0; w < 32; ++w) {
+        uint32_t c = whist[w * 256 + tid];
+        whist[w * 256 + tid] = tot;
+        tot += c;
+      }
+    }
+    // exclusive scan of the 256 digit totals
+    uint32_t x = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wtot[warp] = x;
+    __syncthreads();
+    if (tid < 256) {
+      uint32_t base = 0;
+      for (int w = 0; w < warp; ++w) base += wtot[w];
+      dsum[tid] = base + x - tot;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) tmp[dsum[d[i]] + whist[warp * 256 + d[i]] + rk[i]] = k[i];
+    __syncthreads();
+    uint32_t* t = a;
+    a = tmp;
+    tmp = t;
+  }
+}
+
+// The cut is located from a sample first: SAMPLE_N probabilities at evenly
+// spaced positions, reduced to the top 32 bits of their inverted bit pattern
+// (exponent and 20 mantissa bits), are sorted in shared memory; the sample
+// rank of the cut is estimated (count: K * SAMPLE_N / N; mass: the sample
+// prefix whose mass fraction reaches p) and a window of +-4 binomial
+// standard deviations (+16; doubled for mass) around it becomes a
+// probability interval [lo, hi], rounded outwards.  The sample only steers
+// the work: the cut found afterwards is the exact one either way.
+__global__ void __launch_bounds__(SAMPLE_THREADS) k_sample_window(const uint64_t* __restrict__ probs,
+                                                                  uint64_t n, Ctl* ctl, int mode,
+                                                                  uint64_t count_target, double p) {
+  extern __shared__ __align__(16) uint8_t s_dyn[];
+  uint32_t* a = reinterpret_cast<uint32_t*>(s_dyn);
+  uint32_t* tmp = a + SAMPLE_N;
+  uint32_t* whist = tmp + SAMPLE_N;
+  double* pre = reinterpret_cast<double*>(whist + 32 * 256);
+  __shared__ uint32_t dsum[256], wtot[32];
+  __shared__ int s_rank;
+  const int tid = threadIdx.x;
+  // stratified random sample: one term at a hashed offset inside each of
+  // SAMPLE_N equal strata (a fixed stride would alias with the 2^m-periodic
+  // layout of the candidates)
+  for (int j = tid; j < SAMPLE_N; j += SAMPLE_THREADS) {
+    const uint64_t b0 = (uint64_t)j * (n / SAMPLE_N) + ((uint64_t)j * (n % SAMPLE_N)) / SAMPLE_N;
+    const uint64_t b1 = (uint64_t)(j + 1) * (n / SAMPLE_N) + ((uint64_t)(j + 1) * (n % SAMPLE_N)) / SAMPLE_N;
+    uint64_t h = (uint64_t)j * 0x9E3779B97F4A7C15ull;
+    h ^= h >> 31;
+    h *= 0xBF58476D1CE4E5B9ull;
+    h ^= h >> 29;
+    const uint64_t idx = b1 > b0 ? b0 + h % (b1 - b0) : (b0 < n ? b0 : n - 1);
+    a[j] = (uint32_t)((~probs[idx]) >> 31);  // drop the constant top bit, keep 32 bits
+  }
+  __syncthreads();
+  block_sort_samples(a, tmp, whist, dsum, wtot);  // 4 passes: result back in a
+  if (mode == 1) {
+    if (tid == 0) {
+      double r = (double)count_target * SAMPLE_N / (double)n - 1.0;
+      s_rank = (int)(r < 0 ? 0 : (r > SAMPLE_N - 1 ? SAMPLE_N - 1 : r));
+    }
+  } else {
+    constexpr int PER = SAMPLE_N / SAMPLE_THREADS;
+    double loc = 0.0;
+    for (int k = 0; k < PER; ++k)
+      loc += __longlong_as_double((long long)~(((uint64_t)a[tid * PER + k] << 31) | (1ull << 63)));
+    pre[tid] = loc;
+    __syncthreads();
+    if (tid == 0) {
+      double tot = 0.0;
+      for (int t = 0; t < SAMPLE_THREADS; ++t) tot += pre[t];
+      double goal = p * tot, acc = 0.0;
+      int r = SAMPLE_N - 1;
+      for (int t = 0; t < SAMPLE_THREADS; ++t) {
+        if (acc + pre[t] >= goal) {
+          for (int k = 0; k < PER; ++k) {
+            acc += __longlong_as_double((long long)~(((uint64_t)a[t * PER + k] << 31) | (1ull << 63)));
+            if (acc >= goal) {
+              r = t * PER + k;
+              break;
+            }
+          }
+          break;
+        }
+        acc += pre[t];
+      }
+      s_rank = r;
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const int r = s_rank;
+    const double q = (r + 1.0) / SAMPLE_N;
+    const int delta = (int)(4.0 * sqrt(SAMPLE_N * q * (1.0 - q)) + 16.0) * (mode == 1 ? 1 : 2);
+    const int rh = r - delta, rl = r + delta;
+    // inverted patterns: a smaller value is a larger probability
+    ctl->win_hi = rh <= 0 ? 0x7ff0000000000000ull : ~(((uint64_t)a[rh] << 31) | (1ull << 63));
+    ctl->win_lo = rl >= SAMPLE_N - 1 ? 0ull : ~((((uint64_t)a[rl] << 31) | (1ull << 63)) | 0x7fffffffull);
+  }
+}
+
+constexpr int WP_BLOCK = 256, WP_ITEMS = 16;
+constexpr int WP_TILE = WP_BLOCK * WP_ITEMS;
+
+__device__ __forceinline__ u128 warp_sum_u128(u128 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    uint64_t hi = __shfl_xor_sync(0xffffffffu, (unsigned long long)(v >> 64), o);
+    uint64_t lo = __shfl_xor_sync(0xffffffffu, (unsigned long long)(uint64_t)v, o);
+    v += make_u128(hi, lo);
+  }
+  return v;
+}
+
+// One streaming pass over all terms (tile t = terms [t*WP_TILE, ...),
+// static assignment): the exact fixed-point total mass, the count and mass
+// above the window, the window's mass and its terms (probability, key, index)
+// gathered into the window buffer, and per tile the number of terms above
+// the window (they are kept whatever the exact cut is).
+__global__ void __launch_bounds__(WP_BLOCK) k_window_pass(const uint64_t* __restrict__ probs,
+                                                          const uint64_t* __restrict__ keys, uint64_t n,
+                                                          Ctl* ctl, uint64_t* __restrict__ wp,
+                                                          uint64_t* __restrict__ wk, uint32_t* __restrict__ wi,
+                                                          uint64_t cap, uint32_t* __restrict__ tile_keep) {
+  typedef TileLayout<WP_BLOCK, WP_ITEMS> L;
+  __shared__ uint32_t s_warp[WP_BLOCK / 32];
+  __shared__ uint32_t s_above[WP_BLOCK / 32];
+  __shared__ uint64_t s_base;
+  const uint64_t hi = ctl->win_hi, lo = ctl->win_lo;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t lt = (1u << lane) - 1u;
+  u128 tot = 0, above_m = 0, win_m = 0;
+  uint64_t above_c = 0;
+  const uint64_t tiles = (n + L::TILE - 1) / L::TILE;
+  for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const uint64_t base = tile * L::TILE;
+    uint64_t pbv[WP_ITEMS];
+#pragma unroll
+    for (int j = 0; j < WP_ITEMS; ++j) {  // all loads first
+      const uint64_t i = L::index(base, j);
+      pbv[j] = i < n ? probs[i] : 0ull;
+    }
+    uint32_t wmask = 0, run = 0, tile_above = 0;
+    uint16_t wpos[WP_ITEMS];
+#pragma unroll
+    for (int j = 0; j < WP_ITEMS; ++j) {
+      const uint64_t pb = pbv[j];
+      const u128 f = fx_from_bits(pb, &ctl->err);
+      tot += f;
+      const bool valid = L::index(base, j) < n;
+      const bool above = valid && pb > hi;
+      const bool inwin = valid && !above && pb >= lo;
+      if (above) {
+        ++tile_above;
+        above_m += f;
+      }
+      if (inwin) {
+        win_m += f;
+        wmask |= 1u << j;
+      }
+      const uint32_t b = __ballot_sync(0xffffffffu, inwin);
+      wpos[j] = (uint16_t)(run + __popc(b & lt));
+      run += __popc(b);
+    }
+    above_c += tile_above;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tile_above += __shfl_xor_sync(0xffffffffu, tile_above, o);
+    if (lane == 0) {
+      s_warp[warp] = run;
+      s_above[warp] = tile_above;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t acc = 0, ab = 0;
+      for (int w = 0; w < WP_BLOCK / 32; ++w) {
+        uint32_t c = s_warp[w];
+        s_warp[w] = acc;
+        acc += c;
+        ab += s_above[w];
+      }
+      tile_keep[tile] = ab;
+      s_base = acc ? atomicAdd((unsigned long long*)&ctl->win_n, (unsigned long long)acc) : 0ull;
+    }
+    __syncthreads();
+    const uint64_t wbase = s_base + s_warp[warp];
+#pragma unroll
+    for (int j = 0; j < WP_ITEMS; ++j) {
+      if ((wmask >> j) & 1u) {
+        const uint64_t o = wbase + wpos[j];
+        const uint64_t i = L::index(base, j);
+        if (o < cap) {
+          wp[o] = pbv[j];
+          wk[o] = keys[i];
+          wi[o] = (uint32_t)i;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  tot = warp_sum_u128(tot);
+  above_m = warp_sum_u128(above_m);
+  win_m = warp_sum_u128(win_m);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) above_c += __shfl_xor_sync(0xffffffffu, (unsigned long long)above_c, o);
+  if (lane == 0) {
+    atomic_add_u128(&ctl->total_mass_hi, &ctl->total_mass_lo, tot);
+    atomic_add_u128(&ctl->above_mass_hi, &ctl->above_mass_lo, above_m);
+    atomic_add_u128(&ctl->win_mass_hi, &ctl->win_mass_lo, win_m);
+    atomicAdd((unsigned long long*)&ctl->above_count, (unsigned long long)above_c);
+  }
+}
+
+// One thread: choose between the window and the full list and set up the
+// select state (target from the exact total mass).
+__global__ void k_window_decide(Ctl* ctl, int mode, uint64_t count_target, double p, uint64_t cap) {
+  const u128 total = make_u128(ctl->total_mass_hi, ctl->total_mass_lo);
+  u128 target;
+  if (mode == 0) {
+    double T = __dmul_rn(p, fx_to_double(total));
+    target = fx_from_bits((uint64_t)__double_as_longlong(T), &ctl->err);
+  } else {
+    target = (u128)count_target;
+  }
+  const u128 am = make_u128(ctl->above_mass_hi, ctl->above_mass_lo);
+  const u128 wm = make_u128(ctl->win_mass_hi, ctl->win_mass_lo);
+  const uint64_t ac = ctl->above_count, wn = ctl->win_n;
+  bool valid = wn <= cap && wn > 0;
+  if (mode == 1) valid = valid && (u128)ac < target && target <= (u128)(ac + wn);
+  else valid = valid && am < target && target <= am + wm;
+  // Every window term has ~prob in [~hi, ~lo], so all share the common
+  // leading bits of those two patterns: the select starts below them.
+  uint64_t zh = ~ctl->win_hi, zl = ~ctl->win_lo;
+  int common = valid ? __clzll((long long)(zh ^ zl)) : 1;
+  if (common < 1) common = 1;
+  if (common > 64) common = 64;
+  ctl->sel_prefix_hi = common >= 64 ? zh : (zh & ~((~0ull) >> common));
+  ctl->sel_prefix_lo = 0;
+  ctl->sel_bits = (uint32_t)common;
+  ctl->sel_mode = (uint32_t)mode;
+  ctl->sel_done = 0;
+  ctl->sel_target_hi = (uint64_t)(target >> 64);
+  ctl->sel_target_lo = (uint64_t)target;
+  ctl->compact_n = 0;
+  ctl->use_window = valid ? 1u : 0u;
+  ctl->sel_before_count = valid ? ac : 0;
+  ctl->sel_before_mass_hi = valid ? ctl->above_mass_hi : 0;
+  ctl->sel_before_mass_lo = valid ? ctl->above_mass_lo : 0;
+  ctl->sel_bin_count = valid ? wn : 0;
+}
+
+void launch_select_window(const uint64_t* probs, const uint64_t* keys, uint64_t n, Ctl* ctl,
+                          const SelectScratch& ss, int mode, uint64_t count_target, double p,
+                          cudaStream_t st) {
+  static bool attr_set = false;
+  const size_t smem = 4 * (2 * SAMPLE_N + 32 * 256) + 8 * SAMPLE_THREADS;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_sample_window, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr_set = true;
+  }
+  cudaMemsetAsync(&ctl->win_n, 0, sizeof(uint64_t) * 6, st);  // win_n .. win_mass_lo
+  cudaMemsetAsync(&ctl->total_mass_hi, 0, sizeof(uint64_t) * 2, st);
+  k_sample_window<<<1, SAMPLE_THREADS, smem, st>>>(probs, n, ctl, mode, count_target, p);
+  uint64_t tiles = (n + WP_TILE - 1) / WP_TILE;
+  uint64_t grid = tiles < 148 * 8 ? tiles : 148 * 8;
+  if (grid == 0) grid = 1;
+  k_window_pass<<<(unsigned)grid, WP_BLOCK, 0, st>>>(probs, keys, n, ctl, ss.win_p, ss.win_k, ss.win_i,
+                                                     ss.win_cap, ss.tile_keep);
+  k_window_decide<<<1, 1, 0, st>>>(ctl, mode, count_target, p, ss.win_cap);
+}
+
+uint64_t window_tiles(uint64_t n) { return (n + WP_TILE - 1) / WP_TILE; }
+
+// ---------------------------------------------------------------- windowed compaction
+// After a select on the window: every tile's kept count is its count above
+// the window plus its window terms not after the cut.
+__global__ void k_window_tile_counts(const uint64_t* __restrict__ wp, const uint64_t* __restrict__ wk,
+                                     const uint32_t* __restrict__ wi, Ctl* ctl,
+                                     uint32_t* __restrict__ tile_keep) {
+  const uint64_t wn = ctl->win_n;
+  const uint64_t pc = ctl->cut_pbits, kc = ctl->cut_key;
+  for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < wn;
+       j += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t pb = wp[j];
+    if (pb > pc || (pb == pc && wk[j] <= kc)) atomicAdd(&tile_keep[wi[j] / WP_TILE], 1u);
+  }
+}
+
+// Exclusive scan of the per-tile kept counts by one block.
+__global__ void __launch_bounds__(1024) k_tile_scan(const uint32_t* __restrict__ tile_keep, uint64_t tiles,
+                                                    uint64_t* __restrict__ tile_off, Ctl* ctl) {
+  __shared__ uint64_t wsum[32];
+  __shared__ uint64_t s_carry;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) s_carry = 0;
+  __syncthreads();
+  for (uint64_t b0 = 0; b0 < tiles; b0 += 1024) {
+    const uint64_t t = b0 + threadIdx.x;
+    const uint64_t v = t < tiles ? tile_keep[t] : 0;
+    uint64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint64_t y = __shfl_up_sync(0xffffffffu, (unsigned long long)x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    uint64_t base = s_carry;
+    for (int w = 0; w < warp; ++w) base += wsum[w];
+    if (t < tiles) tile_off[t] = base + x - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) s_carry = base + x;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) ctl->count[2] = s_carry;
 }
 
 // ---------------------------------------------------------------- pick
@@ -130,7 +519,6 @@ __device__ void block_pick(const uint32_t* cnt, const uint64_t* mass /* [nbins][
   __shared__ uint64_t w_c[PICK_THREADS / 32];
   __shared__ u128 w_m[PICK_THREADS / 32];
   __shared__ uint32_t s_first;
-  __shared__ u128 s_total;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int bits = (int)ctl->sel_bits;
   int D, shift;
@@ -173,18 +561,6 @@ __device__ void block_pick(const uint32_t* cnt, const uint64_t* mass /* [nbins][
   }
   const uint64_t excl_c = base_c + xc - my_c;
   const u128 excl_m = base_m + xm - my_m;
-  if (bits == 1 && tid == 0) {
-    // first level: every term is in some bin, so this is S_N
-    ctl->total_mass_hi = (uint64_t)(total >> 64);
-    ctl->total_mass_lo = (uint64_t)total;
-    if (ctl->sel_mode == 0) {
-      double T = __dmul_rn(p, fx_to_double(total));
-      u128 t = fx_from_bits((uint64_t)__double_as_longlong(T), &ctl->err);
-      ctl->sel_target_hi = (uint64_t)(t >> 64);
-      ctl->sel_target_lo = (uint64_t)t;
-    }
-    s_total = total;
-  }
   __syncthreads();
   const uint32_t mode = ctl->sel_mode;
   const u128 target = make_u128(ctl->sel_target_hi, ctl->sel_target_lo);
@@ -325,7 +701,7 @@ __global__ void k_set_scale(Ctl* ctl) {
 
 void launch_set_scale(Ctl* ctl, cudaStream_t st) { k_set_scale<<<1, 1, 0, st>>>(ctl); }
 
-constexpr int TC_BLOCK = 256, TC_ITEMS = 4;
+constexpr int TC_BLOCK = 256, TC_ITEMS = 8;
 
 template <typename C2>
 __device__ __forceinline__ C2 scale_amp(C2 a, double s);
@@ -339,6 +715,10 @@ __device__ __forceinline__ float2 scale_amp<float2>(float2 a, double s) {
                      __double2float_rn(__dmul_rn((double)a.y, s)));
 }
 
+// Keep the terms not after the cut (probability above the cut's, or equal
+// with key not above it), in input order, scaled by ctl->scale.  Only the
+// probability is read for every term; keys (for ties at the cut) and
+// amplitudes are read for the kept terms.
 template <typename C2>
 __global__ void __launch_bounds__(TC_BLOCK) k_truncate_compact(
     const uint64_t* __restrict__ keys, const C2* __restrict__ amps, const uint64_t* __restrict__ probs,
@@ -358,33 +738,24 @@ __global__ void __launch_bounds__(TC_BLOCK) k_truncate_compact(
     const uint64_t base = tile * L::TILE;
     bool flag[TC_ITEMS];
     uint32_t pos[TC_ITEMS];
-    uint64_t kk[TC_ITEMS];
 #pragma unroll
     for (int j = 0; j < TC_ITEMS; ++j) {
-      uint64_t i = L::index(base, j);
+      const uint64_t i = L::index(base, j);
       bool f = false;
-      uint64_t key = 0;
       if (i < n) {
-        uint64_t pb = probs[i];
-        if (pb > pc) {
-          f = true;
-          key = keys[i];
-        } else if (pb == pc) {
-          key = keys[i];
-          f = key <= kc;
-        }
+        const uint64_t pb = probs[i];
+        f = pb > pc || (pb == pc && keys[i] <= kc);
       }
       flag[j] = f;
-      kk[j] = key;
     }
     tile_compact<TC_BLOCK, TC_ITEMS>(flag, pos, cs, lookback, tile, &ctl->err);
 #pragma unroll
     for (int j = 0; j < TC_ITEMS; ++j) {
       if (flag[j]) {
-        uint64_t i = L::index(base, j);
-        uint64_t o = cs.tile_base_out + pos[j];
-        C2 a = scale_amp<C2>(amps[i], s);
-        keys_out[o] = kk[j];
+        const uint64_t i = L::index(base, j);
+        const uint64_t o = cs.tile_base_out + pos[j];
+        const C2 a = scale_amp<C2>(amps[i], s);
+        keys_out[o] = keys[i];
         amps_out[o] = a;
         probs_out[o] = (uint64_t)__double_as_longlong(prob_of((double)a.x, (double)a.y));
       }
@@ -392,6 +763,67 @@ __global__ void __launch_bounds__(TC_BLOCK) k_truncate_compact(
     if (tile == tiles - 1 && threadIdx.x == 0) ctl->count[2] = cs.tile_base_out + cs.tile_total;
     __syncthreads();
   }
+}
+
+// Windowed compaction: tile t (same tiling as the window pass) writes its
+// kept terms from tile_off[t] on, in input order; no cross-tile waiting.
+template <typename C2>
+__global__ void __launch_bounds__(WP_BLOCK) k_truncate_write(
+    const uint64_t* __restrict__ keys, const C2* __restrict__ amps, const uint64_t* __restrict__ probs,
+    uint64_t n, const uint64_t* __restrict__ tile_off, uint64_t* __restrict__ keys_out,
+    C2* __restrict__ amps_out, uint64_t* __restrict__ probs_out, const Ctl* ctl) {
+  typedef TileLayout<WP_BLOCK, WP_ITEMS> L;
+  __shared__ CompactShared<WP_BLOCK> cs;
+  const uint64_t pc = ctl->cut_pbits, kc = ctl->cut_key;
+  const double s = ctl->scale;
+  const uint64_t tiles = (n + L::TILE - 1) / L::TILE;
+  for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const uint64_t base = tile * L::TILE;
+    uint64_t pbv[WP_ITEMS];
+#pragma unroll
+    for (int j = 0; j < WP_ITEMS; ++j) {
+      const uint64_t i = L::index(base, j);
+      pbv[j] = i < n ? probs[i] : 0ull;
+    }
+    bool flag[WP_ITEMS];
+    uint32_t pos[WP_ITEMS];
+#pragma unroll
+    for (int j = 0; j < WP_ITEMS; ++j) {
+      const uint64_t i = L::index(base, j);
+      flag[j] = i < n && (pbv[j] > pc || (pbv[j] == pc && keys[i] <= kc));
+    }
+    tile_local_positions<WP_BLOCK, WP_ITEMS>(flag, pos, cs);
+    const uint64_t ob = tile_off[tile];
+#pragma unroll
+    for (int j = 0; j < WP_ITEMS; ++j) {
+      if (flag[j]) {
+        const uint64_t i = L::index(base, j);
+        const uint64_t o = ob + pos[j];
+        const C2 a = scale_amp<C2>(amps[i], s);
+        keys_out[o] = keys[i];
+        amps_out[o] = a;
+        probs_out[o] = (uint64_t)__double_as_longlong(prob_of((double)a.x, (double)a.y));
+      }
+    }
+    __syncthreads();
+  }
+}
+
+void launch_truncate_windowed(int prec, const uint64_t* keys, const void* amps, const uint64_t* probs,
+                              uint64_t n, uint64_t* keys_out, void* amps_out, uint64_t* probs_out,
+                              const SelectScratch& ss, Ctl* ctl, cudaStream_t st) {
+  const uint64_t tiles = window_tiles(n);
+  k_set_scale<<<1, 1, 0, st>>>(ctl);
+  k_window_tile_counts<<<148 * 4, 256, 0, st>>>(ss.win_p, ss.win_k, ss.win_i, ctl, ss.tile_keep);
+  k_tile_scan<<<1, 1024, 0, st>>>(ss.tile_keep, tiles, ss.tile_off, ctl);
+  uint64_t grid = tiles < 148 * 8 ? tiles : 148 * 8;
+  if (grid == 0) grid = 1;
+  if (prec == 0)
+    k_truncate_write<double2><<<(unsigned)grid, WP_BLOCK, 0, st>>>(
+        keys, (const double2*)amps, probs, n, ss.tile_off, keys_out, (double2*)amps_out, probs_out, ctl);
+  else
+    k_truncate_write<float2><<<(unsigned)grid, WP_BLOCK, 0, st>>>(
+        keys, (const float2*)amps, probs, n, ss.tile_off, keys_out, (float2*)amps_out, probs_out, ctl);
 }
 
 void launch_truncate_compact(int prec, const uint64_t* keys, const void* amps, const uint64_t* probs,
@@ -402,7 +834,7 @@ void launch_truncate_compact(int prec, const uint64_t* keys, const void* amps, c
   cudaMemsetAsync(&ctl->tile_counter[2], 0, sizeof(uint64_t), st);
   cudaMemsetAsync(&ctl->count[2], 0, sizeof(uint64_t), st);
   if (n == 0) return;
-  uint64_t grid = tiles < 148 * 4 ? tiles : 148 * 4;
+  uint64_t grid = tiles < 148 * 8 ? tiles : 148 * 8;
   if (prec == 0)
     k_truncate_compact<double2><<<(unsigned)grid, TC_BLOCK, 0, st>>>(
         keys, (const double2*)amps, probs, n, keys_out, (double2*)amps_out, probs_out, lookback, ctl);
