@@ -127,6 +127,8 @@ def phase_model(ph: str, totals: dict, prec: str, passes: int):
         return {"bytes": 8 * n_kept, "flops": 0.0}
     if ph == "heads":
         return {"bytes": 8 * n_in, "flops": 0.0}
+    if ph == "local":    # read key + amplitude per input; write key + amp + prob per candidate
+        return {"bytes": (8 + sa) * n_in + (16 + sa) * n_pre, "flops": totals["dfma"] * 2.0}
     return {"bytes": 0.0, "flops": 0.0}
 
 
@@ -208,9 +210,11 @@ def run_ours(args, rank, world):
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             ms = float(t.item())
         peak = st.peak()
+        fin = st.stats()
+        paths = {k: fin[k] for k in ("local_gates", "global_gates", "local_fallbacks")}
         st.close()
         return {"ms": ms, "totals": totals, "phases": phases, "launches": launches, "clocks": clk,
-                "peak": peak, "hidden": circ.hidden}
+                "peak": peak, "hidden": circ.hidden, "paths": paths}
 
     main = run_prec(args.prec, args.K, args.steps, args.warmup, sample_clocks=True)
     res = {"main": main}
@@ -402,6 +406,7 @@ def main():
         "clocks": main_r["clocks"],
         "peak_key": main_r["peak"][0],
         "totals": {k: (int(v) if isinstance(v, (int, float)) and k != "dfma" else v) for k, v in tot.items()},
+        "gate_paths": main_r.get("paths"),
     }
     if "c64" in res:
         c = res["c64"]

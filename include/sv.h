@@ -127,7 +127,9 @@ const char* sv_last_error(const sv_state* s);
  * terms before the gate, candidates after it, terms kept by the last
  * truncation, radix-sort passes run, select levels run, the total and kept
  * probability masses of the last truncation, how many of its selects ran on
- * the sampled window (window_hits) and the window size of the last one. */
+ * the sampled window (window_hits) and the window size of the last one, and
+ * how many gates so far were applied inside buckets of the state versus
+ * through the global grouping sort. */
 typedef struct {
   uint64_t n_in, n_pre, n_kept;
   uint32_t sort_passes;
@@ -136,6 +138,9 @@ typedef struct {
   uint32_t window_hits;
   uint32_t pad;
   uint64_t window_terms;
+  uint64_t local_gates;   /* gates applied bucket-locally so far (no global sort) */
+  uint64_t global_gates;  /* gates that needed the global sort so far */
+  uint64_t local_fallbacks; /* local attempts redone globally (bucket too large) */
 } sv_stats;
 sv_status sv_last_stats(const sv_state* s, sv_stats* out);
 
@@ -145,9 +150,10 @@ sv_status sv_last_stats(const sv_state* s, sv_stats* out);
  * order: 0 gate key transform + digit histograms, 1 radix-sort passes,
  * 2 partner-group heads, 3 group mat-vec, 4 truncation select levels,
  * 5 truncation compaction, 6 peak, 7 other (readout, load), 8 truncation
- * sample window pass.  ms and launches (nullable) receive SV_NUM_PHASES
- * entries: milliseconds and kernel launches. */
-#define SV_NUM_PHASES 9
+ * sample window pass, 9 bucket-local gate (and bucket-size check).  ms and
+ * launches (nullable) receive SV_NUM_PHASES entries: milliseconds and kernel
+ * launches. */
+#define SV_NUM_PHASES 10
 sv_status sv_set_timing(sv_state* s, int enable);
 sv_status sv_phase_times(const sv_state* s, double* ms, uint64_t* launches);
 

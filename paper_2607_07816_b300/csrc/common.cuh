@@ -12,6 +12,7 @@ typedef unsigned __int128 u128;
 constexpr uint32_t ERR_TIMEOUT = 1u;   // a bounded spin-wait gave up
 constexpr uint32_t ERR_MASS = 2u;      // a probability too large for the fixed-point mass
 constexpr uint32_t ERR_INVARIANT = 4u; // duplicate keys reached a gate (groups larger than 2^m)
+constexpr uint32_t ERR_BUCKET = 8u;    // a bucket exceeded the local-gate batch limit (recoverable)
 
 // Bounded waits: a decoupled look-back poll gives up after this many polls
 // (with exponential __nanosleep back-off capped at 256 ns: about a second).
@@ -103,6 +104,49 @@ __device__ __forceinline__ uint64_t lookback_exclusive(uint64_t* lb, uint32_t st
   return excl;
 }
 
+// As lookback_exclusive, but each round issues four independent loads of the
+// nearest unresolved predecessors, cutting the dependent-load latency of a
+// long walk by four.
+__device__ __forceinline__ uint64_t lookback_exclusive_x4(uint64_t* lb, uint32_t stride, uint64_t tile,
+                                                          uint64_t agg, uint32_t* err) {
+  if (tile == 0) {
+    st_release(lb, LB_INC | agg);
+    return 0;
+  }
+  st_release(lb + tile * stride, LB_AGG | agg);
+  uint64_t excl = 0;
+  int64_t t = (int64_t)tile - 1;
+  uint32_t spins = 0, ns = 8;
+  while (t >= 0) {
+    uint64_t v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = (t - k >= 0) ? ld_acquire(lb + (uint64_t)(t - k) * stride) : LB_INC;
+    int k = 0;
+    bool done = false;
+    for (; k < 4; ++k) {
+      const uint64_t st = v[k] >> 62;
+      if (st == 0) break;
+      excl += v[k] & LB_VAL;
+      if (st == 2) {
+        done = true;
+        break;
+      }
+    }
+    if (done) break;
+    t -= k;
+    if (k < 4) {
+      if (++spins > SPIN_LIMIT) {
+        atomicOr(err, ERR_TIMEOUT);
+        break;
+      }
+      __nanosleep(ns);
+      if (ns < 256) ns <<= 1;
+    }
+  }
+  st_release(lb + tile * stride, LB_INC | (excl + agg));
+  return excl;
+}
+
 // Warp-cooperative decoupled look-back over a single chain: all 32 lanes of
 // one warp call it.  The warp polls a window of 32 predecessor descriptors at
 // once, waits until every descriptor from the nearest inclusive prefix up to
@@ -176,6 +220,15 @@ __device__ __forceinline__ uint64_t spread_in(uint64_t x, const int* qs, int m) 
     }
   }
   return x;
+}
+
+// A bit permutation of 64-bit keys as 16 nibble tables: the image of x is
+// the OR of t[k][nibble k of x].
+__device__ __forceinline__ uint64_t permute_bits(const uint64_t (*t)[16], uint64_t x) {
+  uint64_t y = 0;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) y |= t[k][(x >> (4 * k)) & 15u];
+  return y;
 }
 
 // floor(p * 2^120) for the bit pattern b of a non-negative double p < 2^7.

@@ -13,28 +13,18 @@
 
 namespace sv {
 
-struct KeyParams {
-  uint64_t qmask;
-  int m;
-  int q[4];
-  int qs[4];
-};
-
 __global__ void __launch_bounds__(256) k_gate_keys(const uint64_t* __restrict__ keys, uint64_t n,
-                                                   KeyParams kp, uint64_t* __restrict__ sk,
-                                                   uint32_t* __restrict__ sidx,
+                                                   const BitPerm* __restrict__ perm,
+                                                   uint64_t* __restrict__ sk, uint32_t* __restrict__ sidx,
                                                    uint32_t* __restrict__ hist, int passes) {
   __shared__ uint32_t sh[MAX_PASSES][RADIX];
+  __shared__ uint64_t fwd[16][16];
   for (int i = threadIdx.x; i < MAX_PASSES * RADIX; i += blockDim.x) (&sh[0][0])[i] = 0;
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) (&fwd[0][0])[i] = (&perm->fwd[0][0])[i];
   __syncthreads();
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
        i += (uint64_t)gridDim.x * blockDim.x) {
-    uint64_t key = keys[i];
-    uint32_t r = 0;
-#pragma unroll
-    for (int t = 0; t < 4; ++t)
-      if (t < kp.m) r |= (uint32_t)((key >> kp.q[t]) & 1ull) << t;
-    uint64_t s = (squeeze_out(key, kp.qs, kp.m) << kp.m) | r;
+    const uint64_t s = permute_bits(fwd, keys[i]);
     sk[i] = s;
     sidx[i] = (uint32_t)i;
     for (int p = 0; p < passes; ++p) atomicAdd(&sh[p][(s >> (RADIX_BITS * p)) & (RADIX - 1)], 1u);
@@ -48,18 +38,11 @@ __global__ void __launch_bounds__(256) k_gate_keys(const uint64_t* __restrict__ 
 
 void launch_gate_keys(const uint64_t* keys, uint64_t n, const GateParams& gp, uint64_t* sk,
                       uint32_t* sidx, uint32_t* hist, int passes, cudaStream_t st) {
-  KeyParams kp;
-  kp.qmask = gp.qmask;
-  kp.m = gp.m;
-  for (int t = 0; t < 4; ++t) {
-    kp.q[t] = gp.q[t];
-    kp.qs[t] = gp.qs[t];
-  }
   cudaMemsetAsync(hist, 0, sizeof(uint32_t) * MAX_PASSES * RADIX, st);
   if (n == 0) return;
   uint64_t blocks = (n + 255) / 256;
   if (blocks > 148 * 8) blocks = 148 * 8;
-  k_gate_keys<<<(unsigned)blocks, 256, 0, st>>>(keys, n, kp, sk, sidx, hist, passes);
+  k_gate_keys<<<(unsigned)blocks, 256, 0, st>>>(keys, n, gp.perm, sk, sidx, hist, passes);
 }
 
 // ------------------------------------------------------------------ heads
@@ -122,25 +105,32 @@ struct Cplx<float> {
 __device__ __forceinline__ double fma_r(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ float fma_r(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 
-constexpr int APPLY_BLOCK = 256, APPLY_ITEMS = 8;
-constexpr int APPLY_TILE = APPLY_BLOCK * APPLY_ITEMS;  // output slots per tile (multiple of 16)
+constexpr int APPLY_BLOCK = 512;
+constexpr int APPLY_TILE = 2048;                      // output slots per tile (multiple of 16)
+constexpr int APPLY_ITEMS = APPLY_TILE / APPLY_BLOCK;  // 4
 
 template <typename Real>
 struct ApplySmem {
   typedef typename Cplx<Real>::T C2;
-  C2 x[APPLY_TILE];                    // gathered member amplitudes
-  uint8_t r[APPLY_TILE];               // member local index
-  uint32_t head[APPLY_TILE / 2 + 1];   // member offsets of the tile's groups
-  uint64_t rest[APPLY_TILE / 2];       // squeezed key of each group
+  C2 x[APPLY_TILE];                     // gathered member amplitudes
+  C2 y[APPLY_TILE];                     // outputs, by slot
+  uint64_t rest[APPLY_TILE / 2];        // squeezed key of each group
+  uint32_t head[APPLY_TILE / 2 + 1];    // member offsets of the tile's groups
+  uint16_t order[APPLY_TILE / 2];       // groups sorted by member count
+  uint32_t present[APPLY_TILE / 2];     // member mask of each group
+  uint8_t r[APPLY_TILE];                // member local index
+  uint32_t size_count[17];
 };
 
 // One tile = APPLY_TILE consecutive output slots (group g, output r'), i.e.
-// APPLY_TILE / 2^m whole groups.  Phase 1 stages the groups' members (their
-// r and gathered amplitudes) in shared memory with independent loads;
-// phase 2 computes one output per slot from shared memory; phase 3 drops
-// zero outputs and writes the survivors in slot order.
+// APPLY_TILE / 2^m whole groups.  Phase 1 stages the groups' members (local
+// index and gathered amplitude) in shared memory with independent loads and
+// orders the groups by member count, so that the lanes of a warp run
+// multiply-add chains of equal length.  Phase 2 computes one output per slot
+// in that order and parks it in shared memory under its original slot.
+// Phase 3 drops exact zeros and writes the survivors in slot order.
 template <typename Real>
-__global__ void __launch_bounds__(APPLY_BLOCK) k_gate_apply(
+__global__ void __launch_bounds__(APPLY_BLOCK, 2) k_gate_apply(
     const uint64_t* __restrict__ sk, const uint32_t* __restrict__ sidx, uint64_t n,
     const uint32_t* __restrict__ heads, const typename Cplx<Real>::T* __restrict__ amps_in,
     const GateParams gp, uint64_t* __restrict__ keys_out, typename Cplx<Real>::T* __restrict__ amps_out,
@@ -151,10 +141,12 @@ __global__ void __launch_bounds__(APPLY_BLOCK) k_gate_apply(
   ApplySmem<Real>& sm = *reinterpret_cast<ApplySmem<Real>*>(s_dyn);
   __shared__ Real sU[512];
   __shared__ uint32_t s_re_nz[16], s_im_nz[16];
+  __shared__ uint64_t s_inv[16][16];
   __shared__ CompactShared<APPLY_BLOCK> cs;
   __shared__ uint64_t s_tile;
   const int m = gp.m, d = 1 << m;
   for (int i = threadIdx.x; i < 2 * d * d; i += APPLY_BLOCK) sU[i] = (Real)gp.U[i];
+  for (int i = threadIdx.x; i < 256; i += APPLY_BLOCK) (&s_inv[0][0])[i] = (&gp.perm->inv[0][0])[i];
   if (threadIdx.x < 16) {
     s_re_nz[threadIdx.x] = gp.re_nz[threadIdx.x];
     s_im_nz[threadIdx.x] = gp.im_nz[threadIdx.x];
@@ -166,11 +158,12 @@ __global__ void __launch_bounds__(APPLY_BLOCK) k_gate_apply(
   const uint32_t groups_per_tile = (uint32_t)APPLY_TILE >> m;
   while (true) {
     if (threadIdx.x == 0) s_tile = atomicAdd((unsigned long long*)&ctl->tile_counter[1], 1ull);
+    if (threadIdx.x < 17) sm.size_count[threadIdx.x] = 0;
     __syncthreads();
     const uint64_t tile = s_tile;
     if (tile >= tiles) break;
     const uint64_t base = tile * APPLY_TILE;
-    // ---- phase 1: stage
+    // ---- phase 1: stage members, group heads and sizes
     const uint64_t g0 = base >> m;
     const uint64_t g1 = g0 + groups_per_tile < G ? g0 + groups_per_tile : G;
     const uint32_t ng = (uint32_t)(g1 - g0);
@@ -183,7 +176,7 @@ __global__ void __launch_bounds__(APPLY_BLOCK) k_gate_apply(
     }
     for (uint32_t k = threadIdx.x; k < ng; k += APPLY_BLOCK) {
       uint64_t h = heads[g0 + k];
-      sm.head[k] = (uint32_t)(h - mbase);
+      sm.head[k] = min((uint32_t)(h - mbase), nm);
       sm.rest[k] = sk[h] >> m;
     }
     if (threadIdx.x == 0) sm.head[ng] = nm;
@@ -193,25 +186,38 @@ __global__ void __launch_bounds__(APPLY_BLOCK) k_gate_apply(
       sm.x[k] = amps_in[sidx[i]];
     }
     __syncthreads();
-    // ---- phase 2: one output per slot
-    bool flag[APPLY_ITEMS];
-    uint32_t pos[APPLY_ITEMS];
-    Real yr[APPLY_ITEMS], yi[APPLY_ITEMS];
-    uint64_t ykey[APPLY_ITEMS];
+    for (uint32_t k = threadIdx.x; k < ng; k += APPLY_BLOCK) {
+      uint32_t pm = 0;
+      for (uint32_t q = sm.head[k]; q < sm.head[k + 1]; ++q) pm |= 1u << sm.r[q];
+      sm.present[k] = pm;
+      atomicAdd(&sm.size_count[__popc(pm)], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {  // exclusive offsets of the size classes
+      uint32_t acc = 0;
+      for (int c = 0; c <= 16; ++c) {
+        uint32_t v = sm.size_count[c];
+        sm.size_count[c] = acc;
+        acc += v;
+      }
+    }
+    __syncthreads();
+    for (uint32_t k = threadIdx.x; k < ng; k += APPLY_BLOCK)
+      sm.order[atomicAdd(&sm.size_count[__popc(sm.present[k])], 1u)] = (uint16_t)k;
+    __syncthreads();
+    // ---- phase 2: one output per slot, groups in size order
+    const uint32_t nslots = ng << m;
 #pragma unroll
     for (int j = 0; j < APPLY_ITEMS; ++j) {
-      const uint64_t slot = L::index(base, j);
-      Real re = (Real)0, im = (Real)0;
-      uint64_t key = 0;
-      if (slot < S) {
-        const uint32_t ls = (uint32_t)(slot - base);
-        const uint32_t gl = ls >> m;
+      const uint32_t ls = (uint32_t)j * APPLY_BLOCK + threadIdx.x;
+      if (ls < nslots) {
+        const uint32_t gl = sm.order[ls >> m];
         const uint32_t ro = ls & dmask;
-        const uint32_t h = min(sm.head[gl], nm), e = min(sm.head[gl + 1], nm);
-        uint32_t present = 0;
-        for (uint32_t k = h; k < e; ++k) present |= 1u << sm.r[k];
+        const uint32_t h = sm.head[gl];
+        const uint32_t present = sm.present[gl];
         const uint32_t rnz = s_re_nz[ro] & present, inz = s_im_nz[ro] & present;
         uint32_t cols = rnz | inz;
+        Real re = (Real)0, im = (Real)0;
         while (cols) {
           const int r = __ffs(cols) - 1;
           cols &= cols - 1u;
@@ -226,28 +232,40 @@ __global__ void __launch_bounds__(APPLY_BLOCK) k_gate_apply(
             im = fma_r(ui, x.x, im);
           }
         }
-        key = spread_in(sm.rest[gl], gp.qs, m);
-#pragma unroll
-        for (int t = 0; t < 4; ++t)
-          if (t < m) key |= (uint64_t)((ro >> t) & 1u) << gp.q[t];
+        C2 yv;
+        yv.x = re;
+        yv.y = im;
+        sm.y[(gl << m) | ro] = yv;
       }
-      yr[j] = re;
-      yi[j] = im;
-      ykey[j] = key;
-      flag[j] = (slot < S) && !(re == (Real)0 && im == (Real)0);
     }
+    __syncthreads();
     // ---- phase 3: drop zeros, write in slot order
+    bool flag[APPLY_ITEMS];
+    uint32_t pos[APPLY_ITEMS];
+#pragma unroll
+    for (int j = 0; j < APPLY_ITEMS; ++j) {
+      const uint64_t slot = L::index(base, j);
+      const uint32_t ls = (uint32_t)(slot - base);
+      bool f = false;
+      if (slot < S) {
+        const C2 yv = sm.y[ls];
+        f = !(yv.x == (Real)0 && yv.y == (Real)0);
+      }
+      flag[j] = f;
+    }
     tile_compact<APPLY_BLOCK, APPLY_ITEMS>(flag, pos, cs, lookback, tile, &ctl->err);
 #pragma unroll
     for (int j = 0; j < APPLY_ITEMS; ++j) {
       if (flag[j]) {
+        const uint64_t slot = L::index(base, j);
+        const uint32_t ls = (uint32_t)(slot - base);
+        const uint32_t gl = ls >> m, ro = ls & dmask;
+        const uint64_t key = permute_bits(s_inv, (sm.rest[gl] << m) | ro);
+        const C2 yv = sm.y[ls];
         const uint64_t o = cs.tile_base_out + pos[j];
-        keys_out[o] = ykey[j];
-        C2 y;
-        y.x = yr[j];
-        y.y = yi[j];
-        amps_out[o] = y;
-        probs_out[o] = (uint64_t)__double_as_longlong(prob_of((double)yr[j], (double)yi[j]));
+        keys_out[o] = key;
+        amps_out[o] = yv;
+        probs_out[o] = (uint64_t)__double_as_longlong(prob_of((double)yv.x, (double)yv.y));
       }
     }
     if (tile == tiles - 1 && threadIdx.x == 0) ctl->count[1] = cs.tile_base_out + cs.tile_total;

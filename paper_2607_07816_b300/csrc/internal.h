@@ -38,6 +38,16 @@ void launch_digit_hist(const uint64_t* k, uint64_t n, int nbits, uint32_t* hist,
 int radix_sort_pairs(uint64_t* kA, uint32_t* vA, uint64_t* kB, uint32_t* vB, uint64_t n, int nbits,
                      const SortScratch& sc, cudaStream_t st, int* passes_run, cudaError_t* cerr);
 
+// Sort-key bit permutation of a gate: the bucket qubits P on top (first
+// listed = most significant), the remaining qubits outside the gate below
+// them in descending order, and the gate qubits at the bottom with
+// qubits[t] at bit t.  Equal (sort key >> m) <=> same partner group, with
+// members in ascending r; equal top |P| bits <=> same bucket.
+struct BitPerm {
+  uint64_t fwd[16][16];  // key -> sort key
+  uint64_t inv[16][16];  // sort key -> key
+};
+
 // Gate parameters passed by value to the gate kernels.
 struct GateParams {
   uint64_t qmask;
@@ -48,6 +58,10 @@ struct GateParams {
   uint32_t re_nz[16];  // bit r set when Re U[r_out][r] != 0
   uint32_t im_nz[16];  // bit r set when Im U[r_out][r] != 0
   double U[512];       // U[r_out][r] as (re, im), row-major
+  const BitPerm* perm; // device copy of this gate's sort-key permutation
+  int n;               // qubits
+  int tbits;           // number of bucket qubits (top bits of the sort key)
+  uint64_t pmask;      // bucket qubits as a key mask
 };
 
 void launch_gate_keys(const uint64_t* keys, uint64_t n, const GateParams& gp, uint64_t* sk,
@@ -64,6 +78,31 @@ void launch_gate_apply(int prec, const uint64_t* sk, const uint32_t* sidx, uint6
                        const uint32_t* heads, const void* amps_in, const GateParams& gp,
                        uint64_t* keys_out, void* amps_out, uint64_t* probs_out, uint64_t* lookback,
                        Ctl* ctl, cudaStream_t st, uint64_t max_tiles);
+
+// Local gate on a bucket-contiguous state (no bucket qubit in the gate):
+// each block takes the buckets that start in its chunk, sorts them in
+// shared memory by the gate's sort key, and writes its outputs into one
+// atomically reserved range sized by the structurally nonzero outputs.
+// Exact-zero outputs that the structure did not predict are written with a
+// zero amplitude and counted in ctl->count[3] (removed by
+// launch_drop_zero_terms).  Output count in ctl->count[1]; a bucket larger
+// than the batch limit sets ERR_BUCKET.
+constexpr int LOCAL_CHUNK = 4096;
+constexpr int LOCAL_CAP = 8192;
+constexpr uint64_t LOCAL_BUCKET_MAX = LOCAL_CAP - LOCAL_CHUNK;
+void launch_local_gate(int prec, const uint64_t* keys, const void* amps, uint64_t n, const GateParams& gp,
+                       uint64_t* keys_out, void* amps_out, uint64_t* probs_out, Ctl* ctl, cudaStream_t st);
+// Number of keys with each bit set (counts[0..63], device), for choosing
+// balanced bucket qubits.
+void launch_bit_counts(const uint64_t* keys, uint64_t n, int nbits, uint64_t* counts, cudaStream_t st);
+// Exact size of the largest bucket (up to limit; longer: limit + 1) into
+// ctl->count[0].
+void launch_bucket_check(const uint64_t* keys, uint64_t n, uint64_t pmask, uint64_t limit, Ctl* ctl,
+                         cudaStream_t st);
+// Order-preserving removal of zero-amplitude terms (count in ctl->count[2]).
+void launch_drop_zero_terms(int prec, const uint64_t* keys, const void* amps, const uint64_t* probs,
+                            uint64_t n, uint64_t* keys_out, void* amps_out, uint64_t* probs_out,
+                            uint64_t* lookback, Ctl* ctl, cudaStream_t st);
 
 // Truncation select.
 constexpr int SEL_BITS = 11;

@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(BLOCK) k_onesweep(const uint64_t* __restrict__
   const uint32_t local = block_exclusive_scan<BLOCK>(cnt, s_wtot);
   if (digit_thread) {
     s_local[tid] = local;
-    uint64_t excl = lookback_exclusive(lookback + tid, RADIX, tile, cnt, err);
+    uint64_t excl = lookback_exclusive_x4(lookback + tid, RADIX, tile, cnt, err);
     s_global[tid] = digit_base + excl;
   }
   __syncthreads();

@@ -11,6 +11,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 
@@ -20,7 +21,7 @@
 using namespace sv;
 
 // Phases timed with CUDA events when timing is on (sv_set_timing).
-enum Phase { PH_KEYS = 0, PH_SORT, PH_HEADS, PH_APPLY, PH_SELECT, PH_COMPACT, PH_PEAK, PH_OTHER, PH_WINDOW, PH_COUNT };
+enum Phase { PH_KEYS = 0, PH_SORT, PH_HEADS, PH_APPLY, PH_SELECT, PH_COMPACT, PH_PEAK, PH_OTHER, PH_WINDOW, PH_LOCAL, PH_COUNT };
 
 static std::atomic<uint64_t> g_launches{0};
 static std::atomic<uint64_t> g_h2d{0}, g_d2h{0};  // bytes crossing PCIe (copies and gate parameters)
@@ -60,6 +61,21 @@ struct sv_state {
   std::string err;
   bool broken = false;
   sv_stats stats{};
+
+  // bucket-contiguity of the state (see local.cu)
+  bool bucket_ok = false;       // terms equal on the bucket qubits are adjacent
+  uint64_t pmask = 0;           // bucket qubits
+  int tbits = 0;
+  int plist[64] = {};           // bucket qubits, most significant first
+  uint64_t max_bucket = 0;      // upper bound on the largest bucket (0: unknown)
+  uint64_t live = 0;            // superset of the key bits that vary over the state
+  int64_t last_use[64] = {};    // gate index of each qubit's last use (-1: never)
+  int64_t gate_index = 0;
+  BitPerm* perm_dev = nullptr;
+  BitPerm* perm_host = nullptr;
+  uint64_t* bitcnt_dev = nullptr;
+  uint64_t* bitcnt_host = nullptr;
+  uint64_t local_gates = 0, global_gates = 0, local_fallbacks = 0;
 
   bool timing = false;
   cudaEvent_t ev_beg[PH_COUNT] = {};
@@ -319,6 +335,81 @@ double u128_to_double(uint64_t hi, uint64_t lo) {
   return std::ldexp((double)v, -120);
 }
 
+// Sort-key permutation of a gate: bucket qubits (plist) on top, the other
+// qubits outside the gate below them in descending order, gate qubit t at
+// bit t.  Writes the forward and inverse nibble tables.
+void build_perm(int n, int m, const int* q, int tbits, const int* plist, BitPerm* bp) {
+  int pos[64];
+  for (int b = 0; b < 64; ++b) pos[b] = -1;
+  for (int t = 0; t < m; ++t) pos[q[t]] = t;
+  int next = n - 1;
+  for (int i = 0; i < tbits; ++i) pos[plist[i]] = next--;
+  for (int b = n - 1; b >= 0; --b)
+    if (pos[b] < 0) pos[b] = next--;
+  std::memset(bp, 0, sizeof(BitPerm));
+  for (int k = 0; k < 16; ++k)
+    for (int v = 0; v < 16; ++v)
+      for (int j = 0; j < 4; ++j)
+        if ((v >> j) & 1) {
+          const int b = 4 * k + j;
+          if (b < n) bp->fwd[k][v] |= 1ull << pos[b];
+        }
+  int from[64];
+  for (int b = 0; b < 64; ++b) from[b] = -1;
+  for (int b = 0; b < n; ++b) from[pos[b]] = b;
+  for (int k = 0; k < 16; ++k)
+    for (int v = 0; v < 16; ++v)
+      for (int j = 0; j < 4; ++j)
+        if ((v >> j) & 1) {
+          const int p = 4 * k + j;
+          if (p < n) bp->inv[k][v] |= 1ull << from[p];
+        }
+}
+
+// Bucket qubits for a gate that needs the global path: qubits outside the
+// gate whose bit is the most evenly split over the current terms (from
+// `ones`, the number of terms with each bit set), most recently used first
+// among equals, enough of them that the average bucket of the next state
+// holds about 128 terms.
+void choose_buckets(sv_state* s, uint64_t qmask, uint64_t n_est, const uint64_t* ones, uint64_t N) {
+  int cand[64], nc = 0;
+  double skew[64];
+  for (int b = 0; b < s->n; ++b) {
+    if ((qmask >> b) & 1ull) continue;
+    const double f = N ? (double)ones[b] / (double)N : 0.0;
+    if (f <= 0.0 || f >= 1.0) continue;  // constant bit: useless for bucketing
+    skew[b] = f > 0.5 ? f - 0.5 : 0.5 - f;
+    cand[nc++] = b;
+  }
+  for (int i = 1; i < nc; ++i)
+    for (int j = i; j > 0; --j) {
+      const int a = cand[j - 1], b = cand[j];
+      const bool swap = skew[b] < skew[a] || (skew[b] == skew[a] && s->last_use[b] > s->last_use[a]);
+      if (!swap) break;
+      cand[j - 1] = b;
+      cand[j] = a;
+    }
+  int t = 0;
+  while (t < nc && (n_est >> t) > 128) ++t;
+  s->tbits = t;
+  s->pmask = 0;
+  for (int i = 0; i < t; ++i) {
+    s->plist[i] = cand[i];
+    s->pmask |= 1ull << cand[i];
+  }
+}
+
+sv_status upload_perm(sv_state* s, GateParams& gp) {
+  build_perm(s->n, gp.m, gp.q, s->tbits, s->plist, s->perm_host);
+  gp.perm = s->perm_dev;
+  gp.n = s->n;
+  gp.tbits = s->tbits;
+  gp.pmask = s->pmask;
+  g_h2d += sizeof(BitPerm);
+  return cuda_check(s, cudaMemcpyAsync(s->perm_dev, s->perm_host, sizeof(BitPerm), cudaMemcpyHostToDevice, s->st),
+                    "gate permutation upload");
+}
+
 #define SV_GUARD(s)                                                    \
   do {                                                                 \
     if (!(s)) return SV_E_ARG;                                         \
@@ -356,9 +447,17 @@ sv_status sv_create_ex(int n, uint64_t K, double p, int prec, void* cuda_stream,
   s->ss.buf = (uint64_t*)dev_alloc(s, sizeof(uint64_t) * 2 * FINISH_CAP);
   if (!s->hist || !s->tile_counter || !s->ctl || !s->ss.hist_count || !s->ss.hist_mass || !s->ss.buf)
     rc = SV_E_NOMEM;
+  s->perm_dev = (BitPerm*)dev_alloc(s, sizeof(BitPerm));
+  s->bitcnt_dev = (uint64_t*)dev_alloc(s, 64 * sizeof(uint64_t));
+  if (!s->perm_dev || !s->bitcnt_dev) rc = SV_E_NOMEM;
+  if (rc == SV_OK && cudaMallocHost(&s->bitcnt_host, 64 * sizeof(uint64_t)) != cudaSuccess) rc = SV_E_CUDA;
   if (rc == SV_OK && (cudaMallocHost(&s->hist_host, sizeof(uint32_t) * MAX_PASSES * RADIX) != cudaSuccess ||
-                      cudaMallocHost(&s->ctl_host, sizeof(Ctl)) != cudaSuccess))
+                      cudaMallocHost(&s->ctl_host, sizeof(Ctl)) != cudaSuccess ||
+                      cudaMallocHost(&s->perm_host, sizeof(BitPerm)) != cudaSuccess))
     rc = SV_E_CUDA;
+  for (int b = 0; b < 64; ++b) s->last_use[b] = -1;
+  s->bucket_ok = true;  // one term: a single bucket (no bucket qubits)
+  s->max_bucket = 1;
   if (rc == SV_OK) rc = ensure_state_cap(s, 4096);
   if (rc == SV_OK) rc = ensure_sort_cap(s, 4096);
   if (rc == SV_OK) {
@@ -412,6 +511,10 @@ sv_status sv_destroy(sv_state* s) {
   }
   if (s->hist_host) cudaFreeHost(s->hist_host);
   if (s->ctl_host) cudaFreeHost(s->ctl_host);
+  if (s->perm_host) cudaFreeHost(s->perm_host);
+  if (s->bitcnt_host) cudaFreeHost(s->bitcnt_host);
+  dev_free(s, s->perm_dev);
+  dev_free(s, s->bitcnt_dev);
   delete s;
   return SV_OK;
 }
@@ -464,31 +567,108 @@ sv_status sv_apply_gate(sv_state* s, int m, const int* qubits, const double* U) 
   const uint64_t apply_tiles = ((N << m) + 2047) / 2048 + 1;
   if (rc == SV_OK) rc = ensure_lookback(s, apply_tiles + 16);
   if (rc != SV_OK) return rc;
-  const int passes = (s->n + RADIX_BITS - 1) / RADIX_BITS;
-  ph_begin(s, PH_KEYS);
-  launch_gate_keys(s->keys[s->cur], N, gp, s->sk[0], s->sidx[0], s->hist, passes, s->st);
-  ph_end(s, PH_KEYS);
-  g_h2d += sizeof(GateParams);
-  launched(s, PH_KEYS, 1);
-  int w = 0, run = 0;
-  rc = sort_pairs(s, N, s->n, true, &w, &run);
-  if (rc != SV_OK) return rc;
-  s->stats.sort_passes = (uint32_t)run;
   const int alt = 1 - s->cur;
-  ph_begin(s, PH_HEADS);
-  launch_group_heads(s->sk[w], N, m, s->heads, s->lookback, s->ctl, s->st);
-  ph_end(s, PH_HEADS);
-  ph_begin(s, PH_APPLY);
-  launch_gate_apply(s->prec, s->sk[w], s->sidx[w], N, s->heads, s->amps[s->cur], gp, s->keys[alt],
-                    s->amps[alt], s->probs[alt], s->lookback, s->ctl, s->st, apply_tiles);
-  ph_end(s, PH_APPLY);
-  launched(s, PH_HEADS, 1);
-  launched(s, PH_APPLY, 1);
-  rc = sync_ctl(s, "sv_apply_gate");
-  if (rc != SV_OK) return rc;
-  s->cur = alt;
-  s->N = s->ctl_host->count[1];
+  const uint64_t qmask = gp.qmask;
+  bool local = s->bucket_ok && (s->pmask & qmask) == 0 && (s->tbits > 0 || N <= LOCAL_BUCKET_MAX);
+  if (local && s->tbits > 0 && (s->max_bucket == 0 || s->max_bucket > LOCAL_BUCKET_MAX)) {
+    // the bound is unknown or too loose: measure the buckets exactly
+    ph_begin(s, PH_LOCAL);
+    launch_bucket_check(s->keys[s->cur], N, s->pmask, LOCAL_BUCKET_MAX, s->ctl, s->st);
+    ph_end(s, PH_LOCAL);
+    launched(s, PH_LOCAL, 1);
+    rc = sync_ctl(s, "sv_apply_gate");
+    if (rc != SV_OK) return rc;
+    s->max_bucket = s->ctl_host->count[0];
+    local = s->max_bucket <= LOCAL_BUCKET_MAX;
+  }
+  static const bool debug = getenv("SV_DEBUG") != nullptr;
+  if (debug)
+    fprintf(stderr, "[sv] gate %lld N=%llu q=(%d,%d) P&Q=%d tbits=%d max_bucket=%llu -> %s\n",
+            (long long)s->gate_index, (unsigned long long)N, gp.q[0], m > 1 ? gp.q[1] : -1,
+            (s->pmask & qmask) != 0, s->tbits, (unsigned long long)s->max_bucket, local ? "local" : "global");
+  bool done = false;
+  if (local) {
+    rc = upload_perm(s, gp);
+    if (rc != SV_OK) return rc;
+    ph_begin(s, PH_LOCAL);
+    launch_local_gate(s->prec, s->keys[s->cur], s->amps[s->cur], N, gp, s->keys[alt], s->amps[alt],
+                      s->probs[alt], s->ctl, s->st);
+    ph_end(s, PH_LOCAL);
+    launched(s, PH_LOCAL, 1);
+    rc = sync_ctl(s, "sv_apply_gate");
+    if (rc != SV_OK) return rc;
+    if (s->ctl_host->err & ERR_BUCKET) {  // a bucket outgrew the batch limit: redo globally
+      ++s->local_fallbacks;
+      rc = cuda_check(s, cudaMemsetAsync(&s->ctl->err, 0, sizeof(uint32_t), s->st), "sv_apply_gate");
+      if (rc != SV_OK) return rc;
+    } else {
+      ++s->local_gates;
+      done = true;
+      s->max_bucket = s->ctl_host->count[0];
+      const uint64_t npre = s->ctl_host->count[1];
+      if (s->ctl_host->count[3] != 0) {  // exact cancellations: drop the zero terms
+        rc = ensure_lookback(s, npre / 2048 + 16);
+        if (rc != SV_OK) return rc;
+        ph_begin(s, PH_APPLY);
+        launch_drop_zero_terms(s->prec, s->keys[alt], s->amps[alt], s->probs[alt], npre, s->keys[s->cur],
+                               s->amps[s->cur], s->probs[s->cur], s->lookback, s->ctl, s->st);
+        ph_end(s, PH_APPLY);
+        launched(s, PH_APPLY, 1);
+        rc = sync_ctl(s, "sv_apply_gate");
+        if (rc != SV_OK) return rc;
+        s->N = s->ctl_host->count[2];
+      } else {
+        s->cur = alt;
+        s->N = npre;
+      }
+    }
+  }
+  if (!done) {
+    ++s->global_gates;
+    const uint64_t npre_max = N << m;
+    ph_begin(s, PH_LOCAL);
+    launch_bit_counts(s->keys[s->cur], N, s->n, s->bitcnt_dev, s->st);
+    ph_end(s, PH_LOCAL);
+    launched(s, PH_LOCAL, 1);
+    rc = cuda_check(s, cudaMemcpyAsync(s->bitcnt_host, s->bitcnt_dev, 64 * sizeof(uint64_t),
+                                       cudaMemcpyDeviceToHost, s->st), "bit statistics");
+    if (rc == SV_OK) rc = cuda_check(s, cudaStreamSynchronize(s->st), "bit statistics");
+    if (rc != SV_OK) return rc;
+    choose_buckets(s, qmask, npre_max < s->K ? npre_max : (N > s->K ? N : s->K), s->bitcnt_host, N);
+    rc = upload_perm(s, gp);
+    if (rc != SV_OK) return rc;
+    const int passes = (s->n + RADIX_BITS - 1) / RADIX_BITS;
+    ph_begin(s, PH_KEYS);
+    launch_gate_keys(s->keys[s->cur], N, gp, s->sk[0], s->sidx[0], s->hist, passes, s->st);
+    ph_end(s, PH_KEYS);
+    launched(s, PH_KEYS, 1);
+    int w = 0, run = 0;
+    rc = sort_pairs(s, N, s->n, true, &w, &run);
+    if (rc != SV_OK) return rc;
+    s->stats.sort_passes = (uint32_t)run;
+    ph_begin(s, PH_HEADS);
+    launch_group_heads(s->sk[w], N, m, s->heads, s->lookback, s->ctl, s->st);
+    ph_end(s, PH_HEADS);
+    ph_begin(s, PH_APPLY);
+    launch_gate_apply(s->prec, s->sk[w], s->sidx[w], N, s->heads, s->amps[s->cur], gp, s->keys[alt],
+                      s->amps[alt], s->probs[alt], s->lookback, s->ctl, s->st, apply_tiles);
+    ph_end(s, PH_APPLY);
+    launched(s, PH_HEADS, 1);
+    launched(s, PH_APPLY, 1);
+    rc = sync_ctl(s, "sv_apply_gate");
+    if (rc != SV_OK) return rc;
+    s->cur = alt;
+    s->N = s->ctl_host->count[1];
+    s->bucket_ok = true;
+    s->max_bucket = 0;  // unknown until a local gate measures it
+  }
+  for (int t = 0; t < m; ++t) s->last_use[gp.q[t]] = s->gate_index;
+  ++s->gate_index;
+  s->live |= qmask;
   s->stats.n_pre = s->N;
+  s->stats.local_gates = s->local_gates;
+  s->stats.global_gates = s->global_gates;
+  s->stats.local_fallbacks = s->local_fallbacks;
   return SV_OK;
 }
 
@@ -769,6 +949,14 @@ sv_status sv_load(sv_state* s, const uint64_t* keys, const double* amps, uint64_
   if (s->ctl_host->count[3] != 0) return fail(s, SV_E_ARG, "sv_load: duplicate keys");
   s->cur = alt;
   s->N = s->ctl_host->count[2];
+  uint64_t orv = 0, andv = ~0ull;
+  for (uint64_t i = 0; i < N; ++i) {
+    orv |= keys[i];
+    andv &= keys[i];
+  }
+  s->live = orv ^ andv;
+  s->bucket_ok = false;  // sorted by key, but no bucket qubits chosen yet
+  s->max_bucket = 0;
   return SV_OK;
 }
 

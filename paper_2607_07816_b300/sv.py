@@ -24,7 +24,7 @@ _STATUS = {0: "SV_OK", -1: "SV_E_ARG", -2: "SV_E_NOMEM", -3: "SV_E_CUDA", -4: "S
 EXPORTED = ["sv_create", "sv_create_ex", "sv_destroy", "sv_apply_gate", "sv_truncate", "sv_peak",
             "sv_probs", "sv_num_terms", "sv_retained_mass", "sv_export", "sv_load", "sv_last_error",
             "sv_last_stats", "sv_set_timing", "sv_phase_times", "sv_launch_count", "sv_transfer_bytes", "sv_peak_noalloc"]
-PHASES = ["keys", "sort", "heads", "apply", "select", "compact", "peak", "other", "window"]
+PHASES = ["keys", "sort", "heads", "apply", "select", "compact", "peak", "other", "window", "local"]
 
 
 class SVError(RuntimeError):
@@ -43,7 +43,9 @@ class sv_stats(ctypes.Structure):
     _fields_ = [("n_in", ctypes.c_uint64), ("n_pre", ctypes.c_uint64), ("n_kept", ctypes.c_uint64),
                 ("sort_passes", ctypes.c_uint32), ("select_levels", ctypes.c_uint32),
                 ("total_mass", ctypes.c_double), ("kept_mass", ctypes.c_double),
-                ("window_hits", ctypes.c_uint32), ("pad", ctypes.c_uint32), ("window_terms", ctypes.c_uint64)]
+                ("window_hits", ctypes.c_uint32), ("pad", ctypes.c_uint32), ("window_terms", ctypes.c_uint64),
+                ("local_gates", ctypes.c_uint64), ("global_gates", ctypes.c_uint64),
+                ("local_fallbacks", ctypes.c_uint64)]
 
 
 _lib = None

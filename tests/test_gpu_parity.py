@@ -193,3 +193,45 @@ def test_probs_dump_and_export_roundtrip(sv, oracle_mod):
     g2 = sv.SparseState(33)
     g2.load(ek, ea)
     assert_states_equal(g2, o, what="reload")
+
+
+def test_exact_cancellation_drops_zero_terms(sv, oracle_mod):
+    """H on every qubit twice: the second layer cancels all but one term
+    exactly, so the library must drop exact zeros (Sec. IV-A)."""
+    n = 14
+    for prec in (0, 1):
+        g = sv.SparseState(n, prec=prec)
+        o = oracle_mod.Oracle(n, prec=prec)
+        gates = [((i,), C.mat_h()) for i in range(n)] + [((i,), C.mat_h()) for i in reversed(range(n))]
+        run_both(gates, g, o, truncate=False, check_every=False)
+        assert g.num_terms() == o.num_terms()
+
+
+def test_skewed_buckets_fall_back(sv, oracle_mod):
+    """Most keys share their high bits: buckets chosen on those bits overflow
+    the local batch limit and the gate must be redone through the global
+    path with the same result."""
+    rng = np.random.default_rng(123)
+    n = 30
+    low = rng.choice(1 << 20, size=30000, replace=False).astype(np.uint64)
+    high = (rng.choice(1 << 10, size=200, replace=False).astype(np.uint64) << np.uint64(20)) | np.uint64(7)
+    keys = np.unique(np.concatenate([low, high]))
+    amps = (rng.standard_normal(len(keys)) + 1j * rng.standard_normal(len(keys)))
+    amps /= np.linalg.norm(amps)
+    g = sv.SparseState(n, 1 << 20, 1.0)
+    o = oracle_mod.Oracle(n, 1 << 20, 1.0)
+    g.load(keys, amps)
+    o.load(keys, amps)
+    gates = [C.random_gate(n, 2, rng, "haar") for _ in range(3)]
+    gates += [((0, 1), C.haar_unitary(4, rng)), ((2, 3), C.haar_unitary(4, rng)), ((4,), C.mat_h())]
+    run_both(gates, g, o)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_brickwork_local_and_global_gates(sv, oracle_mod, prec):
+    c = C.brickwork_circuit(24, 6, seed=77, sigma=0.05, K=1 << 14, p=1.0)
+    g = sv.SparseState(c.n, c.K, c.p, prec=prec)
+    o = oracle_mod.Oracle(c.n, c.K, c.p, prec=prec)
+    run_both(c.gates, g, o, check_every=False)
+    st = g.stats()
+    assert st["local_gates"] > 0 and st["global_gates"] > 0
