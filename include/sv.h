@@ -164,6 +164,48 @@ uint64_t sv_launch_count(void);
  * and device->host (copies) in this process.  Either pointer may be NULL. */
 void sv_transfer_bytes(uint64_t* h2d, uint64_t* d2h);
 
+/* ---------------------------------------------------------------------
+ * Batched form.  Many circuits share one device-resident state: each circuit
+ * is a segment (a slot) with its own qubit count n (1..54) and top-k limit K.
+ * One svb_step applies one gate to every listed slot (slots not listed are
+ * left unchanged) and then truncates every slot above its K to its own top-K
+ * (Sec. III, p-mass is not offered in this form).  All slots go through one
+ * grouping sort, one mat-vec pass and one segmented select per step; each
+ * slot's result is the one the single-state path gives for the same gates.
+ * Gate conventions are those of sv_apply_gate.  Calls enqueue on the
+ * handle's stream and synchronise before returning.
+ * ------------------------------------------------------------------- */
+typedef struct svb_state svb_state;
+typedef struct {
+  int slot;          /* target slot */
+  int m;             /* 1..4 */
+  int qubits[4];     /* qubits[0..m-1], distinct, below the slot's n */
+  const double* U;   /* 2*4^m doubles, row-major U[r_out][r_in], (re, im); read before return */
+} svb_gate;
+
+/* Create a batch with room for max_slots (1..1023) circuits, amplitude
+ * precision prec, a cudaStream_t (NULL = legacy default) and an allocator
+ * (NULL = cudaMalloc). */
+sv_status svb_create(int max_slots, int prec, void* cuda_stream, const sv_allocator* alloc, svb_state** out);
+sv_status svb_destroy(svb_state* b);
+/* Add a circuit in the state |0...0>; *slot receives its slot.  p must be 1
+ * (top-k only).  SV_E_ARG when no slot is free. */
+sv_status svb_add(svb_state* b, int n, uint64_t K, double p, int* slot);
+/* Retire a slot; its terms are dropped by the next step and the slot is free
+ * after it. */
+sv_status svb_remove(svb_state* b, int slot);
+/* One gate per listed slot (at most one per slot), then per-slot top-k. */
+sv_status svb_step(svb_state* b, const svb_gate* gates, int count);
+sv_status svb_num_terms(svb_state* b, int slot, uint64_t* N);
+/* Product of the slot's retained fractions (Sec. III). */
+sv_status svb_retained_mass(svb_state* b, int slot, double* F);
+/* Most probable basis state of the slot in canonical order (Sec. V). */
+sv_status svb_peak(svb_state* b, int slot, uint64_t* key, double* prob);
+/* The slot's keys and amplitudes (interleaved re, im doubles) in storage
+ * order, min(cap, N) of them; *count = N. */
+sv_status svb_export(svb_state* b, int slot, uint64_t* keys, double* amps, uint64_t cap, uint64_t* count);
+const char* svb_last_error(const svb_state* b);
+
 /* Peak readout that allocates nothing.  The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc where they need
  * the readout (their device memory is owned by another runtime or pool,

@@ -1,0 +1,57 @@
+// Internal interfaces of the batched (segmented) form.
+#pragma once
+
+#include "internal.h"
+
+namespace sv {
+
+// Gate of one segment for one step.  m == 0 is the identity (each term its
+// own group); m < 0 marks a removed segment whose terms are dropped.
+struct SegGate {
+  int m;
+  int q[4];
+  uint32_t re_nz[16];
+  uint32_t im_nz[16];
+  double U[512];
+  BitPerm perm;
+};
+
+// Select state of one segment (top-k by count, as the single-state select).
+struct SegSel {
+  uint32_t active;     // this segment is truncated in this step
+  uint32_t done;       // 1: cut found, 2: no cut
+  uint32_t bits;
+  uint32_t pad;
+  uint64_t prefix_hi, prefix_lo;
+  uint64_t target;     // rank of the cut (K)
+  uint64_t before_count;
+  uint64_t before_mass_hi, before_mass_lo;
+  uint64_t bin_count;
+  uint64_t total_mass_hi, total_mass_lo;
+  uint64_t cut_pbits, cut_key, cut_count;
+  uint64_t cut_mass_hi, cut_mass_lo;
+  double scale;
+};
+
+void launch_seg_keys(const uint64_t* keys, const uint16_t* seg, uint64_t n, const SegGate* gates, int shift,
+                     uint64_t* sk, uint32_t* sidx, uint32_t* hist, int passes, cudaStream_t st);
+void launch_seg_heads(const uint64_t* sk, uint64_t n, int shift, const SegGate* gates, uint32_t* heads,
+                      uint64_t* lookback, Ctl* ctl, cudaStream_t st);
+void launch_seg_apply(int prec, const uint64_t* sk, const uint32_t* sidx, uint64_t n, const uint32_t* heads,
+                      const void* amps_in, int shift, int mmax, const SegGate* gates, uint64_t* keys_out,
+                      void* amps_out, uint64_t* probs_out, uint16_t* seg_out, uint64_t* lookback, Ctl* ctl,
+                      uint64_t max_tiles, cudaStream_t st);
+void launch_seg_bounds(const uint16_t* seg, uint64_t n, uint64_t* start, uint64_t* end, int slots,
+                       cudaStream_t st);
+void launch_segsel_level(const uint64_t* probs, const uint64_t* keys, const uint16_t* seg, uint64_t n, SegSel* sel,
+                         int slots, uint32_t* g_cnt, uint64_t* g_mass, uint32_t* err, cudaStream_t st);
+void launch_segsel_finish(const uint64_t* probs, const uint64_t* keys, const uint64_t* seg_start,
+                          const uint64_t* seg_end, SegSel* sel, int slots, uint32_t* err, cudaStream_t st);
+void launch_segsel_scale(SegSel* sel, int slots, cudaStream_t st);
+void launch_seg_truncate(int prec, const uint64_t* keys, const void* amps, const uint64_t* probs, const uint16_t* seg,
+                         uint64_t n, const SegSel* sel, uint64_t* keys_out, void* amps_out, uint64_t* probs_out,
+                         uint16_t* seg_out, uint64_t* lookback, Ctl* ctl, cudaStream_t st);
+void launch_seg_append(uint64_t* keys, void* amps, uint64_t* probs, uint16_t* seg, uint64_t at, int slot, int prec,
+                       cudaStream_t st);
+
+}  // namespace sv

@@ -1,0 +1,563 @@
+// C ABI of the batched form (svb_*, declared in include/sv.h): many circuits,
+// each a segment of one device-resident state, advanced one gate per circuit
+// per step with per-circuit top-k truncation (Sec. III) after every step.
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "batch.h"
+#include "host_util.h"
+#include "sv.h"
+
+using namespace sv;
+
+namespace {
+
+enum SlotState { SLOT_FREE = 0, SLOT_USED = 1, SLOT_REMOVING = 2 };
+
+struct Slot {
+  int state = SLOT_FREE;
+  int n = 0;
+  uint64_t K = 0;
+  uint64_t count = 0;   // terms of this segment
+  uint64_t offset = 0;  // first term in the current buffers
+  double F = 1.0;
+};
+
+}  // namespace
+
+struct svb_state {
+  int prec = 0;
+  cudaStream_t st = nullptr;
+  sv_allocator alloc{};
+  bool custom_alloc = false;
+  size_t amp_bytes = 16;
+  int max_slots = 0;
+  std::vector<Slot> slots;
+
+  uint64_t N = 0, cap = 0;
+  uint64_t* keys[2] = {nullptr, nullptr};
+  void* amps[2] = {nullptr, nullptr};
+  uint64_t* probs[2] = {nullptr, nullptr};
+  uint16_t* seg[2] = {nullptr, nullptr};
+  int cur = 0;
+
+  uint64_t sort_cap = 0;
+  uint64_t* sk[2] = {nullptr, nullptr};
+  uint32_t* sidx[2] = {nullptr, nullptr};
+  uint32_t* heads = nullptr;
+  uint64_t lb_entries = 0;
+  uint64_t* lookback = nullptr;
+  uint32_t* hist = nullptr;
+  uint32_t* hist_host = nullptr;
+  uint64_t* tile_counter = nullptr;
+
+  SegGate* gates_dev = nullptr;
+  SegGate* gates_host = nullptr;
+  SegSel* sel_dev = nullptr;
+  SegSel* sel_host = nullptr;
+  uint32_t* sel_cnt = nullptr;
+  uint64_t* sel_mass = nullptr;
+  uint64_t* bounds_dev = nullptr;   // [2][max_slots] start, end
+  uint64_t* bounds_host = nullptr;
+  Ctl* ctl = nullptr;
+  Ctl* ctl_host = nullptr;
+
+  std::string err;
+  bool broken = false;
+  uint64_t steps = 0;
+};
+
+namespace {
+
+void* b_alloc(svb_state* b, size_t bytes) {
+  if (bytes == 0) bytes = 256;
+  if (b->custom_alloc) return b->alloc.alloc(bytes, b->alloc.ctx);
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void b_free(svb_state* b, void* p) {
+  if (!p) return;
+  if (b->custom_alloc) b->alloc.free(p, b->alloc.ctx);
+  else cudaFree(p);
+}
+
+sv_status b_fail(svb_state* b, sv_status code, const std::string& msg) {
+  b->err = msg;
+  return code;
+}
+
+sv_status b_cuda(svb_state* b, cudaError_t e, const char* where) {
+  if (e == cudaSuccess) return SV_OK;
+  b->broken = true;
+  return b_fail(b, SV_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+sv_status b_sync_ctl(svb_state* b, const char* where) {
+  cudaError_t e = cudaMemcpyAsync(b->ctl_host, b->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, b->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  sv_status rc = b_cuda(b, e, where);
+  if (rc != SV_OK) return rc;
+  if (b->ctl_host->err & ERR_TIMEOUT) {
+    b->broken = true;
+    return b_fail(b, SV_E_TIMEOUT, std::string(where) + ": a bounded device wait ran out");
+  }
+  if (b->ctl_host->err & (ERR_MASS | ERR_INVARIANT)) {
+    b->broken = true;
+    return b_fail(b, SV_E_STATE, std::string(where) + ": device state error");
+  }
+  return SV_OK;
+}
+
+sv_status b_lookback(svb_state* b, uint64_t entries) {
+  if (entries <= b->lb_entries) return SV_OK;
+  const uint64_t want = entries + entries / 2 + 1024;
+  uint64_t* p = (uint64_t*)b_alloc(b, want * 8);
+  if (!p) return b_fail(b, SV_E_NOMEM, "look-back buffer allocation failed");
+  b_free(b, b->lookback);
+  b->lookback = p;
+  b->lb_entries = want;
+  return SV_OK;
+}
+
+// Buffers for `need` terms; the current contents are preserved.
+sv_status b_state_cap(svb_state* b, uint64_t need) {
+  if (need <= b->cap) return SV_OK;
+  uint64_t cap = b->cap * 2 > need ? b->cap * 2 : need;
+  if (cap < 4096) cap = 4096;
+  uint64_t* k[2];
+  void* a[2];
+  uint64_t* p[2];
+  uint16_t* g[2];
+  for (int i = 0; i < 2; ++i) {
+    k[i] = (uint64_t*)b_alloc(b, cap * 8);
+    a[i] = b_alloc(b, cap * b->amp_bytes);
+    p[i] = (uint64_t*)b_alloc(b, cap * 8);
+    g[i] = (uint16_t*)b_alloc(b, cap * 2);
+    if (!k[i] || !a[i] || !p[i] || !g[i]) {
+      for (int j = 0; j <= i; ++j) {
+        b_free(b, k[j]);
+        b_free(b, a[j]);
+        b_free(b, p[j]);
+        b_free(b, g[j]);
+      }
+      return b_fail(b, SV_E_NOMEM, "batch state allocation failed");
+    }
+  }
+  if (b->N) {
+    cudaMemcpyAsync(k[0], b->keys[b->cur], b->N * 8, cudaMemcpyDeviceToDevice, b->st);
+    cudaMemcpyAsync(a[0], b->amps[b->cur], b->N * b->amp_bytes, cudaMemcpyDeviceToDevice, b->st);
+    cudaMemcpyAsync(p[0], b->probs[b->cur], b->N * 8, cudaMemcpyDeviceToDevice, b->st);
+    cudaMemcpyAsync(g[0], b->seg[b->cur], b->N * 2, cudaMemcpyDeviceToDevice, b->st);
+  }
+  sv_status rc = b_cuda(b, cudaStreamSynchronize(b->st), "batch state growth");
+  for (int i = 0; i < 2; ++i) {
+    b_free(b, b->keys[i]);
+    b_free(b, b->amps[i]);
+    b_free(b, b->probs[i]);
+    b_free(b, b->seg[i]);
+    b->keys[i] = k[i];
+    b->amps[i] = a[i];
+    b->probs[i] = p[i];
+    b->seg[i] = g[i];
+  }
+  b->cur = 0;
+  b->cap = cap;
+  return rc;
+}
+
+sv_status b_sort_cap(svb_state* b, uint64_t need) {
+  if (need > b->sort_cap) {
+    uint64_t cap = b->sort_cap * 2 > need ? b->sort_cap * 2 : need;
+    if (cap < 4096) cap = 4096;
+    for (int i = 0; i < 2; ++i) {
+      b_free(b, b->sk[i]);
+      b_free(b, b->sidx[i]);
+      b->sk[i] = (uint64_t*)b_alloc(b, cap * 8);
+      b->sidx[i] = (uint32_t*)b_alloc(b, cap * 4);
+    }
+    b_free(b, b->heads);
+    b->heads = (uint32_t*)b_alloc(b, cap * 4);
+    if (!b->sk[0] || !b->sk[1] || !b->sidx[0] || !b->sidx[1] || !b->heads) {
+      b->sort_cap = 0;
+      return b_fail(b, SV_E_NOMEM, "batch sort buffer allocation failed");
+    }
+    b->sort_cap = cap;
+  }
+  return b_lookback(b, sort_tiles(need) * RADIX + 16);
+}
+
+// Per-slot offsets and counts from the segment bounds of the current buffer.
+sv_status b_read_bounds(svb_state* b, uint64_t n) {
+  launch_seg_bounds(b->seg[b->cur], n, b->bounds_dev, b->bounds_dev + b->max_slots, b->max_slots, b->st);
+  cudaMemcpyAsync(b->bounds_host, b->bounds_dev, sizeof(uint64_t) * 2 * b->max_slots, cudaMemcpyDeviceToHost, b->st);
+  sv_status rc = b_cuda(b, cudaStreamSynchronize(b->st), "segment bounds");
+  if (rc != SV_OK) return rc;
+  for (int s = 0; s < b->max_slots; ++s) {
+    Slot& sl = b->slots[s];
+    if (sl.state != SLOT_USED) continue;
+    const uint64_t a = b->bounds_host[s], e = b->bounds_host[b->max_slots + s];
+    sl.offset = a;
+    sl.count = e > a ? e - a : 0;
+  }
+  return SV_OK;
+}
+
+#define SVB_GUARD(b)                                                                                   \
+  do {                                                                                                 \
+    if (!(b)) return SV_E_ARG;                                                                         \
+    if ((b)->broken) return b_fail((b), SV_E_STATE, "batch handle unusable after an earlier failure: " + (b)->err); \
+  } while (0)
+
+}  // namespace
+
+extern "C" {
+
+sv_status svb_destroy(svb_state* b);
+
+sv_status svb_create(int max_slots, int prec, void* cuda_stream, const sv_allocator* alloc, svb_state** out) {
+  if (!out) return SV_E_ARG;
+  *out = nullptr;
+  if (max_slots < 1 || max_slots > 1023 || (prec != SV_C128 && prec != SV_C64)) return SV_E_ARG;
+  if (alloc && (!alloc->alloc || !alloc->free)) return SV_E_ARG;
+  svb_state* b = new svb_state();
+  b->prec = prec;
+  b->st = (cudaStream_t)cuda_stream;
+  b->amp_bytes = prec == SV_C128 ? 16 : 8;
+  b->max_slots = max_slots;
+  b->slots.resize(max_slots);
+  if (alloc) {
+    b->alloc = *alloc;
+    b->custom_alloc = true;
+  }
+  sv_status rc = SV_OK;
+  b->hist = (uint32_t*)b_alloc(b, sizeof(uint32_t) * MAX_PASSES * RADIX);
+  b->tile_counter = (uint64_t*)b_alloc(b, 256);
+  b->ctl = (Ctl*)b_alloc(b, sizeof(Ctl));
+  b->gates_dev = (SegGate*)b_alloc(b, sizeof(SegGate) * max_slots);
+  b->sel_dev = (SegSel*)b_alloc(b, sizeof(SegSel) * max_slots);
+  b->sel_cnt = (uint32_t*)b_alloc(b, sizeof(uint32_t) * SEL_BINS * max_slots);
+  b->sel_mass = (uint64_t*)b_alloc(b, sizeof(uint64_t) * 2 * SEL_BINS * max_slots);
+  b->bounds_dev = (uint64_t*)b_alloc(b, sizeof(uint64_t) * 2 * max_slots);
+  if (!b->hist || !b->tile_counter || !b->ctl || !b->gates_dev || !b->sel_dev || !b->sel_cnt || !b->sel_mass ||
+      !b->bounds_dev)
+    rc = SV_E_NOMEM;
+  if (rc == SV_OK && (cudaMallocHost(&b->hist_host, sizeof(uint32_t) * MAX_PASSES * RADIX) != cudaSuccess ||
+                      cudaMallocHost(&b->ctl_host, sizeof(Ctl)) != cudaSuccess ||
+                      cudaMallocHost(&b->gates_host, sizeof(SegGate) * max_slots) != cudaSuccess ||
+                      cudaMallocHost(&b->sel_host, sizeof(SegSel) * max_slots) != cudaSuccess ||
+                      cudaMallocHost(&b->bounds_host, sizeof(uint64_t) * 2 * max_slots) != cudaSuccess))
+    rc = SV_E_CUDA;
+  if (rc == SV_OK) rc = b_state_cap(b, 4096);
+  if (rc == SV_OK) rc = b_sort_cap(b, 4096);
+  if (rc == SV_OK) rc = b_cuda(b, cudaMemsetAsync(b->ctl, 0, sizeof(Ctl), b->st), "svb_create");
+  if (rc != SV_OK) {
+    svb_destroy(b);
+    return rc;
+  }
+  *out = b;
+  return SV_OK;
+}
+
+sv_status svb_destroy(svb_state* b) {
+  if (!b) return SV_OK;
+  if (b->st) cudaStreamSynchronize(b->st);
+  else cudaDeviceSynchronize();
+  for (int i = 0; i < 2; ++i) {
+    b_free(b, b->keys[i]);
+    b_free(b, b->amps[i]);
+    b_free(b, b->probs[i]);
+    b_free(b, b->seg[i]);
+    b_free(b, b->sk[i]);
+    b_free(b, b->sidx[i]);
+  }
+  b_free(b, b->heads);
+  b_free(b, b->lookback);
+  b_free(b, b->hist);
+  b_free(b, b->tile_counter);
+  b_free(b, b->ctl);
+  b_free(b, b->gates_dev);
+  b_free(b, b->sel_dev);
+  b_free(b, b->sel_cnt);
+  b_free(b, b->sel_mass);
+  b_free(b, b->bounds_dev);
+  if (b->hist_host) cudaFreeHost(b->hist_host);
+  if (b->ctl_host) cudaFreeHost(b->ctl_host);
+  if (b->gates_host) cudaFreeHost(b->gates_host);
+  if (b->sel_host) cudaFreeHost(b->sel_host);
+  if (b->bounds_host) cudaFreeHost(b->bounds_host);
+  delete b;
+  return SV_OK;
+}
+
+sv_status svb_add(svb_state* b, int n, uint64_t K, double p, int* slot) {
+  SVB_GUARD(b);
+  if (!slot || n < 1 || n > 54 || K < 1) return b_fail(b, SV_E_ARG, "svb_add: n must be 1..54 and K >= 1");
+  if (!(p >= 1.0)) return b_fail(b, SV_E_ARG, "svb_add: the batched form truncates by top-k only (p must be 1)");
+  int s = -1;
+  for (int i = 0; i < b->max_slots; ++i)
+    if (b->slots[i].state == SLOT_FREE) {
+      s = i;
+      break;
+    }
+  if (s < 0) return b_fail(b, SV_E_ARG, "svb_add: no free slot");
+  sv_status rc = b_state_cap(b, b->N + 1);
+  if (rc != SV_OK) return rc;
+  launch_seg_append(b->keys[b->cur], b->amps[b->cur], b->probs[b->cur], b->seg[b->cur], b->N, s, b->prec, b->st);
+  rc = b_cuda(b, cudaGetLastError(), "svb_add");
+  if (rc != SV_OK) return rc;
+  Slot& sl = b->slots[s];
+  sl.state = SLOT_USED;
+  sl.n = n;
+  sl.K = K;
+  sl.count = 1;
+  sl.offset = b->N;
+  sl.F = 1.0;
+  b->N += 1;
+  *slot = s;
+  return SV_OK;
+}
+
+sv_status svb_remove(svb_state* b, int slot) {
+  SVB_GUARD(b);
+  if (slot < 0 || slot >= b->max_slots || b->slots[slot].state != SLOT_USED)
+    return b_fail(b, SV_E_ARG, "svb_remove: slot not in use");
+  b->slots[slot].state = SLOT_REMOVING;  // its terms are dropped by the next step
+  return SV_OK;
+}
+
+sv_status svb_step(svb_state* b, const svb_gate* gates, int count) {
+  SVB_GUARD(b);
+  if (count < 0 || (count > 0 && !gates)) return b_fail(b, SV_E_ARG, "svb_step: bad gate list");
+  // gate table: listed slots get their gate, other used slots the identity,
+  // removed slots the drop marker
+  std::vector<int> listed(b->max_slots, -1);
+  for (int i = 0; i < count; ++i) {
+    const svb_gate& g = gates[i];
+    if (g.slot < 0 || g.slot >= b->max_slots || b->slots[g.slot].state != SLOT_USED)
+      return b_fail(b, SV_E_ARG, "svb_step: slot not in use");
+    if (listed[g.slot] >= 0) return b_fail(b, SV_E_ARG, "svb_step: two gates for one slot");
+    if (g.m < 1 || g.m > 4 || !g.U) return b_fail(b, SV_E_ARG, "svb_step: bad m or U");
+    uint64_t qm = 0;
+    for (int t = 0; t < g.m; ++t) {
+      if (g.qubits[t] < 0 || g.qubits[t] >= b->slots[g.slot].n || (qm >> g.qubits[t]) & 1ull)
+        return b_fail(b, SV_E_ARG, "svb_step: bad qubit");
+      qm |= 1ull << g.qubits[t];
+    }
+    if (!is_unitary(g.m, g.U)) return b_fail(b, SV_E_NOT_UNITARY, "svb_step: U is not unitary within 1e-10");
+    listed[g.slot] = i;
+  }
+  int top = 0, maxn = 1, mmax = 0;
+  uint64_t removed = 0;
+  for (int s = 0; s < b->max_slots; ++s) {
+    const Slot& sl = b->slots[s];
+    SegGate& gt = b->gates_host[s];
+    if (sl.state == SLOT_FREE) {
+      gt.m = -1;
+      continue;
+    }
+    top = s + 1;
+    if (sl.state == SLOT_REMOVING) {
+      gt.m = -1;
+      removed += sl.count;
+      continue;
+    }
+    maxn = sl.n > maxn ? sl.n : maxn;
+    std::memset(&gt, 0, sizeof(SegGate));
+    if (listed[s] < 0) {
+      gt.m = 0;
+      gt.re_nz[0] = 1;
+      gt.U[0] = 1.0;
+      build_perm(sl.n, 0, gt.q, 0, nullptr, &gt.perm);
+      continue;
+    }
+    const svb_gate& g = gates[listed[s]];
+    gt.m = g.m;
+    mmax = g.m > mmax ? g.m : mmax;
+    const int d = 1 << g.m;
+    for (int t = 0; t < g.m; ++t) gt.q[t] = g.qubits[t];
+    for (int ro = 0; ro < d; ++ro)
+      for (int r = 0; r < d; ++r) {
+        const double ur = g.U[2 * (ro * d + r)], ui = g.U[2 * (ro * d + r) + 1];
+        gt.U[2 * (ro * d + r)] = ur;
+        gt.U[2 * (ro * d + r) + 1] = ui;
+        const bool rz = b->prec == SV_C128 ? ur != 0.0 : (float)ur != 0.0f;
+        const bool iz = b->prec == SV_C128 ? ui != 0.0 : (float)ui != 0.0f;
+        if (rz) gt.re_nz[ro] |= 1u << r;
+        if (iz) gt.im_nz[ro] |= 1u << r;
+      }
+    build_perm(sl.n, g.m, gt.q, 0, nullptr, &gt.perm);
+  }
+  ++b->steps;
+  const uint64_t N = b->N;
+  if (N == 0 || top == 0) {
+    for (int s = 0; s < b->max_slots; ++s)
+      if (b->slots[s].state == SLOT_REMOVING) b->slots[s] = Slot();
+    b->N = 0;
+    return SV_OK;
+  }
+  const uint64_t nkeep = N - removed;
+  int segbits = 0;
+  while ((1 << segbits) <= top) ++segbits;  // every real sort key is below the drop marker
+  const int shift = maxn;
+  const int nbits = shift + segbits;
+  sv_status rc = b_state_cap(b, nkeep << mmax > N ? nkeep << mmax : N);
+  if (rc == SV_OK) rc = b_sort_cap(b, N);
+  const uint64_t apply_tiles = ((nkeep << mmax) + 1023) / 1024 + 1;
+  if (rc == SV_OK) rc = b_lookback(b, apply_tiles + 16);
+  if (rc != SV_OK) return rc;
+  rc = b_cuda(b, cudaMemcpyAsync(b->gates_dev, b->gates_host, sizeof(SegGate) * top, cudaMemcpyHostToDevice, b->st),
+              "svb_step gate upload");
+  if (rc != SV_OK) return rc;
+  const int passes = (nbits + RADIX_BITS - 1) / RADIX_BITS;
+  launch_seg_keys(b->keys[b->cur], b->seg[b->cur], N, b->gates_dev, shift, b->sk[0], b->sidx[0], b->hist, passes,
+                  b->st);
+  cudaMemcpyAsync(b->hist_host, b->hist, sizeof(uint32_t) * MAX_PASSES * RADIX, cudaMemcpyDeviceToHost, b->st);
+  rc = b_cuda(b, cudaStreamSynchronize(b->st), "svb_step keys");
+  if (rc != SV_OK) return rc;
+  SortScratch sc;
+  sc.hist = b->hist;
+  sc.hist_host = b->hist_host;
+  sc.lookback = b->lookback;
+  sc.lookback_tiles = b->lb_entries / RADIX;
+  sc.tile_counter = b->tile_counter;
+  sc.err = &b->ctl->err;
+  cudaError_t ce;
+  int run = 0;
+  const int w = radix_sort_pairs(b->sk[0], b->sidx[0], b->sk[1], b->sidx[1], N, nbits, sc, b->st, &run, &ce);
+  rc = b_cuda(b, ce, "svb_step sort");
+  if (rc != SV_OK) return rc;
+  const int alt = 1 - b->cur;
+  launch_seg_heads(b->sk[w], nkeep, shift, b->gates_dev, b->heads, b->lookback, b->ctl, b->st);
+  launch_seg_apply(b->prec, b->sk[w], b->sidx[w], nkeep, b->heads, b->amps[b->cur], shift, mmax, b->gates_dev,
+                   b->keys[alt], b->amps[alt], b->probs[alt], b->seg[alt], b->lookback, b->ctl, apply_tiles, b->st);
+  rc = b_sync_ctl(b, "svb_step apply");
+  if (rc != SV_OK) return rc;
+  for (int s = 0; s < b->max_slots; ++s)
+    if (b->slots[s].state == SLOT_REMOVING) b->slots[s] = Slot();
+  b->cur = alt;
+  b->N = b->ctl_host->count[1];
+  rc = b_read_bounds(b, b->N);
+  if (rc != SV_OK) return rc;
+
+  // ---- per-segment top-k
+  int ntrunc = 0;
+  for (int s = 0; s < top; ++s) {
+    SegSel& st = b->sel_host[s];
+    std::memset(&st, 0, sizeof(SegSel));
+    const Slot& sl = b->slots[s];
+    if (sl.state == SLOT_USED && sl.count > sl.K) {
+      st.active = 1;
+      st.bits = 1;
+      st.prefix_hi = 1ull << 63;
+      st.target = sl.K;
+      ++ntrunc;
+    }
+  }
+  if (ntrunc == 0) return SV_OK;
+  rc = b_cuda(b, cudaMemcpyAsync(b->sel_dev, b->sel_host, sizeof(SegSel) * top, cudaMemcpyHostToDevice, b->st),
+              "svb_step select upload");
+  if (rc != SV_OK) return rc;
+  const uint64_t NP = b->N;
+  bool all_done = false;
+  for (int level = 0; level < 16 && !all_done; ++level) {
+    launch_segsel_level(b->probs[b->cur], b->keys[b->cur], b->seg[b->cur], NP, b->sel_dev, top, b->sel_cnt,
+                        b->sel_mass, &b->ctl->err, b->st);
+    launch_segsel_finish(b->probs[b->cur], b->keys[b->cur], b->bounds_dev, b->bounds_dev + b->max_slots, b->sel_dev,
+                         top, &b->ctl->err, b->st);
+    cudaMemcpyAsync(b->sel_host, b->sel_dev, sizeof(SegSel) * top, cudaMemcpyDeviceToHost, b->st);
+    rc = b_sync_ctl(b, "svb_step select");
+    if (rc != SV_OK) return rc;
+    all_done = true;
+    for (int s = 0; s < top; ++s)
+      if (b->sel_host[s].active && !b->sel_host[s].done) all_done = false;
+  }
+  if (!all_done) {
+    b->broken = true;
+    return b_fail(b, SV_E_STATE, "svb_step: segmented select did not resolve");
+  }
+  launch_segsel_scale(b->sel_dev, top, b->st);
+  rc = b_lookback(b, NP / 2048 + 16);
+  if (rc != SV_OK) return rc;
+  const int alt2 = 1 - b->cur;
+  launch_seg_truncate(b->prec, b->keys[b->cur], b->amps[b->cur], b->probs[b->cur], b->seg[b->cur], NP, b->sel_dev,
+                      b->keys[alt2], b->amps[alt2], b->probs[alt2], b->seg[alt2], b->lookback, b->ctl, b->st);
+  cudaMemcpyAsync(b->sel_host, b->sel_dev, sizeof(SegSel) * top, cudaMemcpyDeviceToHost, b->st);
+  rc = b_sync_ctl(b, "svb_step truncate");
+  if (rc != SV_OK) return rc;
+  b->cur = alt2;
+  b->N = b->ctl_host->count[2];
+  for (int s = 0; s < top; ++s) {
+    const SegSel& st = b->sel_host[s];
+    if (st.active && st.done == 1) {
+      const double Sc = u128_to_double(st.cut_mass_hi, st.cut_mass_lo);
+      const double SN = u128_to_double(st.total_mass_hi, st.total_mass_lo);
+      b->slots[s].F = b->slots[s].F * (Sc / SN);
+    }
+  }
+  return b_read_bounds(b, b->N);
+}
+
+sv_status svb_num_terms(svb_state* b, int slot, uint64_t* N) {
+  SVB_GUARD(b);
+  if (!N || slot < 0 || slot >= b->max_slots || b->slots[slot].state != SLOT_USED)
+    return b_fail(b, SV_E_ARG, "svb_num_terms: slot not in use");
+  *N = b->slots[slot].count;
+  return SV_OK;
+}
+
+sv_status svb_retained_mass(svb_state* b, int slot, double* F) {
+  SVB_GUARD(b);
+  if (!F || slot < 0 || slot >= b->max_slots || b->slots[slot].state != SLOT_USED)
+    return b_fail(b, SV_E_ARG, "svb_retained_mass: slot not in use");
+  *F = b->slots[slot].F;
+  return SV_OK;
+}
+
+sv_status svb_peak(svb_state* b, int slot, uint64_t* key, double* prob) {
+  SVB_GUARD(b);
+  if (!key || !prob || slot < 0 || slot >= b->max_slots || b->slots[slot].state != SLOT_USED)
+    return b_fail(b, SV_E_ARG, "svb_peak: slot not in use");
+  const Slot& sl = b->slots[slot];
+  if (sl.count == 0) return b_fail(b, SV_E_STATE, "svb_peak: empty segment");
+  launch_peak(b->probs[b->cur] + sl.offset, b->keys[b->cur] + sl.offset, sl.count, b->ctl, b->st);
+  sv_status rc = b_sync_ctl(b, "svb_peak");
+  if (rc != SV_OK) return rc;
+  *key = b->ctl_host->peak_z_lo;
+  uint64_t bits = b->ctl_host->peak_z_hi;
+  std::memcpy(prob, &bits, 8);
+  return SV_OK;
+}
+
+sv_status svb_export(svb_state* b, int slot, uint64_t* keys, double* amps, uint64_t cap, uint64_t* count) {
+  SVB_GUARD(b);
+  if (!count || slot < 0 || slot >= b->max_slots || b->slots[slot].state != SLOT_USED)
+    return b_fail(b, SV_E_ARG, "svb_export: slot not in use");
+  const Slot& sl = b->slots[slot];
+  *count = sl.count;
+  const uint64_t w = cap < sl.count ? cap : sl.count;
+  if (w == 0) return SV_OK;
+  sv_status rc = b_sort_cap(b, w);
+  if (rc != SV_OK) return rc;
+  double* tmp = (double*)b_alloc(b, w * 16);
+  if (!tmp) return b_fail(b, SV_E_NOMEM, "svb_export: staging allocation failed");
+  launch_iota(b->sidx[0], w, b->st);
+  launch_gather_terms(b->prec, b->sidx[0], w, b->keys[b->cur] + sl.offset,
+                      (const char*)b->amps[b->cur] + sl.offset * b->amp_bytes, b->probs[b->cur] + sl.offset,
+                      nullptr, tmp, nullptr, b->st);
+  if (keys) cudaMemcpyAsync(keys, b->keys[b->cur] + sl.offset, w * 8, cudaMemcpyDeviceToHost, b->st);
+  if (amps) cudaMemcpyAsync(amps, tmp, w * 16, cudaMemcpyDeviceToHost, b->st);
+  rc = b_cuda(b, cudaStreamSynchronize(b->st), "svb_export");
+  b_free(b, tmp);
+  return rc;
+}
+
+const char* svb_last_error(const svb_state* b) { return b ? b->err.c_str() : "null handle"; }
+
+}  // extern "C"

@@ -23,7 +23,9 @@ _STATUS = {0: "SV_OK", -1: "SV_E_ARG", -2: "SV_E_NOMEM", -3: "SV_E_CUDA", -4: "S
 
 EXPORTED = ["sv_create", "sv_create_ex", "sv_destroy", "sv_apply_gate", "sv_truncate", "sv_peak",
             "sv_probs", "sv_num_terms", "sv_retained_mass", "sv_export", "sv_load", "sv_last_error",
-            "sv_last_stats", "sv_set_timing", "sv_phase_times", "sv_launch_count", "sv_transfer_bytes", "sv_peak_noalloc"]
+            "sv_last_stats", "sv_set_timing", "sv_phase_times", "sv_launch_count", "sv_transfer_bytes", "sv_peak_noalloc",
+            "svb_create", "svb_destroy", "svb_add", "svb_remove", "svb_step", "svb_num_terms",
+            "svb_retained_mass", "svb_peak", "svb_export", "svb_last_error"]
 PHASES = ["keys", "sort", "heads", "apply", "select", "compact", "peak", "other", "window", "local"]
 
 
@@ -37,6 +39,11 @@ class sv_allocator(ctypes.Structure):
     _fields_ = [("alloc", ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)),
                 ("free", ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)),
                 ("ctx", ctypes.c_void_p)]
+
+
+class svb_gate(ctypes.Structure):
+    _fields_ = [("slot", ctypes.c_int), ("m", ctypes.c_int), ("qubits", ctypes.c_int * 4),
+                ("U", ctypes.POINTER(ctypes.c_double))]
 
 
 class sv_stats(ctypes.Structure):
@@ -99,6 +106,26 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.sv_phase_times.argtypes = [vp, P(dbl), P(u64)]
     lib.sv_launch_count.restype = u64
     lib.sv_launch_count.argtypes = []
+    lib.svb_create.restype = i32
+    lib.svb_create.argtypes = [i32, i32, vp, P(sv_allocator), P(vp)]
+    lib.svb_destroy.restype = i32
+    lib.svb_destroy.argtypes = [vp]
+    lib.svb_add.restype = i32
+    lib.svb_add.argtypes = [vp, i32, u64, dbl, P(ctypes.c_int)]
+    lib.svb_remove.restype = i32
+    lib.svb_remove.argtypes = [vp, i32]
+    lib.svb_step.restype = i32
+    lib.svb_step.argtypes = [vp, P(svb_gate), i32]
+    lib.svb_num_terms.restype = i32
+    lib.svb_num_terms.argtypes = [vp, i32, P(u64)]
+    lib.svb_retained_mass.restype = i32
+    lib.svb_retained_mass.argtypes = [vp, i32, P(dbl)]
+    lib.svb_peak.restype = i32
+    lib.svb_peak.argtypes = [vp, i32, P(u64), P(dbl)]
+    lib.svb_export.restype = i32
+    lib.svb_export.argtypes = [vp, i32, vp, vp, u64, P(u64)]
+    lib.svb_last_error.restype = ctypes.c_char_p
+    lib.svb_last_error.argtypes = [vp]
     lib.sv_peak_noalloc.restype = i32
     lib.sv_peak_noalloc.argtypes = [i32, vp, vp, u64, vp, P(u64), P(dbl)]
     lib.sv_transfer_bytes.restype = None
@@ -300,3 +327,118 @@ class SparseState:
             if truncate:
                 self.truncate()
         return self
+
+
+# ------------------------------------------------ batched form (svb_*)
+def _bcheck(h, rc):
+    if rc != SV_OK:
+        raise SVError(rc, _lib.svb_last_error(h).decode() if h else "")
+
+
+def svb_create(max_slots: int, prec: int = SV_C64, stream: int = 0) -> int:
+    lib = load_library()
+    h = ctypes.c_void_p()
+    _bcheck(None, lib.svb_create(max_slots, prec, ctypes.c_void_p(stream), None, ctypes.byref(h)))
+    return h.value
+
+
+def svb_destroy(h: int) -> None:
+    load_library().svb_destroy(ctypes.c_void_p(h))
+
+
+def svb_add(h: int, n: int, K: int, p: float = 1.0) -> int:
+    s = ctypes.c_int()
+    _bcheck(h, load_library().svb_add(ctypes.c_void_p(h), n, ctypes.c_uint64(K), p, ctypes.byref(s)))
+    return s.value
+
+
+def svb_remove(h: int, slot: int) -> None:
+    _bcheck(h, load_library().svb_remove(ctypes.c_void_p(h), slot))
+
+
+def svb_step(h: int, gates) -> None:
+    """gates: iterable of (slot, qubits, U)."""
+    gates = list(gates)
+    arr = (svb_gate * max(1, len(gates)))()
+    keep = []
+    for i, (slot, q, u) in enumerate(gates):
+        ub = _u_buffer(u)
+        keep.append(ub)
+        arr[i].slot = slot
+        arr[i].m = len(q)
+        for t, x in enumerate(q):
+            arr[i].qubits[t] = int(x)
+        arr[i].U = ub.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    _bcheck(h, load_library().svb_step(ctypes.c_void_p(h), arr, len(gates)))
+
+
+def svb_num_terms(h: int, slot: int) -> int:
+    n = ctypes.c_uint64()
+    _bcheck(h, load_library().svb_num_terms(ctypes.c_void_p(h), slot, ctypes.byref(n)))
+    return n.value
+
+
+def svb_retained_mass(h: int, slot: int) -> float:
+    f = ctypes.c_double()
+    _bcheck(h, load_library().svb_retained_mass(ctypes.c_void_p(h), slot, ctypes.byref(f)))
+    return f.value
+
+
+def svb_peak(h: int, slot: int):
+    k, p = ctypes.c_uint64(), ctypes.c_double()
+    _bcheck(h, load_library().svb_peak(ctypes.c_void_p(h), slot, ctypes.byref(k), ctypes.byref(p)))
+    return k.value, p.value
+
+
+def svb_export(h: int, slot: int):
+    n = svb_num_terms(h, slot)
+    keys = np.zeros(n, dtype=np.uint64)
+    amps = np.zeros(2 * n, dtype=np.float64)
+    cnt = ctypes.c_uint64()
+    _bcheck(h, load_library().svb_export(ctypes.c_void_p(h), slot, keys.ctypes.data, amps.ctypes.data,
+                                         ctypes.c_uint64(n), ctypes.byref(cnt)))
+    return keys, amps.view(np.complex128)
+
+
+def svb_last_error(h: int) -> str:
+    return load_library().svb_last_error(ctypes.c_void_p(h)).decode()
+
+
+class Batch:
+    """Many circuits advanced together (segmented state on the device)."""
+
+    def __init__(self, max_slots: int, prec: int = SV_C64, stream: int = 0):
+        self.h = svb_create(max_slots, prec, stream)
+        self.prec = prec
+
+    def close(self):
+        if getattr(self, "h", None):
+            svb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add(self, n: int, K: int) -> int:
+        return svb_add(self.h, n, K, 1.0)
+
+    def remove(self, slot: int) -> None:
+        svb_remove(self.h, slot)
+
+    def step(self, gates) -> None:
+        svb_step(self.h, gates)
+
+    def num_terms(self, slot: int) -> int:
+        return svb_num_terms(self.h, slot)
+
+    def retained_mass(self, slot: int) -> float:
+        return svb_retained_mass(self.h, slot)
+
+    def peak(self, slot: int):
+        return svb_peak(self.h, slot)
+
+    def export(self, slot: int):
+        return svb_export(self.h, slot)

@@ -1,0 +1,129 @@
+"""Batched form (svb_*): many circuits of uneven n, K and length advanced
+together in one segmented state must each give exactly the result of the
+oracle run on that circuit alone (same gates, same per-gate top-k)."""
+import numpy as np
+import pytest
+
+from paper_2607_07816_b300 import circuits as C
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sv():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2607_07816_b300 import sv as _sv
+    _sv.load_library()
+    return _sv
+
+
+def _as_dict(keys, amps):
+    return {int(k): complex(a) for k, a in zip(keys, amps)}
+
+
+def _check_slot(b, slot, orc, what):
+    gk, ga = b.export(slot)
+    ok, oa, _ = orc.export()
+    g, o = _as_dict(gk, ga), _as_dict(ok, oa)
+    assert g.keys() == o.keys(), f"{what}: key sets differ ({len(g)} vs {len(o)})"
+    bad = [k for k in g if g[k] != o[k]]
+    assert not bad, f"{what}: {len(bad)} amplitudes differ"
+    assert b.peak(slot) == orc.peak(), what
+    assert b.retained_mass(slot) == orc.retained_mass(), what
+
+
+def _circuits(rng, count):
+    out = []
+    for j in range(count):
+        n = int(rng.integers(10, 31))
+        depth = int(rng.integers(1, 4))
+        K = 1 << int(rng.integers(6, 13))
+        out.append(C.brickwork_circuit(n, depth, seed=int(rng.integers(1 << 30)), sigma=0.05, K=K, p=1.0))
+    return out
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batch_matches_oracle_per_circuit(sv, oracle_mod, prec):
+    rng = np.random.default_rng(31 + prec)
+    circs = _circuits(rng, 10)
+    b = sv.Batch(16, prec=prec)
+    slots = [b.add(c.n, c.K) for c in circs]
+    orcs = [oracle_mod.Oracle(c.n, c.K, 1.0, prec=prec) for c in circs]
+    pos = [0] * len(circs)
+    done = [False] * len(circs)
+    step = 0
+    while not all(done):
+        gates = []
+        for j, c in enumerate(circs):
+            if done[j]:
+                continue
+            # every third step circuit j sits out once (identity pass-through)
+            if (step + j) % 3 == 0 and pos[j] > 0 and pos[j] % 2 == 1:
+                continue
+            q, u = c.gates[pos[j]]
+            gates.append((slots[j], q, u))
+            orcs[j].apply_gate(q, u)
+            orcs[j].truncate()
+            pos[j] += 1
+        b.step(gates)
+        for j, c in enumerate(circs):
+            if not done[j] and pos[j] == len(c.gates):
+                _check_slot(b, slots[j], orcs[j], f"circuit {j} (n={c.n}, K={c.K})")
+                b.remove(slots[j])
+                done[j] = True
+        step += 1
+    b.step([])  # drops the retired slots
+    b.close()
+
+
+def test_batch_slot_reuse_and_late_arrivals(sv, oracle_mod):
+    rng = np.random.default_rng(7)
+    circs = _circuits(rng, 8)
+    b = sv.Batch(4, prec=1)
+    live = {}  # slot -> (circuit index, position, oracle)
+    queue = list(range(len(circs)))
+    finished = 0
+    while finished < len(circs):
+        while queue and len(live) < 4:
+            j = queue.pop(0)
+            c = circs[j]
+            s = b.add(c.n, c.K)
+            assert s not in live
+            live[s] = [j, 0, oracle_mod.Oracle(c.n, c.K, 1.0, prec=1)]
+        gates = []
+        for s, (j, p, o) in live.items():
+            q, u = circs[j].gates[p]
+            gates.append((s, q, u))
+            o.apply_gate(q, u)
+            o.truncate()
+            live[s][1] += 1
+        b.step(gates)
+        for s in list(live):
+            j, p, o = live[s]
+            if p == len(circs[j].gates):
+                _check_slot(b, s, o, f"circuit {j}")
+                b.remove(s)
+                del live[s]
+                finished += 1
+        b.step([])  # frees the retired slots for the next arrivals
+    b.close()
+
+
+def test_batch_argument_errors(sv):
+    b = sv.Batch(2, prec=1)
+    s = b.add(8, 64)
+    with pytest.raises(sv.SVError):
+        b.add(60, 4)                       # n above 54
+    with pytest.raises(sv.SVError):
+        sv.svb_add(b.h, 8, 16, 0.9)        # p-mass not offered in the batched form
+    with pytest.raises(sv.SVError):
+        b.step([(s, (0, 0), np.eye(4))])  # repeated qubit
+    with pytest.raises(sv.SVError):
+        b.step([(s, (9,), np.eye(2))])     # qubit above n
+    with pytest.raises(sv.SVError):
+        b.step([(1, (0,), np.eye(2))])     # slot not in use
+    b.step([(s, (0,), C.mat_h())])
+    assert b.num_terms(s) == 2
+    b.close()
