@@ -166,7 +166,7 @@ void sv_transfer_bytes(uint64_t* h2d, uint64_t* d2h);
 
 /* ---------------------------------------------------------------------
  * Batched form.  Many circuits share one device-resident state: each circuit
- * is a segment (a slot) with its own qubit count n (1..54) and top-k limit K.
+ * is a segment (a slot) with its own qubit count n (1..63) and top-k limit K.
  * One svb_step applies one gate to every listed slot (slots not listed are
  * left unchanged) and then truncates every slot above its K to its own top-K
  * (Sec. III, p-mass is not offered in this form).  All slots go through one
@@ -188,8 +188,14 @@ typedef struct {
  * (NULL = cudaMalloc). */
 sv_status svb_create(int max_slots, int prec, void* cuda_stream, const sv_allocator* alloc, svb_state** out);
 sv_status svb_destroy(svb_state* b);
-/* Add a circuit in the state |0...0>; *slot receives its slot.  p must be 1
- * (top-k only).  SV_E_ARG when no slot is free. */
+/* Add a circuit in the state |0...0>; *slot receives its slot (the lowest
+ * free one).  p must be 1 (top-k only).  One step sorts (slot, key) pairs as
+ * 64-bit words, so the largest n among the slots in use plus the bits of the
+ * highest slot index in use (floor(log2(top)) + 1, top = highest slot + 1,
+ * counting slots removed since the last step) must stay within 64: n <= 54
+ * always fits 1023 slots, n = 56 fits while at most 255 are in use.
+ * SV_E_ARG when no slot is free or that bound would be broken (nothing
+ * changes; the call can be retried after slots are retired). */
 sv_status svb_add(svb_state* b, int n, uint64_t K, double p, int* slot);
 /* Retire a slot; its terms are dropped by the next step and the slot is free
  * after it. */

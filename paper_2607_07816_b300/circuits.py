@@ -224,6 +224,24 @@ def batch_circuits(count: int = 512, seed: int = 1004, n_range=(16, 48), depth_r
     return out
 
 
+def serving_request(j: int, seed: int = 1005, large_frac: float = 0.02, large=(56, 12, 25),
+                    n_range=(16, 48), depth_range=(2, 10), k_range=(10, 20)) -> Circuit:
+    """Request j of the serving stream: a mirrored brickwork peaked circuit
+    drawn like batch_circuits, except that a large_frac share are large
+    ones of (n, forward depth, log2 K) = large."""
+    s = splitmix64(seed ^ (j * 0x9E3779B97F4A7C15 & 0xFFFFFFFFFFFFFFFF))
+    rng = np.random.default_rng(s)
+    if rng.random() < large_frac:
+        n, depth, k = large
+        name = f"serve_{j}_large"
+    else:
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        depth = int(rng.integers(depth_range[0], depth_range[1] + 1))
+        k = int(rng.integers(k_range[0], k_range[1] + 1))
+        name = f"serve_{j}"
+    return brickwork_circuit(n, depth, int(s & 0x7FFFFFFF), 0.05, K=1 << k, p=1.0, name=name)
+
+
 def random_gate(n: int, m: int, rng: np.random.Generator, kind: str = "haar") -> Gate:
     """One gate on m distinct random qubits (parity fuzzing)."""
     qs = tuple(int(q) for q in rng.choice(n, size=m, replace=False))

@@ -298,15 +298,24 @@ sv_status svb_destroy(svb_state* b) {
 
 sv_status svb_add(svb_state* b, int n, uint64_t K, double p, int* slot) {
   SVB_GUARD(b);
-  if (!slot || n < 1 || n > 54 || K < 1) return b_fail(b, SV_E_ARG, "svb_add: n must be 1..54 and K >= 1");
+  if (!slot || n < 1 || n > 63 || K < 1) return b_fail(b, SV_E_ARG, "svb_add: n must be 1..63 and K >= 1");
   if (!(p >= 1.0)) return b_fail(b, SV_E_ARG, "svb_add: the batched form truncates by top-k only (p must be 1)");
-  int s = -1;
-  for (int i = 0; i < b->max_slots; ++i)
-    if (b->slots[i].state == SLOT_FREE) {
-      s = i;
-      break;
+  int s = -1, top = 0, maxn = n;
+  for (int i = 0; i < b->max_slots; ++i) {
+    const Slot& sl = b->slots[i];
+    if (sl.state == SLOT_FREE) {
+      if (s < 0) s = i;
+      continue;
     }
+    top = i + 1;
+    if (sl.state == SLOT_USED && sl.n > maxn) maxn = sl.n;
+  }
   if (s < 0) return b_fail(b, SV_E_ARG, "svb_add: no free slot");
+  if (s + 1 > top) top = s + 1;
+  int segbits = 0;
+  while ((1 << segbits) <= top) ++segbits;
+  if (maxn + segbits > 64)
+    return b_fail(b, SV_E_ARG, "svb_add: the largest n plus the slot-index bits exceed the 64-bit sort key");
   sv_status rc = b_state_cap(b, b->N + 1);
   if (rc != SV_OK) return rc;
   launch_seg_append(b->keys[b->cur], b->amps[b->cur], b->probs[b->cur], b->seg[b->cur], b->N, s, b->prec, b->st);

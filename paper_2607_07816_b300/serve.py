@@ -1,0 +1,188 @@
+"""Serving form: continuous batching of circuit requests over the batched C ABI.
+
+Requests (circuits) arrive over time.  The loop admits an arrived request
+into a free slot of the device-resident batch whenever its footprint
+(K * 2^m_max * 16 bytes, the most a gate can expand its state to) fits the
+HBM budget next to the circuits already resident, advances every resident
+circuit by one gate per step (one svb_step for all of them), and retires a
+circuit as soon as its last gate has run: its most probable basis state
+(Sec. V) is read back and its slot and budget are released for the next
+arrivals.  Work of newly admitted and long-running circuits overlaps in the
+same steps.  The loop itself only orders requests and marshals gates; every
+gate, truncation and readout runs in the library's kernels.
+"""
+from __future__ import annotations
+
+import dataclasses
+import time
+from collections import deque
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+from . import sv
+
+
+@dataclasses.dataclass
+class Result:
+    index: int
+    peak_key: int
+    peak_prob: float
+    retained_mass: float
+    arrival: float
+    admitted: float
+    finished: float
+    keys: Optional[np.ndarray] = None
+    amps: Optional[np.ndarray] = None
+
+    @property
+    def latency(self) -> float:
+        return self.finished - self.arrival
+
+
+def footprint(circuit) -> int:
+    """Admission size of a request: K * 2^m_max * 16 bytes, the most its
+    state can grow to inside one gate before the cut (Sec. IV-A)."""
+    m_max = max((len(q) for q, _ in circuit.gates), default=1)
+    return int(circuit.K) * (1 << m_max) * 16
+
+
+def poisson_arrivals(count: int, rate: float, seed: int) -> np.ndarray:
+    """Arrival times (seconds) of a Poisson stream of the given rate."""
+    rng = np.random.default_rng(seed)
+    return np.cumsum(rng.exponential(1.0 / rate, size=count))
+
+
+def slot_limit(n_max: int, max_slots: int) -> int:
+    """Most slots a batch may hold while a circuit of n_max qubits can still be
+    admitted: the step's 64-bit sort key holds the slot index above the key."""
+    bits = 64 - n_max
+    return max(1, min(max_slots, (1 << bits) - 1))
+
+
+class Server:
+    """A continuous-batching request loop on one GPU.
+
+    budget_bytes bounds the sum of the resident requests' footprints;
+    max_slots bounds how many are resident at once (lowered when n_max, the
+    largest qubit count that will be served, needs more key bits)."""
+
+    def __init__(self, budget_bytes: int, max_slots: int = 512, n_max: int = 54, prec: int = sv.SV_C64,
+                 stream: int = 0, batch=None):
+        self.budget = int(budget_bytes)
+        self.max_slots = slot_limit(n_max, max_slots)
+        self.batch = batch if batch is not None else sv.Batch(self.max_slots, prec=prec, stream=stream)
+        self.steps = 0
+        self.peak_resident = 0
+        self.peak_bytes = 0
+
+    def close(self):
+        self.batch.close()
+
+    def run(self, circuits: Sequence, arrivals: Optional[Sequence[float]] = None, clock=None,
+            export: bool = False) -> List[Result]:
+        """Serve every circuit and return one Result per circuit, in input
+        order.  arrivals[j] is when request j arrives, in the units of clock
+        (seconds after the start by default; all 0 when None: a saturated
+        run).  A request is admitted, in arrival order, once it has arrived,
+        a slot is free and its footprint fits the budget (one request is
+        always admitted into an empty batch).  With export the final state of
+        each circuit is returned as well."""
+        n = len(circuits)
+        arrivals = np.zeros(n) if arrivals is None else np.asarray(arrivals, dtype=float)
+        if clock is None:
+            t0 = time.perf_counter()
+            clock = lambda: time.perf_counter() - t0  # noqa: E731
+        order = deque(np.argsort(arrivals, kind="stable").tolist())
+        results: List[Optional[Result]] = [None] * n
+        live = {}  # slot -> [request index, next gate, admission time]
+        used = 0
+        retiring = 0  # slots removed since the last step (free after it)
+        done = 0
+        while done < n:
+            now = clock()
+            while order and arrivals[order[0]] <= now and len(live) + retiring < self.max_slots:
+                j = order[0]
+                c = circuits[j]
+                fp = footprint(c)
+                if used + fp > self.budget and live:
+                    break  # wait for resident requests to finish
+                order.popleft()
+                if not c.gates:
+                    results[j] = Result(j, 0, 1.0, 1.0, float(arrivals[j]), now, now)
+                    done += 1
+                    continue
+                slot = self.batch.add(c.n, c.K)
+                live[slot] = [j, 0, now]
+                used += fp
+            self.peak_resident = max(self.peak_resident, len(live))
+            self.peak_bytes = max(self.peak_bytes, used)
+            if not live:
+                if retiring:  # an empty step frees the retired slots
+                    self.batch.step([])
+                    retiring = 0
+                elif order:  # idle until the next arrival
+                    wait = arrivals[order[0]] - clock()
+                    if wait > 0:
+                        time.sleep(min(wait, 0.01))
+                continue
+            gates = []
+            for slot, (j, g, _) in live.items():
+                q, u = circuits[j].gates[g]
+                gates.append((slot, q, u))
+            self.batch.step(gates)
+            self.steps += 1
+            retiring = 0
+            for slot in list(live):
+                entry = live[slot]
+                j, g, admitted = entry
+                entry[1] = g + 1
+                if g + 1 < len(circuits[j].gates):
+                    continue
+                key, prob = self.batch.peak(slot)
+                f = self.batch.retained_mass(slot)
+                ks = am = None
+                if export:
+                    ks, am = self.batch.export(slot)
+                self.batch.remove(slot)
+                retiring += 1
+                del live[slot]
+                used -= footprint(circuits[j])
+                results[j] = Result(j, key, prob, f, float(arrivals[j]), admitted, clock(), ks, am)
+                done += 1
+        return results  # type: ignore[return-value]
+
+
+def percentiles(results: Sequence[Result]):
+    lat = np.array([r.latency for r in results])
+    return float(np.percentile(lat, 50)), float(np.percentile(lat, 99))
+
+
+def serve_serial_plain(circuits: Sequence, prec: int = sv.SV_C128, stream: int = 0,
+                       clock=time.perf_counter):
+    """The serial plain path: every circuit alone, one after the other, on
+    the single-state API (gate, then top-k truncation, then the peak).
+    Returns the service time of each circuit and its peak."""
+    out = []
+    for c in circuits:
+        t = clock()
+        st = sv.SparseState(c.n, c.K, 1.0, prec=prec, stream=stream)
+        for (q, u) in c.gates:
+            st.apply_gate(q, u)
+            st.truncate()
+        key, prob = st.peak()
+        st.close()
+        out.append((clock() - t, key, prob))
+    return out
+
+
+def fifo_latencies(arrivals: Sequence[float], service: Sequence[float]) -> np.ndarray:
+    """Completion minus arrival of a single FIFO server with the given
+    service times (the serial path cannot overlap circuits)."""
+    t = 0.0
+    lat = []
+    for a, s in zip(arrivals, service):
+        start = max(t, a)
+        t = start + s
+        lat.append(t - a)
+    return np.array(lat)

@@ -115,7 +115,7 @@ def test_batch_argument_errors(sv):
     b = sv.Batch(2, prec=1)
     s = b.add(8, 64)
     with pytest.raises(sv.SVError):
-        b.add(60, 4)                       # n above 54
+        b.add(64, 4)                       # n above 63
     with pytest.raises(sv.SVError):
         sv.svb_add(b.h, 8, 16, 0.9)        # p-mass not offered in the batched form
     with pytest.raises(sv.SVError):
@@ -126,4 +126,26 @@ def test_batch_argument_errors(sv):
         b.step([(1, (0,), np.eye(2))])     # slot not in use
     b.step([(s, (0,), C.mat_h())])
     assert b.num_terms(s) == 2
+    b.close()
+
+
+def test_batch_sort_key_bit_bound(sv):
+    """n plus the slot-index bits must fit the 64-bit sort key: n = 56 fits
+    while the highest slot in use is below 255, and not after."""
+    b = sv.Batch(400, prec=1)
+    big = b.add(56, 16)
+    assert big == 0
+    small = [b.add(8, 16) for _ in range(254)]  # slots 1..254: top = 255, 8 bits
+    with pytest.raises(sv.SVError):
+        b.add(8, 16)                       # slot 255 would need a ninth bit
+    b.remove(big)
+    b.step([])                             # frees slot 0
+    with pytest.raises(sv.SVError):
+        b.add(57, 16)                      # 57 + 8 bits
+    s = b.add(56, 16)                      # lowest free slot is 0 again
+    assert s == 0
+    b.step([(s, (55,), C.mat_h())] + [(t, (0,), C.mat_h()) for t in small[:3]])
+    assert b.num_terms(s) == 2 and b.num_terms(small[0]) == 2 and b.num_terms(small[5]) == 1
+    keys, _ = b.export(s)
+    assert sorted(int(k) for k in keys) == [0, 1 << 55]
     b.close()
