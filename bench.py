@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-c64", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=128,
+                    help="requests of the serving stream measured (0: skip the serving leg)")
     return ap.parse_args()
 
 
@@ -222,6 +224,8 @@ def run_ours(args, rank, world):
         res["c64"] = run_prec("c64", args.K, args.steps, args.warmup, sample_clocks=False)
     if not args.no_e2e:
         res["e2e"] = run_e2e(args, rank, dev, stream)
+    if args.serve_requests > 0:
+        res["serving"] = run_serving(args, rank, dev, stream)
     return res, peaks
 
 
@@ -253,6 +257,84 @@ def run_e2e(args, rank, dev, stream):
     return {"value": n_in / wall, "unit": "terms/s", "h2d_bytes_per_step": int((h1 - h0) / g),
             "d2h_bytes_per_step": int((d1 - d0) / g), "wall_s": wall, "gates": g,
             "peak_is_hidden": bool(key == circ.hidden), "peak_prob": pr}
+
+
+def run_serving(args, rank, dev, stream):
+    """Serving form against the serial plain path on the same requests.
+
+    Requests: the first R of the seeded serving stream (mirrored brickwork
+    circuits, n in [16,48], forward depth in [2,10], K = 2^k with k in
+    [10,20], and a 2% share of large ones with n=56, depth 12, K=2^25).
+    serial  : each request alone on the single-state complex128 path, one
+              after the other (create, every gate + top-k, peak, destroy);
+              the service time of every request is measured.
+    batched : the continuous-batching loop on the complex64 batched form,
+              160 GB admission budget: a saturated run (all requests at t=0)
+              gives the capacity; then a Poisson stream at 80% of it gives
+              arrival-to-peak latencies.  The serial latencies at the same
+              arrival times follow from its measured service times (one
+              FIFO server)."""
+    import numpy as np
+    import torch
+    from paper_2607_07816_b300 import circuits as C
+    from paper_2607_07816_b300 import serve, sv
+
+    R = args.serve_requests
+    reqs = [C.serving_request(j) for j in range(R)]
+    n_max = max(c.n for c in reqs)
+    sv_stream = stream.cuda_stream
+    torch.cuda.synchronize(dev)
+    # warm-up of both paths on a few small requests
+    small = [c for c in reqs if c.K <= 1 << 12][:4]
+    serve.serve_serial_plain(small, prec=sv.SV_C128, stream=sv_stream)
+    w = serve.Server(160 << 30, n_max=n_max, prec=sv.SV_C64, stream=sv_stream)
+    w.run(small)
+    w.close()
+    torch.cuda.synchronize(dev)
+
+    t0 = time.perf_counter()
+    ser = serve.serve_serial_plain(reqs, prec=sv.SV_C128, stream=sv_stream)
+    torch.cuda.synchronize(dev)
+    serial_s = time.perf_counter() - t0
+    svc = np.array([x[0] for x in ser])
+
+    srv = serve.Server(160 << 30, n_max=n_max, prec=sv.SV_C64, stream=sv_stream)
+    t0 = time.perf_counter()
+    closed = srv.run(reqs)
+    torch.cuda.synchronize(dev)
+    closed_s = time.perf_counter() - t0
+    steps_closed, resident = srv.steps, srv.peak_resident
+    srv.close()
+    fin = np.sort([r.finished for r in closed])
+    lo, hi = fin[len(fin) // 4], fin[(3 * len(fin)) // 4]
+    mid_rate = ((3 * len(fin)) // 4 - len(fin) // 4) / (hi - lo) if hi > lo else None
+    capacity = R / closed_s
+    rate = 0.8 * capacity
+    arrivals = serve.poisson_arrivals(R, rate, 1005)
+    srv = serve.Server(160 << 30, n_max=n_max, prec=sv.SV_C64, stream=sv_stream)
+    t0 = time.perf_counter()
+    opened = srv.run(reqs, arrivals=arrivals)
+    torch.cuda.synchronize(dev)
+    open_s = time.perf_counter() - t0
+    srv.close()
+    p50, p99 = serve.percentiles(opened)
+    s_lat = serve.fifo_latencies(arrivals, svc)
+    same_peak = sum(int(a.peak_key == b[1]) for a, b in zip(closed, ser))
+    same_open = sum(int(a.peak_key == b.peak_key and a.peak_prob == b.peak_prob) for a, b in zip(opened, closed))
+    large = [j for j, c in enumerate(reqs) if c.n == 56]
+    return {
+        "requests": R, "large_requests": len(large), "budget_gb": 160, "prec": "c64 batched vs c128 serial",
+        "serial": {"circuits_per_s": R / svc.sum(), "wall_s": serial_s,
+                   "p50_s": float(np.percentile(s_lat, 50)), "p99_s": float(np.percentile(s_lat, 99)),
+                   "service_ms_p50": float(np.percentile(svc, 50) * 1e3)},
+        "batched_closed": {"circuits_per_s": capacity, "wall_s": closed_s, "steps": steps_closed,
+                           "max_resident": resident, "mid_run_circuits_per_s": mid_rate},
+        "served": {"arrival_rate": rate, "circuits_per_s": R / (max(r.finished for r in opened) - arrivals[0]),
+                   "p50_s": p50, "p99_s": p99, "wall_s": open_s},
+        "speedup_circuits_per_s": capacity / (R / svc.sum()),
+        "peaks_equal_to_serial_c128": f"{same_peak}/{R}",
+        "served_results_equal_to_saturated_run": f"{same_open}/{R}",
+    }
 
 
 def roofline(main, prec, peaks):
@@ -418,6 +500,8 @@ def main():
                        "phases_ms": {k: round(v[0], 3) for k, v in c["phases"].items()}}
     if "e2e" in res:
         line["e2e"] = res["e2e"]
+    if "serving" in res:
+        line["serving"] = res["serving"]
     if not args.no_cpu and world == 1:
         line["cpu_baseline"] = oracle_sample(seconds=15.0, K_cap=args.K)
         line["cpu_baseline"]["cores"] = 1

@@ -13,6 +13,7 @@
 #include "internal.h"
 #include "tile.cuh"
 #include "batch.h"
+#include "select.cuh"
 
 namespace sv {
 
@@ -32,7 +33,9 @@ __global__ void __launch_bounds__(256) k_seg_keys(const uint64_t* __restrict__ k
     if (gates[sg].m < 0) {
       s = ~0ull;  // term of a removed segment: sorts last and is cut off
     } else {
-      s = ((uint64_t)sg << shift) | permute_bits(gates[sg].perm.fwd, keys[i]);
+      const SegGate& gt = gates[sg];
+      const uint64_t k = keys[i];
+      s = ((uint64_t)sg << shift) | (squeeze_out(k, gt.qs, gt.m) << gt.m) | seg_gather_r(k, gt.q, gt.m);
     }
     sk[i] = s;
     sidx[i] = (uint32_t)i;
@@ -190,7 +193,7 @@ __global__ void __launch_bounds__(SA_BLOCK) k_seg_apply(
             }
           }
           const uint64_t local = s0 & ((1ull << shift) - 1ull);
-          key = permute_bits(gt.perm.inv, ((local >> m) << m) | ro);
+          key = spread_in(local >> m, gt.qs, m) | seg_deposit_r(ro, gt.q, m);
           f = !(re == (Real)0 && im == (Real)0);
         }
       }
@@ -261,163 +264,200 @@ void launch_seg_bounds(const uint16_t* seg, uint64_t n, uint64_t* start, uint64_
 }
 
 // ---------------------------------------------------------------- segmented select
-// The single-state radix select run for every segment at once: each segment
-// has its own select state (prefix, target rank, counts and masses before
-// its bin); a histogram level walks the terms in chunks, keeping the
-// histogram of the segment it is in and flushing it when the segment changes.
+// The single-state radix select run for every segment at once, top-k only:
+// each segment has its own select state (prefix of the select key
+// z = (~prob_bits, key), target rank, count before its bin).  A level scans
+// all terms in contiguous chunks, walked as runs of one segment each.  While
+// a segment's bin is large the scan builds its digit histogram (counts only:
+// the rank decides the bin); once the bin holds at most SF_CAP terms, the
+// next scan copies them out for the finish kernel and sums, in the exact
+// fixed point of the masses, the segment's total mass and the mass of the
+// terms ranked before the bin.  The cut's mass is then the latter plus the
+// masses of the bin's terms up to the cut, added by the finish kernel.
 constexpr int SS_BINS = SEL_BINS;
+constexpr int SS_BLOCK = 256, SS_ILP = 4;
+constexpr int SF_CAP = SEGSEL_CAP;
 
-__device__ __forceinline__ void seg_add_u128(uint64_t* hi, uint64_t* lo, u128 v) {
-  const uint64_t vl = (uint64_t)v;
-  uint64_t vh = (uint64_t)(v >> 64);
-  if (vl) {
-    const uint64_t old = atomicAdd((unsigned long long*)lo, (unsigned long long)vl);
-    if (old + vl < old) vh += 1;
+// A segment whose current bin holds at most SF_CAP terms is in collect mode.
+__device__ __forceinline__ bool seg_collects(const SegSel& st) {
+  return st.active && !st.done && st.bin_count <= (uint64_t)SF_CAP;
+}
+
+// Is z ranked before (strictly above) every key under the bits-long prefix?
+__device__ __forceinline__ bool z_before_prefix(uint64_t hi, uint64_t lo, uint64_t ph, uint64_t pl, int bits) {
+  if (bits <= 64) return (hi >> (64 - bits)) < (ph >> (64 - bits));
+  if (hi != ph) return hi < ph;
+  return (lo >> (128 - bits)) < (pl >> (128 - bits));
+}
+
+__device__ __forceinline__ u128 warp_sum_u128(u128 v) {
+  uint64_t lo = (uint64_t)v, hi = (uint64_t)(v >> 64);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const uint64_t l2 = __shfl_down_sync(0xffffffffu, (unsigned long long)lo, o);
+    const uint64_t h2 = __shfl_down_sync(0xffffffffu, (unsigned long long)hi, o);
+    const uint64_t s = lo + l2;
+    hi += h2 + (s < lo ? 1u : 0u);
+    lo = s;
   }
-  if (vh) atomicAdd((unsigned long long*)hi, (unsigned long long)vh);
+  return make_u128(hi, lo);
 }
 
-__device__ __forceinline__ bool seg_z_match(uint64_t hi, uint64_t lo, uint64_t ph, uint64_t pl, int bits) {
-  if (bits <= 64) return ((hi ^ ph) >> (64 - bits)) == 0;
-  if (hi != ph) return false;
-  return ((lo ^ pl) >> (128 - bits)) == 0;
-}
-
-__device__ __forceinline__ void seg_digit(int bits, int* D, int* shift) {
-  const int d = 128 - bits;
-  *D = d < SEL_BITS ? d : SEL_BITS;
-  *shift = 128 - bits - *D;
-}
-
-constexpr int SS_CHUNK = 16384;
-
-__global__ void __launch_bounds__(256) k_segsel_hist(const uint64_t* __restrict__ probs,
-                                                     const uint64_t* __restrict__ keys,
-                                                     const uint16_t* __restrict__ seg, uint64_t n,
-                                                     const SegSel* __restrict__ sel, uint32_t* __restrict__ g_cnt,
-                                                     uint64_t* __restrict__ g_mass, uint32_t* err) {
+__global__ void __launch_bounds__(SS_BLOCK) k_segsel_hist(const uint64_t* __restrict__ probs,
+                                                          const uint64_t* __restrict__ keys,
+                                                          const uint16_t* __restrict__ seg, uint64_t n,
+                                                          uint64_t chunk, const SegSel* __restrict__ sel,
+                                                          uint32_t* __restrict__ g_cnt, uint64_t* __restrict__ g_sum,
+                                                          uint64_t* __restrict__ g_buf, uint32_t* __restrict__ g_bufn,
+                                                          uint32_t* err) {
   __shared__ uint32_t s_cnt[SS_BINS];
-  __shared__ uint64_t s_mass[2 * SS_BINS];
+  __shared__ u128 s_part[2][SS_BLOCK / 32];
   __shared__ uint32_t s_seg;
-  const uint64_t chunks = (n + SS_CHUNK - 1) / SS_CHUNK;
-  for (uint64_t c = blockIdx.x; c < chunks; c += gridDim.x) {
-    const uint64_t c0 = c * SS_CHUNK, c1 = c0 + SS_CHUNK < n ? c0 + SS_CHUNK : n;
-    uint64_t i0 = c0;
-    while (i0 < c1) {
-      // the run of this chunk that belongs to one segment
-      if (threadIdx.x == 0) s_seg = seg[i0];
-      for (int b = threadIdx.x; b < SS_BINS; b += blockDim.x) {
-        s_cnt[b] = 0;
-        s_mass[2 * b] = s_mass[2 * b + 1] = 0;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint64_t c0 = blockIdx.x * chunk;
+  if (c0 >= n) return;
+  const uint64_t c1 = c0 + chunk < n ? c0 + chunk : n;
+  uint64_t i0 = c0;
+  while (i0 < c1) {
+    if (tid == 0) s_seg = seg[i0];
+    __syncthreads();
+    const uint32_t sg = s_seg;
+    const SegSel& st = sel[sg];
+    const bool collect = seg_collects(st);
+    const bool count = st.active && !st.done && !collect;
+    const int bits = (int)st.bits;
+    const uint64_t ph = st.prefix_hi, pl = st.prefix_lo;
+    int D, sh;
+    sel_digit(bits, &D, &sh);
+    uint64_t i1;
+    {  // end of the run: first index in [i0, c1) of another segment
+      uint64_t lo = i0, hi = c1;
+      while (lo < hi) {
+        const uint64_t mid = (lo + hi) / 2;
+        if (seg[mid] == sg) lo = mid + 1;
+        else hi = mid;
       }
+      i1 = lo;
+    }
+    if (count) {
+      for (int b = tid; b < SS_BINS; b += SS_BLOCK) s_cnt[b] = 0;
       __syncthreads();
-      const uint32_t sg = s_seg;
-      const SegSel& st = sel[sg];
-      const bool active = st.active && !st.done;
-      const int bits = (int)st.bits;
-      int D, sh;
-      seg_digit(bits, &D, &sh);
-      uint64_t i1 = i0;
-      // find the end of the run (segments are contiguous)
-      {
-        uint64_t lo = i0, hi = c1;  // first index in [i0, c1) with another segment
-        while (lo < hi) {
-          const uint64_t mid = (lo + hi) / 2;
-          if (seg[mid] == sg) lo = mid + 1;
-          else hi = mid;
+      const bool need_lo = bits > 64 || sh < 64;
+      for (uint64_t b0 = i0; b0 < i1; b0 += (uint64_t)SS_BLOCK * SS_ILP) {
+        uint64_t pb[SS_ILP];
+#pragma unroll
+        for (int u = 0; u < SS_ILP; ++u) {
+          const uint64_t i = b0 + (uint64_t)u * SS_BLOCK + tid;
+          pb[u] = i < i1 ? probs[i] : 0ull;
         }
-        i1 = lo;
-      }
-      if (active) {
-        for (uint64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-          const uint64_t pb = probs[i];
-          const uint64_t hi = ~pb;
-          if (bits <= 64 && ((hi ^ st.prefix_hi) >> (64 - bits)) != 0) continue;
-          const uint64_t lo = (bits > 64 || sh < 64) ? keys[i] : 0ull;
-          if (!seg_z_match(hi, lo, st.prefix_hi, st.prefix_lo, bits)) continue;
-          const u128 z = make_u128(hi, lo);
-          const uint32_t dg = (uint32_t)(z >> sh) & ((1u << D) - 1u);
-          atomicAdd(&s_cnt[dg], 1u);
-          seg_add_u128(&s_mass[2 * dg], &s_mass[2 * dg + 1], fx_from_bits(pb, err));
-        }
-      }
-      __syncthreads();
-      if (active) {
-        uint32_t* gc = g_cnt + (uint64_t)sg * SS_BINS;
-        uint64_t* gm = g_mass + (uint64_t)sg * 2 * SS_BINS;
-        for (int b = threadIdx.x; b < (1 << D); b += blockDim.x) {
-          if (s_cnt[b]) {
-            atomicAdd(&gc[b], s_cnt[b]);
-            seg_add_u128(&gm[2 * b], &gm[2 * b + 1], make_u128(s_mass[2 * b], s_mass[2 * b + 1]));
+#pragma unroll
+        for (int u = 0; u < SS_ILP; ++u) {
+          const uint64_t i = b0 + (uint64_t)u * SS_BLOCK + tid;
+          const uint64_t hi = ~pb[u];
+          bool act = i < i1 && (bits > 64 || ((hi ^ ph) >> (64 - bits)) == 0);
+          const uint64_t lo = act && need_lo ? keys[i] : 0ull;
+          if (act && bits > 64) act = z_matches(hi, lo, ph, pl, bits);
+          if (bits == 1) {
+            // first level: the digit is the exponent, shared by most lanes
+            const uint32_t dg = act ? z_digit(hi, lo, sh, D) : 0xffffffffu;
+            const uint32_t peers = __match_any_sync(0xffffffffu, dg);
+            if (act && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&s_cnt[dg], (uint32_t)__popc(peers));
+          } else if (act) {
+            atomicAdd(&s_cnt[z_digit(hi, lo, sh, D)], 1u);
           }
         }
       }
       __syncthreads();
-      i0 = i1;
+      uint32_t* gc = g_cnt + (uint64_t)sg * SS_BINS;
+      for (int b = tid; b < (1 << D); b += SS_BLOCK)
+        if (s_cnt[b]) atomicAdd(&gc[b], s_cnt[b]);
+    } else if (collect) {
+      uint64_t* buf = g_buf + (uint64_t)sg * 2 * SF_CAP;
+      u128 tot = 0, above = 0;
+      for (uint64_t b0 = i0; b0 < i1; b0 += (uint64_t)SS_BLOCK * SS_ILP) {
+        uint64_t pb[SS_ILP];
+#pragma unroll
+        for (int u = 0; u < SS_ILP; ++u) {
+          const uint64_t i = b0 + (uint64_t)u * SS_BLOCK + tid;
+          pb[u] = i < i1 ? probs[i] : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < SS_ILP; ++u) {
+          const uint64_t i = b0 + (uint64_t)u * SS_BLOCK + tid;
+          if (i >= i1) continue;
+          const uint64_t hi = ~pb[u];
+          const u128 v = fx_from_bits(pb[u], err);
+          tot += v;
+          if (bits <= 64 && ((hi ^ ph) >> (64 - bits)) != 0) {
+            if (z_before_prefix(hi, 0, ph, pl, bits)) above += v;
+            continue;
+          }
+          const uint64_t lo = keys[i];
+          if (!z_matches(hi, lo, ph, pl, bits)) {
+            if (z_before_prefix(hi, lo, ph, pl, bits)) above += v;
+            continue;
+          }
+          const uint32_t p = atomicAdd(&g_bufn[sg], 1u);
+          if (p < SF_CAP) {
+            buf[2 * p] = hi;
+            buf[2 * p + 1] = lo;
+          } else {
+            atomicOr(err, ERR_INVARIANT);
+          }
+        }
+      }
+      tot = warp_sum_u128(tot);
+      above = warp_sum_u128(above);
+      if (lane == 0) {
+        s_part[0][warp] = tot;
+        s_part[1][warp] = above;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        u128 t = 0, a = 0;
+        for (int w = 0; w < SS_BLOCK / 32; ++w) {
+          t += s_part[0][w];
+          a += s_part[1][w];
+        }
+        if (t) atomic_add_u128(&g_sum[4 * sg], &g_sum[4 * sg + 1], t);
+        if (a) atomic_add_u128(&g_sum[4 * sg + 2], &g_sum[4 * sg + 3], a);
+      }
     }
+    __syncthreads();
+    i0 = i1;
   }
 }
 
-// One block per segment: pick the bin of the cut (same rule as the
-// single-state select) and update the segment's select state.
-__global__ void __launch_bounds__(256) k_segsel_pick(SegSel* __restrict__ sel, const uint32_t* __restrict__ g_cnt,
-                                                     const uint64_t* __restrict__ g_mass, uint32_t* err) {
+// One block per counting segment: pick the bin holding the target rank.
+__global__ void __launch_bounds__(256) k_segsel_pick(SegSel* __restrict__ sel, const uint32_t* __restrict__ g_cnt) {
   __shared__ uint64_t w_c[8];
-  __shared__ u128 w_m[8];
   __shared__ uint32_t s_first;
   SegSel& st = sel[blockIdx.x];
-  if (!st.active || st.done) return;
+  if (!st.active || st.done || seg_collects(st)) return;
   const uint32_t* cnt = g_cnt + (uint64_t)blockIdx.x * SS_BINS;
-  const uint64_t* mass = g_mass + (uint64_t)blockIdx.x * 2 * SS_BINS;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int bits = (int)st.bits;
   int D, shift;
-  seg_digit(bits, &D, &shift);
+  sel_digit(bits, &D, &shift);
   const int nbins = 1 << D;
   const int per = (nbins + 255) / 256;
   const int b0 = tid * per;
   uint64_t my_c = 0;
-  u128 my_m = 0;
-  for (int b = b0; b < b0 + per && b < nbins; ++b) {
-    my_c += cnt[b];
-    my_m += make_u128(mass[2 * b], mass[2 * b + 1]);
-  }
+  for (int b = b0; b < b0 + per && b < nbins; ++b) my_c += cnt[b];
   uint64_t xc = my_c;
-  u128 xm = my_m;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const uint64_t yc = __shfl_up_sync(0xffffffffu, (unsigned long long)xc, o);
-    const uint64_t yh = __shfl_up_sync(0xffffffffu, (unsigned long long)(xm >> 64), o);
-    const uint64_t yl = __shfl_up_sync(0xffffffffu, (unsigned long long)(uint64_t)xm, o);
-    if (lane >= o) {
-      xc += yc;
-      xm += make_u128(yh, yl);
-    }
+    if (lane >= o) xc += yc;
   }
-  if (lane == 31) {
-    w_c[warp] = xc;
-    w_m[warp] = xm;
-  }
+  if (lane == 31) w_c[warp] = xc;
   if (tid == 0) s_first = 0xffffffffu;
   __syncthreads();
   uint64_t base_c = 0;
-  u128 base_m = 0, total = 0;
-  for (int w = 0; w < 8; ++w) {
-    if (w < warp) {
-      base_c += w_c[w];
-      base_m += w_m[w];
-    }
-    total += w_m[w];
-  }
+  for (int w = 0; w < warp; ++w) base_c += w_c[w];
   const uint64_t excl_c = base_c + xc - my_c;
-  const u128 excl_m = base_m + xm - my_m;
-  if (bits == 1 && tid == 0) {  // first level: every term of the segment is in some bin
-    st.total_mass_hi = (uint64_t)(total >> 64);
-    st.total_mass_lo = (uint64_t)total;
-  }
   const uint64_t target = st.target;
   const uint64_t before_c = st.before_count;
-  const u128 before_m = make_u128(st.before_mass_hi, st.before_mass_lo);
   {
     uint64_t cc = before_c + excl_c;
     for (int b = b0; b < b0 + per && b < nbins; ++b) {
@@ -432,64 +472,50 @@ __global__ void __launch_bounds__(256) k_segsel_pick(SegSel* __restrict__ sel, c
   __syncthreads();
   const uint32_t first = s_first;
   if (first == 0xffffffffu) {
-    if (tid == 0) st.done = 2;
+    if (tid == 0) st.done = 2;  // fewer terms than the target: not reached for an active segment
     return;
   }
   if ((int)first >= b0 && (int)first < b0 + per) {
     uint64_t bc = before_c + excl_c;
-    u128 bm = before_m + excl_m;
-    for (int b = b0; b < (int)first; ++b) {
-      bc += cnt[b];
-      bm += make_u128(mass[2 * b], mass[2 * b + 1]);
-    }
+    for (int b = b0; b < (int)first; ++b) bc += cnt[b];
     u128 prefix = make_u128(st.prefix_hi, st.prefix_lo);
     prefix |= ((u128)first) << shift;
-    const int nb = bits + D;
     st.prefix_hi = (uint64_t)(prefix >> 64);
     st.prefix_lo = (uint64_t)prefix;
-    st.bits = (uint32_t)nb;
+    st.bits = (uint32_t)(bits + D);
     st.before_count = bc;
-    st.before_mass_hi = (uint64_t)(bm >> 64);
-    st.before_mass_lo = (uint64_t)bm;
-    st.bin_count = cnt[first];
-    if (nb == 128) {
-      const uint64_t pbits = ~(uint64_t)(prefix >> 64);
-      const u128 sc = bm + fx_from_bits(pbits, err);
-      st.cut_pbits = pbits;
-      st.cut_key = (uint64_t)prefix;
-      st.cut_count = bc + 1;
-      st.cut_mass_hi = (uint64_t)(sc >> 64);
-      st.cut_mass_lo = (uint64_t)sc;
-      st.done = 1;
-    }
+    st.bin_count = cnt[first];  // at 128 bits a single term: collected next
   }
 }
 
 void launch_segsel_level(const uint64_t* probs, const uint64_t* keys, const uint16_t* seg, uint64_t n, SegSel* sel,
-                         int slots, uint32_t* g_cnt, uint64_t* g_mass, uint32_t* err, cudaStream_t st) {
+                         int slots, uint32_t* g_cnt, uint64_t* g_sum, uint64_t* g_buf, uint32_t* g_bufn,
+                         uint32_t* err, cudaStream_t st) {
   cudaMemsetAsync(g_cnt, 0, sizeof(uint32_t) * SS_BINS * slots, st);
-  cudaMemsetAsync(g_mass, 0, sizeof(uint64_t) * 2 * SS_BINS * slots, st);
+  cudaMemsetAsync(g_sum, 0, sizeof(uint64_t) * 4 * slots, st);
+  cudaMemsetAsync(g_bufn, 0, sizeof(uint32_t) * slots, st);
   if (n > 0) {
-    const uint64_t chunks = (n + SS_CHUNK - 1) / SS_CHUNK;
-    const uint64_t grid = chunks < 148 * 4 ? chunks : 148 * 4;
-    k_segsel_hist<<<(unsigned)grid, 256, 0, st>>>(probs, keys, seg, n, sel, g_cnt, g_mass, err);
+    // 4 blocks per SM, one contiguous chunk each (whole multiples of a block's sweep)
+    const uint64_t sweep = (uint64_t)SS_BLOCK * SS_ILP;
+    uint64_t chunk = (n + 148 * 4 - 1) / (148 * 4);
+    chunk = (chunk + sweep - 1) / sweep * sweep;
+    if (chunk < 4 * sweep) chunk = 4 * sweep;
+    const uint64_t grid = (n + chunk - 1) / chunk;
+    k_segsel_hist<<<(unsigned)grid, SS_BLOCK, 0, st>>>(probs, keys, seg, n, chunk, sel, g_cnt, g_sum, g_buf, g_bufn,
+                                                       err);
   }
-  k_segsel_pick<<<slots, 256, 0, st>>>(sel, g_cnt, g_mass, err);
+  k_segsel_pick<<<slots, 256, 0, st>>>(sel, g_cnt);
 }
 
-// Finish: one block per unresolved segment walks the terms of its current
-// bin (already few) level after level inside shared memory.
-constexpr int SF_CAP = 4096;
-
-__global__ void __launch_bounds__(256) k_segsel_finish(const uint64_t* __restrict__ probs,
-                                                       const uint64_t* __restrict__ keys,
-                                                       const uint64_t* __restrict__ seg_start,
-                                                       const uint64_t* __restrict__ seg_end, SegSel* sel,
+// Finish: one block per segment collected in this level's scan resolves the
+// cut among the copied terms, level after level inside shared memory.
+__global__ void __launch_bounds__(256) k_segsel_finish(const uint64_t* __restrict__ g_buf,
+                                                       const uint32_t* __restrict__ g_bufn,
+                                                       const uint64_t* __restrict__ g_sum, SegSel* sel,
                                                        uint32_t* err) {
   extern __shared__ __align__(16) uint8_t s_dyn[];
   uint64_t* bhi = reinterpret_cast<uint64_t*>(s_dyn);
   uint64_t* blo = bhi + SF_CAP;
-  __shared__ uint32_t s_n;
   __shared__ uint32_t s_cnt[SS_BINS];
   __shared__ uint64_t s_mass[2 * SS_BINS];
   __shared__ uint64_t w_c[8];
@@ -499,32 +525,34 @@ __global__ void __launch_bounds__(256) k_segsel_finish(const uint64_t* __restric
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) {
     st = sel[blockIdx.x];
-    s_n = 0;
   }
   __syncthreads();
-  if (!st.active || st.done || st.bin_count > SF_CAP) return;
+  // only segments whose terms this level's scan copied (a collected bin is
+  // never empty; a segment that entered collect mode in this level's pick
+  // has nothing copied yet and waits for the next scan)
+  const uint32_t copied = g_bufn[blockIdx.x];
+  if (!st.active || st.done || copied == 0) return;
+  const uint32_t nb = copied < SF_CAP ? copied : SF_CAP;
+  if (tid == 0) {
+    st.total_mass_hi = g_sum[4 * blockIdx.x];
+    st.total_mass_lo = g_sum[4 * blockIdx.x + 1];
+    st.before_mass_hi = g_sum[4 * blockIdx.x + 2];
+    st.before_mass_lo = g_sum[4 * blockIdx.x + 3];
+  }
   {
-    const int bits = (int)st.bits;
-    for (uint64_t i = seg_start[blockIdx.x] + tid; i < seg_end[blockIdx.x]; i += blockDim.x) {
-      const uint64_t hi = ~probs[i];
-      if (bits <= 64 && ((hi ^ st.prefix_hi) >> (64 - bits)) != 0) continue;
-      const uint64_t lo = keys[i];
-      if (!seg_z_match(hi, lo, st.prefix_hi, st.prefix_lo, bits)) continue;
-      const uint32_t p = atomicAdd(&s_n, 1u);
-      if (p < SF_CAP) {
-        bhi[p] = hi;
-        blo[p] = lo;
-      }
+    const uint64_t* buf = g_buf + (uint64_t)blockIdx.x * 2 * SF_CAP;
+    for (uint32_t i = tid; i < nb; i += blockDim.x) {
+      bhi[i] = buf[2 * i];
+      blo[i] = buf[2 * i + 1];
     }
   }
   __syncthreads();
-  const uint32_t nb = s_n < SF_CAP ? s_n : SF_CAP;
   for (int it = 0; it < 128; ++it) {
     __syncthreads();
     if (st.done) break;
     const int bits = (int)st.bits;
     int D, shift;
-    seg_digit(bits, &D, &shift);
+    sel_digit(bits, &D, &shift);
     for (int b = tid; b < SS_BINS; b += blockDim.x) {
       s_cnt[b] = 0;
       s_mass[2 * b] = s_mass[2 * b + 1] = 0;
@@ -532,10 +560,10 @@ __global__ void __launch_bounds__(256) k_segsel_finish(const uint64_t* __restric
     if (tid == 0) s_first = 0xffffffffu;
     __syncthreads();
     for (uint32_t i = tid; i < nb; i += blockDim.x) {
-      if (!seg_z_match(bhi[i], blo[i], st.prefix_hi, st.prefix_lo, bits)) continue;
+      if (!z_matches(bhi[i], blo[i], st.prefix_hi, st.prefix_lo, bits)) continue;
       const uint32_t dg = (uint32_t)(make_u128(bhi[i], blo[i]) >> shift) & ((1u << D) - 1u);
       atomicAdd(&s_cnt[dg], 1u);
-      seg_add_u128(&s_mass[2 * dg], &s_mass[2 * dg + 1], fx_from_bits(~bhi[i], err));
+      atomic_add_u128(&s_mass[2 * dg], &s_mass[2 * dg + 1], fx_from_bits(~bhi[i], err));
     }
     __syncthreads();
     const int nbins = 1 << D;
@@ -626,15 +654,15 @@ __global__ void __launch_bounds__(256) k_segsel_finish(const uint64_t* __restric
   if (tid == 0) sel[blockIdx.x] = st;
 }
 
-void launch_segsel_finish(const uint64_t* probs, const uint64_t* keys, const uint64_t* seg_start,
-                          const uint64_t* seg_end, SegSel* sel, int slots, uint32_t* err, cudaStream_t st) {
+void launch_segsel_finish(const uint64_t* g_buf, const uint32_t* g_bufn, const uint64_t* g_sum, SegSel* sel,
+                          int slots, uint32_t* err, cudaStream_t st) {
   static bool attr_set = false;
   const size_t smem = 2 * sizeof(uint64_t) * SF_CAP;
   if (!attr_set) {
     cudaFuncSetAttribute(k_segsel_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr_set = true;
   }
-  k_segsel_finish<<<slots, 256, smem, st>>>(probs, keys, seg_start, seg_end, sel, err);
+  k_segsel_finish<<<slots, 256, smem, st>>>(g_buf, g_bufn, g_sum, sel, err);
 }
 
 // Renormalisation scale of every segment that found a cut.

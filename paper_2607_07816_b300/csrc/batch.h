@@ -6,15 +6,34 @@
 namespace sv {
 
 // Gate of one segment for one step.  m == 0 is the identity (each term its
-// own group); m < 0 marks a removed segment whose terms are dropped.
+// own group); m < 0 marks a removed segment whose terms are dropped.  The
+// sort key of a term is (segment, key with the gate bits taken out, r): the
+// gate bits are squeezed out at the ascending positions qs and r gathers
+// bit q[t] of the key into bit t.
 struct SegGate {
   int m;
-  int q[4];
+  int q[4];   // gate order (bit t of r)
+  int qs[4];  // the same qubits ascending
   uint32_t re_nz[16];
   uint32_t im_nz[16];
   double U[512];
-  BitPerm perm;
 };
+
+__device__ __forceinline__ uint32_t seg_gather_r(uint64_t key, const int* q, int m) {
+  uint32_t r = 0;
+#pragma unroll
+  for (int t = 0; t < 4; ++t)
+    if (t < m) r |= (uint32_t)((key >> q[t]) & 1ull) << t;
+  return r;
+}
+
+__device__ __forceinline__ uint64_t seg_deposit_r(uint32_t r, const int* q, int m) {
+  uint64_t x = 0;
+#pragma unroll
+  for (int t = 0; t < 4; ++t)
+    if (t < m) x |= (uint64_t)((r >> t) & 1u) << q[t];
+  return x;
+}
 
 // Select state of one segment (top-k by count, as the single-state select).
 struct SegSel {
@@ -43,10 +62,12 @@ void launch_seg_apply(int prec, const uint64_t* sk, const uint32_t* sidx, uint64
                       uint64_t max_tiles, cudaStream_t st);
 void launch_seg_bounds(const uint16_t* seg, uint64_t n, uint64_t* start, uint64_t* end, int slots,
                        cudaStream_t st);
+constexpr int SEGSEL_CAP = 4096;  // terms per segment copied for the finish kernel
 void launch_segsel_level(const uint64_t* probs, const uint64_t* keys, const uint16_t* seg, uint64_t n, SegSel* sel,
-                         int slots, uint32_t* g_cnt, uint64_t* g_mass, uint32_t* err, cudaStream_t st);
-void launch_segsel_finish(const uint64_t* probs, const uint64_t* keys, const uint64_t* seg_start,
-                          const uint64_t* seg_end, SegSel* sel, int slots, uint32_t* err, cudaStream_t st);
+                         int slots, uint32_t* g_cnt, uint64_t* g_sum, uint64_t* g_buf, uint32_t* g_bufn,
+                         uint32_t* err, cudaStream_t st);
+void launch_segsel_finish(const uint64_t* g_buf, const uint32_t* g_bufn, const uint64_t* g_sum, SegSel* sel,
+                          int slots, uint32_t* err, cudaStream_t st);
 void launch_segsel_scale(SegSel* sel, int slots, cudaStream_t st);
 void launch_seg_truncate(int prec, const uint64_t* keys, const void* amps, const uint64_t* probs, const uint16_t* seg,
                          uint64_t n, const SegSel* sel, uint64_t* keys_out, void* amps_out, uint64_t* probs_out,

@@ -1,6 +1,7 @@
 // C ABI of the batched form (svb_*, declared in include/sv.h): many circuits,
 // each a segment of one device-resident state, advanced one gate per circuit
 // per step with per-circuit top-k truncation (Sec. III) after every step.
+#include <algorithm>
 #include <cstdio>
 #include <string>
 #include <vector>
@@ -57,7 +58,9 @@ struct svb_state {
   SegSel* sel_dev = nullptr;
   SegSel* sel_host = nullptr;
   uint32_t* sel_cnt = nullptr;
-  uint64_t* sel_mass = nullptr;
+  uint64_t* sel_mass = nullptr;  // [max_slots][4]: total and before-bin mass (u128 each) of the collect scan
+  uint64_t* sel_buf = nullptr;   // [max_slots][SEGSEL_CAP] (hi, lo) copies of a segment's cut bin
+  uint32_t* sel_bufn = nullptr;
   uint64_t* bounds_dev = nullptr;   // [2][max_slots] start, end
   uint64_t* bounds_host = nullptr;
   Ctl* ctl = nullptr;
@@ -243,10 +246,12 @@ sv_status svb_create(int max_slots, int prec, void* cuda_stream, const sv_alloca
   b->gates_dev = (SegGate*)b_alloc(b, sizeof(SegGate) * max_slots);
   b->sel_dev = (SegSel*)b_alloc(b, sizeof(SegSel) * max_slots);
   b->sel_cnt = (uint32_t*)b_alloc(b, sizeof(uint32_t) * SEL_BINS * max_slots);
-  b->sel_mass = (uint64_t*)b_alloc(b, sizeof(uint64_t) * 2 * SEL_BINS * max_slots);
+  b->sel_mass = (uint64_t*)b_alloc(b, sizeof(uint64_t) * 4 * max_slots);
+  b->sel_buf = (uint64_t*)b_alloc(b, sizeof(uint64_t) * 2 * SEGSEL_CAP * max_slots);
+  b->sel_bufn = (uint32_t*)b_alloc(b, sizeof(uint32_t) * max_slots);
   b->bounds_dev = (uint64_t*)b_alloc(b, sizeof(uint64_t) * 2 * max_slots);
   if (!b->hist || !b->tile_counter || !b->ctl || !b->gates_dev || !b->sel_dev || !b->sel_cnt || !b->sel_mass ||
-      !b->bounds_dev)
+      !b->sel_buf || !b->sel_bufn || !b->bounds_dev)
     rc = SV_E_NOMEM;
   if (rc == SV_OK && (cudaMallocHost(&b->hist_host, sizeof(uint32_t) * MAX_PASSES * RADIX) != cudaSuccess ||
                       cudaMallocHost(&b->ctl_host, sizeof(Ctl)) != cudaSuccess ||
@@ -286,6 +291,8 @@ sv_status svb_destroy(svb_state* b) {
   b_free(b, b->sel_dev);
   b_free(b, b->sel_cnt);
   b_free(b, b->sel_mass);
+  b_free(b, b->sel_buf);
+  b_free(b, b->sel_bufn);
   b_free(b, b->bounds_dev);
   if (b->hist_host) cudaFreeHost(b->hist_host);
   if (b->ctl_host) cudaFreeHost(b->ctl_host);
@@ -383,7 +390,6 @@ sv_status svb_step(svb_state* b, const svb_gate* gates, int count) {
       gt.m = 0;
       gt.re_nz[0] = 1;
       gt.U[0] = 1.0;
-      build_perm(sl.n, 0, gt.q, 0, nullptr, &gt.perm);
       continue;
     }
     const svb_gate& g = gates[listed[s]];
@@ -401,7 +407,8 @@ sv_status svb_step(svb_state* b, const svb_gate* gates, int count) {
         if (rz) gt.re_nz[ro] |= 1u << r;
         if (iz) gt.im_nz[ro] |= 1u << r;
       }
-    build_perm(sl.n, g.m, gt.q, 0, nullptr, &gt.perm);
+    for (int t = 0; t < g.m; ++t) gt.qs[t] = g.qubits[t];
+    std::sort(gt.qs, gt.qs + g.m);
   }
   ++b->steps;
   const uint64_t N = b->N;
@@ -466,6 +473,7 @@ sv_status svb_step(svb_state* b, const svb_gate* gates, int count) {
       st.bits = 1;
       st.prefix_hi = 1ull << 63;
       st.target = sl.K;
+      st.bin_count = sl.count;  // a small segment is copied whole by the first scan
       ++ntrunc;
     }
   }
@@ -474,12 +482,16 @@ sv_status svb_step(svb_state* b, const svb_gate* gates, int count) {
               "svb_step select upload");
   if (rc != SV_OK) return rc;
   const uint64_t NP = b->N;
+  // Levels run without a host round trip in between (resolved segments cost
+  // nothing in later levels); the host checks after the third level, by
+  // which point a segment is normally resolved (exponent bin, top mantissa
+  // bin, then the copied bin), and then after every further level.
   bool all_done = false;
   for (int level = 0; level < 16 && !all_done; ++level) {
     launch_segsel_level(b->probs[b->cur], b->keys[b->cur], b->seg[b->cur], NP, b->sel_dev, top, b->sel_cnt,
-                        b->sel_mass, &b->ctl->err, b->st);
-    launch_segsel_finish(b->probs[b->cur], b->keys[b->cur], b->bounds_dev, b->bounds_dev + b->max_slots, b->sel_dev,
-                         top, &b->ctl->err, b->st);
+                        b->sel_mass, b->sel_buf, b->sel_bufn, &b->ctl->err, b->st);
+    launch_segsel_finish(b->sel_buf, b->sel_bufn, b->sel_mass, b->sel_dev, top, &b->ctl->err, b->st);
+    if (level < 2) continue;
     cudaMemcpyAsync(b->sel_host, b->sel_dev, sizeof(SegSel) * top, cudaMemcpyDeviceToHost, b->st);
     rc = b_sync_ctl(b, "svb_step select");
     if (rc != SV_OK) return rc;
