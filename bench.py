@@ -107,6 +107,35 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ------------------------------------------------------------------ ranks
+def dist_reduce(vals, op: str):
+    """Element-wise max or sum of a list of floats over all ranks (the list
+    unchanged without a process group).  NCCL groups reduce on the current
+    CUDA device, gloo groups on the CPU."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in vals]
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return [float(x) for x in t.tolist()]
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.barrier()
+
+
+def whole_job_rate(units_local: float, ms_local: float):
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time (weak scaling, every rank runs its own replica)."""
+    units = dist_reduce([units_local], "sum")[0]
+    ms = dist_reduce([ms_local], "max")[0]
+    return units / (ms / 1e3), units, ms
+
+
 # ------------------------------------------------------------------ roofline
 def phase_model(ph: str, totals: dict, prec: str, passes: int):
     """Algorithmic bytes and FP64 flops of one phase over the timed steps.
@@ -172,8 +201,7 @@ def run_ours(args, rank, world):
             st.peak()
             gi += 1
         torch.cuda.synchronize(dev)
-        if world > 1:
-            torch.distributed.barrier()
+        barrier()
         st.set_timing(True)
         totals = {"n_in": 0, "n_pre": 0, "n_kept": 0, "dfma": 0.0, "select_levels": 0, "steps": steps,
                   "sort_passes": 0, "window_hits": 0, "window_terms": 0}
@@ -207,16 +235,14 @@ def run_ours(args, rank, world):
         ms = e0.elapsed_time(e1)
         clk = clocks.stop() if clocks else None
         phases = st.phase_times()
-        if world > 1:
-            t = torch.tensor([ms], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+        barrier()
+        rate, units_all, ms = whole_job_rate(totals["n_in"], ms)
         peak = st.peak()
         fin = st.stats()
         paths = {k: fin[k] for k in ("local_gates", "global_gates", "local_fallbacks")}
         st.close()
         return {"ms": ms, "totals": totals, "phases": phases, "launches": launches, "clocks": clk,
-                "peak": peak, "hidden": circ.hidden, "paths": paths}
+                "peak": peak, "hidden": circ.hidden, "paths": paths, "rate": rate, "units_all": units_all}
 
     main = run_prec(args.prec, args.K, args.steps, args.warmup, sample_clocks=True)
     res = {"main": main}
@@ -240,6 +266,7 @@ def run_e2e(args, rank, dev, stream):
     # host-resident inputs: the gate matrices in pinned host memory
     pinned = [(q, torch.from_numpy(np.ascontiguousarray(u)).pin_memory().numpy()) for (q, u) in circ.gates]
     torch.cuda.synchronize(dev)
+    barrier()
     h0, d0 = sv.sv_transfer_bytes()
     t0 = time.perf_counter()
     st = sv.SparseState(circ.n, args.K, 1.0, prec=prec, stream=stream.cuda_stream)
@@ -254,7 +281,9 @@ def run_e2e(args, rank, dev, stream):
     wall = time.perf_counter() - t0
     h1, d1 = sv.sv_transfer_bytes()
     g = len(pinned)
-    return {"value": n_in / wall, "unit": "terms/s", "h2d_bytes_per_step": int((h1 - h0) / g),
+    barrier()
+    rate, _, _ = whole_job_rate(n_in, wall * 1e3)
+    return {"value": rate, "unit": "terms/s", "h2d_bytes_per_step": int((h1 - h0) / g),
             "d2h_bytes_per_step": int((d1 - d0) / g), "wall_s": wall, "gates": g,
             "peak_is_hidden": bool(key == circ.hidden), "peak_prob": pr}
 
@@ -466,7 +495,7 @@ def main():
     main_r = res["main"]
     tot = main_r["totals"]
     ms = main_r["ms"]
-    value = tot["n_in"] * world / (ms / 1e3)
+    value = main_r["rate"]
     bm, bstrict = gate_bytes_method(tot, args.prec)
     bw = peaks["hbm_gbs"] * 1e9
     line = {
@@ -494,7 +523,7 @@ def main():
         c = res["c64"]
         ct = c["totals"]
         cb, _ = gate_bytes_method(ct, "c64")
-        line["c64"] = {"value": ct["n_in"] / (c["ms"] / 1e3), "unit": "terms/s", "ms_per_step": c["ms"] / args.steps,
+        line["c64"] = {"value": c["rate"], "unit": "terms/s", "ms_per_step": c["ms"] / args.steps,
                        "B_method_frac": round(cb / (c["ms"] / 1e3) / bw, 4),
                        "roofline": roofline(c, "c64", peaks),
                        "phases_ms": {k: round(v[0], 3) for k, v in c["phases"].items()}}
