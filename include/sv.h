@@ -228,6 +228,18 @@ const char* svb_last_error(const svb_state* b);
 sv_status sv_peak_noalloc(int prec, const uint64_t* keys, const void* amps, uint64_t n,
                           void* cuda_stream, uint64_t* key, double* prob);
 
+/* Device self-test of the complex64 arithmetic that the library forms
+ * without float<->double conversion instructions (widening and rounding by
+ * bit manipulation, bit-identical by construction): which = 0 checks the
+ * probability fma(double(re), double(re), double(im) * double(im)),
+ * which = 1 the rescaled amplitude float(double(x) * s).  n cases drawn from
+ * seed (random bit patterns, subnormals, few-bit significands for exact
+ * rounding ties) are compared on the default stream with the results of the
+ * conversion instructions; *mismatches receives the count and *first_bad
+ * the lowest failing case index (UINT64_MAX when none).  SV_E_ARG for
+ * another `which` or NULL outputs. */
+sv_status sv_selftest(int which, uint64_t n, uint64_t seed, uint64_t* mismatches, uint64_t* first_bad);
+
 #ifdef __cplusplus
 }
 #endif

@@ -13,6 +13,7 @@
 #include "internal.h"
 #include "tile.cuh"
 #include "batch.h"
+#include "c64_exact.cuh"
 #include "select.cuh"
 
 namespace sv {
@@ -126,102 +127,185 @@ struct SCplx<float> {
 __device__ __forceinline__ double sfma(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ float sfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 
-constexpr int SA_BLOCK = 256, SA_ITEMS = 4;
+constexpr int SA_BLOCK = 256;
 
-// One thread per output slot (group, r'); every group owns 2^mmax slots and
-// uses the first 2^m of them (m of its segment).  U entries are rounded to
-// the amplitude precision exactly as in the single-state path.
-template <typename Real>
+// One thread per partner group (GPT consecutive groups per thread, MAXD =
+// 2^mmax outputs per group at most).  A thread reads its group's members
+// once, in ascending r, and runs every output's fused multiply-add chain in
+// registers (the single-state order, U rounded to the amplitude precision,
+// products with a zero U component skipped).  Nonzero outputs are placed in
+// (group, r') order: a block scan of the per-thread counts and a decoupled
+// look-back over tiles give each thread its output range.
+template <typename Real, int MAXD, int GPT>
 __global__ void __launch_bounds__(SA_BLOCK) k_seg_apply(
     const uint64_t* __restrict__ sk, const uint32_t* __restrict__ sidx, uint64_t n,
     const uint32_t* __restrict__ heads, const typename SCplx<Real>::T* __restrict__ amps_in, int shift,
-    int mmax, const SegGate* __restrict__ gates, uint64_t* __restrict__ keys_out,
+    const SegGate* __restrict__ gates, uint64_t* __restrict__ keys_out,
     typename SCplx<Real>::T* __restrict__ amps_out, uint64_t* __restrict__ probs_out,
-    uint16_t* __restrict__ seg_out, uint64_t* lookback, Ctl* ctl) {
-  typedef TileLayout<SA_BLOCK, SA_ITEMS> L;
+    uint16_t* __restrict__ seg_out, uint64_t* lookback, uint64_t max_tiles, Ctl* ctl) {
   typedef typename SCplx<Real>::T C2;
-  __shared__ CompactShared<SA_BLOCK> cs;
+  constexpr int TILE_G = SA_BLOCK * GPT;
+  constexpr int WARPS = SA_BLOCK / 32;
+  __shared__ uint32_t s_warp[WARPS];
+  __shared__ uint64_t s_base;
+  __shared__ uint32_t s_total;
   __shared__ uint64_t s_tile;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint64_t G = ctl->count[0];
-  const uint64_t S = G << mmax;
-  const uint64_t tiles = (S + L::TILE - 1) / L::TILE;
+  const uint64_t tiles = (G + TILE_G - 1) / TILE_G;
+  if (tiles > max_tiles) {  // the look-back buffer was sized for fewer tiles
+    if (blockIdx.x == 0 && tid == 0) atomicOr(&ctl->err, ERR_INVARIANT);
+    return;
+  }
   while (true) {
-    if (threadIdx.x == 0) s_tile = atomicAdd((unsigned long long*)&ctl->tile_counter[1], 1ull);
+    if (tid == 0) s_tile = atomicAdd((unsigned long long*)&ctl->tile_counter[1], 1ull);
     __syncthreads();
     const uint64_t tile = s_tile;
     if (tile >= tiles) break;
-    const uint64_t base = tile * L::TILE;
-    bool flag[SA_ITEMS];
-    uint32_t pos[SA_ITEMS];
-    Real yr[SA_ITEMS], yi[SA_ITEMS];
-    uint64_t ykey[SA_ITEMS];
-    uint16_t ysg[SA_ITEMS];
+    const uint64_t g0 = tile * TILE_G + (uint64_t)tid * GPT;
+    Real yr[GPT][MAXD], yi[GPT][MAXD];
+    uint32_t keep[GPT], qpack[GPT];
+    int mj[GPT];
+    uint64_t rest[GPT];
+    uint16_t sgj[GPT];
+    uint32_t cnt = 0;
+    // the loads of the GPT groups are issued together, level by level
+    // (heads, first sort key and index, first amplitude): most groups of a
+    // truncated state have a single member
+    uint64_t hb[GPT + 1], s0v[GPT];
+    C2 x0v[GPT];
 #pragma unroll
-    for (int j = 0; j < SA_ITEMS; ++j) {
-      const uint64_t slot = L::index(base, j);
-      Real re = (Real)0, im = (Real)0;
-      bool f = false;
-      uint64_t key = 0;
-      uint32_t sg = 0;
-      if (slot < S) {
-        const uint64_t g = slot >> mmax;
-        const uint32_t ro = (uint32_t)(slot & ((1u << mmax) - 1u));
-        const uint64_t h = heads[g];
-        const uint64_t e = g + 1 < G ? (uint64_t)heads[g + 1] : n;
-        const uint64_t s0 = sk[h];
-        sg = (uint32_t)(s0 >> shift);
-        const SegGate& gt = gates[sg];
-        const int m = gt.m;
-        const int d = 1 << m;
-        if ((int)ro < d) {
-          uint32_t present = 0;
-          for (uint64_t i = h; i < e; ++i) present |= 1u << (uint32_t)(sk[i] & (uint64_t)(d - 1));
-          const uint32_t rnz = gt.re_nz[ro] & present, inz = gt.im_nz[ro] & present;
-          uint32_t cols = rnz | inz;
-          while (cols) {
-            const int r = __ffs(cols) - 1;
-            cols &= cols - 1u;
-            const C2 x = amps_in[sidx[h + __popc(present & ((1u << r) - 1u))]];
-            const Real ur = (Real)gt.U[2 * (ro * d + r)], ui = (Real)gt.U[2 * (ro * d + r) + 1];
-            if ((rnz >> r) & 1u) {
-              re = sfma(ur, x.x, re);
-              im = sfma(ur, x.y, im);
-            }
-            if ((inz >> r) & 1u) {
-              re = sfma(-ui, x.y, re);
-              im = sfma(ui, x.x, im);
-            }
+    for (int j = 0; j <= GPT; ++j) {
+      const uint64_t g = g0 + j;
+      hb[j] = g < G ? (uint64_t)heads[g] : n;
+    }
+#pragma unroll
+    for (int j = 0; j < GPT; ++j) {
+      const bool ok = g0 + j < G;
+      s0v[j] = ok ? sk[hb[j]] : 0ull;
+      const uint32_t ix = ok ? sidx[hb[j]] : 0u;
+      x0v[j] = ok ? amps_in[ix] : C2();
+    }
+#pragma unroll
+    for (int j = 0; j < GPT; ++j) {
+      keep[j] = 0;
+      qpack[j] = 0;
+      mj[j] = 0;
+      rest[j] = 0;
+      sgj[j] = 0;
+#pragma unroll
+      for (int ro = 0; ro < MAXD; ++ro) yr[j][ro] = yi[j][ro] = (Real)0;
+      const uint64_t g = g0 + j;
+      if (g >= G) continue;
+      const uint64_t h = hb[j];
+      const uint64_t e = hb[j + 1];
+      const uint64_t s0 = s0v[j];
+      const uint32_t sg = (uint32_t)(s0 >> shift);
+      const SegGate& gt = gates[sg];
+      const int m = gt.m;
+      const int d = 1 << m;
+      for (uint64_t i = h; i < e; ++i) {
+        const uint32_t r = (uint32_t)((i == h ? s0 : sk[i]) & (uint64_t)(d - 1));
+        const C2 x = i == h ? x0v[j] : amps_in[sidx[i]];
+#pragma unroll
+        for (int ro = 0; ro < MAXD; ++ro) {
+          if (ro >= d) break;
+          const bool rnz = (gt.re_nz[ro] >> r) & 1u, inz = (gt.im_nz[ro] >> r) & 1u;
+          if (rnz) {
+            const Real ur = (Real)gt.U[2 * (ro * d + r)];
+            yr[j][ro] = sfma(ur, x.x, yr[j][ro]);
+            yi[j][ro] = sfma(ur, x.y, yi[j][ro]);
           }
-          const uint64_t local = s0 & ((1ull << shift) - 1ull);
-          key = spread_in(local >> m, gt.qs, m) | seg_deposit_r(ro, gt.q, m);
-          f = !(re == (Real)0 && im == (Real)0);
+          if (inz) {
+            const Real ui = (Real)gt.U[2 * (ro * d + r) + 1];
+            yr[j][ro] = sfma(-ui, x.y, yr[j][ro]);
+            yi[j][ro] = sfma(ui, x.x, yi[j][ro]);
+          }
         }
       }
-      yr[j] = re;
-      yi[j] = im;
-      ykey[j] = key;
-      ysg[j] = (uint16_t)sg;
-      flag[j] = f;
-    }
-    tile_compact<SA_BLOCK, SA_ITEMS>(flag, pos, cs, lookback, tile, &ctl->err);
 #pragma unroll
-    for (int j = 0; j < SA_ITEMS; ++j) {
-      if (flag[j]) {
-        const uint64_t o = cs.tile_base_out + pos[j];
-        keys_out[o] = ykey[j];
-        C2 y;
-        y.x = yr[j];
-        y.y = yi[j];
-        amps_out[o] = y;
-        probs_out[o] = (uint64_t)__double_as_longlong(prob_of((double)yr[j], (double)yi[j]));
-        seg_out[o] = ysg[j];
+      for (int ro = 0; ro < MAXD; ++ro)
+        if (ro < d && !(yr[j][ro] == (Real)0 && yi[j][ro] == (Real)0)) keep[j] |= 1u << ro;
+      for (int t = 0; t < m; ++t) qpack[j] |= (uint32_t)gt.q[t] << (8 * t);
+      mj[j] = m;
+      rest[j] = spread_in((s0 & low_mask(shift)) >> m, gt.qs, m);
+      sgj[j] = (uint16_t)sg;
+      cnt += __popc(keep[j]);
+    }
+    // block exclusive scan of the counts, then the tile's global base
+    uint32_t x = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      const uint32_t v = lane < WARPS ? s_warp[lane] : 0u;
+      uint32_t w = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += y;
+      }
+      if (lane < WARPS) s_warp[lane] = w - v;
+      const uint32_t total = __shfl_sync(0xffffffffu, w, 31);
+      const uint64_t base = lookback_exclusive_warp(lookback, tile, total, &ctl->err);
+      if (lane == 0) {
+        s_total = total;
+        s_base = base;
       }
     }
-    if (tile == tiles - 1 && threadIdx.x == 0) ctl->count[1] = cs.tile_base_out + cs.tile_total;
+    __syncthreads();
+    uint64_t o = s_base + s_warp[warp] + (x - cnt);
+#pragma unroll
+    for (int j = 0; j < GPT; ++j) {
+      if (!keep[j]) continue;
+      int q[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) q[t] = (int)((qpack[j] >> (8 * t)) & 0xffu);
+#pragma unroll
+      for (int ro = 0; ro < MAXD; ++ro) {
+        if (!((keep[j] >> ro) & 1u)) continue;
+        keys_out[o] = rest[j] | seg_deposit_r((uint32_t)ro, q, mj[j]);
+        C2 y;
+        y.x = yr[j][ro];
+        y.y = yi[j][ro];
+        amps_out[o] = y;
+        probs_out[o] = amp_prob_bits(yr[j][ro], yi[j][ro]);
+        seg_out[o] = sgj[j];
+        ++o;
+      }
+    }
+    if (tile == tiles - 1 && tid == 0) ctl->count[1] = s_base + s_total;
     __syncthreads();
   }
 }
 
+template <typename Real>
+void seg_apply_dispatch(int mmax, unsigned grid, cudaStream_t st, const uint64_t* sk, const uint32_t* sidx,
+                        uint64_t n, const uint32_t* heads, const void* amps_in, int shift, const SegGate* gates,
+                        uint64_t* keys_out, void* amps_out, uint64_t* probs_out, uint16_t* seg_out,
+                        uint64_t* lookback, uint64_t max_tiles, Ctl* ctl) {
+  typedef typename SCplx<Real>::T C2;
+  const C2* ai = (const C2*)amps_in;
+  C2* ao = (C2*)amps_out;
+#define SV_SEG_APPLY(MAXD, GPT)                                                                         \
+  k_seg_apply<Real, MAXD, GPT><<<grid, SA_BLOCK, 0, st>>>(sk, sidx, n, heads, ai, shift, gates, keys_out, ao, \
+                                                          probs_out, seg_out, lookback, max_tiles, ctl)
+  switch (mmax) {
+    case 0: SV_SEG_APPLY(1, 4); break;
+    case 1: SV_SEG_APPLY(2, 4); break;
+    case 2: SV_SEG_APPLY(4, 2); break;
+    case 3: SV_SEG_APPLY(8, 1); break;
+    default: SV_SEG_APPLY(16, 1); break;
+  }
+#undef SV_SEG_APPLY
+}
+
+// max_tiles bounds the look-back buffer: at least (n << mmax) / 1024 + 1,
+// which covers the ceil(groups / (256 * GPT)) tiles of every instantiation.
 void launch_seg_apply(int prec, const uint64_t* sk, const uint32_t* sidx, uint64_t n, const uint32_t* heads,
                       const void* amps_in, int shift, int mmax, const SegGate* gates, uint64_t* keys_out,
                       void* amps_out, uint64_t* probs_out, uint16_t* seg_out, uint64_t* lookback, Ctl* ctl,
@@ -232,13 +316,11 @@ void launch_seg_apply(int prec, const uint64_t* sk, const uint32_t* sidx, uint64
   if (n == 0) return;
   const uint64_t grid = max_tiles < 148 * 4 ? (max_tiles ? max_tiles : 1) : 148 * 4;
   if (prec == 0)
-    k_seg_apply<double><<<(unsigned)grid, SA_BLOCK, 0, st>>>(sk, sidx, n, heads, (const double2*)amps_in, shift,
-                                                             mmax, gates, keys_out, (double2*)amps_out,
-                                                             probs_out, seg_out, lookback, ctl);
+    seg_apply_dispatch<double>(mmax, (unsigned)grid, st, sk, sidx, n, heads, amps_in, shift, gates, keys_out,
+                               amps_out, probs_out, seg_out, lookback, max_tiles, ctl);
   else
-    k_seg_apply<float><<<(unsigned)grid, SA_BLOCK, 0, st>>>(sk, sidx, n, heads, (const float2*)amps_in, shift,
-                                                            mmax, gates, keys_out, (float2*)amps_out, probs_out,
-                                                            seg_out, lookback, ctl);
+    seg_apply_dispatch<float>(mmax, (unsigned)grid, st, sk, sidx, n, heads, amps_in, shift, gates, keys_out,
+                              amps_out, probs_out, seg_out, lookback, max_tiles, ctl);
 }
 
 // ---------------------------------------------------------------- segment bounds
@@ -680,21 +762,10 @@ void launch_segsel_scale(SegSel* sel, int slots, cudaStream_t st) {
 // ---------------------------------------------------------------- compaction
 constexpr int SC_BLOCK = 256, SC_ITEMS = 8;
 
-template <typename C2>
-__device__ __forceinline__ C2 seg_scale(C2 a, double s);
-template <>
-__device__ __forceinline__ double2 seg_scale<double2>(double2 a, double s) {
-  return make_double2(__dmul_rn(a.x, s), __dmul_rn(a.y, s));
-}
-template <>
-__device__ __forceinline__ float2 seg_scale<float2>(float2 a, double s) {
-  return make_float2(__double2float_rn(__dmul_rn((double)a.x, s)), __double2float_rn(__dmul_rn((double)a.y, s)));
-}
-
 // Keep, in each segment with a cut, the terms not after its cut (scaled);
 // other segments keep everything unchanged.
 template <typename C2>
-__global__ void __launch_bounds__(SC_BLOCK) k_seg_truncate(
+__global__ void __launch_bounds__(SC_BLOCK, 4) k_seg_truncate(
     const uint64_t* __restrict__ keys, const C2* __restrict__ amps, const uint64_t* __restrict__ probs,
     const uint16_t* __restrict__ seg, uint64_t n, const SegSel* __restrict__ sel, uint64_t* __restrict__ keys_out,
     C2* __restrict__ amps_out, uint64_t* __restrict__ probs_out, uint16_t* __restrict__ seg_out,
@@ -711,39 +782,60 @@ __global__ void __launch_bounds__(SC_BLOCK) k_seg_truncate(
     const uint64_t base = tile * L::TILE;
     bool flag[SC_ITEMS];
     uint32_t pos[SC_ITEMS];
+    uint16_t sgv[SC_ITEMS];
+    uint64_t pbv[SC_ITEMS];
+#pragma unroll
+    for (int j = 0; j < SC_ITEMS; ++j) {
+      const uint64_t i = L::index(base, j);
+      sgv[j] = i < n ? seg[i] : (uint16_t)0;
+      pbv[j] = i < n ? probs[i] : 0ull;
+    }
+    // a segment's cut, cached across a thread's items (a tile rarely spans
+    // more than one segment)
+    int last = -1;
+    bool cut_on = false;
+    uint64_t cut_pb = 0, cut_key = 0;
+    double scale = 1.0;
 #pragma unroll
     for (int j = 0; j < SC_ITEMS; ++j) {
       const uint64_t i = L::index(base, j);
       bool f = false;
       if (i < n) {
-        const SegSel& st = sel[seg[i]];
-        if (st.active && st.done == 1) {
-          const uint64_t pb = probs[i];
-          f = pb > st.cut_pbits || (pb == st.cut_pbits && keys[i] <= st.cut_key);
-        } else {
-          f = true;
+        if ((int)sgv[j] != last) {
+          last = sgv[j];
+          const SegSel& st = sel[last];
+          cut_on = st.active && st.done == 1;
+          cut_pb = st.cut_pbits;
+          cut_key = st.cut_key;
+          scale = st.scale;
         }
+        f = !cut_on || pbv[j] > cut_pb || (pbv[j] == cut_pb && keys[i] <= cut_key);
       }
       flag[j] = f;
     }
     tile_compact<SC_BLOCK, SC_ITEMS>(flag, pos, cs, lookback, tile, &ctl->err);
+    last = -1;
 #pragma unroll
     for (int j = 0; j < SC_ITEMS; ++j) {
       if (flag[j]) {
         const uint64_t i = L::index(base, j);
         const uint64_t o = cs.tile_base_out + pos[j];
-        const uint16_t sg = seg[i];
-        const SegSel& st = sel[sg];
+        if ((int)sgv[j] != last) {
+          last = sgv[j];
+          const SegSel& st = sel[last];
+          cut_on = st.active && st.done == 1;
+          scale = st.scale;
+        }
         C2 a = amps[i];
-        uint64_t pb = probs[i];
-        if (st.active && st.done == 1) {
-          a = seg_scale<C2>(a, st.scale);
-          pb = (uint64_t)__double_as_longlong(prob_of((double)a.x, (double)a.y));
+        uint64_t pb = pbv[j];
+        if (cut_on) {
+          a = amp_scaled(a, scale);
+          pb = amp_prob_bits(a);
         }
         keys_out[o] = keys[i];
         amps_out[o] = a;
         probs_out[o] = pb;
-        seg_out[o] = sg;
+        seg_out[o] = sgv[j];
       }
     }
     if (tile == tiles - 1 && threadIdx.x == 0) ctl->count[2] = cs.tile_base_out + cs.tile_total;

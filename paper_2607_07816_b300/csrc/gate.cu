@@ -8,6 +8,7 @@
 // is a run of equal sk >> m with its members in ascending r.  One thread then
 // computes one output (group, r') in registers, and zero outputs are dropped
 // while the survivors are compacted in (group, r') order.
+#include "c64_exact.cuh"
 #include "internal.h"
 #include "tile.cuh"
 
@@ -265,7 +266,7 @@ __global__ void __launch_bounds__(APPLY_BLOCK, 2) k_gate_apply(
         const uint64_t o = cs.tile_base_out + pos[j];
         keys_out[o] = key;
         amps_out[o] = yv;
-        probs_out[o] = (uint64_t)__double_as_longlong(prob_of((double)yv.x, (double)yv.y));
+        probs_out[o] = amp_prob_bits(yv);
       }
     }
     if (tile == tiles - 1 && threadIdx.x == 0) ctl->count[1] = cs.tile_base_out + cs.tile_total;

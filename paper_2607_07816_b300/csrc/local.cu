@@ -17,6 +17,7 @@
 // result is again bucket-contiguous; the order of batches in the output is
 // not fixed, which changes no result (truncation and readout do not depend on
 // the order of terms).
+#include "c64_exact.cuh"
 #include "internal.h"
 #include "tile.cuh"
 
@@ -336,7 +337,7 @@ __global__ void __launch_bounds__(LG_THREADS, 1) k_local_gate(
       yv.x = re;
       yv.y = im;
       amps_out[o] = yv;
-      probs_out[o] = (uint64_t)__double_as_longlong(prob_of((double)re, (double)im));
+      probs_out[o] = amp_prob_bits(re, im);
       if (re == (Real)0 && im == (Real)0) ++zeros;
     }
     if (zeros) atomicAdd((unsigned long long*)&ctl->count[3], (unsigned long long)zeros);

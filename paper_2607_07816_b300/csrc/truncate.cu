@@ -13,6 +13,7 @@
 // block.  A final compaction keeps every term not after the cut and applies
 // the renormalisation.
 #include "internal.h"
+#include "c64_exact.cuh"
 #include "select.cuh"
 #include "tile.cuh"
 
@@ -642,18 +643,6 @@ void launch_set_scale(Ctl* ctl, cudaStream_t st) { k_set_scale<<<1, 1, 0, st>>>(
 
 constexpr int TC_BLOCK = 256, TC_ITEMS = 8;
 
-template <typename C2>
-__device__ __forceinline__ C2 scale_amp(C2 a, double s);
-template <>
-__device__ __forceinline__ double2 scale_amp<double2>(double2 a, double s) {
-  return make_double2(__dmul_rn(a.x, s), __dmul_rn(a.y, s));
-}
-template <>
-__device__ __forceinline__ float2 scale_amp<float2>(float2 a, double s) {
-  return make_float2(__double2float_rn(__dmul_rn((double)a.x, s)),
-                     __double2float_rn(__dmul_rn((double)a.y, s)));
-}
-
 // Keep the terms not after the cut (probability above the cut's, or equal
 // with key not above it), in input order, scaled by ctl->scale.  Only the
 // probability is read for every term; keys (for ties at the cut) and
@@ -693,10 +682,10 @@ __global__ void __launch_bounds__(TC_BLOCK) k_truncate_compact(
       if (flag[j]) {
         const uint64_t i = L::index(base, j);
         const uint64_t o = cs.tile_base_out + pos[j];
-        const C2 a = scale_amp<C2>(amps[i], s);
+        const C2 a = amp_scaled(amps[i], s);
         keys_out[o] = keys[i];
         amps_out[o] = a;
-        probs_out[o] = (uint64_t)__double_as_longlong(prob_of((double)a.x, (double)a.y));
+        probs_out[o] = amp_prob_bits(a);
       }
     }
     if (tile == tiles - 1 && threadIdx.x == 0) ctl->count[2] = cs.tile_base_out + cs.tile_total;
@@ -738,10 +727,10 @@ __global__ void __launch_bounds__(WP_BLOCK) k_truncate_write(
       if (flag[j]) {
         const uint64_t i = L::index(base, j);
         const uint64_t o = ob + pos[j];
-        const C2 a = scale_amp<C2>(amps[i], s);
+        const C2 a = amp_scaled(amps[i], s);
         keys_out[o] = keys[i];
         amps_out[o] = a;
-        probs_out[o] = (uint64_t)__double_as_longlong(prob_of((double)a.x, (double)a.y));
+        probs_out[o] = amp_prob_bits(a);
       }
     }
     __syncthreads();
@@ -943,7 +932,7 @@ __global__ void __launch_bounds__(TC_BLOCK) k_load_compact(const uint64_t* __res
         uint64_t o = cs.tile_base_out + pos[j];
         keys_out[o] = skeys[i];
         amps_out[o] = av[j];
-        probs_out[o] = (uint64_t)__double_as_longlong(prob_of((double)av[j].x, (double)av[j].y));
+        probs_out[o] = amp_prob_bits(av[j]);
       }
     }
     if (tile == tiles - 1 && threadIdx.x == 0) ctl->count[2] = cs.tile_base_out + cs.tile_total;

@@ -25,7 +25,7 @@ EXPORTED = ["sv_create", "sv_create_ex", "sv_destroy", "sv_apply_gate", "sv_trun
             "sv_probs", "sv_num_terms", "sv_retained_mass", "sv_export", "sv_load", "sv_last_error",
             "sv_last_stats", "sv_set_timing", "sv_phase_times", "sv_launch_count", "sv_transfer_bytes", "sv_peak_noalloc",
             "svb_create", "svb_destroy", "svb_add", "svb_remove", "svb_step", "svb_num_terms",
-            "svb_retained_mass", "svb_peak", "svb_export", "svb_last_error"]
+            "svb_retained_mass", "svb_peak", "svb_export", "svb_last_error", "sv_selftest"]
 PHASES = ["keys", "sort", "heads", "apply", "select", "compact", "peak", "other", "window", "local"]
 
 
@@ -128,6 +128,8 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.svb_last_error.argtypes = [vp]
     lib.sv_peak_noalloc.restype = i32
     lib.sv_peak_noalloc.argtypes = [i32, vp, vp, u64, vp, P(u64), P(dbl)]
+    lib.sv_selftest.restype = i32
+    lib.sv_selftest.argtypes = [i32, u64, u64, P(u64), P(u64)]
     lib.sv_transfer_bytes.restype = None
     lib.sv_transfer_bytes.argtypes = [P(u64), P(u64)]
     _lib = lib
@@ -266,6 +268,18 @@ def sv_peak_noalloc(prec: int, keys_ptr: int, amps_ptr: int, n: int, stream: int
     if rc != SV_OK:
         raise SVError(rc, "sv_peak_noalloc failed")
     return k.value, p.value
+
+
+def sv_selftest(which: int, n: int, seed: int = 1):
+    """Device self-test of the conversion-free complex64 arithmetic against
+    the conversion instructions (see include/sv.h): returns (mismatches,
+    first bad case index or None)."""
+    bad, first = ctypes.c_uint64(), ctypes.c_uint64()
+    rc = load_library().sv_selftest(which, ctypes.c_uint64(n), ctypes.c_uint64(seed), ctypes.byref(bad),
+                                    ctypes.byref(first))
+    if rc != SV_OK:
+        raise SVError(rc, "sv_selftest failed")
+    return bad.value, (None if first.value == (1 << 64) - 1 else first.value)
 
 
 # ------------------------------------------------ convenience wrapper
