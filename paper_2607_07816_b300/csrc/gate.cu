@@ -106,8 +106,6 @@ struct Cplx<float> {
 __device__ __forceinline__ double fma_r(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ float fma_r(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 
-constexpr int APPLY_BLOCK = 512;
-constexpr int APPLY_TILE = 2048;                      // output slots per tile (multiple of 16)
 constexpr int APPLY_ITEMS = APPLY_TILE / APPLY_BLOCK;  // 4
 
 template <typename Real>
@@ -131,7 +129,7 @@ struct ApplySmem {
 // in that order and parks it in shared memory under its original slot.
 // Phase 3 drops exact zeros and writes the survivors in slot order.
 template <typename Real>
-__global__ void __launch_bounds__(APPLY_BLOCK, 2) k_gate_apply(
+__global__ void __launch_bounds__(APPLY_BLOCK, 4) k_gate_apply(
     const uint64_t* __restrict__ sk, const uint32_t* __restrict__ sidx, uint64_t n,
     const uint32_t* __restrict__ heads, const typename Cplx<Real>::T* __restrict__ amps_in,
     const GateParams gp, uint64_t* __restrict__ keys_out, typename Cplx<Real>::T* __restrict__ amps_out,

@@ -14,6 +14,8 @@ constexpr int MAX_PASSES = 8;
 constexpr int SORT_THREADS = 512;
 constexpr int SORT_ITEMS = 8;
 constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;
+constexpr int APPLY_BLOCK = 256;
+constexpr int APPLY_TILE = 1024;  // output slots per tile of the group mat-vec (multiple of 16)
 
 // Scratch used by one LSD radix sort.
 struct SortScratch {

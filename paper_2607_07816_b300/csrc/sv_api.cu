@@ -511,7 +511,7 @@ sv_status sv_apply_gate(sv_state* s, int m, const int* qubits, const double* U) 
     return fail(s, SV_E_ARG, "sv_apply_gate: state too large for 32-bit term indices");
   sv_status rc = ensure_state_cap(s, N << m);
   if (rc == SV_OK) rc = ensure_sort_cap(s, N);
-  const uint64_t apply_tiles = ((N << m) + 2047) / 2048 + 1;
+  const uint64_t apply_tiles = ((N << m) + APPLY_TILE - 1) / APPLY_TILE + 1;
   if (rc == SV_OK) rc = ensure_lookback(s, apply_tiles + 16);
   if (rc != SV_OK) return rc;
   const int alt = 1 - s->cur;

@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(SAMPLE_THREADS) k_sample_window(const uint64_t
   }
 }
 
-constexpr int WP_BLOCK = 256, WP_ITEMS = 16;
+constexpr int WP_BLOCK = 256, WP_ITEMS = 8;
 constexpr int WP_TILE = WP_BLOCK * WP_ITEMS;
 
 __device__ __forceinline__ u128 warp_sum_u128(u128 v) {
@@ -245,7 +245,7 @@ __device__ __forceinline__ u128 warp_sum_u128(u128 v) {
 // above the window, the window's mass and its terms (probability, key, index)
 // gathered into the window buffer, and per tile the number of terms above
 // the window (they are kept whatever the exact cut is).
-__global__ void __launch_bounds__(WP_BLOCK) k_window_pass(const uint64_t* __restrict__ probs,
+__global__ void __launch_bounds__(WP_BLOCK, 4) k_window_pass(const uint64_t* __restrict__ probs,
                                                           const uint64_t* __restrict__ keys, uint64_t n,
                                                           Ctl* ctl, uint64_t* __restrict__ wp,
                                                           uint64_t* __restrict__ wk, uint32_t* __restrict__ wi,
@@ -269,7 +269,6 @@ __global__ void __launch_bounds__(WP_BLOCK) k_window_pass(const uint64_t* __rest
       pbv[j] = i < n ? probs[i] : 0ull;
     }
     uint32_t wmask = 0, run = 0, tile_above = 0;
-    uint16_t wpos[WP_ITEMS];
 #pragma unroll
     for (int j = 0; j < WP_ITEMS; ++j) {
       const uint64_t pb = pbv[j];
@@ -286,9 +285,7 @@ __global__ void __launch_bounds__(WP_BLOCK) k_window_pass(const uint64_t* __rest
         win_m += f;
         wmask |= 1u << j;
       }
-      const uint32_t b = __ballot_sync(0xffffffffu, inwin);
-      wpos[j] = (uint16_t)(run + __popc(b & lt));
-      run += __popc(b);
+      run += __popc(__ballot_sync(0xffffffffu, inwin));
     }
     above_c += tile_above;
 #pragma unroll
@@ -311,10 +308,15 @@ __global__ void __launch_bounds__(WP_BLOCK) k_window_pass(const uint64_t* __rest
     }
     __syncthreads();
     const uint64_t wbase = s_base + s_warp[warp];
+    uint32_t wrun = 0;  // window positions: the same ballots again, in item order
 #pragma unroll
     for (int j = 0; j < WP_ITEMS; ++j) {
-      if ((wmask >> j) & 1u) {
-        const uint64_t o = wbase + wpos[j];
+      const bool inwin = (wmask >> j) & 1u;
+      const uint32_t b = __ballot_sync(0xffffffffu, inwin);
+      const uint32_t wpos = wrun + __popc(b & lt);
+      wrun += __popc(b);
+      if (inwin) {
+        const uint64_t o = wbase + wpos;
         const uint64_t i = L::index(base, j);
         if (o < cap) {
           wp[o] = pbv[j];
