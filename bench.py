@@ -147,7 +147,8 @@ def phase_model(ph: str, totals: dict, prec: str, passes: int):
     if ph == "keys":     # read key, write sort key + index
         return {"bytes": 20 * n_in, "flops": 0.0}
     if ph == "apply":    # read sorted key + index + amplitude per input; write key+amp+prob per candidate
-        return {"bytes": (12 + sa) * n_in + (16 + sa) * n_pre, "flops": totals["dfma"] * 2.0}
+        return {"bytes": (12 + sa) * totals["n_in_apply"] + (16 + sa) * totals["n_pre_apply"],
+                "flops": totals["fp64_apply"]}
     if ph == "window":   # one streaming pass over the probabilities (+ window keys)
         return {"bytes": 8 * n_pre, "flops": 0.0}
     if ph == "select":   # histogram levels over the window terms
@@ -159,7 +160,8 @@ def phase_model(ph: str, totals: dict, prec: str, passes: int):
     if ph == "heads":
         return {"bytes": 8 * n_in, "flops": 0.0}
     if ph == "local":    # read key + amplitude per input; write key + amp + prob per candidate
-        return {"bytes": (8 + sa) * n_in + (16 + sa) * n_pre, "flops": totals["dfma"] * 2.0}
+        return {"bytes": (8 + sa) * totals["n_in_local"] + (16 + sa) * totals["n_pre_local"],
+                "flops": totals["fp64_local"]}
     return {"bytes": 0.0, "flops": 0.0}
 
 
@@ -203,8 +205,11 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize(dev)
         barrier()
         st.set_timing(True)
-        totals = {"n_in": 0, "n_pre": 0, "n_kept": 0, "dfma": 0.0, "select_levels": 0, "steps": steps,
-                  "sort_passes": 0, "window_hits": 0, "window_terms": 0}
+        totals = {"n_in": 0, "n_pre": 0, "n_kept": 0, "select_levels": 0, "steps": steps,
+                  "sort_passes": 0, "window_hits": 0, "window_terms": 0,
+                  # per gate path: the sorted path (sort + group mat-vec) or the bucket-local kernel
+                  "n_in_apply": 0, "n_pre_apply": 0, "fp64_apply": 0.0,
+                  "n_in_local": 0, "n_pre_local": 0, "fp64_local": 0.0}
         clocks = ClockSampler(dev.index) if sample_clocks else None
         if clocks:
             clocks.start()
@@ -216,11 +221,23 @@ def run_ours(args, rank, world):
         for _ in range(steps):
             q, u = gates[gi % len(gates)]
             gi += 1
+            loc0 = st.stats()["local_gates"]
             st.apply_gate(q, u)
             s1 = st.stats()
             st.truncate()
             s2 = st.stats()
             st.peak()
+            path = "local" if s1["local_gates"] > loc0 else "apply"
+            totals["n_in_" + path] += s1["n_in"]
+            totals["n_pre_" + path] += s1["n_pre"]
+            # FP64 pipe work of the mat-vec kernel, counted as 2 flops per operation:
+            # complex128 runs 4 fused multiply-adds per (input, output) pair, and
+            # every candidate's probability is a multiply + fma (complex64 runs
+            # the mat-vec in FP32, so only the probabilities are FP64)
+            fp64_ops = 2.0 * s1["n_pre"]
+            if prec == sv.SV_C128:
+                fp64_ops += dense_dfma_per_gate(len(q), s1["n_in"])
+            totals["fp64_" + path] += 2.0 * fp64_ops
             totals["n_in"] += s1["n_in"]
             totals["n_pre"] += s1["n_pre"]
             totals["n_kept"] += s2["n_kept"]
@@ -228,7 +245,6 @@ def run_ours(args, rank, world):
             totals["select_levels"] += s2["select_levels"]
             totals["window_hits"] += s2["window_hits"]
             totals["window_terms"] += s2["window_terms"]
-            totals["dfma"] += dense_dfma_per_gate(len(q), s1["n_in"]) + 2.0 * s1["n_pre"] + 2.0 * s2["n_kept"]
         e1.record(stream)
         torch.cuda.synchronize(dev)
         launches = sv.sv_launch_count() - l0
@@ -516,7 +532,7 @@ def main():
         "gpu_launches": main_r["launches"],
         "clocks": main_r["clocks"],
         "peak_key": main_r["peak"][0],
-        "totals": {k: (int(v) if isinstance(v, (int, float)) and k != "dfma" else v) for k, v in tot.items()},
+        "totals": {k: (v if k.startswith("fp64") else int(v)) for k, v in tot.items()},
         "gate_paths": main_r.get("paths"),
     }
     if "c64" in res:

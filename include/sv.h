@@ -211,6 +211,16 @@ sv_status svb_peak(svb_state* b, int slot, uint64_t* key, double* prob);
  * order, min(cap, N) of them; *count = N. */
 sv_status svb_export(svb_state* b, int slot, uint64_t* keys, double* amps, uint64_t cap, uint64_t* count);
 const char* svb_last_error(const svb_state* b);
+/* Autotuning of the step's launch shapes (on by default): for every class of
+ * step (kernel, precision, widest gate of the step, floor(log2) of the term
+ * count) each candidate shape of the group mat-vec (groups per thread), the
+ * select scan and the compaction (blocks per SM) is timed twice on live steps
+ * with CUDA events, then the fastest is kept.  Every shape computes the same
+ * result.  Off: fixed default shapes. */
+sv_status svb_set_autotune(svb_state* b, int on);
+/* Timed trials so far, step classes seen, and classes whose every shape has
+ * been timed (the tuner has settled them). */
+sv_status svb_autotune_stats(const svb_state* b, uint64_t* trials, uint64_t* classes, uint64_t* settled);
 
 /* Peak readout that allocates nothing.  The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc where they need

@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(SA_BLOCK) k_seg_apply(
 }
 
 template <typename Real>
-void seg_apply_dispatch(int mmax, unsigned grid, cudaStream_t st, const uint64_t* sk, const uint32_t* sidx,
+void seg_apply_dispatch(int mmax, int gpt, unsigned grid, cudaStream_t st, const uint64_t* sk, const uint32_t* sidx,
                         uint64_t n, const uint32_t* heads, const void* amps_in, int shift, const SegGate* gates,
                         uint64_t* keys_out, void* amps_out, uint64_t* probs_out, uint16_t* seg_out,
                         uint64_t* lookback, uint64_t max_tiles, Ctl* ctl) {
@@ -294,39 +294,52 @@ void seg_apply_dispatch(int mmax, unsigned grid, cudaStream_t st, const uint64_t
 #define SV_SEG_APPLY(MAXD, GPT)                                                                         \
   k_seg_apply<Real, MAXD, GPT><<<grid, SA_BLOCK, 0, st>>>(sk, sidx, n, heads, ai, shift, gates, keys_out, ao, \
                                                           probs_out, seg_out, lookback, max_tiles, ctl)
-  switch (mmax) {
-    case 0: SV_SEG_APPLY(1, 4); break;
-    case 1: SV_SEG_APPLY(2, 4); break;
-    case 2: SV_SEG_APPLY(4, 2); break;
-    case 3: SV_SEG_APPLY(8, 1); break;
-    default: SV_SEG_APPLY(16, 1); break;
+  if (mmax <= 1) {
+    if (gpt == 1) SV_SEG_APPLY(2, 1);
+    else if (gpt == 2) SV_SEG_APPLY(2, 2);
+    else SV_SEG_APPLY(2, 4);
+  } else if (mmax == 2) {
+    if (gpt == 1) SV_SEG_APPLY(4, 1);
+    else if (gpt == 2) SV_SEG_APPLY(4, 2);
+    else SV_SEG_APPLY(4, 4);
+  } else if (mmax == 3) {
+    if (gpt == 1) SV_SEG_APPLY(8, 1);
+    else SV_SEG_APPLY(8, 2);
+  } else {
+    SV_SEG_APPLY(16, 1);
   }
 #undef SV_SEG_APPLY
 }
 
-// max_tiles bounds the look-back buffer: at least (n << mmax) / 1024 + 1,
-// which covers the ceil(groups / (256 * GPT)) tiles of every instantiation.
+int seg_apply_configs(int mmax) { return mmax <= 2 ? 3 : (mmax == 3 ? 2 : 1); }
+
+// cfg picks the groups per thread (1, 2 or 4 where the accumulators fit);
+// max_tiles bounds the look-back buffer: at least groups / 256 + 1, the tile
+// count of one group per thread.
 void launch_seg_apply(int prec, const uint64_t* sk, const uint32_t* sidx, uint64_t n, const uint32_t* heads,
                       const void* amps_in, int shift, int mmax, const SegGate* gates, uint64_t* keys_out,
                       void* amps_out, uint64_t* probs_out, uint16_t* seg_out, uint64_t* lookback, Ctl* ctl,
-                      uint64_t max_tiles, cudaStream_t st) {
+                      uint64_t max_tiles, int cfg, cudaStream_t st) {
   cudaMemsetAsync(lookback, 0, sizeof(uint64_t) * (max_tiles + 1), st);
   cudaMemsetAsync(&ctl->tile_counter[1], 0, sizeof(uint64_t), st);
   cudaMemsetAsync(&ctl->count[1], 0, sizeof(uint64_t), st);
   if (n == 0) return;
+  const int ncfg = seg_apply_configs(mmax);
+  const int gpt = 1 << (cfg < ncfg ? cfg : ncfg - 1);
   const uint64_t grid = max_tiles < 148 * 4 ? (max_tiles ? max_tiles : 1) : 148 * 4;
   if (prec == 0)
-    seg_apply_dispatch<double>(mmax, (unsigned)grid, st, sk, sidx, n, heads, amps_in, shift, gates, keys_out,
+    seg_apply_dispatch<double>(mmax, gpt, (unsigned)grid, st, sk, sidx, n, heads, amps_in, shift, gates, keys_out,
                                amps_out, probs_out, seg_out, lookback, max_tiles, ctl);
   else
-    seg_apply_dispatch<float>(mmax, (unsigned)grid, st, sk, sidx, n, heads, amps_in, shift, gates, keys_out,
+    seg_apply_dispatch<float>(mmax, gpt, (unsigned)grid, st, sk, sidx, n, heads, amps_in, shift, gates, keys_out,
                               amps_out, probs_out, seg_out, lookback, max_tiles, ctl);
 }
 
 // ---------------------------------------------------------------- segment bounds
 // Segments are contiguous: record where each one starts and ends.
-__global__ void k_seg_bounds(const uint16_t* __restrict__ seg, uint64_t n, uint64_t* __restrict__ start,
-                             uint64_t* __restrict__ end) {
+__global__ void k_seg_bounds(const uint16_t* __restrict__ seg, const uint64_t* __restrict__ n_dev,
+                             uint64_t* __restrict__ start, uint64_t* __restrict__ end) {
+  const uint64_t n = *n_dev;
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
        i += (uint64_t)gridDim.x * blockDim.x) {
     const uint16_t s = seg[i];
@@ -335,14 +348,11 @@ __global__ void k_seg_bounds(const uint16_t* __restrict__ seg, uint64_t n, uint6
   }
 }
 
-void launch_seg_bounds(const uint16_t* seg, uint64_t n, uint64_t* start, uint64_t* end, int slots,
+void launch_seg_bounds(const uint16_t* seg, const uint64_t* n_dev, uint64_t* start, uint64_t* end, int slots,
                        cudaStream_t st) {
   cudaMemsetAsync(start, 0, sizeof(uint64_t) * slots, st);
   cudaMemsetAsync(end, 0, sizeof(uint64_t) * slots, st);
-  if (n == 0) return;
-  uint64_t blocks = (n + 255) / 256;
-  if (blocks > 148 * 8) blocks = 148 * 8;
-  k_seg_bounds<<<(unsigned)blocks, 256, 0, st>>>(seg, n, start, end);
+  k_seg_bounds<<<148 * 8, 256, 0, st>>>(seg, n_dev, start, end);
 }
 
 // ---------------------------------------------------------------- segmented select
@@ -387,8 +397,9 @@ __device__ __forceinline__ u128 warp_sum_u128(u128 v) {
 
 __global__ void __launch_bounds__(SS_BLOCK) k_segsel_hist(const uint64_t* __restrict__ probs,
                                                           const uint64_t* __restrict__ keys,
-                                                          const uint16_t* __restrict__ seg, uint64_t n,
-                                                          uint64_t chunk, const SegSel* __restrict__ sel,
+                                                          const uint16_t* __restrict__ seg,
+                                                          const uint64_t* __restrict__ n_dev,
+                                                          const SegSel* __restrict__ sel,
                                                           uint32_t* __restrict__ g_cnt, uint64_t* __restrict__ g_sum,
                                                           uint64_t* __restrict__ g_buf, uint32_t* __restrict__ g_bufn,
                                                           uint32_t* err) {
@@ -396,6 +407,12 @@ __global__ void __launch_bounds__(SS_BLOCK) k_segsel_hist(const uint64_t* __rest
   __shared__ u128 s_part[2][SS_BLOCK / 32];
   __shared__ uint32_t s_seg;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // one contiguous chunk per block, whole multiples of a block's sweep
+  const uint64_t n = *n_dev;
+  const uint64_t sweep = (uint64_t)SS_BLOCK * SS_ILP;
+  uint64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  chunk = (chunk + sweep - 1) / sweep * sweep;
+  if (chunk < 4 * sweep) chunk = 4 * sweep;
   const uint64_t c0 = blockIdx.x * chunk;
   if (c0 >= n) return;
   const uint64_t c1 = c0 + chunk < n ? c0 + chunk : n;
@@ -570,23 +587,41 @@ __global__ void __launch_bounds__(256) k_segsel_pick(SegSel* __restrict__ sel, c
   }
 }
 
-void launch_segsel_level(const uint64_t* probs, const uint64_t* keys, const uint16_t* seg, uint64_t n, SegSel* sel,
-                         int slots, uint32_t* g_cnt, uint64_t* g_sum, uint64_t* g_buf, uint32_t* g_bufn,
-                         uint32_t* err, cudaStream_t st) {
+// cfg picks the scan's blocks per SM: 2, 4 or 8.
+void launch_segsel_level(const uint64_t* probs, const uint64_t* keys, const uint16_t* seg, const uint64_t* n_dev,
+                         SegSel* sel, int slots, uint32_t* g_cnt, uint64_t* g_sum, uint64_t* g_buf, uint32_t* g_bufn,
+                         uint32_t* err, int cfg, cudaStream_t st) {
   cudaMemsetAsync(g_cnt, 0, sizeof(uint32_t) * SS_BINS * slots, st);
   cudaMemsetAsync(g_sum, 0, sizeof(uint64_t) * 4 * slots, st);
   cudaMemsetAsync(g_bufn, 0, sizeof(uint32_t) * slots, st);
-  if (n > 0) {
-    // 4 blocks per SM, one contiguous chunk each (whole multiples of a block's sweep)
-    const uint64_t sweep = (uint64_t)SS_BLOCK * SS_ILP;
-    uint64_t chunk = (n + 148 * 4 - 1) / (148 * 4);
-    chunk = (chunk + sweep - 1) / sweep * sweep;
-    if (chunk < 4 * sweep) chunk = 4 * sweep;
-    const uint64_t grid = (n + chunk - 1) / chunk;
-    k_segsel_hist<<<(unsigned)grid, SS_BLOCK, 0, st>>>(probs, keys, seg, n, chunk, sel, g_cnt, g_sum, g_buf, g_bufn,
-                                                       err);
-  }
+  const unsigned grid = 148u * (2u << (cfg < 0 ? 0 : (cfg > 2 ? 2 : cfg)));
+  k_segsel_hist<<<grid, SS_BLOCK, 0, st>>>(probs, keys, seg, n_dev, sel, g_cnt, g_sum, g_buf, g_bufn, err);
   k_segsel_pick<<<slots, 256, 0, st>>>(sel, g_cnt);
+}
+
+// Select state of every slot for this step: a slot in use with more terms
+// than its K is truncated to its top K (Sec. III).
+__global__ void k_segsel_init(SegSel* __restrict__ sel, const SegGate* __restrict__ gates,
+                              const uint64_t* __restrict__ start, const uint64_t* __restrict__ end, int slots) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= slots) return;
+  SegSel st;
+  memset(&st, 0, sizeof(SegSel));
+  const uint64_t count = end[s] > start[s] ? end[s] - start[s] : 0;
+  const SegGate& g = gates[s];
+  if (g.m >= 0 && g.K > 0 && count > g.K) {
+    st.active = 1;
+    st.bits = 1;
+    st.prefix_hi = 1ull << 63;
+    st.target = g.K;
+    st.bin_count = count;  // a small segment is copied whole by the first scan
+  }
+  sel[s] = st;
+}
+
+void launch_segsel_init(SegSel* sel, const SegGate* gates, const uint64_t* start, const uint64_t* end, int slots,
+                        cudaStream_t st) {
+  k_segsel_init<<<(slots + 127) / 128, 128, 0, st>>>(sel, gates, start, end, slots);
 }
 
 // Finish: one block per segment collected in this level's scan resolves the
@@ -767,12 +802,17 @@ constexpr int SC_BLOCK = 256, SC_ITEMS = 8;
 template <typename C2>
 __global__ void __launch_bounds__(SC_BLOCK, 4) k_seg_truncate(
     const uint64_t* __restrict__ keys, const C2* __restrict__ amps, const uint64_t* __restrict__ probs,
-    const uint16_t* __restrict__ seg, uint64_t n, const SegSel* __restrict__ sel, uint64_t* __restrict__ keys_out,
-    C2* __restrict__ amps_out, uint64_t* __restrict__ probs_out, uint16_t* __restrict__ seg_out,
-    uint64_t* lookback, Ctl* ctl) {
+    const uint16_t* __restrict__ seg, const uint64_t* __restrict__ n_dev, uint64_t n_max,
+    const SegSel* __restrict__ sel, uint64_t* __restrict__ keys_out, C2* __restrict__ amps_out,
+    uint64_t* __restrict__ probs_out, uint16_t* __restrict__ seg_out, uint64_t* lookback, Ctl* ctl) {
   typedef TileLayout<SC_BLOCK, SC_ITEMS> L;
   __shared__ CompactShared<SC_BLOCK> cs;
   __shared__ uint64_t s_tile;
+  const uint64_t n = *n_dev;
+  if (n > n_max) {  // the look-back buffer was sized for n_max terms
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&ctl->err, ERR_INVARIANT);
+    return;
+  }
   const uint64_t tiles = (n + L::TILE - 1) / L::TILE;
   while (true) {
     if (threadIdx.x == 0) s_tile = atomicAdd((unsigned long long*)&ctl->tile_counter[2], 1ull);
@@ -844,21 +884,24 @@ __global__ void __launch_bounds__(SC_BLOCK, 4) k_seg_truncate(
 }
 
 void launch_seg_truncate(int prec, const uint64_t* keys, const void* amps, const uint64_t* probs, const uint16_t* seg,
-                         uint64_t n, const SegSel* sel, uint64_t* keys_out, void* amps_out, uint64_t* probs_out,
-                         uint16_t* seg_out, uint64_t* lookback, Ctl* ctl, cudaStream_t st) {
-  const uint64_t tiles = (n + SC_BLOCK * SC_ITEMS - 1) / (SC_BLOCK * SC_ITEMS);
+                         const uint64_t* n_dev, uint64_t n_max, const SegSel* sel, uint64_t* keys_out,
+                         void* amps_out, uint64_t* probs_out, uint16_t* seg_out, uint64_t* lookback, Ctl* ctl,
+                         int cfg, cudaStream_t st) {
+  const uint64_t tiles = (n_max + SC_BLOCK * SC_ITEMS - 1) / (SC_BLOCK * SC_ITEMS);
   cudaMemsetAsync(lookback, 0, sizeof(uint64_t) * (tiles + 1), st);
   cudaMemsetAsync(&ctl->tile_counter[2], 0, sizeof(uint64_t), st);
   cudaMemsetAsync(&ctl->count[2], 0, sizeof(uint64_t), st);
-  if (n == 0) return;
-  const uint64_t grid = tiles < 148 * 8 ? tiles : 148 * 8;
+  if (n_max == 0) return;
+  // cfg picks the persistent blocks per SM: 4 or 8
+  const uint64_t per_sm = cfg == 0 ? 4 : 8;
+  const uint64_t grid = tiles < 148 * per_sm ? tiles : 148 * per_sm;
   if (prec == 0)
-    k_seg_truncate<double2><<<(unsigned)grid, SC_BLOCK, 0, st>>>(keys, (const double2*)amps, probs, seg, n, sel,
-                                                                 keys_out, (double2*)amps_out, probs_out, seg_out,
-                                                                 lookback, ctl);
+    k_seg_truncate<double2><<<(unsigned)grid, SC_BLOCK, 0, st>>>(keys, (const double2*)amps, probs, seg, n_dev, n_max,
+                                                                 sel, keys_out, (double2*)amps_out, probs_out,
+                                                                 seg_out, lookback, ctl);
   else
-    k_seg_truncate<float2><<<(unsigned)grid, SC_BLOCK, 0, st>>>(keys, (const float2*)amps, probs, seg, n, sel,
-                                                                keys_out, (float2*)amps_out, probs_out, seg_out,
+    k_seg_truncate<float2><<<(unsigned)grid, SC_BLOCK, 0, st>>>(keys, (const float2*)amps, probs, seg, n_dev, n_max,
+                                                                sel, keys_out, (float2*)amps_out, probs_out, seg_out,
                                                                 lookback, ctl);
 }
 

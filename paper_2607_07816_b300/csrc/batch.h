@@ -11,6 +11,7 @@ namespace sv {
 // gate bits are squeezed out at the ascending positions qs and r gathers
 // bit q[t] of the key into bit t.
 struct SegGate {
+  uint64_t K;  // top-k limit of the slot (0: slot not in use)
   int m;
   int q[4];   // gate order (bit t of r)
   int qs[4];  // the same qubits ascending
@@ -56,22 +57,33 @@ void launch_seg_keys(const uint64_t* keys, const uint16_t* seg, uint64_t n, cons
                      uint64_t* sk, uint32_t* sidx, uint32_t* hist, int passes, cudaStream_t st);
 void launch_seg_heads(const uint64_t* sk, uint64_t n, int shift, const SegGate* gates, uint32_t* heads,
                       uint64_t* lookback, Ctl* ctl, cudaStream_t st);
+// Launch shapes that the batched step tunes (every shape gives the same
+// result): the mat-vec's groups per thread, the select scan's and the
+// compaction's blocks per SM.
+int seg_apply_configs(int mmax);
+constexpr int SEGSEL_CONFIGS = 3;
+constexpr int SEGTRUNC_CONFIGS = 2;
 void launch_seg_apply(int prec, const uint64_t* sk, const uint32_t* sidx, uint64_t n, const uint32_t* heads,
                       const void* amps_in, int shift, int mmax, const SegGate* gates, uint64_t* keys_out,
                       void* amps_out, uint64_t* probs_out, uint16_t* seg_out, uint64_t* lookback, Ctl* ctl,
-                      uint64_t max_tiles, cudaStream_t st);
-void launch_seg_bounds(const uint16_t* seg, uint64_t n, uint64_t* start, uint64_t* end, int slots,
+                      uint64_t max_tiles, int cfg, cudaStream_t st);
+// Sizes marked n_dev are read on the device (a term count written by an
+// earlier kernel on the stream); launches are sized for at most n_max terms.
+void launch_seg_bounds(const uint16_t* seg, const uint64_t* n_dev, uint64_t* start, uint64_t* end, int slots,
                        cudaStream_t st);
+void launch_segsel_init(SegSel* sel, const SegGate* gates, const uint64_t* start, const uint64_t* end, int slots,
+                        cudaStream_t st);
 constexpr int SEGSEL_CAP = 4096;  // terms per segment copied for the finish kernel
-void launch_segsel_level(const uint64_t* probs, const uint64_t* keys, const uint16_t* seg, uint64_t n, SegSel* sel,
-                         int slots, uint32_t* g_cnt, uint64_t* g_sum, uint64_t* g_buf, uint32_t* g_bufn,
-                         uint32_t* err, cudaStream_t st);
+void launch_segsel_level(const uint64_t* probs, const uint64_t* keys, const uint16_t* seg, const uint64_t* n_dev,
+                         SegSel* sel, int slots, uint32_t* g_cnt, uint64_t* g_sum, uint64_t* g_buf, uint32_t* g_bufn,
+                         uint32_t* err, int cfg, cudaStream_t st);
 void launch_segsel_finish(const uint64_t* g_buf, const uint32_t* g_bufn, const uint64_t* g_sum, SegSel* sel,
                           int slots, uint32_t* err, cudaStream_t st);
 void launch_segsel_scale(SegSel* sel, int slots, cudaStream_t st);
 void launch_seg_truncate(int prec, const uint64_t* keys, const void* amps, const uint64_t* probs, const uint16_t* seg,
-                         uint64_t n, const SegSel* sel, uint64_t* keys_out, void* amps_out, uint64_t* probs_out,
-                         uint16_t* seg_out, uint64_t* lookback, Ctl* ctl, cudaStream_t st);
+                         const uint64_t* n_dev, uint64_t n_max, const SegSel* sel, uint64_t* keys_out,
+                         void* amps_out, uint64_t* probs_out, uint16_t* seg_out, uint64_t* lookback, Ctl* ctl,
+                         int cfg, cudaStream_t st);
 void launch_seg_append(uint64_t* keys, void* amps, uint64_t* probs, uint16_t* seg, uint64_t at, int slot, int prec,
                        cudaStream_t st);
 

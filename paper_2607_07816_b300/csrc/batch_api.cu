@@ -3,6 +3,7 @@
 // per step with per-circuit top-k truncation (Sec. III) after every step.
 #include <algorithm>
 #include <cstdio>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -69,6 +70,18 @@ struct svb_state {
   std::string err;
   bool broken = false;
   uint64_t steps = 0;
+
+  // autotuner: per (kernel, precision, widest gate, size class) the launch
+  // shape of each tuned kernel, chosen by timing every shape twice on live
+  // steps of that class (any shape gives the same result)
+  bool autotune = true;
+  struct TuneEntry {
+    std::vector<float> ms;  // [2 * shapes], -1 = not timed yet
+    int best = -1;
+  };
+  std::map<uint64_t, TuneEntry> tune;
+  uint64_t tune_trials = 0;
+  cudaEvent_t tev[3][2] = {};
 };
 
 namespace {
@@ -196,20 +209,42 @@ sv_status b_sort_cap(svb_state* b, uint64_t need) {
   return b_lookback(b, sort_tiles(need) * RADIX + 16);
 }
 
-// Per-slot offsets and counts from the segment bounds of the current buffer.
-sv_status b_read_bounds(svb_state* b, uint64_t n) {
-  launch_seg_bounds(b->seg[b->cur], n, b->bounds_dev, b->bounds_dev + b->max_slots, b->max_slots, b->st);
-  cudaMemcpyAsync(b->bounds_host, b->bounds_dev, sizeof(uint64_t) * 2 * b->max_slots, cudaMemcpyDeviceToHost, b->st);
-  sv_status rc = b_cuda(b, cudaStreamSynchronize(b->st), "segment bounds");
-  if (rc != SV_OK) return rc;
-  for (int s = 0; s < b->max_slots; ++s) {
-    Slot& sl = b->slots[s];
-    if (sl.state != SLOT_USED) continue;
-    const uint64_t a = b->bounds_host[s], e = b->bounds_host[b->max_slots + s];
-    sl.offset = a;
-    sl.count = e > a ? e - a : 0;
+enum TuneKernel { TK_APPLY = 0, TK_SELECT = 1, TK_TRUNC = 2 };
+
+uint64_t tune_key(int kernel, int prec, int mmax, uint64_t n) {
+  const int sclass = n ? 63 - __builtin_clzll(n) : 0;
+  return ((uint64_t)kernel << 24) | ((uint64_t)prec << 16) | ((uint64_t)mmax << 8) | (uint64_t)sclass;
+}
+
+// The shape to run: the first one not yet timed twice, else the fastest.
+int tune_pick(svb_state* b, uint64_t key, int shapes, int dflt) {
+  if (!b->autotune || shapes <= 1) return dflt;
+  svb_state::TuneEntry& e = b->tune[key];
+  if (e.ms.empty()) e.ms.assign(2 * shapes, -1.f);
+  for (int i = 0; i < 2 * shapes; ++i)
+    if (e.ms[i] < 0.f) return i % shapes;
+  if (e.best < 0) {
+    float best = 0.f;
+    for (int c = 0; c < shapes; ++c) {
+      const float t = std::min(e.ms[c], e.ms[c + shapes]);
+      if (e.best < 0 || t < best) {
+        e.best = c;
+        best = t;
+      }
+    }
   }
-  return SV_OK;
+  return e.best;
+}
+
+void tune_record(svb_state* b, uint64_t key, int shapes, int shape, float ms) {
+  if (!b->autotune || shapes <= 1) return;
+  svb_state::TuneEntry& e = b->tune[key];
+  for (int i = 0; i < (int)e.ms.size(); ++i)
+    if (e.ms[i] < 0.f && i % shapes == shape) {
+      e.ms[i] = ms;
+      ++b->tune_trials;
+      return;
+    }
 }
 
 #define SVB_GUARD(b)                                                                                   \
@@ -259,6 +294,9 @@ sv_status svb_create(int max_slots, int prec, void* cuda_stream, const sv_alloca
                       cudaMallocHost(&b->sel_host, sizeof(SegSel) * max_slots) != cudaSuccess ||
                       cudaMallocHost(&b->bounds_host, sizeof(uint64_t) * 2 * max_slots) != cudaSuccess))
     rc = SV_E_CUDA;
+  for (int k = 0; k < 3 && rc == SV_OK; ++k)
+    for (int j = 0; j < 2 && rc == SV_OK; ++j)
+      if (cudaEventCreate(&b->tev[k][j]) != cudaSuccess) rc = SV_E_CUDA;
   if (rc == SV_OK) rc = b_state_cap(b, 4096);
   if (rc == SV_OK) rc = b_sort_cap(b, 4096);
   if (rc == SV_OK) rc = b_cuda(b, cudaMemsetAsync(b->ctl, 0, sizeof(Ctl), b->st), "svb_create");
@@ -294,6 +332,9 @@ sv_status svb_destroy(svb_state* b) {
   b_free(b, b->sel_buf);
   b_free(b, b->sel_bufn);
   b_free(b, b->bounds_dev);
+  for (int k = 0; k < 3; ++k)
+    for (int j = 0; j < 2; ++j)
+      if (b->tev[k][j]) cudaEventDestroy(b->tev[k][j]);
   if (b->hist_host) cudaFreeHost(b->hist_host);
   if (b->ctl_host) cudaFreeHost(b->ctl_host);
   if (b->gates_host) cudaFreeHost(b->gates_host);
@@ -371,21 +412,28 @@ sv_status svb_step(svb_state* b, const svb_gate* gates, int count) {
   }
   int top = 0, maxn = 1, mmax = 0;
   uint64_t removed = 0;
+  bool may_truncate = false;
   for (int s = 0; s < b->max_slots; ++s) {
     const Slot& sl = b->slots[s];
     SegGate& gt = b->gates_host[s];
     if (sl.state == SLOT_FREE) {
       gt.m = -1;
+      gt.K = 0;
       continue;
     }
     top = s + 1;
     if (sl.state == SLOT_REMOVING) {
       gt.m = -1;
+      gt.K = 0;
       removed += sl.count;
       continue;
     }
     maxn = sl.n > maxn ? sl.n : maxn;
     std::memset(&gt, 0, sizeof(SegGate));
+    gt.K = sl.K;
+    // a slot can exceed its K after this step only if its count times the
+    // gate's expansion does
+    if ((sl.count << (listed[s] >= 0 ? gates[listed[s]].m : 0)) > sl.K) may_truncate = true;
     if (listed[s] < 0) {
       gt.m = 0;
       gt.re_nz[0] = 1;
@@ -425,21 +473,20 @@ sv_status svb_step(svb_state* b, const svb_gate* gates, int count) {
   const int nbits = shift + segbits;
   sv_status rc = b_state_cap(b, nkeep << mmax > N ? nkeep << mmax : N);
   if (rc == SV_OK) rc = b_sort_cap(b, N);
-  const uint64_t apply_tiles = ((nkeep << mmax) + 1023) / 1024 + 1;
+  const uint64_t apply_tiles = nkeep / 256 + 2;  // one group per thread: the most tiles of any shape
   if (rc == SV_OK) rc = b_lookback(b, apply_tiles + 16);
   if (rc != SV_OK) return rc;
   rc = b_cuda(b, cudaMemcpyAsync(b->gates_dev, b->gates_host, sizeof(SegGate) * top, cudaMemcpyHostToDevice, b->st),
               "svb_step gate upload");
   if (rc != SV_OK) return rc;
+  // The step is enqueued with device-side term counts; the host waits twice:
+  // once to confirm every segment's cut is resolved, once for the new counts.
   const int passes = (nbits + RADIX_BITS - 1) / RADIX_BITS;
   launch_seg_keys(b->keys[b->cur], b->seg[b->cur], N, b->gates_dev, shift, b->sk[0], b->sidx[0], b->hist, passes,
                   b->st);
-  cudaMemcpyAsync(b->hist_host, b->hist, sizeof(uint32_t) * MAX_PASSES * RADIX, cudaMemcpyDeviceToHost, b->st);
-  rc = b_cuda(b, cudaStreamSynchronize(b->st), "svb_step keys");
-  if (rc != SV_OK) return rc;
   SortScratch sc;
   sc.hist = b->hist;
-  sc.hist_host = b->hist_host;
+  sc.hist_host = nullptr;  // every pass runs (no read-back of the digit counts)
   sc.lookback = b->lookback;
   sc.lookback_tiles = b->lb_entries / RADIX;
   sc.tile_counter = b->tile_counter;
@@ -451,78 +498,124 @@ sv_status svb_step(svb_state* b, const svb_gate* gates, int count) {
   if (rc != SV_OK) return rc;
   const int alt = 1 - b->cur;
   launch_seg_heads(b->sk[w], nkeep, shift, b->gates_dev, b->heads, b->lookback, b->ctl, b->st);
+  const uint64_t key_apply = tune_key(TK_APPLY, b->prec, mmax, nkeep);
+  const int n_apply = seg_apply_configs(mmax);
+  const int cfg_apply = tune_pick(b, key_apply, n_apply, mmax == 2 ? 1 : 0);
+  cudaEventRecord(b->tev[TK_APPLY][0], b->st);
   launch_seg_apply(b->prec, b->sk[w], b->sidx[w], nkeep, b->heads, b->amps[b->cur], shift, mmax, b->gates_dev,
-                   b->keys[alt], b->amps[alt], b->probs[alt], b->seg[alt], b->lookback, b->ctl, apply_tiles, b->st);
-  rc = b_sync_ctl(b, "svb_step apply");
-  if (rc != SV_OK) return rc;
+                   b->keys[alt], b->amps[alt], b->probs[alt], b->seg[alt], b->lookback, b->ctl, apply_tiles,
+                   cfg_apply, b->st);
+  cudaEventRecord(b->tev[TK_APPLY][1], b->st);
+  uint64_t* start_dev = b->bounds_dev;
+  uint64_t* end_dev = b->bounds_dev + b->max_slots;
+  launch_seg_bounds(b->seg[alt], &b->ctl->count[1], start_dev, end_dev, top, b->st);
   for (int s = 0; s < b->max_slots; ++s)
     if (b->slots[s].state == SLOT_REMOVING) b->slots[s] = Slot();
   b->cur = alt;
-  b->N = b->ctl_host->count[1];
-  rc = b_read_bounds(b, b->N);
-  if (rc != SV_OK) return rc;
-
-  // ---- per-segment top-k
-  int ntrunc = 0;
-  for (int s = 0; s < top; ++s) {
-    SegSel& st = b->sel_host[s];
-    std::memset(&st, 0, sizeof(SegSel));
-    const Slot& sl = b->slots[s];
-    if (sl.state == SLOT_USED && sl.count > sl.K) {
-      st.active = 1;
-      st.bits = 1;
-      st.prefix_hi = 1ull << 63;
-      st.target = sl.K;
-      st.bin_count = sl.count;  // a small segment is copied whole by the first scan
-      ++ntrunc;
+  const uint64_t n_cand = nkeep << mmax;  // the most candidates the mat-vec can emit
+  const uint64_t* n_dev = &b->ctl->count[1];
+  bool truncated = false;
+  const uint64_t key_sel = tune_key(TK_SELECT, b->prec, mmax, n_cand);
+  const uint64_t key_trunc = tune_key(TK_TRUNC, b->prec, mmax, n_cand);
+  int cfg_sel = -1, cfg_trunc = -1;
+  if (may_truncate) {
+    // ---- per-segment top-k: three levels normally resolve every cut
+    // (exponent bin, top mantissa bin, the copied bin); the host checks then
+    // and runs further levels only when a segment is still open
+    launch_segsel_init(b->sel_dev, b->gates_dev, start_dev, end_dev, top, b->st);
+    cfg_sel = tune_pick(b, key_sel, SEGSEL_CONFIGS, 1);
+    cudaEventRecord(b->tev[TK_SELECT][0], b->st);
+    bool all_done = false;
+    for (int level = 0; level < 16 && !all_done; ++level) {
+      launch_segsel_level(b->probs[b->cur], b->keys[b->cur], b->seg[b->cur], n_dev, b->sel_dev, top, b->sel_cnt,
+                          b->sel_mass, b->sel_buf, b->sel_bufn, &b->ctl->err, cfg_sel, b->st);
+      launch_segsel_finish(b->sel_buf, b->sel_bufn, b->sel_mass, b->sel_dev, top, &b->ctl->err, b->st);
+      if (level == 2) cudaEventRecord(b->tev[TK_SELECT][1], b->st);
+      if (level < 2) continue;
+      cudaMemcpyAsync(b->sel_host, b->sel_dev, sizeof(SegSel) * top, cudaMemcpyDeviceToHost, b->st);
+      rc = b_sync_ctl(b, "svb_step select");
+      if (rc != SV_OK) return rc;
+      all_done = true;
+      for (int s = 0; s < top; ++s)
+        if (b->sel_host[s].active && !b->sel_host[s].done) all_done = false;
     }
-  }
-  if (ntrunc == 0) return SV_OK;
-  rc = b_cuda(b, cudaMemcpyAsync(b->sel_dev, b->sel_host, sizeof(SegSel) * top, cudaMemcpyHostToDevice, b->st),
-              "svb_step select upload");
-  if (rc != SV_OK) return rc;
-  const uint64_t NP = b->N;
-  // Levels run without a host round trip in between (resolved segments cost
-  // nothing in later levels); the host checks after the third level, by
-  // which point a segment is normally resolved (exponent bin, top mantissa
-  // bin, then the copied bin), and then after every further level.
-  bool all_done = false;
-  for (int level = 0; level < 16 && !all_done; ++level) {
-    launch_segsel_level(b->probs[b->cur], b->keys[b->cur], b->seg[b->cur], NP, b->sel_dev, top, b->sel_cnt,
-                        b->sel_mass, b->sel_buf, b->sel_bufn, &b->ctl->err, b->st);
-    launch_segsel_finish(b->sel_buf, b->sel_bufn, b->sel_mass, b->sel_dev, top, &b->ctl->err, b->st);
-    if (level < 2) continue;
-    cudaMemcpyAsync(b->sel_host, b->sel_dev, sizeof(SegSel) * top, cudaMemcpyDeviceToHost, b->st);
-    rc = b_sync_ctl(b, "svb_step select");
-    if (rc != SV_OK) return rc;
-    all_done = true;
+    if (!all_done) {
+      b->broken = true;
+      return b_fail(b, SV_E_STATE, "svb_step: segmented select did not resolve");
+    }
+    truncated = false;
     for (int s = 0; s < top; ++s)
-      if (b->sel_host[s].active && !b->sel_host[s].done) all_done = false;
+      if (b->sel_host[s].active && b->sel_host[s].done == 1) truncated = true;
   }
-  if (!all_done) {
-    b->broken = true;
-    return b_fail(b, SV_E_STATE, "svb_step: segmented select did not resolve");
+  if (truncated) {
+    launch_segsel_scale(b->sel_dev, top, b->st);
+    rc = b_lookback(b, n_cand / 2048 + 16);
+    if (rc != SV_OK) return rc;
+    const int alt2 = 1 - b->cur;
+    cfg_trunc = tune_pick(b, key_trunc, SEGTRUNC_CONFIGS, 1);
+    cudaEventRecord(b->tev[TK_TRUNC][0], b->st);
+    launch_seg_truncate(b->prec, b->keys[b->cur], b->amps[b->cur], b->probs[b->cur], b->seg[b->cur], n_dev, n_cand,
+                        b->sel_dev, b->keys[alt2], b->amps[alt2], b->probs[alt2], b->seg[alt2], b->lookback, b->ctl,
+                        cfg_trunc, b->st);
+    cudaEventRecord(b->tev[TK_TRUNC][1], b->st);
+    b->cur = alt2;
+    n_dev = &b->ctl->count[2];
+    launch_seg_bounds(b->seg[b->cur], n_dev, start_dev, end_dev, top, b->st);
   }
-  launch_segsel_scale(b->sel_dev, top, b->st);
-  rc = b_lookback(b, NP / 2048 + 16);
+  // ---- the new counts
+  cudaMemcpyAsync(b->bounds_host, b->bounds_dev, sizeof(uint64_t) * 2 * b->max_slots, cudaMemcpyDeviceToHost, b->st);
+  rc = b_sync_ctl(b, "svb_step");
   if (rc != SV_OK) return rc;
-  const int alt2 = 1 - b->cur;
-  launch_seg_truncate(b->prec, b->keys[b->cur], b->amps[b->cur], b->probs[b->cur], b->seg[b->cur], NP, b->sel_dev,
-                      b->keys[alt2], b->amps[alt2], b->probs[alt2], b->seg[alt2], b->lookback, b->ctl, b->st);
-  cudaMemcpyAsync(b->sel_host, b->sel_dev, sizeof(SegSel) * top, cudaMemcpyDeviceToHost, b->st);
-  rc = b_sync_ctl(b, "svb_step truncate");
-  if (rc != SV_OK) return rc;
-  b->cur = alt2;
-  b->N = b->ctl_host->count[2];
-  for (int s = 0; s < top; ++s) {
-    const SegSel& st = b->sel_host[s];
-    if (st.active && st.done == 1) {
-      const double Sc = u128_to_double(st.cut_mass_hi, st.cut_mass_lo);
-      const double SN = u128_to_double(st.total_mass_hi, st.total_mass_lo);
-      b->slots[s].F = b->slots[s].F * (Sc / SN);
+  b->N = truncated ? b->ctl_host->count[2] : b->ctl_host->count[1];
+  if (b->autotune) {  // the stream is idle: every recorded interval is complete
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, b->tev[TK_APPLY][0], b->tev[TK_APPLY][1]) == cudaSuccess)
+      tune_record(b, key_apply, n_apply, cfg_apply, ms);
+    if (cfg_sel >= 0 && cudaEventElapsedTime(&ms, b->tev[TK_SELECT][0], b->tev[TK_SELECT][1]) == cudaSuccess)
+      tune_record(b, key_sel, SEGSEL_CONFIGS, cfg_sel, ms);
+    if (cfg_trunc >= 0 && cudaEventElapsedTime(&ms, b->tev[TK_TRUNC][0], b->tev[TK_TRUNC][1]) == cudaSuccess)
+      tune_record(b, key_trunc, SEGTRUNC_CONFIGS, cfg_trunc, ms);
+    cudaGetLastError();
+  }
+  for (int s = 0; s < b->max_slots; ++s) {
+    Slot& sl = b->slots[s];
+    if (sl.state != SLOT_USED) continue;
+    if (s < top) {
+      const uint64_t a = b->bounds_host[s], e = b->bounds_host[b->max_slots + s];
+      sl.offset = a;
+      sl.count = e > a ? e - a : 0;
+    }
+    if (truncated && s < top) {
+      const SegSel& st = b->sel_host[s];
+      if (st.active && st.done == 1) {
+        const double Sc = u128_to_double(st.cut_mass_hi, st.cut_mass_lo);
+        const double SN = u128_to_double(st.total_mass_hi, st.total_mass_lo);
+        sl.F = sl.F * (Sc / SN);
+      }
     }
   }
-  return b_read_bounds(b, b->N);
+  return SV_OK;
+}
+
+sv_status svb_set_autotune(svb_state* b, int on) {
+  SVB_GUARD(b);
+  b->autotune = on != 0;
+  return SV_OK;
+}
+
+sv_status svb_autotune_stats(const svb_state* b, uint64_t* trials, uint64_t* classes, uint64_t* settled) {
+  if (!b || !trials || !classes || !settled) return SV_E_ARG;
+  *trials = b->tune_trials;
+  *classes = b->tune.size();
+  uint64_t done = 0;
+  for (const auto& kv : b->tune) {
+    bool all = !kv.second.ms.empty();
+    for (float t : kv.second.ms)
+      if (t < 0.f) all = false;
+    if (all) ++done;
+  }
+  *settled = done;
+  return SV_OK;
 }
 
 sv_status svb_num_terms(svb_state* b, int slot, uint64_t* N) {

@@ -169,12 +169,15 @@ int radix_sort_pairs(uint64_t* kA, uint32_t* vA, uint64_t* kB, uint32_t* vB, uin
   uint64_t tiles = sort_tiles(n);
   if (n > 1) {
     for (int p = 0; p < passes; ++p) {
-      // a pass whose digit is the same for every key is the identity
-      const uint32_t* hh = sc.hist_host + p * RADIX;
-      bool trivial = false;
-      for (int dgt = 0; dgt < RADIX; ++dgt)
-        if (hh[dgt] == n) trivial = true;
-      if (trivial) continue;
+      // a pass whose digit is the same for every key is the identity (known
+      // only when the caller read the histograms back: hist_host != NULL)
+      if (sc.hist_host) {
+        const uint32_t* hh = sc.hist_host + p * RADIX;
+        bool trivial = false;
+        for (int dgt = 0; dgt < RADIX; ++dgt)
+          if (hh[dgt] == n) trivial = true;
+        if (trivial) continue;
+      }
       if (tiles > sc.lookback_tiles) {
         *cerr = cudaErrorInvalidValue;
         return cur;

@@ -25,7 +25,8 @@ EXPORTED = ["sv_create", "sv_create_ex", "sv_destroy", "sv_apply_gate", "sv_trun
             "sv_probs", "sv_num_terms", "sv_retained_mass", "sv_export", "sv_load", "sv_last_error",
             "sv_last_stats", "sv_set_timing", "sv_phase_times", "sv_launch_count", "sv_transfer_bytes", "sv_peak_noalloc",
             "svb_create", "svb_destroy", "svb_add", "svb_remove", "svb_step", "svb_num_terms",
-            "svb_retained_mass", "svb_peak", "svb_export", "svb_last_error", "sv_selftest"]
+            "svb_retained_mass", "svb_peak", "svb_export", "svb_last_error", "svb_set_autotune",
+            "svb_autotune_stats", "sv_selftest"]
 PHASES = ["keys", "sort", "heads", "apply", "select", "compact", "peak", "other", "window", "local"]
 
 
@@ -126,6 +127,10 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.svb_export.argtypes = [vp, i32, vp, vp, u64, P(u64)]
     lib.svb_last_error.restype = ctypes.c_char_p
     lib.svb_last_error.argtypes = [vp]
+    lib.svb_set_autotune.restype = i32
+    lib.svb_set_autotune.argtypes = [vp, i32]
+    lib.svb_autotune_stats.restype = i32
+    lib.svb_autotune_stats.argtypes = [vp, P(u64), P(u64), P(u64)]
     lib.sv_peak_noalloc.restype = i32
     lib.sv_peak_noalloc.argtypes = [i32, vp, vp, u64, vp, P(u64), P(dbl)]
     lib.sv_selftest.restype = i32
@@ -418,6 +423,17 @@ def svb_last_error(h: int) -> str:
     return load_library().svb_last_error(ctypes.c_void_p(h)).decode()
 
 
+def svb_set_autotune(h: int, on: bool) -> None:
+    _bcheck(h, load_library().svb_set_autotune(ctypes.c_void_p(h), 1 if on else 0))
+
+
+def svb_autotune_stats(h: int):
+    t, c, d = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    _bcheck(h, load_library().svb_autotune_stats(ctypes.c_void_p(h), ctypes.byref(t), ctypes.byref(c),
+                                                 ctypes.byref(d)))
+    return {"trials": t.value, "classes": c.value, "settled": d.value}
+
+
 class Batch:
     """Many circuits advanced together (segmented state on the device)."""
 
@@ -456,3 +472,9 @@ class Batch:
 
     def export(self, slot: int):
         return svb_export(self.h, slot)
+
+    def set_autotune(self, on: bool) -> None:
+        svb_set_autotune(self.h, on)
+
+    def autotune_stats(self):
+        return svb_autotune_stats(self.h)

@@ -149,3 +149,29 @@ def test_batch_sort_key_bit_bound(sv):
     keys, _ = b.export(s)
     assert sorted(int(k) for k in keys) == [0, 1 << 55]
     b.close()
+
+
+def test_autotuned_shapes_give_identical_results(sv):
+    """The autotuner runs every candidate launch shape on live steps; the
+    result of every circuit must be the same as with the fixed shapes."""
+    rng = np.random.default_rng(71)
+    circs = _circuits(rng, 8)
+    out = []
+    for tune in (False, True):
+        b = sv.Batch(16, prec=1)
+        b.set_autotune(tune)
+        slots = [b.add(c.n, c.K) for c in circs]
+        longest = max(len(c.gates) for c in circs)
+        for g in range(longest):
+            b.step([(slots[j], *c.gates[g]) for j, c in enumerate(circs) if g < len(c.gates)])
+        res = [(b.export(s), b.peak(s), b.retained_mass(s)) for s in slots]
+        stats = b.autotune_stats()
+        b.close()
+        out.append(res)
+        if tune:
+            assert stats["trials"] > 0 and stats["classes"] > 0
+        else:
+            assert stats["trials"] == 0
+    for (ea, pa, fa), (eb, pb, fb) in zip(out[0], out[1]):
+        assert _as_dict(*ea) == _as_dict(*eb)
+        assert pa == pb and fa == fb
