@@ -771,14 +771,22 @@ __global__ void __launch_bounds__(256) k_segsel_finish(const uint64_t* __restric
   if (tid == 0) sel[blockIdx.x] = st;
 }
 
-void launch_segsel_finish(const uint64_t* g_buf, const uint32_t* g_bufn, const uint64_t* g_sum, SegSel* sel,
-                          int slots, uint32_t* err, cudaStream_t st) {
+// Kernel attributes (dynamic shared memory) set once, outside any stream
+// capture.
+void batch_prepare() {
   static bool attr_set = false;
-  const size_t smem = 2 * sizeof(uint64_t) * SF_CAP;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_segsel_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_segsel_finish, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(2 * sizeof(uint64_t) * SF_CAP));
     attr_set = true;
   }
+  sort_prepare();
+}
+
+void launch_segsel_finish(const uint64_t* g_buf, const uint32_t* g_bufn, const uint64_t* g_sum, SegSel* sel,
+                          int slots, uint32_t* err, cudaStream_t st) {
+  const size_t smem = 2 * sizeof(uint64_t) * SF_CAP;
+  batch_prepare();
   k_segsel_finish<<<slots, 256, smem, st>>>(g_buf, g_bufn, g_sum, sel, err);
 }
 

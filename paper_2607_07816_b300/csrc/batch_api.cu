@@ -2,6 +2,7 @@
 // each a segment of one device-resident state, advanced one gate per circuit
 // per step with per-circuit top-k truncation (Sec. III) after every step.
 #include <algorithm>
+#include <array>
 #include <cstdio>
 #include <map>
 #include <string>
@@ -82,6 +83,15 @@ struct svb_state {
   std::map<uint64_t, TuneEntry> tune;
   uint64_t tune_trials = 0;
   cudaEvent_t tev[3][2] = {};
+
+  // CUDA graphs of the two enqueued parts of a step, keyed by everything
+  // that is baked into the launches (sizes, shapes, buffer parity and the
+  // buffer generation, bumped by every reallocation)
+  bool own_stream = false;
+  bool graphs_on = true;
+  uint64_t gen = 0;
+  std::map<std::array<uint64_t, 12>, cudaGraphExec_t> graphs;
+  uint64_t graph_launches = 0, graph_captures = 0;
 };
 
 namespace {
@@ -139,6 +149,7 @@ sv_status b_lookback(svb_state* b, uint64_t entries) {
   b_free(b, b->lookback);
   b->lookback = p;
   b->lb_entries = want;
+  ++b->gen;
   return SV_OK;
 }
 
@@ -185,6 +196,7 @@ sv_status b_state_cap(svb_state* b, uint64_t need) {
   }
   b->cur = 0;
   b->cap = cap;
+  ++b->gen;
   return rc;
 }
 
@@ -205,6 +217,7 @@ sv_status b_sort_cap(svb_state* b, uint64_t need) {
       return b_fail(b, SV_E_NOMEM, "batch sort buffer allocation failed");
     }
     b->sort_cap = cap;
+    ++b->gen;
   }
   return b_lookback(b, sort_tiles(need) * RADIX + 16);
 }
@@ -234,6 +247,73 @@ int tune_pick(svb_state* b, uint64_t key, int shapes, int dflt) {
     }
   }
   return e.best;
+}
+
+bool tune_settled(svb_state* b, uint64_t key, int shapes) {
+  if (!b->autotune || shapes <= 1) return true;
+  auto it = b->tune.find(key);
+  if (it == b->tune.end() || it->second.ms.empty()) return false;
+  for (float t : it->second.ms)
+    if (t < 0.f) return false;
+  return true;
+}
+
+void drop_graphs(svb_state* b) {
+  for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+  b->graphs.clear();
+}
+
+// Enqueue one part of a step: replay its graph when one was captured under
+// the same key, else capture it now (the first time) or, with graphs off or
+// unavailable, enqueue the launches directly.
+template <typename F>
+sv_status run_part(svb_state* b, bool use_graph, const std::array<uint64_t, 12>& key, F&& enqueue) {
+  if (!(use_graph && b->graphs_on)) return enqueue();
+  auto it = b->graphs.find(key);
+  if (it == b->graphs.end()) {
+    if (b->graphs.size() >= 64) drop_graphs(b);
+    if (cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      b->graphs_on = false;
+      return enqueue();
+    }
+    const sv_status rc = enqueue();
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(b->st, &g);
+    cudaGraphExec_t x = nullptr;
+    if (rc != SV_OK || e != cudaSuccess || cudaGraphInstantiate(&x, g, 0) != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      b->graphs_on = false;  // run this and later steps without graphs
+      return rc != SV_OK ? rc : enqueue();
+    }
+    cudaGraphDestroy(g);
+    it = b->graphs.emplace(key, x).first;
+    ++b->graph_captures;
+  }
+  ++b->graph_launches;
+  if (cudaGraphLaunch(it->second, b->st) != cudaSuccess) {
+    cudaGetLastError();
+    return b_fail(b, SV_E_CUDA, "svb_step: graph launch failed");
+  }
+  return SV_OK;
+}
+
+// Wait for the stream and check the control block read back with it.
+sv_status b_wait(svb_state* b, const char* where) {
+  cudaError_t e = cudaStreamSynchronize(b->st);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  sv_status rc = b_cuda(b, e, where);
+  if (rc != SV_OK) return rc;
+  if (b->ctl_host->err & ERR_TIMEOUT) {
+    b->broken = true;
+    return b_fail(b, SV_E_TIMEOUT, std::string(where) + ": a bounded device wait ran out");
+  }
+  if (b->ctl_host->err & (ERR_MASS | ERR_INVARIANT)) {
+    b->broken = true;
+    return b_fail(b, SV_E_STATE, std::string(where) + ": device state error");
+  }
+  return SV_OK;
 }
 
 void tune_record(svb_state* b, uint64_t key, int shapes, int shape, float ms) {
@@ -267,6 +347,15 @@ sv_status svb_create(int max_slots, int prec, void* cuda_stream, const sv_alloca
   svb_state* b = new svb_state();
   b->prec = prec;
   b->st = (cudaStream_t)cuda_stream;
+  batch_prepare();
+  if (!b->st) {  // a stream of its own: the legacy default stream cannot be captured into graphs
+    if (cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      b->st = nullptr;
+    } else {
+      b->own_stream = true;
+    }
+  }
   b->amp_bytes = prec == SV_C128 ? 16 : 8;
   b->max_slots = max_slots;
   b->slots.resize(max_slots);
@@ -335,6 +424,8 @@ sv_status svb_destroy(svb_state* b) {
   for (int k = 0; k < 3; ++k)
     for (int j = 0; j < 2; ++j)
       if (b->tev[k][j]) cudaEventDestroy(b->tev[k][j]);
+  drop_graphs(b);
+  if (b->own_stream) cudaStreamDestroy(b->st);
   if (b->hist_host) cudaFreeHost(b->hist_host);
   if (b->ctl_host) cudaFreeHost(b->ctl_host);
   if (b->gates_host) cudaFreeHost(b->gates_host);
@@ -476,104 +567,131 @@ sv_status svb_step(svb_state* b, const svb_gate* gates, int count) {
   const uint64_t apply_tiles = nkeep / 256 + 2;  // one group per thread: the most tiles of any shape
   if (rc == SV_OK) rc = b_lookback(b, apply_tiles + 16);
   if (rc != SV_OK) return rc;
-  rc = b_cuda(b, cudaMemcpyAsync(b->gates_dev, b->gates_host, sizeof(SegGate) * top, cudaMemcpyHostToDevice, b->st),
-              "svb_step gate upload");
+  const uint64_t n_cand = nkeep << mmax;  // the most candidates the mat-vec can emit
+  if (may_truncate) rc = b_lookback(b, std::max(apply_tiles, n_cand / 2048 + 2) + 16);
   if (rc != SV_OK) return rc;
-  // The step is enqueued with device-side term counts; the host waits twice:
-  // once to confirm every segment's cut is resolved, once for the new counts.
+  // The step is enqueued with device-side term counts in two parts (each
+  // replayed as a CUDA graph once its shapes are settled); the host waits
+  // after each: to confirm every segment's cut is resolved, and for the new
+  // counts.
   const int passes = (nbits + RADIX_BITS - 1) / RADIX_BITS;
-  launch_seg_keys(b->keys[b->cur], b->seg[b->cur], N, b->gates_dev, shift, b->sk[0], b->sidx[0], b->hist, passes,
-                  b->st);
-  SortScratch sc;
-  sc.hist = b->hist;
-  sc.hist_host = nullptr;  // every pass runs (no read-back of the digit counts)
-  sc.lookback = b->lookback;
-  sc.lookback_tiles = b->lb_entries / RADIX;
-  sc.tile_counter = b->tile_counter;
-  sc.err = &b->ctl->err;
-  cudaError_t ce;
-  int run = 0;
-  const int w = radix_sort_pairs(b->sk[0], b->sidx[0], b->sk[1], b->sidx[1], N, nbits, sc, b->st, &run, &ce);
-  rc = b_cuda(b, ce, "svb_step sort");
-  if (rc != SV_OK) return rc;
   const int alt = 1 - b->cur;
-  launch_seg_heads(b->sk[w], nkeep, shift, b->gates_dev, b->heads, b->lookback, b->ctl, b->st);
-  const uint64_t key_apply = tune_key(TK_APPLY, b->prec, mmax, nkeep);
-  const int n_apply = seg_apply_configs(mmax);
-  const int cfg_apply = tune_pick(b, key_apply, n_apply, mmax == 2 ? 1 : 0);
-  cudaEventRecord(b->tev[TK_APPLY][0], b->st);
-  launch_seg_apply(b->prec, b->sk[w], b->sidx[w], nkeep, b->heads, b->amps[b->cur], shift, mmax, b->gates_dev,
-                   b->keys[alt], b->amps[alt], b->probs[alt], b->seg[alt], b->lookback, b->ctl, apply_tiles,
-                   cfg_apply, b->st);
-  cudaEventRecord(b->tev[TK_APPLY][1], b->st);
   uint64_t* start_dev = b->bounds_dev;
   uint64_t* end_dev = b->bounds_dev + b->max_slots;
-  launch_seg_bounds(b->seg[alt], &b->ctl->count[1], start_dev, end_dev, top, b->st);
+  const uint64_t key_apply = tune_key(TK_APPLY, b->prec, mmax, nkeep);
+  const uint64_t key_sel = tune_key(TK_SELECT, b->prec, mmax, n_cand);
+  const uint64_t key_trunc = tune_key(TK_TRUNC, b->prec, mmax, n_cand);
+  const int n_apply = seg_apply_configs(mmax);
+  const int cfg_apply = tune_pick(b, key_apply, n_apply, mmax == 2 ? 1 : 0);
+  const int cfg_sel = may_truncate ? tune_pick(b, key_sel, SEGSEL_CONFIGS, 1) : -1;
+  const int cfg_trunc = may_truncate ? tune_pick(b, key_trunc, SEGTRUNC_CONFIGS, 1) : -1;
+  const bool settled = tune_settled(b, key_apply, n_apply) &&
+                       (!may_truncate || (tune_settled(b, key_sel, SEGSEL_CONFIGS) &&
+                                          tune_settled(b, key_trunc, SEGTRUNC_CONFIGS)));
+  const bool timing = b->autotune && !settled;  // events only while shapes are explored
+  std::array<uint64_t, 12> key_a = {0, N, nkeep, (uint64_t)top, (uint64_t)shift, (uint64_t)nbits, (uint64_t)mmax,
+                                    (uint64_t)cfg_apply, (uint64_t)(cfg_sel + 1), (uint64_t)b->cur, b->gen,
+                                    (uint64_t)may_truncate};
+  rc = run_part(b, settled, key_a, [&]() -> sv_status {
+    cudaMemcpyAsync(b->gates_dev, b->gates_host, sizeof(SegGate) * top, cudaMemcpyHostToDevice, b->st);
+    launch_seg_keys(b->keys[b->cur], b->seg[b->cur], N, b->gates_dev, shift, b->sk[0], b->sidx[0], b->hist, passes,
+                    b->st);
+    SortScratch sc;
+    sc.hist = b->hist;
+    sc.hist_host = nullptr;  // every pass runs (no read-back of the digit counts)
+    sc.lookback = b->lookback;
+    sc.lookback_tiles = b->lb_entries / RADIX;
+    sc.tile_counter = b->tile_counter;
+    sc.err = &b->ctl->err;
+    cudaError_t ce;
+    int run = 0;
+    const int w = radix_sort_pairs(b->sk[0], b->sidx[0], b->sk[1], b->sidx[1], N, nbits, sc, b->st, &run, &ce);
+    if (ce != cudaSuccess) return b_cuda(b, ce, "svb_step sort");
+    launch_seg_heads(b->sk[w], nkeep, shift, b->gates_dev, b->heads, b->lookback, b->ctl, b->st);
+    if (timing) cudaEventRecord(b->tev[TK_APPLY][0], b->st);
+    launch_seg_apply(b->prec, b->sk[w], b->sidx[w], nkeep, b->heads, b->amps[b->cur], shift, mmax, b->gates_dev,
+                     b->keys[alt], b->amps[alt], b->probs[alt], b->seg[alt], b->lookback, b->ctl, apply_tiles,
+                     cfg_apply, b->st);
+    if (timing) cudaEventRecord(b->tev[TK_APPLY][1], b->st);
+    launch_seg_bounds(b->seg[alt], &b->ctl->count[1], start_dev, end_dev, top, b->st);
+    if (may_truncate) {
+      // per-segment top-k: three levels normally resolve every cut
+      // (exponent bin, top mantissa bin, the copied bin)
+      launch_segsel_init(b->sel_dev, b->gates_dev, start_dev, end_dev, top, b->st);
+      if (timing) cudaEventRecord(b->tev[TK_SELECT][0], b->st);
+      for (int level = 0; level < 3; ++level) {
+        launch_segsel_level(b->probs[alt], b->keys[alt], b->seg[alt], &b->ctl->count[1], b->sel_dev, top, b->sel_cnt,
+                            b->sel_mass, b->sel_buf, b->sel_bufn, &b->ctl->err, cfg_sel, b->st);
+        launch_segsel_finish(b->sel_buf, b->sel_bufn, b->sel_mass, b->sel_dev, top, &b->ctl->err, b->st);
+      }
+      if (timing) cudaEventRecord(b->tev[TK_SELECT][1], b->st);
+      cudaMemcpyAsync(b->sel_host, b->sel_dev, sizeof(SegSel) * top, cudaMemcpyDeviceToHost, b->st);
+    } else {
+      cudaMemcpyAsync(b->bounds_host, b->bounds_dev, sizeof(uint64_t) * 2 * b->max_slots, cudaMemcpyDeviceToHost,
+                      b->st);
+    }
+    cudaMemcpyAsync(b->ctl_host, b->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, b->st);
+    return SV_OK;
+  });
+  if (rc != SV_OK) return rc;
+  rc = b_wait(b, "svb_step");
+  if (rc != SV_OK) return rc;
   for (int s = 0; s < b->max_slots; ++s)
     if (b->slots[s].state == SLOT_REMOVING) b->slots[s] = Slot();
   b->cur = alt;
-  const uint64_t n_cand = nkeep << mmax;  // the most candidates the mat-vec can emit
-  const uint64_t* n_dev = &b->ctl->count[1];
   bool truncated = false;
-  const uint64_t key_sel = tune_key(TK_SELECT, b->prec, mmax, n_cand);
-  const uint64_t key_trunc = tune_key(TK_TRUNC, b->prec, mmax, n_cand);
-  int cfg_sel = -1, cfg_trunc = -1;
   if (may_truncate) {
-    // ---- per-segment top-k: three levels normally resolve every cut
-    // (exponent bin, top mantissa bin, the copied bin); the host checks then
-    // and runs further levels only when a segment is still open
-    launch_segsel_init(b->sel_dev, b->gates_dev, start_dev, end_dev, top, b->st);
-    cfg_sel = tune_pick(b, key_sel, SEGSEL_CONFIGS, 1);
-    cudaEventRecord(b->tev[TK_SELECT][0], b->st);
+    // rarely a cut needs more levels (long runs of equal probabilities)
     bool all_done = false;
-    for (int level = 0; level < 16 && !all_done; ++level) {
-      launch_segsel_level(b->probs[b->cur], b->keys[b->cur], b->seg[b->cur], n_dev, b->sel_dev, top, b->sel_cnt,
-                          b->sel_mass, b->sel_buf, b->sel_bufn, &b->ctl->err, cfg_sel, b->st);
-      launch_segsel_finish(b->sel_buf, b->sel_bufn, b->sel_mass, b->sel_dev, top, &b->ctl->err, b->st);
-      if (level == 2) cudaEventRecord(b->tev[TK_SELECT][1], b->st);
-      if (level < 2) continue;
-      cudaMemcpyAsync(b->sel_host, b->sel_dev, sizeof(SegSel) * top, cudaMemcpyDeviceToHost, b->st);
-      rc = b_sync_ctl(b, "svb_step select");
-      if (rc != SV_OK) return rc;
+    for (int extra = 0;; ++extra) {
       all_done = true;
       for (int s = 0; s < top; ++s)
         if (b->sel_host[s].active && !b->sel_host[s].done) all_done = false;
+      if (all_done || extra >= 13) break;
+      launch_segsel_level(b->probs[b->cur], b->keys[b->cur], b->seg[b->cur], &b->ctl->count[1], b->sel_dev, top,
+                          b->sel_cnt, b->sel_mass, b->sel_buf, b->sel_bufn, &b->ctl->err, cfg_sel, b->st);
+      launch_segsel_finish(b->sel_buf, b->sel_bufn, b->sel_mass, b->sel_dev, top, &b->ctl->err, b->st);
+      cudaMemcpyAsync(b->sel_host, b->sel_dev, sizeof(SegSel) * top, cudaMemcpyDeviceToHost, b->st);
+      rc = b_sync_ctl(b, "svb_step select");
+      if (rc != SV_OK) return rc;
     }
     if (!all_done) {
       b->broken = true;
       return b_fail(b, SV_E_STATE, "svb_step: segmented select did not resolve");
     }
-    truncated = false;
     for (int s = 0; s < top; ++s)
       if (b->sel_host[s].active && b->sel_host[s].done == 1) truncated = true;
-  }
-  if (truncated) {
-    launch_segsel_scale(b->sel_dev, top, b->st);
-    rc = b_lookback(b, n_cand / 2048 + 16);
-    if (rc != SV_OK) return rc;
     const int alt2 = 1 - b->cur;
-    cfg_trunc = tune_pick(b, key_trunc, SEGTRUNC_CONFIGS, 1);
-    cudaEventRecord(b->tev[TK_TRUNC][0], b->st);
-    launch_seg_truncate(b->prec, b->keys[b->cur], b->amps[b->cur], b->probs[b->cur], b->seg[b->cur], n_dev, n_cand,
-                        b->sel_dev, b->keys[alt2], b->amps[alt2], b->probs[alt2], b->seg[alt2], b->lookback, b->ctl,
-                        cfg_trunc, b->st);
-    cudaEventRecord(b->tev[TK_TRUNC][1], b->st);
-    b->cur = alt2;
-    n_dev = &b->ctl->count[2];
-    launch_seg_bounds(b->seg[b->cur], n_dev, start_dev, end_dev, top, b->st);
+    std::array<uint64_t, 12> key_b = {1, N, nkeep, (uint64_t)top, n_cand, (uint64_t)truncated, (uint64_t)mmax,
+                                      (uint64_t)cfg_trunc, 0, (uint64_t)b->cur, b->gen, 0};
+    rc = run_part(b, settled, key_b, [&]() -> sv_status {
+      if (truncated) {
+        launch_segsel_scale(b->sel_dev, top, b->st);
+        if (timing) cudaEventRecord(b->tev[TK_TRUNC][0], b->st);
+        launch_seg_truncate(b->prec, b->keys[b->cur], b->amps[b->cur], b->probs[b->cur], b->seg[b->cur],
+                            &b->ctl->count[1], n_cand, b->sel_dev, b->keys[alt2], b->amps[alt2], b->probs[alt2],
+                            b->seg[alt2], b->lookback, b->ctl, cfg_trunc, b->st);
+        if (timing) cudaEventRecord(b->tev[TK_TRUNC][1], b->st);
+        launch_seg_bounds(b->seg[alt2], &b->ctl->count[2], start_dev, end_dev, top, b->st);
+      }
+      cudaMemcpyAsync(b->bounds_host, b->bounds_dev, sizeof(uint64_t) * 2 * b->max_slots, cudaMemcpyDeviceToHost,
+                      b->st);
+      cudaMemcpyAsync(b->ctl_host, b->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, b->st);
+      return SV_OK;
+    });
+    if (rc != SV_OK) return rc;
+    rc = b_wait(b, "svb_step truncate");
+    if (rc != SV_OK) return rc;
+    if (truncated) b->cur = alt2;
   }
-  // ---- the new counts
-  cudaMemcpyAsync(b->bounds_host, b->bounds_dev, sizeof(uint64_t) * 2 * b->max_slots, cudaMemcpyDeviceToHost, b->st);
-  rc = b_sync_ctl(b, "svb_step");
-  if (rc != SV_OK) return rc;
   b->N = truncated ? b->ctl_host->count[2] : b->ctl_host->count[1];
-  if (b->autotune) {  // the stream is idle: every recorded interval is complete
+  if (timing) {  // the stream is idle: every recorded interval is complete
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, b->tev[TK_APPLY][0], b->tev[TK_APPLY][1]) == cudaSuccess)
       tune_record(b, key_apply, n_apply, cfg_apply, ms);
     if (cfg_sel >= 0 && cudaEventElapsedTime(&ms, b->tev[TK_SELECT][0], b->tev[TK_SELECT][1]) == cudaSuccess)
       tune_record(b, key_sel, SEGSEL_CONFIGS, cfg_sel, ms);
-    if (cfg_trunc >= 0 && cudaEventElapsedTime(&ms, b->tev[TK_TRUNC][0], b->tev[TK_TRUNC][1]) == cudaSuccess)
+    if (truncated && cudaEventElapsedTime(&ms, b->tev[TK_TRUNC][0], b->tev[TK_TRUNC][1]) == cudaSuccess)
       tune_record(b, key_trunc, SEGTRUNC_CONFIGS, cfg_trunc, ms);
     cudaGetLastError();
   }
@@ -600,6 +718,20 @@ sv_status svb_step(svb_state* b, const svb_gate* gates, int count) {
 sv_status svb_set_autotune(svb_state* b, int on) {
   SVB_GUARD(b);
   b->autotune = on != 0;
+  return SV_OK;
+}
+
+sv_status svb_set_graphs(svb_state* b, int on) {
+  SVB_GUARD(b);
+  b->graphs_on = on != 0;
+  if (!b->graphs_on) drop_graphs(b);
+  return SV_OK;
+}
+
+sv_status svb_graph_stats(const svb_state* b, uint64_t* captures, uint64_t* launches) {
+  if (!b || !captures || !launches) return SV_E_ARG;
+  *captures = b->graph_captures;
+  *launches = b->graph_launches;
   return SV_OK;
 }
 

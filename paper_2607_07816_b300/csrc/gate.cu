@@ -14,10 +14,12 @@
 
 namespace sv {
 
+// vbits > 0: the term index is packed below the sort key (sk = s << vbits |
+// i) and no index array is written.
 __global__ void __launch_bounds__(256) k_gate_keys(const uint64_t* __restrict__ keys, uint64_t n,
                                                    const BitPerm* __restrict__ perm,
                                                    uint64_t* __restrict__ sk, uint32_t* __restrict__ sidx,
-                                                   uint32_t* __restrict__ hist, int passes) {
+                                                   uint32_t* __restrict__ hist, int passes, int vbits) {
   __shared__ uint32_t sh[MAX_PASSES][RADIX];
   __shared__ uint64_t fwd[16][16];
   for (int i = threadIdx.x; i < MAX_PASSES * RADIX; i += blockDim.x) (&sh[0][0])[i] = 0;
@@ -26,8 +28,12 @@ __global__ void __launch_bounds__(256) k_gate_keys(const uint64_t* __restrict__ 
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
        i += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t s = permute_bits(fwd, keys[i]);
-    sk[i] = s;
-    sidx[i] = (uint32_t)i;
+    if (vbits) {
+      sk[i] = (s << vbits) | i;
+    } else {
+      sk[i] = s;
+      sidx[i] = (uint32_t)i;
+    }
     for (int p = 0; p < passes; ++p) atomicAdd(&sh[p][(s >> (RADIX_BITS * p)) & (RADIX - 1)], 1u);
   }
   __syncthreads();
@@ -43,14 +49,14 @@ void launch_gate_keys(const uint64_t* keys, uint64_t n, const GateParams& gp, ui
   if (n == 0) return;
   uint64_t blocks = (n + 255) / 256;
   if (blocks > 148 * 8) blocks = 148 * 8;
-  k_gate_keys<<<(unsigned)blocks, 256, 0, st>>>(keys, n, gp.perm, sk, sidx, hist, passes);
+  k_gate_keys<<<(unsigned)blocks, 256, 0, st>>>(keys, n, gp.perm, sk, sidx, hist, passes, gp.vbits);
 }
 
 // ------------------------------------------------------------------ heads
 constexpr int HEAD_BLOCK = 256, HEAD_ITEMS = 16;
 
 __global__ void __launch_bounds__(HEAD_BLOCK) k_group_heads(const uint64_t* __restrict__ sk, uint64_t n,
-                                                            int m, uint32_t* __restrict__ heads,
+                                                            int shift, uint32_t* __restrict__ heads,
                                                             uint64_t* lookback, Ctl* ctl) {
   typedef TileLayout<HEAD_BLOCK, HEAD_ITEMS> L;
   __shared__ CompactShared<HEAD_BLOCK> cs;
@@ -68,7 +74,7 @@ __global__ void __launch_bounds__(HEAD_BLOCK) k_group_heads(const uint64_t* __re
     for (int j = 0; j < HEAD_ITEMS; ++j) {
       uint64_t i = L::index(base, j);
       bool f = false;
-      if (i < n) f = (i == 0) || ((sk[i] >> m) != (sk[i - 1] >> m));
+      if (i < n) f = (i == 0) || ((sk[i] >> shift) != (sk[i - 1] >> shift));
       flag[j] = f;
     }
     tile_compact<HEAD_BLOCK, HEAD_ITEMS>(flag, pos, cs, lookback, tile, &ctl->err);
@@ -80,7 +86,8 @@ __global__ void __launch_bounds__(HEAD_BLOCK) k_group_heads(const uint64_t* __re
   }
 }
 
-void launch_group_heads(const uint64_t* sk, uint64_t n, int m, uint32_t* heads, uint64_t* lookback,
+// shift: sort-key bits below the group key (m, plus the packed index bits)
+void launch_group_heads(const uint64_t* sk, uint64_t n, int shift, uint32_t* heads, uint64_t* lookback,
                         Ctl* ctl, cudaStream_t st) {
   uint64_t tiles = (n + HEAD_BLOCK * HEAD_ITEMS - 1) / (HEAD_BLOCK * HEAD_ITEMS);
   cudaMemsetAsync(lookback, 0, sizeof(uint64_t) * (tiles + 1), st);
@@ -88,7 +95,7 @@ void launch_group_heads(const uint64_t* sk, uint64_t n, int m, uint32_t* heads, 
   cudaMemsetAsync(&ctl->count[0], 0, sizeof(uint64_t), st);
   if (n == 0) return;
   uint64_t grid = tiles < 148 * 4 ? tiles : 148 * 4;
-  k_group_heads<<<(unsigned)grid, HEAD_BLOCK, 0, st>>>(sk, n, m, heads, lookback, ctl);
+  k_group_heads<<<(unsigned)grid, HEAD_BLOCK, 0, st>>>(sk, n, shift, heads, lookback, ctl);
 }
 
 // ------------------------------------------------------------------ apply
@@ -173,16 +180,18 @@ __global__ void __launch_bounds__(APPLY_BLOCK, 4) k_gate_apply(
       if (threadIdx.x == 0) atomicOr(&ctl->err, ERR_INVARIANT);
       nm = APPLY_TILE;
     }
+    const int vb = gp.vbits;
     for (uint32_t k = threadIdx.x; k < ng; k += APPLY_BLOCK) {
       uint64_t h = heads[g0 + k];
       sm.head[k] = min((uint32_t)(h - mbase), nm);
-      sm.rest[k] = sk[h] >> m;
+      sm.rest[k] = sk[h] >> (m + vb);
     }
     if (threadIdx.x == 0) sm.head[ng] = nm;
     for (uint32_t k = threadIdx.x; k < nm; k += APPLY_BLOCK) {
-      uint64_t i = mbase + k;
-      sm.r[k] = (uint8_t)(sk[i] & dmask);
-      sm.x[k] = amps_in[sidx[i]];
+      const uint64_t i = mbase + k;
+      const uint64_t v = sk[i];
+      sm.r[k] = (uint8_t)((v >> vb) & dmask);
+      sm.x[k] = amps_in[vb ? (uint32_t)(v & ((1ull << vb) - 1ull)) : sidx[i]];
     }
     __syncthreads();
     for (uint32_t k = threadIdx.x; k < ng; k += APPLY_BLOCK) {

@@ -37,6 +37,12 @@ void launch_digit_hist(const uint64_t* k, uint64_t n, int nbits, uint32_t* hist,
 // hist_on_host).  Passes whose digit is constant over all keys are skipped.
 // The result lands in (kA, vA) when the return value is 0, in (kB, vB)
 // when it is 1.  *passes_run receives the number of scatter passes.
+// Keys-only LSD sort on the bits [lo, lo + nbits) of each key (bits below lo
+// ride along, e.g. a packed index); histograms in sc.hist are of the digits
+// of key >> lo.  Returns the buffer holding the result (0: kA, 1: kB).
+int radix_sort_keys(uint64_t* kA, uint64_t* kB, uint64_t n, int lo, int nbits, const SortScratch& sc,
+                    cudaStream_t st, int* passes_run, cudaError_t* cerr);
+void sort_prepare();
 int radix_sort_pairs(uint64_t* kA, uint32_t* vA, uint64_t* kB, uint32_t* vB, uint64_t n, int nbits,
                      const SortScratch& sc, cudaStream_t st, int* passes_run, cudaError_t* cerr);
 
@@ -64,6 +70,7 @@ struct GateParams {
   int n;               // qubits
   int tbits;           // number of bucket qubits (top bits of the sort key)
   uint64_t pmask;      // bucket qubits as a key mask
+  int vbits;           // > 0: sort keys carry the term index in their low vbits bits (no index array)
 };
 
 void launch_gate_keys(const uint64_t* keys, uint64_t n, const GateParams& gp, uint64_t* sk,
@@ -71,7 +78,7 @@ void launch_gate_keys(const uint64_t* keys, uint64_t n, const GateParams& gp, ui
 
 // Mark partner-group heads of the grouped sequence and compact their
 // positions; the group count lands in ctl->count[0].
-void launch_group_heads(const uint64_t* sk, uint64_t n, int m, uint32_t* heads, uint64_t* lookback,
+void launch_group_heads(const uint64_t* sk, uint64_t n, int shift, uint32_t* heads, uint64_t* lookback,
                         Ctl* ctl, cudaStream_t st);
 
 // Per-group mat-vec + zero drop; writes candidates and their probabilities,
@@ -96,6 +103,8 @@ void launch_local_gate(int prec, const uint64_t* keys, const void* amps, uint64_
                        uint64_t* keys_out, void* amps_out, uint64_t* probs_out, Ctl* ctl, cudaStream_t st);
 // Number of keys with each bit set (counts[0..63], device), for choosing
 // balanced bucket qubits.
+// Sample positions of the bit statistics for n keys (every *stride-th key).
+uint64_t bit_count_sample(uint64_t n, uint64_t* stride);
 void launch_bit_counts(const uint64_t* keys, uint64_t n, int nbits, uint64_t* counts, cudaStream_t st);
 // Exact size of the largest bucket (up to limit; longer: limit + 1) into
 // ctl->count[0].

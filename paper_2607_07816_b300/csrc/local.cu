@@ -434,7 +434,11 @@ void launch_bucket_check(const uint64_t* keys, uint64_t n, uint64_t pmask, uint6
 }
 
 // ---------------------------------------------------------------- bit statistics
-__global__ void __launch_bounds__(256) k_bit_counts(const uint64_t* __restrict__ keys, uint64_t n, int nbits,
+// One-counts of the key bits over the sample keys[0], keys[sample_step], ...
+// (n sample positions): bucket bits are chosen for balance, which a sample
+// of about a million keys measures well enough.
+__global__ void __launch_bounds__(256) k_bit_counts(const uint64_t* __restrict__ keys, uint64_t n,
+                                                    uint64_t sample_step, int nbits,
                                                     unsigned long long* __restrict__ counts) {
   __shared__ unsigned long long sc[64];
   if (threadIdx.x < 64) sc[threadIdx.x] = 0;
@@ -445,7 +449,7 @@ __global__ void __launch_bounds__(256) k_bit_counts(const uint64_t* __restrict__
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t nround = (n + stride - 1) / stride * stride;
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nround; i += stride) {
-    const uint64_t k = i < n ? keys[i] : 0ull;
+    const uint64_t k = i < n ? keys[i * sample_step] : 0ull;
     for (int b = 0; b < nbits; ++b) {
       const uint32_t c = __popc(__ballot_sync(0xffffffffu, (k >> b) & 1ull));
       if (b < 32) {
@@ -461,12 +465,19 @@ __global__ void __launch_bounds__(256) k_bit_counts(const uint64_t* __restrict__
   if (threadIdx.x < 64 && sc[threadIdx.x]) atomicAdd(&counts[threadIdx.x], sc[threadIdx.x]);
 }
 
+uint64_t bit_count_sample(uint64_t n, uint64_t* stride) {
+  *stride = n > (1ull << 20) ? n >> 20 : 1;
+  return (n + *stride - 1) / *stride;
+}
+
 void launch_bit_counts(const uint64_t* keys, uint64_t n, int nbits, uint64_t* counts, cudaStream_t st) {
   cudaMemsetAsync(counts, 0, sizeof(uint64_t) * 64, st);
   if (n == 0) return;
-  uint64_t blocks = (n + 255) / 256;
+  uint64_t stride;
+  const uint64_t ns = bit_count_sample(n, &stride);
+  uint64_t blocks = (ns + 255) / 256;
   if (blocks > 148 * 4) blocks = 148 * 4;
-  k_bit_counts<<<(unsigned)blocks, 256, 0, st>>>(keys, n, nbits, (unsigned long long*)counts);
+  k_bit_counts<<<(unsigned)blocks, 256, 0, st>>>(keys, ns, stride, nbits, (unsigned long long*)counts);
 }
 
 // ---------------------------------------------------------------- zero removal

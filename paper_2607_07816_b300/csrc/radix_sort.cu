@@ -65,7 +65,9 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* w
 // input order and the sort is stable.  Threads 0..255 then own one digit
 // each: exclusive offsets across warps, the tile-local digit offsets, and
 // the decoupled look-back over earlier tiles for the digit's global base.
-template <int BLOCK, int ITEMS>
+// PAIRS = false sorts keys alone (a key may carry its payload in the bits
+// below `shift`).
+template <int BLOCK, int ITEMS, bool PAIRS>
 __global__ void __launch_bounds__(BLOCK) k_onesweep(const uint64_t* __restrict__ kin,
                                                    const uint32_t* __restrict__ vin,
                                                    uint64_t* __restrict__ kout,
@@ -101,7 +103,7 @@ __global__ void __launch_bounds__(BLOCK) k_onesweep(const uint64_t* __restrict__
     uint64_t idx = base + (uint64_t)warp * 32 * ITEMS + i * 32 + lane;
     bool valid = idx < n;
     k[i] = valid ? kin[idx] : 0ull;
-    v[i] = valid ? vin[idx] : 0u;
+    v[i] = (PAIRS && valid) ? vin[idx] : 0u;
     d[i] = valid ? (uint32_t)((k[i] >> shift) & (RADIX - 1)) : (uint32_t)RADIX;
   }
 #pragma unroll
@@ -139,7 +141,7 @@ __global__ void __launch_bounds__(BLOCK) k_onesweep(const uint64_t* __restrict__
     if (d[i] < RADIX) {
       uint32_t pos = s_local[d[i]] + s_whist[warp][d[i]] + rank[i];
       s_keys[pos] = k[i];
-      s_vals[pos] = v[i];
+      if (PAIRS) s_vals[pos] = v[i];
     }
   }
   __syncthreads();
@@ -149,23 +151,31 @@ __global__ void __launch_bounds__(BLOCK) k_onesweep(const uint64_t* __restrict__
     uint32_t dd = (uint32_t)((key >> shift) & (RADIX - 1));
     uint64_t out = s_global[dd] + (j - s_local[dd]);
     kout[out] = key;
-    vout[out] = s_vals[j];
+    if (PAIRS) vout[out] = s_vals[j];
   }
 }
 
-static size_t onesweep_smem() { return (sizeof(uint64_t) + sizeof(uint32_t)) * SORT_TILE; }
+static size_t onesweep_smem(bool pairs) { return (sizeof(uint64_t) + (pairs ? sizeof(uint32_t) : 0)) * SORT_TILE; }
+
+// Kernel attributes (dynamic shared memory) set once, outside any stream
+// capture.
+void sort_prepare() {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_onesweep<SORT_THREADS, SORT_ITEMS, true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)onesweep_smem(true));
+    cudaFuncSetAttribute(k_onesweep<SORT_THREADS, SORT_ITEMS, false>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)onesweep_smem(false));
+    attr_set = true;
+  }
+}
 
 int radix_sort_pairs(uint64_t* kA, uint32_t* vA, uint64_t* kB, uint32_t* vB, uint64_t n, int nbits,
                      const SortScratch& sc, cudaStream_t st, int* passes_run, cudaError_t* cerr) {
   int passes = (nbits + RADIX_BITS - 1) / RADIX_BITS;
   int cur = 0, run = 0;
   *cerr = cudaSuccess;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_onesweep<SORT_THREADS, SORT_ITEMS>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)onesweep_smem());
-    attr_set = true;
-  }
+  sort_prepare();
   uint64_t tiles = sort_tiles(n);
   if (n > 1) {
     for (int p = 0; p < passes; ++p) {
@@ -188,8 +198,44 @@ int radix_sort_pairs(uint64_t* kA, uint32_t* vA, uint64_t* kB, uint32_t* vB, uin
       const uint32_t* vi = cur ? vB : vA;
       uint64_t* ko = cur ? kA : kB;
       uint32_t* vo = cur ? vA : vB;
-      k_onesweep<SORT_THREADS, SORT_ITEMS><<<(unsigned)tiles, SORT_THREADS, onesweep_smem(), st>>>(
+      k_onesweep<SORT_THREADS, SORT_ITEMS, true><<<(unsigned)tiles, SORT_THREADS, onesweep_smem(true), st>>>(
           ki, vi, ko, vo, n, RADIX_BITS * p, sc.hist + p * RADIX, sc.lookback, sc.tile_counter,
+          sc.err);
+      cur ^= 1;
+      ++run;
+    }
+  }
+  *passes_run = run;
+  *cerr = cudaGetLastError();
+  return cur;
+}
+
+int radix_sort_keys(uint64_t* kA, uint64_t* kB, uint64_t n, int lo, int nbits, const SortScratch& sc,
+                    cudaStream_t st, int* passes_run, cudaError_t* cerr) {
+  const int passes = (nbits + RADIX_BITS - 1) / RADIX_BITS;
+  int cur = 0, run = 0;
+  *cerr = cudaSuccess;
+  sort_prepare();
+  const uint64_t tiles = sort_tiles(n);
+  if (n > 1) {
+    for (int p = 0; p < passes; ++p) {
+      if (sc.hist_host) {  // a pass whose digit is the same for every key is the identity
+        const uint32_t* hh = sc.hist_host + p * RADIX;
+        bool trivial = false;
+        for (int dgt = 0; dgt < RADIX; ++dgt)
+          if (hh[dgt] == n) trivial = true;
+        if (trivial) continue;
+      }
+      if (tiles > sc.lookback_tiles) {
+        *cerr = cudaErrorInvalidValue;
+        return cur;
+      }
+      cudaMemsetAsync(sc.lookback, 0, sizeof(uint64_t) * RADIX * tiles, st);
+      cudaMemsetAsync(sc.tile_counter, 0, sizeof(uint64_t), st);
+      const uint64_t* ki = cur ? kB : kA;
+      uint64_t* ko = cur ? kA : kB;
+      k_onesweep<SORT_THREADS, SORT_ITEMS, false><<<(unsigned)tiles, SORT_THREADS, onesweep_smem(false), st>>>(
+          ki, nullptr, ko, nullptr, n, lo + RADIX_BITS * p, sc.hist + p * RADIX, sc.lookback, sc.tile_counter,
           sc.err);
       cur ^= 1;
       ++run;

@@ -279,6 +279,23 @@ sv_status sort_pairs(sv_state* s, uint64_t n, int nbits, bool hist_ready, int* w
   return cuda_check(s, e, "radix sort");
 }
 
+// Keys-only sort of s->sk[0] on the bits [lo, lo + nbits) (the histograms of
+// those digits are already in s->hist).
+sv_status sort_keys(sv_state* s, uint64_t n, int lo, int nbits, int* which, int* passes) {
+  cudaMemcpyAsync(s->hist_host, s->hist, sizeof(uint32_t) * MAX_PASSES * RADIX, cudaMemcpyDeviceToHost,
+                  s->st);
+  g_d2h += sizeof(uint32_t) * MAX_PASSES * RADIX;
+  sv_status rc = cuda_check(s, cudaStreamSynchronize(s->st), "digit histogram");
+  if (rc != SV_OK) return rc;
+  ph_collect(s);
+  cudaError_t e;
+  ph_begin(s, PH_SORT);
+  *which = radix_sort_keys(s->sk[0], s->sk[1], n, lo, nbits, sort_scratch(s), s->st, passes, &e);
+  ph_end(s, PH_SORT);
+  launched(s, PH_SORT, (uint64_t)*passes);
+  return cuda_check(s, e, "radix sort");
+}
+
 // Canonical order (probability descending, key ascending) of the current
 // state: the permutation ends in sidx[*which].
 sv_status canonical_perm(sv_state* s, int* which) {
@@ -581,20 +598,26 @@ sv_status sv_apply_gate(sv_state* s, int m, const int* qubits, const double* U) 
                                        cudaMemcpyDeviceToHost, s->st), "bit statistics");
     if (rc == SV_OK) rc = cuda_check(s, cudaStreamSynchronize(s->st), "bit statistics");
     if (rc != SV_OK) return rc;
-    choose_buckets(s, qmask, npre_max < s->K ? npre_max : (N > s->K ? N : s->K), s->bitcnt_host, N);
+    uint64_t stride;
+    const uint64_t n_sample = bit_count_sample(N, &stride);
+    choose_buckets(s, qmask, npre_max < s->K ? npre_max : (N > s->K ? N : s->K), s->bitcnt_host, n_sample);
     rc = upload_perm(s, gp);
     if (rc != SV_OK) return rc;
     const int passes = (s->n + RADIX_BITS - 1) / RADIX_BITS;
+    // pack the term index below the sort key when both fit in 64 bits
+    int vbits = 1;
+    while (vbits < 63 && (N - 1) >> vbits) ++vbits;
+    gp.vbits = s->n + vbits <= 64 ? vbits : 0;
     ph_begin(s, PH_KEYS);
     launch_gate_keys(s->keys[s->cur], N, gp, s->sk[0], s->sidx[0], s->hist, passes, s->st);
     ph_end(s, PH_KEYS);
     launched(s, PH_KEYS, 1);
     int w = 0, run = 0;
-    rc = sort_pairs(s, N, s->n, true, &w, &run);
+    rc = gp.vbits ? sort_keys(s, N, gp.vbits, s->n, &w, &run) : sort_pairs(s, N, s->n, true, &w, &run);
     if (rc != SV_OK) return rc;
     s->stats.sort_passes = (uint32_t)run;
     ph_begin(s, PH_HEADS);
-    launch_group_heads(s->sk[w], N, m, s->heads, s->lookback, s->ctl, s->st);
+    launch_group_heads(s->sk[w], N, m + gp.vbits, s->heads, s->lookback, s->ctl, s->st);
     ph_end(s, PH_HEADS);
     ph_begin(s, PH_APPLY);
     launch_gate_apply(s->prec, s->sk[w], s->sidx[w], N, s->heads, s->amps[s->cur], gp, s->keys[alt],

@@ -87,7 +87,12 @@ class Server:
         run).  A request is admitted, in arrival order, once it has arrived,
         a slot is free and its footprint fits the budget (one request is
         always admitted into an empty batch).  With export the final state of
-        each circuit is returned as well."""
+        each circuit is returned as well.
+
+        Each admitted circuit's gates are converted once into the library's
+        gate layout; the gate table of a step is then gathered with array
+        indexing from the concatenated tables of the resident circuits
+        (rebuilt only when residents change)."""
         n = len(circuits)
         arrivals = np.zeros(n) if arrivals is None else np.asarray(arrivals, dtype=float)
         if clock is None:
@@ -95,10 +100,13 @@ class Server:
             clock = lambda: time.perf_counter() - t0  # noqa: E731
         order = deque(np.argsort(arrivals, kind="stable").tolist())
         results: List[Optional[Result]] = [None] * n
-        live = {}  # slot -> [request index, next gate, admission time]
+        live = {}  # slot -> [request index, next gate, admission time, prepared gates]
         used = 0
         retiring = 0  # slots removed since the last step (free after it)
         done = 0
+        dirty = True
+        slots = np.zeros(0, dtype=np.int32)
+        pos = np.zeros(0, dtype=np.int64)
         while done < n:
             now = clock()
             while order and arrivals[order[0]] <= now and len(live) + retiring < self.max_slots:
@@ -113,8 +121,9 @@ class Server:
                     done += 1
                     continue
                 slot = self.batch.add(c.n, c.K)
-                live[slot] = [j, 0, now]
+                live[slot] = [j, 0, now, sv.PreparedGates(c.gates)]
                 used += fp
+                dirty = True
             self.peak_resident = max(self.peak_resident, len(live))
             self.peak_bytes = max(self.peak_bytes, used)
             if not live:
@@ -126,19 +135,32 @@ class Server:
                     if wait > 0:
                         time.sleep(min(wait, 0.01))
                 continue
-            gates = []
-            for slot, (j, g, _) in live.items():
-                q, u = circuits[j].gates[g]
-                gates.append((slot, q, u))
-            self.batch.step(gates)
+            if dirty:  # residents changed: concatenate their gate tables
+                for k, sl in enumerate(slots):  # positions of the circuits that stay
+                    if int(sl) in live:
+                        live[int(sl)][1] = int(pos[k])
+                slots = np.array(list(live), dtype=np.int32)
+                preps = [live[int(sl)][3] for sl in slots]
+                counts = np.array([p.count for p in preps], dtype=np.int64)
+                base = np.concatenate([[0], np.cumsum(counts)[:-1]])
+                tm = np.concatenate([p.m for p in preps])
+                tq = np.concatenate([p.q for p in preps])
+                tu = np.concatenate([p.uptr for p in preps])
+                pos = np.array([live[int(sl)][1] for sl in slots], dtype=np.int64)
+                table = np.empty(len(slots), dtype=sv.GATE_DTYPE)
+                table["slot"] = slots
+                dirty = False
+            idx = base + pos
+            table["m"] = tm[idx]
+            table["q"] = tq[idx]
+            table["U"] = tu[idx]
+            self.batch.step_table(table)
             self.steps += 1
             retiring = 0
-            for slot in list(live):
-                entry = live[slot]
-                j, g, admitted = entry
-                entry[1] = g + 1
-                if g + 1 < len(circuits[j].gates):
-                    continue
+            pos += 1
+            for k in np.nonzero(pos == counts)[0]:
+                slot = int(slots[k])
+                j, _, admitted, _ = live[slot]
                 key, prob = self.batch.peak(slot)
                 f = self.batch.retained_mass(slot)
                 ks = am = None
@@ -150,6 +172,13 @@ class Server:
                 used -= footprint(circuits[j])
                 results[j] = Result(j, key, prob, f, float(arrivals[j]), admitted, clock(), ks, am)
                 done += 1
+                dirty = True
+            if dirty:  # retirements: save the positions before a slot can be reused
+                for k, sl in enumerate(slots):
+                    if int(sl) in live:
+                        live[int(sl)][1] = int(pos[k])
+                slots = np.zeros(0, dtype=np.int32)
+                pos = np.zeros(0, dtype=np.int64)
         return results  # type: ignore[return-value]
 
 

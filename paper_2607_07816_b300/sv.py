@@ -26,7 +26,7 @@ EXPORTED = ["sv_create", "sv_create_ex", "sv_destroy", "sv_apply_gate", "sv_trun
             "sv_last_stats", "sv_set_timing", "sv_phase_times", "sv_launch_count", "sv_transfer_bytes", "sv_peak_noalloc",
             "svb_create", "svb_destroy", "svb_add", "svb_remove", "svb_step", "svb_num_terms",
             "svb_retained_mass", "svb_peak", "svb_export", "svb_last_error", "svb_set_autotune",
-            "svb_autotune_stats", "sv_selftest"]
+            "svb_autotune_stats", "svb_set_graphs", "svb_graph_stats", "sv_selftest"]
 PHASES = ["keys", "sort", "heads", "apply", "select", "compact", "peak", "other", "window", "local"]
 
 
@@ -116,7 +116,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.svb_remove.restype = i32
     lib.svb_remove.argtypes = [vp, i32]
     lib.svb_step.restype = i32
-    lib.svb_step.argtypes = [vp, P(svb_gate), i32]
+    lib.svb_step.argtypes = [vp, vp, i32]
     lib.svb_num_terms.restype = i32
     lib.svb_num_terms.argtypes = [vp, i32, P(u64)]
     lib.svb_retained_mass.restype = i32
@@ -131,6 +131,10 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.svb_set_autotune.argtypes = [vp, i32]
     lib.svb_autotune_stats.restype = i32
     lib.svb_autotune_stats.argtypes = [vp, P(u64), P(u64), P(u64)]
+    lib.svb_set_graphs.restype = i32
+    lib.svb_set_graphs.argtypes = [vp, i32]
+    lib.svb_graph_stats.restype = i32
+    lib.svb_graph_stats.argtypes = [vp, P(u64), P(u64)]
     lib.sv_peak_noalloc.restype = i32
     lib.sv_peak_noalloc.argtypes = [i32, vp, vp, u64, vp, P(u64), P(dbl)]
     lib.sv_selftest.restype = i32
@@ -375,6 +379,36 @@ def svb_remove(h: int, slot: int) -> None:
     _bcheck(h, load_library().svb_remove(ctypes.c_void_p(h), slot))
 
 
+# numpy layout of svb_gate (slot, m, qubits[4], U pointer): 32 bytes
+GATE_DTYPE = np.dtype([("slot", "<i4"), ("m", "<i4"), ("q", "<i4", (4,)), ("U", "<u8")])
+assert GATE_DTYPE.itemsize == ctypes.sizeof(svb_gate)
+
+
+class PreparedGates:
+    """A circuit's gates in the svb_gate layout, converted once: m, qubits
+    and the address of each U inside one float64 buffer (kept alive here)."""
+
+    def __init__(self, gates):
+        gates = list(gates)
+        self.count = len(gates)
+        self.m = np.array([len(q) for q, _ in gates], dtype=np.int32)
+        self.q = np.zeros((self.count, 4), dtype=np.int32)
+        sizes = np.array([2 << (2 * int(m)) for m in self.m], dtype=np.int64)
+        offs = np.concatenate([[0], np.cumsum(sizes)[:-1]]) if self.count else np.zeros(0, np.int64)
+        self.buf = np.empty(int(sizes.sum()) if self.count else 1, dtype=np.float64)
+        for i, (q, u) in enumerate(gates):
+            self.q[i, :len(q)] = q
+            self.buf[offs[i]:offs[i] + sizes[i]] = _u_buffer(u)
+        self.uptr = (self.buf.ctypes.data + 8 * offs).astype(np.uint64)
+
+
+def svb_step_table(h: int, table: np.ndarray) -> None:
+    """One step from a GATE_DTYPE array (its U addresses must stay valid
+    for the call)."""
+    table = np.ascontiguousarray(table, dtype=GATE_DTYPE)
+    _bcheck(h, load_library().svb_step(ctypes.c_void_p(h), ctypes.c_void_p(table.ctypes.data), len(table)))
+
+
 def svb_step(h: int, gates) -> None:
     """gates: iterable of (slot, qubits, U)."""
     gates = list(gates)
@@ -388,7 +422,7 @@ def svb_step(h: int, gates) -> None:
         for t, x in enumerate(q):
             arr[i].qubits[t] = int(x)
         arr[i].U = ub.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-    _bcheck(h, load_library().svb_step(ctypes.c_void_p(h), arr, len(gates)))
+    _bcheck(h, load_library().svb_step(ctypes.c_void_p(h), ctypes.cast(arr, ctypes.c_void_p), len(gates)))
 
 
 def svb_num_terms(h: int, slot: int) -> int:
@@ -427,6 +461,16 @@ def svb_set_autotune(h: int, on: bool) -> None:
     _bcheck(h, load_library().svb_set_autotune(ctypes.c_void_p(h), 1 if on else 0))
 
 
+def svb_set_graphs(h: int, on: bool) -> None:
+    _bcheck(h, load_library().svb_set_graphs(ctypes.c_void_p(h), 1 if on else 0))
+
+
+def svb_graph_stats(h: int):
+    c, n = ctypes.c_uint64(), ctypes.c_uint64()
+    _bcheck(h, load_library().svb_graph_stats(ctypes.c_void_p(h), ctypes.byref(c), ctypes.byref(n)))
+    return {"captures": c.value, "launches": n.value}
+
+
 def svb_autotune_stats(h: int):
     t, c, d = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
     _bcheck(h, load_library().svb_autotune_stats(ctypes.c_void_p(h), ctypes.byref(t), ctypes.byref(c),
@@ -461,6 +505,9 @@ class Batch:
     def step(self, gates) -> None:
         svb_step(self.h, gates)
 
+    def step_table(self, table: np.ndarray) -> None:
+        svb_step_table(self.h, table)
+
     def num_terms(self, slot: int) -> int:
         return svb_num_terms(self.h, slot)
 
@@ -478,3 +525,9 @@ class Batch:
 
     def autotune_stats(self):
         return svb_autotune_stats(self.h)
+
+    def set_graphs(self, on: bool) -> None:
+        svb_set_graphs(self.h, on)
+
+    def graph_stats(self):
+        return svb_graph_stats(self.h)

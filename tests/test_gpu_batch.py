@@ -151,27 +151,47 @@ def test_batch_sort_key_bit_bound(sv):
     b.close()
 
 
+def _run_batch(sv, circs, tune, graphs, reps=1):
+    b = sv.Batch(16, prec=1)
+    b.set_autotune(tune)
+    b.set_graphs(graphs)
+    slots = [b.add(c.n, c.K) for c in circs]
+    longest = max(len(c.gates) for c in circs)
+    for _ in range(reps):
+        for g in range(longest):
+            b.step([(slots[j], *c.gates[g]) for j, c in enumerate(circs) if g < len(c.gates)])
+    res = [(b.export(s), b.peak(s), b.retained_mass(s)) for s in slots]
+    stats = (b.autotune_stats(), b.graph_stats())
+    b.close()
+    return res, stats
+
+
+def _same(ra, rb):
+    for (ea, pa, fa), (eb, pb, fb) in zip(ra, rb):
+        assert _as_dict(*ea) == _as_dict(*eb)
+        assert pa == pb and fa == fb
+
+
 def test_autotuned_shapes_give_identical_results(sv):
     """The autotuner runs every candidate launch shape on live steps; the
     result of every circuit must be the same as with the fixed shapes."""
-    rng = np.random.default_rng(71)
-    circs = _circuits(rng, 8)
-    out = []
-    for tune in (False, True):
-        b = sv.Batch(16, prec=1)
-        b.set_autotune(tune)
-        slots = [b.add(c.n, c.K) for c in circs]
-        longest = max(len(c.gates) for c in circs)
-        for g in range(longest):
-            b.step([(slots[j], *c.gates[g]) for j, c in enumerate(circs) if g < len(c.gates)])
-        res = [(b.export(s), b.peak(s), b.retained_mass(s)) for s in slots]
-        stats = b.autotune_stats()
-        b.close()
-        out.append(res)
-        if tune:
-            assert stats["trials"] > 0 and stats["classes"] > 0
-        else:
-            assert stats["trials"] == 0
-    for (ea, pa, fa), (eb, pb, fb) in zip(out[0], out[1]):
-        assert _as_dict(*ea) == _as_dict(*eb)
-        assert pa == pb and fa == fb
+    circs = _circuits(np.random.default_rng(71), 8)
+    fixed, (tstats, _) = _run_batch(sv, circs, tune=False, graphs=False)
+    tuned, (tstats2, _) = _run_batch(sv, circs, tune=True, graphs=False)
+    assert tstats["trials"] == 0
+    assert tstats2["trials"] > 0 and tstats2["classes"] > 0
+    _same(fixed, tuned)
+
+
+def test_graph_replay_gives_identical_results(sv):
+    """Circuits held at their K repeat the same step sizes, so the captured
+    graphs are replayed; results must equal direct launches."""
+    rng = np.random.default_rng(72)
+    circs = [C.brickwork_circuit(20, 3, seed=int(rng.integers(1 << 30)), sigma=0.05, K=64, p=1.0)
+             for _ in range(5)]
+    direct, _ = _run_batch(sv, circs, tune=False, graphs=False)
+    graphed, (_, gstats) = _run_batch(sv, circs, tune=False, graphs=True)
+    assert gstats["captures"] >= 1 and gstats["launches"] > gstats["captures"]
+    _same(direct, graphed)
+    tuned, (tstats, gstats2) = _run_batch(sv, circs, tune=True, graphs=True)
+    _same(direct, tuned)

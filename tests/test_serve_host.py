@@ -48,6 +48,9 @@ class FakeBatch:
             del self.state[s]
         self.steps.append(sorted(slots))
 
+    def step_table(self, table):
+        self.step([(int(r["slot"]), tuple(int(x) for x in r["q"][:int(r["m"])]), None) for r in table])
+
     def peak(self, slot):
         return (self.applied[slot], 0.5)
 
