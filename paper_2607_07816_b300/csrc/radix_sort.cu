@@ -1,15 +1,17 @@
-// Stable LSD radix sort of (uint64 key, uint32 value) pairs.
+// Stable LSD radix sort of (uint64 key, uint32 value) pairs, or of keys
+// alone (a key may carry its payload in the bits below the sorted ones).
 //
 // This is the grouping step of the gate application: contributions to the
 // same basis state must be brought together before they are summed (the
 // segmented sum of Sec. IV-A), and sorting on the bits outside the gate makes
 // every partner group contiguous.  It is also used by the canonical readout.
 //
-// One histogram kernel counts every 8-bit digit in one read; each pass is a
-// single "onesweep" kernel: a tile ranks its keys per warp with
-// __match_any_sync, gets the exclusive digit offsets of all earlier tiles by
-// decoupled look-back (bounded waits), stages the tile in shared memory in
-// digit order and writes each digit run contiguously.
+// One histogram kernel counts every 8-bit digit in one read.  Each pass then
+// runs three kernels with no waiting between blocks: the digit counts of
+// every tile, their exclusive scan over the tiles for every digit (plus the
+// digit's base from the global histogram), and the scatter, in which a tile
+// ranks its keys per warp with __match_any_sync, stages them in shared
+// memory in digit order and writes each digit run at its scanned offset.
 #include "internal.h"
 
 namespace sv {
@@ -40,76 +42,132 @@ void launch_digit_hist(const uint64_t* k, uint64_t n, int nbits, uint32_t* hist,
   k_digit_hist<<<(unsigned)blocks, 256, 0, st>>>(k, n, passes, hist);
 }
 
-// Exclusive scan of one value per thread over the block (values of threads
-// that have none are 0); all BLOCK threads call it.
-template <int BLOCK>
-__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* warp_tot) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t x = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) warp_tot[warp] = x;
-  __syncthreads();
-  uint32_t base = 0;
-  for (int w = 0; w < warp; ++w) base += warp_tot[w];
-  __syncthreads();
-  return base + x - v;
+// Tile layout shared by the counting and scatter kernels: tile t holds keys
+// [t * SORT_TILE, ...); warp w of the tile owns [w*32*ITEMS, (w+1)*32*ITEMS)
+// lane-interleaved, so warp-local ranks follow the input order (stability).
+constexpr int ST_WARPS = SORT_THREADS / 32;
+
+__device__ __forceinline__ uint32_t sort_digit(uint64_t k, int shift) {
+  return (uint32_t)((k >> shift) & (RADIX - 1));
 }
 
-// One pass of the LSD sort over the 8-bit digit at `shift`.  Warp w of the
-// tile owns elements [w*32*ITEMS, (w+1)*32*ITEMS) (lane-interleaved), so the
-// warp-local ranks (match_any + a per-warp counter per digit) follow the
-// input order and the sort is stable.  Threads 0..255 then own one digit
-// each: exclusive offsets across warps, the tile-local digit offsets, and
-// the decoupled look-back over earlier tiles for the digit's global base.
-// PAIRS = false sorts keys alone (a key may carry its payload in the bits
-// below `shift`).
-template <int BLOCK, int ITEMS, bool PAIRS>
-__global__ void __launch_bounds__(BLOCK) k_onesweep(const uint64_t* __restrict__ kin,
-                                                   const uint32_t* __restrict__ vin,
-                                                   uint64_t* __restrict__ kout,
-                                                   uint32_t* __restrict__ vout, uint64_t n,
-                                                   int shift, const uint32_t* __restrict__ hist,
-                                                   uint64_t* lookback, uint64_t* tile_counter,
-                                                   uint32_t* err) {
-  static_assert(BLOCK >= RADIX, "one thread per digit");
-  constexpr int TILE = BLOCK * ITEMS;
-  constexpr int WARPS = BLOCK / 32;
-  extern __shared__ __align__(16) uint8_t s_dyn[];
-  uint64_t* s_keys = reinterpret_cast<uint64_t*>(s_dyn);
-  uint32_t* s_vals = reinterpret_cast<uint32_t*>(s_dyn + sizeof(uint64_t) * TILE);
-  __shared__ uint32_t s_whist[WARPS][RADIX];
-  __shared__ uint32_t s_local[RADIX];
-  __shared__ uint64_t s_global[RADIX];
-  __shared__ uint32_t s_wtot[WARPS];
-  __shared__ uint64_t s_tile;
-
+// 1. Digit counts of every tile: cnt[d * tiles + t].
+__global__ void __launch_bounds__(SORT_THREADS) k_tile_counts(const uint64_t* __restrict__ kin, uint64_t n,
+                                                              int shift, uint64_t tiles,
+                                                              uint32_t* __restrict__ cnt) {
+  __shared__ uint32_t h[RADIX];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const bool digit_thread = tid < RADIX;
-  if (tid == 0) s_tile = atomicAdd((unsigned long long*)tile_counter, 1ull);
-  for (int i = tid; i < WARPS * RADIX; i += BLOCK) (&s_whist[0][0])[i] = 0;
-  const uint32_t digit_base = block_exclusive_scan<BLOCK>(digit_thread ? hist[tid] : 0u, s_wtot);
-  const uint64_t tile = s_tile;
-  const uint64_t base = tile * TILE;
-
-  uint64_t k[ITEMS];
-  uint32_t v[ITEMS], d[ITEMS], rank[ITEMS];
-  const uint32_t lt_mask = (1u << lane) - 1u;
+  for (int i = tid; i < RADIX; i += SORT_THREADS) h[i] = 0;
+  __syncthreads();
+  const uint64_t t = blockIdx.x;
+  const uint64_t base = t * SORT_TILE;
+  uint64_t k[SORT_ITEMS];
 #pragma unroll
-  for (int i = 0; i < ITEMS; ++i) {
-    uint64_t idx = base + (uint64_t)warp * 32 * ITEMS + i * 32 + lane;
-    bool valid = idx < n;
-    k[i] = valid ? kin[idx] : 0ull;
-    v[i] = (PAIRS && valid) ? vin[idx] : 0u;
-    d[i] = valid ? (uint32_t)((k[i] >> shift) & (RADIX - 1)) : (uint32_t)RADIX;
+  for (int i = 0; i < SORT_ITEMS; ++i) {
+    const uint64_t idx = base + (uint64_t)warp * 32 * SORT_ITEMS + i * 32 + lane;
+    k[i] = idx < n ? kin[idx] : 0ull;
   }
 #pragma unroll
-  for (int i = 0; i < ITEMS; ++i) {
-    uint32_t peers = __match_any_sync(0xffffffffu, d[i]);
-    int leader = __ffs(peers) - 1;
+  for (int i = 0; i < SORT_ITEMS; ++i) {
+    const uint64_t idx = base + (uint64_t)warp * 32 * SORT_ITEMS + i * 32 + lane;
+    const uint32_t d = idx < n ? sort_digit(k[i], shift) : (uint32_t)RADIX;
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    if (d < RADIX && lane == __ffs(peers) - 1) atomicAdd(&h[d], (uint32_t)__popc(peers));
+  }
+  __syncthreads();
+  for (int d = tid; d < RADIX; d += SORT_THREADS) cnt[(uint64_t)d * tiles + t] = h[d];
+}
+
+// 2. One block per digit: off[d * tiles + t] = base(d) + counts of digit d in
+// tiles before t, base(d) = number of keys with a smaller digit (from the
+// global histogram of this pass).
+constexpr int SCAN_THREADS = 1024;
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_tile_offsets(const uint32_t* __restrict__ cnt,
+                                                               const uint32_t* __restrict__ hist, uint64_t tiles,
+                                                               uint32_t* __restrict__ off) {
+  __shared__ uint32_t wsum[SCAN_THREADS / 32];
+  __shared__ uint32_t s_carry;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int d = blockIdx.x;
+  if (tid == 0) {
+    uint32_t b = 0;
+    for (int e = 0; e < d; ++e) b += hist[e];
+    s_carry = b;
+  }
+  __syncthreads();
+  const uint32_t* row = cnt + (uint64_t)d * tiles;
+  uint32_t* orow = off + (uint64_t)d * tiles;
+  for (uint64_t c0 = 0; c0 < tiles; c0 += SCAN_THREADS) {
+    const uint64_t t = c0 + tid;
+    const uint32_t v = t < tiles ? row[t] : 0u;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      const uint32_t w = wsum[lane];
+      uint32_t z = w;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, z, o);
+        if (lane >= o) z += y;
+      }
+      wsum[lane] = z - w;  // exclusive over warps
+    }
+    __syncthreads();
+    const uint32_t carry = s_carry;
+    if (t < tiles) orow[t] = carry + wsum[warp] + x - v;
+    __syncthreads();
+    if (tid == SCAN_THREADS - 1) s_carry = carry + wsum[warp] + x;
+    __syncthreads();
+  }
+}
+
+// 3. Scatter: rank the tile's keys per warp (match_any and per-warp digit
+// counters), turn the counters into per-warp offsets within each digit, scan
+// the tile's digit counts, stage the tile in shared memory in digit order
+// and write every digit run at off[d * tiles + t].  PAIRS = false sorts the
+// keys alone.
+template <bool PAIRS>
+__global__ void __launch_bounds__(SORT_THREADS) k_tile_scatter(const uint64_t* __restrict__ kin,
+                                                               const uint32_t* __restrict__ vin,
+                                                               uint64_t* __restrict__ kout,
+                                                               uint32_t* __restrict__ vout, uint64_t n, int shift,
+                                                               uint64_t tiles, const uint32_t* __restrict__ off) {
+  static_assert(SORT_THREADS >= RADIX, "one thread per digit");
+  extern __shared__ __align__(16) uint8_t s_dyn[];
+  uint64_t* s_keys = reinterpret_cast<uint64_t*>(s_dyn);
+  uint32_t* s_vals = reinterpret_cast<uint32_t*>(s_dyn + sizeof(uint64_t) * SORT_TILE);
+  __shared__ uint32_t s_whist[ST_WARPS][RADIX];
+  __shared__ uint32_t s_local[RADIX];
+  __shared__ uint32_t s_out[RADIX];
+  __shared__ uint32_t s_wtot[ST_WARPS];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint64_t t = blockIdx.x;
+  const uint64_t base = t * SORT_TILE;
+  for (int i = tid; i < ST_WARPS * RADIX; i += SORT_THREADS) (&s_whist[0][0])[i] = 0;
+  if (tid < RADIX) s_out[tid] = off[(uint64_t)tid * tiles + t];
+  uint64_t k[SORT_ITEMS];
+  uint32_t v[SORT_ITEMS], d[SORT_ITEMS], rank[SORT_ITEMS];
+  const uint32_t lt_mask = (1u << lane) - 1u;
+#pragma unroll
+  for (int i = 0; i < SORT_ITEMS; ++i) {
+    const uint64_t idx = base + (uint64_t)warp * 32 * SORT_ITEMS + i * 32 + lane;
+    const bool valid = idx < n;
+    k[i] = valid ? kin[idx] : 0ull;
+    v[i] = (PAIRS && valid) ? vin[idx] : 0u;
+    d[i] = valid ? sort_digit(k[i], shift) : (uint32_t)RADIX;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < SORT_ITEMS; ++i) {
+    const uint32_t peers = __match_any_sync(0xffffffffu, d[i]);
+    const int leader = __ffs(peers) - 1;
     uint32_t old = 0;
     if (lane == leader && d[i] < RADIX) {
       old = s_whist[warp][d[i]];
@@ -120,104 +178,84 @@ __global__ void __launch_bounds__(BLOCK) k_onesweep(const uint64_t* __restrict__
     __syncwarp();
   }
   __syncthreads();
+  // per digit: offsets of the warps within the digit, and the digit's count
   uint32_t cnt = 0;
-  if (digit_thread) {
+  if (tid < RADIX) {
 #pragma unroll
-    for (int w = 0; w < WARPS; ++w) {
-      uint32_t c = s_whist[w][tid];
+    for (int w = 0; w < ST_WARPS; ++w) {
+      const uint32_t c = s_whist[w][tid];
       s_whist[w][tid] = cnt;
       cnt += c;
     }
   }
-  const uint32_t local = block_exclusive_scan<BLOCK>(cnt, s_wtot);
-  if (digit_thread) {
-    s_local[tid] = local;
-    uint64_t excl = lookback_exclusive_x4(lookback + tid, RADIX, tile, cnt, err);
-    s_global[tid] = digit_base + excl;
+  // exclusive scan of the digit counts over the tile (threads 0..RADIX-1)
+  uint32_t x = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_wtot[warp] = x;
+  __syncthreads();
+  if (tid < RADIX) {
+    uint32_t b = 0;
+    for (int w = 0; w < warp; ++w) b += s_wtot[w];
+    s_local[tid] = b + x - cnt;
   }
   __syncthreads();
 #pragma unroll
-  for (int i = 0; i < ITEMS; ++i) {
+  for (int i = 0; i < SORT_ITEMS; ++i) {
     if (d[i] < RADIX) {
-      uint32_t pos = s_local[d[i]] + s_whist[warp][d[i]] + rank[i];
+      const uint32_t pos = s_local[d[i]] + s_whist[warp][d[i]] + rank[i];
       s_keys[pos] = k[i];
       if (PAIRS) s_vals[pos] = v[i];
     }
   }
   __syncthreads();
-  uint64_t tile_n = n - base < (uint64_t)TILE ? n - base : (uint64_t)TILE;
-  for (uint32_t j = tid; j < tile_n; j += BLOCK) {
-    uint64_t key = s_keys[j];
-    uint32_t dd = (uint32_t)((key >> shift) & (RADIX - 1));
-    uint64_t out = s_global[dd] + (j - s_local[dd]);
+  const uint32_t tile_n = (uint32_t)(n - base < (uint64_t)SORT_TILE ? n - base : (uint64_t)SORT_TILE);
+  for (uint32_t j = tid; j < tile_n; j += SORT_THREADS) {
+    const uint64_t key = s_keys[j];
+    const uint32_t dd = sort_digit(key, shift);
+    const uint64_t out = (uint64_t)s_out[dd] + (j - s_local[dd]);
     kout[out] = key;
     if (PAIRS) vout[out] = s_vals[j];
   }
 }
 
-static size_t onesweep_smem(bool pairs) { return (sizeof(uint64_t) + (pairs ? sizeof(uint32_t) : 0)) * SORT_TILE; }
+static size_t scatter_smem(bool pairs) { return (sizeof(uint64_t) + (pairs ? sizeof(uint32_t) : 0)) * SORT_TILE; }
 
 // Kernel attributes (dynamic shared memory) set once, outside any stream
 // capture.
 void sort_prepare() {
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_onesweep<SORT_THREADS, SORT_ITEMS, true>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)onesweep_smem(true));
-    cudaFuncSetAttribute(k_onesweep<SORT_THREADS, SORT_ITEMS, false>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)onesweep_smem(false));
+    cudaFuncSetAttribute(k_tile_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)scatter_smem(true));
+    cudaFuncSetAttribute(k_tile_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)scatter_smem(false));
     attr_set = true;
   }
 }
 
-int radix_sort_pairs(uint64_t* kA, uint32_t* vA, uint64_t* kB, uint32_t* vB, uint64_t n, int nbits,
-                     const SortScratch& sc, cudaStream_t st, int* passes_run, cudaError_t* cerr) {
-  int passes = (nbits + RADIX_BITS - 1) / RADIX_BITS;
-  int cur = 0, run = 0;
-  *cerr = cudaSuccess;
-  sort_prepare();
-  uint64_t tiles = sort_tiles(n);
-  if (n > 1) {
-    for (int p = 0; p < passes; ++p) {
-      // a pass whose digit is the same for every key is the identity (known
-      // only when the caller read the histograms back: hist_host != NULL)
-      if (sc.hist_host) {
-        const uint32_t* hh = sc.hist_host + p * RADIX;
-        bool trivial = false;
-        for (int dgt = 0; dgt < RADIX; ++dgt)
-          if (hh[dgt] == n) trivial = true;
-        if (trivial) continue;
-      }
-      if (tiles > sc.lookback_tiles) {
-        *cerr = cudaErrorInvalidValue;
-        return cur;
-      }
-      cudaMemsetAsync(sc.lookback, 0, sizeof(uint64_t) * RADIX * tiles, st);
-      cudaMemsetAsync(sc.tile_counter, 0, sizeof(uint64_t), st);
-      const uint64_t* ki = cur ? kB : kA;
-      const uint32_t* vi = cur ? vB : vA;
-      uint64_t* ko = cur ? kA : kB;
-      uint32_t* vo = cur ? vA : vB;
-      k_onesweep<SORT_THREADS, SORT_ITEMS, true><<<(unsigned)tiles, SORT_THREADS, onesweep_smem(true), st>>>(
-          ki, vi, ko, vo, n, RADIX_BITS * p, sc.hist + p * RADIX, sc.lookback, sc.tile_counter,
-          sc.err);
-      cur ^= 1;
-      ++run;
-    }
-  }
-  *passes_run = run;
-  *cerr = cudaGetLastError();
-  return cur;
-}
-
-int radix_sort_keys(uint64_t* kA, uint64_t* kB, uint64_t n, int lo, int nbits, const SortScratch& sc,
-                    cudaStream_t st, int* passes_run, cudaError_t* cerr) {
+// The passes of one sort: digits at lo + 8p for p < ceil(nbits / 8);
+// vA/vB == nullptr sorts keys alone.  The per-tile counts and offsets live
+// in sc.lookback (2 * RADIX * tiles 32-bit words).
+static int sort_passes(uint64_t* kA, uint32_t* vA, uint64_t* kB, uint32_t* vB, uint64_t n, int lo, int nbits,
+                       const SortScratch& sc, cudaStream_t st, int* passes_run, cudaError_t* cerr) {
   const int passes = (nbits + RADIX_BITS - 1) / RADIX_BITS;
+  const bool pairs = vA != nullptr;
   int cur = 0, run = 0;
   *cerr = cudaSuccess;
   sort_prepare();
   const uint64_t tiles = sort_tiles(n);
   if (n > 1) {
+    if (tiles > sc.lookback_tiles || n > 0xffffffffull) {
+      *cerr = cudaErrorInvalidValue;
+      *passes_run = 0;
+      return 0;
+    }
+    uint32_t* cnt = reinterpret_cast<uint32_t*>(sc.lookback);
+    uint32_t* off = cnt + RADIX * tiles;
     for (int p = 0; p < passes; ++p) {
       if (sc.hist_host) {  // a pass whose digit is the same for every key is the identity
         const uint32_t* hh = sc.hist_host + p * RADIX;
@@ -226,17 +264,19 @@ int radix_sort_keys(uint64_t* kA, uint64_t* kB, uint64_t n, int lo, int nbits, c
           if (hh[dgt] == n) trivial = true;
         if (trivial) continue;
       }
-      if (tiles > sc.lookback_tiles) {
-        *cerr = cudaErrorInvalidValue;
-        return cur;
-      }
-      cudaMemsetAsync(sc.lookback, 0, sizeof(uint64_t) * RADIX * tiles, st);
-      cudaMemsetAsync(sc.tile_counter, 0, sizeof(uint64_t), st);
+      const int shift = lo + RADIX_BITS * p;
       const uint64_t* ki = cur ? kB : kA;
+      const uint32_t* vi = cur ? vB : vA;
       uint64_t* ko = cur ? kA : kB;
-      k_onesweep<SORT_THREADS, SORT_ITEMS, false><<<(unsigned)tiles, SORT_THREADS, onesweep_smem(false), st>>>(
-          ki, nullptr, ko, nullptr, n, lo + RADIX_BITS * p, sc.hist + p * RADIX, sc.lookback, sc.tile_counter,
-          sc.err);
+      uint32_t* vo = cur ? vA : vB;
+      k_tile_counts<<<(unsigned)tiles, SORT_THREADS, 0, st>>>(ki, n, shift, tiles, cnt);
+      k_tile_offsets<<<RADIX, SCAN_THREADS, 0, st>>>(cnt, sc.hist + p * RADIX, tiles, off);
+      if (pairs)
+        k_tile_scatter<true><<<(unsigned)tiles, SORT_THREADS, scatter_smem(true), st>>>(ki, vi, ko, vo, n, shift,
+                                                                                         tiles, off);
+      else
+        k_tile_scatter<false><<<(unsigned)tiles, SORT_THREADS, scatter_smem(false), st>>>(ki, nullptr, ko, nullptr,
+                                                                                          n, shift, tiles, off);
       cur ^= 1;
       ++run;
     }
@@ -244,6 +284,16 @@ int radix_sort_keys(uint64_t* kA, uint64_t* kB, uint64_t n, int lo, int nbits, c
   *passes_run = run;
   *cerr = cudaGetLastError();
   return cur;
+}
+
+int radix_sort_pairs(uint64_t* kA, uint32_t* vA, uint64_t* kB, uint32_t* vB, uint64_t n, int nbits,
+                     const SortScratch& sc, cudaStream_t st, int* passes_run, cudaError_t* cerr) {
+  return sort_passes(kA, vA, kB, vB, n, 0, nbits, sc, st, passes_run, cerr);
+}
+
+int radix_sort_keys(uint64_t* kA, uint64_t* kB, uint64_t n, int lo, int nbits, const SortScratch& sc,
+                    cudaStream_t st, int* passes_run, cudaError_t* cerr) {
+  return sort_passes(kA, nullptr, kB, nullptr, n, lo, nbits, sc, st, passes_run, cerr);
 }
 
 }  // namespace sv
