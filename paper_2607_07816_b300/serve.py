@@ -80,14 +80,15 @@ class Server:
         self.batch.close()
 
     def run(self, circuits: Sequence, arrivals: Optional[Sequence[float]] = None, clock=None,
-            export: bool = False) -> List[Result]:
+            export: bool = False, max_steps: Optional[int] = None) -> List[Result]:
         """Serve every circuit and return one Result per circuit, in input
         order.  arrivals[j] is when request j arrives, in the units of clock
         (seconds after the start by default; all 0 when None: a saturated
         run).  A request is admitted, in arrival order, once it has arrived,
         a slot is free and its footprint fits the budget (one request is
         always admitted into an empty batch).  With export the final state of
-        each circuit is returned as well.
+        each circuit is returned as well.  max_steps stops the loop after that
+        many steps (unfinished requests then have no Result).
 
         Each admitted circuit's gates are converted once into the library's
         gate layout; the gate table of a step is then gathered with array
@@ -107,7 +108,7 @@ class Server:
         dirty = True
         slots = np.zeros(0, dtype=np.int32)
         pos = np.zeros(0, dtype=np.int64)
-        while done < n:
+        while done < n and (max_steps is None or self.steps < max_steps):
             now = clock()
             while order and arrivals[order[0]] <= now and len(live) + retiring < self.max_slots:
                 j = order[0]
@@ -215,3 +216,45 @@ def fifo_latencies(arrivals: Sequence[float], service: Sequence[float]) -> np.nd
         t = start + s
         lat.append(t - a)
     return np.array(lat)
+
+
+def main(argv=None) -> None:
+    """Serve a seeded synthetic request stream and print one JSON summary
+    (python -m paper_2607_07816_b300.serve --help)."""
+    import argparse
+    import json
+
+    from . import circuits as C
+
+    ap = argparse.ArgumentParser(description=main.__doc__)
+    ap.add_argument("--requests", type=int, default=64)
+    ap.add_argument("--seed", type=int, default=1005)
+    ap.add_argument("--large-frac", type=float, default=0.02)
+    ap.add_argument("--k-min", type=int, default=10)
+    ap.add_argument("--k-max", type=int, default=20)
+    ap.add_argument("--rate", type=float, default=0.0, help="Poisson arrivals per second (0: all at t=0)")
+    ap.add_argument("--prec", choices=["c64", "c128"], default="c64")
+    ap.add_argument("--budget-gb", type=float, default=160.0)
+    ap.add_argument("--max-steps", type=int, default=None)
+    a = ap.parse_args(argv)
+    reqs = [C.serving_request(j, seed=a.seed, large_frac=a.large_frac, k_range=(a.k_min, a.k_max))
+            for j in range(a.requests)]
+    arrivals = poisson_arrivals(len(reqs), a.rate, a.seed) if a.rate > 0 else None
+    srv = Server(int(a.budget_gb * (1 << 30)), n_max=max(c.n for c in reqs),
+                 prec=sv.SV_C64 if a.prec == "c64" else sv.SV_C128)
+    t0 = time.perf_counter()
+    res = srv.run(reqs, arrivals=arrivals, max_steps=a.max_steps)
+    wall = time.perf_counter() - t0
+    fin = [r for r in res if r is not None]
+    out = {"requests": len(reqs), "finished": len(fin), "steps": srv.steps, "wall_s": wall,
+           "circuits_per_s": len(fin) / wall if wall > 0 else None, "max_resident": srv.peak_resident,
+           "graphs": srv.batch.graph_stats(), "autotune": srv.batch.autotune_stats()}
+    if fin:
+        lat = np.array([r.latency for r in fin])
+        out.update({"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99))})
+    srv.close()
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()
