@@ -245,6 +245,42 @@ __device__ __forceinline__ u128 warp_sum_u128(u128 v) {
 // above the window, the window's mass and its terms (probability, key, index)
 // gathered into the window buffer, and per tile the number of terms above
 // the window (they are kept whatever the exact cut is).
+// Window terms are staged in shared memory and written out in batches, one
+// atomic reservation per batch (a reservation per tile contended on a single
+// counter); a tile with more window terms than the stage holds writes them
+// directly.  The order of the window buffer is immaterial (the select works
+// on values, the tile counts on indices).
+constexpr int WP_STAGE = 1024;
+
+struct WindowStage {
+  uint64_t p[WP_STAGE];
+  uint64_t k[WP_STAGE];
+  uint32_t i[WP_STAGE];
+  uint32_t n;
+  uint64_t base;
+};
+
+__device__ __forceinline__ void window_flush(WindowStage& st, Ctl* ctl, uint64_t* __restrict__ wp,
+                                             uint64_t* __restrict__ wk, uint32_t* __restrict__ wi, uint64_t cap) {
+  // all threads call it; st.n is block-uniform
+  const uint32_t cnt = st.n;
+  if (cnt == 0) return;
+  if (threadIdx.x == 0) st.base = atomicAdd((unsigned long long*)&ctl->win_n, (unsigned long long)cnt);
+  __syncthreads();
+  const uint64_t b = st.base;
+  for (uint32_t j = threadIdx.x; j < cnt; j += WP_BLOCK) {
+    const uint64_t o = b + j;
+    if (o < cap) {
+      wp[o] = st.p[j];
+      wk[o] = st.k[j];
+      wi[o] = st.i[j];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) st.n = 0;
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(WP_BLOCK, 4) k_window_pass(const uint64_t* __restrict__ probs,
                                                           const uint64_t* __restrict__ keys, uint64_t n,
                                                           Ctl* ctl, uint64_t* __restrict__ wp,
@@ -253,10 +289,13 @@ __global__ void __launch_bounds__(WP_BLOCK, 4) k_window_pass(const uint64_t* __r
   typedef TileLayout<WP_BLOCK, WP_ITEMS> L;
   __shared__ uint32_t s_warp[WP_BLOCK / 32];
   __shared__ uint32_t s_above[WP_BLOCK / 32];
-  __shared__ uint64_t s_base;
+  __shared__ uint32_t s_acc;
+  __shared__ uint64_t s_direct;
+  __shared__ WindowStage st;
   const uint64_t hi = ctl->win_hi, lo = ctl->win_lo;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt = (1u << lane) - 1u;
+  if (threadIdx.x == 0) st.n = 0;
   u128 tot = 0, above_m = 0, win_m = 0;
   uint64_t above_c = 0;
   const uint64_t tiles = (n + L::TILE - 1) / L::TILE;
@@ -304,29 +343,43 @@ __global__ void __launch_bounds__(WP_BLOCK, 4) k_window_pass(const uint64_t* __r
         ab += s_above[w];
       }
       tile_keep[tile] = ab;
-      s_base = acc ? atomicAdd((unsigned long long*)&ctl->win_n, (unsigned long long)acc) : 0ull;
+      s_acc = acc;
+      s_direct = acc > WP_STAGE ? atomicAdd((unsigned long long*)&ctl->win_n, (unsigned long long)acc) : 0ull;
     }
     __syncthreads();
-    const uint64_t wbase = s_base + s_warp[warp];
+    const uint32_t acc = s_acc;
+    if (acc == 0) continue;  // block-uniform
+    const bool direct = acc > WP_STAGE;
+    if (!direct && st.n + acc > WP_STAGE) window_flush(st, ctl, wp, wk, wi, cap);
+    const uint32_t sbase = st.n;
     uint32_t wrun = 0;  // window positions: the same ballots again, in item order
 #pragma unroll
     for (int j = 0; j < WP_ITEMS; ++j) {
       const bool inwin = (wmask >> j) & 1u;
       const uint32_t b = __ballot_sync(0xffffffffu, inwin);
-      const uint32_t wpos = wrun + __popc(b & lt);
+      const uint32_t wpos = s_warp[warp] + wrun + __popc(b & lt);
       wrun += __popc(b);
       if (inwin) {
-        const uint64_t o = wbase + wpos;
         const uint64_t i = L::index(base, j);
-        if (o < cap) {
-          wp[o] = pbv[j];
-          wk[o] = keys[i];
-          wi[o] = (uint32_t)i;
+        if (direct) {
+          const uint64_t o = s_direct + wpos;
+          if (o < cap) {
+            wp[o] = pbv[j];
+            wk[o] = keys[i];
+            wi[o] = (uint32_t)i;
+          }
+        } else {
+          st.p[sbase + wpos] = pbv[j];
+          st.k[sbase + wpos] = keys[i];
+          st.i[sbase + wpos] = (uint32_t)i;
         }
       }
     }
     __syncthreads();
+    if (!direct && threadIdx.x == 0) st.n = sbase + acc;
+    __syncthreads();
   }
+  window_flush(st, ctl, wp, wk, wi, cap);
   tot = warp_sum_u128(tot);
   above_m = warp_sum_u128(above_m);
   win_m = warp_sum_u128(win_m);
