@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-c64", action="store_true")
+    ap.add_argument("--no-ring", action="store_true", help="skip the ring u3/cz (fusion) leg")
     ap.add_argument("--serve-requests", type=int, default=128,
                     help="requests of the serving stream measured (0: skip the serving leg)")
     return ap.parse_args()
@@ -268,6 +269,8 @@ def run_ours(args, rank, world):
         res["e2e"] = run_e2e(args, rank, dev, stream)
     if args.serve_requests > 0:
         res["serving"] = run_serving(args, rank, dev, stream)
+    if not args.no_ring:
+        res["ring"] = run_ring(args, dev, stream)
     return res, peaks
 
 
@@ -380,6 +383,39 @@ def run_serving(args, rank, dev, stream):
         "peaks_equal_to_serial_c128": f"{same_peak}/{R}",
         "served_results_equal_to_saturated_run": f"{same_open}/{R}",
     }
+
+
+def run_ring(args, dev, stream):
+    """The ring-connected u3/cz workload shaped like the paper's example
+    (44 qubits, 93 (u3, u3, cz) blocks walking the ring, their perturbed
+    mirror, X on a seeded hidden string: about 580 instructions), run whole
+    through the single-state complex128 path as given, after reordering and
+    fusion into 2-qubit blocks (one update and truncation per block), and
+    fused into blocks of up to 4 qubits: gates or blocks, wall time, and
+    whether the peak is the hidden string."""
+    import torch
+    from paper_2607_07816_b300 import fusion, qasm, sv
+
+    c = qasm.sharp_peak_circuit(n=44, blocks=93, K=32)
+    variants = {"as_given": c.gates, "reordered_fused2": fusion.prepare(c.gates, 2),
+                "fused4": fusion.fuse(c.gates, 4)}
+    out = {"instructions": len(c.gates)}
+    for K in (32, 1 << 10):
+        for name, gates in variants.items():
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            st = sv.SparseState(c.n, K, 1.0, prec=sv.SV_C128, stream=stream.cuda_stream)
+            for (q, u) in gates:
+                st.apply_gate(q, u)
+                st.truncate()
+            key, pr = st.peak()
+            F = st.retained_mass()
+            st.close()
+            torch.cuda.synchronize(dev)
+            out[f"{name}_K{K}"] = {"updates": len(gates), "wall_ms": round(1e3 * (time.perf_counter() - t0), 2),
+                                   "peak_is_hidden": bool(key == c.hidden), "peak_prob": pr,
+                                   "retained_mass": F}
+    return out
 
 
 def roofline(main, prec, peaks):
@@ -547,6 +583,8 @@ def main():
         line["e2e"] = res["e2e"]
     if "serving" in res:
         line["serving"] = res["serving"]
+    if "ring" in res:
+        line["ring_u3cz"] = res["ring"]
     if not args.no_cpu and world == 1:
         line["cpu_baseline"] = oracle_sample(seconds=15.0, K_cap=args.K)
         line["cpu_baseline"]["cores"] = 1

@@ -235,3 +235,19 @@ def test_brickwork_local_and_global_gates(sv, oracle_mod, prec):
     run_both(c.gates, g, o, check_every=False)
     st = g.stats()
     assert st["local_gates"] > 0 and st["global_gates"] > 0
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_ring_u3cz_reordered_and_fused(sv, oracle_mod, prec):
+    """The ring-connected u3/cz workload after reordering and fusion into
+    two-qubit blocks (one update and one truncation per block), GPU against
+    the oracle on the same block list."""
+    from paper_2607_07816_b300 import fusion, qasm
+    c = qasm.sharp_peak_circuit(n=44, blocks=93, K=32)
+    blocks = fusion.prepare(c.gates, 2)
+    g = sv.SparseState(c.n, c.K, 1.0, prec=prec)
+    o = oracle_mod.Oracle(c.n, c.K, 1.0, prec=prec)
+    run_both(blocks, g, o, check_every=False)
+    gq = sv.SparseState(c.n, 1 << 12, 1.0, prec=prec)
+    oq = oracle_mod.Oracle(c.n, 1 << 12, 1.0, prec=prec)
+    run_both(fusion.fuse(c.gates, 4), gq, oq, check_every=False)
