@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-c64", action="store_true")
     ap.add_argument("--no-ring", action="store_true", help="skip the ring u3/cz (fusion) leg")
+    ap.add_argument("--no-ab", action="store_true", help="skip the group-first / expand-first comparison")
     ap.add_argument("--serve-requests", type=int, default=128,
                     help="requests of the serving stream measured (0: skip the serving leg)")
     return ap.parse_args()
@@ -271,6 +272,8 @@ def run_ours(args, rank, world):
         res["serving"] = run_serving(args, rank, dev, stream)
     if not args.no_ring:
         res["ring"] = run_ring(args, dev, stream)
+    if not args.no_ab:
+        res["variant_ab"] = run_variant_ab(args, rank, dev, stream)
     return res, peaks
 
 
@@ -383,6 +386,44 @@ def run_serving(args, rank, dev, stream):
         "peaks_equal_to_serial_c128": f"{same_peak}/{R}",
         "served_results_equal_to_saturated_run": f"{same_open}/{R}",
     }
+
+
+def run_variant_ab(args, rank, dev, stream, steps=8):
+    """Group-first (default) against expand-first (the paper's formulation:
+    one record per term and output, sorted, then summed per output) on the
+    benchmark state at K terms: the same gates, alternating blocks of steps,
+    CUDA-event time per step (gate + truncation) on the library's stream."""
+    import torch
+    from paper_2607_07816_b300 import circuits as C
+    from paper_2607_07816_b300 import sv
+
+    circ = C.brickwork_n40(seed=SEED + rank, layers=LAYERS, K=args.K)
+    st = sv.SparseState(circ.n, args.K, 1.0, prec=sv.SV_C128, stream=stream.cuda_stream)
+    gi = 0
+    while gi < len(circ.gates) and st.num_terms() < args.K:
+        q, u = circ.gates[gi]
+        st.apply_gate(q, u)
+        st.truncate()
+        gi += 1
+    ms = {0: [], 1: []}
+    for rep in range(2):
+        for variant in (0, 1):
+            st.set_variant(variant)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            for _ in range(steps // 2):
+                q, u = circ.gates[gi % len(circ.gates)]
+                gi += 1
+                st.apply_gate(q, u)
+                st.truncate()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms[variant].append(e0.elapsed_time(e1) / (steps // 2))
+    st.close()
+    g, e = statistics.mean(ms[0]), statistics.mean(ms[1])
+    return {"K": args.K, "steps_each": steps, "group_first_ms_per_step": round(g, 3),
+            "expand_first_ms_per_step": round(e, 3), "expand_over_group": round(e / g, 3)}
 
 
 def run_ring(args, dev, stream):
@@ -585,6 +626,8 @@ def main():
         line["serving"] = res["serving"]
     if "ring" in res:
         line["ring_u3cz"] = res["ring"]
+    if "variant_ab" in res:
+        line["apply_variant_ab"] = res["variant_ab"]
     if not args.no_cpu and world == 1:
         line["cpu_baseline"] = oracle_sample(seconds=15.0, K_cap=args.K)
         line["cpu_baseline"]["cores"] = 1

@@ -157,6 +157,17 @@ sv_status sv_last_stats(const sv_state* s, sv_stats* out);
 sv_status sv_set_timing(sv_state* s, int enable);
 sv_status sv_phase_times(const sv_state* s, double* ms, uint64_t* launches);
 
+/* Gate application variant for the handle's next gates: 0 (default)
+ * group-first -- sort the terms once with the gate bits moved to the bottom,
+ * then expand each partner group to its 2^m outputs inside the mat-vec (and
+ * the bucket-local path where it applies); 1 expand-first -- the paper's
+ * formulation (Sec. IV-A): every term contributes one record to each of its
+ * 2^m outputs, the records are sorted by (output, source gate bits) and each
+ * output's contributions are summed in ascending source order.  Both give
+ * the same terms and amplitudes bit for bit; expand-first sorts 2^m times as
+ * many records and exists for comparison.  SV_E_ARG for other values. */
+sv_status sv_set_apply_variant(sv_state* s, int variant);
+
 /* Number of CUDA kernels this library has launched in this process. */
 uint64_t sv_launch_count(void);
 
@@ -184,8 +195,9 @@ typedef struct {
 } svb_gate;
 
 /* Create a batch with room for max_slots (1..1023) circuits, amplitude
- * precision prec, a cudaStream_t (NULL = legacy default) and an allocator
- * (NULL = cudaMalloc). */
+ * precision prec, a cudaStream_t (NULL: the handle creates a stream of its
+ * own; every call returns when the work it needs is complete) and an
+ * allocator (NULL = cudaMalloc). */
 sv_status svb_create(int max_slots, int prec, void* cuda_stream, const sv_allocator* alloc, svb_state** out);
 sv_status svb_destroy(svb_state* b);
 /* Add a circuit in the state |0...0>; *slot receives its slot (the lowest
@@ -221,6 +233,15 @@ sv_status svb_set_autotune(svb_state* b, int on);
 /* Timed trials so far, step classes seen, and classes whose every shape has
  * been timed (the tuner has settled them). */
 sv_status svb_autotune_stats(const svb_state* b, uint64_t* trials, uint64_t* classes, uint64_t* settled);
+/* CUDA graphs (on by default): once a step's launch shapes are settled, each
+ * of its two enqueued parts (gate table upload through the first select
+ * levels; compaction and read-back) is captured into a graph the first time
+ * its sizes, shapes and buffers occur, and replayed when they recur (steps
+ * of circuits at their K repeat exactly).  Off: direct launches.  Results
+ * are the same either way. */
+sv_status svb_set_graphs(svb_state* b, int on);
+/* Graphs captured and graph launches so far. */
+sv_status svb_graph_stats(const svb_state* b, uint64_t* captures, uint64_t* launches);
 
 /* Peak readout that allocates nothing.  The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc where they need

@@ -73,6 +73,15 @@ struct GateParams {
   int vbits;           // > 0: sort keys carry the term index in their low vbits bits (no index array)
 };
 
+// Expand-first gate application (Sec. IV-A as the paper states it): records
+// (output sort key << m | source r, source index) for every term and output,
+// and the per-output reduction over the sorted records.
+void launch_expand_records(const uint64_t* keys, uint64_t n, const GateParams& gp, uint64_t* sk, uint32_t* sidx,
+                           uint32_t* hist, int passes, cudaStream_t st);
+void launch_segment_reduce(int prec, const uint64_t* sk, const uint32_t* sidx, uint64_t nrec, const uint32_t* heads,
+                           const void* amps_in, const GateParams& gp, uint64_t* keys_out, void* amps_out,
+                           uint64_t* probs_out, uint64_t* lookback, Ctl* ctl, uint64_t max_tiles, cudaStream_t st);
+
 void launch_gate_keys(const uint64_t* keys, uint64_t n, const GateParams& gp, uint64_t* sk,
                       uint32_t* sv_out, uint32_t* hist, int passes, cudaStream_t st);
 

@@ -65,6 +65,7 @@ struct sv_state {
 
   // bucket-contiguity of the state (see local.cu)
   bool bucket_ok = false;       // terms equal on the bucket qubits are adjacent
+  int variant = 0;              // 0: group-first (sort terms, expand in the mat-vec); 1: expand-first
   uint64_t pmask = 0;           // bucket qubits
   int tbits = 0;
   int plist[64] = {};           // bucket qubits, most significant first
@@ -533,7 +534,8 @@ sv_status sv_apply_gate(sv_state* s, int m, const int* qubits, const double* U) 
   if (rc != SV_OK) return rc;
   const int alt = 1 - s->cur;
   const uint64_t qmask = gp.qmask;
-  bool local = s->bucket_ok && (s->pmask & qmask) == 0 && (s->tbits > 0 || N <= LOCAL_BUCKET_MAX);
+  bool local = s->variant == 0 && s->bucket_ok && (s->pmask & qmask) == 0 &&
+               (s->tbits > 0 || N <= LOCAL_BUCKET_MAX);
   if (local && s->tbits > 0 && (s->max_bucket == 0 || s->max_bucket > LOCAL_BUCKET_MAX)) {
     // the bound is unknown or too loose: measure the buckets exactly
     ph_begin(s, PH_LOCAL);
@@ -586,6 +588,45 @@ sv_status sv_apply_gate(sv_state* s, int m, const int* qubits, const double* U) 
         s->N = npre;
       }
     }
+  }
+  if (!done && s->variant == 1) {
+    // expand-first: one record per (term, output) pair, sorted by (output, source r), then
+    // one fused multiply-add chain per output
+    ++s->global_gates;
+    const uint64_t nrec = N << m;
+    rc = ensure_sort_cap(s, nrec);
+    const uint64_t red_tiles = nrec / 1024 + 2;
+    if (rc == SV_OK) rc = ensure_lookback(s, red_tiles + 16);
+    if (rc != SV_OK) return rc;
+    s->tbits = 0;
+    s->pmask = 0;
+    rc = upload_perm(s, gp);
+    if (rc != SV_OK) return rc;
+    const int nbits = s->n + m;
+    const int passes = (nbits + RADIX_BITS - 1) / RADIX_BITS;
+    ph_begin(s, PH_KEYS);
+    launch_expand_records(s->keys[s->cur], N, gp, s->sk[0], s->sidx[0], s->hist, passes, s->st);
+    ph_end(s, PH_KEYS);
+    launched(s, PH_KEYS, 1);
+    int w = 0, run = 0;
+    rc = sort_pairs(s, nrec, nbits, true, &w, &run);
+    if (rc != SV_OK) return rc;
+    s->stats.sort_passes = (uint32_t)run;
+    ph_begin(s, PH_HEADS);
+    launch_group_heads(s->sk[w], nrec, m, s->heads, s->lookback, s->ctl, s->st);
+    ph_end(s, PH_HEADS);
+    ph_begin(s, PH_APPLY);
+    launch_segment_reduce(s->prec, s->sk[w], s->sidx[w], nrec, s->heads, s->amps[s->cur], gp, s->keys[alt],
+                          s->amps[alt], s->probs[alt], s->lookback, s->ctl, red_tiles, s->st);
+    ph_end(s, PH_APPLY);
+    launched(s, PH_HEADS, 1);
+    launched(s, PH_APPLY, 1);
+    rc = sync_ctl(s, "sv_apply_gate");
+    if (rc != SV_OK) return rc;
+    s->cur = alt;
+    s->N = s->ctl_host->count[1];
+    s->bucket_ok = false;
+    done = true;
   }
   if (!done) {
     ++s->global_gates;
@@ -938,6 +979,14 @@ const char* sv_last_error(const sv_state* s) {
 sv_status sv_last_stats(const sv_state* s, sv_stats* out) {
   if (!s || !out) return SV_E_ARG;
   *out = s->stats;
+  return SV_OK;
+}
+
+sv_status sv_set_apply_variant(sv_state* s, int variant) {
+  SV_GUARD(s);
+  if (variant != 0 && variant != 1) return fail(s, SV_E_ARG, "sv_set_apply_variant: variant must be 0 or 1");
+  s->variant = variant;
+  if (variant == 1) s->bucket_ok = false;
   return SV_OK;
 }
 

@@ -26,7 +26,7 @@ EXPORTED = ["sv_create", "sv_create_ex", "sv_destroy", "sv_apply_gate", "sv_trun
             "sv_last_stats", "sv_set_timing", "sv_phase_times", "sv_launch_count", "sv_transfer_bytes", "sv_peak_noalloc",
             "svb_create", "svb_destroy", "svb_add", "svb_remove", "svb_step", "svb_num_terms",
             "svb_retained_mass", "svb_peak", "svb_export", "svb_last_error", "svb_set_autotune",
-            "svb_autotune_stats", "svb_set_graphs", "svb_graph_stats", "sv_selftest"]
+            "svb_autotune_stats", "svb_set_graphs", "svb_graph_stats", "sv_selftest", "sv_set_apply_variant"]
 PHASES = ["keys", "sort", "heads", "apply", "select", "compact", "peak", "other", "window", "local"]
 
 
@@ -137,6 +137,8 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.svb_graph_stats.argtypes = [vp, P(u64), P(u64)]
     lib.sv_peak_noalloc.restype = i32
     lib.sv_peak_noalloc.argtypes = [i32, vp, vp, u64, vp, P(u64), P(dbl)]
+    lib.sv_set_apply_variant.restype = i32
+    lib.sv_set_apply_variant.argtypes = [vp, i32]
     lib.sv_selftest.restype = i32
     lib.sv_selftest.argtypes = [i32, u64, u64, P(u64), P(u64)]
     lib.sv_transfer_bytes.restype = None
@@ -291,6 +293,10 @@ def sv_selftest(which: int, n: int, seed: int = 1):
     return bad.value, (None if first.value == (1 << 64) - 1 else first.value)
 
 
+def sv_set_apply_variant(h: int, variant: int) -> None:
+    _check(h, load_library().sv_set_apply_variant(ctypes.c_void_p(h), int(variant)))
+
+
 # ------------------------------------------------ convenience wrapper
 class SparseState:
     """A device-resident sparse state: keys u64, amplitudes complex128
@@ -340,6 +346,10 @@ class SparseState:
 
     def set_timing(self, enable: bool = True) -> None:
         sv_set_timing(self.h, enable)
+
+    def set_variant(self, variant: int) -> None:
+        """0: group-first (default), 1: expand-first (see include/sv.h)."""
+        sv_set_apply_variant(self.h, variant)
 
     def phase_times(self) -> dict:
         return sv_phase_times(self.h)

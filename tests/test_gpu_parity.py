@@ -251,3 +251,26 @@ def test_ring_u3cz_reordered_and_fused(sv, oracle_mod, prec):
     gq = sv.SparseState(c.n, 1 << 12, 1.0, prec=prec)
     oq = oracle_mod.Oracle(c.n, 1 << 12, 1.0, prec=prec)
     run_both(fusion.fuse(c.gates, 4), gq, oq, check_every=False)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_expand_first_variant_matches_oracle_and_group_first(sv, oracle_mod, prec):
+    """The paper's expand-first formulation gives the oracle's result bit for
+    bit, and the same storage order as the group-first path."""
+    rng = np.random.default_rng(640 + prec)
+    for trial in range(3):
+        n = int(rng.integers(8, 30))
+        K = int(rng.choice([50, 3000, 1 << 16]))
+        gates = [C.random_gate(n, int(rng.integers(1, 5)) if n >= 4 else 1, rng,
+                               str(rng.choice(["haar", "mcx", "h"]))) for _ in range(16)]
+        e = sv.SparseState(n, K, 1.0, prec=prec)
+        e.set_variant(1)
+        o = oracle_mod.Oracle(n, K, 1.0, prec=prec)
+        run_both(gates, e, o)
+        g = sv.SparseState(n, K, 1.0, prec=prec)
+        g.run(gates)
+        ek, ea = e.export()
+        gk, ga = g.export()
+        assert np.array_equal(ek, gk) and np.array_equal(ea, ga)
+    with pytest.raises(sv.SVError):
+        e.set_variant(2)
