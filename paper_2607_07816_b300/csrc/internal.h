@@ -139,8 +139,10 @@ struct SelectScratch {
   uint64_t win_cap;
   uint32_t* tile_keep;    // [window tiles] kept terms per tile
   uint64_t* tile_off;     // [window tiles] output offset per tile
+  uint32_t* keep_bits;    // [window tiles * WINDOW_TILE / 32] keep flag of every term
   uint64_t tiles_cap;
 };
+constexpr int WINDOW_TILE = 2048;  // terms per tile of the window pass and windowed compaction
 
 // Number of tiles of the window pass (and of the windowed compaction).
 uint64_t window_tiles(uint64_t n);

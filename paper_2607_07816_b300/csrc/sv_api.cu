@@ -470,6 +470,12 @@ sv_status sv_destroy(sv_state* s) {
   dev_free(s, s->ss.hist_count);
   dev_free(s, s->ss.hist_mass);
   dev_free(s, s->ss.buf);
+  dev_free(s, s->ss.win_p);
+  dev_free(s, s->ss.win_k);
+  dev_free(s, s->ss.win_i);
+  dev_free(s, s->ss.tile_keep);
+  dev_free(s, s->ss.tile_off);
+  dev_free(s, s->ss.keep_bits);
   for (int ph = 0; ph < PH_COUNT; ++ph) {
     if (s->ev_beg[ph]) cudaEventDestroy(s->ev_beg[ph]);
     if (s->ev_end[ph]) cudaEventDestroy(s->ev_end[ph]);
@@ -709,9 +715,11 @@ sv_status ensure_window_cap(sv_state* s, uint64_t N) {
     uint64_t cap = tiles + tiles / 2 + 64;
     dev_free(s, s->ss.tile_keep);
     dev_free(s, s->ss.tile_off);
+    dev_free(s, s->ss.keep_bits);
     s->ss.tile_keep = (uint32_t*)dev_alloc(s, cap * 4);
     s->ss.tile_off = (uint64_t*)dev_alloc(s, cap * 8);
-    if (!s->ss.tile_keep || !s->ss.tile_off) {
+    s->ss.keep_bits = (uint32_t*)dev_alloc(s, cap * (WINDOW_TILE / 32) * 4);
+    if (!s->ss.tile_keep || !s->ss.tile_off || !s->ss.keep_bits) {
       s->ss.tiles_cap = 0;
       return fail(s, SV_E_NOMEM, "select tile table allocation failed");
     }

@@ -228,6 +228,7 @@ __global__ void __launch_bounds__(SAMPLE_THREADS) k_sample_window(const uint64_t
 }
 
 constexpr int WP_BLOCK = 256, WP_ITEMS = 8;
+static_assert(WP_BLOCK * WP_ITEMS == WINDOW_TILE, "window tiling");
 constexpr int WP_TILE = WP_BLOCK * WP_ITEMS;
 
 __device__ __forceinline__ u128 warp_sum_u128(u128 v) {
@@ -285,7 +286,8 @@ __global__ void __launch_bounds__(WP_BLOCK, 4) k_window_pass(const uint64_t* __r
                                                           const uint64_t* __restrict__ keys, uint64_t n,
                                                           Ctl* ctl, uint64_t* __restrict__ wp,
                                                           uint64_t* __restrict__ wk, uint32_t* __restrict__ wi,
-                                                          uint64_t cap, uint32_t* __restrict__ tile_keep) {
+                                                          uint64_t cap, uint32_t* __restrict__ tile_keep,
+                                                          uint32_t* __restrict__ keep_bits) {
   typedef TileLayout<WP_BLOCK, WP_ITEMS> L;
   __shared__ uint32_t s_warp[WP_BLOCK / 32];
   __shared__ uint32_t s_above[WP_BLOCK / 32];
@@ -325,6 +327,11 @@ __global__ void __launch_bounds__(WP_BLOCK, 4) k_window_pass(const uint64_t* __r
         wmask |= 1u << j;
       }
       run += __popc(__ballot_sync(0xffffffffu, inwin));
+      // terms above the window are kept whatever the exact cut: one flag word
+      // per 32 consecutive terms (window terms kept by the cut are added later)
+      const uint32_t kb = __ballot_sync(0xffffffffu, above);
+      const uint64_t row = L::index(base, j) - lane;
+      if (lane == 0 && row < n) keep_bits[row >> 5] = kb;
     }
     above_c += tile_above;
 #pragma unroll
@@ -447,7 +454,7 @@ void launch_select_window(const uint64_t* probs, const uint64_t* keys, uint64_t 
   uint64_t grid = tiles < 148 * 8 ? tiles : 148 * 8;
   if (grid == 0) grid = 1;
   k_window_pass<<<(unsigned)grid, WP_BLOCK, 0, st>>>(probs, keys, n, ctl, ss.win_p, ss.win_k, ss.win_i,
-                                                     ss.win_cap, ss.tile_keep);
+                                                     ss.win_cap, ss.tile_keep, ss.keep_bits);
   k_window_decide<<<1, 1, 0, st>>>(ctl, mode, count_target, p, ss.win_cap);
 }
 
@@ -458,13 +465,17 @@ uint64_t window_tiles(uint64_t n) { return (n + WP_TILE - 1) / WP_TILE; }
 // the window plus its window terms not after the cut.
 __global__ void k_window_tile_counts(const uint64_t* __restrict__ wp, const uint64_t* __restrict__ wk,
                                      const uint32_t* __restrict__ wi, Ctl* ctl,
-                                     uint32_t* __restrict__ tile_keep) {
+                                     uint32_t* __restrict__ tile_keep, uint32_t* __restrict__ keep_bits) {
   const uint64_t wn = ctl->win_n;
   const uint64_t pc = ctl->cut_pbits, kc = ctl->cut_key;
   for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < wn;
        j += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t pb = wp[j];
-    if (pb > pc || (pb == pc && wk[j] <= kc)) atomicAdd(&tile_keep[wi[j] / WP_TILE], 1u);
+    if (pb > pc || (pb == pc && wk[j] <= kc)) {
+      const uint32_t i = wi[j];
+      atomicAdd(&tile_keep[i / WP_TILE], 1u);
+      atomicOr(&keep_bits[i >> 5], 1u << (i & 31));
+    }
   }
 }
 
@@ -750,31 +761,31 @@ __global__ void __launch_bounds__(TC_BLOCK) k_truncate_compact(
 
 // Windowed compaction: tile t (same tiling as the window pass) writes its
 // kept terms from tile_off[t] on, in input order; no cross-tile waiting.
+// The keep flags come from the window pass (terms above the window) and the
+// window's own cut decisions, one bit per term, so only the kept terms' keys
+// and amplitudes are read.
 template <typename C2>
 __global__ void __launch_bounds__(WP_BLOCK) k_truncate_write(
-    const uint64_t* __restrict__ keys, const C2* __restrict__ amps, const uint64_t* __restrict__ probs,
+    const uint64_t* __restrict__ keys, const C2* __restrict__ amps, const uint32_t* __restrict__ keep_bits,
     uint64_t n, const uint64_t* __restrict__ tile_off, uint64_t* __restrict__ keys_out,
     C2* __restrict__ amps_out, uint64_t* __restrict__ probs_out, const Ctl* ctl) {
   typedef TileLayout<WP_BLOCK, WP_ITEMS> L;
   __shared__ CompactShared<WP_BLOCK> cs;
-  const uint64_t pc = ctl->cut_pbits, kc = ctl->cut_key;
   const double s = ctl->scale;
+  const int lane = threadIdx.x & 31;
   const uint64_t tiles = (n + L::TILE - 1) / L::TILE;
   for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const uint64_t base = tile * L::TILE;
-    uint64_t pbv[WP_ITEMS];
+    uint32_t words[WP_ITEMS];
 #pragma unroll
     for (int j = 0; j < WP_ITEMS; ++j) {
-      const uint64_t i = L::index(base, j);
-      pbv[j] = i < n ? probs[i] : 0ull;
+      const uint64_t row = L::index(base, j) - lane;
+      words[j] = row < n ? keep_bits[row >> 5] : 0u;
     }
     bool flag[WP_ITEMS];
     uint32_t pos[WP_ITEMS];
 #pragma unroll
-    for (int j = 0; j < WP_ITEMS; ++j) {
-      const uint64_t i = L::index(base, j);
-      flag[j] = i < n && (pbv[j] > pc || (pbv[j] == pc && keys[i] <= kc));
-    }
+    for (int j = 0; j < WP_ITEMS; ++j) flag[j] = L::index(base, j) < n && ((words[j] >> lane) & 1u);
     tile_local_positions<WP_BLOCK, WP_ITEMS>(flag, pos, cs);
     const uint64_t ob = tile_off[tile];
 #pragma unroll
@@ -795,18 +806,19 @@ __global__ void __launch_bounds__(WP_BLOCK) k_truncate_write(
 void launch_truncate_windowed(int prec, const uint64_t* keys, const void* amps, const uint64_t* probs,
                               uint64_t n, uint64_t* keys_out, void* amps_out, uint64_t* probs_out,
                               const SelectScratch& ss, Ctl* ctl, cudaStream_t st) {
+  (void)probs;  // the keep flags replace the probabilities here
   const uint64_t tiles = window_tiles(n);
   k_set_scale<<<1, 1, 0, st>>>(ctl);
-  k_window_tile_counts<<<148 * 4, 256, 0, st>>>(ss.win_p, ss.win_k, ss.win_i, ctl, ss.tile_keep);
+  k_window_tile_counts<<<148 * 4, 256, 0, st>>>(ss.win_p, ss.win_k, ss.win_i, ctl, ss.tile_keep, ss.keep_bits);
   k_tile_scan<<<1, 1024, 0, st>>>(ss.tile_keep, tiles, ss.tile_off, ctl);
   uint64_t grid = tiles < 148 * 8 ? tiles : 148 * 8;
   if (grid == 0) grid = 1;
   if (prec == 0)
     k_truncate_write<double2><<<(unsigned)grid, WP_BLOCK, 0, st>>>(
-        keys, (const double2*)amps, probs, n, ss.tile_off, keys_out, (double2*)amps_out, probs_out, ctl);
+        keys, (const double2*)amps, ss.keep_bits, n, ss.tile_off, keys_out, (double2*)amps_out, probs_out, ctl);
   else
     k_truncate_write<float2><<<(unsigned)grid, WP_BLOCK, 0, st>>>(
-        keys, (const float2*)amps, probs, n, ss.tile_off, keys_out, (float2*)amps_out, probs_out, ctl);
+        keys, (const float2*)amps, ss.keep_bits, n, ss.tile_off, keys_out, (float2*)amps_out, probs_out, ctl);
 }
 
 void launch_truncate_compact(int prec, const uint64_t* keys, const void* amps, const uint64_t* probs,
