@@ -274,3 +274,29 @@ def test_expand_first_variant_matches_oracle_and_group_first(sv, oracle_mod, pre
         assert np.array_equal(ek, gk) and np.array_equal(ea, ga)
     with pytest.raises(sv.SVError):
         e.set_variant(2)
+
+
+def test_handles_release_device_memory(sv):
+    """Creating, using and destroying handles (plain and batched) returns
+    their device memory: the free memory after many cycles matches the
+    free memory after the first (allocator caches aside, nothing grows)."""
+    import torch
+    c = C.brickwork_circuit(22, 2, seed=9, sigma=0.05, K=1 << 14, p=0.99)
+
+    def cycle():
+        g = sv.SparseState(c.n, c.K, c.p)
+        g.run(c.gates)
+        g.close()
+        b = sv.Batch(8, prec=1)
+        s = b.add(c.n, c.K)
+        for (q, u) in c.gates[:6]:
+            b.step([(s, q, u)])
+        b.close()
+        torch.cuda.synchronize()
+
+    cycle()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(8):
+        cycle()
+    free1 = torch.cuda.mem_get_info()[0]
+    assert free0 - free1 < 32 << 20, (free0, free1)
