@@ -15,7 +15,6 @@ constexpr int SORT_THREADS = 512;
 constexpr int SORT_ITEMS = 8;
 constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;
 constexpr int APPLY_BLOCK = 256;
-constexpr int APPLY_TILE = 1024;  // output slots per tile of the group mat-vec (multiple of 16)
 
 // Scratch used by one LSD radix sort.
 struct SortScratch {
@@ -92,8 +91,9 @@ void launch_group_heads(const uint64_t* sk, uint64_t n, int shift, uint32_t* hea
 
 // Per-group mat-vec + zero drop; writes candidates and their probabilities,
 // the candidate count lands in ctl->count[1].
+uint64_t gate_apply_tiles(uint64_t n, int m);
 void launch_gate_apply(int prec, const uint64_t* sk, const uint32_t* sidx, uint64_t n,
-                       const uint32_t* heads, const void* amps_in, const GateParams& gp,
+                       const uint32_t* heads, const void* amps_in, const uint64_t* keys_in, const GateParams& gp,
                        uint64_t* keys_out, void* amps_out, uint64_t* probs_out, uint64_t* lookback,
                        Ctl* ctl, cudaStream_t st, uint64_t max_tiles);
 

@@ -535,7 +535,7 @@ sv_status sv_apply_gate(sv_state* s, int m, const int* qubits, const double* U) 
     return fail(s, SV_E_ARG, "sv_apply_gate: state too large for 32-bit term indices");
   sv_status rc = ensure_state_cap(s, N << m);
   if (rc == SV_OK) rc = ensure_sort_cap(s, N);
-  const uint64_t apply_tiles = ((N << m) + APPLY_TILE - 1) / APPLY_TILE + 1;
+  const uint64_t apply_tiles = gate_apply_tiles(N, m);
   if (rc == SV_OK) rc = ensure_lookback(s, apply_tiles + 16);
   if (rc != SV_OK) return rc;
   const int alt = 1 - s->cur;
@@ -667,7 +667,8 @@ sv_status sv_apply_gate(sv_state* s, int m, const int* qubits, const double* U) 
     launch_group_heads(s->sk[w], N, m + gp.vbits, s->heads, s->lookback, s->ctl, s->st);
     ph_end(s, PH_HEADS);
     ph_begin(s, PH_APPLY);
-    launch_gate_apply(s->prec, s->sk[w], s->sidx[w], N, s->heads, s->amps[s->cur], gp, s->keys[alt],
+    launch_gate_apply(s->prec, s->sk[w], s->sidx[w], N, s->heads, s->amps[s->cur], s->keys[s->cur], gp,
+                      s->keys[alt],
                       s->amps[alt], s->probs[alt], s->lookback, s->ctl, s->st, apply_tiles);
     ph_end(s, PH_APPLY);
     launched(s, PH_HEADS, 1);
