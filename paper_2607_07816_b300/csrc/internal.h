@@ -101,6 +101,8 @@ void launch_gate_apply(int prec, const uint64_t* sk, const uint32_t* sidx, uint6
 // each block takes the buckets that start in its chunk, sorts them in
 // shared memory by the gate's sort key, and writes its outputs into one
 // atomically reserved range sized by the structurally nonzero outputs.
+// The library uses it with no bucket qubits for states of at most
+// LOCAL_BUCKET_MAX terms (one block does the whole gate).
 // Exact-zero outputs that the structure did not predict are written with a
 // zero amplitude and counted in ctl->count[3] (removed by
 // launch_drop_zero_terms).  Output count in ctl->count[1]; a bucket larger
@@ -110,15 +112,6 @@ constexpr int LOCAL_CAP = 8192;
 constexpr uint64_t LOCAL_BUCKET_MAX = LOCAL_CAP - LOCAL_CHUNK;
 void launch_local_gate(int prec, const uint64_t* keys, const void* amps, uint64_t n, const GateParams& gp,
                        uint64_t* keys_out, void* amps_out, uint64_t* probs_out, Ctl* ctl, cudaStream_t st);
-// Number of keys with each bit set (counts[0..63], device), for choosing
-// balanced bucket qubits.
-// Sample positions of the bit statistics for n keys (every *stride-th key).
-uint64_t bit_count_sample(uint64_t n, uint64_t* stride);
-void launch_bit_counts(const uint64_t* keys, uint64_t n, int nbits, uint64_t* counts, cudaStream_t st);
-// Exact size of the largest bucket (up to limit; longer: limit + 1) into
-// ctl->count[0].
-void launch_bucket_check(const uint64_t* keys, uint64_t n, uint64_t pmask, uint64_t limit, Ctl* ctl,
-                         cudaStream_t st);
 // Order-preserving removal of zero-amplitude terms (count in ctl->count[2]).
 void launch_drop_zero_terms(int prec, const uint64_t* keys, const void* amps, const uint64_t* probs,
                             uint64_t n, uint64_t* keys_out, void* amps_out, uint64_t* probs_out,

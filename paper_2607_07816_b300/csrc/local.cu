@@ -1,22 +1,21 @@
-// Local gate application on a bucket-contiguous state.
+// Local gate application inside shared memory.
 //
-// The state keeps every bucket -- the terms that agree on a set P of bucket
-// qubits -- contiguous.  A gate whose qubits are all outside P only combines
-// terms of the same bucket (partners differ only in the gate qubits, Sec. I
-// and Sec. IV-A), so whole buckets can be processed independently: one
-// block loads the buckets that start in its chunk of the state, sorts them
-// in shared memory by the gate's sort key (P on top, the gate qubits at the
-// bottom in local-index order), finds the partner groups, computes each
-// output y[r'] = sum over present r ascending of U[r'][r] x[r] (Eq. 3 with
-// the same fused multiply-add order as the rest of the library) and writes
-// the outputs of the batch into one contiguous range.  The range is reserved
-// with one atomic add, sized by the outputs that are structurally nonzero (a
-// present input meets a nonzero entry of U's row); outputs that cancel
-// exactly are written with a zero amplitude and counted, and a later
-// order-preserving pass drops them.  Outputs keep the bucket bits, so the
-// result is again bucket-contiguous; the order of batches in the output is
-// not fixed, which changes no result (truncation and readout do not depend on
-// the order of terms).
+// A gate whose qubits avoid a set P of bucket qubits only combines terms that
+// agree on P (partners differ only in the gate qubits, Sec. I and Sec.
+// IV-A), so on a state where such buckets are contiguous, whole buckets can
+// be processed independently: one block loads the buckets that start in its
+// chunk of the state, sorts them in shared memory by the gate's sort key (P
+// on top, the gate qubits at the bottom in local-index order), finds the
+// partner groups, computes each output y[r'] = sum over present r ascending
+// of U[r'][r] x[r] (Eq. 3 with the same fused multiply-add order as the rest
+// of the library) and writes the outputs of the batch into one contiguous
+// range.  The range is reserved with one atomic add, sized by the outputs
+// that are structurally nonzero (a present input meets a nonzero entry of
+// U's row); outputs that cancel exactly are written with a zero amplitude
+// and counted, and a later order-preserving pass drops them.  The library
+// runs it with P empty on states of at most one batch (a single launch for
+// the whole gate); larger states take the sorted path, which measured as
+// fast or faster on this GPU.
 #include "c64_exact.cuh"
 #include "internal.h"
 #include "tile.cuh"
@@ -373,111 +372,6 @@ void launch_local_gate(int prec, const uint64_t* keys, const void* amps, uint64_
   else
     k_local_gate<float><<<(unsigned)grid, LG_THREADS, sizeof(LocalSmem<float>), st>>>(
         keys, (const float2*)amps, n, gp, keys_out, (float2*)amps_out, probs_out, ctl);
-}
-
-// ---------------------------------------------------------------- bucket sizes
-// Largest bucket of a bucket-contiguous state (terms equal on pmask are
-// adjacent), exact up to `limit` (longer buckets report limit + 1).  Each warp
-// walks its region 32 terms at a time; a ballot marks bucket starts and the
-// warp closes every bucket at the next start.  The bucket still open at the
-// region end is closed by reading on past it; a leading bucket that started
-// in an earlier region is left to the warp that saw its start.
-__global__ void __launch_bounds__(256) k_bucket_check(const uint64_t* __restrict__ keys, uint64_t n,
-                                                      uint64_t pmask, uint64_t region, uint64_t limit,
-                                                      Ctl* ctl) {
-  const int lane = threadIdx.x & 31;
-  const uint64_t wid = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
-  const uint64_t r0 = wid * region;
-  if (r0 >= n) return;
-  const uint64_t r1 = r0 + region < n ? r0 + region : n;
-  int64_t cur = r0 == 0 ? 0 : -1;  // start of the open bucket (-1: none seen yet)
-  uint64_t best = 0;
-  for (uint64_t b = r0;; b += 32) {
-    if (b >= n) {
-      if (cur >= 0) best = max(best, n - (uint64_t)cur);
-      break;
-    }
-    const uint64_t i = b + lane;
-    const bool start = i < n && (i == 0 || ((keys[i] ^ keys[i - 1]) & pmask) != 0);
-    uint32_t S = __ballot_sync(0xffffffffu, start);
-    if (b >= r1) {  // past the region: only close the open bucket
-      if (cur < 0) break;
-      if (S) {
-        best = max(best, b + (uint64_t)(__ffs(S) - 1) - (uint64_t)cur);
-        break;
-      }
-      if (b + 32 - (uint64_t)cur > limit) {
-        best = limit + 1;
-        break;
-      }
-      continue;
-    }
-    while (S) {
-      const uint64_t pos = b + (uint64_t)(__ffs(S) - 1);
-      if (cur >= 0) best = max(best, pos - (uint64_t)cur);
-      cur = (int64_t)pos;
-      S &= S - 1u;
-    }
-  }
-  if (best > limit) best = limit + 1;
-  if (lane == 0 && best) atomicMax((unsigned long long*)&ctl->count[0], (unsigned long long)best);
-}
-
-void launch_bucket_check(const uint64_t* keys, uint64_t n, uint64_t pmask, uint64_t limit, Ctl* ctl,
-                         cudaStream_t st) {
-  cudaMemsetAsync(&ctl->count[0], 0, sizeof(uint64_t), st);
-  if (n == 0) return;
-  const uint64_t region = 4096;
-  const uint64_t warps = (n + region - 1) / region;
-  const uint64_t blocks = (warps + 7) / 8;
-  k_bucket_check<<<(unsigned)blocks, 256, 0, st>>>(keys, n, pmask, region, limit, ctl);
-}
-
-// ---------------------------------------------------------------- bit statistics
-// One-counts of the key bits over the sample keys[0], keys[sample_step], ...
-// (n sample positions): bucket bits are chosen for balance, which a sample
-// of about a million keys measures well enough.
-__global__ void __launch_bounds__(256) k_bit_counts(const uint64_t* __restrict__ keys, uint64_t n,
-                                                    uint64_t sample_step, int nbits,
-                                                    unsigned long long* __restrict__ counts) {
-  __shared__ unsigned long long sc[64];
-  if (threadIdx.x < 64) sc[threadIdx.x] = 0;
-  __syncthreads();
-  const int lane = threadIdx.x & 31;
-  uint64_t local = 0;  // lane b keeps the count of bit b (and lane b owns bit b + 32 in `local2`)
-  uint64_t local2 = 0;
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  const uint64_t nround = (n + stride - 1) / stride * stride;
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nround; i += stride) {
-    const uint64_t k = i < n ? keys[i * sample_step] : 0ull;
-    for (int b = 0; b < nbits; ++b) {
-      const uint32_t c = __popc(__ballot_sync(0xffffffffu, (k >> b) & 1ull));
-      if (b < 32) {
-        if (lane == b) local += c;
-      } else if (lane == b - 32) {
-        local2 += c;
-      }
-    }
-  }
-  if (local) atomicAdd(&sc[lane], (unsigned long long)local);
-  if (local2) atomicAdd(&sc[lane + 32], (unsigned long long)local2);
-  __syncthreads();
-  if (threadIdx.x < 64 && sc[threadIdx.x]) atomicAdd(&counts[threadIdx.x], sc[threadIdx.x]);
-}
-
-uint64_t bit_count_sample(uint64_t n, uint64_t* stride) {
-  *stride = n > (1ull << 20) ? n >> 20 : 1;
-  return (n + *stride - 1) / *stride;
-}
-
-void launch_bit_counts(const uint64_t* keys, uint64_t n, int nbits, uint64_t* counts, cudaStream_t st) {
-  cudaMemsetAsync(counts, 0, sizeof(uint64_t) * 64, st);
-  if (n == 0) return;
-  uint64_t stride;
-  const uint64_t ns = bit_count_sample(n, &stride);
-  uint64_t blocks = (ns + 255) / 256;
-  if (blocks > 148 * 4) blocks = 148 * 4;
-  k_bit_counts<<<(unsigned)blocks, 256, 0, st>>>(keys, ns, stride, nbits, (unsigned long long*)counts);
 }
 
 // ---------------------------------------------------------------- zero removal

@@ -64,19 +64,10 @@ struct sv_state {
   sv_stats stats{};
 
   // bucket-contiguity of the state (see local.cu)
-  bool bucket_ok = false;       // terms equal on the bucket qubits are adjacent
   int variant = 0;              // 0: group-first (sort terms, expand in the mat-vec); 1: expand-first
-  uint64_t pmask = 0;           // bucket qubits
-  int tbits = 0;
-  int plist[64] = {};           // bucket qubits, most significant first
-  uint64_t max_bucket = 0;      // upper bound on the largest bucket (0: unknown)
-  uint64_t live = 0;            // superset of the key bits that vary over the state
-  int64_t last_use[64] = {};    // gate index of each qubit's last use (-1: never)
   int64_t gate_index = 0;
   BitPerm* perm_dev = nullptr;
   BitPerm* perm_host = nullptr;
-  uint64_t* bitcnt_dev = nullptr;
-  uint64_t* bitcnt_host = nullptr;
   uint64_t local_gates = 0, global_gates = 0, local_fallbacks = 0;
 
   bool timing = false;
@@ -336,40 +327,12 @@ sv_status canonical_perm(sv_state* s, int* which) {
 // `ones`, the number of terms with each bit set), most recently used first
 // among equals, enough of them that the average bucket of the next state
 // holds about 128 terms.
-void choose_buckets(sv_state* s, uint64_t qmask, uint64_t n_est, const uint64_t* ones, uint64_t N) {
-  int cand[64], nc = 0;
-  double skew[64];
-  for (int b = 0; b < s->n; ++b) {
-    if ((qmask >> b) & 1ull) continue;
-    const double f = N ? (double)ones[b] / (double)N : 0.0;
-    if (f <= 0.0 || f >= 1.0) continue;  // constant bit: useless for bucketing
-    skew[b] = f > 0.5 ? f - 0.5 : 0.5 - f;
-    cand[nc++] = b;
-  }
-  for (int i = 1; i < nc; ++i)
-    for (int j = i; j > 0; --j) {
-      const int a = cand[j - 1], b = cand[j];
-      const bool swap = skew[b] < skew[a] || (skew[b] == skew[a] && s->last_use[b] > s->last_use[a]);
-      if (!swap) break;
-      cand[j - 1] = b;
-      cand[j] = a;
-    }
-  int t = 0;
-  while (t < nc && (n_est >> t) > 128) ++t;
-  s->tbits = t;
-  s->pmask = 0;
-  for (int i = 0; i < t; ++i) {
-    s->plist[i] = cand[i];
-    s->pmask |= 1ull << cand[i];
-  }
-}
-
 sv_status upload_perm(sv_state* s, GateParams& gp) {
-  build_perm(s->n, gp.m, gp.q, s->tbits, s->plist, s->perm_host);
+  build_perm(s->n, gp.m, gp.q, 0, nullptr, s->perm_host);
   gp.perm = s->perm_dev;
   gp.n = s->n;
-  gp.tbits = s->tbits;
-  gp.pmask = s->pmask;
+  gp.tbits = 0;
+  gp.pmask = 0;
   g_h2d += sizeof(BitPerm);
   return cuda_check(s, cudaMemcpyAsync(s->perm_dev, s->perm_host, sizeof(BitPerm), cudaMemcpyHostToDevice, s->st),
                     "gate permutation upload");
@@ -413,16 +376,11 @@ sv_status sv_create_ex(int n, uint64_t K, double p, int prec, void* cuda_stream,
   if (!s->hist || !s->tile_counter || !s->ctl || !s->ss.hist_count || !s->ss.hist_mass || !s->ss.buf)
     rc = SV_E_NOMEM;
   s->perm_dev = (BitPerm*)dev_alloc(s, sizeof(BitPerm));
-  s->bitcnt_dev = (uint64_t*)dev_alloc(s, 64 * sizeof(uint64_t));
-  if (!s->perm_dev || !s->bitcnt_dev) rc = SV_E_NOMEM;
-  if (rc == SV_OK && cudaMallocHost(&s->bitcnt_host, 64 * sizeof(uint64_t)) != cudaSuccess) rc = SV_E_CUDA;
+  if (!s->perm_dev) rc = SV_E_NOMEM;
   if (rc == SV_OK && (cudaMallocHost(&s->hist_host, sizeof(uint32_t) * MAX_PASSES * RADIX) != cudaSuccess ||
                       cudaMallocHost(&s->ctl_host, sizeof(Ctl)) != cudaSuccess ||
                       cudaMallocHost(&s->perm_host, sizeof(BitPerm)) != cudaSuccess))
     rc = SV_E_CUDA;
-  for (int b = 0; b < 64; ++b) s->last_use[b] = -1;
-  s->bucket_ok = true;  // one term: a single bucket (no bucket qubits)
-  s->max_bucket = 1;
   if (rc == SV_OK) rc = ensure_state_cap(s, 4096);
   if (rc == SV_OK) rc = ensure_sort_cap(s, 4096);
   if (rc == SV_OK) {
@@ -483,9 +441,7 @@ sv_status sv_destroy(sv_state* s) {
   if (s->hist_host) cudaFreeHost(s->hist_host);
   if (s->ctl_host) cudaFreeHost(s->ctl_host);
   if (s->perm_host) cudaFreeHost(s->perm_host);
-  if (s->bitcnt_host) cudaFreeHost(s->bitcnt_host);
   dev_free(s, s->perm_dev);
-  dev_free(s, s->bitcnt_dev);
   delete s;
   return SV_OK;
 }
@@ -539,25 +495,14 @@ sv_status sv_apply_gate(sv_state* s, int m, const int* qubits, const double* U) 
   if (rc == SV_OK) rc = ensure_lookback(s, apply_tiles + 16);
   if (rc != SV_OK) return rc;
   const int alt = 1 - s->cur;
-  const uint64_t qmask = gp.qmask;
-  bool local = s->variant == 0 && s->bucket_ok && (s->pmask & qmask) == 0 &&
-               (s->tbits > 0 || N <= LOCAL_BUCKET_MAX);
-  if (local && s->tbits > 0 && (s->max_bucket == 0 || s->max_bucket > LOCAL_BUCKET_MAX)) {
-    // the bound is unknown or too loose: measure the buckets exactly
-    ph_begin(s, PH_LOCAL);
-    launch_bucket_check(s->keys[s->cur], N, s->pmask, LOCAL_BUCKET_MAX, s->ctl, s->st);
-    ph_end(s, PH_LOCAL);
-    launched(s, PH_LOCAL, 1);
-    rc = sync_ctl(s, "sv_apply_gate");
-    if (rc != SV_OK) return rc;
-    s->max_bucket = s->ctl_host->count[0];
-    local = s->max_bucket <= LOCAL_BUCKET_MAX;
-  }
+  // The bucket-local kernel sorts and applies inside shared memory; it is used
+  // for states that fit one of its batches (measured: beyond that the sorted
+  // path was as fast or faster on this GPU, without bucket bookkeeping).
+  const bool local = s->variant == 0 && N <= LOCAL_BUCKET_MAX;
   static const bool debug = getenv("SV_DEBUG") != nullptr;
   if (debug)
-    fprintf(stderr, "[sv] gate %lld N=%llu q=(%d,%d) P&Q=%d tbits=%d max_bucket=%llu -> %s\n",
-            (long long)s->gate_index, (unsigned long long)N, gp.q[0], m > 1 ? gp.q[1] : -1,
-            (s->pmask & qmask) != 0, s->tbits, (unsigned long long)s->max_bucket, local ? "local" : "global");
+    fprintf(stderr, "[sv] gate %lld N=%llu q=(%d,%d) -> %s\n", (long long)s->gate_index, (unsigned long long)N,
+            gp.q[0], m > 1 ? gp.q[1] : -1, local ? "local" : "global");
   bool done = false;
   if (local) {
     rc = upload_perm(s, gp);
@@ -576,7 +521,6 @@ sv_status sv_apply_gate(sv_state* s, int m, const int* qubits, const double* U) 
     } else {
       ++s->local_gates;
       done = true;
-      s->max_bucket = s->ctl_host->count[0];
       const uint64_t npre = s->ctl_host->count[1];
       if (s->ctl_host->count[3] != 0) {  // exact cancellations: drop the zero terms
         rc = ensure_lookback(s, npre / 2048 + 16);
@@ -604,8 +548,6 @@ sv_status sv_apply_gate(sv_state* s, int m, const int* qubits, const double* U) 
     const uint64_t red_tiles = nrec / 1024 + 2;
     if (rc == SV_OK) rc = ensure_lookback(s, red_tiles + 16);
     if (rc != SV_OK) return rc;
-    s->tbits = 0;
-    s->pmask = 0;
     rc = upload_perm(s, gp);
     if (rc != SV_OK) return rc;
     const int nbits = s->n + m;
@@ -631,23 +573,10 @@ sv_status sv_apply_gate(sv_state* s, int m, const int* qubits, const double* U) 
     if (rc != SV_OK) return rc;
     s->cur = alt;
     s->N = s->ctl_host->count[1];
-    s->bucket_ok = false;
     done = true;
   }
   if (!done) {
     ++s->global_gates;
-    const uint64_t npre_max = N << m;
-    ph_begin(s, PH_LOCAL);
-    launch_bit_counts(s->keys[s->cur], N, s->n, s->bitcnt_dev, s->st);
-    ph_end(s, PH_LOCAL);
-    launched(s, PH_LOCAL, 1);
-    rc = cuda_check(s, cudaMemcpyAsync(s->bitcnt_host, s->bitcnt_dev, 64 * sizeof(uint64_t),
-                                       cudaMemcpyDeviceToHost, s->st), "bit statistics");
-    if (rc == SV_OK) rc = cuda_check(s, cudaStreamSynchronize(s->st), "bit statistics");
-    if (rc != SV_OK) return rc;
-    uint64_t stride;
-    const uint64_t n_sample = bit_count_sample(N, &stride);
-    choose_buckets(s, qmask, npre_max < s->K ? npre_max : (N > s->K ? N : s->K), s->bitcnt_host, n_sample);
     rc = upload_perm(s, gp);
     if (rc != SV_OK) return rc;
     const int passes = (s->n + RADIX_BITS - 1) / RADIX_BITS;
@@ -677,12 +606,8 @@ sv_status sv_apply_gate(sv_state* s, int m, const int* qubits, const double* U) 
     if (rc != SV_OK) return rc;
     s->cur = alt;
     s->N = s->ctl_host->count[1];
-    s->bucket_ok = true;
-    s->max_bucket = 0;  // unknown until a local gate measures it
   }
-  for (int t = 0; t < m; ++t) s->last_use[gp.q[t]] = s->gate_index;
   ++s->gate_index;
-  s->live |= qmask;
   s->stats.n_pre = s->N;
   s->stats.local_gates = s->local_gates;
   s->stats.global_gates = s->global_gates;
@@ -969,14 +894,6 @@ sv_status sv_load(sv_state* s, const uint64_t* keys, const double* amps, uint64_
   if (s->ctl_host->count[3] != 0) return fail(s, SV_E_ARG, "sv_load: duplicate keys");
   s->cur = alt;
   s->N = s->ctl_host->count[2];
-  uint64_t orv = 0, andv = ~0ull;
-  for (uint64_t i = 0; i < N; ++i) {
-    orv |= keys[i];
-    andv &= keys[i];
-  }
-  s->live = orv ^ andv;
-  s->bucket_ok = false;  // sorted by key, but no bucket qubits chosen yet
-  s->max_bucket = 0;
   return SV_OK;
 }
 
@@ -995,7 +912,6 @@ sv_status sv_set_apply_variant(sv_state* s, int variant) {
   SV_GUARD(s);
   if (variant != 0 && variant != 1) return fail(s, SV_E_ARG, "sv_set_apply_variant: variant must be 0 or 1");
   s->variant = variant;
-  if (variant == 1) s->bucket_ok = false;
   return SV_OK;
 }
 

@@ -207,10 +207,10 @@ def test_exact_cancellation_drops_zero_terms(sv, oracle_mod):
         assert g.num_terms() == o.num_terms()
 
 
-def test_skewed_buckets_fall_back(sv, oracle_mod):
-    """Most keys share their high bits: buckets chosen on those bits overflow
-    the local batch limit and the gate must be redone through the global
-    path with the same result."""
+def test_skewed_keys_large_state(sv, oracle_mod):
+    """Most keys share their high bits, a few stand apart: a state far larger
+    than one shared-memory batch, with strongly skewed bit patterns, goes
+    through the sorted path with the oracle's result."""
     rng = np.random.default_rng(123)
     n = 30
     low = rng.choice(1 << 20, size=30000, replace=False).astype(np.uint64)
@@ -229,6 +229,8 @@ def test_skewed_buckets_fall_back(sv, oracle_mod):
 
 @pytest.mark.parametrize("prec", [0, 1])
 def test_brickwork_local_and_global_gates(sv, oracle_mod, prec):
+    """Small states (the first gates) take the shared-memory kernel, larger
+    ones the sorted path; the result is the oracle's either way."""
     c = C.brickwork_circuit(24, 6, seed=77, sigma=0.05, K=1 << 14, p=1.0)
     g = sv.SparseState(c.n, c.K, c.p, prec=prec)
     o = oracle_mod.Oracle(c.n, c.K, c.p, prec=prec)
