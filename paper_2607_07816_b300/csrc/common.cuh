@@ -53,7 +53,7 @@ struct Ctl {
   uint64_t above_mass_hi, above_mass_lo;
   uint64_t win_mass_hi, win_mass_lo;
   uint32_t use_window;                     // 1: select over the window, 0: over all terms
-  uint32_t pad1;
+  uint32_t sel_gated;                      // 1: select kernels decide on the device which of them run
 };
 
 __device__ __forceinline__ uint64_t ld_acquire(const uint64_t* p) {

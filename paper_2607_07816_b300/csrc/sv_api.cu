@@ -667,19 +667,32 @@ sv_status run_select(sv_state* s, int mode, uint64_t count_target, uint32_t* lev
                        s->st);
   ph_end(s, PH_WINDOW);
   launched(s, PH_WINDOW, 3);
+  // Two levels and the finish are enqueued behind the window without a host
+  // wait: the kernels read on the device whether the window was taken, how
+  // long the list is and whether the bin is small enough to finish; the host
+  // continues level by level only when that did not resolve the cut.
+  ph_begin(s, PH_SELECT);
+  cudaMemsetAsync(&s->ctl->sel_gated, 1, sizeof(uint32_t), s->st);  // nonzero: gated
+  for (int level = 0; level < 2; ++level) {
+    launch_select_hist(s->probs[s->cur], s->keys[s->cur], N, s->ctl, s->ss, s->st);
+    launch_select_pick(s->ctl, s->ss, s->p, s->st);
+  }
+  launch_select_compact(s->probs[s->cur], s->keys[s->cur], N, s->ctl, s->ss, s->st);
+  launch_select_finish(s->ctl, s->ss, s->p, s->st);
+  cudaMemsetAsync(&s->ctl->sel_gated, 0, sizeof(uint32_t), s->st);
+  ph_end(s, PH_SELECT);
+  launched(s, PH_SELECT, 6);
+  *levels += 2;
   rc = sync_ctl(s, "truncation select");
   if (rc != SV_OK) return rc;
-  const bool win = s->ctl_host->use_window != 0;
   s->stats.window_terms = s->ctl_host->win_n;
-  s->stats.window_hits += win ? 1 : 0;
-  const uint64_t* lp = win ? s->ss.win_p : s->probs[s->cur];
-  const uint64_t* lk = win ? s->ss.win_k : s->keys[s->cur];
-  const uint64_t ln = win ? s->ctl_host->win_n : N;
-  bool small = win && ln <= (uint64_t)FINISH_CAP;
+  s->stats.window_hits += s->ctl_host->use_window ? 1 : 0;
+  if (s->ctl_host->sel_done) return SV_OK;
+  bool small = s->ctl_host->sel_bin_count <= (uint64_t)FINISH_CAP;
   for (int level = 0; level < 16; ++level) {
     if (!small) {
       ph_begin(s, PH_SELECT);
-      launch_select_hist(lp, lk, ln, s->ctl, s->ss, s->st);
+      launch_select_hist(s->probs[s->cur], s->keys[s->cur], N, s->ctl, s->ss, s->st);
       launch_select_pick(s->ctl, s->ss, s->p, s->st);
       ph_end(s, PH_SELECT);
       launched(s, PH_SELECT, 2);
@@ -691,7 +704,7 @@ sv_status run_select(sv_state* s, int mode, uint64_t count_target, uint32_t* lev
     }
     if (small) {
       ph_begin(s, PH_SELECT);
-      launch_select_compact(lp, lk, ln, s->ctl, s->ss, s->st);
+      launch_select_compact(s->probs[s->cur], s->keys[s->cur], N, s->ctl, s->ss, s->st);
       launch_select_finish(s->ctl, s->ss, s->p, s->st);
       ph_end(s, PH_SELECT);
       launched(s, PH_SELECT, 2);

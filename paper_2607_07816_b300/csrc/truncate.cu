@@ -19,13 +19,29 @@
 
 namespace sv {
 
+// The list is the window buffer when the window pass set use_window, else
+// all terms: the choice and the list length are read on the device, so the
+// select can be enqueued before the window is known.  Block b scans a
+// contiguous chunk of at least 8192 terms (each block flushes up to
+// 3 * SEL_BINS global atomics, so blocks get a large share each).
 __global__ void __launch_bounds__(256) k_select_hist(const uint64_t* __restrict__ probs,
                                                      const uint64_t* __restrict__ keys, uint64_t n,
+                                                     const uint64_t* __restrict__ wp, const uint64_t* __restrict__ wk,
                                                      Ctl* ctl, uint32_t* __restrict__ g_cnt,
                                                      uint64_t* __restrict__ g_mass) {
   __shared__ uint32_t s_cnt[SEL_BINS];
   __shared__ uint64_t s_mass[2 * SEL_BINS];
   if (ctl->sel_done) return;
+  if (ctl->sel_gated && ctl->sel_bin_count <= (uint64_t)FINISH_CAP) return;  // the finish takes over
+  const bool win = ctl->use_window != 0;
+  const uint64_t* P = win ? wp : probs;
+  const uint64_t* Kk = win ? wk : keys;
+  const uint64_t nn = win ? ctl->win_n : n;
+  uint64_t chunk = (nn + gridDim.x - 1) / gridDim.x;
+  if (chunk < 8192) chunk = 8192;
+  const uint64_t c0 = blockIdx.x * chunk;
+  if (c0 >= nn) return;
+  const uint64_t c1 = c0 + chunk < nn ? c0 + chunk : nn;
   const int bits = (int)ctl->sel_bits;
   const uint64_t ph = ctl->sel_prefix_hi, pl = ctl->sel_prefix_lo;
   int D, shift;
@@ -36,15 +52,14 @@ __global__ void __launch_bounds__(256) k_select_hist(const uint64_t* __restrict_
     s_mass[2 * i] = s_mass[2 * i + 1] = 0;
   }
   __syncthreads();
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   // whole warps iterate together (the warp reductions need all 32 lanes)
-  const uint64_t nround = (n + stride - 1) / stride * stride;
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nround; i += stride) {
-    bool active = i < n;
-    uint64_t pb = active ? probs[i] : 0ull;
+  const uint64_t span = (c1 - c0 + blockDim.x - 1) / blockDim.x * blockDim.x;
+  for (uint64_t i = c0 + threadIdx.x; i < c0 + span; i += blockDim.x) {
+    bool active = i < c1;
+    uint64_t pb = active ? P[i] : 0ull;
     uint64_t hi = ~pb;
     if (active && bits <= 64 && ((hi ^ ph) >> (64 - bits)) != 0) active = false;
-    uint64_t lo = (active && need_lo) ? keys[i] : 0ull;
+    uint64_t lo = (active && need_lo) ? Kk[i] : 0ull;
     if (active && bits > 64 && !z_matches(hi, lo, ph, pl, bits)) active = false;
     uint32_t dg = active ? z_digit(hi, lo, shift, D) : 0u;
     warp_hist_add(active, dg, pb, s_cnt, s_mass, &ctl->err);
@@ -63,11 +78,10 @@ void launch_select_hist(const uint64_t* probs, const uint64_t* keys, uint64_t n,
   cudaMemsetAsync(ss.hist_count, 0, sizeof(uint32_t) * SEL_BINS, st);
   cudaMemsetAsync(ss.hist_mass, 0, sizeof(uint64_t) * 2 * SEL_BINS, st);
   if (n == 0) return;
-  // each block flushes up to 3 * SEL_BINS global atomics: give every block a
-  // large share of the list
   uint64_t blocks = (n + 8191) / 8192;
   if (blocks > 148 * 4) blocks = 148 * 4;
-  k_select_hist<<<(unsigned)blocks, 256, 0, st>>>(probs, keys, n, ctl, ss.hist_count, ss.hist_mass);
+  k_select_hist<<<(unsigned)blocks, 256, 0, st>>>(probs, keys, n, ss.win_p, ss.win_k, ctl, ss.hist_count,
+                                                  ss.hist_mass);
 }
 
 // ---------------------------------------------------------------- sample window
@@ -402,7 +416,7 @@ __global__ void __launch_bounds__(WP_BLOCK, 4) k_window_pass(const uint64_t* __r
 
 // One thread: choose between the window and the full list and set up the
 // select state (target from the exact total mass).
-__global__ void k_window_decide(Ctl* ctl, int mode, uint64_t count_target, double p, uint64_t cap) {
+__global__ void k_window_decide(Ctl* ctl, int mode, uint64_t count_target, double p, uint64_t cap, uint64_t n) {
   const u128 total = make_u128(ctl->total_mass_hi, ctl->total_mass_lo);
   u128 target;
   if (mode == 0) {
@@ -435,7 +449,7 @@ __global__ void k_window_decide(Ctl* ctl, int mode, uint64_t count_target, doubl
   ctl->sel_before_count = valid ? ac : 0;
   ctl->sel_before_mass_hi = valid ? ctl->above_mass_hi : 0;
   ctl->sel_before_mass_lo = valid ? ctl->above_mass_lo : 0;
-  ctl->sel_bin_count = valid ? wn : 0;
+  ctl->sel_bin_count = valid ? wn : n;
 }
 
 void launch_select_window(const uint64_t* probs, const uint64_t* keys, uint64_t n, Ctl* ctl,
@@ -455,7 +469,7 @@ void launch_select_window(const uint64_t* probs, const uint64_t* keys, uint64_t 
   if (grid == 0) grid = 1;
   k_window_pass<<<(unsigned)grid, WP_BLOCK, 0, st>>>(probs, keys, n, ctl, ss.win_p, ss.win_k, ss.win_i,
                                                      ss.win_cap, ss.tile_keep, ss.keep_bits);
-  k_window_decide<<<1, 1, 0, st>>>(ctl, mode, count_target, p, ss.win_cap);
+  k_window_decide<<<1, 1, 0, st>>>(ctl, mode, count_target, p, ss.win_cap, n);
 }
 
 uint64_t window_tiles(uint64_t n) { return (n + WP_TILE - 1) / WP_TILE; }
@@ -627,6 +641,7 @@ __device__ void block_pick(const uint32_t* cnt, const uint64_t* mass /* [nbins][
 __global__ void __launch_bounds__(PICK_THREADS) k_select_pick(Ctl* ctl, const uint32_t* cnt,
                                                               const uint64_t* mass, double p) {
   if (ctl->sel_done) return;
+  if (ctl->sel_gated && ctl->sel_bin_count <= (uint64_t)FINISH_CAP) return;
   block_pick(cnt, mass, ctl, p);
 }
 
@@ -636,17 +651,23 @@ void launch_select_pick(Ctl* ctl, const SelectScratch& ss, double p, cudaStream_
 
 // ---------------------------------------------------------------- gather + finish
 __global__ void __launch_bounds__(256) k_select_compact(const uint64_t* __restrict__ probs,
-                                                        const uint64_t* __restrict__ keys,
-                                                        uint64_t n, Ctl* ctl,
+                                                        const uint64_t* __restrict__ keys, uint64_t n,
+                                                        const uint64_t* __restrict__ wp,
+                                                        const uint64_t* __restrict__ wk, Ctl* ctl,
                                                         uint64_t* __restrict__ buf) {
   if (ctl->sel_done) return;
+  if (ctl->sel_gated && ctl->sel_bin_count > (uint64_t)FINISH_CAP) return;  // more levels first
+  const bool win = ctl->use_window != 0;
+  const uint64_t* P = win ? wp : probs;
+  const uint64_t* Kk = win ? wk : keys;
+  const uint64_t nn = win ? ctl->win_n : n;
   const int bits = (int)ctl->sel_bits;
   const uint64_t ph = ctl->sel_prefix_hi, pl = ctl->sel_prefix_lo;
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nn;
        i += (uint64_t)gridDim.x * blockDim.x) {
-    uint64_t hi = ~probs[i];
+    uint64_t hi = ~P[i];
     if (bits <= 64 && ((hi ^ ph) >> (64 - bits)) != 0) continue;
-    uint64_t lo = keys[i];
+    uint64_t lo = Kk[i];
     if (!z_matches(hi, lo, ph, pl, bits)) continue;
     uint64_t pos = atomicAdd((unsigned long long*)&ctl->compact_n, 1ull);
     if (pos < FINISH_CAP) {
@@ -662,13 +683,14 @@ void launch_select_compact(const uint64_t* probs, const uint64_t* keys, uint64_t
   if (n == 0) return;
   uint64_t blocks = (n + 255) / 256;
   if (blocks > 148 * 4) blocks = 148 * 4;
-  k_select_compact<<<(unsigned)blocks, 256, 0, st>>>(probs, keys, n, ctl, ss.buf);
+  k_select_compact<<<(unsigned)blocks, 256, 0, st>>>(probs, keys, n, ss.win_p, ss.win_k, ctl, ss.buf);
 }
 
 __global__ void __launch_bounds__(PICK_THREADS) k_select_finish(Ctl* ctl, const uint64_t* buf,
                                                                 double p) {
   __shared__ uint32_t s_cnt[SEL_BINS];
   __shared__ uint64_t s_mass[2 * SEL_BINS];
+  if (ctl->sel_gated && ctl->sel_bin_count > (uint64_t)FINISH_CAP) return;
   uint64_t nb = ctl->compact_n;
   if (nb > FINISH_CAP) nb = FINISH_CAP;
   for (int it = 0; it < 128; ++it) {
