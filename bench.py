@@ -371,6 +371,10 @@ def run_serving(args, rank, dev, stream):
     p50, p99 = serve.percentiles(opened)
     s_lat = serve.fifo_latencies(arrivals, svc)
     same_peak = sum(int(a.peak_key == b[1]) for a, b in zip(closed, ser))
+    # where the argmax differs, the two peak probabilities (complex64 batched,
+    # complex128 serial): near-equal values mean a near-tie between strings
+    differ = [(a.peak_prob, b[2]) for a, b in zip(closed, ser) if a.peak_key != b[1]]
+    rel = [abs(x - y) / max(x, y) for x, y in differ]
     same_open = sum(int(a.peak_key == b.peak_key and a.peak_prob == b.peak_prob) for a, b in zip(opened, closed))
     large = [j for j, c in enumerate(reqs) if c.n == 56]
     return {
@@ -384,6 +388,8 @@ def run_serving(args, rank, dev, stream):
                    "p50_s": p50, "p99_s": p99, "wall_s": open_s},
         "speedup_circuits_per_s": capacity / (R / svc.sum()),
         "peaks_equal_to_serial_c128": f"{same_peak}/{R}",
+        "differing_peaks_max_rel_prob_gap": max(rel) if rel else 0.0,
+        "differing_peaks_max_prob": max((max(x, y) for x, y in differ), default=0.0),
         "served_results_equal_to_saturated_run": f"{same_open}/{R}",
     }
 

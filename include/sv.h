@@ -267,8 +267,12 @@ sv_status sv_peak_noalloc(int prec, const uint64_t* keys, const void* amps, uint
  * seed (random bit patterns, subnormals, few-bit significands for exact
  * rounding ties) are compared on the default stream with the results of the
  * conversion instructions; *mismatches receives the count and *first_bad
- * the lowest failing case index (UINT64_MAX when none).  SV_E_ARG for
- * another `which` or NULL outputs. */
+ * the lowest failing case index (UINT64_MAX when none).  which = 2 checks
+ * the bounded waits of the library's scans instead: a kernel waits for a
+ * descriptor that nothing publishes, must give up after its poll limit and
+ * flag a timeout, and return normally (the CUDA context stays usable);
+ * *mismatches is 0 when it did, and *first_bad receives the error flags it
+ * raised.  SV_E_ARG for another `which` or NULL outputs. */
 sv_status sv_selftest(int which, uint64_t n, uint64_t seed, uint64_t* mismatches, uint64_t* first_bad);
 
 #ifdef __cplusplus

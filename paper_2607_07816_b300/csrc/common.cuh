@@ -66,95 +66,18 @@ __device__ __forceinline__ void st_release(uint64_t* p, uint64_t v) {
   asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// Decoupled look-back (single-pass prefix scan, Merrill & Garland): publish
-// this tile's aggregate, walk back over earlier tiles until an inclusive
-// prefix is found, publish the inclusive prefix and return the exclusive
-// one.  Entry t of the chain lives at lb[t * stride].  Tiles obtain their
-// ids in launch order from an atomic counter, so every tile waited on has
-// already started; the wait is still bounded and sets ERR_TIMEOUT instead of
-// hanging.
-__device__ __forceinline__ uint64_t lookback_exclusive(uint64_t* lb, uint32_t stride,
-                                                       uint64_t tile, uint64_t agg,
-                                                       uint32_t* err) {
-  if (tile == 0) {
-    st_release(lb, LB_INC | agg);
-    return 0;
-  }
-  st_release(lb + tile * stride, LB_AGG | agg);
-  uint64_t excl = 0;
-  int64_t t = (int64_t)tile - 1;
-  uint32_t spins = 0, ns = 8;
-  while (t >= 0) {
-    uint64_t v = ld_acquire(lb + (uint64_t)t * stride);
-    uint64_t st = v >> 62;
-    if (st == 0) {
-      if (++spins > SPIN_LIMIT) {
-        atomicOr(err, ERR_TIMEOUT);
-        break;
-      }
-      __nanosleep(ns);
-      if (ns < 256) ns <<= 1;
-      continue;
-    }
-    excl += v & LB_VAL;
-    if (st == 2) break;
-    --t;
-  }
-  st_release(lb + tile * stride, LB_INC | (excl + agg));
-  return excl;
-}
-
-// As lookback_exclusive, but each round issues four independent loads of the
-// nearest unresolved predecessors, cutting the dependent-load latency of a
-// long walk by four.
-__device__ __forceinline__ uint64_t lookback_exclusive_x4(uint64_t* lb, uint32_t stride, uint64_t tile,
-                                                          uint64_t agg, uint32_t* err) {
-  if (tile == 0) {
-    st_release(lb, LB_INC | agg);
-    return 0;
-  }
-  st_release(lb + tile * stride, LB_AGG | agg);
-  uint64_t excl = 0;
-  int64_t t = (int64_t)tile - 1;
-  uint32_t spins = 0, ns = 8;
-  while (t >= 0) {
-    uint64_t v[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) v[k] = (t - k >= 0) ? ld_acquire(lb + (uint64_t)(t - k) * stride) : LB_INC;
-    int k = 0;
-    bool done = false;
-    for (; k < 4; ++k) {
-      const uint64_t st = v[k] >> 62;
-      if (st == 0) break;
-      excl += v[k] & LB_VAL;
-      if (st == 2) {
-        done = true;
-        break;
-      }
-    }
-    if (done) break;
-    t -= k;
-    if (k < 4) {
-      if (++spins > SPIN_LIMIT) {
-        atomicOr(err, ERR_TIMEOUT);
-        break;
-      }
-      __nanosleep(ns);
-      if (ns < 256) ns <<= 1;
-    }
-  }
-  st_release(lb + tile * stride, LB_INC | (excl + agg));
-  return excl;
-}
-
-// Warp-cooperative decoupled look-back over a single chain: all 32 lanes of
-// one warp call it.  The warp polls a window of 32 predecessor descriptors at
-// once, waits until every descriptor from the nearest inclusive prefix up to
-// the tile is published, sums them with a warp reduction and moves the window
-// back when the window holds no inclusive prefix.  Same contract and bounded
-// wait as lookback_exclusive; every lane returns the exclusive prefix.
+// Decoupled look-back (single-pass prefix scan, Merrill & Garland) over one
+// chain, warp-cooperative: all 32 lanes of one warp call it.  The tile
+// publishes its aggregate, then the warp polls a window of 32 predecessor
+// descriptors at once, waits until every descriptor from the nearest
+// inclusive prefix up to the tile is published, sums them with a warp
+// reduction and moves the window back when it holds no inclusive prefix;
+// finally the tile publishes its inclusive prefix.  Every lane returns the
+// exclusive prefix.  Tiles obtain their ids in launch order from an atomic
+// counter, so every tile waited on has already started; the wait is still
+// bounded (spin_limit polls) and sets ERR_TIMEOUT instead of hanging.
 __device__ __forceinline__ uint64_t lookback_exclusive_warp(uint64_t* lb, uint64_t tile, uint64_t agg,
-                                                            uint32_t* err) {
+                                                            uint32_t* err, uint32_t spin_limit = SPIN_LIMIT) {
   const int lane = threadIdx.x & 31;
   if (tile == 0) {
     if (lane == 0) st_release(lb, LB_INC | agg);
@@ -173,7 +96,7 @@ __device__ __forceinline__ uint64_t lookback_exclusive_warp(uint64_t* lb, uint64
     const int hi = inc ? 31 - __clz((int)inc) : 0;  // nearest inclusive prefix in the window
     const uint32_t need = inc ? (0xffffffffu << hi) : 0xffffffffu;
     if (notready & need) {
-      if (++spins > SPIN_LIMIT) {
+      if (++spins > spin_limit) {
         if (lane == 0) atomicOr(err, ERR_TIMEOUT);
         break;
       }

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include "c64_exact.cuh"
+#include "common.cuh"
 #include "sv.h"
 
 namespace sv {
@@ -74,11 +75,43 @@ __global__ void k_selftest(int which, uint64_t n, uint64_t seed, unsigned long l
   }
 }
 
+// A bounded wait that runs out: tile 1 waits for tile 0's descriptor, which
+// nothing publishes.  The kernel must give up after the poll limit, flag
+// ERR_TIMEOUT and return normally.
+__global__ void k_wait_runs_out(uint64_t* lb, uint32_t* err, uint32_t limit) {
+  lookback_exclusive_warp(lb, 1, 5, err, limit);
+}
+
 }  // namespace
 }  // namespace sv
 
+static sv_status selftest_wait(uint64_t* mismatches, uint64_t* first_bad) {
+  uint64_t* lb = nullptr;
+  uint32_t* err = nullptr;
+  if (cudaMalloc(&lb, 4 * sizeof(uint64_t)) != cudaSuccess || cudaMalloc(&err, sizeof(uint32_t)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(lb);
+    return SV_E_NOMEM;
+  }
+  cudaError_t e = cudaMemset(lb, 0, 4 * sizeof(uint64_t));
+  if (e == cudaSuccess) e = cudaMemset(err, 0, sizeof(uint32_t));
+  if (e == cudaSuccess) {
+    sv::k_wait_runs_out<<<1, 32>>>(lb, err, 1u << 14);
+    e = cudaGetLastError();
+  }
+  uint32_t flags = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&flags, err, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+  cudaFree(lb);
+  cudaFree(err);
+  if (e != cudaSuccess) return SV_E_CUDA;
+  *mismatches = (flags & sv::ERR_TIMEOUT) ? 0 : 1;
+  *first_bad = flags;
+  return SV_OK;
+}
+
 extern "C" sv_status sv_selftest(int which, uint64_t n, uint64_t seed, uint64_t* mismatches, uint64_t* first_bad) {
-  if ((which != 0 && which != 1) || !mismatches || !first_bad) return SV_E_ARG;
+  if ((which < 0 || which > 2) || !mismatches || !first_bad) return SV_E_ARG;
+  if (which == 2) return selftest_wait(mismatches, first_bad);
   unsigned long long* d = nullptr;
   if (cudaMalloc(&d, 2 * sizeof(unsigned long long)) != cudaSuccess) {
     cudaGetLastError();

@@ -1,6 +1,7 @@
 """The complex64 probability and rescaling that the kernels form without
 float<->double conversion instructions give the bits of the conversion
 instructions, over random bit patterns, subnormals and exact ties."""
+import numpy as np
 import pytest
 
 pytestmark = pytest.mark.gpu
@@ -25,4 +26,14 @@ def test_integer_pipe_matches_fp64(sv, which):
 
 def test_selftest_rejects_bad_arguments(sv):
     with pytest.raises(sv.SVError):
-        sv.sv_selftest(2, 10)
+        sv.sv_selftest(3, 10)
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(sv):
+    """A look-back wait on a descriptor nothing publishes gives up, flags a
+    timeout and returns; the device then keeps working."""
+    bad, flags = sv.sv_selftest(2, 0)
+    assert bad == 0 and flags == 1  # ERR_TIMEOUT
+    g = sv.SparseState(6)
+    g.apply_gate((0,), np.array([[1, 1], [1, -1]]) / np.sqrt(2))
+    assert g.num_terms() == 2
