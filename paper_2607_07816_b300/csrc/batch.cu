@@ -816,6 +816,7 @@ __global__ void __launch_bounds__(SC_BLOCK, 4) k_seg_truncate(
   typedef TileLayout<SC_BLOCK, SC_ITEMS> L;
   __shared__ CompactShared<SC_BLOCK> cs;
   __shared__ uint64_t s_tile;
+  __shared__ uint16_t s_list[SC_BLOCK * SC_ITEMS];
   const uint64_t n = *n_dev;
   if (n > n_max) {  // the look-back buffer was sized for n_max terms
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&ctl->err, ERR_INVARIANT);
@@ -862,29 +863,36 @@ __global__ void __launch_bounds__(SC_BLOCK, 4) k_seg_truncate(
       flag[j] = f;
     }
     tile_compact<SC_BLOCK, SC_ITEMS>(flag, pos, cs, lookback, tile, &ctl->err);
-    last = -1;
+    // list the kept terms, then process the list densely (all lanes busy,
+    // contiguous writes)
 #pragma unroll
-    for (int j = 0; j < SC_ITEMS; ++j) {
-      if (flag[j]) {
-        const uint64_t i = L::index(base, j);
-        const uint64_t o = cs.tile_base_out + pos[j];
-        if ((int)sgv[j] != last) {
-          last = sgv[j];
-          const SegSel& st = sel[last];
-          cut_on = st.active && st.done == 1;
-          scale = st.scale;
-        }
-        C2 a = amps[i];
-        uint64_t pb = pbv[j];
-        if (cut_on) {
-          a = amp_scaled(a, scale);
-          pb = amp_prob_bits(a);
-        }
-        keys_out[o] = keys[i];
-        amps_out[o] = a;
-        probs_out[o] = pb;
-        seg_out[o] = sgv[j];
+    for (int j = 0; j < SC_ITEMS; ++j)
+      if (flag[j]) s_list[pos[j]] = (uint16_t)(L::index(base, j) - base);
+    __syncthreads();
+    last = -1;
+    const uint32_t kept = cs.tile_total;
+    const uint64_t ob = cs.tile_base_out;
+    for (uint32_t t = threadIdx.x; t < kept; t += SC_BLOCK) {
+      const uint64_t i = base + s_list[t];
+      const uint16_t sg = seg[i];
+      if ((int)sg != last) {
+        last = sg;
+        const SegSel& st = sel[last];
+        cut_on = st.active && st.done == 1;
+        scale = st.scale;
       }
+      C2 a = amps[i];
+      uint64_t pb;
+      if (cut_on) {
+        a = amp_scaled(a, scale);
+        pb = amp_prob_bits(a);
+      } else {
+        pb = probs[i];
+      }
+      keys_out[ob + t] = keys[i];
+      amps_out[ob + t] = a;
+      probs_out[ob + t] = pb;
+      seg_out[ob + t] = sg;
     }
     if (tile == tiles - 1 && threadIdx.x == 0) ctl->count[2] = cs.tile_base_out + cs.tile_total;
     __syncthreads();

@@ -793,6 +793,7 @@ __global__ void __launch_bounds__(WP_BLOCK) k_truncate_write(
     C2* __restrict__ amps_out, uint64_t* __restrict__ probs_out, const Ctl* ctl) {
   typedef TileLayout<WP_BLOCK, WP_ITEMS> L;
   __shared__ CompactShared<WP_BLOCK> cs;
+  __shared__ uint16_t s_list[WP_TILE];
   const double s = ctl->scale;
   const int lane = threadIdx.x & 31;
   const uint64_t tiles = (n + L::TILE - 1) / L::TILE;
@@ -809,17 +810,21 @@ __global__ void __launch_bounds__(WP_BLOCK) k_truncate_write(
 #pragma unroll
     for (int j = 0; j < WP_ITEMS; ++j) flag[j] = L::index(base, j) < n && ((words[j] >> lane) & 1u);
     tile_local_positions<WP_BLOCK, WP_ITEMS>(flag, pos, cs);
-    const uint64_t ob = tile_off[tile];
+    // list the kept terms (tile-local index, in input order), then process
+    // the list densely: every lane does useful rescaling work and the
+    // outputs are written contiguously
 #pragma unroll
-    for (int j = 0; j < WP_ITEMS; ++j) {
-      if (flag[j]) {
-        const uint64_t i = L::index(base, j);
-        const uint64_t o = ob + pos[j];
-        const C2 a = amp_scaled(amps[i], s);
-        keys_out[o] = keys[i];
-        amps_out[o] = a;
-        probs_out[o] = amp_prob_bits(a);
-      }
+    for (int j = 0; j < WP_ITEMS; ++j)
+      if (flag[j]) s_list[pos[j]] = (uint16_t)(L::index(base, j) - base);
+    __syncthreads();
+    const uint64_t ob = tile_off[tile];
+    const uint32_t kept = cs.tile_total;
+    for (uint32_t t = threadIdx.x; t < kept; t += WP_BLOCK) {
+      const uint64_t i = base + s_list[t];
+      const C2 a = amp_scaled(amps[i], s);
+      keys_out[ob + t] = keys[i];
+      amps_out[ob + t] = a;
+      probs_out[ob + t] = amp_prob_bits(a);
     }
     __syncthreads();
   }
