@@ -395,10 +395,12 @@ def run_serving(args, rank, dev, stream):
 
 
 def run_variant_ab(args, rank, dev, stream, steps=8):
-    """Group-first (default) against expand-first (the paper's formulation:
-    one record per term and output, sorted, then summed per output) on the
-    benchmark state at K terms: the same gates, alternating blocks of steps,
-    CUDA-event time per step (gate + truncation) on the library's stream."""
+    """Group-first (default: grouping by partition and merge) against
+    group-first with a full radix sort and against expand-first (the paper's
+    formulation: one record per term and output, sorted, then summed per
+    output) on the benchmark state at K terms: the same gates, alternating
+    blocks of steps, CUDA-event time per step (gate + truncation) on the
+    library's stream."""
     import torch
     from paper_2607_07816_b300 import circuits as C
     from paper_2607_07816_b300 import sv
@@ -411,9 +413,9 @@ def run_variant_ab(args, rank, dev, stream, steps=8):
         st.apply_gate(q, u)
         st.truncate()
         gi += 1
-    ms = {0: [], 1: []}
+    ms = {0: [], 1: [], 2: []}
     for rep in range(2):
-        for variant in (0, 1):
+        for variant in (0, 2, 1):
             st.set_variant(variant)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize(dev)
@@ -427,9 +429,11 @@ def run_variant_ab(args, rank, dev, stream, steps=8):
             torch.cuda.synchronize(dev)
             ms[variant].append(e0.elapsed_time(e1) / (steps // 2))
     st.close()
-    g, e = statistics.mean(ms[0]), statistics.mean(ms[1])
+    g, e, r = statistics.mean(ms[0]), statistics.mean(ms[1]), statistics.mean(ms[2])
     return {"K": args.K, "steps_each": steps, "group_first_ms_per_step": round(g, 3),
-            "expand_first_ms_per_step": round(e, 3), "expand_over_group": round(e / g, 3)}
+            "group_first_radix_sort_ms_per_step": round(r, 3),
+            "expand_first_ms_per_step": round(e, 3), "expand_over_group": round(e / g, 3),
+            "radix_over_merge_grouping": round(r / g, 3)}
 
 
 def run_ring(args, dev, stream):

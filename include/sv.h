@@ -157,15 +157,21 @@ sv_status sv_last_stats(const sv_state* s, sv_stats* out);
 sv_status sv_set_timing(sv_state* s, int enable);
 sv_status sv_phase_times(const sv_state* s, double* ms, uint64_t* launches);
 
-/* Gate application variant for the handle's next gates: 0 (default)
- * group-first -- sort the terms once with the gate bits moved to the bottom,
- * then expand each partner group to its 2^m outputs inside the mat-vec (and
- * the bucket-local path where it applies); 1 expand-first -- the paper's
+/* Gate application variant for the handle's next gates.  0 (default)
+ * group-first -- bring every partner group together with the gate bits at
+ * the bottom of the sort key, then expand each group to its 2^m outputs
+ * inside the mat-vec (states of at most 4096 terms do all of it in shared
+ * memory).  Every gate leaves the state sorted by its own sort key, and the
+ * next gate's key keeps the other qubits in that order, so the grouping is
+ * a stable partition by the gate bits followed by m levels of pairwise
+ * merges.  2 group-first with the grouping done by a full LSD radix sort of
+ * the sort keys (for comparison).  1 expand-first -- the paper's
  * formulation (Sec. IV-A): every term contributes one record to each of its
  * 2^m outputs, the records are sorted by (output, source gate bits) and each
- * output's contributions are summed in ascending source order.  Both give
- * the same terms and amplitudes bit for bit; expand-first sorts 2^m times as
- * many records and exists for comparison.  SV_E_ARG for other values. */
+ * output's contributions are summed in ascending source order.  All three
+ * give the same terms and amplitudes bit for bit; expand-first sorts 2^m
+ * times as many records and exists for comparison.  SV_E_ARG for other
+ * values. */
 sv_status sv_set_apply_variant(sv_state* s, int variant);
 
 /* Number of CUDA kernels this library has launched in this process. */

@@ -9,17 +9,22 @@
 
 namespace sv {
 
-// Sort-key permutation of a gate: bucket qubits (plist) on top, the other
-// qubits outside the gate below them in descending order, gate qubit t at
-// bit t.  Writes the forward and inverse nibble tables.
-inline void build_perm(int n, int m, const int* q, int tbits, const int* plist, BitPerm* bp) {
+// Sort-key permutation of a gate: gate qubit q[t] at bit t, the other
+// qubits above in the order of order[] (order[b] = bit of qubit b in the
+// sort key the state is currently sorted by).  Writes the forward and
+// inverse nibble tables, and the new order into next[] (may alias order).
+inline void build_perm(int n, int m, const int* q, const int* order, BitPerm* bp, int* next) {
   int pos[64];
   for (int b = 0; b < 64; ++b) pos[b] = -1;
   for (int t = 0; t < m; ++t) pos[q[t]] = t;
-  int next = n - 1;
-  for (int i = 0; i < tbits; ++i) pos[plist[i]] = next--;
-  for (int b = n - 1; b >= 0; --b)
-    if (pos[b] < 0) pos[b] = next--;
+  int by_bit[64];
+  for (int b = 0; b < 64; ++b) by_bit[b] = -1;
+  for (int b = 0; b < n; ++b) by_bit[order[b]] = b;
+  int nextbit = m;
+  for (int p = 0; p < n; ++p) {
+    const int b = by_bit[p];
+    if (b >= 0 && pos[b] < 0) pos[b] = nextbit++;
+  }
   std::memset(bp, 0, sizeof(BitPerm));
   for (int k = 0; k < 16; ++k)
     for (int v = 0; v < 16; ++v)
@@ -38,6 +43,7 @@ inline void build_perm(int n, int m, const int* q, int tbits, const int* plist, 
           const int p = 4 * k + j;
           if (p < n) bp->inv[k][v] |= 1ull << from[p];
         }
+  for (int b = 0; b < n; ++b) next[b] = pos[b];
 }
 
 inline bool is_unitary(int m, const double* U) {

@@ -45,11 +45,16 @@ void sort_prepare();
 int radix_sort_pairs(uint64_t* kA, uint32_t* vA, uint64_t* kB, uint32_t* vB, uint64_t n, int nbits,
                      const SortScratch& sc, cudaStream_t st, int* passes_run, cudaError_t* cerr);
 
-// Sort-key bit permutation of a gate: the bucket qubits P on top (first
-// listed = most significant), the remaining qubits outside the gate below
-// them in descending order, and the gate qubits at the bottom with
-// qubits[t] at bit t.  Equal (sort key >> m) <=> same partner group, with
-// members in ascending r; equal top |P| bits <=> same bucket.
+// Exclusive scan over tiles of per-tile digit counts cnt[d * tiles + t]
+// for digits d < digits, each digit's run starting after the smaller
+// digits' totals (hist[d]): off[d * tiles + t].
+void launch_tile_offsets(const uint32_t* cnt, const uint32_t* hist, uint64_t tiles, int digits, uint32_t* off,
+                         cudaStream_t st);
+
+// Sort-key bit permutation of a gate: the qubits outside the gate on top,
+// in the order they have in the state's current sort key, and the gate
+// qubits at the bottom with qubits[t] at bit t.  Equal (sort key >> m) <=>
+// same partner group, with members in ascending r.
 struct BitPerm {
   uint64_t fwd[16][16];  // key -> sort key
   uint64_t inv[16][16];  // sort key -> key
@@ -71,6 +76,17 @@ struct GateParams {
   uint64_t pmask;      // bucket qubits as a key mask
   int vbits;           // > 0: sort keys carry the term index in their low vbits bits (no index array)
 };
+
+// Grouping of a state that is sorted by the previous gate's sort key when
+// gp.perm keeps the other qubits in that order (gate qubits at the bottom):
+// stable partition by the gate bits r, then m levels of pairwise merges.
+// The sorted keys (packed with the term index when gp.vbits > 0, else with
+// indices in sidx) end in sk[w], w the return value; *launches receives
+// the number of kernels launched.  The scratch's lookback words hold the
+// per-tile counts and offsets, hist the counts per r.
+int regroup_terms(const uint64_t* keys, uint64_t n, const GateParams& gp, uint64_t* sk[2], uint32_t* sidx[2],
+                  const SortScratch& sc, cudaStream_t st, int* launches, cudaError_t* cerr);
+void regroup_prepare();
 
 // Expand-first gate application (Sec. IV-A as the paper states it): records
 // (output sort key << m | source r, source index) for every term and output,

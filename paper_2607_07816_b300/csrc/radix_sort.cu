@@ -128,6 +128,11 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_tile_offsets(const uint32_t* _
   }
 }
 
+void launch_tile_offsets(const uint32_t* cnt, const uint32_t* hist, uint64_t tiles, int digits, uint32_t* off,
+                         cudaStream_t st) {
+  k_tile_offsets<<<digits, SCAN_THREADS, 0, st>>>(cnt, hist, tiles, off);
+}
+
 // 3. Scatter: rank the tile's keys per warp (match_any and per-warp digit
 // counters), turn the counters into per-warp offsets within each digit, scan
 // the tile's digit counts, stage the tile in shared memory in digit order

@@ -1,0 +1,358 @@
+// Regrouping by partition and merge: the grouping step of the gate
+// application (Sec. IV-A brings contributions to the same basis state
+// together before summing them) for a state that is already in the order of
+// the previous gate.
+//
+// Every gate path leaves the state sorted by the sort key of the gate just
+// applied: a fixed arrangement of the qubits outside the gate above the gate
+// qubits.  The next gate's sort key keeps the qubits outside its own gate in
+// the same relative order and moves its gate qubits to the bottom.  Among
+// the terms with equal gate bits r the two keys therefore compare alike, so
+// the state, split stably by r, consists of 2^m runs that are each already
+// sorted by the new key.  The grouping is then one stable partition by r and
+// m levels of pairwise merges, instead of a radix sort over all n key bits:
+//
+//   * counts: per tile of 4096 terms, the number of terms with each r (and
+//     the totals per r);
+//   * offsets: for every r and tile, the output position of the tile's first
+//     term with that r (the radix sort's scan kernel);
+//   * scatter: each term's new sort key (with the term's index packed below
+//     it, or in a separate index array), written stably to its run;
+//   * merge levels: runs 2k and 2k+1 are merged into one; a block takes 4096
+//     outputs of a merge, finds where they begin in each input run by a
+//     search over the merge path (32 probes per step, one warp per end),
+//     stages both slices in shared memory, and each thread merges 8 outputs
+//     and writes them back through shared memory.
+//
+// Equal keys cannot occur (basis states are unique), and on ties the left
+// run goes first, so the result equals the stable radix sort of the new
+// keys bit for bit.
+#include "internal.h"
+
+namespace sv {
+
+constexpr int RG_THREADS = 512, RG_ITEMS = 8, RG_TILE = RG_THREADS * RG_ITEMS;
+constexpr int RG_WARPS = RG_THREADS / 32;
+static_assert(RG_TILE == SORT_TILE, "partition tiles share the sort's scan kernel and scratch");
+constexpr int MG_THREADS = 512, MG_ITEMS = 8, MG_TILE = MG_THREADS * MG_ITEMS;
+
+__device__ __forceinline__ uint32_t gate_index_of(uint64_t key, const int* q, int m) {
+  uint32_t r = 0;
+#pragma unroll
+  for (int t = 0; t < 4; ++t)
+    if (t < m) r |= (uint32_t)((key >> q[t]) & 1ull) << t;
+  return r;
+}
+
+// Number of terms with each local index r, per tile (cnt[r * tiles + t])
+// and in total (hist[r], zeroed by the launcher).
+__global__ void __launch_bounds__(RG_THREADS) k_part_counts(const uint64_t* __restrict__ keys, uint64_t n,
+                                                            const GateParams gp, uint64_t tiles,
+                                                            uint32_t* __restrict__ cnt, uint32_t* __restrict__ hist) {
+  __shared__ uint32_t h[16];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int m = gp.m, D = 1 << m;
+  int q[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) q[t] = gp.q[t];
+  if (tid < 16) h[tid] = 0;
+  __syncthreads();
+  const uint64_t t = blockIdx.x;
+  const uint64_t base = t * RG_TILE + (uint64_t)warp * 32 * RG_ITEMS + lane;
+  uint64_t k[RG_ITEMS];
+#pragma unroll
+  for (int i = 0; i < RG_ITEMS; ++i) {
+    const uint64_t idx = base + i * 32;
+    k[i] = idx < n ? keys[idx] : 0ull;
+  }
+#pragma unroll
+  for (int i = 0; i < RG_ITEMS; ++i) {
+    const uint64_t idx = base + i * 32;
+    const uint32_t d = idx < n ? gate_index_of(k[i], q, m) : 16u;
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    if (d < 16 && lane == __ffs(peers) - 1) atomicAdd(&h[d], (uint32_t)__popc(peers));
+  }
+  __syncthreads();
+  if (tid < D) {
+    const uint32_t c = h[tid];
+    cnt[(uint64_t)tid * tiles + t] = c;
+    if (c) atomicAdd(&hist[tid], c);
+  }
+}
+
+// Stable scatter of the new sort keys into the runs: a tile ranks its terms
+// per warp and local index, stages them in shared memory in run order and
+// writes each run's slice at off[r * tiles + t].
+template <bool PAIRS>
+__global__ void __launch_bounds__(RG_THREADS) k_part_scatter(const uint64_t* __restrict__ keys, uint64_t n,
+                                                             const GateParams gp, uint64_t tiles,
+                                                             const uint32_t* __restrict__ off,
+                                                             uint64_t* __restrict__ sk, uint32_t* __restrict__ sidx) {
+  extern __shared__ __align__(16) uint8_t s_dyn[];
+  uint64_t* s_keys = reinterpret_cast<uint64_t*>(s_dyn);
+  uint32_t* s_vals = reinterpret_cast<uint32_t*>(s_dyn + sizeof(uint64_t) * RG_TILE);
+  __shared__ uint64_t fwd[16][16];
+  __shared__ uint32_t s_whist[RG_WARPS][16];
+  __shared__ uint32_t s_local[16];
+  __shared__ uint32_t s_out[16];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int m = gp.m, D = 1 << m, vb = gp.vbits;
+  const uint32_t dmask = (uint32_t)D - 1u;
+  for (int i = tid; i < 256; i += RG_THREADS) (&fwd[0][0])[i] = (&gp.perm->fwd[0][0])[i];
+  for (int i = tid; i < RG_WARPS * 16; i += RG_THREADS) (&s_whist[0][0])[i] = 0;
+  const uint64_t t = blockIdx.x;
+  if (tid < D) s_out[tid] = off[(uint64_t)tid * tiles + t];
+  __syncthreads();
+  const uint64_t base = t * RG_TILE + (uint64_t)warp * 32 * RG_ITEMS + lane;
+  uint64_t k[RG_ITEMS];
+  uint32_t d[RG_ITEMS], rank[RG_ITEMS];
+#pragma unroll
+  for (int i = 0; i < RG_ITEMS; ++i) {
+    const uint64_t idx = base + i * 32;
+    const bool valid = idx < n;
+    const uint64_t s = valid ? permute_bits(fwd, keys[idx]) : 0ull;
+    k[i] = vb ? ((s << vb) | idx) : s;
+    d[i] = valid ? (uint32_t)(s & dmask) : 16u;
+  }
+  const uint32_t lt_mask = (1u << lane) - 1u;
+#pragma unroll
+  for (int i = 0; i < RG_ITEMS; ++i) {
+    const uint32_t peers = __match_any_sync(0xffffffffu, d[i]);
+    const int leader = __ffs(peers) - 1;
+    uint32_t old = 0;
+    if (lane == leader && d[i] < 16) {
+      old = s_whist[warp][d[i]];
+      s_whist[warp][d[i]] = old + __popc(peers);
+    }
+    old = __shfl_sync(0xffffffffu, old, leader);
+    rank[i] = old + __popc(peers & lt_mask);
+    __syncwarp();
+  }
+  __syncthreads();
+  if (warp == 0) {  // per run: offsets of the warps within the run, then the runs' offsets in the tile
+    uint32_t cnt = 0;
+    if (lane < D) {
+      for (int w = 0; w < RG_WARPS; ++w) {
+        const uint32_t c = s_whist[w][lane];
+        s_whist[w][lane] = cnt;
+        cnt += c;
+      }
+    }
+    uint32_t x = cnt;
+#pragma unroll
+    for (int o = 1; o < 16; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane < D) s_local[lane] = x - cnt;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < RG_ITEMS; ++i) {
+    if (d[i] < 16) {
+      const uint32_t pos = s_local[d[i]] + s_whist[warp][d[i]] + rank[i];
+      s_keys[pos] = k[i];
+      if (PAIRS) s_vals[pos] = (uint32_t)(base + i * 32);
+    }
+  }
+  __syncthreads();
+  const uint32_t tile_n = (uint32_t)(n - t * RG_TILE < (uint64_t)RG_TILE ? n - t * RG_TILE : (uint64_t)RG_TILE);
+  for (uint32_t j = tid; j < tile_n; j += RG_THREADS) {
+    const uint64_t key = s_keys[j];
+    const uint32_t dd = (uint32_t)(key >> vb) & dmask;
+    const uint64_t o = (uint64_t)s_out[dd] + (j - s_local[dd]);
+    sk[o] = key;
+    if (PAIRS) sidx[o] = s_vals[j];
+  }
+}
+
+// Number of elements of A among the first o outputs of the merge of A and B
+// (ties: A first), found by one warp with 32 probes per step.
+__device__ __forceinline__ uint32_t merge_path_warp(const uint64_t* __restrict__ A, uint32_t la,
+                                                    const uint64_t* __restrict__ B, uint32_t lb, uint32_t o,
+                                                    int lane) {
+  uint32_t lo = o > lb ? o - lb : 0u, hi = o < la ? o : la;
+  while (hi - lo > 32) {
+    const uint32_t span = hi - lo;
+    const uint32_t x = lo + (uint32_t)(((uint64_t)span * (uint32_t)(lane + 1)) / 33u);
+    const bool before = A[x] <= B[o - 1 - x];  // A[x] is among the first o outputs
+    const uint32_t bt = __ballot_sync(0xffffffffu, before);
+    const int c = __popc(bt);
+    const uint32_t x_last = __shfl_sync(0xffffffffu, x, c > 0 ? c - 1 : 0);
+    const uint32_t x_first = __shfl_sync(0xffffffffu, x, c < 32 ? c : 31);
+    const uint32_t nlo = c > 0 ? x_last + 1 : lo;
+    const uint32_t nhi = c < 32 ? x_first : hi;
+    lo = nlo;
+    hi = nhi;
+  }
+  const uint32_t x = lo + (uint32_t)lane;
+  const bool before = x < hi && A[x] <= B[o - 1 - x];
+  return lo + (uint32_t)__popc(__ballot_sync(0xffffffffu, before));
+}
+
+__host__ __device__ __forceinline__ constexpr uint32_t mg_pad(uint32_t p) { return p + (p >> 4); }
+
+// One merge level: runs [R(2k L), R((2k+1) L)) and [R((2k+1) L), R((2k+2) L))
+// of the input are merged into the same positions of the output, where
+// R(e) = hist[0] + ... + hist[e-1] and L = 2^(level-1).
+template <bool PAIRS>
+__global__ void __launch_bounds__(MG_THREADS) k_merge_level(const uint64_t* __restrict__ kin,
+                                                            const uint32_t* __restrict__ vin,
+                                                            uint64_t* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                            const uint32_t* __restrict__ hist, int D, int level) {
+  extern __shared__ __align__(16) uint8_t s_dyn[];
+  uint64_t* s_k = reinterpret_cast<uint64_t*>(s_dyn);
+  uint32_t* s_v = reinterpret_cast<uint32_t*>(s_dyn + sizeof(uint64_t) * mg_pad(MG_TILE));
+  __shared__ uint32_t s_a0, s_la, s_lb, s_o0, s_o1, s_split[2];
+  __shared__ int s_live;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) {
+    uint32_t R[17];
+    R[0] = 0;
+    for (int e = 0; e < D; ++e) R[e + 1] = R[e] + hist[e];
+    const int L = 1 << (level - 1);
+    uint32_t b = blockIdx.x;
+    int live = 0;
+    for (int e = 0; e + 2 * L <= D; e += 2 * L) {
+      const uint32_t a0 = R[e], a1 = R[e + L], b1 = R[e + 2 * L];
+      const uint32_t tiles = (b1 - a0 + MG_TILE - 1) / MG_TILE;
+      if (b < tiles) {
+        s_a0 = a0;
+        s_la = a1 - a0;
+        s_lb = b1 - a1;
+        s_o0 = b * MG_TILE;
+        s_o1 = min(b * MG_TILE + MG_TILE, b1 - a0);
+        live = 1;
+        break;
+      }
+      b -= tiles;
+    }
+    s_live = live;
+  }
+  __syncthreads();
+  if (!s_live) return;
+  const uint32_t a0 = s_a0, la = s_la, lb = s_lb, o0 = s_o0, o1 = s_o1;
+  const uint64_t* A = kin + a0;
+  const uint64_t* B = A + la;
+  if (warp < 2) {
+    const uint32_t o = warp == 0 ? o0 : o1;
+    const uint32_t a = merge_path_warp(A, la, B, lb, o, lane);
+    if (lane == 0) s_split[warp] = a;
+  }
+  __syncthreads();
+  const uint32_t ia = s_split[0], na = s_split[1] - ia;
+  const uint32_t ib = o0 - ia, nb = (o1 - s_split[1]) - ib;
+  const uint32_t len = na + nb;
+  for (uint32_t j = tid; j < na; j += MG_THREADS) {
+    s_k[j] = A[ia + j];
+    if (PAIRS) s_v[j] = vin[a0 + ia + j];
+  }
+  for (uint32_t j = tid; j < nb; j += MG_THREADS) {
+    s_k[na + j] = B[ib + j];
+    if (PAIRS) s_v[na + j] = vin[a0 + la + ib + j];
+  }
+  __syncthreads();
+  // this thread's outputs: [diag, diag + MG_ITEMS) of the block's slice
+  const uint32_t diag = min((uint32_t)tid * MG_ITEMS, len);
+  uint32_t lo = diag > nb ? diag - nb : 0u, hi = diag < na ? diag : na;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (s_k[mid] <= s_k[na + diag - 1 - mid])
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  uint32_t pa = lo, pb = diag - lo;
+  uint64_t ok[MG_ITEMS];
+  uint32_t ov[MG_ITEMS];
+#pragma unroll
+  for (int j = 0; j < MG_ITEMS; ++j) {
+    ok[j] = 0;
+    ov[j] = 0;
+    if (diag + j < len) {
+      const bool take_a = pb >= nb || (pa < na && s_k[pa] <= s_k[na + pb]);
+      const uint32_t src = take_a ? pa : na + pb;
+      ok[j] = s_k[src];
+      if (PAIRS) ov[j] = s_v[src];
+      if (take_a)
+        ++pa;
+      else
+        ++pb;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < MG_ITEMS; ++j) {
+    const uint32_t p = diag + j;
+    if (p < len) {
+      s_k[mg_pad(p)] = ok[j];
+      if (PAIRS) s_v[mg_pad(p)] = ov[j];
+    }
+  }
+  __syncthreads();
+  const uint64_t ob = (uint64_t)a0 + o0;
+  for (uint32_t j = tid; j < len; j += MG_THREADS) {
+    kout[ob + j] = s_k[mg_pad(j)];
+    if (PAIRS) vout[ob + j] = s_v[mg_pad(j)];
+  }
+}
+
+static size_t part_smem(bool pairs) { return (sizeof(uint64_t) + (pairs ? sizeof(uint32_t) : 0)) * RG_TILE; }
+static size_t merge_smem(bool pairs) {
+  return (sizeof(uint64_t) + (pairs ? sizeof(uint32_t) : 0)) * (size_t)mg_pad(MG_TILE);
+}
+
+void regroup_prepare() {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_part_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)part_smem(true));
+    cudaFuncSetAttribute(k_part_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)part_smem(false));
+    cudaFuncSetAttribute(k_merge_level<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)merge_smem(true));
+    cudaFuncSetAttribute(k_merge_level<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)merge_smem(false));
+    attr_set = true;
+  }
+}
+
+int regroup_terms(const uint64_t* keys, uint64_t n, const GateParams& gp, uint64_t* sk[2], uint32_t* sidx[2],
+                  const SortScratch& sc, cudaStream_t st, int* launches, cudaError_t* cerr) {
+  const bool pairs = gp.vbits == 0;
+  const int m = gp.m, D = 1 << m;
+  const uint64_t tiles = (n + RG_TILE - 1) / RG_TILE;
+  *cerr = cudaSuccess;
+  *launches = 0;
+  regroup_prepare();
+  if (n == 0) return 0;
+  if (tiles > sc.lookback_tiles || n > 0xffffffffull || m < 1 || m > 4) {
+    *cerr = cudaErrorInvalidValue;
+    return 0;
+  }
+  uint32_t* cnt = reinterpret_cast<uint32_t*>(sc.lookback);
+  uint32_t* off = cnt + (uint64_t)D * tiles;
+  cudaMemsetAsync(sc.hist, 0, sizeof(uint32_t) * 16, st);
+  k_part_counts<<<(unsigned)tiles, RG_THREADS, 0, st>>>(keys, n, gp, tiles, cnt, sc.hist);
+  launch_tile_offsets(cnt, sc.hist, tiles, D, off, st);
+  if (pairs)
+    k_part_scatter<true><<<(unsigned)tiles, RG_THREADS, part_smem(true), st>>>(keys, n, gp, tiles, off, sk[0],
+                                                                               sidx[0]);
+  else
+    k_part_scatter<false><<<(unsigned)tiles, RG_THREADS, part_smem(false), st>>>(keys, n, gp, tiles, off, sk[0],
+                                                                                 nullptr);
+  *launches = 3;
+  int cur = 0;
+  const uint64_t grid = (n + MG_TILE - 1) / MG_TILE + (uint64_t)D;
+  for (int level = 1; level <= m; ++level) {
+    if (pairs)
+      k_merge_level<true><<<(unsigned)grid, MG_THREADS, merge_smem(true), st>>>(sk[cur], sidx[cur], sk[1 - cur],
+                                                                                sidx[1 - cur], sc.hist, D, level);
+    else
+      k_merge_level<false><<<(unsigned)grid, MG_THREADS, merge_smem(false), st>>>(sk[cur], nullptr, sk[1 - cur],
+                                                                                  nullptr, sc.hist, D, level);
+    cur ^= 1;
+    ++*launches;
+  }
+  *cerr = cudaGetLastError();
+  return cur;
+}
+
+}  // namespace sv

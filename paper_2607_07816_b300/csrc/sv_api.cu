@@ -63,8 +63,14 @@ struct sv_state {
   bool broken = false;
   sv_stats stats{};
 
-  // bucket-contiguity of the state (see local.cu)
-  int variant = 0;              // 0: group-first (sort terms, expand in the mat-vec); 1: expand-first
+  // 0: group-first, grouping by partition and merge; 1: expand-first;
+  // 2: group-first, grouping by a full radix sort
+  int variant = 0;
+  // order[b]: bit of qubit b in the sort key the state is sorted by (every
+  // gate leaves the state in its own sort-key order); order_next: the order
+  // the gate being applied will leave
+  int order[64] = {};
+  int order_next[64] = {};
   int64_t gate_index = 0;
   BitPerm* perm_dev = nullptr;
   BitPerm* perm_host = nullptr;
@@ -322,13 +328,10 @@ sv_status canonical_perm(sv_state* s, int* which) {
 
 
 
-// Bucket qubits for a gate that needs the global path: qubits outside the
-// gate whose bit is the most evenly split over the current terms (from
-// `ones`, the number of terms with each bit set), most recently used first
-// among equals, enough of them that the average bucket of the next state
-// holds about 128 terms.
+// Sort-key permutation of the gate for the state's current order, uploaded
+// for the kernels; the order it leaves goes to order_next.
 sv_status upload_perm(sv_state* s, GateParams& gp) {
-  build_perm(s->n, gp.m, gp.q, 0, nullptr, s->perm_host);
+  build_perm(s->n, gp.m, gp.q, s->order, s->perm_host, s->order_next);
   gp.perm = s->perm_dev;
   gp.n = s->n;
   gp.tbits = 0;
@@ -396,6 +399,7 @@ sv_status sv_create_ex(int n, uint64_t K, double p, int prec, void* cuda_stream,
     rc = cuda_check(s, cudaStreamSynchronize(s->st), "sv_create");
     s->N = 1;
     s->cur = 0;
+    for (int b = 0; b < 64; ++b) s->order[b] = b;
   }
   if (rc != SV_OK) {
     sv_destroy(s);
@@ -498,7 +502,7 @@ sv_status sv_apply_gate(sv_state* s, int m, const int* qubits, const double* U) 
   // The bucket-local kernel sorts and applies inside shared memory; it is used
   // for states that fit one of its batches (measured: beyond that the sorted
   // path was as fast or faster on this GPU, without bucket bookkeeping).
-  const bool local = s->variant == 0 && N <= LOCAL_BUCKET_MAX;
+  const bool local = s->variant != 1 && N <= LOCAL_BUCKET_MAX;
   static const bool debug = getenv("SV_DEBUG") != nullptr;
   if (debug)
     fprintf(stderr, "[sv] gate %lld N=%llu q=(%d,%d) -> %s\n", (long long)s->gate_index, (unsigned long long)N,
@@ -584,13 +588,27 @@ sv_status sv_apply_gate(sv_state* s, int m, const int* qubits, const double* U) 
     int vbits = 1;
     while (vbits < 63 && (N - 1) >> vbits) ++vbits;
     gp.vbits = s->n + vbits <= 64 ? vbits : 0;
-    ph_begin(s, PH_KEYS);
-    launch_gate_keys(s->keys[s->cur], N, gp, s->sk[0], s->sidx[0], s->hist, passes, s->st);
-    ph_end(s, PH_KEYS);
-    launched(s, PH_KEYS, 1);
     int w = 0, run = 0;
-    rc = gp.vbits ? sort_keys(s, N, gp.vbits, s->n, &w, &run) : sort_pairs(s, N, s->n, true, &w, &run);
-    if (rc != SV_OK) return rc;
+    if (s->variant == 0) {
+      // the state is sorted by the previous gate's key: partition by the gate
+      // bits and merge
+      cudaError_t e;
+      int nl = 0;
+      ph_begin(s, PH_SORT);
+      w = regroup_terms(s->keys[s->cur], N, gp, s->sk, s->sidx, sort_scratch(s), s->st, &nl, &e);
+      ph_end(s, PH_SORT);
+      launched(s, PH_SORT, (uint64_t)nl);
+      rc = cuda_check(s, e, "regroup");
+      if (rc != SV_OK) return rc;
+      run = 1 + m;
+    } else {
+      ph_begin(s, PH_KEYS);
+      launch_gate_keys(s->keys[s->cur], N, gp, s->sk[0], s->sidx[0], s->hist, passes, s->st);
+      ph_end(s, PH_KEYS);
+      launched(s, PH_KEYS, 1);
+      rc = gp.vbits ? sort_keys(s, N, gp.vbits, s->n, &w, &run) : sort_pairs(s, N, s->n, true, &w, &run);
+      if (rc != SV_OK) return rc;
+    }
     s->stats.sort_passes = (uint32_t)run;
     ph_begin(s, PH_HEADS);
     launch_group_heads(s->sk[w], N, m + gp.vbits, s->heads, s->lookback, s->ctl, s->st);
@@ -608,6 +626,7 @@ sv_status sv_apply_gate(sv_state* s, int m, const int* qubits, const double* U) 
     s->N = s->ctl_host->count[1];
   }
   ++s->gate_index;
+  for (int b = 0; b < s->n; ++b) s->order[b] = s->order_next[b];
   s->stats.n_pre = s->N;
   s->stats.local_gates = s->local_gates;
   s->stats.global_gates = s->global_gates;
@@ -907,6 +926,7 @@ sv_status sv_load(sv_state* s, const uint64_t* keys, const double* amps, uint64_
   if (s->ctl_host->count[3] != 0) return fail(s, SV_E_ARG, "sv_load: duplicate keys");
   s->cur = alt;
   s->N = s->ctl_host->count[2];
+  for (int b = 0; b < 64; ++b) s->order[b] = b;  // sorted by key
   return SV_OK;
 }
 
@@ -923,7 +943,7 @@ sv_status sv_last_stats(const sv_state* s, sv_stats* out) {
 
 sv_status sv_set_apply_variant(sv_state* s, int variant) {
   SV_GUARD(s);
-  if (variant != 0 && variant != 1) return fail(s, SV_E_ARG, "sv_set_apply_variant: variant must be 0 or 1");
+  if (variant < 0 || variant > 2) return fail(s, SV_E_ARG, "sv_set_apply_variant: variant must be 0, 1 or 2");
   s->variant = variant;
   return SV_OK;
 }

@@ -348,7 +348,9 @@ class SparseState:
         sv_set_timing(self.h, enable)
 
     def set_variant(self, variant: int) -> None:
-        """0: group-first (default), 1: expand-first (see include/sv.h)."""
+        """0: group-first with grouping by partition and merge (default),
+        1: expand-first, 2: group-first with a full radix sort (see
+        include/sv.h)."""
         sv_set_apply_variant(self.h, variant)
 
     def phase_times(self) -> dict:

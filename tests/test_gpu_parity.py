@@ -275,7 +275,29 @@ def test_expand_first_variant_matches_oracle_and_group_first(sv, oracle_mod, pre
         gk, ga = g.export()
         assert np.array_equal(ek, gk) and np.array_equal(ea, ga)
     with pytest.raises(sv.SVError):
-        e.set_variant(2)
+        e.set_variant(3)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_radix_grouping_variant_matches_merge_grouping(sv, oracle_mod, prec):
+    """Grouping by a full radix sort (variant 2) and by partition and merge
+    (the default) give the oracle's result and the same storage order, on
+    gates of every width, over states large enough for many merge tiles."""
+    rng = np.random.default_rng(650 + prec)
+    for trial in range(3):
+        n = int(rng.integers(20, 41))
+        K = int(rng.choice([5000, 1 << 15, 1 << 16]))
+        gates = [C.random_gate(n, int(rng.integers(1, 5)), rng, str(rng.choice(["haar", "mcx", "h"])))
+                 for _ in range(20)]
+        a = sv.SparseState(n, K, 1.0, prec=prec)
+        a.set_variant(2)
+        o = oracle_mod.Oracle(n, K, 1.0, prec=prec)
+        run_both(gates, a, o, check_every=False)
+        b = sv.SparseState(n, K, 1.0, prec=prec)
+        b.run(gates)
+        ak, aa = a.export()
+        bk, ba = b.export()
+        assert np.array_equal(ak, bk) and np.array_equal(aa, ba)
 
 
 def test_handles_release_device_memory(sv):
@@ -302,3 +324,21 @@ def test_handles_release_device_memory(sv):
         cycle()
     free1 = torch.cuda.mem_get_info()[0]
     assert free0 - free1 < 32 << 20, (free0, free1)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_merge_grouping_with_empty_and_lopsided_runs(sv, oracle_mod, prec):
+    """Gates on qubits no earlier gate touched put every term in one run of
+    the partition (the other runs empty); gates mixing fresh and used qubits
+    give lopsided runs.  Checked against the oracle after every gate."""
+    rng = np.random.default_rng(660 + prec)
+    n = 36
+    h = C.mat_h()
+    gates = [((q,), h) for q in range(14)]            # 16384 terms on qubits 0..13
+    gates += [((20, 30), C.haar_unitary(4, rng))]     # both fresh: one run of four
+    gates += [((31, 3, 22), C.haar_unitary(8, rng))]  # two fresh, one used
+    gates += [((5,), h), ((35, 34, 33, 32), C.haar_unitary(16, rng))]
+    gates += [((20, 31), C.haar_unitary(4, rng)), ((0, 35), C.haar_unitary(4, rng))]
+    g = sv.SparseState(n, 1 << 16, 1.0, prec=prec)
+    o = oracle_mod.Oracle(n, 1 << 16, 1.0, prec=prec)
+    run_both(gates, g, o)
