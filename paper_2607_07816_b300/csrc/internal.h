@@ -105,6 +105,21 @@ void launch_gate_keys(const uint64_t* keys, uint64_t n, const GateParams& gp, ui
 void launch_group_heads(const uint64_t* sk, uint64_t n, int shift, uint32_t* heads, uint64_t* lookback,
                         Ctl* ctl, cudaStream_t st);
 
+// Partner-group heads of the grouped sort keys with, per group, the present
+// mask pm (bit r: member with gate bits r present) | output mask om << 16
+// (bit r': some present r meets a nonzero U[r'][r]) in gmask, and the
+// group's first output position (exclusive scan of popc(om)) in ooff.
+// Group count in ctl->count[0], candidate count in ctl->count[1].  Uses
+// 2 * (n / 8192 + 2) lookback words.
+void launch_group_scan(const uint64_t* sk, uint64_t n, const GateParams& gp, uint32_t* heads, uint32_t* gmask,
+                       uint64_t* ooff, uint64_t* lookback, Ctl* ctl, cudaStream_t st);
+// Per-group mat-vec writing each structurally nonzero output at its
+// precomputed position; exact zeros are written as zero and counted in
+// ctl->count[3] (to be removed by launch_drop_zero_terms).
+void launch_gate_apply_slots(int prec, const uint64_t* sk, const uint32_t* sidx, uint64_t n, const uint32_t* heads,
+                             const uint32_t* gmask, const uint64_t* ooff, const void* amps_in, const GateParams& gp,
+                             uint64_t* keys_out, void* amps_out, uint64_t* probs_out, Ctl* ctl, cudaStream_t st);
+
 // Per-group mat-vec + zero drop; writes candidates and their probabilities,
 // the candidate count lands in ctl->count[1].
 uint64_t gate_apply_tiles(uint64_t n, int m);

@@ -48,6 +48,8 @@ struct sv_state {
   uint64_t* sk[2] = {nullptr, nullptr};
   uint32_t* sidx[2] = {nullptr, nullptr};
   uint32_t* heads = nullptr;
+  uint32_t* gmask = nullptr;  // per group: present mask | output mask << 16
+  uint64_t* ooff = nullptr;   // per group: first output position
   uint64_t lb_entries = 0;
   uint64_t* lookback = nullptr;
 
@@ -234,8 +236,12 @@ sv_status ensure_sort_cap(sv_state* s, uint64_t need) {
       s->sidx[i] = (uint32_t*)dev_alloc(s, cap * 4);
     }
     dev_free(s, s->heads);
+    dev_free(s, s->gmask);
+    dev_free(s, s->ooff);
     s->heads = (uint32_t*)dev_alloc(s, cap * 4);
-    if (!s->sk[0] || !s->sk[1] || !s->sidx[0] || !s->sidx[1] || !s->heads) {
+    s->gmask = (uint32_t*)dev_alloc(s, cap * 4);
+    s->ooff = (uint64_t*)dev_alloc(s, cap * 8);
+    if (!s->sk[0] || !s->sk[1] || !s->sidx[0] || !s->sidx[1] || !s->heads || !s->gmask || !s->ooff) {
       s->sort_cap = 0;
       return fail(s, SV_E_NOMEM, "sort buffer allocation failed");
     }
@@ -425,6 +431,8 @@ sv_status sv_destroy(sv_state* s) {
     dev_free(s, s->sidx[i]);
   }
   dev_free(s, s->heads);
+  dev_free(s, s->gmask);
+  dev_free(s, s->ooff);
   dev_free(s, s->lookback);
   dev_free(s, s->hist);
   dev_free(s, s->tile_counter);
@@ -611,19 +619,32 @@ sv_status sv_apply_gate(sv_state* s, int m, const int* qubits, const double* U) 
     }
     s->stats.sort_passes = (uint32_t)run;
     ph_begin(s, PH_HEADS);
-    launch_group_heads(s->sk[w], N, m + gp.vbits, s->heads, s->lookback, s->ctl, s->st);
+    launch_group_scan(s->sk[w], N, gp, s->heads, s->gmask, s->ooff, s->lookback, s->ctl, s->st);
     ph_end(s, PH_HEADS);
     ph_begin(s, PH_APPLY);
-    launch_gate_apply(s->prec, s->sk[w], s->sidx[w], N, s->heads, s->amps[s->cur], s->keys[s->cur], gp,
-                      s->keys[alt],
-                      s->amps[alt], s->probs[alt], s->lookback, s->ctl, s->st, apply_tiles);
+    launch_gate_apply_slots(s->prec, s->sk[w], s->sidx[w], N, s->heads, s->gmask, s->ooff, s->amps[s->cur], gp,
+                            s->keys[alt], s->amps[alt], s->probs[alt], s->ctl, s->st);
     ph_end(s, PH_APPLY);
     launched(s, PH_HEADS, 1);
     launched(s, PH_APPLY, 1);
     rc = sync_ctl(s, "sv_apply_gate");
     if (rc != SV_OK) return rc;
-    s->cur = alt;
-    s->N = s->ctl_host->count[1];
+    const uint64_t npre = s->ctl_host->count[1];
+    if (s->ctl_host->count[3] != 0) {  // exact cancellations: drop the zero terms in order
+      rc = ensure_lookback(s, npre / 2048 + 16);
+      if (rc != SV_OK) return rc;
+      ph_begin(s, PH_APPLY);
+      launch_drop_zero_terms(s->prec, s->keys[alt], s->amps[alt], s->probs[alt], npre, s->keys[s->cur],
+                             s->amps[s->cur], s->probs[s->cur], s->lookback, s->ctl, s->st);
+      ph_end(s, PH_APPLY);
+      launched(s, PH_APPLY, 1);
+      rc = sync_ctl(s, "sv_apply_gate");
+      if (rc != SV_OK) return rc;
+      s->N = s->ctl_host->count[2];
+    } else {
+      s->cur = alt;
+      s->N = npre;
+    }
   }
   ++s->gate_index;
   for (int b = 0; b < s->n; ++b) s->order[b] = s->order_next[b];
