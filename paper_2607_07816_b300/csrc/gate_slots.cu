@@ -51,13 +51,13 @@ __device__ __forceinline__ bool is_zero_amp(float re, float im) {
   return ((__float_as_uint(re) | __float_as_uint(im)) << 1) == 0;
 }
 
-constexpr int GS_BLOCK = 256, GS_WARPS = GS_BLOCK / 32, GS_ITEMS = 32;
-constexpr int GS_TILE = GS_BLOCK * GS_ITEMS;  // 8192 terms; warp w owns [1024 w, 1024 (w + 1))
+constexpr int GS_BLOCK = 512, GS_WARPS = GS_BLOCK / 32, GS_ITEMS = 16;
+constexpr int GS_TILE = GS_BLOCK * GS_ITEMS;  // 8192 terms; warp w owns [512 w, 512 (w + 1))
 constexpr int GS_HALO = 16;                   // a group reaches at most 15 terms past its head
 constexpr size_t GS_SMEM = sizeof(uint64_t) * (GS_TILE + GS_HALO + 1);
 
 // Term e of the staged tile (e = -1: the term before the tile) is s_k[e + 1].
-// Item j of a warp's lane l is term 1024 w + 32 j + l, so the lanes of an
+// Item j of a warp's lane l is term 512 w + 32 j + l, so the lanes of an
 // item hold consecutive terms and consecutive heads get consecutive group
 // indices (coalesced writes).
 __device__ __forceinline__ bool gs_head(const uint64_t* s_k, int e, int staged, int shift, int vb, uint32_t dmask,
@@ -109,6 +109,7 @@ __global__ void __launch_bounds__(GS_BLOCK) k_group_scan(const uint64_t* __restr
     const int wbase = warp * 32 * GS_ITEMS;
     // pass 1: the warp's head and output counts
     uint32_t nh = 0, no = 0;
+#pragma unroll 4
     for (int j = 0; j < GS_ITEMS; ++j) {
       const int e = wbase + j * 32 + lane;
       uint32_t pm, om;
@@ -147,6 +148,7 @@ __global__ void __launch_bounds__(GS_BLOCK) k_group_scan(const uint64_t* __restr
     __syncthreads();
     // pass 2: positions and coalesced writes
     uint64_t g = s_hbase + s_wh[warp], o = s_obase + s_wo[warp];
+#pragma unroll 4
     for (int j = 0; j < GS_ITEMS; ++j) {
       const int e = wbase + j * 32 + lane;
       uint32_t pm = 0, om = 0;

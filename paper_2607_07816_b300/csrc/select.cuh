@@ -35,38 +35,37 @@ __device__ __forceinline__ uint32_t z_digit(uint64_t hi, uint64_t lo, int shift,
   return (uint32_t)(z >> shift) & ((1u << D) - 1u);
 }
 
-// Adds one element per lane to the shared histograms.  Lanes with the same
-// digit are merged first (__match_any_sync): the lowest lane of each group
-// adds the group's count and mass, so a hot bin takes one atomic per warp
-// instead of one per element.  All lanes of a bin share the probability's
-// exponent (the exponent is fixed before any other bits), so the group mass
-// is the exact sum of the mantissas times a common power of two; the
-// mantissa sum is formed by three 18-bit chunked warp reductions (no chunk
-// sum can exceed 32 bits).  Probabilities below 2^-68, whose fixed-point
-// value is a truncated shift, and those of 2 or more (whose group sum could
-// exceed 128 bits) are added one by one.
-__device__ __forceinline__ void warp_hist_add(bool active, uint32_t dg, uint64_t pb, uint32_t* cnt,
-                                              uint64_t* mass, uint32_t* err) {
-  const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t key = active ? dg : 0xffffffffu;
-  const uint32_t peers = __match_any_sync(0xffffffffu, key);
-  const uint32_t e = (uint32_t)(pb >> 52) & 0x7ffu;
-  const int sh = (int)e - 955;
-  const bool exact_shift = active && e != 0 && sh >= 0 && sh <= 68;
-  uint64_t mant = exact_shift ? ((pb & ((1ull << 52) - 1)) | (1ull << 52)) : 0ull;
-  const uint32_t s0 = __reduce_add_sync(peers, (uint32_t)(mant & 0x3ffffull));
-  const uint32_t s1 = __reduce_add_sync(peers, (uint32_t)((mant >> 18) & 0x3ffffull));
-  const uint32_t s2 = __reduce_add_sync(peers, (uint32_t)(mant >> 36));
-  if (!active) return;
-  if (lane == (uint32_t)(__ffs(peers) - 1)) {
-    atomicAdd(&cnt[dg], (uint32_t)__popc(peers));
-    const uint64_t msum = (uint64_t)s0 + ((uint64_t)s1 << 18) + ((uint64_t)s2 << 36);
-    if (msum) atomic_add_u128(&mass[2 * dg], &mass[2 * dg + 1], ((u128)msum) << sh);
+// Histogram adds with one bin's pending (count, exact fixed-point mass)
+// held in each thread's registers: a thread touches the shared histogram only
+// when its element falls into another bin than its last one.  A level whose
+// elements fall into a few bins -- the first levels over a narrow window --
+// then costs one shared atomic per thread and bin change instead of one per
+// element on a few hot addresses (64-bit shared atomics on a hot address
+// serialise).  Each thread flushes its cache before the block reads the
+// histogram.
+struct BinCache {
+  uint32_t bin = 0xffffffffu;
+  uint32_t cnt = 0;
+  u128 mass = 0;
+};
+
+__device__ __forceinline__ void bin_cache_flush(BinCache& c, uint32_t* cnt, uint64_t* mass) {
+  if (c.cnt) {
+    atomicAdd(&cnt[c.bin], c.cnt);
+    if (c.mass) atomic_add_u128(&mass[2 * c.bin], &mass[2 * c.bin + 1], c.mass);
   }
-  if (active && !exact_shift && e != 0) {  // tiny (or above 2) probability: added alone
-    u128 v = fx_from_bits(pb, err);
-    if (v) atomic_add_u128(&mass[2 * dg], &mass[2 * dg + 1], v);
+  c.cnt = 0;
+  c.mass = 0;
+}
+
+__device__ __forceinline__ void hist_add(uint32_t dg, uint64_t pb, uint32_t* cnt, uint64_t* mass, uint32_t* err,
+                                         BinCache& c) {
+  if (c.bin != dg) {
+    bin_cache_flush(c, cnt, mass);
+    c.bin = dg;
   }
+  c.cnt += 1;
+  c.mass += fx_from_bits(pb, err);
 }
 
 }  // namespace sv

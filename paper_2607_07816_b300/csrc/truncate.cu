@@ -52,18 +52,16 @@ __global__ void __launch_bounds__(256) k_select_hist(const uint64_t* __restrict_
     s_mass[2 * i] = s_mass[2 * i + 1] = 0;
   }
   __syncthreads();
-  // whole warps iterate together (the warp reductions need all 32 lanes)
-  const uint64_t span = (c1 - c0 + blockDim.x - 1) / blockDim.x * blockDim.x;
-  for (uint64_t i = c0 + threadIdx.x; i < c0 + span; i += blockDim.x) {
-    bool active = i < c1;
-    uint64_t pb = active ? P[i] : 0ull;
-    uint64_t hi = ~pb;
-    if (active && bits <= 64 && ((hi ^ ph) >> (64 - bits)) != 0) active = false;
-    uint64_t lo = (active && need_lo) ? Kk[i] : 0ull;
-    if (active && bits > 64 && !z_matches(hi, lo, ph, pl, bits)) active = false;
-    uint32_t dg = active ? z_digit(hi, lo, shift, D) : 0u;
-    warp_hist_add(active, dg, pb, s_cnt, s_mass, &ctl->err);
+  BinCache cache;
+  for (uint64_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
+    const uint64_t pb = P[i];
+    const uint64_t hi = ~pb;
+    if (bits <= 64 && bits > 0 && ((hi ^ ph) >> (64 - bits)) != 0) continue;
+    const uint64_t lo = need_lo ? Kk[i] : 0ull;
+    if (bits > 64 && !z_matches(hi, lo, ph, pl, bits)) continue;
+    hist_add(z_digit(hi, lo, shift, D), pb, s_cnt, s_mass, &ctl->err, cache);
   }
+  bin_cache_flush(cache, s_cnt, s_mass);
   __syncthreads();
   for (int i = threadIdx.x; i < (1 << D); i += blockDim.x) {
     if (s_cnt[i]) {
@@ -85,10 +83,10 @@ void launch_select_hist(const uint64_t* probs, const uint64_t* keys, uint64_t n,
 }
 
 // ---------------------------------------------------------------- sample window
-// The cut is located from a sample first: SAMPLE_N probabilities at evenly
-// spaced positions are sorted in shared memory, the sample rank of the cut is
-// estimated (count: K * SAMPLE_N / N; mass: the sample prefix whose mass
-// fraction reaches p) and a window of +-4 binomial standard deviations (+16)
+// The cut is located from a sample first: from SAMPLE_N probabilities at
+// evenly spaced positions the sample rank of the cut is estimated (count:
+// K * SAMPLE_N / N, two order statistics found by a radix select; mass: the
+// prefix of the sorted sample whose mass fraction reaches p) and a window of +-4 binomial standard deviations (+16)
 // around it is turned into a probability interval [lo, hi].  One streaming
 // pass then sums the exact fixed-point mass of all terms, counts and sums the
 // terms above hi, and gathers the terms inside [lo, hi].  If the window
@@ -162,11 +160,75 @@ __device__ void block_sort_samples(uint32_t* a, uint32_t* tmp, uint32_t* whist /
   }
 }
 
+// Values of ascending ranks r[0] and r[1] among the SAMPLE_N 32-bit keys in
+// a (shared memory), by a radix select: four 8-bit digits, most significant
+// first; for each rank a histogram of the digit among the keys that match the
+// digits fixed so far (warp-aggregated shared atomics), then the bin that
+// holds the rank.  out[t] receives the value of rank r[t].
+__device__ void block_select_two(const uint32_t* a, const int* r, uint32_t* hist /* [2][256] */,
+                                 uint32_t* pref /* [2] */, uint32_t* rem /* [2] */) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int ITEMS = SAMPLE_N / SAMPLE_THREADS;
+  uint32_t k[ITEMS];
+#pragma unroll
+  for (int i = 0; i < ITEMS; ++i) k[i] = a[i * SAMPLE_THREADS + tid];
+  if (tid < 2) {
+    pref[tid] = 0;
+    rem[tid] = (uint32_t)r[tid];
+  }
+  for (int pass = 0; pass < 4; ++pass) {
+    const int shift = 24 - 8 * pass;
+    for (int i = tid; i < 512; i += SAMPLE_THREADS) hist[i] = 0;
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const uint32_t pf = pref[t];
+#pragma unroll
+      for (int i = 0; i < ITEMS; ++i) {
+        const bool match = pass == 0 || ((k[i] ^ pf) >> (shift + 8)) == 0;
+        const uint32_t d = match ? (k[i] >> shift) & 255u : 256u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        if (d < 256u && lane == __ffs(peers) - 1) atomicAdd(&hist[t * 256 + d], (uint32_t)__popc(peers));
+      }
+    }
+    __syncthreads();
+    if (warp < 2) {  // warp t finds the bin of rank rem[t]: lane l scans bins 8l .. 8l + 7
+      const uint32_t* h = hist + warp * 256;
+      uint32_t c[8], sum = 0;
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        c[b] = h[lane * 8 + b];
+        sum += c[b];
+      }
+      uint32_t x = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      const uint32_t before = x - sum, want = rem[warp];
+      if (want >= before && want < x) {  // exactly one lane holds the rank
+        uint32_t acc = before;
+        for (int b = 0; b < 8; ++b) {
+          if (want < acc + c[b]) {
+            pref[warp] |= (uint32_t)(lane * 8 + b) << shift;
+            rem[warp] = want - acc;
+            break;
+          }
+          acc += c[b];
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // The cut is located from a sample first: SAMPLE_N probabilities at evenly
 // spaced positions, reduced to the top 32 bits of their inverted bit pattern
-// (exponent and 20 mantissa bits), are sorted in shared memory; the sample
-// rank of the cut is estimated (count: K * SAMPLE_N / N; mass: the sample
-// prefix whose mass fraction reaches p) and a window of +-4 binomial
+// (exponent and 20 mantissa bits), are ranked in shared memory; the sample
+// rank of the cut is estimated (count: K * SAMPLE_N / N, and only the two
+// window ends are selected; mass: the sorted sample's prefix whose mass
+// fraction reaches p) and a window of +-4 binomial
 // standard deviations (+16; doubled for mass) around it becomes a
 // probability interval [lo, hi], rounded outwards.  The sample only steers
 // the work: the cut found afterwards is the exact one either way.
@@ -195,13 +257,30 @@ __global__ void __launch_bounds__(SAMPLE_THREADS) k_sample_window(const uint64_t
     a[j] = (uint32_t)((~probs[idx]) >> 31);  // drop the constant top bit, keep 32 bits
   }
   __syncthreads();
-  block_sort_samples(a, tmp, whist, dsum, wtot);  // 4 passes: result back in a
-  if (mode == 1) {
+  if (mode == 1) {  // by count: only two order statistics of the sample are needed
+    __shared__ int s_r[2];
+    __shared__ uint32_t s_pref[2], s_rem[2];
     if (tid == 0) {
-      double r = (double)count_target * SAMPLE_N / (double)n - 1.0;
-      s_rank = (int)(r < 0 ? 0 : (r > SAMPLE_N - 1 ? SAMPLE_N - 1 : r));
+      const double rr = (double)count_target * SAMPLE_N / (double)n - 1.0;
+      const int r = (int)(rr < 0 ? 0 : (rr > SAMPLE_N - 1 ? SAMPLE_N - 1 : rr));
+      const double q = (r + 1.0) / SAMPLE_N;
+      const int delta = (int)(4.0 * sqrt(SAMPLE_N * q * (1.0 - q)) + 16.0);
+      s_r[0] = r - delta;
+      s_r[1] = r + delta;
     }
-  } else {
+    __syncthreads();
+    const int rh = s_r[0], rl = s_r[1];
+    const int rs[2] = {rh < 0 ? 0 : rh, rl > SAMPLE_N - 1 ? SAMPLE_N - 1 : rl};
+    block_select_two(a, rs, whist, s_pref, s_rem);
+    if (tid == 0) {
+      // inverted patterns: a smaller value is a larger probability
+      ctl->win_hi = rh <= 0 ? 0x7ff0000000000000ull : ~(((uint64_t)s_pref[0] << 31) | (1ull << 63));
+      ctl->win_lo = rl >= SAMPLE_N - 1 ? 0ull : ~((((uint64_t)s_pref[1] << 31) | (1ull << 63)) | 0x7fffffffull);
+    }
+    return;
+  }
+  block_sort_samples(a, tmp, whist, dsum, wtot);  // 4 passes: result back in a
+  {
     constexpr int PER = SAMPLE_N / SAMPLE_THREADS;
     double loc = 0.0;
     for (int k = 0; k < PER; ++k)
@@ -233,7 +312,7 @@ __global__ void __launch_bounds__(SAMPLE_THREADS) k_sample_window(const uint64_t
   if (tid == 0) {
     const int r = s_rank;
     const double q = (r + 1.0) / SAMPLE_N;
-    const int delta = (int)(4.0 * sqrt(SAMPLE_N * q * (1.0 - q)) + 16.0) * (mode == 1 ? 1 : 2);
+    const int delta = (int)(4.0 * sqrt(SAMPLE_N * q * (1.0 - q)) + 16.0) * 2;
     const int rh = r - delta, rl = r + delta;
     // inverted patterns: a smaller value is a larger probability
     ctl->win_hi = rh <= 0 ? 0x7ff0000000000000ull : ~(((uint64_t)a[rh] << 31) | (1ull << 63));
@@ -705,13 +784,13 @@ __global__ void __launch_bounds__(PICK_THREADS) k_select_finish(Ctl* ctl, const 
       s_mass[2 * i] = s_mass[2 * i + 1] = 0;
     }
     __syncthreads();
+    BinCache cache;
     for (uint64_t i = threadIdx.x; i < nb; i += blockDim.x) {
-      uint64_t hi = buf[2 * i], lo = buf[2 * i + 1];
+      const uint64_t hi = buf[2 * i], lo = buf[2 * i + 1];
       if (!z_matches(hi, lo, ph, pl, bits)) continue;
-      uint32_t dg = z_digit(hi, lo, shift, D);
-      atomicAdd(&s_cnt[dg], 1u);
-      atomic_add_u128(&s_mass[2 * dg], &s_mass[2 * dg + 1], fx_from_bits(~hi, &ctl->err));
+      hist_add(z_digit(hi, lo, shift, D), ~hi, s_cnt, s_mass, &ctl->err, cache);
     }
+    bin_cache_flush(cache, s_cnt, s_mass);
     __syncthreads();
     block_pick(s_cnt, s_mass, ctl, p);
   }
