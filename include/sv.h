@@ -91,7 +91,10 @@ sv_status sv_apply_gate(sv_state* s, int m, const int* qubits, const double* U);
  * canonical order whose mass reaches p * total), then c = min(c_p, K); if
  * c < N the first c terms are kept and scaled by 1/sqrt(kept mass).
  * kept (nullable) receives c; retained_fraction (nullable) receives
- * kept mass / total mass (1 when nothing was cut).  Synchronises. */
+ * kept mass / total mass (1 when nothing was cut).  Waits for the cut; the
+ * renormalising compaction is left running on the stream and the number of
+ * terms it wrote is checked at the handle's next wait (an unexpected count
+ * then fails that call with SV_E_STATE). */
 sv_status sv_truncate(sv_state* s, uint64_t* kept, double* retained_fraction);
 
 /* Most probable basis state in canonical order (Sec. V).  Synchronises;

@@ -14,7 +14,6 @@ constexpr int MAX_PASSES = 8;
 constexpr int SORT_THREADS = 512;
 constexpr int SORT_ITEMS = 8;
 constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;
-constexpr int APPLY_BLOCK = 256;
 
 // Scratch used by one LSD radix sort.
 struct SortScratch {
@@ -60,6 +59,14 @@ struct BitPerm {
   uint64_t inv[16][16];  // sort key -> key
 };
 
+// Per-gate tables uploaded once per gate (one copy) and read by the kernels
+// through the pointers in GateParams, which stays small enough to pass by
+// value cheaply.
+struct GateTables {
+  BitPerm perm;
+  double U[512];
+};
+
 // Gate parameters passed by value to the gate kernels.
 struct GateParams {
   uint64_t qmask;
@@ -69,7 +76,7 @@ struct GateParams {
   int qs[4];           // the same qubits in ascending order
   uint32_t re_nz[16];  // bit r set when Re U[r_out][r] != 0
   uint32_t im_nz[16];  // bit r set when Im U[r_out][r] != 0
-  double U[512];       // U[r_out][r] as (re, im), row-major
+  const double* U;     // device copy of U[r_out][r] as (re, im), row-major
   const BitPerm* perm; // device copy of this gate's sort-key permutation
   int n;               // qubits
   int tbits;           // number of bucket qubits (top bits of the sort key)
@@ -119,14 +126,6 @@ void launch_group_scan(const uint64_t* sk, uint64_t n, const GateParams& gp, uin
 void launch_gate_apply_slots(int prec, const uint64_t* sk, const uint32_t* sidx, uint64_t n, const uint32_t* heads,
                              const uint32_t* gmask, const uint64_t* ooff, const void* amps_in, const GateParams& gp,
                              uint64_t* keys_out, void* amps_out, uint64_t* probs_out, Ctl* ctl, cudaStream_t st);
-
-// Per-group mat-vec + zero drop; writes candidates and their probabilities,
-// the candidate count lands in ctl->count[1].
-uint64_t gate_apply_tiles(uint64_t n, int m);
-void launch_gate_apply(int prec, const uint64_t* sk, const uint32_t* sidx, uint64_t n,
-                       const uint32_t* heads, const void* amps_in, const uint64_t* keys_in, const GateParams& gp,
-                       uint64_t* keys_out, void* amps_out, uint64_t* probs_out, uint64_t* lookback,
-                       Ctl* ctl, cudaStream_t st, uint64_t max_tiles);
 
 // Local gate on a bucket-contiguous state (no bucket qubit in the gate):
 // each block takes the buckets that start in its chunk, sorts them in

@@ -2,12 +2,15 @@
 // sequences the kernels of one gate application, one truncation and the
 // readouts on the handle's stream.
 //
-// Per gate (Sec. IV-A): key transform + digit histograms -> LSD radix sort
-// on (bits outside the gate, then the gate bits) -> partner-group heads ->
-// per-group mat-vec with zero drop and ordered compaction.
-// Per truncation (Sec. III, Sec. IV-B): radix select of the cut on the
-// canonical composite by mass (p) and/or by count (K) -> renormalising
-// compaction.  Readout (Sec. V): argmax in canonical order.
+// Per gate (Sec. IV-A): grouping of the terms by the gate's sort key (the
+// qubits outside the gate in the state's current order, the gate bits at the
+// bottom) by a stable partition on the gate bits and pairwise merges ->
+// partner-group heads with their output positions -> per-group mat-vec,
+// exact zeros removed by an order-preserving pass when there are any; states
+// of at most 4096 terms do the gate in one shared-memory kernel.
+// Per truncation (Sec. III, Sec. IV-B): sampled window, radix select of the
+// cut on the canonical composite by mass (p) and/or by count (K) ->
+// renormalising compaction.  Readout (Sec. V): argmax in canonical order.
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -73,9 +76,13 @@ struct sv_state {
   // the gate being applied will leave
   int order[64] = {};
   int order_next[64] = {};
+  // a truncation returns without waiting for its compaction; the count it
+  // wrote is compared with the cut at the next wait on the stream
+  bool kept_pending = false;
+  uint64_t kept_expected = 0;
   int64_t gate_index = 0;
-  BitPerm* perm_dev = nullptr;
-  BitPerm* perm_host = nullptr;
+  GateTables* tab_dev = nullptr;   // this gate's permutation and U
+  GateTables* tab_host = nullptr;  // pinned staging of tab_dev
   uint64_t local_gates = 0, global_gates = 0, local_fallbacks = 0;
 
   bool timing = false;
@@ -103,10 +110,12 @@ void* dev_alloc(sv_state* s, size_t bytes) {
 
 void dev_free(sv_state* s, void* p) {
   if (!p) return;
-  if (s->custom_alloc)
+  if (s->custom_alloc) {
+    cudaStreamSynchronize(s->st);  // work enqueued without a wait may still use p
     s->alloc.free(p, s->alloc.ctx);
-  else
+  } else {
     cudaFree(p);
+  }
 }
 
 void ph_begin(sv_state* s, int ph) {
@@ -165,6 +174,13 @@ sv_status sync_ctl(sv_state* s, const char* where) {
   if (s->ctl_host->err & ERR_INVARIANT) {
     s->broken = true;
     return fail(s, SV_E_STATE, std::string(where) + ": duplicate keys in the state");
+  }
+  if (s->kept_pending) {
+    s->kept_pending = false;
+    if (s->ctl_host->kept_check != s->kept_expected) {
+      s->broken = true;
+      return fail(s, SV_E_STATE, std::string(where) + ": truncation kept an unexpected number of terms");
+    }
   }
   if (s->ctl_host->err & ERR_MASS) {
     s->broken = true;
@@ -337,14 +353,17 @@ sv_status canonical_perm(sv_state* s, int* which) {
 // Sort-key permutation of the gate for the state's current order, uploaded
 // for the kernels; the order it leaves goes to order_next.
 sv_status upload_perm(sv_state* s, GateParams& gp) {
-  build_perm(s->n, gp.m, gp.q, s->order, s->perm_host, s->order_next);
-  gp.perm = s->perm_dev;
+  build_perm(s->n, gp.m, gp.q, s->order, &s->tab_host->perm, s->order_next);
+  gp.perm = &s->tab_dev->perm;
+  gp.U = s->tab_dev->U;
   gp.n = s->n;
   gp.tbits = 0;
   gp.pmask = 0;
-  g_h2d += sizeof(BitPerm);
-  return cuda_check(s, cudaMemcpyAsync(s->perm_dev, s->perm_host, sizeof(BitPerm), cudaMemcpyHostToDevice, s->st),
-                    "gate permutation upload");
+  // the permutation and the 2 d^2 doubles of U in one copy
+  const size_t bytes = offsetof(GateTables, U) + sizeof(double) * 2 * (1u << (2 * gp.m));
+  g_h2d += bytes;
+  return cuda_check(s, cudaMemcpyAsync(s->tab_dev, s->tab_host, bytes, cudaMemcpyHostToDevice, s->st),
+                    "gate table upload");
 }
 
 #define SV_GUARD(s)                                                    \
@@ -384,11 +403,11 @@ sv_status sv_create_ex(int n, uint64_t K, double p, int prec, void* cuda_stream,
   s->ss.buf = (uint64_t*)dev_alloc(s, sizeof(uint64_t) * 2 * FINISH_CAP);
   if (!s->hist || !s->tile_counter || !s->ctl || !s->ss.hist_count || !s->ss.hist_mass || !s->ss.buf)
     rc = SV_E_NOMEM;
-  s->perm_dev = (BitPerm*)dev_alloc(s, sizeof(BitPerm));
-  if (!s->perm_dev) rc = SV_E_NOMEM;
+  s->tab_dev = (GateTables*)dev_alloc(s, sizeof(GateTables));
+  if (!s->tab_dev) rc = SV_E_NOMEM;
   if (rc == SV_OK && (cudaMallocHost(&s->hist_host, sizeof(uint32_t) * MAX_PASSES * RADIX) != cudaSuccess ||
                       cudaMallocHost(&s->ctl_host, sizeof(Ctl)) != cudaSuccess ||
-                      cudaMallocHost(&s->perm_host, sizeof(BitPerm)) != cudaSuccess))
+                      cudaMallocHost(&s->tab_host, sizeof(GateTables)) != cudaSuccess))
     rc = SV_E_CUDA;
   if (rc == SV_OK) rc = ensure_state_cap(s, 4096);
   if (rc == SV_OK) rc = ensure_sort_cap(s, 4096);
@@ -452,8 +471,8 @@ sv_status sv_destroy(sv_state* s) {
   }
   if (s->hist_host) cudaFreeHost(s->hist_host);
   if (s->ctl_host) cudaFreeHost(s->ctl_host);
-  if (s->perm_host) cudaFreeHost(s->perm_host);
-  dev_free(s, s->perm_dev);
+  if (s->tab_host) cudaFreeHost(s->tab_host);
+  dev_free(s, s->tab_dev);
   delete s;
   return SV_OK;
 }
@@ -484,8 +503,8 @@ sv_status sv_apply_gate(sv_state* s, int m, const int* qubits, const double* U) 
   for (int ro = 0; ro < d; ++ro)
     for (int r = 0; r < d; ++r) {
       double ur = U[2 * (ro * d + r)], ui = U[2 * (ro * d + r) + 1];
-      gp.U[2 * (ro * d + r)] = ur;
-      gp.U[2 * (ro * d + r) + 1] = ui;
+      s->tab_host->U[2 * (ro * d + r)] = ur;  // uploaded with the permutation
+      s->tab_host->U[2 * (ro * d + r) + 1] = ui;
       // complex64: the zero pattern is that of the float-rounded entries
       bool rz = s->prec == SV_C128 ? ur != 0.0 : (float)ur != 0.0f;
       bool iz = s->prec == SV_C128 ? ui != 0.0 : (float)ui != 0.0f;
@@ -503,8 +522,7 @@ sv_status sv_apply_gate(sv_state* s, int m, const int* qubits, const double* U) 
     return fail(s, SV_E_ARG, "sv_apply_gate: state too large for 32-bit term indices");
   sv_status rc = ensure_state_cap(s, N << m);
   if (rc == SV_OK) rc = ensure_sort_cap(s, N);
-  const uint64_t apply_tiles = gate_apply_tiles(N, m);
-  if (rc == SV_OK) rc = ensure_lookback(s, apply_tiles + 16);
+  if (rc == SV_OK) rc = ensure_lookback(s, 2 * (N / 8192 + 2) + 16);  // the group scan's two look-backs
   if (rc != SV_OK) return rc;
   const int alt = 1 - s->cur;
   // The bucket-local kernel sorts and applies inside shared memory; it is used
@@ -816,12 +834,13 @@ sv_status sv_truncate(sv_state* s, uint64_t* kept, double* retained_fraction) {
         launched(s, PH_COMPACT, 2);
       }
       ph_end(s, PH_COMPACT);
-      rc = sync_ctl(s, "sv_truncate");
+      // no wait here: the next wait on the stream checks the count written
+      rc = cuda_check(s, cudaMemcpyAsync(&s->ctl->kept_check, &s->ctl->count[2], sizeof(uint64_t),
+                                         cudaMemcpyDeviceToDevice, s->st),
+                      "sv_truncate");
       if (rc != SV_OK) return rc;
-      if (s->ctl_host->count[2] != c) {
-        s->broken = true;
-        return fail(s, SV_E_STATE, "truncation kept an unexpected number of terms");
-      }
+      s->kept_pending = true;
+      s->kept_expected = c;
       double Sc = u128_to_double(s->ctl_host->cut_mass_hi, s->ctl_host->cut_mass_lo);
       f = Sc / SN;
       s->F = s->F * f;
