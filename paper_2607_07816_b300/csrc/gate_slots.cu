@@ -15,9 +15,9 @@
 //     head count and popc(om) are scanned over the block and over the tiles
 //     (two decoupled look-backs, one warp each), and every group's head
 //     position, masks and first output position are written;
-//   * k_gate_apply_slots: a warp takes 32 groups, stages their members'
-//     amplitudes in shared memory, orders the groups' output slots by member
-//     count (so the lanes of a round run chains of equal length), and each
+//   * k_gate_apply_slots: a warp takes a batch of groups, stages their
+//     members' amplitudes in shared memory, orders the groups' output slots
+//     by member count (so the lanes of a round run chains of equal length), and each
 //     lane computes one output with the fused multiply-add chain of the rest
 //     of the library (present r ascending, zero components of U skipped) and
 //     writes it at its position.  No barrier or look-back follows the
@@ -195,30 +195,60 @@ void launch_group_scan(const uint64_t* sk, uint64_t n, const GateParams& gp, uin
                                                            lookback + tiles + 1, ctl);
 }
 
-constexpr int AS_BLOCK = 256, AS_WARPS = AS_BLOCK / 32;
+// A warp takes a batch of 32 * gpl groups.  Larger batches leave fewer
+// rounds whose lanes run chains of different lengths; smaller ones leave
+// room for more warps per SM.  The complex64 mat-vec takes gpl = 4 (for
+// m <= 2), the complex128 one, bound by the FP64 pipe, gpl = 1.  A batch
+// holds at most 32 * gpl * 2^m members and output slots.
+constexpr int AS_WARPS = 8, AS_BLOCK = AS_WARPS * 32;
 
-template <typename Real>
-static size_t slots_smem(int m) {
-  return (size_t)AS_WARPS * (32u << m) * (sizeof(typename SCplx<Real>::T) + sizeof(uint16_t));
+__host__ __device__ __forceinline__ int slots_gpl(int prec, int m) {
+  return prec == 0 ? 1 : (m <= 2 ? 4 : (m == 3 ? 2 : 1));
 }
 
-template <typename Real>
+// Per-warp shared layout of a batch of GC = 32 * gpl groups and MC = GC * 2^m
+// members: x[MC] (amplitudes), ob[GC], rest[GC], pmom[GC], mb[GC], sst[GC],
+// slots[MC], oc[GC].
+template <typename C2>
+struct SlotsLayout {
+  C2* x;
+  uint64_t *ob, *rest;
+  uint32_t* pmom;
+  uint16_t *mb, *sst, *slots;
+  uint8_t* oc;
+  __host__ __device__ static size_t bytes(uint32_t gc, uint32_t mc) {
+    const size_t b = (size_t)mc * sizeof(C2) + (size_t)gc * (8 + 8 + 4 + 2 + 2 + 1) + (size_t)mc * 2;
+    return (b + 15) & ~(size_t)15;
+  }
+  __device__ SlotsLayout(uint8_t* base, uint32_t gc, uint32_t mc) {
+    x = reinterpret_cast<C2*>(base);
+    ob = reinterpret_cast<uint64_t*>(base + (size_t)mc * sizeof(C2));
+    rest = ob + gc;
+    pmom = reinterpret_cast<uint32_t*>(rest + gc);
+    mb = reinterpret_cast<uint16_t*>(pmom + gc);
+    sst = mb + gc;
+    slots = sst + gc;
+    oc = reinterpret_cast<uint8_t*>(slots + mc);
+  }
+};
+
+template <typename Real, int GPL>
 __global__ void __launch_bounds__(AS_BLOCK) k_gate_apply_slots(
     const uint64_t* __restrict__ sk, const uint32_t* __restrict__ sidx, const uint32_t* __restrict__ heads,
     const uint32_t* __restrict__ gmask, const uint64_t* __restrict__ ooff,
     const typename SCplx<Real>::T* __restrict__ amps_in, const GateParams gp, uint64_t* __restrict__ keys_out,
     typename SCplx<Real>::T* __restrict__ amps_out, uint64_t* __restrict__ probs_out, Ctl* ctl) {
+  constexpr int gpl = GPL;
   typedef typename SCplx<Real>::T C2;
   extern __shared__ __align__(16) uint8_t s_dyn[];
   __shared__ Real sU[512];
   __shared__ uint32_t s_re_nz[16], s_im_nz[16];
   __shared__ uint64_t s_inv[16][16];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int m = gp.m, d = 1 << m, vb = gp.vbits;
-  const uint32_t cap = 32u << m;  // members (and output slots) of 32 groups at most
-  C2* xs = reinterpret_cast<C2*>(s_dyn) + (size_t)warp * cap;
-  uint16_t* slots = reinterpret_cast<uint16_t*>(reinterpret_cast<C2*>(s_dyn) + (size_t)AS_WARPS * cap) +
-                    (size_t)warp * cap;
+  const uint32_t lt = (1u << lane) - 1u;
+  const int m = gp.m, d = 1 << m, vb = gp.vbits, shift = m + vb;
+  const uint32_t gc = 32u * gpl, mc = gc << m;
+  SlotsLayout<C2> w(s_dyn + (size_t)warp * SlotsLayout<C2>::bytes(gc, mc), gc, mc);
   for (int i = tid; i < 2 * d * d; i += AS_BLOCK) sU[i] = (Real)gp.U[i];
   for (int i = tid; i < 256; i += AS_BLOCK) (&s_inv[0][0])[i] = (&gp.perm->inv[0][0])[i];
   if (tid < 16) {
@@ -229,69 +259,127 @@ __global__ void __launch_bounds__(AS_BLOCK) k_gate_apply_slots(
   const uint64_t G = ctl->count[0];
   const uint64_t imask = vb ? ((1ull << vb) - 1ull) : 0ull;
   uint32_t zeros = 0;
-  for (uint64_t wb = (uint64_t)blockIdx.x * AS_WARPS + warp; wb * 32 < G; wb += (uint64_t)gridDim.x * AS_WARPS) {
-    const uint64_t g = wb * 32 + lane;
-    const bool valid = g < G;
-    uint32_t h = 0, gmv = 0;
-    uint64_t ob = 0;
-    if (valid) {
-      h = heads[g];
-      gmv = gmask[g];
-      ob = ooff[g];
-    }
-    const uint32_t pm = gmv & 0xffffu, om = gmv >> 16;
-    const uint32_t s = (uint32_t)__popc(pm), c = (uint32_t)__popc(om);
-    // members of the 32 groups, packed in group order
-    uint32_t mx = s;
+  for (uint64_t wb = (uint64_t)blockIdx.x * AS_WARPS + warp; wb * gc < G; wb += (uint64_t)gridDim.x * AS_WARPS) {
+    // group j = 32 k + lane of the batch; all group loads first
+    uint32_t s[GPL], c[GPL], pos[GPL], h[GPL], gmv[GPL];
+    uint64_t ob[GPL];
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, mx, o);
-      if (lane >= o) mx += y;
+    for (int k = 0; k < GPL; ++k) {
+      h[k] = 0;
+      gmv[k] = 0;
+      ob[k] = 0;
+      const uint64_t g = wb * gc + 32 * k + lane;
+      if (k < gpl && g < G) {
+        h[k] = heads[g];
+        gmv[k] = gmask[g];
+        ob[k] = ooff[g];
+      }
     }
-    const uint32_t mb = mx - s;
-    uint64_t rest = 0;
-    for (uint32_t k = 0; k < s; ++k) {
-      const uint64_t v = sk[h + k];
-      if (k == 0) rest = v >> (m + vb);
-      const uint64_t idx = vb ? (v & imask) : (uint64_t)sidx[h + k];
-      xs[mb + k] = amps_in[idx];
+    uint32_t mrun = 0, ng = 0, mb[GPL];
+#pragma unroll
+    for (int k = 0; k < GPL; ++k) {
+      s[k] = (uint32_t)__popc(gmv[k] & 0xffffu);
+      c[k] = (uint32_t)__popc(gmv[k] >> 16);
+      uint32_t mx = s[k];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, mx, o);
+        if (lane >= o) mx += y;
+      }
+      mb[k] = mrun + mx - s[k];
+      mrun += __shfl_sync(0xffffffffu, mx, 31);
+      ng += (uint32_t)__popc(__ballot_sync(0xffffffffu, s[k] != 0));
     }
-    // output slots ordered by member count, then by group
-    uint32_t start = 0, T = 0;
-    for (int l = 0; l < 32; ++l) {
-      const uint32_t s2 = __shfl_sync(0xffffffffu, s, l), c2 = __shfl_sync(0xffffffffu, c, l);
-      T += c2;
-      if (s2 < s || (s2 == s && l < lane)) start += c2;
+    // member keys, then amplitudes (independent loads in flight together)
+    uint64_t rest[GPL];
+#pragma unroll
+    for (int k = 0; k < GPL; ++k) rest[k] = s[k] ? sk[h[k]] : 0ull;
+#pragma unroll
+    for (int k = 0; k < GPL; ++k) {
+      if (!s[k]) continue;
+      const uint64_t v0 = rest[k];
+      w.x[mb[k]] = amps_in[vb ? (v0 & imask) : (uint64_t)sidx[h[k]]];
+      for (uint32_t t = 1; t < s[k]; ++t) {
+        const uint64_t v = sk[h[k] + t];
+        w.x[mb[k] + t] = amps_in[vb ? (v & imask) : (uint64_t)sidx[h[k] + t]];
+      }
+      const uint32_t j = 32u * k + lane;
+      w.pmom[j] = gmv[k];
+      w.mb[j] = (uint16_t)mb[k];
+      w.ob[j] = ob[k];
+      w.rest[j] = v0 >> shift;
     }
+    // order the groups by member count (ballots per count), then give each
+    // ordered position its first slot (scan of the output counts)
+    uint32_t cnt = 0;
+    for (int v = 1; v <= d; ++v) {
+#pragma unroll
+      for (int k = 0; k < GPL; ++k) {
+        if (k >= gpl) continue;
+        const bool hit = s[k] == (uint32_t)v;
+        const uint32_t b = __ballot_sync(0xffffffffu, hit);
+        if (hit) pos[k] = cnt + (uint32_t)__popc(b & lt);
+        cnt += (uint32_t)__popc(b);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < GPL; ++k)
+      if (k < gpl && s[k]) w.oc[pos[k]] = (uint8_t)c[k];
+    __syncwarp();
     {
-      uint32_t rem = om, k = 0;
-      while (rem) {
-        const uint32_t ro = (uint32_t)(__ffs(rem) - 1);
-        rem &= rem - 1u;
-        slots[start + k++] = (uint16_t)((lane << 4) | ro);
+      uint32_t loc[GPL], sum = 0;
+#pragma unroll
+      for (int i = 0; i < GPL; ++i) {
+        const uint32_t p = (uint32_t)lane * gpl + i;
+        loc[i] = (i < gpl && p < ng) ? w.oc[p] : 0u;
+        sum += loc[i];
+      }
+      uint32_t x = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      uint32_t run = x - sum;
+#pragma unroll
+      for (int i = 0; i < GPL; ++i) {
+        const uint32_t p = (uint32_t)lane * gpl + i;
+        if (i < gpl && p < ng) w.sst[p] = (uint16_t)run;
+        run += loc[i];
+      }
+    }
+    __syncwarp();
+    uint32_t T = 0;
+#pragma unroll
+    for (int k = 0; k < GPL; ++k) {
+      if (k >= gpl) continue;
+      T += __reduce_add_sync(0xffffffffu, c[k]);
+      if (s[k]) {
+        const uint32_t j = 32u * k + lane;
+        uint32_t rem = w.pmom[j] >> 16, st = w.sst[pos[k]];
+        while (rem) {
+          const uint32_t ro = (uint32_t)(__ffs(rem) - 1);
+          rem &= rem - 1u;
+          w.slots[st++] = (uint16_t)((j << 4) | ro);
+        }
       }
     }
     __syncwarp();
     for (uint32_t b0 = 0; b0 < T; b0 += 32) {
       const uint32_t si = b0 + lane;
-      const bool act = si < T;
-      const uint32_t e = act ? slots[si] : 0u;
-      const int gl = (int)(e >> 4);
-      const uint32_t ro = e & 15u;
-      const uint32_t pm_g = __shfl_sync(0xffffffffu, pm, gl);
-      const uint32_t om_g = __shfl_sync(0xffffffffu, om, gl);
-      const uint32_t mb_g = __shfl_sync(0xffffffffu, mb, gl);
-      const uint64_t ob_g = __shfl_sync(0xffffffffu, ob, gl);
-      const uint64_t rest_g = __shfl_sync(0xffffffffu, rest, gl);
       bool z = false;
-      if (act) {
+      if (si < T) {
+        const uint32_t e = w.slots[si];
+        const uint32_t j = e >> 4, ro = e & 15u;
+        const uint32_t pmom = w.pmom[j], pm_g = pmom & 0xffffu, om_g = pmom >> 16;
+        const uint32_t mb_g = w.mb[j];
         const uint32_t rnz = s_re_nz[ro] & pm_g, inz = s_im_nz[ro] & pm_g;
         uint32_t cols = rnz | inz;
         Real re = (Real)0, im = (Real)0;
         while (cols) {
           const int r = __ffs(cols) - 1;
           cols &= cols - 1u;
-          const C2 x = xs[mb_g + __popc(pm_g & ((1u << r) - 1u))];
+          const C2 x = w.x[mb_g + __popc(pm_g & ((1u << r) - 1u))];
           const Real ur = sU[2 * (ro * d + r)], ui = sU[2 * (ro * d + r) + 1];
           if ((rnz >> r) & 1u) {
             re = sfma(ur, x.x, re);
@@ -302,11 +390,11 @@ __global__ void __launch_bounds__(AS_BLOCK) k_gate_apply_slots(
             im = sfma(ui, x.x, im);
           }
         }
-        const uint64_t o = ob_g + (uint64_t)__popc(om_g & ((1u << ro) - 1u));
+        const uint64_t o = w.ob[j] + (uint64_t)__popc(om_g & ((1u << ro) - 1u));
         C2 y;
         y.x = re;
         y.y = im;
-        keys_out[o] = permute_bits(s_inv, (rest_g << m) | ro);
+        keys_out[o] = permute_bits(s_inv, (w.rest[j] << m) | ro);
         amps_out[o] = y;
         probs_out[o] = amp_prob_bits(y);
         z = is_zero_amp(re, im);
@@ -322,24 +410,51 @@ void launch_gate_apply_slots(int prec, const uint64_t* sk, const uint32_t* sidx,
                              const uint32_t* gmask, const uint64_t* ooff, const void* amps_in, const GateParams& gp,
                              uint64_t* keys_out, void* amps_out, uint64_t* probs_out, Ctl* ctl, cudaStream_t st) {
   static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_gate_apply_slots<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)slots_smem<double>(4));
-    cudaFuncSetAttribute(k_gate_apply_slots<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)slots_smem<float>(4));
+  if (!attr_set) {  // the largest layouts: 32 * GPL groups of up to 16 members
+    cudaFuncSetAttribute(k_gate_apply_slots<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(SlotsLayout<double2>::bytes(32, 512) * AS_WARPS));
+    cudaFuncSetAttribute(k_gate_apply_slots<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(SlotsLayout<float2>::bytes(128, 512) * AS_WARPS));
+    cudaFuncSetAttribute(k_gate_apply_slots<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(SlotsLayout<float2>::bytes(64, 512) * AS_WARPS));
+    cudaFuncSetAttribute(k_gate_apply_slots<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(SlotsLayout<float2>::bytes(32, 512) * AS_WARPS));
     attr_set = true;
   }
   cudaMemsetAsync(&ctl->count[3], 0, sizeof(uint64_t), st);
   if (n == 0) return;
-  const uint64_t batches = (n + 31) / 32;  // groups <= n
+  const int gpl = slots_gpl(prec, gp.m);
+  const uint32_t gc = 32u * gpl, mc = gc << gp.m;
+  const size_t smem = AS_WARPS * (prec == 0 ? SlotsLayout<double2>::bytes(gc, mc) : SlotsLayout<float2>::bytes(gc, mc));
+  const uint64_t batches = (n + gc - 1) / gc;  // groups <= n
   uint64_t grid = (batches + AS_WARPS - 1) / AS_WARPS;
-  if (grid > 148ull * 4) grid = 148ull * 4;
+  static int occ[2][5] = {};  // resident blocks per SM, by precision and m
+  int& per_sm = occ[prec ? 1 : 0][gp.m];
+  if (per_sm == 0) {
+    if (prec == 0)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gate_apply_slots<double, 1>, AS_BLOCK, smem);
+    else if (gpl == 4)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gate_apply_slots<float, 4>, AS_BLOCK, smem);
+    else if (gpl == 2)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gate_apply_slots<float, 2>, AS_BLOCK, smem);
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gate_apply_slots<float, 1>, AS_BLOCK, smem);
+    if (per_sm < 1) per_sm = 1;
+  }
+  if (grid > 148ull * per_sm) grid = 148ull * per_sm;
+  const unsigned g = (unsigned)grid;
   if (prec == 0)
-    k_gate_apply_slots<double><<<(unsigned)grid, AS_BLOCK, slots_smem<double>(gp.m), st>>>(
-        sk, sidx, heads, gmask, ooff, (const double2*)amps_in, gp, keys_out, (double2*)amps_out, probs_out, ctl);
+    k_gate_apply_slots<double, 1><<<g, AS_BLOCK, smem, st>>>(sk, sidx, heads, gmask, ooff, (const double2*)amps_in,
+                                                             gp, keys_out, (double2*)amps_out, probs_out, ctl);
+  else if (gpl == 4)
+    k_gate_apply_slots<float, 4><<<g, AS_BLOCK, smem, st>>>(sk, sidx, heads, gmask, ooff, (const float2*)amps_in,
+                                                            gp, keys_out, (float2*)amps_out, probs_out, ctl);
+  else if (gpl == 2)
+    k_gate_apply_slots<float, 2><<<g, AS_BLOCK, smem, st>>>(sk, sidx, heads, gmask, ooff, (const float2*)amps_in,
+                                                            gp, keys_out, (float2*)amps_out, probs_out, ctl);
   else
-    k_gate_apply_slots<float><<<(unsigned)grid, AS_BLOCK, slots_smem<float>(gp.m), st>>>(
-        sk, sidx, heads, gmask, ooff, (const float2*)amps_in, gp, keys_out, (float2*)amps_out, probs_out, ctl);
+    k_gate_apply_slots<float, 1><<<g, AS_BLOCK, smem, st>>>(sk, sidx, heads, gmask, ooff, (const float2*)amps_in,
+                                                            gp, keys_out, (float2*)amps_out, probs_out, ctl);
 }
 
 }  // namespace sv
