@@ -197,13 +197,14 @@ void launch_group_scan(const uint64_t* sk, uint64_t n, const GateParams& gp, uin
 
 // A warp takes a batch of 32 * gpl groups.  Larger batches leave fewer
 // rounds whose lanes run chains of different lengths; smaller ones leave
-// room for more warps per SM.  The complex64 mat-vec takes gpl = 4 (for
-// m <= 2), the complex128 one, bound by the FP64 pipe, gpl = 1.  A batch
-// holds at most 32 * gpl * 2^m members and output slots.
+// room for more warps per SM (measured best: gpl = 4 for complex64 and 2
+// for complex128, which is bound by the FP64 pipe, while 32 * gpl * 2^m
+// stays at most 512).  A batch holds at most 32 * gpl * 2^m members and
+// output slots.
 constexpr int AS_WARPS = 8, AS_BLOCK = AS_WARPS * 32;
 
 __host__ __device__ __forceinline__ int slots_gpl(int prec, int m) {
-  return prec == 0 ? 1 : (m <= 2 ? 4 : (m == 3 ? 2 : 1));
+  return prec == 0 ? (m <= 3 ? 2 : 1) : (m <= 2 ? 4 : (m == 3 ? 2 : 1));
 }
 
 // Per-warp shared layout of a batch of GC = 32 * gpl groups and MC = GC * 2^m
@@ -409,52 +410,41 @@ __global__ void __launch_bounds__(AS_BLOCK) k_gate_apply_slots(
 void launch_gate_apply_slots(int prec, const uint64_t* sk, const uint32_t* sidx, uint64_t n, const uint32_t* heads,
                              const uint32_t* gmask, const uint64_t* ooff, const void* amps_in, const GateParams& gp,
                              uint64_t* keys_out, void* amps_out, uint64_t* probs_out, Ctl* ctl, cudaStream_t st) {
-  static bool attr_set = false;
-  if (!attr_set) {  // the largest layouts: 32 * GPL groups of up to 16 members
-    cudaFuncSetAttribute(k_gate_apply_slots<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(SlotsLayout<double2>::bytes(32, 512) * AS_WARPS));
-    cudaFuncSetAttribute(k_gate_apply_slots<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(SlotsLayout<float2>::bytes(128, 512) * AS_WARPS));
-    cudaFuncSetAttribute(k_gate_apply_slots<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(SlotsLayout<float2>::bytes(64, 512) * AS_WARPS));
-    cudaFuncSetAttribute(k_gate_apply_slots<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(SlotsLayout<float2>::bytes(32, 512) * AS_WARPS));
-    attr_set = true;
-  }
-  cudaMemsetAsync(&ctl->count[3], 0, sizeof(uint64_t), st);
-  if (n == 0) return;
   const int gpl = slots_gpl(prec, gp.m);
   const uint32_t gc = 32u * gpl, mc = gc << gp.m;
   const size_t smem = AS_WARPS * (prec == 0 ? SlotsLayout<double2>::bytes(gc, mc) : SlotsLayout<float2>::bytes(gc, mc));
+  cudaMemsetAsync(&ctl->count[3], 0, sizeof(uint64_t), st);
+  if (n == 0) return;
   const uint64_t batches = (n + gc - 1) / gc;  // groups <= n
   uint64_t grid = (batches + AS_WARPS - 1) / AS_WARPS;
   static int occ[2][5] = {};  // resident blocks per SM, by precision and m
   int& per_sm = occ[prec ? 1 : 0][gp.m];
-  if (per_sm == 0) {
-    if (prec == 0)
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gate_apply_slots<double, 1>, AS_BLOCK, smem);
-    else if (gpl == 4)
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gate_apply_slots<float, 4>, AS_BLOCK, smem);
-    else if (gpl == 2)
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gate_apply_slots<float, 2>, AS_BLOCK, smem);
+#define SV_SLOTS(R, C2, GPLV)                                                                                 \
+  do {                                                                                                        \
+    if (per_sm == 0) {                                                                                        \
+      cudaFuncSetAttribute(k_gate_apply_slots<R, GPLV>, cudaFuncAttributeMaxDynamicSharedMemorySize,          \
+                           (int)(AS_WARPS * SlotsLayout<C2>::bytes(32 * GPLV, 512)));                         \
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gate_apply_slots<R, GPLV>, AS_BLOCK, smem);    \
+      if (per_sm < 1) per_sm = 1;                                                                             \
+    }                                                                                                         \
+    if (grid > 148ull * per_sm) grid = 148ull * per_sm;                                                       \
+    k_gate_apply_slots<R, GPLV><<<(unsigned)grid, AS_BLOCK, smem, st>>>(                                      \
+        sk, sidx, heads, gmask, ooff, (const C2*)amps_in, gp, keys_out, (C2*)amps_out, probs_out, ctl);       \
+  } while (0)
+  if (prec == 0) {
+    if (gpl == 2)
+      SV_SLOTS(double, double2, 2);
     else
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gate_apply_slots<float, 1>, AS_BLOCK, smem);
-    if (per_sm < 1) per_sm = 1;
+      SV_SLOTS(double, double2, 1);
+  } else {
+    if (gpl == 4)
+      SV_SLOTS(float, float2, 4);
+    else if (gpl == 2)
+      SV_SLOTS(float, float2, 2);
+    else
+      SV_SLOTS(float, float2, 1);
   }
-  if (grid > 148ull * per_sm) grid = 148ull * per_sm;
-  const unsigned g = (unsigned)grid;
-  if (prec == 0)
-    k_gate_apply_slots<double, 1><<<g, AS_BLOCK, smem, st>>>(sk, sidx, heads, gmask, ooff, (const double2*)amps_in,
-                                                             gp, keys_out, (double2*)amps_out, probs_out, ctl);
-  else if (gpl == 4)
-    k_gate_apply_slots<float, 4><<<g, AS_BLOCK, smem, st>>>(sk, sidx, heads, gmask, ooff, (const float2*)amps_in,
-                                                            gp, keys_out, (float2*)amps_out, probs_out, ctl);
-  else if (gpl == 2)
-    k_gate_apply_slots<float, 2><<<g, AS_BLOCK, smem, st>>>(sk, sidx, heads, gmask, ooff, (const float2*)amps_in,
-                                                            gp, keys_out, (float2*)amps_out, probs_out, ctl);
-  else
-    k_gate_apply_slots<float, 1><<<g, AS_BLOCK, smem, st>>>(sk, sidx, heads, gmask, ooff, (const float2*)amps_in,
-                                                            gp, keys_out, (float2*)amps_out, probs_out, ctl);
+#undef SV_SLOTS
 }
 
 }  // namespace sv

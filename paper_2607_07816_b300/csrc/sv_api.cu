@@ -80,6 +80,11 @@ struct sv_state {
   // wrote is compared with the cut at the next wait on the stream
   bool kept_pending = false;
   uint64_t kept_expected = 0;
+  // per-block best kept terms of the last compaction; valid until the state
+  // changes again (the peak readout then reduces them)
+  uint64_t* peak_part = nullptr;
+  uint32_t peak_blocks = 0;
+  bool peak_ready = false;
   int64_t gate_index = 0;
   GateTables* tab_dev = nullptr;   // this gate's permutation and U
   GateTables* tab_host = nullptr;  // pinned staging of tab_dev
@@ -404,7 +409,8 @@ sv_status sv_create_ex(int n, uint64_t K, double p, int prec, void* cuda_stream,
   if (!s->hist || !s->tile_counter || !s->ctl || !s->ss.hist_count || !s->ss.hist_mass || !s->ss.buf)
     rc = SV_E_NOMEM;
   s->tab_dev = (GateTables*)dev_alloc(s, sizeof(GateTables));
-  if (!s->tab_dev) rc = SV_E_NOMEM;
+  s->peak_part = (uint64_t*)dev_alloc(s, sizeof(uint64_t) * 2 * PEAK_PARTS);
+  if (!s->tab_dev || !s->peak_part) rc = SV_E_NOMEM;
   if (rc == SV_OK && (cudaMallocHost(&s->hist_host, sizeof(uint32_t) * MAX_PASSES * RADIX) != cudaSuccess ||
                       cudaMallocHost(&s->ctl_host, sizeof(Ctl)) != cudaSuccess ||
                       cudaMallocHost(&s->tab_host, sizeof(GateTables)) != cudaSuccess))
@@ -473,6 +479,7 @@ sv_status sv_destroy(sv_state* s) {
   if (s->ctl_host) cudaFreeHost(s->ctl_host);
   if (s->tab_host) cudaFreeHost(s->tab_host);
   dev_free(s, s->tab_dev);
+  dev_free(s, s->peak_part);
   delete s;
   return SV_OK;
 }
@@ -512,6 +519,7 @@ sv_status sv_apply_gate(sv_state* s, int m, const int* qubits, const double* U) 
       if (iz) gp.im_nz[ro] |= 1u << r;
     }
   const uint64_t N = s->N;
+  s->peak_ready = false;
   s->stats.n_in = N;
   s->stats.sort_passes = 0;
   if (N == 0) {
@@ -825,12 +833,14 @@ sv_status sv_truncate(sv_state* s, uint64_t* kept, double* retained_fraction) {
       ph_begin(s, PH_COMPACT);
       if (s->ctl_host->use_window) {
         launch_truncate_windowed(s->prec, s->keys[s->cur], s->amps[s->cur], s->probs[s->cur], N,
-                                 s->keys[alt], s->amps[alt], s->probs[alt], s->ss, s->ctl, s->st);
+                                 s->keys[alt], s->amps[alt], s->probs[alt], s->ss, s->ctl, s->st, s->peak_part,
+                                 &s->peak_blocks);
         launched(s, PH_COMPACT, 4);
       } else {
         launch_set_scale(s->ctl, s->st);
         launch_truncate_compact(s->prec, s->keys[s->cur], s->amps[s->cur], s->probs[s->cur], N,
-                                s->keys[alt], s->amps[alt], s->probs[alt], s->lookback, s->ctl, s->st);
+                                s->keys[alt], s->amps[alt], s->probs[alt], s->lookback, s->ctl, s->st, s->peak_part,
+                                &s->peak_blocks);
         launched(s, PH_COMPACT, 2);
       }
       ph_end(s, PH_COMPACT);
@@ -841,6 +851,7 @@ sv_status sv_truncate(sv_state* s, uint64_t* kept, double* retained_fraction) {
       if (rc != SV_OK) return rc;
       s->kept_pending = true;
       s->kept_expected = c;
+      s->peak_ready = s->peak_blocks > 0;
       double Sc = u128_to_double(s->ctl_host->cut_mass_hi, s->ctl_host->cut_mass_lo);
       f = Sc / SN;
       s->F = s->F * f;
@@ -860,9 +871,14 @@ sv_status sv_peak(sv_state* s, uint64_t* key, double* prob) {
   if (!key || !prob) return fail(s, SV_E_ARG, "sv_peak: null output");
   if (s->N == 0) return fail(s, SV_E_STATE, "sv_peak: empty state");
   ph_begin(s, PH_PEAK);
-  launch_peak(s->probs[s->cur], s->keys[s->cur], s->N, s->ctl, s->st);
+  if (s->peak_ready) {  // the last truncation's compaction left per-block partials
+    launch_peak_partials(s->peak_part, s->peak_blocks, s->ctl, s->st);
+    launched(s, PH_PEAK, 1);
+  } else {
+    launch_peak(s->probs[s->cur], s->keys[s->cur], s->N, s->ctl, s->st);
+    launched(s, PH_PEAK, 2);
+  }
   ph_end(s, PH_PEAK);
-  launched(s, PH_PEAK, 2);
   sv_status rc = sync_ctl(s, "sv_peak");
   if (rc != SV_OK) return rc;
   *key = s->ctl_host->peak_z_lo;
@@ -930,6 +946,7 @@ sv_status sv_export(sv_state* s, uint64_t* keys, double* amps, uint64_t cap, uin
 
 sv_status sv_load(sv_state* s, const uint64_t* keys, const double* amps, uint64_t N) {
   SV_GUARD(s);
+  s->peak_ready = false;
   if (N > 0 && (!keys || !amps)) return fail(s, SV_E_ARG, "sv_load: null input");
   if (N > MAX_TERMS) return fail(s, SV_E_ARG, "sv_load: too many terms");
   if (s->n < 64)

@@ -800,6 +800,66 @@ void launch_select_finish(Ctl* ctl, const SelectScratch& ss, double p, cudaStrea
   k_select_finish<<<1, PICK_THREADS, 0, st>>>(ctl, ss.buf, p);
 }
 
+// ---------------------------------------------------------------- peak partials
+// The compactions write every kept term's final probability, so they also
+// keep each block's canonical best term (probability bits larger, then key
+// smaller): the peak readout after a truncation reduces these partials
+// instead of reading the state again.
+__device__ __forceinline__ void peak_take(uint64_t& bp, uint64_t& bk, uint64_t p, uint64_t k) {
+  if (p > bp || (p == bp && k < bk)) {
+    bp = p;
+    bk = k;
+  }
+}
+
+// Block-wide best of (bp, bk) into out[0] (probability bits), out[1] (key);
+// all threads must call it.
+__device__ void block_peak_write(uint64_t bp, uint64_t bk, uint64_t* out) {
+  __shared__ uint64_t s_p[32], s_k[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, warps = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const uint64_t p2 = __shfl_down_sync(0xffffffffu, (unsigned long long)bp, o);
+    const uint64_t k2 = __shfl_down_sync(0xffffffffu, (unsigned long long)bk, o);
+    peak_take(bp, bk, p2, k2);
+  }
+  if (lane == 0) {
+    s_p[warp] = bp;
+    s_k[warp] = bk;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    bp = lane < warps ? s_p[lane] : 0ull;
+    bk = lane < warps ? s_k[lane] : ~0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const uint64_t p2 = __shfl_down_sync(0xffffffffu, (unsigned long long)bp, o);
+      const uint64_t k2 = __shfl_down_sync(0xffffffffu, (unsigned long long)bk, o);
+      peak_take(bp, bk, p2, k2);
+    }
+    if (lane == 0) {
+      out[0] = bp;
+      out[1] = bk;
+    }
+  }
+}
+
+// Reduce the partials of the last compaction (n blocks) into ctl->peak_z_*.
+__global__ void __launch_bounds__(256) k_peak_partials(const uint64_t* __restrict__ part, uint32_t n, Ctl* ctl) {
+  uint64_t bp = 0, bk = ~0ull;
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) peak_take(bp, bk, part[2 * i], part[2 * i + 1]);
+  __shared__ uint64_t out[2];
+  block_peak_write(bp, bk, out);
+  if (threadIdx.x == 0) {
+    ctl->peak_z_hi = out[0];
+    ctl->peak_z_lo = out[1];
+  }
+}
+
+void launch_peak_partials(const uint64_t* part, uint32_t n, Ctl* ctl, cudaStream_t st) {
+  k_peak_partials<<<1, 256, 0, st>>>(part, n, ctl);
+}
+
 // ---------------------------------------------------------------- compaction
 __global__ void k_set_scale(Ctl* ctl) {
   double sc = fx_to_double(make_u128(ctl->cut_mass_hi, ctl->cut_mass_lo));
@@ -818,8 +878,9 @@ template <typename C2>
 __global__ void __launch_bounds__(TC_BLOCK) k_truncate_compact(
     const uint64_t* __restrict__ keys, const C2* __restrict__ amps, const uint64_t* __restrict__ probs,
     uint64_t n, uint64_t* __restrict__ keys_out, C2* __restrict__ amps_out,
-    uint64_t* __restrict__ probs_out, uint64_t* lookback, Ctl* ctl) {
+    uint64_t* __restrict__ probs_out, uint64_t* lookback, Ctl* ctl, uint64_t* __restrict__ peak_part) {
   typedef TileLayout<TC_BLOCK, TC_ITEMS> L;
+  uint64_t bp = 0, bk = ~0ull;
   __shared__ CompactShared<TC_BLOCK> cs;
   __shared__ uint64_t s_tile;
   const uint64_t pc = ctl->cut_pbits, kc = ctl->cut_key;
@@ -850,14 +911,17 @@ __global__ void __launch_bounds__(TC_BLOCK) k_truncate_compact(
         const uint64_t i = L::index(base, j);
         const uint64_t o = cs.tile_base_out + pos[j];
         const C2 a = amp_scaled(amps[i], s);
-        keys_out[o] = keys[i];
+        const uint64_t k = keys[i], pb = amp_prob_bits(a);
+        keys_out[o] = k;
         amps_out[o] = a;
-        probs_out[o] = amp_prob_bits(a);
+        probs_out[o] = pb;
+        peak_take(bp, bk, pb, k);
       }
     }
     if (tile == tiles - 1 && threadIdx.x == 0) ctl->count[2] = cs.tile_base_out + cs.tile_total;
     __syncthreads();
   }
+  block_peak_write(bp, bk, peak_part + 2 * blockIdx.x);
 }
 
 // Windowed compaction: tile t (same tiling as the window pass) writes its
@@ -869,10 +933,11 @@ template <typename C2>
 __global__ void __launch_bounds__(WP_BLOCK) k_truncate_write(
     const uint64_t* __restrict__ keys, const C2* __restrict__ amps, const uint32_t* __restrict__ keep_bits,
     uint64_t n, const uint64_t* __restrict__ tile_off, uint64_t* __restrict__ keys_out,
-    C2* __restrict__ amps_out, uint64_t* __restrict__ probs_out, const Ctl* ctl) {
+    C2* __restrict__ amps_out, uint64_t* __restrict__ probs_out, const Ctl* ctl, uint64_t* __restrict__ peak_part) {
   typedef TileLayout<WP_BLOCK, WP_ITEMS> L;
   __shared__ CompactShared<WP_BLOCK> cs;
   __shared__ uint16_t s_list[WP_TILE];
+  uint64_t bp = 0, bk = ~0ull;
   const double s = ctl->scale;
   const int lane = threadIdx.x & 31;
   const uint64_t tiles = (n + L::TILE - 1) / L::TILE;
@@ -901,47 +966,57 @@ __global__ void __launch_bounds__(WP_BLOCK) k_truncate_write(
     for (uint32_t t = threadIdx.x; t < kept; t += WP_BLOCK) {
       const uint64_t i = base + s_list[t];
       const C2 a = amp_scaled(amps[i], s);
-      keys_out[ob + t] = keys[i];
+      const uint64_t k = keys[i], pb = amp_prob_bits(a);
+      keys_out[ob + t] = k;
       amps_out[ob + t] = a;
-      probs_out[ob + t] = amp_prob_bits(a);
+      probs_out[ob + t] = pb;
+      peak_take(bp, bk, pb, k);
     }
     __syncthreads();
   }
+  block_peak_write(bp, bk, peak_part + 2 * blockIdx.x);
 }
 
 void launch_truncate_windowed(int prec, const uint64_t* keys, const void* amps, const uint64_t* probs,
                               uint64_t n, uint64_t* keys_out, void* amps_out, uint64_t* probs_out,
-                              const SelectScratch& ss, Ctl* ctl, cudaStream_t st) {
+                              const SelectScratch& ss, Ctl* ctl, cudaStream_t st, uint64_t* peak_part,
+                              uint32_t* peak_blocks) {
   (void)probs;  // the keep flags replace the probabilities here
   const uint64_t tiles = window_tiles(n);
   k_set_scale<<<1, 1, 0, st>>>(ctl);
   k_window_tile_counts<<<148 * 4, 256, 0, st>>>(ss.win_p, ss.win_k, ss.win_i, ctl, ss.tile_keep, ss.keep_bits);
   k_tile_scan<<<1, 1024, 0, st>>>(ss.tile_keep, tiles, ss.tile_off, ctl);
-  uint64_t grid = tiles < 148 * 8 ? tiles : 148 * 8;
+  uint64_t grid = tiles < PEAK_PARTS ? tiles : PEAK_PARTS;
   if (grid == 0) grid = 1;
+  *peak_blocks = (uint32_t)grid;
   if (prec == 0)
     k_truncate_write<double2><<<(unsigned)grid, WP_BLOCK, 0, st>>>(
-        keys, (const double2*)amps, ss.keep_bits, n, ss.tile_off, keys_out, (double2*)amps_out, probs_out, ctl);
+        keys, (const double2*)amps, ss.keep_bits, n, ss.tile_off, keys_out, (double2*)amps_out, probs_out, ctl,
+        peak_part);
   else
     k_truncate_write<float2><<<(unsigned)grid, WP_BLOCK, 0, st>>>(
-        keys, (const float2*)amps, ss.keep_bits, n, ss.tile_off, keys_out, (float2*)amps_out, probs_out, ctl);
+        keys, (const float2*)amps, ss.keep_bits, n, ss.tile_off, keys_out, (float2*)amps_out, probs_out, ctl,
+        peak_part);
 }
 
 void launch_truncate_compact(int prec, const uint64_t* keys, const void* amps, const uint64_t* probs,
                              uint64_t n, uint64_t* keys_out, void* amps_out, uint64_t* probs_out,
-                             uint64_t* lookback, Ctl* ctl, cudaStream_t st) {
+                             uint64_t* lookback, Ctl* ctl, cudaStream_t st, uint64_t* peak_part,
+                             uint32_t* peak_blocks) {
   uint64_t tiles = (n + TC_BLOCK * TC_ITEMS - 1) / (TC_BLOCK * TC_ITEMS);
   cudaMemsetAsync(lookback, 0, sizeof(uint64_t) * (tiles + 1), st);
   cudaMemsetAsync(&ctl->tile_counter[2], 0, sizeof(uint64_t), st);
   cudaMemsetAsync(&ctl->count[2], 0, sizeof(uint64_t), st);
+  *peak_blocks = 0;
   if (n == 0) return;
-  uint64_t grid = tiles < 148 * 8 ? tiles : 148 * 8;
+  uint64_t grid = tiles < PEAK_PARTS ? tiles : PEAK_PARTS;
+  *peak_blocks = (uint32_t)grid;
   if (prec == 0)
     k_truncate_compact<double2><<<(unsigned)grid, TC_BLOCK, 0, st>>>(
-        keys, (const double2*)amps, probs, n, keys_out, (double2*)amps_out, probs_out, lookback, ctl);
+        keys, (const double2*)amps, probs, n, keys_out, (double2*)amps_out, probs_out, lookback, ctl, peak_part);
   else
     k_truncate_compact<float2><<<(unsigned)grid, TC_BLOCK, 0, st>>>(
-        keys, (const float2*)amps, probs, n, keys_out, (float2*)amps_out, probs_out, lookback, ctl);
+        keys, (const float2*)amps, probs, n, keys_out, (float2*)amps_out, probs_out, lookback, ctl, peak_part);
 }
 
 // ---------------------------------------------------------------- peak

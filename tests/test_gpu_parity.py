@@ -82,8 +82,29 @@ def test_equal_probabilities_cut_by_key(sv, oracle_mod):
             g.apply_gate(q, u)
             o.apply_gate(q, u)
         assert g.num_terms() == 1 << n
+        assert g.peak() == o.peak()  # read from the state (no truncation yet)
         assert g.truncate() == o.truncate()
+        assert g.peak() == o.peak()  # reduced from the compaction's per-block partials
         assert_states_equal(g, o, what=f"K={K}")
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_peak_ties_across_many_compaction_blocks(sv, oracle_mod, prec):
+    """2^20 equal probabilities cut to K: the peak after the truncation is the
+    smallest kept key, found among the partial results of many blocks; after
+    one more gate the peak is read from the state again."""
+    n = 20
+    for K in [(1 << 19) + 12345, 3]:
+        g = sv.SparseState(n, K, 1.0, prec=prec)
+        o = oracle_mod.Oracle(n, K, 1.0, prec=prec)
+        for i in range(n):
+            g.apply_gate((i,), C.mat_h())
+            o.apply_gate((i,), C.mat_h())
+        assert g.truncate() == o.truncate()
+        assert g.peak() == o.peak()
+        g.apply_gate((3, 11), C.mat_cz())
+        o.apply_gate((3, 11), C.mat_cz())
+        assert g.peak() == o.peak()
 
 
 def test_p_cut_on_exact_prefix_and_forced_ties(sv, oracle_mod):
@@ -110,6 +131,7 @@ def test_tied_random_states(sv, oracle_mod):
         g.load(keys, amps)
         o.load(keys, amps)
         assert g.truncate() == o.truncate()
+        assert g.peak() == o.peak()
         assert_states_equal(g, o, what=f"trial {trial}")
 
 
