@@ -144,22 +144,22 @@ def phase_model(ph: str, totals: dict, prec: str, passes: int):
     S_a = amplitude bytes; per term: key 8 B, probability 8 B."""
     sa = 16 if prec == "c128" else 8
     n_in, n_pre, n_kept = totals["n_in"], totals["n_pre"], totals["n_kept"]
-    if ph == "sort":     # each pass reads and writes (sort key 8 B + index 4 B)
-        return {"bytes": passes * 24 * n_in, "flops": 0.0}
-    if ph == "keys":     # read key, write sort key + index
+    if ph == "sort":     # count pass (8 B) + scatter and merge passes (read + write the packed key: 16 B)
+        return {"bytes": (8 + 16 * passes) * n_in, "flops": 0.0}
+    if ph == "keys":     # radix-sort variant only: read key, write sort key + index
         return {"bytes": 20 * n_in, "flops": 0.0}
-    if ph == "apply":    # read sorted key + index + amplitude per input; write key+amp+prob per candidate
-        return {"bytes": (12 + sa) * totals["n_in_apply"] + (16 + sa) * totals["n_pre_apply"],
+    if ph == "apply":    # read grouped key + gathered amplitude per input; write key+amp+prob per candidate
+        return {"bytes": (8 + sa) * totals["n_in_apply"] + (16 + sa) * totals["n_pre_apply"],
                 "flops": totals["fp64_apply"]}
     if ph == "window":   # one streaming pass over the probabilities (+ window keys)
         return {"bytes": 8 * n_pre, "flops": 0.0}
     if ph == "select":   # histogram levels over the window terms
         return {"bytes": 16 * totals.get("window_terms", 0), "flops": 0.0}
-    if ph == "compact":  # read prob (+ key, amp of kept); write kept key, amp, prob
-        return {"bytes": 8 * n_pre + (8 + sa) * n_kept + (16 + sa) * n_kept, "flops": 0.0}
-    if ph == "peak":
-        return {"bytes": 8 * n_kept, "flops": 0.0}
-    if ph == "heads":
+    if ph == "compact":  # keep bit per candidate; read kept key + amp; write kept key, amp, prob
+        return {"bytes": n_pre / 8 + (8 + sa) * n_kept + (16 + sa) * n_kept, "flops": 0.0}
+    if ph == "peak":     # after a truncation: the compaction's per-block partials
+        return {"bytes": 16 * 1184 * totals["steps"], "flops": 0.0}
+    if ph == "heads":    # read the grouped keys (group records written: not counted)
         return {"bytes": 8 * n_in, "flops": 0.0}
     if ph == "local":    # read key + amplitude per input; write key + amp + prob per candidate
         return {"bytes": (8 + sa) * totals["n_in_local"] + (16 + sa) * totals["n_pre_local"],
@@ -477,10 +477,7 @@ def roofline(main, prec, peaks):
     per_launch_s = ms / 1e3 / max(1, launches)
     passes = tot["sort_passes"] / max(1, tot["steps"])
     model = phase_model(dom, tot, prec, passes if dom == "sort" else 1)
-    if dom == "sort":
-        bytes_per_launch = 24.0 * tot["n_in"] / max(1, tot["steps"])   # one pass over N_in
-    else:
-        bytes_per_launch = model["bytes"] / max(1, launches)
+    bytes_per_launch = model["bytes"] / max(1, launches)
     gbs = bytes_per_launch / per_launch_s / 1e9
     hbm_frac = gbs / peaks["hbm_gbs"]
     out = {"kernel": dom, "bound": "hbm", "achieved": round(gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
