@@ -51,6 +51,18 @@ void launch_gate_keys(const uint64_t* keys, uint64_t n, const GateParams& gp, ui
   k_gate_keys<<<(unsigned)blocks, 256, 0, st>>>(keys, n, gp.perm, sk, sidx, hist, passes, gp.vbits);
 }
 
+// ------------------------------------------------------------------ gate tables
+__global__ void __launch_bounds__(256) k_store_tables(const GateTables t, GateTables* __restrict__ dst,
+                                                      uint32_t words) {
+  const uint64_t* src = reinterpret_cast<const uint64_t*>(&t);
+  uint64_t* out = reinterpret_cast<uint64_t*>(dst);
+  for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) out[i] = src[i];
+}
+
+void launch_store_tables(const GateTables& t, GateTables* dst, size_t bytes, cudaStream_t st) {
+  k_store_tables<<<1, 256, 0, st>>>(t, dst, (uint32_t)((bytes + 7) / 8));
+}
+
 // ------------------------------------------------------------------ heads
 constexpr int HEAD_BLOCK = 256, HEAD_ITEMS = 16;
 

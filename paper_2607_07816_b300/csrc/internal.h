@@ -67,6 +67,9 @@ struct GateTables {
   double U[512];
 };
 
+// Stores the first `bytes` bytes of t (passed by value) at dst.
+void launch_store_tables(const GateTables& t, GateTables* dst, size_t bytes, cudaStream_t st);
+
 // Gate parameters passed by value to the gate kernels.
 struct GateParams {
   uint64_t qmask;

@@ -364,11 +364,14 @@ sv_status upload_perm(sv_state* s, GateParams& gp) {
   gp.n = s->n;
   gp.tbits = 0;
   gp.pmask = 0;
-  // the permutation and the 2 d^2 doubles of U in one copy
+  // the permutation and the 2 d^2 doubles of U travel as the parameters of
+  // one small kernel that stores them (no copy-engine transfer to wait for
+  // in the stream)
   const size_t bytes = offsetof(GateTables, U) + sizeof(double) * 2 * (1u << (2 * gp.m));
   g_h2d += bytes;
-  return cuda_check(s, cudaMemcpyAsync(s->tab_dev, s->tab_host, bytes, cudaMemcpyHostToDevice, s->st),
-                    "gate table upload");
+  launch_store_tables(*s->tab_host, s->tab_dev, bytes, s->st);
+  launched(s, PH_OTHER, 1);
+  return cuda_check(s, cudaGetLastError(), "gate table upload");
 }
 
 #define SV_GUARD(s)                                                    \

@@ -602,7 +602,7 @@ __global__ void __launch_bounds__(1024) k_tile_scan(const uint32_t* __restrict__
 }
 
 // ---------------------------------------------------------------- pick
-constexpr int PICK_THREADS = 256;
+constexpr int PICK_THREADS = 1024;
 
 __device__ __forceinline__ u128 shfl_up_u128(u128 v, int o) {
   uint64_t hi = __shfl_up_sync(0xffffffffu, (unsigned long long)(v >> 64), o);
