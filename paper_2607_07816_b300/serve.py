@@ -8,12 +8,21 @@ circuit by one gate per step (one svb_step for all of them), and retires a
 circuit as soon as its last gate has run: its most probable basis state
 (Sec. V) is read back and its slot and budget are released for the next
 arrivals.  Work of newly admitted and long-running circuits overlaps in the
-same steps.  The loop itself only orders requests and marshals gates; every
+same steps.
+
+A request whose K reaches solo_min_terms is not batched: a state that large
+fills the GPU by itself, so batching gains it nothing, while the single-state
+engine groups its terms faster.  It is admitted against the same budget and
+runs gate by gate on a handle and stream of its own, in a host thread, while
+the batch keeps stepping; the two streams' kernels share the GPU.  The
+result is bit for bit that of the same circuit alone on the single-state
+engine.  The loop itself only orders requests and marshals gates; every
 gate, truncation and readout runs in the library's kernels.
 """
 from __future__ import annotations
 
 import dataclasses
+import threading
 import time
 from collections import deque
 from typing import List, Optional, Sequence
@@ -60,21 +69,33 @@ def slot_limit(n_max: int, max_slots: int) -> int:
     return max(1, min(max_slots, (1 << bits) - 1))
 
 
+def _new_stream():
+    """A stream for a solo request (PyTorch supplies the CUDA streams)."""
+    import torch
+    return torch.cuda.Stream()
+
+
 class Server:
     """A continuous-batching request loop on one GPU.
 
     budget_bytes bounds the sum of the resident requests' footprints;
     max_slots bounds how many are resident at once (lowered when n_max, the
-    largest qubit count that will be served, needs more key bits)."""
+    largest qubit count that will be served, needs more key bits).  Requests
+    with K >= solo_min_terms run on single-state handles of their own, each
+    on a stream from solo_stream() (an object with a cuda_stream handle)."""
 
     def __init__(self, budget_bytes: int, max_slots: int = 512, n_max: int = 54, prec: int = sv.SV_C64,
-                 stream: int = 0, batch=None):
+                 stream: int = 0, batch=None, solo_min_terms: int = 1 << 22, solo_stream=None):
         self.budget = int(budget_bytes)
         self.max_slots = slot_limit(n_max, max_slots)
+        self.prec = prec
         self.batch = batch if batch is not None else sv.Batch(self.max_slots, prec=prec, stream=stream)
+        self.solo_min_terms = int(solo_min_terms)
+        self.solo_stream = solo_stream if solo_stream is not None else _new_stream
         self.steps = 0
         self.peak_resident = 0
         self.peak_bytes = 0
+        self.solo_served = 0
 
     def close(self):
         self.batch.close()
@@ -108,78 +129,129 @@ class Server:
         dirty = True
         slots = np.zeros(0, dtype=np.int32)
         pos = np.zeros(0, dtype=np.int64)
-        while done < n and (max_steps is None or self.steps < max_steps):
-            now = clock()
-            while order and arrivals[order[0]] <= now and len(live) + retiring < self.max_slots:
-                j = order[0]
-                c = circuits[j]
-                fp = footprint(c)
-                if used + fp > self.budget and live:
-                    break  # wait for resident requests to finish
-                order.popleft()
-                if not c.gates:
-                    results[j] = Result(j, 0, 1.0, 1.0, float(arrivals[j]), now, now)
+        solo_lock = threading.Lock()
+        solo_finished: List = []  # (request index, Result or exception) from the solo threads
+        solo_threads: List[threading.Thread] = []
+        solo_running = 0
+
+        def solo(j: int, c, admitted: float) -> None:
+            try:
+                stream = self.solo_stream()
+                st = sv.SparseState(c.n, c.K, 1.0, prec=self.prec, stream=stream.cuda_stream)
+                try:
+                    for (q, u) in c.gates:
+                        st.apply_gate(q, u)
+                        st.truncate()
+                    key, prob = st.peak()
+                    f = st.retained_mass()
+                    ks = am = None
+                    if export:
+                        ks, am = st.export()
+                finally:
+                    st.close()
+                out = Result(j, key, prob, f, float(arrivals[j]), admitted, clock(), ks, am)
+            except BaseException as e:  # noqa: BLE001 - re-raised by the loop
+                out = e
+            with solo_lock:
+                solo_finished.append((j, out))
+
+        try:
+            while done < n and (max_steps is None or self.steps < max_steps):
+                now = clock()
+                with solo_lock:
+                    finished, solo_finished[:] = list(solo_finished), []
+                for j, out in finished:
+                    if isinstance(out, BaseException):
+                        raise out
+                    results[j] = out
+                    used -= footprint(circuits[j])
+                    solo_running -= 1
                     done += 1
+                while order and arrivals[order[0]] <= now:
+                    j = order[0]
+                    c = circuits[j]
+                    fp = footprint(c)
+                    is_solo = c.K >= self.solo_min_terms and c.gates
+                    if not is_solo and len(live) + retiring >= self.max_slots:
+                        break  # wait for a slot
+                    if used + fp > self.budget and (live or solo_running):
+                        break  # wait for resident requests to finish
+                    order.popleft()
+                    if not c.gates:
+                        results[j] = Result(j, 0, 1.0, 1.0, float(arrivals[j]), now, now)
+                        done += 1
+                        continue
+                    used += fp
+                    if is_solo:
+                        t = threading.Thread(target=solo, args=(j, c, now), daemon=True)
+                        solo_running += 1
+                        self.solo_served += 1
+                        solo_threads.append(t)
+                        t.start()
+                        continue
+                    slot = self.batch.add(c.n, c.K)
+                    live[slot] = [j, 0, now, sv.PreparedGates(c.gates)]
+                    dirty = True
+                self.peak_resident = max(self.peak_resident, len(live) + solo_running)
+                self.peak_bytes = max(self.peak_bytes, used)
+                if not live:
+                    if retiring:  # an empty step frees the retired slots
+                        self.batch.step([])
+                        retiring = 0
+                    elif solo_running:  # only solo requests are running
+                        time.sleep(0.0005)
+                    elif order:  # idle until the next arrival
+                        wait = arrivals[order[0]] - clock()
+                        if wait > 0:
+                            time.sleep(min(wait, 0.01))
                     continue
-                slot = self.batch.add(c.n, c.K)
-                live[slot] = [j, 0, now, sv.PreparedGates(c.gates)]
-                used += fp
-                dirty = True
-            self.peak_resident = max(self.peak_resident, len(live))
-            self.peak_bytes = max(self.peak_bytes, used)
-            if not live:
-                if retiring:  # an empty step frees the retired slots
-                    self.batch.step([])
-                    retiring = 0
-                elif order:  # idle until the next arrival
-                    wait = arrivals[order[0]] - clock()
-                    if wait > 0:
-                        time.sleep(min(wait, 0.01))
-                continue
-            if dirty:  # residents changed: concatenate their gate tables
-                for k, sl in enumerate(slots):  # positions of the circuits that stay
-                    if int(sl) in live:
-                        live[int(sl)][1] = int(pos[k])
-                slots = np.array(list(live), dtype=np.int32)
-                preps = [live[int(sl)][3] for sl in slots]
-                counts = np.array([p.count for p in preps], dtype=np.int64)
-                base = np.concatenate([[0], np.cumsum(counts)[:-1]])
-                tm = np.concatenate([p.m for p in preps])
-                tq = np.concatenate([p.q for p in preps])
-                tu = np.concatenate([p.uptr for p in preps])
-                pos = np.array([live[int(sl)][1] for sl in slots], dtype=np.int64)
-                table = np.empty(len(slots), dtype=sv.GATE_DTYPE)
-                table["slot"] = slots
-                dirty = False
-            idx = base + pos
-            table["m"] = tm[idx]
-            table["q"] = tq[idx]
-            table["U"] = tu[idx]
-            self.batch.step_table(table)
-            self.steps += 1
-            retiring = 0
-            pos += 1
-            for k in np.nonzero(pos == counts)[0]:
-                slot = int(slots[k])
-                j, _, admitted, _ = live[slot]
-                key, prob = self.batch.peak(slot)
-                f = self.batch.retained_mass(slot)
-                ks = am = None
-                if export:
-                    ks, am = self.batch.export(slot)
-                self.batch.remove(slot)
-                retiring += 1
-                del live[slot]
-                used -= footprint(circuits[j])
-                results[j] = Result(j, key, prob, f, float(arrivals[j]), admitted, clock(), ks, am)
-                done += 1
-                dirty = True
-            if dirty:  # retirements: save the positions before a slot can be reused
-                for k, sl in enumerate(slots):
-                    if int(sl) in live:
-                        live[int(sl)][1] = int(pos[k])
-                slots = np.zeros(0, dtype=np.int32)
-                pos = np.zeros(0, dtype=np.int64)
+                if dirty:  # residents changed: concatenate their gate tables
+                    for k, sl in enumerate(slots):  # positions of the circuits that stay
+                        if int(sl) in live:
+                            live[int(sl)][1] = int(pos[k])
+                    slots = np.array(list(live), dtype=np.int32)
+                    preps = [live[int(sl)][3] for sl in slots]
+                    counts = np.array([p.count for p in preps], dtype=np.int64)
+                    base = np.concatenate([[0], np.cumsum(counts)[:-1]])
+                    tm = np.concatenate([p.m for p in preps])
+                    tq = np.concatenate([p.q for p in preps])
+                    tu = np.concatenate([p.uptr for p in preps])
+                    pos = np.array([live[int(sl)][1] for sl in slots], dtype=np.int64)
+                    table = np.empty(len(slots), dtype=sv.GATE_DTYPE)
+                    table["slot"] = slots
+                    dirty = False
+                idx = base + pos
+                table["m"] = tm[idx]
+                table["q"] = tq[idx]
+                table["U"] = tu[idx]
+                self.batch.step_table(table)
+                self.steps += 1
+                retiring = 0
+                pos += 1
+                for k in np.nonzero(pos == counts)[0]:
+                    slot = int(slots[k])
+                    j, _, admitted, _ = live[slot]
+                    key, prob = self.batch.peak(slot)
+                    f = self.batch.retained_mass(slot)
+                    ks = am = None
+                    if export:
+                        ks, am = self.batch.export(slot)
+                    self.batch.remove(slot)
+                    retiring += 1
+                    del live[slot]
+                    used -= footprint(circuits[j])
+                    results[j] = Result(j, key, prob, f, float(arrivals[j]), admitted, clock(), ks, am)
+                    done += 1
+                    dirty = True
+                if dirty:  # retirements: save the positions before a slot can be reused
+                    for k, sl in enumerate(slots):
+                        if int(sl) in live:
+                            live[int(sl)][1] = int(pos[k])
+                    slots = np.zeros(0, dtype=np.int32)
+                    pos = np.zeros(0, dtype=np.int64)
+        finally:
+            for t in solo_threads:
+                t.join()
         return results  # type: ignore[return-value]
 
 

@@ -94,3 +94,26 @@ def test_serving_stream_completes_with_large_request(serve):
         assert r.finished >= r.admitted >= r.arrival
     p50, p99 = serve.percentiles(res)
     assert 0 < p50 <= p99
+
+
+def test_solo_lane_results_equal_single_state_path(serve):
+    """Requests at or above solo_min_terms run on single-state handles of
+    their own beside the batch: each result equals the single-state path's
+    result for that circuit in the same precision, bit for bit."""
+    from paper_2607_07816_b300 import sv
+    circs = [C.serving_request(j, seed=91, large_frac=0.0, k_range=(6, 12), depth_range=(1, 3))
+             for j in range(24)]
+    circs[3] = C.brickwork_circuit(56, 2, seed=6, sigma=0.05, K=1 << 12, p=1.0)
+    arrivals = serve.poisson_arrivals(len(circs), 300.0, 4)
+    srv = serve.Server(160 << 30, n_max=56, prec=1, solo_min_terms=1 << 11)
+    res = srv.run(circs, arrivals=arrivals, export=True)
+    srv.close()
+    assert srv.solo_served == sum(1 for c in circs if c.K >= 1 << 11) >= 2
+    for r, c in zip(res, circs):
+        g = sv.SparseState(c.n, c.K, 1.0, prec=1)
+        g.run(c.gates)
+        assert (r.peak_key, r.peak_prob) == g.peak()
+        assert r.retained_mass == g.retained_mass()
+        gk, ga = g.export()
+        assert _as_dict(r.keys, r.amps) == _as_dict(gk, ga)
+        g.close()

@@ -122,3 +122,67 @@ def test_fifo_latencies_and_percentiles():
     t = serve.poisson_arrivals(20000, 50.0, 1)
     assert np.all(np.diff(t) > 0)
     assert 20000 / t[-1] == pytest.approx(50.0, rel=0.03)
+
+
+class FakeState:
+    """Stands in for a single-state handle on the CPU: counts gates."""
+    made = []
+
+    def __init__(self, n, K, p, prec=0, stream=0):
+        self.n, self.K, self.stream = n, K, stream
+        self.gates = 0
+        FakeState.made.append(self)
+
+    def apply_gate(self, q, u):
+        self.gates += 1
+
+    def truncate(self):
+        return (self.K, 1.0)
+
+    def peak(self):
+        return (1000 + self.gates, 0.25)
+
+    def retained_mass(self):
+        return 0.5
+
+    def export(self):
+        return np.zeros(0, np.uint64), np.zeros(0)
+
+    def close(self):
+        pass
+
+
+class FakeStream:
+    cuda_stream = 7
+
+
+def test_large_requests_run_solo_beside_the_batch(monkeypatch):
+    monkeypatch.setattr(serve.sv, "SparseState", FakeState)
+    FakeState.made = []
+    circs = [FakeCircuit(8, 100, [2] * 4), FakeCircuit(8, 1 << 20, [2] * 6), FakeCircuit(8, 100, [2] * 3),
+             FakeCircuit(8, 1 << 21, [1] * 5)]
+    fb = FakeBatch(8)
+    srv = serve.Server(1 << 40, max_slots=8, batch=fb, solo_min_terms=1 << 20, solo_stream=FakeStream)
+    res = srv.run(circs)
+    assert srv.solo_served == 2
+    assert [s.K for s in FakeState.made] == [1 << 20, 1 << 21]
+    assert all(s.stream == 7 for s in FakeState.made)
+    # solo requests: every gate on their own handle; batched ones: in the batch's steps
+    assert res[1].peak_key == 1006 and res[3].peak_key == 1005
+    assert res[0].peak_key == 4 and res[2].peak_key == 3
+    assert sorted(s for _, _, s in fb.adds) == [0, 1]
+    assert all(r.finished >= r.admitted for r in res)
+
+
+def test_solo_requests_share_the_budget(monkeypatch):
+    monkeypatch.setattr(serve.sv, "SparseState", FakeState)
+    FakeState.made = []
+    big = FakeCircuit(8, 1 << 20, [2] * 2)
+    small = FakeCircuit(8, 100, [2] * 2)
+    budget = serve.footprint(big) + serve.footprint(small) // 2
+    fb = FakeBatch(8)
+    srv = serve.Server(budget, max_slots=8, batch=fb, solo_min_terms=1 << 20, solo_stream=FakeStream)
+    res = srv.run([big, small])
+    # the small request does not fit beside the solo one: admitted after it finished
+    assert res[1].admitted >= res[0].finished
+    assert srv.peak_bytes <= budget
