@@ -19,10 +19,11 @@
 //   * scatter: each term's new sort key (with the term's index packed below
 //     it, or in a separate index array), written stably to its run;
 //   * merge levels: runs 2k and 2k+1 are merged into one; a block takes 4096
-//     outputs of a merge, finds where they begin in each input run by a
-//     search over the merge path (32 probes per step, one warp per end),
-//     stages both slices in shared memory, and each thread merges 8 outputs
-//     and writes them back through shared memory.
+//     outputs of a merge, whose start in each input run a first kernel finds
+//     by a search over the merge path (one warp per block, 32 probes per
+//     step, all searches in flight together); the block stages both slices in
+//     shared memory, and each thread merges 8 outputs and writes them back
+//     through shared memory.
 //
 // Equal keys cannot occur (basis states are unique), and on ties the left
 // run goes first, so the result equals the stable radix sort of the new
@@ -194,52 +195,78 @@ __host__ __device__ __forceinline__ constexpr uint32_t mg_pad(uint32_t p) { retu
 
 // One merge level: runs [R(2k L), R((2k+1) L)) and [R((2k+1) L), R((2k+2) L))
 // of the input are merged into the same positions of the output, where
-// R(e) = hist[0] + ... + hist[e-1] and L = 2^(level-1).
+// R(e) = hist[0] + ... + hist[e-1] and L = 2^(level-1).  Block b of the
+// level takes MG_TILE consecutive outputs of one pair: merge_block finds
+// which, and false for blocks past the last pair's last tile.
+__device__ __forceinline__ bool merge_block(const uint32_t* __restrict__ hist, int D, int level, uint32_t b,
+                                            uint32_t& a0, uint32_t& la, uint32_t& lb, uint32_t& o0,
+                                            uint32_t& o1) {
+  uint32_t R[17];
+  R[0] = 0;
+  for (int e = 0; e < D; ++e) R[e + 1] = R[e] + hist[e];
+  const int L = 1 << (level - 1);
+  for (int e = 0; e + 2 * L <= D; e += 2 * L) {
+    const uint32_t r0 = R[e], r1 = R[e + L], r2 = R[e + 2 * L];
+    const uint32_t tiles = (r2 - r0 + MG_TILE - 1) / MG_TILE;
+    if (b < tiles) {
+      a0 = r0;
+      la = r1 - r0;
+      lb = r2 - r1;
+      o0 = b * MG_TILE;
+      o1 = min(b * MG_TILE + MG_TILE, r2 - r0);
+      return true;
+    }
+    b -= tiles;
+  }
+  return false;
+}
+
+// Where every block of a merge level starts in its pair's first run: one warp
+// per block, all searches in flight together (the merge blocks then start
+// without a search of their own).
+__global__ void __launch_bounds__(256) k_merge_splits(const uint64_t* __restrict__ kin,
+                                                      const uint32_t* __restrict__ hist, int D, int level,
+                                                      uint32_t nblocks, uint32_t* __restrict__ splits) {
+  const uint32_t b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (b >= nblocks) return;
+  uint32_t a0, la, lb, o0, o1;
+  if (!merge_block(hist, D, level, b, a0, la, lb, o0, o1)) return;
+  const uint64_t* A = kin + a0;
+  const uint32_t a = merge_path_warp(A, la, A + la, lb, o0, lane);
+  if (lane == 0) splits[b] = a;
+}
+
 template <bool PAIRS>
 __global__ void __launch_bounds__(MG_THREADS) k_merge_level(const uint64_t* __restrict__ kin,
                                                             const uint32_t* __restrict__ vin,
                                                             uint64_t* __restrict__ kout, uint32_t* __restrict__ vout,
-                                                            const uint32_t* __restrict__ hist, int D, int level) {
+                                                            const uint32_t* __restrict__ hist, int D, int level,
+                                                            const uint32_t* __restrict__ splits) {
   extern __shared__ __align__(16) uint8_t s_dyn[];
   uint64_t* s_k = reinterpret_cast<uint64_t*>(s_dyn);
   uint32_t* s_v = reinterpret_cast<uint32_t*>(s_dyn + sizeof(uint64_t) * mg_pad(MG_TILE));
-  __shared__ uint32_t s_a0, s_la, s_lb, s_o0, s_o1, s_split[2];
+  __shared__ uint32_t s_a0, s_la, s_o0, s_o1, s_split[2];
   __shared__ int s_live;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x;
   if (tid == 0) {
-    uint32_t R[17];
-    R[0] = 0;
-    for (int e = 0; e < D; ++e) R[e + 1] = R[e] + hist[e];
-    const int L = 1 << (level - 1);
-    uint32_t b = blockIdx.x;
-    int live = 0;
-    for (int e = 0; e + 2 * L <= D; e += 2 * L) {
-      const uint32_t a0 = R[e], a1 = R[e + L], b1 = R[e + 2 * L];
-      const uint32_t tiles = (b1 - a0 + MG_TILE - 1) / MG_TILE;
-      if (b < tiles) {
-        s_a0 = a0;
-        s_la = a1 - a0;
-        s_lb = b1 - a1;
-        s_o0 = b * MG_TILE;
-        s_o1 = min(b * MG_TILE + MG_TILE, b1 - a0);
-        live = 1;
-        break;
-      }
-      b -= tiles;
+    uint32_t a0, la, lb, o0, o1;
+    const bool live = merge_block(hist, D, level, blockIdx.x, a0, la, lb, o0, o1);
+    if (live) {
+      s_a0 = a0;
+      s_la = la;
+      s_o0 = o0;
+      s_o1 = o1;
+      s_split[0] = splits[blockIdx.x];
+      s_split[1] = o1 == la + lb ? la : splits[blockIdx.x + 1];  // the pair's next tile is the next block
     }
     s_live = live;
   }
   __syncthreads();
   if (!s_live) return;
-  const uint32_t a0 = s_a0, la = s_la, lb = s_lb, o0 = s_o0, o1 = s_o1;
+  const uint32_t a0 = s_a0, la = s_la, o0 = s_o0, o1 = s_o1;
   const uint64_t* A = kin + a0;
   const uint64_t* B = A + la;
-  if (warp < 2) {
-    const uint32_t o = warp == 0 ? o0 : o1;
-    const uint32_t a = merge_path_warp(A, la, B, lb, o, lane);
-    if (lane == 0) s_split[warp] = a;
-  }
-  __syncthreads();
   const uint32_t ia = s_split[0], na = s_split[1] - ia;
   const uint32_t ib = o0 - ia, nb = (o1 - s_split[1]) - ib;
   const uint32_t len = na + nb;
@@ -341,15 +368,18 @@ int regroup_terms(const uint64_t* keys, uint64_t n, const GateParams& gp, uint64
   *launches = 3;
   int cur = 0;
   const uint64_t grid = (n + MG_TILE - 1) / MG_TILE + (uint64_t)D;
+  uint32_t* splits = cnt;  // the partition's counts and offsets are no longer needed
   for (int level = 1; level <= m; ++level) {
+    k_merge_splits<<<(unsigned)((grid * 32 + 255) / 256), 256, 0, st>>>(sk[cur], sc.hist, D, level, (uint32_t)grid,
+                                                                       splits);
     if (pairs)
-      k_merge_level<true><<<(unsigned)grid, MG_THREADS, merge_smem(true), st>>>(sk[cur], sidx[cur], sk[1 - cur],
-                                                                                sidx[1 - cur], sc.hist, D, level);
+      k_merge_level<true><<<(unsigned)grid, MG_THREADS, merge_smem(true), st>>>(
+          sk[cur], sidx[cur], sk[1 - cur], sidx[1 - cur], sc.hist, D, level, splits);
     else
-      k_merge_level<false><<<(unsigned)grid, MG_THREADS, merge_smem(false), st>>>(sk[cur], nullptr, sk[1 - cur],
-                                                                                  nullptr, sc.hist, D, level);
+      k_merge_level<false><<<(unsigned)grid, MG_THREADS, merge_smem(false), st>>>(
+          sk[cur], nullptr, sk[1 - cur], nullptr, sc.hist, D, level, splits);
     cur ^= 1;
-    ++*launches;
+    *launches += 2;
   }
   *cerr = cudaGetLastError();
   return cur;
