@@ -83,6 +83,7 @@ __global__ void __launch_bounds__(GS_BLOCK) k_group_scan(const uint64_t* __restr
   extern __shared__ __align__(16) uint8_t s_dyn[];
   uint64_t* s_k = reinterpret_cast<uint64_t*>(s_dyn);
   __shared__ uint32_t s_wh[GS_WARPS], s_wo[GS_WARPS], s_colnz[16];
+  __shared__ bool s_dense;
   __shared__ uint64_t s_tile, s_hbase, s_obase, s_th, s_to;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int m = gp.m, vb = gp.vbits, shift = m + vb;
@@ -92,6 +93,13 @@ __global__ void __launch_bounds__(GS_BLOCK) k_group_scan(const uint64_t* __restr
     for (int ro = 0; ro < (1 << m); ++ro)
       if (((gp.re_nz[ro] | gp.im_nz[ro]) >> tid) & 1u) c |= 1u << ro;
     s_colnz[tid] = c;
+  }
+  if (tid == 0) {  // every column of U nonzero in every row
+    bool dense = true;
+    for (int r = 0; r < (1 << m); ++r)
+      for (int ro = 0; ro < (1 << m); ++ro)
+        if (!(((gp.re_nz[ro] | gp.im_nz[ro]) >> r) & 1u)) dense = false;
+    s_dense = dense;
   }
   const uint64_t tiles = (n + GS_TILE - 1) / GS_TILE;
   while (true) {
@@ -107,15 +115,26 @@ __global__ void __launch_bounds__(GS_BLOCK) k_group_scan(const uint64_t* __restr
     for (int e = tid; e < staged; e += GS_BLOCK) s_k[e + 1] = sk[base + e];
     __syncthreads();
     const int wbase = warp * 32 * GS_ITEMS;
-    // pass 1: the warp's head and output counts
+    // pass 1: the warp's head and output counts (for a U without zero
+    // entries every group has all 2^m outputs: the heads alone decide)
     uint32_t nh = 0, no = 0;
+    if (s_dense) {
 #pragma unroll 4
-    for (int j = 0; j < GS_ITEMS; ++j) {
-      const int e = wbase + j * 32 + lane;
-      uint32_t pm, om;
-      const bool f = e < tn && gs_head(s_k, e, staged, shift, vb, dmask, s_colnz, pm, om);
-      nh += (uint32_t)__popc(__ballot_sync(0xffffffffu, f));
-      no += __reduce_add_sync(0xffffffffu, f ? (uint32_t)__popc(om) : 0u);
+      for (int j = 0; j < GS_ITEMS; ++j) {
+        const int e = wbase + j * 32 + lane;
+        const bool f = e < tn && (s_k[e] >> shift) != (s_k[e + 1] >> shift);
+        nh += (uint32_t)__popc(__ballot_sync(0xffffffffu, f));
+      }
+      no = nh << m;
+    } else {
+#pragma unroll 4
+      for (int j = 0; j < GS_ITEMS; ++j) {
+        const int e = wbase + j * 32 + lane;
+        uint32_t pm, om;
+        const bool f = e < tn && gs_head(s_k, e, staged, shift, vb, dmask, s_colnz, pm, om);
+        nh += (uint32_t)__popc(__ballot_sync(0xffffffffu, f));
+        no += __reduce_add_sync(0xffffffffu, f ? (uint32_t)__popc(om) : 0u);
+      }
     }
     if (lane == 0) {
       s_wh[warp] = nh;
