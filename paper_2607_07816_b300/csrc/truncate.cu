@@ -963,14 +963,31 @@ __global__ void __launch_bounds__(WP_BLOCK) k_truncate_write(
     __syncthreads();
     const uint64_t ob = tile_off[tile];
     const uint32_t kept = cs.tile_total;
-    for (uint32_t t = threadIdx.x; t < kept; t += WP_BLOCK) {
-      const uint64_t i = base + s_list[t];
-      const C2 a = amp_scaled(amps[i], s);
-      const uint64_t k = keys[i], pb = amp_prob_bits(a);
-      keys_out[ob + t] = k;
-      amps_out[ob + t] = a;
-      probs_out[ob + t] = pb;
-      peak_take(bp, bk, pb, k);
+    constexpr int U = 4;  // kept terms per thread whose loads are issued together
+    for (uint32_t t0 = threadIdx.x; t0 < kept; t0 += U * WP_BLOCK) {
+      C2 a[U];
+      uint64_t k[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const uint32_t t = t0 + u * WP_BLOCK;
+        if (t < kept) {
+          const uint64_t i = base + s_list[t];
+          a[u] = amps[i];
+          k[u] = keys[i];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const uint32_t t = t0 + u * WP_BLOCK;
+        if (t < kept) {
+          const C2 y = amp_scaled(a[u], s);
+          const uint64_t pb = amp_prob_bits(y);
+          keys_out[ob + t] = k[u];
+          amps_out[ob + t] = y;
+          probs_out[ob + t] = pb;
+          peak_take(bp, bk, pb, k[u]);
+        }
+      }
     }
     __syncthreads();
   }
