@@ -796,7 +796,7 @@ sv_status svb_export(svb_state* b, int slot, uint64_t* keys, double* amps, uint6
   launch_iota(b->sidx[0], w, b->st);
   launch_gather_terms(b->prec, b->sidx[0], w, b->keys[b->cur] + sl.offset,
                       (const char*)b->amps[b->cur] + sl.offset * b->amp_bytes, b->probs[b->cur] + sl.offset,
-                      nullptr, tmp, nullptr, b->st);
+                      nullptr, tmp, nullptr, nullptr, b->st);
   if (keys) cudaMemcpyAsync(keys, b->keys[b->cur] + sl.offset, w * 8, cudaMemcpyDeviceToHost, b->st);
   if (amps) cudaMemcpyAsync(amps, tmp, w * 16, cudaMemcpyDeviceToHost, b->st);
   rc = b_cuda(b, cudaStreamSynchronize(b->st), "svb_export");

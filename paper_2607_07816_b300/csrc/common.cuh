@@ -55,6 +55,7 @@ struct Ctl {
   uint32_t use_window;                     // 1: select over the window, 0: over all terms
   uint32_t sel_gated;                      // 1: select kernels decide on the device which of them run
   uint64_t kept_check;                     // terms the last truncation wrote (checked at the next wait)
+  const uint64_t* nat;                     // natural-key table of the stored keys (null: keys are natural)
 };
 
 __device__ __forceinline__ uint64_t ld_acquire(const uint64_t* p) {

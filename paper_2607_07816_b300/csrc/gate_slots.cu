@@ -263,14 +263,12 @@ __global__ void __launch_bounds__(AS_BLOCK) k_gate_apply_slots(
   extern __shared__ __align__(16) uint8_t s_dyn[];
   __shared__ Real sU[512];
   __shared__ uint32_t s_re_nz[16], s_im_nz[16];
-  __shared__ uint64_t s_inv[16][16];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t lt = (1u << lane) - 1u;
   const int m = gp.m, d = 1 << m, vb = gp.vbits, shift = m + vb;
   const uint32_t gc = 32u * gpl, mc = gc << m;
   SlotsLayout<C2> w(s_dyn + (size_t)warp * SlotsLayout<C2>::bytes(gc, mc), gc, mc);
   for (int i = tid; i < 2 * d * d; i += AS_BLOCK) sU[i] = (Real)gp.U[i];
-  for (int i = tid; i < 256; i += AS_BLOCK) (&s_inv[0][0])[i] = (&gp.perm->inv[0][0])[i];
   if (tid < 16) {
     s_re_nz[tid] = gp.re_nz[tid];
     s_im_nz[tid] = gp.im_nz[tid];
@@ -414,7 +412,7 @@ __global__ void __launch_bounds__(AS_BLOCK) k_gate_apply_slots(
         C2 y;
         y.x = re;
         y.y = im;
-        keys_out[o] = permute_bits(s_inv, (w.rest[j] << m) | ro);
+        keys_out[o] = (w.rest[j] << m) | ro;  // outputs are stored in the gate's sort-key order
         amps_out[o] = y;
         probs_out[o] = amp_prob_bits(y);
         z = is_zero_amp(re, im);

@@ -9,15 +9,16 @@
 
 namespace sv {
 
-// Sort-key permutation of a gate: gate qubit q[t] at bit t, the other
-// qubits above in the order of order[] (order[b] = bit of qubit b in the
-// sort key the state is currently sorted by).  Writes the forward and
-// inverse nibble tables, and the new order into next[] (may alias order).
-inline void build_perm(int n, int m, const int* q, const int* order, BitPerm* bp, int* next) {
-  int pos[64];
+// Tables of a gate on stored keys (see BitPerm): order[b] is the bit of
+// qubit b in the stored keys before the gate.  Writes the sort-key
+// permutation (fwd: stored -> sort key; inv: identity), the natural-key table
+// of the outputs, the gate qubits' stored positions qpos[t], and the qubit
+// order after the gate into next[] (may alias order).
+inline void build_gate_tables(int n, int m, const int* q, const int* order, GateTables* t, int* qpos, int* next) {
+  int pos[64];  // qubit -> bit after the gate
   for (int b = 0; b < 64; ++b) pos[b] = -1;
-  for (int t = 0; t < m; ++t) pos[q[t]] = t;
-  int by_bit[64];
+  for (int k = 0; k < m; ++k) pos[q[k]] = k;
+  int by_bit[64];  // stored bit -> qubit, before the gate
   for (int b = 0; b < 64; ++b) by_bit[b] = -1;
   for (int b = 0; b < n; ++b) by_bit[order[b]] = b;
   int nextbit = m;
@@ -25,25 +26,42 @@ inline void build_perm(int n, int m, const int* q, const int* order, BitPerm* bp
     const int b = by_bit[p];
     if (b >= 0 && pos[b] < 0) pos[b] = nextbit++;
   }
-  std::memset(bp, 0, sizeof(BitPerm));
-  for (int k = 0; k < 16; ++k)
-    for (int v = 0; v < 16; ++v)
-      for (int j = 0; j < 4; ++j)
-        if ((v >> j) & 1) {
-          const int b = 4 * k + j;
-          if (b < n) bp->fwd[k][v] |= 1ull << pos[b];
-        }
-  int from[64];
-  for (int b = 0; b < 64; ++b) from[b] = -1;
-  for (int b = 0; b < n; ++b) from[pos[b]] = b;
+  std::memset(&t->perm, 0, sizeof(BitPerm));
+  std::memset(t->nat, 0, sizeof(t->nat));
   for (int k = 0; k < 16; ++k)
     for (int v = 0; v < 16; ++v)
       for (int j = 0; j < 4; ++j)
         if ((v >> j) & 1) {
           const int p = 4 * k + j;
-          if (p < n) bp->inv[k][v] |= 1ull << from[p];
+          if (p >= n) continue;
+          t->perm.fwd[k][v] |= 1ull << pos[by_bit[p]];  // old stored bit p holds qubit by_bit[p]
+          t->perm.inv[k][v] |= 1ull << p;
         }
+  int qubit_at[64];  // bit after the gate -> qubit
+  for (int b = 0; b < n; ++b) qubit_at[pos[b]] = b;
+  for (int k = 0; k < 16; ++k)
+    for (int v = 0; v < 16; ++v)
+      for (int j = 0; j < 4; ++j)
+        if ((v >> j) & 1) {
+          const int p = 4 * k + j;
+          if (p < n) t->nat[k][v] |= 1ull << qubit_at[p];
+        }
+  for (int k = 0; k < m; ++k) qpos[k] = order[q[k]];
   for (int b = 0; b < n; ++b) next[b] = pos[b];
+}
+
+// The natural-key table of stored keys in the qubit order `order`.
+inline void build_nat_table(int n, const int* order, uint64_t (*nat)[16]) {
+  int qubit_at[64];
+  for (int b = 0; b < n; ++b) qubit_at[order[b]] = b;
+  std::memset(nat, 0, sizeof(uint64_t) * 256);
+  for (int k = 0; k < 16; ++k)
+    for (int v = 0; v < 16; ++v)
+      for (int j = 0; j < 4; ++j)
+        if ((v >> j) & 1) {
+          const int p = 4 * k + j;
+          if (p < n) nat[k][v] |= 1ull << qubit_at[p];
+        }
 }
 
 inline bool is_unitary(int m, const double* U) {

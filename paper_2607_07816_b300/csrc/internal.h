@@ -50,20 +50,29 @@ int radix_sort_pairs(uint64_t* kA, uint32_t* vA, uint64_t* kB, uint32_t* vB, uin
 void launch_tile_offsets(const uint32_t* cnt, const uint32_t* hist, uint64_t tiles, int digits, uint32_t* off,
                          cudaStream_t st);
 
-// Sort-key bit permutation of a gate: the qubits outside the gate on top,
-// in the order they have in the state's current sort key, and the gate
-// qubits at the bottom with qubits[t] at bit t.  Equal (sort key >> m) <=>
-// same partner group, with members in ascending r.
+// Stored keys.  The state keeps its terms sorted by the sort key of the last
+// gate, and it stores each term's key in that sort key's bit order (the
+// qubit order): bit order[b] of a stored key is qubit b.  Natural keys
+// (qubit i = bit i) are produced only where they leave the library or decide
+// canonical order: readouts, and probability ties at a cut or a peak.
+//
+// Sort-key bit permutation of a gate, on stored keys: the gate qubits go to
+// the bottom with qubits[t] at bit t, the other bits keep their order above
+// them.  Equal (sort key >> m) <=> same partner group, with members in
+// ascending r.  The gate's outputs are stored in the new order, so inv (new
+// sort key -> new stored key) is the identity.
 struct BitPerm {
-  uint64_t fwd[16][16];  // key -> sort key
-  uint64_t inv[16][16];  // sort key -> key
+  uint64_t fwd[16][16];  // stored key -> sort key
+  uint64_t inv[16][16];  // sort key -> stored key of the outputs
 };
 
 // Per-gate tables uploaded once per gate (one copy) and read by the kernels
 // through the pointers in GateParams, which stays small enough to pass by
-// value cheaply.
+// value cheaply.  nat maps the stored keys of the gate's outputs to natural
+// keys; it stays valid until the next gate.
 struct GateTables {
   BitPerm perm;
+  uint64_t nat[16][16];
   double U[512];
 };
 
@@ -85,7 +94,17 @@ struct GateParams {
   int tbits;           // number of bucket qubits (top bits of the sort key)
   uint64_t pmask;      // bucket qubits as a key mask
   int vbits;           // > 0: sort keys carry the term index in their low vbits bits (no index array)
+  int qpos[4];         // bit of qubits[t] in the stored keys before the gate
 };
+
+// Natural key of a stored key, with the nibble table of GateTables::nat
+// (256 entries, in shared or global memory).
+__device__ __forceinline__ uint64_t to_natural(const uint64_t* nat, uint64_t x) {
+  uint64_t y = 0;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) y |= nat[16 * k + ((x >> (4 * k)) & 15u)];
+  return y;
+}
 
 // Grouping of a state that is sorted by the previous gate's sort key when
 // gp.perm keeps the other qubits in that order (gate qubits at the bottom):
@@ -210,9 +229,13 @@ void launch_peak(const uint64_t* probs, const uint64_t* keys, uint64_t n, Ctl* c
 void launch_iota(uint32_t* v, uint64_t n, cudaStream_t st);
 void launch_not_bits_gather(const uint64_t* probs, const uint32_t* idx, uint64_t n, uint64_t* out,
                             cudaStream_t st);
+// Terms idx[i] gathered; keys made natural with ctl->nat (ctl may be null:
+// natural keys).
 void launch_gather_terms(int prec, const uint32_t* idx, uint64_t n, const uint64_t* keys,
                          const void* amps, const uint64_t* probs, uint64_t* keys_out,
-                         double* amps_out, uint64_t* probs_out, cudaStream_t st);
+                         double* amps_out, uint64_t* probs_out, const Ctl* ctl, cudaStream_t st);
+// Natural keys of stored keys (ctl->nat).
+void launch_keys_natural(const uint64_t* keys, uint64_t n, const Ctl* ctl, uint64_t* out, cudaStream_t st);
 // Load: amplitudes from double pairs (rounded to float for complex64),
 // zeros dropped, duplicates flagged (input sorted by key); probabilities
 // computed.  Count in ctl->count[2], duplicates in ctl->count[3].

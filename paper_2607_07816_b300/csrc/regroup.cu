@@ -16,8 +16,9 @@
 //     the totals per r);
 //   * offsets: for every r and tile, the output position of the tile's first
 //     term with that r (the radix sort's scan kernel);
-//   * scatter: each term's new sort key (with the term's index packed below
-//     it, or in a separate index array), written stably to its run;
+//   * scatter: each term's new sort key (the stored key with the gate bits
+//     moved to the bottom: a few shifts; the term's index packed below it, or
+//     in a separate index array), written stably to its run;
 //   * merge levels: runs 2k and 2k+1 are merged into one; a block takes 4096
 //     outputs of a merge, whose start in each input run a first kernel finds
 //     by a search over the merge path (one warp per block, 32 probes per
@@ -37,12 +38,47 @@ constexpr int RG_WARPS = RG_THREADS / 32;
 static_assert(RG_TILE == SORT_TILE, "partition tiles share the sort's scan kernel and scratch");
 constexpr int MG_THREADS = 512, MG_ITEMS = 8, MG_TILE = MG_THREADS * MG_ITEMS;
 
-__device__ __forceinline__ uint32_t gate_index_of(uint64_t key, const int* q, int m) {
+// Local index r of a stored key: the bits at the gate qubits' stored
+// positions qpos[t].
+__device__ __forceinline__ uint32_t gate_index_of(uint64_t key, const int* qpos, int m) {
   uint32_t r = 0;
 #pragma unroll
   for (int t = 0; t < 4; ++t)
-    if (t < m) r |= (uint32_t)((key >> q[t]) & 1ull) << t;
+    if (t < m) r |= (uint32_t)((key >> qpos[t]) & 1ull) << t;
   return r;
+}
+
+// The gate's sort key of a stored key: the bits at the positions in rem[]
+// (the gate qubits' stored positions, in descending order) are removed, the
+// rest shifts down over them and moves up by m, and r takes the bottom.
+__device__ __forceinline__ uint64_t sort_key_of(uint64_t key, const int* qpos, const int* rem, int m) {
+  const uint32_t r = gate_index_of(key, qpos, m);
+  uint64_t x = key;
+#pragma unroll
+  for (int t = 0; t < 4; ++t)
+    if (t < m) {
+      const int p = rem[t];
+      const uint64_t low = x & ((1ull << p) - 1ull);
+      x = ((x >> p) >> 1 << p) | low;
+    }
+  return (x << m) | r;
+}
+
+__device__ __forceinline__ void gate_positions(const GateParams& gp, int* qpos, int* rem) {
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    qpos[t] = gp.qpos[t];
+    rem[t] = t < gp.m ? gp.qpos[t] : -1;
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)  // descending
+#pragma unroll
+    for (int b = a + 1; b < 4; ++b)
+      if (rem[b] > rem[a]) {
+        const int t = rem[a];
+        rem[a] = rem[b];
+        rem[b] = t;
+      }
 }
 
 // Number of terms with each local index r, per tile (cnt[r * tiles + t])
@@ -55,7 +91,7 @@ __global__ void __launch_bounds__(RG_THREADS) k_part_counts(const uint64_t* __re
   const int m = gp.m, D = 1 << m;
   int q[4];
 #pragma unroll
-  for (int t = 0; t < 4; ++t) q[t] = gp.q[t];
+  for (int t = 0; t < 4; ++t) q[t] = gp.qpos[t];
   if (tid < 16) h[tid] = 0;
   __syncthreads();
   const uint64_t t = blockIdx.x;
@@ -92,14 +128,14 @@ __global__ void __launch_bounds__(RG_THREADS) k_part_scatter(const uint64_t* __r
   extern __shared__ __align__(16) uint8_t s_dyn[];
   uint64_t* s_keys = reinterpret_cast<uint64_t*>(s_dyn);
   uint32_t* s_vals = reinterpret_cast<uint32_t*>(s_dyn + sizeof(uint64_t) * RG_TILE);
-  __shared__ uint64_t fwd[16][16];
   __shared__ uint32_t s_whist[RG_WARPS][16];
   __shared__ uint32_t s_local[16];
   __shared__ uint32_t s_out[16];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int m = gp.m, D = 1 << m, vb = gp.vbits;
   const uint32_t dmask = (uint32_t)D - 1u;
-  for (int i = tid; i < 256; i += RG_THREADS) (&fwd[0][0])[i] = (&gp.perm->fwd[0][0])[i];
+  int qpos[4], rem[4];
+  gate_positions(gp, qpos, rem);
   for (int i = tid; i < RG_WARPS * 16; i += RG_THREADS) (&s_whist[0][0])[i] = 0;
   const uint64_t t = blockIdx.x;
   if (tid < D) s_out[tid] = off[(uint64_t)tid * tiles + t];
@@ -111,7 +147,7 @@ __global__ void __launch_bounds__(RG_THREADS) k_part_scatter(const uint64_t* __r
   for (int i = 0; i < RG_ITEMS; ++i) {
     const uint64_t idx = base + i * 32;
     const bool valid = idx < n;
-    const uint64_t s = valid ? permute_bits(fwd, keys[idx]) : 0ull;
+    const uint64_t s = valid ? sort_key_of(keys[idx], qpos, rem, m) : 0ull;
     k[i] = vb ? ((s << vb) | idx) : s;
     d[i] = valid ? (uint32_t)(s & dmask) : 16u;
   }

@@ -328,8 +328,8 @@ sv_status canonical_perm(sv_state* s, int* which) {
   sv_status rc = ensure_sort_cap(s, N);
   if (rc != SV_OK) return rc;
   launch_iota(s->sidx[0], N, s->st);
-  launched(s, PH_OTHER, 1);
-  cudaMemcpyAsync(s->sk[0], s->keys[s->cur], N * 8, cudaMemcpyDeviceToDevice, s->st);
+  launch_keys_natural(s->keys[s->cur], N, s->ctl, s->sk[0], s->st);  // the stored keys in qubit order
+  launched(s, PH_OTHER, 2);
   int w = 0, passes = 0;
   rc = sort_pairs(s, N, s->n, false, &w, &passes);
   if (rc != SV_OK) return rc;
@@ -355,18 +355,29 @@ sv_status canonical_perm(sv_state* s, int* which) {
 
 
 
+// The natural-key table of the state's current order (after create and
+// load, when no gate has set it).
+sv_status upload_nat(sv_state* s) {
+  build_nat_table(s->n, s->order, s->tab_host->nat);
+  const size_t bytes = offsetof(GateTables, U);
+  g_h2d += sizeof(s->tab_host->nat);
+  launch_store_tables(*s->tab_host, s->tab_dev, bytes, s->st);
+  launched(s, PH_OTHER, 1);
+  return cuda_check(s, cudaGetLastError(), "natural-key table upload");
+}
+
 // Sort-key permutation of the gate for the state's current order, uploaded
 // for the kernels; the order it leaves goes to order_next.
 sv_status upload_perm(sv_state* s, GateParams& gp) {
-  build_perm(s->n, gp.m, gp.q, s->order, &s->tab_host->perm, s->order_next);
+  build_gate_tables(s->n, gp.m, gp.q, s->order, s->tab_host, gp.qpos, s->order_next);
   gp.perm = &s->tab_dev->perm;
   gp.U = s->tab_dev->U;
   gp.n = s->n;
   gp.tbits = 0;
   gp.pmask = 0;
-  // the permutation and the 2 d^2 doubles of U travel as the parameters of
-  // one small kernel that stores them (no copy-engine transfer to wait for
-  // in the stream)
+  // the permutation, the natural-key table and the 2 d^2 doubles of U travel
+  // as the parameters of one small kernel that stores them (no copy-engine
+  // transfer to wait for in the stream)
   const size_t bytes = offsetof(GateTables, U) + sizeof(double) * 2 * (1u << (2 * gp.m));
   g_h2d += bytes;
   launch_store_tables(*s->tab_host, s->tab_dev, bytes, s->st);
@@ -422,6 +433,8 @@ sv_status sv_create_ex(int n, uint64_t K, double p, int prec, void* cuda_stream,
   if (rc == SV_OK) rc = ensure_sort_cap(s, 4096);
   if (rc == SV_OK) {
     cudaMemsetAsync(s->ctl, 0, sizeof(Ctl), s->st);
+    const uint64_t* nat_dev = &s->tab_dev->nat[0][0];
+    cudaMemcpyAsync(&s->ctl->nat, &nat_dev, sizeof(nat_dev), cudaMemcpyHostToDevice, s->st);
     const uint64_t zero_key = 0;
     const double one[2] = {1.0, 0.0};
     const float onef[2] = {1.0f, 0.0f};
@@ -430,10 +443,11 @@ sv_status sv_create_ex(int n, uint64_t K, double p, int prec, void* cuda_stream,
     cudaMemcpyAsync(s->amps[0], prec == SV_C128 ? (const void*)one : (const void*)onef, s->amp_bytes,
                     cudaMemcpyHostToDevice, s->st);
     cudaMemcpyAsync(s->probs[0], &one_bits, 8, cudaMemcpyHostToDevice, s->st);
-    rc = cuda_check(s, cudaStreamSynchronize(s->st), "sv_create");
+    for (int b = 0; b < 64; ++b) s->order[b] = b;
+    rc = upload_nat(s);
+    if (rc == SV_OK) rc = cuda_check(s, cudaStreamSynchronize(s->st), "sv_create");
     s->N = 1;
     s->cur = 0;
-    for (int b = 0; b < 64; ++b) s->order[b] = b;
   }
   if (rc != SV_OK) {
     sv_destroy(s);
@@ -928,7 +942,7 @@ static sv_status dump(sv_state* s, uint64_t* keys, double* amps, double* probs, 
     da = (double*)tmp;
   }
   launch_gather_terms(s->prec, s->sidx[which], w, s->keys[s->cur], s->amps[s->cur], s->probs[s->cur],
-                      dk, da, dp, s->st);
+                      dk, da, dp, s->ctl, s->st);
   launched(s, PH_OTHER, 1);
   g_d2h += w * ((dk ? 8 : 0) + (dp ? 8 : 0) + (da ? 16 : 0));
   if (dk) cudaMemcpyAsync(keys, dk, w * 8, cudaMemcpyDeviceToHost, s->st);
@@ -986,7 +1000,9 @@ sv_status sv_load(sv_state* s, const uint64_t* keys, const double* amps, uint64_
   if (s->ctl_host->count[3] != 0) return fail(s, SV_E_ARG, "sv_load: duplicate keys");
   s->cur = alt;
   s->N = s->ctl_host->count[2];
-  for (int b = 0; b < 64; ++b) s->order[b] = b;  // sorted by key
+  for (int b = 0; b < 64; ++b) s->order[b] = b;  // sorted by key, stored as natural keys
+  rc = upload_nat(s);
+  if (rc != SV_OK) return rc;
   return SV_OK;
 }
 

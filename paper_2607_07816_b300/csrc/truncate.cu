@@ -19,6 +19,11 @@
 
 namespace sv {
 
+// Natural key of a stored key (identity when the keys are natural).
+__device__ __forceinline__ uint64_t natural_key(const uint64_t* nat, uint64_t k) {
+  return nat ? to_natural(nat, k) : k;
+}
+
 // The list is the window buffer when the window pass set use_window, else
 // all terms: the choice and the list length are read on the device, so the
 // select can be enqueued before the window is known.  Block b scans a
@@ -35,7 +40,8 @@ __global__ void __launch_bounds__(256) k_select_hist(const uint64_t* __restrict_
   if (ctl->sel_gated && ctl->sel_bin_count <= (uint64_t)FINISH_CAP) return;  // the finish takes over
   const bool win = ctl->use_window != 0;
   const uint64_t* P = win ? wp : probs;
-  const uint64_t* Kk = win ? wk : keys;
+  const uint64_t* Kk = win ? wk : keys;  // stored keys (made natural where a tie needs them)
+  const uint64_t* nat = ctl->nat;
   const uint64_t nn = win ? ctl->win_n : n;
   uint64_t chunk = (nn + gridDim.x - 1) / gridDim.x;
   if (chunk < 8192) chunk = 8192;
@@ -57,7 +63,7 @@ __global__ void __launch_bounds__(256) k_select_hist(const uint64_t* __restrict_
     const uint64_t pb = P[i];
     const uint64_t hi = ~pb;
     if (bits <= 64 && bits > 0 && ((hi ^ ph) >> (64 - bits)) != 0) continue;
-    const uint64_t lo = need_lo ? Kk[i] : 0ull;
+    const uint64_t lo = need_lo ? natural_key(nat, Kk[i]) : 0ull;
     if (bits > 64 && !z_matches(hi, lo, ph, pl, bits)) continue;
     hist_add(z_digit(hi, lo, shift, D), pb, s_cnt, s_mass, &ctl->err, cache);
   }
@@ -564,7 +570,7 @@ __global__ void k_window_tile_counts(const uint64_t* __restrict__ wp, const uint
   for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < wn;
        j += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t pb = wp[j];
-    if (pb > pc || (pb == pc && wk[j] <= kc)) {
+    if (pb > pc || (pb == pc && natural_key(ctl->nat, wk[j]) <= kc)) {
       const uint32_t i = wi[j];
       atomicAdd(&tile_keep[i / WP_TILE], 1u);
       atomicOr(&keep_bits[i >> 5], 1u << (i & 31));
@@ -746,7 +752,7 @@ __global__ void __launch_bounds__(256) k_select_compact(const uint64_t* __restri
        i += (uint64_t)gridDim.x * blockDim.x) {
     uint64_t hi = ~P[i];
     if (bits <= 64 && ((hi ^ ph) >> (64 - bits)) != 0) continue;
-    uint64_t lo = Kk[i];
+    uint64_t lo = natural_key(ctl->nat, Kk[i]);
     if (!z_matches(hi, lo, ph, pl, bits)) continue;
     uint64_t pos = atomicAdd((unsigned long long*)&ctl->compact_n, 1ull);
     if (pos < FINISH_CAP) {
@@ -811,6 +817,24 @@ __device__ __forceinline__ void peak_take(uint64_t& bp, uint64_t& bk, uint64_t p
     bk = k;
   }
 }
+
+// A thread's best kept term while it writes stored keys: the stored key of
+// the best is kept and made natural once at the end; only exact probability
+// ties compare natural keys on the way.
+struct PeakRun {
+  uint64_t p = 0, k = 0;
+  bool any = false;
+  __device__ __forceinline__ void take(uint64_t pb, uint64_t key, const uint64_t* nat) {
+    if (!any || pb > p) {
+      p = pb;
+      k = key;
+      any = true;
+    } else if (pb == p && natural_key(nat, key) < natural_key(nat, k)) {
+      k = key;
+    }
+  }
+  __device__ __forceinline__ uint64_t natural(const uint64_t* nat) const { return any ? natural_key(nat, k) : ~0ull; }
+};
 
 // Block-wide best of (bp, bk) into out[0] (probability bits), out[1] (key);
 // all threads must call it.
@@ -880,7 +904,7 @@ __global__ void __launch_bounds__(TC_BLOCK) k_truncate_compact(
     uint64_t n, uint64_t* __restrict__ keys_out, C2* __restrict__ amps_out,
     uint64_t* __restrict__ probs_out, uint64_t* lookback, Ctl* ctl, uint64_t* __restrict__ peak_part) {
   typedef TileLayout<TC_BLOCK, TC_ITEMS> L;
-  uint64_t bp = 0, bk = ~0ull;
+  PeakRun best;
   __shared__ CompactShared<TC_BLOCK> cs;
   __shared__ uint64_t s_tile;
   const uint64_t pc = ctl->cut_pbits, kc = ctl->cut_key;
@@ -900,7 +924,7 @@ __global__ void __launch_bounds__(TC_BLOCK) k_truncate_compact(
       bool f = false;
       if (i < n) {
         const uint64_t pb = probs[i];
-        f = pb > pc || (pb == pc && keys[i] <= kc);
+        f = pb > pc || (pb == pc && natural_key(ctl->nat, keys[i]) <= kc);
       }
       flag[j] = f;
     }
@@ -915,13 +939,13 @@ __global__ void __launch_bounds__(TC_BLOCK) k_truncate_compact(
         keys_out[o] = k;
         amps_out[o] = a;
         probs_out[o] = pb;
-        peak_take(bp, bk, pb, k);
+        best.take(pb, k, ctl->nat);
       }
     }
     if (tile == tiles - 1 && threadIdx.x == 0) ctl->count[2] = cs.tile_base_out + cs.tile_total;
     __syncthreads();
   }
-  block_peak_write(bp, bk, peak_part + 2 * blockIdx.x);
+  block_peak_write(best.p, best.natural(ctl->nat), peak_part + 2 * blockIdx.x);
 }
 
 // Windowed compaction: tile t (same tiling as the window pass) writes its
@@ -937,8 +961,9 @@ __global__ void __launch_bounds__(WP_BLOCK) k_truncate_write(
   typedef TileLayout<WP_BLOCK, WP_ITEMS> L;
   __shared__ CompactShared<WP_BLOCK> cs;
   __shared__ uint16_t s_list[WP_TILE];
-  uint64_t bp = 0, bk = ~0ull;
+  PeakRun best;
   const double s = ctl->scale;
+  const uint64_t* nat = ctl->nat;
   const int lane = threadIdx.x & 31;
   const uint64_t tiles = (n + L::TILE - 1) / L::TILE;
   for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
@@ -985,13 +1010,13 @@ __global__ void __launch_bounds__(WP_BLOCK) k_truncate_write(
           keys_out[ob + t] = k[u];
           amps_out[ob + t] = y;
           probs_out[ob + t] = pb;
-          peak_take(bp, bk, pb, k[u]);
+          best.take(pb, k[u], nat);
         }
       }
     }
     __syncthreads();
   }
-  block_peak_write(bp, bk, peak_part + 2 * blockIdx.x);
+  block_peak_write(best.p, best.natural(nat), peak_part + 2 * blockIdx.x);
 }
 
 void launch_truncate_windowed(int prec, const uint64_t* keys, const void* amps, const uint64_t* probs,
@@ -1061,7 +1086,7 @@ __global__ void __launch_bounds__(256) k_peak_key(const uint64_t* __restrict__ p
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
        i += (uint64_t)gridDim.x * blockDim.x) {
     if (probs[i] == pmax) {
-      uint64_t k = keys[i];
+      const uint64_t k = natural_key(ctl->nat, keys[i]);
       best = k < best ? k : best;
     }
   }
@@ -1116,11 +1141,13 @@ template <typename C2>
 __global__ void k_gather_terms(const uint32_t* __restrict__ idx, uint64_t n,
                                const uint64_t* __restrict__ keys, const C2* __restrict__ amps,
                                const uint64_t* __restrict__ probs, uint64_t* __restrict__ keys_out,
-                               double2* __restrict__ amps_out, uint64_t* __restrict__ probs_out) {
+                               double2* __restrict__ amps_out, uint64_t* __restrict__ probs_out,
+                               const Ctl* ctl) {
+  const uint64_t* nat = ctl ? ctl->nat : nullptr;
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
        i += (uint64_t)gridDim.x * blockDim.x) {
     uint32_t j = idx[i];
-    if (keys_out) keys_out[i] = keys[j];
+    if (keys_out) keys_out[i] = natural_key(nat, keys[j]);
     if (amps_out) {
       C2 a = amps[j];
       amps_out[i] = make_double2((double)a.x, (double)a.y);
@@ -1131,16 +1158,31 @@ __global__ void k_gather_terms(const uint32_t* __restrict__ idx, uint64_t n,
 
 void launch_gather_terms(int prec, const uint32_t* idx, uint64_t n, const uint64_t* keys,
                          const void* amps, const uint64_t* probs, uint64_t* keys_out,
-                         double* amps_out, uint64_t* probs_out, cudaStream_t st) {
+                         double* amps_out, uint64_t* probs_out, const Ctl* ctl, cudaStream_t st) {
   if (n == 0) return;
   uint64_t blocks = (n + 255) / 256;
   if (blocks > 148 * 8) blocks = 148 * 8;
   if (prec == 0)
     k_gather_terms<double2><<<(unsigned)blocks, 256, 0, st>>>(
-        idx, n, keys, (const double2*)amps, probs, keys_out, (double2*)amps_out, probs_out);
+        idx, n, keys, (const double2*)amps, probs, keys_out, (double2*)amps_out, probs_out, ctl);
   else
     k_gather_terms<float2><<<(unsigned)blocks, 256, 0, st>>>(
-        idx, n, keys, (const float2*)amps, probs, keys_out, (double2*)amps_out, probs_out);
+        idx, n, keys, (const float2*)amps, probs, keys_out, (double2*)amps_out, probs_out, ctl);
+}
+
+__global__ void k_keys_natural(const uint64_t* __restrict__ keys, uint64_t n, const Ctl* ctl,
+                               uint64_t* __restrict__ out) {
+  const uint64_t* nat = ctl->nat;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    out[i] = natural_key(nat, keys[i]);
+}
+
+void launch_keys_natural(const uint64_t* keys, uint64_t n, const Ctl* ctl, uint64_t* out, cudaStream_t st) {
+  if (n == 0) return;
+  uint64_t blocks = (n + 255) / 256;
+  if (blocks > 148 * 8) blocks = 148 * 8;
+  k_keys_natural<<<(unsigned)blocks, 256, 0, st>>>(keys, n, ctl, out);
 }
 
 // ---------------------------------------------------------------- load
