@@ -382,18 +382,6 @@ __device__ __forceinline__ bool z_before_prefix(uint64_t hi, uint64_t lo, uint64
   return (lo >> (128 - bits)) < (pl >> (128 - bits));
 }
 
-__device__ __forceinline__ u128 warp_sum_u128(u128 v) {
-  uint64_t lo = (uint64_t)v, hi = (uint64_t)(v >> 64);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const uint64_t l2 = __shfl_down_sync(0xffffffffu, (unsigned long long)lo, o);
-    const uint64_t h2 = __shfl_down_sync(0xffffffffu, (unsigned long long)hi, o);
-    const uint64_t s = lo + l2;
-    hi += h2 + (s < lo ? 1u : 0u);
-    lo = s;
-  }
-  return make_u128(hi, lo);
-}
 
 __global__ void __launch_bounds__(SS_BLOCK) k_segsel_hist(const uint64_t* __restrict__ probs,
                                                           const uint64_t* __restrict__ keys,

@@ -28,6 +28,7 @@
 // pass, which gives the same list as dropping them here (A4 zero-drop).
 #include "c64_exact.cuh"
 #include "internal.h"
+#include "select.cuh"
 #include "tile.cuh"
 
 namespace sv {
@@ -277,6 +278,11 @@ __global__ void __launch_bounds__(AS_BLOCK) k_gate_apply_slots(
   const uint64_t G = ctl->count[0];
   const uint64_t imask = vb ? ((1ull << vb) - 1ull) : 0ull;
   uint32_t zeros = 0;
+  // complex128: the exact fixed-point total mass of the candidates, summed on
+  // the integer pipe while the FP64 pipe does the multiply-adds (the
+  // truncation's window pass then needs no per-term mass for a top-K cut)
+  constexpr bool MASS = sizeof(Real) == 8;
+  u128 tot = 0;
   for (uint64_t wb = (uint64_t)blockIdx.x * AS_WARPS + warp; wb * gc < G; wb += (uint64_t)gridDim.x * AS_WARPS) {
     // group j = 32 k + lane of the batch; all group loads first
     uint32_t s[GPL], c[GPL], pos[GPL], h[GPL], gmv[GPL];
@@ -414,7 +420,9 @@ __global__ void __launch_bounds__(AS_BLOCK) k_gate_apply_slots(
         y.y = im;
         keys_out[o] = (w.rest[j] << m) | ro;  // outputs are stored in the gate's sort-key order
         amps_out[o] = y;
-        probs_out[o] = amp_prob_bits(y);
+        const uint64_t pb = amp_prob_bits(y);
+        probs_out[o] = pb;
+        if (MASS) tot += fx_from_bits(pb, &ctl->err);
         z = is_zero_amp(re, im);
       }
       zeros += (uint32_t)__popc(__ballot_sync(0xffffffffu, z));
@@ -422,6 +430,10 @@ __global__ void __launch_bounds__(AS_BLOCK) k_gate_apply_slots(
     __syncwarp();
   }
   if (lane == 0 && zeros) atomicAdd((unsigned long long*)&ctl->count[3], (unsigned long long)zeros);
+  if (MASS) {
+    tot = warp_sum_u128(tot);
+    if (lane == 0 && tot) atomic_add_u128(&ctl->total_mass_hi, &ctl->total_mass_lo, tot);
+  }
 }
 
 void launch_gate_apply_slots(int prec, const uint64_t* sk, const uint32_t* sidx, uint64_t n, const uint32_t* heads,
@@ -431,6 +443,7 @@ void launch_gate_apply_slots(int prec, const uint64_t* sk, const uint32_t* sidx,
   const uint32_t gc = 32u * gpl, mc = gc << gp.m;
   const size_t smem = AS_WARPS * (prec == 0 ? SlotsLayout<double2>::bytes(gc, mc) : SlotsLayout<float2>::bytes(gc, mc));
   cudaMemsetAsync(&ctl->count[3], 0, sizeof(uint64_t), st);
+  cudaMemsetAsync(&ctl->total_mass_hi, 0, sizeof(uint64_t) * 2, st);
   if (n == 0) return;
   const uint64_t batches = (n + gc - 1) / gc;  // groups <= n
   uint64_t grid = (batches + AS_WARPS - 1) / AS_WARPS;

@@ -144,7 +144,8 @@ void launch_group_scan(const uint64_t* sk, uint64_t n, const GateParams& gp, uin
                        uint64_t* ooff, uint64_t* lookback, Ctl* ctl, cudaStream_t st);
 // Per-group mat-vec writing each structurally nonzero output at its
 // precomputed position; exact zeros are written as zero and counted in
-// ctl->count[3] (to be removed by launch_drop_zero_terms).
+// ctl->count[3] (to be removed by launch_drop_zero_terms).  complex128 also
+// sums the candidates' exact fixed-point total mass into ctl->total_mass.
 void launch_gate_apply_slots(int prec, const uint64_t* sk, const uint32_t* sidx, uint64_t n, const uint32_t* heads,
                              const uint32_t* gmask, const uint64_t* ooff, const void* amps_in, const GateParams& gp,
                              uint64_t* keys_out, void* amps_out, uint64_t* probs_out, Ctl* ctl, cudaStream_t st);
@@ -205,9 +206,11 @@ void launch_truncate_windowed(int prec, const uint64_t* keys, const void* amps, 
 // Sample-estimated window, one streaming pass (exact total mass, count and
 // mass above the window, window terms gathered) and the choice of the list
 // the radix select runs on (ctl->use_window); sets the select state.
+// have_total: ctl->total_mass already holds the exact total of the terms
+// (summed by the complex128 mat-vec); a top-K cut then skips it per term.
 void launch_select_window(const uint64_t* probs, const uint64_t* keys, uint64_t n, Ctl* ctl,
                           const SelectScratch& ss, int mode, uint64_t count_target, double p,
-                          cudaStream_t st);
+                          bool have_total, cudaStream_t st);
 
 void launch_select_hist(const uint64_t* probs, const uint64_t* keys, uint64_t n, Ctl* ctl,
                         const SelectScratch& ss, cudaStream_t st);

@@ -16,6 +16,16 @@ __device__ __forceinline__ void atomic_add_u128(uint64_t* hi, uint64_t* lo, u128
   if (vh) atomicAdd((unsigned long long*)hi, (unsigned long long)vh);
 }
 
+__device__ __forceinline__ u128 warp_sum_u128(u128 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    uint64_t hi = __shfl_xor_sync(0xffffffffu, (unsigned long long)(v >> 64), o);
+    uint64_t lo = __shfl_xor_sync(0xffffffffu, (unsigned long long)(uint64_t)v, o);
+    v += make_u128(hi, lo);
+  }
+  return v;
+}
+
 __device__ __forceinline__ bool z_matches(uint64_t hi, uint64_t lo, uint64_t ph, uint64_t pl,
                                           int bits) {
   if (bits <= 64) return bits == 0 || ((hi ^ ph) >> (64 - bits)) == 0;

@@ -85,6 +85,9 @@ struct sv_state {
   uint64_t* peak_part = nullptr;
   uint32_t peak_blocks = 0;
   bool peak_ready = false;
+  // the complex128 mat-vec left the exact total mass of the current terms in
+  // ctl->total_mass (valid until the terms change)
+  bool total_ready = false;
   int64_t gate_index = 0;
   GateTables* tab_dev = nullptr;   // this gate's permutation and U
   GateTables* tab_host = nullptr;  // pinned staging of tab_dev
@@ -537,6 +540,7 @@ sv_status sv_apply_gate(sv_state* s, int m, const int* qubits, const double* U) 
     }
   const uint64_t N = s->N;
   s->peak_ready = false;
+  s->total_ready = false;
   s->stats.n_in = N;
   s->stats.sort_passes = 0;
   if (N == 0) {
@@ -667,6 +671,7 @@ sv_status sv_apply_gate(sv_state* s, int m, const int* qubits, const double* U) 
     ph_begin(s, PH_APPLY);
     launch_gate_apply_slots(s->prec, s->sk[w], s->sidx[w], N, s->heads, s->gmask, s->ooff, s->amps[s->cur], gp,
                             s->keys[alt], s->amps[alt], s->probs[alt], s->ctl, s->st);
+    s->total_ready = s->prec == SV_C128;  // zeros dropped below add no mass
     ph_end(s, PH_APPLY);
     launched(s, PH_HEADS, 1);
     launched(s, PH_APPLY, 1);
@@ -746,7 +751,7 @@ sv_status run_select(sv_state* s, int mode, uint64_t count_target, uint32_t* lev
   sv_status rc = ensure_window_cap(s, N);
   if (rc != SV_OK) return rc;
   ph_begin(s, PH_WINDOW);
-  launch_select_window(s->probs[s->cur], s->keys[s->cur], N, s->ctl, s->ss, mode, count_target, s->p,
+  launch_select_window(s->probs[s->cur], s->keys[s->cur], N, s->ctl, s->ss, mode, count_target, s->p, s->total_ready,
                        s->st);
   ph_end(s, PH_WINDOW);
   launched(s, PH_WINDOW, 3);
@@ -869,6 +874,7 @@ sv_status sv_truncate(sv_state* s, uint64_t* kept, double* retained_fraction) {
       s->kept_pending = true;
       s->kept_expected = c;
       s->peak_ready = s->peak_blocks > 0;
+      s->total_ready = false;
       double Sc = u128_to_double(s->ctl_host->cut_mass_hi, s->ctl_host->cut_mass_lo);
       f = Sc / SN;
       s->F = s->F * f;
@@ -964,6 +970,7 @@ sv_status sv_export(sv_state* s, uint64_t* keys, double* amps, uint64_t cap, uin
 sv_status sv_load(sv_state* s, const uint64_t* keys, const double* amps, uint64_t N) {
   SV_GUARD(s);
   s->peak_ready = false;
+  s->total_ready = false;
   if (N > 0 && (!keys || !amps)) return fail(s, SV_E_ARG, "sv_load: null input");
   if (N > MAX_TERMS) return fail(s, SV_E_ARG, "sv_load: too many terms");
   if (s->n < 64)

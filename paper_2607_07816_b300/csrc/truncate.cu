@@ -330,16 +330,6 @@ constexpr int WP_BLOCK = 256, WP_ITEMS = 8;
 static_assert(WP_BLOCK * WP_ITEMS == WINDOW_TILE, "window tiling");
 constexpr int WP_TILE = WP_BLOCK * WP_ITEMS;
 
-__device__ __forceinline__ u128 warp_sum_u128(u128 v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    uint64_t hi = __shfl_xor_sync(0xffffffffu, (unsigned long long)(v >> 64), o);
-    uint64_t lo = __shfl_xor_sync(0xffffffffu, (unsigned long long)(uint64_t)v, o);
-    v += make_u128(hi, lo);
-  }
-  return v;
-}
-
 // One streaming pass over all terms (tile t = terms [t*WP_TILE, ...),
 // static assignment): the exact fixed-point total mass, the count and mass
 // above the window, the window's mass and its terms (probability, key, index)
@@ -381,6 +371,11 @@ __device__ __forceinline__ void window_flush(WindowStage& st, Ctl* ctl, uint64_t
   __syncthreads();
 }
 
+// LIGHT (a top-K cut after a mat-vec that summed the total mass): no
+// per-term total; the masses of the terms above the window, about a third of
+// them, are summed from a per-warp queue of their probabilities, so the
+// 128-bit conversions run on full warps of above-window terms only.
+template <bool LIGHT>
 __global__ void __launch_bounds__(WP_BLOCK, 4) k_window_pass(const uint64_t* __restrict__ probs,
                                                           const uint64_t* __restrict__ keys, uint64_t n,
                                                           Ctl* ctl, uint64_t* __restrict__ wp,
@@ -393,12 +388,14 @@ __global__ void __launch_bounds__(WP_BLOCK, 4) k_window_pass(const uint64_t* __r
   __shared__ uint32_t s_acc;
   __shared__ uint64_t s_direct;
   __shared__ WindowStage st;
+  __shared__ uint64_t s_aq[LIGHT ? WP_BLOCK / 32 : 1][64];  // per-warp ring of above-window probabilities
   const uint64_t hi = ctl->win_hi, lo = ctl->win_lo;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt = (1u << lane) - 1u;
   if (threadIdx.x == 0) st.n = 0;
   u128 tot = 0, above_m = 0, win_m = 0;
   uint64_t above_c = 0;
+  uint32_t q_head = 0, q_n = 0;  // warp-uniform ring state
   const uint64_t tiles = (n + L::TILE - 1) / L::TILE;
   for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const uint64_t base = tile * L::TILE;
@@ -412,18 +409,35 @@ __global__ void __launch_bounds__(WP_BLOCK, 4) k_window_pass(const uint64_t* __r
 #pragma unroll
     for (int j = 0; j < WP_ITEMS; ++j) {
       const uint64_t pb = pbv[j];
-      const u128 f = fx_from_bits(pb, &ctl->err);
-      tot += f;
       const bool valid = L::index(base, j) < n;
       const bool above = valid && pb > hi;
       const bool inwin = valid && !above && pb >= lo;
-      if (above) {
-        ++tile_above;
-        above_m += f;
-      }
-      if (inwin) {
-        win_m += f;
-        wmask |= 1u << j;
+      if (LIGHT) {
+        const uint32_t ab = __ballot_sync(0xffffffffu, above);
+        if (above) {
+          ++tile_above;
+          s_aq[warp][(q_head + q_n + __popc(ab & lt)) & 63u] = pb;
+        }
+        q_n += __popc(ab);
+        if (q_n >= 32) {  // a full warp of queued terms: one conversion each
+          __syncwarp();
+          above_m += fx_from_bits(s_aq[warp][(q_head + lane) & 63u], &ctl->err);
+          __syncwarp();
+          q_head = (q_head + 32) & 63u;
+          q_n -= 32;
+        }
+        if (inwin) wmask |= 1u << j;
+      } else {
+        const u128 f = fx_from_bits(pb, &ctl->err);
+        tot += f;
+        if (above) {
+          ++tile_above;
+          above_m += f;
+        }
+        if (inwin) {
+          win_m += f;
+          wmask |= 1u << j;
+        }
       }
       run += __popc(__ballot_sync(0xffffffffu, inwin));
       // terms above the window are kept whatever the exact cut: one flag word
@@ -486,13 +500,17 @@ __global__ void __launch_bounds__(WP_BLOCK, 4) k_window_pass(const uint64_t* __r
     __syncthreads();
   }
   window_flush(st, ctl, wp, wk, wi, cap);
+  if (LIGHT) {  // the queue's rest
+    __syncwarp();
+    if ((uint32_t)lane < q_n) above_m += fx_from_bits(s_aq[warp][(q_head + lane) & 63u], &ctl->err);
+  }
   tot = warp_sum_u128(tot);
   above_m = warp_sum_u128(above_m);
   win_m = warp_sum_u128(win_m);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) above_c += __shfl_xor_sync(0xffffffffu, (unsigned long long)above_c, o);
   if (lane == 0) {
-    atomic_add_u128(&ctl->total_mass_hi, &ctl->total_mass_lo, tot);
+    if (!LIGHT) atomic_add_u128(&ctl->total_mass_hi, &ctl->total_mass_lo, tot);
     atomic_add_u128(&ctl->above_mass_hi, &ctl->above_mass_lo, above_m);
     atomic_add_u128(&ctl->win_mass_hi, &ctl->win_mass_lo, win_m);
     atomicAdd((unsigned long long*)&ctl->above_count, (unsigned long long)above_c);
@@ -539,7 +557,8 @@ __global__ void k_window_decide(Ctl* ctl, int mode, uint64_t count_target, doubl
 
 void launch_select_window(const uint64_t* probs, const uint64_t* keys, uint64_t n, Ctl* ctl,
                           const SelectScratch& ss, int mode, uint64_t count_target, double p,
-                          cudaStream_t st) {
+                          bool have_total, cudaStream_t st) {
+  const bool light = have_total && mode == 1;
   static bool attr_set = false;
   const size_t smem = 4 * (2 * SAMPLE_N + 32 * 256) + 8 * SAMPLE_THREADS;
   if (!attr_set) {
@@ -547,13 +566,17 @@ void launch_select_window(const uint64_t* probs, const uint64_t* keys, uint64_t 
     attr_set = true;
   }
   cudaMemsetAsync(&ctl->win_n, 0, sizeof(uint64_t) * 6, st);  // win_n .. win_mass_lo
-  cudaMemsetAsync(&ctl->total_mass_hi, 0, sizeof(uint64_t) * 2, st);
+  if (!light) cudaMemsetAsync(&ctl->total_mass_hi, 0, sizeof(uint64_t) * 2, st);
   k_sample_window<<<1, SAMPLE_THREADS, smem, st>>>(probs, n, ctl, mode, count_target, p);
   uint64_t tiles = (n + WP_TILE - 1) / WP_TILE;
   uint64_t grid = tiles < 148 * 8 ? tiles : 148 * 8;
   if (grid == 0) grid = 1;
-  k_window_pass<<<(unsigned)grid, WP_BLOCK, 0, st>>>(probs, keys, n, ctl, ss.win_p, ss.win_k, ss.win_i,
-                                                     ss.win_cap, ss.tile_keep, ss.keep_bits);
+  if (light)
+    k_window_pass<true><<<(unsigned)grid, WP_BLOCK, 0, st>>>(probs, keys, n, ctl, ss.win_p, ss.win_k, ss.win_i,
+                                                             ss.win_cap, ss.tile_keep, ss.keep_bits);
+  else
+    k_window_pass<false><<<(unsigned)grid, WP_BLOCK, 0, st>>>(probs, keys, n, ctl, ss.win_p, ss.win_k, ss.win_i,
+                                                              ss.win_cap, ss.tile_keep, ss.keep_bits);
   k_window_decide<<<1, 1, 0, st>>>(ctl, mode, count_target, p, ss.win_cap, n);
 }
 
