@@ -399,17 +399,17 @@ __global__ void __launch_bounds__(WP_BLOCK, 4) k_window_pass(const uint64_t* __r
   const uint64_t tiles = (n + L::TILE - 1) / L::TILE;
   for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const uint64_t base = tile * L::TILE;
+    // item j of this lane is term e0 + 32 j (TileLayout); rem: terms left from e0
+    const uint64_t e0 = base + (uint64_t)warp * 32 * WP_ITEMS + lane;
+    const int32_t rem = n > e0 ? (int32_t)min(n - e0, (uint64_t)(32 * WP_ITEMS)) : 0;
     uint64_t pbv[WP_ITEMS];
 #pragma unroll
-    for (int j = 0; j < WP_ITEMS; ++j) {  // all loads first
-      const uint64_t i = L::index(base, j);
-      pbv[j] = i < n ? probs[i] : 0ull;
-    }
+    for (int j = 0; j < WP_ITEMS; ++j) pbv[j] = 32 * j < rem ? probs[e0 + 32 * j] : 0ull;  // all loads first
     uint32_t wmask = 0, run = 0, tile_above = 0;
 #pragma unroll
     for (int j = 0; j < WP_ITEMS; ++j) {
       const uint64_t pb = pbv[j];
-      const bool valid = L::index(base, j) < n;
+      const bool valid = 32 * j < rem;
       const bool above = valid && pb > hi;
       const bool inwin = valid && !above && pb >= lo;
       if (LIGHT) {
@@ -443,8 +443,7 @@ __global__ void __launch_bounds__(WP_BLOCK, 4) k_window_pass(const uint64_t* __r
       // terms above the window are kept whatever the exact cut: one flag word
       // per 32 consecutive terms (window terms kept by the cut are added later)
       const uint32_t kb = __ballot_sync(0xffffffffu, above);
-      const uint64_t row = L::index(base, j) - lane;
-      if (lane == 0 && row < n) keep_bits[row >> 5] = kb;
+      if (lane == 0 && 32 * j < rem) keep_bits[(e0 >> 5) + j] = kb;  // lane 0: e0 starts a 32-term row
     }
     above_c += tile_above;
 #pragma unroll
@@ -480,7 +479,7 @@ __global__ void __launch_bounds__(WP_BLOCK, 4) k_window_pass(const uint64_t* __r
       const uint32_t wpos = s_warp[warp] + wrun + __popc(b & lt);
       wrun += __popc(b);
       if (inwin) {
-        const uint64_t i = L::index(base, j);
+        const uint64_t i = e0 + 32 * j;
         if (direct) {
           const uint64_t o = s_direct + wpos;
           if (o < cap) {
