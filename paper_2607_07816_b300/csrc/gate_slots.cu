@@ -113,7 +113,22 @@ __global__ void __launch_bounds__(GS_BLOCK) k_group_scan(const uint64_t* __restr
     const int staged = (int)(n - base < (uint64_t)(GS_TILE + GS_HALO) ? n - base : (uint64_t)(GS_TILE + GS_HALO));
     // the key before the tile must differ from the first key's group when there is none
     if (tid == 0) s_k[0] = base > 0 ? sk[base - 1] : ~sk[0];
-    for (int e = tid; e < staged; e += GS_BLOCK) s_k[e + 1] = sk[base + e];
+    // stage the tile and its halo, eight loads per thread in flight at a time
+#pragma unroll
+    for (int h = 0; h < GS_ITEMS; h += 8) {
+      uint64_t r[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int e = tid + (h + j) * GS_BLOCK;
+        r[j] = e < staged ? sk[base + e] : 0ull;
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int e = tid + (h + j) * GS_BLOCK;
+        if (e < staged) s_k[e + 1] = r[j];
+      }
+    }
+    if (tid < GS_HALO && GS_TILE + tid < staged) s_k[GS_TILE + tid + 1] = sk[base + GS_TILE + tid];
     __syncthreads();
     const int wbase = warp * 32 * GS_ITEMS;
     // pass 1: the warp's head and output counts (for a U without zero
@@ -185,7 +200,7 @@ __global__ void __launch_bounds__(GS_BLOCK) k_group_scan(const uint64_t* __restr
         const uint64_t gi = g + (uint64_t)__popc(hb & lt);
         heads[gi] = (uint32_t)(base + e);
         gmask[gi] = pm | (om << 16);
-        ooff[gi] = o + (cx - c);
+        if (!s_dense) ooff[gi] = o + (cx - c);  // dense U: group g starts at g 2^m
       }
       g += (uint64_t)__popc(hb);
       o += __shfl_sync(0xffffffffu, cx, 31);
@@ -274,7 +289,9 @@ __global__ void __launch_bounds__(AS_BLOCK) k_gate_apply_slots(
     s_re_nz[tid] = gp.re_nz[tid];
     s_im_nz[tid] = gp.im_nz[tid];
   }
-  __syncthreads();
+  // no zero entry in U: every group has all 2^m outputs, group g's first at
+  // g 2^m (the group scan then writes no output positions)
+  const bool dense = __syncthreads_and(tid >= d || ((gp.re_nz[tid & 15] | gp.im_nz[tid & 15]) & ((1u << d) - 1u)) == (1u << d) - 1u);
   const uint64_t G = ctl->count[0];
   const uint64_t imask = vb ? ((1ull << vb) - 1ull) : 0ull;
   uint32_t zeros = 0;
@@ -296,7 +313,7 @@ __global__ void __launch_bounds__(AS_BLOCK) k_gate_apply_slots(
       if (k < gpl && g < G) {
         h[k] = heads[g];
         gmv[k] = gmask[g];
-        ob[k] = ooff[g];
+        ob[k] = dense ? g << m : ooff[g];
       }
     }
     uint32_t mrun = 0, ng = 0, mb[GPL];

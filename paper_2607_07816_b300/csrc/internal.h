@@ -137,7 +137,8 @@ void launch_group_heads(const uint64_t* sk, uint64_t n, int shift, uint32_t* hea
 // Partner-group heads of the grouped sort keys with, per group, the present
 // mask pm (bit r: member with gate bits r present) | output mask om << 16
 // (bit r': some present r meets a nonzero U[r'][r]) in gmask, and the
-// group's first output position (exclusive scan of popc(om)) in ooff.
+// group's first output position (exclusive scan of popc(om)) in ooff, which
+// is left unwritten when U has no zero entry (group g then starts at g 2^m).
 // Group count in ctl->count[0], candidate count in ctl->count[1].  Uses
 // 2 * (n / 8192 + 2) lookback words.
 void launch_group_scan(const uint64_t* sk, uint64_t n, const GateParams& gp, uint32_t* heads, uint32_t* gmask,

@@ -306,13 +306,28 @@ __global__ void __launch_bounds__(MG_THREADS) k_merge_level(const uint64_t* __re
   const uint32_t ia = s_split[0], na = s_split[1] - ia;
   const uint32_t ib = o0 - ia, nb = (o1 - s_split[1]) - ib;
   const uint32_t len = na + nb;
-  for (uint32_t j = tid; j < na; j += MG_THREADS) {
-    s_k[j] = A[ia + j];
-    if (PAIRS) s_v[j] = vin[a0 + ia + j];
-  }
-  for (uint32_t j = tid; j < nb; j += MG_THREADS) {
-    s_k[na + j] = B[ib + j];
-    if (PAIRS) s_v[na + j] = vin[a0 + la + ib + j];
+  {  // stage both slices: all of a thread's loads in flight together
+    uint64_t r[MG_ITEMS];
+    uint32_t rv[MG_ITEMS];
+#pragma unroll
+    for (int j = 0; j < MG_ITEMS; ++j) {
+      const uint32_t e = (uint32_t)tid + (uint32_t)j * MG_THREADS;
+      const uint64_t src = e < na ? (uint64_t)ia + e : (uint64_t)la + ib + (e - na);  // from A
+      r[j] = 0;
+      rv[j] = 0;
+      if (e < len) {
+        r[j] = A[src];
+        if (PAIRS) rv[j] = vin[a0 + src];
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < MG_ITEMS; ++j) {
+      const uint32_t e = (uint32_t)tid + (uint32_t)j * MG_THREADS;
+      if (e < len) {
+        s_k[e] = r[j];
+        if (PAIRS) s_v[e] = rv[j];
+      }
+    }
   }
   __syncthreads();
   // this thread's outputs: [diag, diag + MG_ITEMS) of the block's slice

@@ -600,7 +600,9 @@ __global__ void k_window_tile_counts(const uint64_t* __restrict__ wp, const uint
   }
 }
 
-// Exclusive scan of the per-tile kept counts by one block.
+// Exclusive scan of the per-tile kept counts by one block: each thread takes
+// 8 consecutive tiles per round (loads first), one block scan per round.
+constexpr int TS_ITEMS = 8;
 __global__ void __launch_bounds__(1024) k_tile_scan(const uint32_t* __restrict__ tile_keep, uint64_t tiles,
                                                     uint64_t* __restrict__ tile_off, Ctl* ctl) {
   __shared__ uint64_t wsum[32];
@@ -608,22 +610,40 @@ __global__ void __launch_bounds__(1024) k_tile_scan(const uint32_t* __restrict__
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) s_carry = 0;
   __syncthreads();
-  for (uint64_t b0 = 0; b0 < tiles; b0 += 1024) {
-    const uint64_t t = b0 + threadIdx.x;
-    const uint64_t v = t < tiles ? tile_keep[t] : 0;
-    uint64_t x = v;
+  for (uint64_t b0 = 0; b0 < tiles; b0 += 1024 * TS_ITEMS) {
+    const uint64_t t0 = b0 + (uint64_t)threadIdx.x * TS_ITEMS;
+    uint32_t v[TS_ITEMS];
+#pragma unroll
+    for (int j = 0; j < TS_ITEMS; ++j) v[j] = t0 + j < tiles ? tile_keep[t0 + j] : 0u;
+    uint64_t sum = 0;
+#pragma unroll
+    for (int j = 0; j < TS_ITEMS; ++j) sum += v[j];
+    uint64_t x = sum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      uint64_t y = __shfl_up_sync(0xffffffffu, (unsigned long long)x, o);
+      const uint64_t y = __shfl_up_sync(0xffffffffu, (unsigned long long)x, o);
       if (lane >= o) x += y;
     }
     if (lane == 31) wsum[warp] = x;
     __syncthreads();
-    uint64_t base = s_carry;
-    for (int w = 0; w < warp; ++w) base += wsum[w];
-    if (t < tiles) tile_off[t] = base + x - v;
+    if (warp == 0) {
+      uint64_t y = wsum[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t z = __shfl_up_sync(0xffffffffu, (unsigned long long)y, o);
+        if (lane >= o) y += z;
+      }
+      wsum[lane] = y;  // inclusive over the warps
+    }
     __syncthreads();
-    if (threadIdx.x == 1023) s_carry = base + x;
+    uint64_t o = s_carry + (warp > 0 ? wsum[warp - 1] : 0ull) + x - sum;
+#pragma unroll
+    for (int j = 0; j < TS_ITEMS; ++j) {
+      if (t0 + j < tiles) tile_off[t0 + j] = o;
+      o += v[j];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) s_carry += wsum[31];
     __syncthreads();
   }
   if (threadIdx.x == 0) ctl->count[2] = s_carry;
@@ -805,6 +825,30 @@ __global__ void __launch_bounds__(PICK_THREADS) k_select_finish(Ctl* ctl, const 
     if (ctl->sel_done) break;
     const int bits = (int)ctl->sel_bits;
     const uint64_t ph = ctl->sel_prefix_hi, pl = ctl->sel_prefix_lo;
+    if (ctl->sel_bin_count == 1) {
+      // one term left under the prefix: it is the cut, and the terms before
+      // it in canonical order are the ones counted so far
+      for (uint64_t i = threadIdx.x; i < nb; i += blockDim.x) {
+        const uint64_t hi = buf[2 * i], lo = buf[2 * i + 1];
+        if (!z_matches(hi, lo, ph, pl, bits)) continue;
+        const uint64_t pbits = ~hi;
+        const u128 sc = make_u128(ctl->sel_before_mass_hi, ctl->sel_before_mass_lo) + fx_from_bits(pbits, &ctl->err);
+        const uint64_t cc = ctl->sel_before_count + 1;
+        const u128 target = make_u128(ctl->sel_target_hi, ctl->sel_target_lo);
+        if (!(ctl->sel_mode == 1 ? (u128)cc >= target : sc >= target)) {
+          ctl->sel_done = 2;  // the target is never reached: no cut
+          continue;
+        }
+        ctl->cut_pbits = pbits;
+        ctl->cut_key = lo;
+        ctl->cut_count = cc;
+        ctl->cut_mass_hi = (uint64_t)(sc >> 64);
+        ctl->cut_mass_lo = (uint64_t)sc;
+        ctl->sel_done = 1;
+      }
+      __syncthreads();
+      if (ctl->sel_done) break;
+    }
     int D, shift;
     sel_digit(bits, &D, &shift);
     for (int i = threadIdx.x; i < SEL_BINS; i += blockDim.x) {
