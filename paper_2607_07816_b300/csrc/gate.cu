@@ -52,15 +52,29 @@ void launch_gate_keys(const uint64_t* keys, uint64_t n, const GateParams& gp, ui
 }
 
 // ------------------------------------------------------------------ gate tables
+constexpr uint32_t RESET_PER_BLOCK = 256 * 16;
+
 __global__ void __launch_bounds__(256) k_store_tables(const GateTables t, GateTables* __restrict__ dst,
-                                                      uint32_t words) {
-  const uint64_t* src = reinterpret_cast<const uint64_t*>(&t);
-  uint64_t* out = reinterpret_cast<uint64_t*>(dst);
-  for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) out[i] = src[i];
+                                                      uint32_t words, const GateReset r) {
+  if (blockIdx.x == 0) {
+    const uint64_t* src = reinterpret_cast<const uint64_t*>(&t);
+    uint64_t* out = reinterpret_cast<uint64_t*>(dst);
+    for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) out[i] = src[i];
+  }
+  if (!r.ctl) return;
+  if (blockIdx.x == 0 && threadIdx.x < 16) r.part_hist[threadIdx.x] = 0u;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    r.ctl->tile_counter[0] = 0;
+    for (int i = 0; i < 4; ++i) r.ctl->count[i] = 0;
+    r.ctl->total_mass_hi = r.ctl->total_mass_lo = 0;
+  }
+  const uint32_t e = blockIdx.x * RESET_PER_BLOCK + threadIdx.x;
+  for (uint32_t i = e; i < r.lb_words && i < (blockIdx.x + 1) * RESET_PER_BLOCK; i += blockDim.x) r.lb[i] = 0;
 }
 
-void launch_store_tables(const GateTables& t, GateTables* dst, size_t bytes, cudaStream_t st) {
-  k_store_tables<<<1, 256, 0, st>>>(t, dst, (uint32_t)((bytes + 7) / 8));
+void launch_store_tables(const GateTables& t, GateTables* dst, size_t bytes, const GateReset& r, cudaStream_t st) {
+  const uint32_t blocks = r.ctl ? 1u + r.lb_words / RESET_PER_BLOCK : 1u;
+  k_store_tables<<<blocks, 256, 0, st>>>(t, dst, (uint32_t)((bytes + 7) / 8), r);
 }
 
 // ------------------------------------------------------------------ heads

@@ -221,9 +221,8 @@ void launch_group_scan(const uint64_t* sk, uint64_t n, const GateParams& gp, uin
     attr_set = true;
   }
   const uint64_t tiles = (n + GS_TILE - 1) / GS_TILE;
-  cudaMemsetAsync(lookback, 0, sizeof(uint64_t) * 2 * (tiles + 1), st);
-  cudaMemsetAsync(&ctl->tile_counter[0], 0, sizeof(uint64_t), st);
-  cudaMemsetAsync(&ctl->count[0], 0, sizeof(uint64_t) * 2, st);
+  // the look-back words, ctl->tile_counter[0] and ctl->count[0..1] arrive
+  // cleared (the gate's table upload clears them)
   if (n == 0) return;
   const uint64_t grid = tiles < 148 * 3 ? tiles : 148 * 3;
   k_group_scan<<<(unsigned)grid, GS_BLOCK, GS_SMEM, st>>>(sk, n, gp, heads, gmask, ooff, lookback,
@@ -459,8 +458,7 @@ void launch_gate_apply_slots(int prec, const uint64_t* sk, const uint32_t* sidx,
   const int gpl = slots_gpl(prec, gp.m);
   const uint32_t gc = 32u * gpl, mc = gc << gp.m;
   const size_t smem = AS_WARPS * (prec == 0 ? SlotsLayout<double2>::bytes(gc, mc) : SlotsLayout<float2>::bytes(gc, mc));
-  cudaMemsetAsync(&ctl->count[3], 0, sizeof(uint64_t), st);
-  cudaMemsetAsync(&ctl->total_mass_hi, 0, sizeof(uint64_t) * 2, st);
+  // ctl->count[3] and the total mass arrive cleared (the gate's table upload)
   if (n == 0) return;
   const uint64_t batches = (n + gc - 1) / gc;  // groups <= n
   uint64_t grid = (batches + AS_WARPS - 1) / AS_WARPS;

@@ -76,8 +76,20 @@ struct GateTables {
   double U[512];
 };
 
-// Stores the first `bytes` bytes of t (passed by value) at dst.
-void launch_store_tables(const GateTables& t, GateTables* dst, size_t bytes, cudaStream_t st);
+// Per-gate counters cleared by the table upload of a gate on the global path
+// (one launch instead of a memset per counter): ctl->tile_counter[0],
+// ctl->count[0..3], the total mass, the 16 partition totals of the
+// regrouping and the group scan's look-back words.  ctl == nullptr: none.
+struct GateReset {
+  Ctl* ctl;
+  uint32_t* part_hist;  // [16]
+  uint64_t* lb;         // [lb_words]
+  uint32_t lb_words;
+};
+
+// Stores the first `bytes` bytes of t (passed by value) at dst and clears
+// what r names.
+void launch_store_tables(const GateTables& t, GateTables* dst, size_t bytes, const GateReset& r, cudaStream_t st);
 
 // Gate parameters passed by value to the gate kernels.
 struct GateParams {
@@ -112,7 +124,8 @@ __device__ __forceinline__ uint64_t to_natural(const uint64_t* nat, uint64_t x) 
 // The sorted keys (packed with the term index when gp.vbits > 0, else with
 // indices in sidx) end in sk[w], w the return value; *launches receives
 // the number of kernels launched.  The scratch's lookback words hold the
-// per-tile counts and offsets, hist the counts per r.
+// per-tile counts and offsets, hist the counts per r (its first 16 words
+// cleared beforehand: GateReset::part_hist).
 int regroup_terms(const uint64_t* keys, uint64_t n, const GateParams& gp, uint64_t* sk[2], uint32_t* sidx[2],
                   const SortScratch& sc, cudaStream_t st, int* launches, cudaError_t* cerr);
 void regroup_prepare();
@@ -140,13 +153,15 @@ void launch_group_heads(const uint64_t* sk, uint64_t n, int shift, uint32_t* hea
 // group's first output position (exclusive scan of popc(om)) in ooff, which
 // is left unwritten when U has no zero entry (group g then starts at g 2^m).
 // Group count in ctl->count[0], candidate count in ctl->count[1].  Uses
-// 2 * (n / 8192 + 2) lookback words.
+// 2 * (n / 8192 + 2) lookback words, which, with ctl->tile_counter[0] and
+// ctl->count[0..1], must be zero on entry (GateReset).
 void launch_group_scan(const uint64_t* sk, uint64_t n, const GateParams& gp, uint32_t* heads, uint32_t* gmask,
                        uint64_t* ooff, uint64_t* lookback, Ctl* ctl, cudaStream_t st);
 // Per-group mat-vec writing each structurally nonzero output at its
 // precomputed position; exact zeros are written as zero and counted in
 // ctl->count[3] (to be removed by launch_drop_zero_terms).  complex128 also
 // sums the candidates' exact fixed-point total mass into ctl->total_mass.
+// ctl->count[3] and the total mass must be zero on entry (GateReset).
 void launch_gate_apply_slots(int prec, const uint64_t* sk, const uint32_t* sidx, uint64_t n, const uint32_t* heads,
                              const uint32_t* gmask, const uint64_t* ooff, const void* amps_in, const GateParams& gp,
                              uint64_t* keys_out, void* amps_out, uint64_t* probs_out, Ctl* ctl, cudaStream_t st);
@@ -181,8 +196,7 @@ struct SelectScratch {
   uint64_t* hist_mass;    // [SEL_BINS][2] (hi, lo)
   uint64_t* buf;          // [FINISH_CAP][2] composite (hi = ~pbits, lo = key)
   uint64_t* win_p;        // [win_cap] probability bits of the window terms
-  uint64_t* win_k;        // [win_cap] keys of the window terms
-  uint32_t* win_i;        // [win_cap] positions of the window terms
+  uint32_t* win_i;        // [win_cap] positions of the window terms (their keys stay in place)
   uint64_t win_cap;
   uint32_t* tile_keep;    // [window tiles] kept terms per tile
   uint64_t* tile_off;     // [window tiles] output offset per tile

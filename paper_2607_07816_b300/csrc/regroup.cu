@@ -407,7 +407,7 @@ int regroup_terms(const uint64_t* keys, uint64_t n, const GateParams& gp, uint64
   }
   uint32_t* cnt = reinterpret_cast<uint32_t*>(sc.lookback);
   uint32_t* off = cnt + (uint64_t)D * tiles;
-  cudaMemsetAsync(sc.hist, 0, sizeof(uint32_t) * 16, st);
+  // sc.hist[0..15] arrives cleared (the gate's table upload clears it)
   k_part_counts<<<(unsigned)tiles, RG_THREADS, 0, st>>>(keys, n, gp, tiles, cnt, sc.hist);
   launch_tile_offsets(cnt, sc.hist, tiles, D, off, st);
   if (pairs)

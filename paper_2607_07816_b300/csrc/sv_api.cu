@@ -55,6 +55,8 @@ struct sv_state {
   uint64_t* ooff = nullptr;   // per group: first output position
   uint64_t lb_entries = 0;
   uint64_t* lookback = nullptr;
+  uint64_t gs_lb_entries = 0;
+  uint64_t* gs_lb = nullptr;  // the group scan's two look-backs (cleared with the gate's tables)
 
   uint32_t* hist = nullptr;
   uint32_t* hist_host = nullptr;
@@ -364,14 +366,14 @@ sv_status upload_nat(sv_state* s) {
   build_nat_table(s->n, s->order, s->tab_host->nat);
   const size_t bytes = offsetof(GateTables, U);
   g_h2d += sizeof(s->tab_host->nat);
-  launch_store_tables(*s->tab_host, s->tab_dev, bytes, s->st);
+  launch_store_tables(*s->tab_host, s->tab_dev, bytes, GateReset{nullptr, nullptr, nullptr, 0}, s->st);
   launched(s, PH_OTHER, 1);
   return cuda_check(s, cudaGetLastError(), "natural-key table upload");
 }
 
 // Sort-key permutation of the gate for the state's current order, uploaded
 // for the kernels; the order it leaves goes to order_next.
-sv_status upload_perm(sv_state* s, GateParams& gp) {
+sv_status upload_perm(sv_state* s, GateParams& gp, const GateReset& reset = GateReset{nullptr, nullptr, nullptr, 0}) {
   build_gate_tables(s->n, gp.m, gp.q, s->order, s->tab_host, gp.qpos, s->order_next);
   gp.perm = &s->tab_dev->perm;
   gp.U = s->tab_dev->U;
@@ -383,7 +385,7 @@ sv_status upload_perm(sv_state* s, GateParams& gp) {
   // transfer to wait for in the stream)
   const size_t bytes = offsetof(GateTables, U) + sizeof(double) * 2 * (1u << (2 * gp.m));
   g_h2d += bytes;
-  launch_store_tables(*s->tab_host, s->tab_dev, bytes, s->st);
+  launch_store_tables(*s->tab_host, s->tab_dev, bytes, reset, s->st);
   launched(s, PH_OTHER, 1);
   return cuda_check(s, cudaGetLastError(), "gate table upload");
 }
@@ -436,6 +438,9 @@ sv_status sv_create_ex(int n, uint64_t K, double p, int prec, void* cuda_stream,
   if (rc == SV_OK) rc = ensure_sort_cap(s, 4096);
   if (rc == SV_OK) {
     cudaMemsetAsync(s->ctl, 0, sizeof(Ctl), s->st);
+    // the select histogram starts cleared; each level's pick clears it again
+    cudaMemsetAsync(s->ss.hist_count, 0, sizeof(uint32_t) * SEL_BINS, s->st);
+    cudaMemsetAsync(s->ss.hist_mass, 0, sizeof(uint64_t) * 2 * SEL_BINS, s->st);
     const uint64_t* nat_dev = &s->tab_dev->nat[0][0];
     cudaMemcpyAsync(&s->ctl->nat, &nat_dev, sizeof(nat_dev), cudaMemcpyHostToDevice, s->st);
     const uint64_t zero_key = 0;
@@ -479,6 +484,7 @@ sv_status sv_destroy(sv_state* s) {
   dev_free(s, s->gmask);
   dev_free(s, s->ooff);
   dev_free(s, s->lookback);
+  dev_free(s, s->gs_lb);
   dev_free(s, s->hist);
   dev_free(s, s->tile_counter);
   dev_free(s, s->ctl);
@@ -486,7 +492,6 @@ sv_status sv_destroy(sv_state* s) {
   dev_free(s, s->ss.hist_mass);
   dev_free(s, s->ss.buf);
   dev_free(s, s->ss.win_p);
-  dev_free(s, s->ss.win_k);
   dev_free(s, s->ss.win_i);
   dev_free(s, s->ss.tile_keep);
   dev_free(s, s->ss.tile_off);
@@ -551,8 +556,15 @@ sv_status sv_apply_gate(sv_state* s, int m, const int* qubits, const double* U) 
     return fail(s, SV_E_ARG, "sv_apply_gate: state too large for 32-bit term indices");
   sv_status rc = ensure_state_cap(s, N << m);
   if (rc == SV_OK) rc = ensure_sort_cap(s, N);
-  if (rc == SV_OK) rc = ensure_lookback(s, 2 * (N / 8192 + 2) + 16);  // the group scan's two look-backs
   if (rc != SV_OK) return rc;
+  const uint64_t gs_words = 2 * (N / 8192 + 2);  // the group scan's two look-backs
+  if (gs_words > s->gs_lb_entries) {
+    dev_free(s, s->gs_lb);
+    s->gs_lb_entries = 0;
+    s->gs_lb = (uint64_t*)dev_alloc(s, (gs_words + gs_words / 2) * sizeof(uint64_t));
+    if (!s->gs_lb) return fail(s, SV_E_NOMEM, "group scan look-back allocation failed");
+    s->gs_lb_entries = gs_words + gs_words / 2;
+  }
   const int alt = 1 - s->cur;
   // The bucket-local kernel sorts and applies inside shared memory; it is used
   // for states that fit one of its batches (measured: beyond that the sorted
@@ -636,7 +648,7 @@ sv_status sv_apply_gate(sv_state* s, int m, const int* qubits, const double* U) 
   }
   if (!done) {
     ++s->global_gates;
-    rc = upload_perm(s, gp);
+    rc = upload_perm(s, gp, GateReset{s->ctl, s->hist, s->gs_lb, (uint32_t)gs_words});
     if (rc != SV_OK) return rc;
     const int passes = (s->n + RADIX_BITS - 1) / RADIX_BITS;
     // pack the term index below the sort key when both fit in 64 bits
@@ -666,7 +678,7 @@ sv_status sv_apply_gate(sv_state* s, int m, const int* qubits, const double* U) 
     }
     s->stats.sort_passes = (uint32_t)run;
     ph_begin(s, PH_HEADS);
-    launch_group_scan(s->sk[w], N, gp, s->heads, s->gmask, s->ooff, s->lookback, s->ctl, s->st);
+    launch_group_scan(s->sk[w], N, gp, s->heads, s->gmask, s->ooff, s->gs_lb, s->ctl, s->st);
     ph_end(s, PH_HEADS);
     ph_begin(s, PH_APPLY);
     launch_gate_apply_slots(s->prec, s->sk[w], s->sidx[w], N, s->heads, s->gmask, s->ooff, s->amps[s->cur], gp,
@@ -713,12 +725,10 @@ sv_status ensure_window_cap(sv_state* s, uint64_t N) {
   if (need > s->ss.win_cap) {
     uint64_t cap = need + need / 2;
     dev_free(s, s->ss.win_p);
-    dev_free(s, s->ss.win_k);
     dev_free(s, s->ss.win_i);
     s->ss.win_p = (uint64_t*)dev_alloc(s, cap * 8);
-    s->ss.win_k = (uint64_t*)dev_alloc(s, cap * 8);
     s->ss.win_i = (uint32_t*)dev_alloc(s, cap * 4);
-    if (!s->ss.win_p || !s->ss.win_k || !s->ss.win_i) {
+    if (!s->ss.win_p || !s->ss.win_i) {
       s->ss.win_cap = 0;
       return fail(s, SV_E_NOMEM, "select window allocation failed");
     }
@@ -760,14 +770,12 @@ sv_status run_select(sv_state* s, int mode, uint64_t count_target, uint32_t* lev
   // long the list is and whether the bin is small enough to finish; the host
   // continues level by level only when that did not resolve the cut.
   ph_begin(s, PH_SELECT);
-  cudaMemsetAsync(&s->ctl->sel_gated, 1, sizeof(uint32_t), s->st);  // nonzero: gated
   for (int level = 0; level < 2; ++level) {
     launch_select_hist(s->probs[s->cur], s->keys[s->cur], N, s->ctl, s->ss, s->st);
     launch_select_pick(s->ctl, s->ss, s->p, s->st);
   }
   launch_select_compact(s->probs[s->cur], s->keys[s->cur], N, s->ctl, s->ss, s->st);
   launch_select_finish(s->ctl, s->ss, s->p, s->st);
-  cudaMemsetAsync(&s->ctl->sel_gated, 0, sizeof(uint32_t), s->st);
   ph_end(s, PH_SELECT);
   launched(s, PH_SELECT, 6);
   *levels += 2;

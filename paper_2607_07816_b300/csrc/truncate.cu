@@ -31,7 +31,7 @@ __device__ __forceinline__ uint64_t natural_key(const uint64_t* nat, uint64_t k)
 // 3 * SEL_BINS global atomics, so blocks get a large share each).
 __global__ void __launch_bounds__(256) k_select_hist(const uint64_t* __restrict__ probs,
                                                      const uint64_t* __restrict__ keys, uint64_t n,
-                                                     const uint64_t* __restrict__ wp, const uint64_t* __restrict__ wk,
+                                                     const uint64_t* __restrict__ wp, const uint32_t* __restrict__ wi,
                                                      Ctl* ctl, uint32_t* __restrict__ g_cnt,
                                                      uint64_t* __restrict__ g_mass) {
   __shared__ uint32_t s_cnt[SEL_BINS];
@@ -40,7 +40,6 @@ __global__ void __launch_bounds__(256) k_select_hist(const uint64_t* __restrict_
   if (ctl->sel_gated && ctl->sel_bin_count <= (uint64_t)FINISH_CAP) return;  // the finish takes over
   const bool win = ctl->use_window != 0;
   const uint64_t* P = win ? wp : probs;
-  const uint64_t* Kk = win ? wk : keys;  // stored keys (made natural where a tie needs them)
   const uint64_t* nat = ctl->nat;
   const uint64_t nn = win ? ctl->win_n : n;
   uint64_t chunk = (nn + gridDim.x - 1) / gridDim.x;
@@ -63,7 +62,8 @@ __global__ void __launch_bounds__(256) k_select_hist(const uint64_t* __restrict_
     const uint64_t pb = P[i];
     const uint64_t hi = ~pb;
     if (bits <= 64 && bits > 0 && ((hi ^ ph) >> (64 - bits)) != 0) continue;
-    const uint64_t lo = need_lo ? natural_key(nat, Kk[i]) : 0ull;
+    // the stored key (made natural) only where a tie on the probability needs it
+    const uint64_t lo = need_lo ? natural_key(nat, keys[win ? (uint64_t)wi[i] : i]) : 0ull;
     if (bits > 64 && !z_matches(hi, lo, ph, pl, bits)) continue;
     hist_add(z_digit(hi, lo, shift, D), pb, s_cnt, s_mass, &ctl->err, cache);
   }
@@ -77,14 +77,14 @@ __global__ void __launch_bounds__(256) k_select_hist(const uint64_t* __restrict_
   }
 }
 
+// The histogram arrives cleared: it is zero when allocated, and the pick that
+// follows every histogram level clears it after reading it.
 void launch_select_hist(const uint64_t* probs, const uint64_t* keys, uint64_t n, Ctl* ctl,
                         const SelectScratch& ss, cudaStream_t st) {
-  cudaMemsetAsync(ss.hist_count, 0, sizeof(uint32_t) * SEL_BINS, st);
-  cudaMemsetAsync(ss.hist_mass, 0, sizeof(uint64_t) * 2 * SEL_BINS, st);
   if (n == 0) return;
   uint64_t blocks = (n + 8191) / 8192;
   if (blocks > 148 * 4) blocks = 148 * 4;
-  k_select_hist<<<(unsigned)blocks, 256, 0, st>>>(probs, keys, n, ss.win_p, ss.win_k, ctl, ss.hist_count,
+  k_select_hist<<<(unsigned)blocks, 256, 0, st>>>(probs, keys, n, ss.win_p, ss.win_i, ctl, ss.hist_count,
                                                   ss.hist_mass);
 }
 
@@ -240,7 +240,7 @@ __device__ void block_select_two(const uint32_t* a, const int* r, uint32_t* hist
 // the work: the cut found afterwards is the exact one either way.
 __global__ void __launch_bounds__(SAMPLE_THREADS) k_sample_window(const uint64_t* __restrict__ probs,
                                                                   uint64_t n, Ctl* ctl, int mode,
-                                                                  uint64_t count_target, double p) {
+                                                                  uint64_t count_target, double p, bool light) {
   extern __shared__ __align__(16) uint8_t s_dyn[];
   uint32_t* a = reinterpret_cast<uint32_t*>(s_dyn);
   uint32_t* tmp = a + SAMPLE_N;
@@ -249,18 +249,30 @@ __global__ void __launch_bounds__(SAMPLE_THREADS) k_sample_window(const uint64_t
   __shared__ uint32_t dsum[256], wtot[32];
   __shared__ int s_rank;
   const int tid = threadIdx.x;
+  if (tid < 6) (&ctl->win_n)[tid] = 0;  // win_n .. win_mass_lo, summed by the window pass
+  if (!light && tid == 0) ctl->total_mass_hi = ctl->total_mass_lo = 0;  // the pass sums the total too
   // stratified random sample: one term at a hashed offset inside each of
   // SAMPLE_N equal strata (a fixed stride would alias with the 2^m-periodic
   // layout of the candidates)
-  for (int j = tid; j < SAMPLE_N; j += SAMPLE_THREADS) {
-    const uint64_t b0 = (uint64_t)j * (n / SAMPLE_N) + ((uint64_t)j * (n % SAMPLE_N)) / SAMPLE_N;
-    const uint64_t b1 = (uint64_t)(j + 1) * (n / SAMPLE_N) + ((uint64_t)(j + 1) * (n % SAMPLE_N)) / SAMPLE_N;
-    uint64_t h = (uint64_t)j * 0x9E3779B97F4A7C15ull;
-    h ^= h >> 31;
-    h *= 0xBF58476D1CE4E5B9ull;
-    h ^= h >> 29;
-    const uint64_t idx = b1 > b0 ? b0 + h % (b1 - b0) : (b0 < n ? b0 : n - 1);
-    a[j] = (uint32_t)((~probs[idx]) >> 31);  // drop the constant top bit, keep 32 bits
+  {
+    constexpr int SI = SAMPLE_N / SAMPLE_THREADS;
+    uint64_t idx[SI], v[SI];
+#pragma unroll
+    for (int t = 0; t < SI; ++t) {
+      const uint64_t j = (uint64_t)(tid + t * SAMPLE_THREADS);
+      const uint64_t b0 = j * (n / SAMPLE_N) + (j * (n % SAMPLE_N)) / SAMPLE_N;
+      const uint64_t b1 = (j + 1) * (n / SAMPLE_N) + ((j + 1) * (n % SAMPLE_N)) / SAMPLE_N;
+      uint64_t h = j * 0x9E3779B97F4A7C15ull;
+      h ^= h >> 31;
+      h *= 0xBF58476D1CE4E5B9ull;
+      h ^= h >> 29;
+      idx[t] = b1 > b0 ? b0 + h % (b1 - b0) : (b0 < n ? b0 : n - 1);
+    }
+#pragma unroll
+    for (int t = 0; t < SI; ++t) v[t] = probs[idx[t]];  // the probes in flight together
+#pragma unroll
+    for (int t = 0; t < SI; ++t)
+      a[tid + t * SAMPLE_THREADS] = (uint32_t)((~v[t]) >> 31);  // drop the constant top bit, keep 32 bits
   }
   __syncthreads();
   if (mode == 1) {  // by count: only two order statistics of the sample are needed
@@ -332,7 +344,7 @@ constexpr int WP_TILE = WP_BLOCK * WP_ITEMS;
 
 // One streaming pass over all terms (tile t = terms [t*WP_TILE, ...),
 // static assignment): the exact fixed-point total mass, the count and mass
-// above the window, the window's mass and its terms (probability, key, index)
+// above the window, the window's mass and its terms (probability, index)
 // gathered into the window buffer, and per tile the number of terms above
 // the window (they are kept whatever the exact cut is).
 // Window terms are staged in shared memory and written out in batches, one
@@ -344,14 +356,13 @@ constexpr int WP_STAGE = 1024;
 
 struct WindowStage {
   uint64_t p[WP_STAGE];
-  uint64_t k[WP_STAGE];
   uint32_t i[WP_STAGE];
   uint32_t n;
   uint64_t base;
 };
 
 __device__ __forceinline__ void window_flush(WindowStage& st, Ctl* ctl, uint64_t* __restrict__ wp,
-                                             uint64_t* __restrict__ wk, uint32_t* __restrict__ wi, uint64_t cap) {
+                                             uint32_t* __restrict__ wi, uint64_t cap) {
   // all threads call it; st.n is block-uniform
   const uint32_t cnt = st.n;
   if (cnt == 0) return;
@@ -362,7 +373,6 @@ __device__ __forceinline__ void window_flush(WindowStage& st, Ctl* ctl, uint64_t
     const uint64_t o = b + j;
     if (o < cap) {
       wp[o] = st.p[j];
-      wk[o] = st.k[j];
       wi[o] = st.i[j];
     }
   }
@@ -377,9 +387,8 @@ __device__ __forceinline__ void window_flush(WindowStage& st, Ctl* ctl, uint64_t
 // 128-bit conversions run on full warps of above-window terms only.
 template <bool LIGHT>
 __global__ void __launch_bounds__(WP_BLOCK, 4) k_window_pass(const uint64_t* __restrict__ probs,
-                                                          const uint64_t* __restrict__ keys, uint64_t n,
-                                                          Ctl* ctl, uint64_t* __restrict__ wp,
-                                                          uint64_t* __restrict__ wk, uint32_t* __restrict__ wi,
+                                                          uint64_t n, Ctl* ctl, uint64_t* __restrict__ wp,
+                                                          uint32_t* __restrict__ wi,
                                                           uint64_t cap, uint32_t* __restrict__ tile_keep,
                                                           uint32_t* __restrict__ keep_bits) {
   typedef TileLayout<WP_BLOCK, WP_ITEMS> L;
@@ -469,7 +478,7 @@ __global__ void __launch_bounds__(WP_BLOCK, 4) k_window_pass(const uint64_t* __r
     const uint32_t acc = s_acc;
     if (acc == 0) continue;  // block-uniform
     const bool direct = acc > WP_STAGE;
-    if (!direct && st.n + acc > WP_STAGE) window_flush(st, ctl, wp, wk, wi, cap);
+    if (!direct && st.n + acc > WP_STAGE) window_flush(st, ctl, wp, wi, cap);
     const uint32_t sbase = st.n;
     uint32_t wrun = 0;  // window positions: the same ballots again, in item order
 #pragma unroll
@@ -484,12 +493,10 @@ __global__ void __launch_bounds__(WP_BLOCK, 4) k_window_pass(const uint64_t* __r
           const uint64_t o = s_direct + wpos;
           if (o < cap) {
             wp[o] = pbv[j];
-            wk[o] = keys[i];
             wi[o] = (uint32_t)i;
           }
         } else {
           st.p[sbase + wpos] = pbv[j];
-          st.k[sbase + wpos] = keys[i];
           st.i[sbase + wpos] = (uint32_t)i;
         }
       }
@@ -498,7 +505,7 @@ __global__ void __launch_bounds__(WP_BLOCK, 4) k_window_pass(const uint64_t* __r
     if (!direct && threadIdx.x == 0) st.n = sbase + acc;
     __syncthreads();
   }
-  window_flush(st, ctl, wp, wk, wi, cap);
+  window_flush(st, ctl, wp, wi, cap);
   if (LIGHT) {  // the queue's rest
     __syncwarp();
     if ((uint32_t)lane < q_n) above_m += fx_from_bits(s_aq[warp][(q_head + lane) & 63u], &ctl->err);
@@ -547,6 +554,7 @@ __global__ void k_window_decide(Ctl* ctl, int mode, uint64_t count_target, doubl
   ctl->sel_target_hi = (uint64_t)(target >> 64);
   ctl->sel_target_lo = (uint64_t)target;
   ctl->compact_n = 0;
+  ctl->sel_gated = 1;  // the levels enqueued behind the window test on the device whether to run
   ctl->use_window = valid ? 1u : 0u;
   ctl->sel_before_count = valid ? ac : 0;
   ctl->sel_before_mass_hi = valid ? ctl->above_mass_hi : 0;
@@ -564,17 +572,15 @@ void launch_select_window(const uint64_t* probs, const uint64_t* keys, uint64_t 
     cudaFuncSetAttribute(k_sample_window, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr_set = true;
   }
-  cudaMemsetAsync(&ctl->win_n, 0, sizeof(uint64_t) * 6, st);  // win_n .. win_mass_lo
-  if (!light) cudaMemsetAsync(&ctl->total_mass_hi, 0, sizeof(uint64_t) * 2, st);
-  k_sample_window<<<1, SAMPLE_THREADS, smem, st>>>(probs, n, ctl, mode, count_target, p);
+  k_sample_window<<<1, SAMPLE_THREADS, smem, st>>>(probs, n, ctl, mode, count_target, p, light);
   uint64_t tiles = (n + WP_TILE - 1) / WP_TILE;
   uint64_t grid = tiles < 148 * 8 ? tiles : 148 * 8;
   if (grid == 0) grid = 1;
   if (light)
-    k_window_pass<true><<<(unsigned)grid, WP_BLOCK, 0, st>>>(probs, keys, n, ctl, ss.win_p, ss.win_k, ss.win_i,
+    k_window_pass<true><<<(unsigned)grid, WP_BLOCK, 0, st>>>(probs, n, ctl, ss.win_p, ss.win_i,
                                                              ss.win_cap, ss.tile_keep, ss.keep_bits);
   else
-    k_window_pass<false><<<(unsigned)grid, WP_BLOCK, 0, st>>>(probs, keys, n, ctl, ss.win_p, ss.win_k, ss.win_i,
+    k_window_pass<false><<<(unsigned)grid, WP_BLOCK, 0, st>>>(probs, n, ctl, ss.win_p, ss.win_i,
                                                               ss.win_cap, ss.tile_keep, ss.keep_bits);
   k_window_decide<<<1, 1, 0, st>>>(ctl, mode, count_target, p, ss.win_cap, n);
 }
@@ -584,7 +590,7 @@ uint64_t window_tiles(uint64_t n) { return (n + WP_TILE - 1) / WP_TILE; }
 // ---------------------------------------------------------------- windowed compaction
 // After a select on the window: every tile's kept count is its count above
 // the window plus its window terms not after the cut.
-__global__ void k_window_tile_counts(const uint64_t* __restrict__ wp, const uint64_t* __restrict__ wk,
+__global__ void k_window_tile_counts(const uint64_t* __restrict__ wp, const uint64_t* __restrict__ keys,
                                      const uint32_t* __restrict__ wi, Ctl* ctl,
                                      uint32_t* __restrict__ tile_keep, uint32_t* __restrict__ keep_bits) {
   const uint64_t wn = ctl->win_n;
@@ -592,8 +598,8 @@ __global__ void k_window_tile_counts(const uint64_t* __restrict__ wp, const uint
   for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < wn;
        j += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t pb = wp[j];
-    if (pb > pc || (pb == pc && natural_key(ctl->nat, wk[j]) <= kc)) {
-      const uint32_t i = wi[j];
+    const uint32_t i = wi[j];
+    if (pb > pc || (pb == pc && natural_key(ctl->nat, keys[i]) <= kc)) {
       atomicAdd(&tile_keep[i / WP_TILE], 1u);
       atomicOr(&keep_bits[i >> 5], 1u << (i & 31));
     }
@@ -765,11 +771,14 @@ __device__ void block_pick(const uint32_t* cnt, const uint64_t* mass /* [nbins][
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(PICK_THREADS) k_select_pick(Ctl* ctl, const uint32_t* cnt,
-                                                              const uint64_t* mass, double p) {
-  if (ctl->sel_done) return;
+__global__ void __launch_bounds__(PICK_THREADS) k_select_pick(Ctl* ctl, uint32_t* cnt, uint64_t* mass, double p) {
+  if (ctl->sel_done) return;  // the level's histogram kernel added nothing either
   if (ctl->sel_gated && ctl->sel_bin_count <= (uint64_t)FINISH_CAP) return;
-  block_pick(cnt, mass, ctl, p);
+  block_pick(cnt, mass, ctl, p);  // ends with a block barrier
+  for (int i = threadIdx.x; i < SEL_BINS; i += PICK_THREADS) {  // cleared for the next level
+    cnt[i] = 0;
+    mass[2 * i] = mass[2 * i + 1] = 0;
+  }
 }
 
 void launch_select_pick(Ctl* ctl, const SelectScratch& ss, double p, cudaStream_t st) {
@@ -780,13 +789,12 @@ void launch_select_pick(Ctl* ctl, const SelectScratch& ss, double p, cudaStream_
 __global__ void __launch_bounds__(256) k_select_compact(const uint64_t* __restrict__ probs,
                                                         const uint64_t* __restrict__ keys, uint64_t n,
                                                         const uint64_t* __restrict__ wp,
-                                                        const uint64_t* __restrict__ wk, Ctl* ctl,
+                                                        const uint32_t* __restrict__ wi, Ctl* ctl,
                                                         uint64_t* __restrict__ buf) {
   if (ctl->sel_done) return;
   if (ctl->sel_gated && ctl->sel_bin_count > (uint64_t)FINISH_CAP) return;  // more levels first
   const bool win = ctl->use_window != 0;
   const uint64_t* P = win ? wp : probs;
-  const uint64_t* Kk = win ? wk : keys;
   const uint64_t nn = win ? ctl->win_n : n;
   const int bits = (int)ctl->sel_bits;
   const uint64_t ph = ctl->sel_prefix_hi, pl = ctl->sel_prefix_lo;
@@ -794,7 +802,7 @@ __global__ void __launch_bounds__(256) k_select_compact(const uint64_t* __restri
        i += (uint64_t)gridDim.x * blockDim.x) {
     uint64_t hi = ~P[i];
     if (bits <= 64 && ((hi ^ ph) >> (64 - bits)) != 0) continue;
-    uint64_t lo = natural_key(ctl->nat, Kk[i]);
+    uint64_t lo = natural_key(ctl->nat, keys[win ? (uint64_t)wi[i] : i]);
     if (!z_matches(hi, lo, ph, pl, bits)) continue;
     uint64_t pos = atomicAdd((unsigned long long*)&ctl->compact_n, 1ull);
     if (pos < FINISH_CAP) {
@@ -804,21 +812,28 @@ __global__ void __launch_bounds__(256) k_select_compact(const uint64_t* __restri
   }
 }
 
+// ctl->compact_n arrives cleared (by the window's decision or the last finish).
 void launch_select_compact(const uint64_t* probs, const uint64_t* keys, uint64_t n, Ctl* ctl,
                            const SelectScratch& ss, cudaStream_t st) {
-  cudaMemsetAsync(&ctl->compact_n, 0, sizeof(uint64_t), st);
   if (n == 0) return;
   uint64_t blocks = (n + 255) / 256;
   if (blocks > 148 * 4) blocks = 148 * 4;
-  k_select_compact<<<(unsigned)blocks, 256, 0, st>>>(probs, keys, n, ss.win_p, ss.win_k, ctl, ss.buf);
+  k_select_compact<<<(unsigned)blocks, 256, 0, st>>>(probs, keys, n, ss.win_p, ss.win_i, ctl, ss.buf);
 }
 
 __global__ void __launch_bounds__(PICK_THREADS) k_select_finish(Ctl* ctl, const uint64_t* buf,
                                                                 double p) {
   __shared__ uint32_t s_cnt[SEL_BINS];
   __shared__ uint64_t s_mass[2 * SEL_BINS];
-  if (ctl->sel_gated && ctl->sel_bin_count > (uint64_t)FINISH_CAP) return;
+  const bool gated = ctl->sel_gated != 0;
+  const uint64_t bin0 = ctl->sel_bin_count;
   uint64_t nb = ctl->compact_n;
+  __syncthreads();
+  if (threadIdx.x == 0) {  // the gated run ends here; the next gather starts from an empty buffer
+    ctl->sel_gated = 0;
+    ctl->compact_n = 0;
+  }
+  if (gated && bin0 > (uint64_t)FINISH_CAP) return;
   if (nb > FINISH_CAP) nb = FINISH_CAP;
   for (int it = 0; it < 128; ++it) {
     __syncthreads();
@@ -1092,7 +1107,7 @@ void launch_truncate_windowed(int prec, const uint64_t* keys, const void* amps, 
   (void)probs;  // the keep flags replace the probabilities here
   const uint64_t tiles = window_tiles(n);
   k_set_scale<<<1, 1, 0, st>>>(ctl);
-  k_window_tile_counts<<<148 * 4, 256, 0, st>>>(ss.win_p, ss.win_k, ss.win_i, ctl, ss.tile_keep, ss.keep_bits);
+  k_window_tile_counts<<<148 * 4, 256, 0, st>>>(ss.win_p, keys, ss.win_i, ctl, ss.tile_keep, ss.keep_bits);
   k_tile_scan<<<1, 1024, 0, st>>>(ss.tile_keep, tiles, ss.tile_off, ctl);
   uint64_t grid = tiles < PEAK_PARTS ? tiles : PEAK_PARTS;
   if (grid == 0) grid = 1;
