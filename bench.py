@@ -219,17 +219,24 @@ def run_ours(args, rank, world):
         l0 = sv.sv_launch_count()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize(dev)
+        loc0 = st.stats()["local_gates"]
+        pending = None
         e0.record(stream)
         for _ in range(steps):
             q, u = gates[gi % len(gates)]
             gi += 1
-            loc0 = st.stats()["local_gates"]
             st.apply_gate(q, u)
-            s1 = st.stats()
             st.truncate()
-            s2 = st.stats()
-            st.peak()
+            # the peak of every step, read back pipelined: its 16 bytes reach
+            # the host while the next step runs, and the statistics are
+            # gathered while the compaction and the readout are on the GPU
+            ticket = st.peak_async()
+            s1 = s2 = st.stats()
+            if pending is not None:
+                st.peak_wait(pending)
+            pending = ticket
             path = "local" if s1["local_gates"] > loc0 else "apply"
+            loc0 = s1["local_gates"]
             totals["n_in_" + path] += s1["n_in"]
             totals["n_pre_" + path] += s1["n_pre"]
             # FP64 pipe work of the mat-vec kernel, counted as 2 flops per operation:
@@ -247,6 +254,8 @@ def run_ours(args, rank, world):
             totals["select_levels"] += s2["select_levels"]
             totals["window_hits"] += s2["window_hits"]
             totals["window_terms"] += s2["window_terms"]
+        if pending is not None:
+            st.peak_wait(pending)
         e1.record(stream)
         torch.cuda.synchronize(dev)
         launches = sv.sv_launch_count() - l0

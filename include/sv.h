@@ -101,6 +101,17 @@ sv_status sv_truncate(sv_state* s, uint64_t* kept, double* retained_fraction);
  * 16 bytes come back to the host.  SV_E_STATE if the state is empty. */
 sv_status sv_peak(sv_state* s, uint64_t* key, double* prob);
 
+/* Pipelined form of sv_peak: enqueues the same readout on the handle's
+ * stream together with a 16-byte copy into a pinned result slot and returns
+ * at once with *ticket naming the result.  sv_peak_wait(s, ticket, ...)
+ * then waits for that copy only (not for later work on the stream) and
+ * returns the key and probability the state had when sv_peak_async was
+ * called.  Eight results can be outstanding; a ticket older than the last
+ * eight, or never issued, gives SV_E_ARG.  Device error flags are reported
+ * by the handle's next waiting call.  SV_E_STATE if the state is empty. */
+sv_status sv_peak_async(sv_state* s, uint64_t* ticket);
+sv_status sv_peak_wait(sv_state* s, uint64_t ticket, uint64_t* key, double* prob);
+
 /* Keys and probabilities in canonical order into host buffers of `cap`
  * entries; writes min(cap, N) entries and sets *count = N.  Either buffer
  * may be NULL.  Synchronises. */

@@ -87,6 +87,12 @@ struct sv_state {
   uint64_t* peak_part = nullptr;
   uint32_t peak_blocks = 0;
   bool peak_ready = false;
+  // pipelined peak readouts: results copied into a ring of pinned slots,
+  // each with the event that marks its copy done
+  static constexpr uint32_t PEAK_RING = 8;
+  uint64_t* peak_host = nullptr;  // [PEAK_RING][2] (probability bits, key)
+  cudaEvent_t peak_ev[PEAK_RING] = {};
+  uint64_t peak_issued = 0;
   // the complex128 mat-vec left the exact total mass of the current terms in
   // ctl->total_mass (valid until the terms change)
   bool total_ready = false;
@@ -501,6 +507,9 @@ sv_status sv_destroy(sv_state* s) {
     if (s->ev_end[ph]) cudaEventDestroy(s->ev_end[ph]);
   }
   if (s->hist_host) cudaFreeHost(s->hist_host);
+  if (s->peak_host) cudaFreeHost(s->peak_host);
+  for (uint32_t i = 0; i < sv_state::PEAK_RING; ++i)
+    if (s->peak_ev[i]) cudaEventDestroy(s->peak_ev[i]);
   if (s->ctl_host) cudaFreeHost(s->ctl_host);
   if (s->tab_host) cudaFreeHost(s->tab_host);
   dev_free(s, s->tab_dev);
@@ -897,10 +906,8 @@ sv_status sv_truncate(sv_state* s, uint64_t* kept, double* retained_fraction) {
   return SV_OK;
 }
 
-sv_status sv_peak(sv_state* s, uint64_t* key, double* prob) {
-  SV_GUARD(s);
-  if (!key || !prob) return fail(s, SV_E_ARG, "sv_peak: null output");
-  if (s->N == 0) return fail(s, SV_E_STATE, "sv_peak: empty state");
+namespace {
+void enqueue_peak(sv_state* s) {
   ph_begin(s, PH_PEAK);
   if (s->peak_ready) {  // the last truncation's compaction left per-block partials
     launch_peak_partials(s->peak_part, s->peak_blocks, s->ctl, s->st);
@@ -910,11 +917,61 @@ sv_status sv_peak(sv_state* s, uint64_t* key, double* prob) {
     launched(s, PH_PEAK, 2);
   }
   ph_end(s, PH_PEAK);
+}
+}  // namespace
+
+sv_status sv_peak(sv_state* s, uint64_t* key, double* prob) {
+  SV_GUARD(s);
+  if (!key || !prob) return fail(s, SV_E_ARG, "sv_peak: null output");
+  if (s->N == 0) return fail(s, SV_E_STATE, "sv_peak: empty state");
+  enqueue_peak(s);
   sv_status rc = sync_ctl(s, "sv_peak");
   if (rc != SV_OK) return rc;
   *key = s->ctl_host->peak_z_lo;
   uint64_t b = s->ctl_host->peak_z_hi;
   std::memcpy(prob, &b, 8);
+  return SV_OK;
+}
+
+sv_status sv_peak_async(sv_state* s, uint64_t* ticket) {
+  SV_GUARD(s);
+  if (!ticket) return fail(s, SV_E_ARG, "sv_peak_async: null ticket");
+  if (s->N == 0) return fail(s, SV_E_STATE, "sv_peak_async: empty state");
+  if (!s->peak_host) {
+    if (cudaMallocHost(&s->peak_host, sizeof(uint64_t) * 2 * sv_state::PEAK_RING) != cudaSuccess) {
+      s->peak_host = nullptr;
+      return fail(s, SV_E_NOMEM, "sv_peak_async: pinned result ring");
+    }
+    for (uint32_t i = 0; i < sv_state::PEAK_RING; ++i) {
+      sv_status rc = cuda_check(s, cudaEventCreateWithFlags(&s->peak_ev[i], cudaEventDisableTiming),
+                                "sv_peak_async");
+      if (rc != SV_OK) return rc;
+    }
+  }
+  enqueue_peak(s);
+  const uint64_t t = s->peak_issued++;
+  const uint32_t slot = (uint32_t)(t % sv_state::PEAK_RING);
+  sv_status rc = cuda_check(s, cudaMemcpyAsync(s->peak_host + 2 * slot, &s->ctl->peak_z_hi, 2 * sizeof(uint64_t),
+                                               cudaMemcpyDeviceToHost, s->st),
+                            "sv_peak_async");
+  if (rc == SV_OK) rc = cuda_check(s, cudaEventRecord(s->peak_ev[slot], s->st), "sv_peak_async");
+  if (rc != SV_OK) return rc;
+  *ticket = t;
+  return SV_OK;
+}
+
+sv_status sv_peak_wait(sv_state* s, uint64_t ticket, uint64_t* key, double* prob) {
+  SV_GUARD(s);
+  if (!key || !prob) return fail(s, SV_E_ARG, "sv_peak_wait: null output");
+  if (ticket >= s->peak_issued || s->peak_issued - ticket > sv_state::PEAK_RING)
+    return fail(s, SV_E_ARG, "sv_peak_wait: unknown ticket or result already overwritten");
+  const uint32_t slot = (uint32_t)(ticket % sv_state::PEAK_RING);
+  // only this result's copy is waited for (device error flags are checked
+  // at the next wait of the other calls)
+  sv_status rc = cuda_check(s, cudaEventSynchronize(s->peak_ev[slot]), "sv_peak_wait");
+  if (rc != SV_OK) return rc;
+  *key = s->peak_host[2 * slot + 1];
+  std::memcpy(prob, &s->peak_host[2 * slot], 8);
   return SV_OK;
 }
 

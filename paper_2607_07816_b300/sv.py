@@ -22,6 +22,7 @@ _STATUS = {0: "SV_OK", -1: "SV_E_ARG", -2: "SV_E_NOMEM", -3: "SV_E_CUDA", -4: "S
            -5: "SV_E_TIMEOUT", -6: "SV_E_STATE"}
 
 EXPORTED = ["sv_create", "sv_create_ex", "sv_destroy", "sv_apply_gate", "sv_truncate", "sv_peak",
+            "sv_peak_async", "sv_peak_wait",
             "sv_probs", "sv_num_terms", "sv_retained_mass", "sv_export", "sv_load", "sv_last_error",
             "sv_last_stats", "sv_set_timing", "sv_phase_times", "sv_launch_count", "sv_transfer_bytes", "sv_peak_noalloc",
             "svb_create", "svb_destroy", "svb_add", "svb_remove", "svb_step", "svb_num_terms",
@@ -87,6 +88,10 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.sv_truncate.argtypes = [vp, P(u64), P(dbl)]
     lib.sv_peak.restype = i32
     lib.sv_peak.argtypes = [vp, P(u64), P(dbl)]
+    lib.sv_peak_async.restype = i32
+    lib.sv_peak_async.argtypes = [vp, P(u64)]
+    lib.sv_peak_wait.restype = i32
+    lib.sv_peak_wait.argtypes = [vp, u64, P(u64), P(dbl)]
     lib.sv_probs.restype = i32
     lib.sv_probs.argtypes = [vp, vp, vp, u64, P(u64)]
     lib.sv_num_terms.restype = i32
@@ -195,6 +200,19 @@ def sv_truncate(h: int):
 def sv_peak(h: int):
     k, p = ctypes.c_uint64(), ctypes.c_double()
     _check(h, load_library().sv_peak(ctypes.c_void_p(h), ctypes.byref(k), ctypes.byref(p)))
+    return k.value, p.value
+
+
+def sv_peak_async(h: int) -> int:
+    t = ctypes.c_uint64()
+    _check(h, load_library().sv_peak_async(ctypes.c_void_p(h), ctypes.byref(t)))
+    return t.value
+
+
+def sv_peak_wait(h: int, ticket: int):
+    k, p = ctypes.c_uint64(), ctypes.c_double()
+    _check(h, load_library().sv_peak_wait(ctypes.c_void_p(h), ctypes.c_uint64(ticket), ctypes.byref(k),
+                                          ctypes.byref(p)))
     return k.value, p.value
 
 
@@ -325,6 +343,14 @@ class SparseState:
 
     def peak(self):
         return sv_peak(self.h)
+
+    def peak_async(self) -> int:
+        """Enqueue the peak readout and return a ticket at once; peak_wait
+        returns the (key, probability) the state had at this call."""
+        return sv_peak_async(self.h)
+
+    def peak_wait(self, ticket: int):
+        return sv_peak_wait(self.h, ticket)
 
     def num_terms(self) -> int:
         return sv_num_terms(self.h)

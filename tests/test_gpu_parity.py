@@ -164,6 +164,35 @@ def test_brickwork_n40_reduced_K(sv, oracle_mod):
     run_both(c.gates, g, o, check_every=False)
 
 
+def test_pipelined_peak_readout_matches_oracle_gate_by_gate(sv, oracle_mod):
+    # every gate's peak is enqueued and read back later (up to 8 in flight);
+    # each must be the peak the oracle has after that gate
+    c = C.brickwork_n40(layers=3, K=1 << 10)
+    g = sv.SparseState(c.n, c.K, c.p)
+    o = oracle_mod.Oracle(c.n, c.K, c.p)
+    tickets, expected, got = [], [], []
+    for q, u in c.gates:
+        g.apply_gate(q, u)
+        g.truncate()
+        o.apply_gate(q, u)
+        o.truncate()
+        tickets.append(g.peak_async())
+        expected.append(o.peak())
+        if len(tickets) - len(got) == 8:
+            got.append(g.peak_wait(tickets[len(got)]))
+    while len(got) < len(tickets):
+        got.append(g.peak_wait(tickets[len(got)]))
+    assert got == expected
+    assert g.peak() == expected[-1]
+    # a ticket whose slot was reused, or one never issued, is rejected
+    with pytest.raises(sv.SVError) as e:
+        g.peak_wait(tickets[0])
+    assert e.value.status == sv.SV_E_ARG
+    with pytest.raises(sv.SVError) as e:
+        g.peak_wait(tickets[-1] + 1)
+    assert e.value.status == sv.SV_E_ARG
+
+
 def test_complex64_close_to_complex128(sv, oracle_mod):
     c = C.brickwork_circuit(16, 4, seed=3, sigma=0.05, K=1 << 10, p=1.0)
     g64 = sv.SparseState(c.n, c.K, c.p, prec=1)
