@@ -9,6 +9,7 @@
 // members in ascending r.
 #include "c64_exact.cuh"
 #include "internal.h"
+#include "launch.cuh"
 #include "tile.cuh"
 
 namespace sv {
@@ -56,6 +57,7 @@ constexpr uint32_t RESET_PER_BLOCK = 256 * 16;
 
 __global__ void __launch_bounds__(256) k_store_tables(const GateTables t, GateTables* __restrict__ dst,
                                                       uint32_t words, const GateReset r) {
+  pdl_prologue();
   if (blockIdx.x == 0) {
     const uint64_t* src = reinterpret_cast<const uint64_t*>(&t);
     uint64_t* out = reinterpret_cast<uint64_t*>(dst);
@@ -74,7 +76,7 @@ __global__ void __launch_bounds__(256) k_store_tables(const GateTables t, GateTa
 
 void launch_store_tables(const GateTables& t, GateTables* dst, size_t bytes, const GateReset& r, cudaStream_t st) {
   const uint32_t blocks = r.ctl ? 1u + r.lb_words / RESET_PER_BLOCK : 1u;
-  k_store_tables<<<blocks, 256, 0, st>>>(t, dst, (uint32_t)((bytes + 7) / 8), r);
+  launch_pdl(k_store_tables, blocks, 256, 0, st, t, dst, (uint32_t)((bytes + 7) / 8), r);
 }
 
 // ------------------------------------------------------------------ heads

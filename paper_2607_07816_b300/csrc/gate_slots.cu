@@ -28,6 +28,7 @@
 // pass, which gives the same list as dropping them here (A4 zero-drop).
 #include "c64_exact.cuh"
 #include "internal.h"
+#include "launch.cuh"
 #include "select.cuh"
 #include "tile.cuh"
 
@@ -81,6 +82,7 @@ __global__ void __launch_bounds__(GS_BLOCK) k_group_scan(const uint64_t* __restr
                                                          const GateParams gp, uint32_t* __restrict__ heads,
                                                          uint32_t* __restrict__ gmask, uint64_t* __restrict__ ooff,
                                                          uint64_t* lb_heads, uint64_t* lb_out, Ctl* ctl) {
+  pdl_prologue();
   extern __shared__ __align__(16) uint8_t s_dyn[];
   uint64_t* s_k = reinterpret_cast<uint64_t*>(s_dyn);
   __shared__ uint32_t s_wh[GS_WARPS], s_wo[GS_WARPS], s_colnz[16];
@@ -225,8 +227,8 @@ void launch_group_scan(const uint64_t* sk, uint64_t n, const GateParams& gp, uin
   // cleared (the gate's table upload clears them)
   if (n == 0) return;
   const uint64_t grid = tiles < 148 * 3 ? tiles : 148 * 3;
-  k_group_scan<<<(unsigned)grid, GS_BLOCK, GS_SMEM, st>>>(sk, n, gp, heads, gmask, ooff, lookback,
-                                                           lookback + tiles + 1, ctl);
+  launch_pdl(k_group_scan, (unsigned)grid, GS_BLOCK, GS_SMEM, st, sk, n, gp, heads, gmask, ooff, lookback,
+             lookback + tiles + 1, ctl);
 }
 
 // A warp takes a batch of 32 * gpl groups.  Larger batches leave fewer
@@ -273,6 +275,7 @@ __global__ void __launch_bounds__(AS_BLOCK) k_gate_apply_slots(
     const uint32_t* __restrict__ gmask, const uint64_t* __restrict__ ooff,
     const typename SCplx<Real>::T* __restrict__ amps_in, const GateParams gp, uint64_t* __restrict__ keys_out,
     typename SCplx<Real>::T* __restrict__ amps_out, uint64_t* __restrict__ probs_out, Ctl* ctl) {
+  pdl_prologue();
   constexpr int gpl = GPL;
   typedef typename SCplx<Real>::T C2;
   extern __shared__ __align__(16) uint8_t s_dyn[];
@@ -290,7 +293,8 @@ __global__ void __launch_bounds__(AS_BLOCK) k_gate_apply_slots(
   }
   // no zero entry in U: every group has all 2^m outputs, group g's first at
   // g 2^m (the group scan then writes no output positions)
-  const bool dense = __syncthreads_and(tid >= d || ((gp.re_nz[tid & 15] | gp.im_nz[tid & 15]) & ((1u << d) - 1u)) == (1u << d) - 1u);
+  const uint32_t full = (1u << d) - 1u;
+  const bool dense = __syncthreads_and(tid >= d || ((gp.re_nz[tid & 15] | gp.im_nz[tid & 15]) & full) == full);
   const uint64_t G = ctl->count[0];
   const uint64_t imask = vb ? ((1ull << vb) - 1ull) : 0ull;
   uint32_t zeros = 0;
@@ -473,8 +477,8 @@ void launch_gate_apply_slots(int prec, const uint64_t* sk, const uint32_t* sidx,
       if (per_sm < 1) per_sm = 1;                                                                             \
     }                                                                                                         \
     if (grid > 148ull * per_sm) grid = 148ull * per_sm;                                                       \
-    k_gate_apply_slots<R, GPLV><<<(unsigned)grid, AS_BLOCK, smem, st>>>(                                      \
-        sk, sidx, heads, gmask, ooff, (const C2*)amps_in, gp, keys_out, (C2*)amps_out, probs_out, ctl);       \
+    launch_pdl(k_gate_apply_slots<R, GPLV>, (unsigned)grid, AS_BLOCK, smem, st, sk, sidx, heads, gmask, ooff,     \
+               (const C2*)amps_in, gp, keys_out, (C2*)amps_out, probs_out, ctl);                               \
   } while (0)
   if (prec == 0) {
     if (gpl == 2)

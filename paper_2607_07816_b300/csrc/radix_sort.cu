@@ -13,6 +13,7 @@
 // ranks its keys per warp with __match_any_sync, stages them in shared
 // memory in digit order and writes each digit run at its scanned offset.
 #include "internal.h"
+#include "launch.cuh"
 
 namespace sv {
 
@@ -86,6 +87,7 @@ constexpr int SCAN_THREADS = 1024;
 __global__ void __launch_bounds__(SCAN_THREADS) k_tile_offsets(const uint32_t* __restrict__ cnt,
                                                                const uint32_t* __restrict__ hist, uint64_t tiles,
                                                                uint32_t* __restrict__ off) {
+  pdl_prologue();
   __shared__ uint32_t wsum[SCAN_THREADS / 32];
   __shared__ uint32_t s_carry;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -130,7 +132,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_tile_offsets(const uint32_t* _
 
 void launch_tile_offsets(const uint32_t* cnt, const uint32_t* hist, uint64_t tiles, int digits, uint32_t* off,
                          cudaStream_t st) {
-  k_tile_offsets<<<digits, SCAN_THREADS, 0, st>>>(cnt, hist, tiles, off);
+  launch_pdl(k_tile_offsets, digits, SCAN_THREADS, 0, st, cnt, hist, tiles, off);
 }
 
 // 3. Scatter: rank the tile's keys per warp (match_any and per-warp digit

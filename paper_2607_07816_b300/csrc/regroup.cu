@@ -30,6 +30,7 @@
 // run goes first, so the result equals the stable radix sort of the new
 // keys bit for bit.
 #include "internal.h"
+#include "launch.cuh"
 
 namespace sv {
 
@@ -86,6 +87,7 @@ __device__ __forceinline__ void gate_positions(const GateParams& gp, int* qpos, 
 __global__ void __launch_bounds__(RG_THREADS) k_part_counts(const uint64_t* __restrict__ keys, uint64_t n,
                                                             const GateParams gp, uint64_t tiles,
                                                             uint32_t* __restrict__ cnt, uint32_t* __restrict__ hist) {
+  pdl_prologue();
   __shared__ uint32_t h[16];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int m = gp.m, D = 1 << m;
@@ -125,6 +127,7 @@ __global__ void __launch_bounds__(RG_THREADS) k_part_scatter(const uint64_t* __r
                                                              const GateParams gp, uint64_t tiles,
                                                              const uint32_t* __restrict__ off,
                                                              uint64_t* __restrict__ sk, uint32_t* __restrict__ sidx) {
+  pdl_prologue();
   extern __shared__ __align__(16) uint8_t s_dyn[];
   uint64_t* s_keys = reinterpret_cast<uint64_t*>(s_dyn);
   uint32_t* s_vals = reinterpret_cast<uint32_t*>(s_dyn + sizeof(uint64_t) * RG_TILE);
@@ -263,6 +266,7 @@ __device__ __forceinline__ bool merge_block(const uint32_t* __restrict__ hist, i
 __global__ void __launch_bounds__(256) k_merge_splits(const uint64_t* __restrict__ kin,
                                                       const uint32_t* __restrict__ hist, int D, int level,
                                                       uint32_t nblocks, uint32_t* __restrict__ splits) {
+  pdl_prologue();
   const uint32_t b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (b >= nblocks) return;
@@ -279,6 +283,7 @@ __global__ void __launch_bounds__(MG_THREADS) k_merge_level(const uint64_t* __re
                                                             uint64_t* __restrict__ kout, uint32_t* __restrict__ vout,
                                                             const uint32_t* __restrict__ hist, int D, int level,
                                                             const uint32_t* __restrict__ splits) {
+  pdl_prologue();
   extern __shared__ __align__(16) uint8_t s_dyn[];
   uint64_t* s_k = reinterpret_cast<uint64_t*>(s_dyn);
   uint32_t* s_v = reinterpret_cast<uint32_t*>(s_dyn + sizeof(uint64_t) * mg_pad(MG_TILE));
@@ -408,27 +413,27 @@ int regroup_terms(const uint64_t* keys, uint64_t n, const GateParams& gp, uint64
   uint32_t* cnt = reinterpret_cast<uint32_t*>(sc.lookback);
   uint32_t* off = cnt + (uint64_t)D * tiles;
   // sc.hist[0..15] arrives cleared (the gate's table upload clears it)
-  k_part_counts<<<(unsigned)tiles, RG_THREADS, 0, st>>>(keys, n, gp, tiles, cnt, sc.hist);
+  launch_pdl(k_part_counts, (unsigned)tiles, RG_THREADS, 0, st, keys, n, gp, tiles, cnt, sc.hist);
   launch_tile_offsets(cnt, sc.hist, tiles, D, off, st);
   if (pairs)
-    k_part_scatter<true><<<(unsigned)tiles, RG_THREADS, part_smem(true), st>>>(keys, n, gp, tiles, off, sk[0],
-                                                                               sidx[0]);
+    launch_pdl(k_part_scatter<true>, (unsigned)tiles, RG_THREADS, part_smem(true), st, keys, n, gp, tiles, off,
+               sk[0], sidx[0]);
   else
-    k_part_scatter<false><<<(unsigned)tiles, RG_THREADS, part_smem(false), st>>>(keys, n, gp, tiles, off, sk[0],
-                                                                                 nullptr);
+    launch_pdl(k_part_scatter<false>, (unsigned)tiles, RG_THREADS, part_smem(false), st, keys, n, gp, tiles, off,
+               sk[0], nullptr);
   *launches = 3;
   int cur = 0;
   const uint64_t grid = (n + MG_TILE - 1) / MG_TILE + (uint64_t)D;
   uint32_t* splits = cnt;  // the partition's counts and offsets are no longer needed
   for (int level = 1; level <= m; ++level) {
-    k_merge_splits<<<(unsigned)((grid * 32 + 255) / 256), 256, 0, st>>>(sk[cur], sc.hist, D, level, (uint32_t)grid,
-                                                                       splits);
+    launch_pdl(k_merge_splits, (unsigned)((grid * 32 + 255) / 256), 256, 0, st, sk[cur], sc.hist, D, level,
+               (uint32_t)grid, splits);
     if (pairs)
-      k_merge_level<true><<<(unsigned)grid, MG_THREADS, merge_smem(true), st>>>(
-          sk[cur], sidx[cur], sk[1 - cur], sidx[1 - cur], sc.hist, D, level, splits);
+      launch_pdl(k_merge_level<true>, (unsigned)grid, MG_THREADS, merge_smem(true), st, sk[cur], sidx[cur],
+                 sk[1 - cur], sidx[1 - cur], sc.hist, D, level, splits);
     else
-      k_merge_level<false><<<(unsigned)grid, MG_THREADS, merge_smem(false), st>>>(
-          sk[cur], nullptr, sk[1 - cur], nullptr, sc.hist, D, level, splits);
+      launch_pdl(k_merge_level<false>, (unsigned)grid, MG_THREADS, merge_smem(false), st, sk[cur], nullptr,
+                 sk[1 - cur], nullptr, sc.hist, D, level, splits);
     cur ^= 1;
     *launches += 2;
   }

@@ -13,6 +13,7 @@
 // block.  A final compaction keeps every term not after the cut and applies
 // the renormalisation.
 #include "internal.h"
+#include "launch.cuh"
 #include "c64_exact.cuh"
 #include "select.cuh"
 #include "tile.cuh"
@@ -34,6 +35,7 @@ __global__ void __launch_bounds__(256) k_select_hist(const uint64_t* __restrict_
                                                      const uint64_t* __restrict__ wp, const uint32_t* __restrict__ wi,
                                                      Ctl* ctl, uint32_t* __restrict__ g_cnt,
                                                      uint64_t* __restrict__ g_mass) {
+  pdl_prologue();
   __shared__ uint32_t s_cnt[SEL_BINS];
   __shared__ uint64_t s_mass[2 * SEL_BINS];
   if (ctl->sel_done) return;
@@ -84,8 +86,8 @@ void launch_select_hist(const uint64_t* probs, const uint64_t* keys, uint64_t n,
   if (n == 0) return;
   uint64_t blocks = (n + 8191) / 8192;
   if (blocks > 148 * 4) blocks = 148 * 4;
-  k_select_hist<<<(unsigned)blocks, 256, 0, st>>>(probs, keys, n, ss.win_p, ss.win_i, ctl, ss.hist_count,
-                                                  ss.hist_mass);
+  launch_pdl(k_select_hist, (unsigned)blocks, 256, 0, st, probs, keys, n, ss.win_p, ss.win_i, ctl, ss.hist_count,
+             ss.hist_mass);
 }
 
 // ---------------------------------------------------------------- sample window
@@ -241,6 +243,7 @@ __device__ void block_select_two(const uint32_t* a, const int* r, uint32_t* hist
 __global__ void __launch_bounds__(SAMPLE_THREADS) k_sample_window(const uint64_t* __restrict__ probs,
                                                                   uint64_t n, Ctl* ctl, int mode,
                                                                   uint64_t count_target, double p, bool light) {
+  pdl_prologue();
   extern __shared__ __align__(16) uint8_t s_dyn[];
   uint32_t* a = reinterpret_cast<uint32_t*>(s_dyn);
   uint32_t* tmp = a + SAMPLE_N;
@@ -391,6 +394,7 @@ __global__ void __launch_bounds__(WP_BLOCK, 4) k_window_pass(const uint64_t* __r
                                                           uint32_t* __restrict__ wi,
                                                           uint64_t cap, uint32_t* __restrict__ tile_keep,
                                                           uint32_t* __restrict__ keep_bits) {
+  pdl_prologue();
   typedef TileLayout<WP_BLOCK, WP_ITEMS> L;
   __shared__ uint32_t s_warp[WP_BLOCK / 32];
   __shared__ uint32_t s_above[WP_BLOCK / 32];
@@ -526,6 +530,7 @@ __global__ void __launch_bounds__(WP_BLOCK, 4) k_window_pass(const uint64_t* __r
 // One thread: choose between the window and the full list and set up the
 // select state (target from the exact total mass).
 __global__ void k_window_decide(Ctl* ctl, int mode, uint64_t count_target, double p, uint64_t cap, uint64_t n) {
+  pdl_prologue();
   const u128 total = make_u128(ctl->total_mass_hi, ctl->total_mass_lo);
   u128 target;
   if (mode == 0) {
@@ -572,17 +577,17 @@ void launch_select_window(const uint64_t* probs, const uint64_t* keys, uint64_t 
     cudaFuncSetAttribute(k_sample_window, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr_set = true;
   }
-  k_sample_window<<<1, SAMPLE_THREADS, smem, st>>>(probs, n, ctl, mode, count_target, p, light);
+  launch_pdl(k_sample_window, 1, SAMPLE_THREADS, smem, st, probs, n, ctl, mode, count_target, p, light);
   uint64_t tiles = (n + WP_TILE - 1) / WP_TILE;
   uint64_t grid = tiles < 148 * 8 ? tiles : 148 * 8;
   if (grid == 0) grid = 1;
   if (light)
-    k_window_pass<true><<<(unsigned)grid, WP_BLOCK, 0, st>>>(probs, n, ctl, ss.win_p, ss.win_i,
-                                                             ss.win_cap, ss.tile_keep, ss.keep_bits);
+    launch_pdl(k_window_pass<true>, (unsigned)grid, WP_BLOCK, 0, st, probs, n, ctl, ss.win_p, ss.win_i, ss.win_cap,
+               ss.tile_keep, ss.keep_bits);
   else
-    k_window_pass<false><<<(unsigned)grid, WP_BLOCK, 0, st>>>(probs, n, ctl, ss.win_p, ss.win_i,
-                                                              ss.win_cap, ss.tile_keep, ss.keep_bits);
-  k_window_decide<<<1, 1, 0, st>>>(ctl, mode, count_target, p, ss.win_cap, n);
+    launch_pdl(k_window_pass<false>, (unsigned)grid, WP_BLOCK, 0, st, probs, n, ctl, ss.win_p, ss.win_i, ss.win_cap,
+               ss.tile_keep, ss.keep_bits);
+  launch_pdl(k_window_decide, 1, 1, 0, st, ctl, mode, count_target, p, ss.win_cap, n);
 }
 
 uint64_t window_tiles(uint64_t n) { return (n + WP_TILE - 1) / WP_TILE; }
@@ -593,6 +598,7 @@ uint64_t window_tiles(uint64_t n) { return (n + WP_TILE - 1) / WP_TILE; }
 __global__ void k_window_tile_counts(const uint64_t* __restrict__ wp, const uint64_t* __restrict__ keys,
                                      const uint32_t* __restrict__ wi, Ctl* ctl,
                                      uint32_t* __restrict__ tile_keep, uint32_t* __restrict__ keep_bits) {
+  pdl_prologue();
   const uint64_t wn = ctl->win_n;
   const uint64_t pc = ctl->cut_pbits, kc = ctl->cut_key;
   for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < wn;
@@ -611,6 +617,7 @@ __global__ void k_window_tile_counts(const uint64_t* __restrict__ wp, const uint
 constexpr int TS_ITEMS = 8;
 __global__ void __launch_bounds__(1024) k_tile_scan(const uint32_t* __restrict__ tile_keep, uint64_t tiles,
                                                     uint64_t* __restrict__ tile_off, Ctl* ctl) {
+  pdl_prologue();
   __shared__ uint64_t wsum[32];
   __shared__ uint64_t s_carry;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -772,6 +779,7 @@ __device__ void block_pick(const uint32_t* cnt, const uint64_t* mass /* [nbins][
 }
 
 __global__ void __launch_bounds__(PICK_THREADS) k_select_pick(Ctl* ctl, uint32_t* cnt, uint64_t* mass, double p) {
+  pdl_prologue();
   if (ctl->sel_done) return;  // the level's histogram kernel added nothing either
   if (ctl->sel_gated && ctl->sel_bin_count <= (uint64_t)FINISH_CAP) return;
   block_pick(cnt, mass, ctl, p);  // ends with a block barrier
@@ -782,7 +790,7 @@ __global__ void __launch_bounds__(PICK_THREADS) k_select_pick(Ctl* ctl, uint32_t
 }
 
 void launch_select_pick(Ctl* ctl, const SelectScratch& ss, double p, cudaStream_t st) {
-  k_select_pick<<<1, PICK_THREADS, 0, st>>>(ctl, ss.hist_count, ss.hist_mass, p);
+  launch_pdl(k_select_pick, 1, PICK_THREADS, 0, st, ctl, ss.hist_count, ss.hist_mass, p);
 }
 
 // ---------------------------------------------------------------- gather + finish
@@ -791,6 +799,7 @@ __global__ void __launch_bounds__(256) k_select_compact(const uint64_t* __restri
                                                         const uint64_t* __restrict__ wp,
                                                         const uint32_t* __restrict__ wi, Ctl* ctl,
                                                         uint64_t* __restrict__ buf) {
+  pdl_prologue();
   if (ctl->sel_done) return;
   if (ctl->sel_gated && ctl->sel_bin_count > (uint64_t)FINISH_CAP) return;  // more levels first
   const bool win = ctl->use_window != 0;
@@ -818,11 +827,12 @@ void launch_select_compact(const uint64_t* probs, const uint64_t* keys, uint64_t
   if (n == 0) return;
   uint64_t blocks = (n + 255) / 256;
   if (blocks > 148 * 4) blocks = 148 * 4;
-  k_select_compact<<<(unsigned)blocks, 256, 0, st>>>(probs, keys, n, ss.win_p, ss.win_i, ctl, ss.buf);
+  launch_pdl(k_select_compact, (unsigned)blocks, 256, 0, st, probs, keys, n, ss.win_p, ss.win_i, ctl, ss.buf);
 }
 
 __global__ void __launch_bounds__(PICK_THREADS) k_select_finish(Ctl* ctl, const uint64_t* buf,
                                                                 double p) {
+  pdl_prologue();
   __shared__ uint32_t s_cnt[SEL_BINS];
   __shared__ uint64_t s_mass[2 * SEL_BINS];
   const bool gated = ctl->sel_gated != 0;
@@ -884,7 +894,7 @@ __global__ void __launch_bounds__(PICK_THREADS) k_select_finish(Ctl* ctl, const 
 }
 
 void launch_select_finish(Ctl* ctl, const SelectScratch& ss, double p, cudaStream_t st) {
-  k_select_finish<<<1, PICK_THREADS, 0, st>>>(ctl, ss.buf, p);
+  launch_pdl(k_select_finish, 1, PICK_THREADS, 0, st, ctl, ss.buf, p);
 }
 
 // ---------------------------------------------------------------- peak partials
@@ -951,6 +961,7 @@ __device__ void block_peak_write(uint64_t bp, uint64_t bk, uint64_t* out) {
 
 // Reduce the partials of the last compaction (n blocks) into ctl->peak_z_*.
 __global__ void __launch_bounds__(256) k_peak_partials(const uint64_t* __restrict__ part, uint32_t n, Ctl* ctl) {
+  pdl_prologue();
   uint64_t bp = 0, bk = ~0ull;
   for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) peak_take(bp, bk, part[2 * i], part[2 * i + 1]);
   __shared__ uint64_t out[2];
@@ -962,16 +973,17 @@ __global__ void __launch_bounds__(256) k_peak_partials(const uint64_t* __restric
 }
 
 void launch_peak_partials(const uint64_t* part, uint32_t n, Ctl* ctl, cudaStream_t st) {
-  k_peak_partials<<<1, 256, 0, st>>>(part, n, ctl);
+  launch_pdl(k_peak_partials, 1, 256, 0, st, part, n, ctl);
 }
 
 // ---------------------------------------------------------------- compaction
 __global__ void k_set_scale(Ctl* ctl) {
+  pdl_prologue();
   double sc = fx_to_double(make_u128(ctl->cut_mass_hi, ctl->cut_mass_lo));
   ctl->scale = __ddiv_rn(1.0, __dsqrt_rn(sc));
 }
 
-void launch_set_scale(Ctl* ctl, cudaStream_t st) { k_set_scale<<<1, 1, 0, st>>>(ctl); }
+void launch_set_scale(Ctl* ctl, cudaStream_t st) { launch_pdl(k_set_scale, 1, 1, 0, st, ctl); }
 
 constexpr int TC_BLOCK = 256, TC_ITEMS = 8;
 
@@ -1039,6 +1051,7 @@ __global__ void __launch_bounds__(WP_BLOCK) k_truncate_write(
     const uint64_t* __restrict__ keys, const C2* __restrict__ amps, const uint32_t* __restrict__ keep_bits,
     uint64_t n, const uint64_t* __restrict__ tile_off, uint64_t* __restrict__ keys_out,
     C2* __restrict__ amps_out, uint64_t* __restrict__ probs_out, const Ctl* ctl, uint64_t* __restrict__ peak_part) {
+  pdl_prologue();
   typedef TileLayout<WP_BLOCK, WP_ITEMS> L;
   __shared__ CompactShared<WP_BLOCK> cs;
   __shared__ uint16_t s_list[WP_TILE];
@@ -1106,20 +1119,18 @@ void launch_truncate_windowed(int prec, const uint64_t* keys, const void* amps, 
                               uint32_t* peak_blocks) {
   (void)probs;  // the keep flags replace the probabilities here
   const uint64_t tiles = window_tiles(n);
-  k_set_scale<<<1, 1, 0, st>>>(ctl);
-  k_window_tile_counts<<<148 * 4, 256, 0, st>>>(ss.win_p, keys, ss.win_i, ctl, ss.tile_keep, ss.keep_bits);
-  k_tile_scan<<<1, 1024, 0, st>>>(ss.tile_keep, tiles, ss.tile_off, ctl);
+  launch_pdl(k_set_scale, 1, 1, 0, st, ctl);
+  launch_pdl(k_window_tile_counts, 148 * 4, 256, 0, st, ss.win_p, keys, ss.win_i, ctl, ss.tile_keep, ss.keep_bits);
+  launch_pdl(k_tile_scan, 1, 1024, 0, st, ss.tile_keep, tiles, ss.tile_off, ctl);
   uint64_t grid = tiles < PEAK_PARTS ? tiles : PEAK_PARTS;
   if (grid == 0) grid = 1;
   *peak_blocks = (uint32_t)grid;
   if (prec == 0)
-    k_truncate_write<double2><<<(unsigned)grid, WP_BLOCK, 0, st>>>(
-        keys, (const double2*)amps, ss.keep_bits, n, ss.tile_off, keys_out, (double2*)amps_out, probs_out, ctl,
-        peak_part);
+    launch_pdl(k_truncate_write<double2>, (unsigned)grid, WP_BLOCK, 0, st, keys, (const double2*)amps, ss.keep_bits,
+               n, ss.tile_off, keys_out, (double2*)amps_out, probs_out, ctl, peak_part);
   else
-    k_truncate_write<float2><<<(unsigned)grid, WP_BLOCK, 0, st>>>(
-        keys, (const float2*)amps, ss.keep_bits, n, ss.tile_off, keys_out, (float2*)amps_out, probs_out, ctl,
-        peak_part);
+    launch_pdl(k_truncate_write<float2>, (unsigned)grid, WP_BLOCK, 0, st, keys, (const float2*)amps, ss.keep_bits,
+               n, ss.tile_off, keys_out, (float2*)amps_out, probs_out, ctl, peak_part);
 }
 
 void launch_truncate_compact(int prec, const uint64_t* keys, const void* amps, const uint64_t* probs,
