@@ -206,7 +206,6 @@ def run_ours(args, rank, world):
             gi += 1
         torch.cuda.synchronize(dev)
         barrier()
-        st.set_timing(True)
         totals = {"n_in": 0, "n_pre": 0, "n_kept": 0, "select_levels": 0, "steps": steps,
                   "sort_passes": 0, "window_hits": 0, "window_terms": 0,
                   # per gate path: the sorted path (sort + group mat-vec) or the bucket-local kernel
@@ -261,9 +260,20 @@ def run_ours(args, rank, world):
         launches = sv.sv_launch_count() - l0
         ms = e0.elapsed_time(e1)
         clk = clocks.stop() if clocks else None
-        phases = st.phase_times()
         barrier()
         rate, units_all, ms = whole_job_rate(totals["n_in"], ms)
+        # the per-phase breakdown: as many more steps with CUDA events around
+        # every phase (kept out of the timed loop above: the events sit
+        # between kernels of a step and cost time of their own)
+        st.set_timing(True)
+        for _ in range(steps):
+            q, u = gates[gi % len(gates)]
+            gi += 1
+            st.apply_gate(q, u)
+            st.truncate()
+            st.peak_wait(st.peak_async())
+        torch.cuda.synchronize(dev)
+        phases = st.phase_times()
         peak = st.peak()
         fin = st.stats()
         paths = {k: fin[k] for k in ("local_gates", "global_gates", "local_fallbacks")}
