@@ -215,6 +215,8 @@ __global__ void __launch_bounds__(GS_BLOCK) k_group_scan(const uint64_t* __restr
   }
 }
 
+uint64_t group_scan_lookback_words(uint64_t n) { return 2 * (n / GS_TILE + 2); }
+
 void launch_group_scan(const uint64_t* sk, uint64_t n, const GateParams& gp, uint32_t* heads, uint32_t* gmask,
                        uint64_t* ooff, uint64_t* lookback, Ctl* ctl, cudaStream_t st) {
   static bool attr_set = false;

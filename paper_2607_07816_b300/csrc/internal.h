@@ -153,10 +153,13 @@ void launch_group_heads(const uint64_t* sk, uint64_t n, int shift, uint32_t* hea
 // group's first output position (exclusive scan of popc(om)) in ooff, which
 // is left unwritten when U has no zero entry (group g then starts at g 2^m).
 // Group count in ctl->count[0], candidate count in ctl->count[1].  Uses
-// 2 * (n / 8192 + 2) lookback words, which, with ctl->tile_counter[0] and
-// ctl->count[0..1], must be zero on entry (GateReset).
+// group_scan_lookback_words(n) lookback words, which, with
+// ctl->tile_counter[0] and ctl->count[0..1], must be zero on entry
+// (GateReset).
 void launch_group_scan(const uint64_t* sk, uint64_t n, const GateParams& gp, uint32_t* heads, uint32_t* gmask,
                        uint64_t* ooff, uint64_t* lookback, Ctl* ctl, cudaStream_t st);
+// Look-back words launch_group_scan uses for n terms (both look-backs).
+uint64_t group_scan_lookback_words(uint64_t n);
 // Per-group mat-vec writing each structurally nonzero output at its
 // precomputed position; exact zeros are written as zero and counted in
 // ctl->count[3] (to be removed by launch_drop_zero_terms).  complex128 also

@@ -566,7 +566,7 @@ sv_status sv_apply_gate(sv_state* s, int m, const int* qubits, const double* U) 
   sv_status rc = ensure_state_cap(s, N << m);
   if (rc == SV_OK) rc = ensure_sort_cap(s, N);
   if (rc != SV_OK) return rc;
-  const uint64_t gs_words = 2 * (N / 8192 + 2);  // the group scan's two look-backs
+  const uint64_t gs_words = group_scan_lookback_words(N);  // the group scan's two look-backs
   if (gs_words > s->gs_lb_entries) {
     dev_free(s, s->gs_lb);
     s->gs_lb_entries = 0;
