@@ -419,18 +419,22 @@ __global__ void __launch_bounds__(WP_BLOCK, 4) k_window_pass(const uint64_t* __r
 #pragma unroll
     for (int j = 0; j < WP_ITEMS; ++j) pbv[j] = 32 * j < rem ? probs[e0 + 32 * j] : 0ull;  // all loads first
     uint32_t wmask = 0, run = 0, tile_above = 0;
+    if (LIGHT) {
+      // tile_above and run are warp-wide counts (the same in every lane);
+      // lane j keeps item j's keep-flag word (one flag per term above the
+      // window: kept whatever the exact cut; window terms kept by the cut are
+      // added later), stored once per warp
+      uint32_t kbits = 0;
 #pragma unroll
-    for (int j = 0; j < WP_ITEMS; ++j) {
-      const uint64_t pb = pbv[j];
-      const bool valid = 32 * j < rem;
-      const bool above = valid && pb > hi;
-      const bool inwin = valid && !above && pb >= lo;
-      if (LIGHT) {
+      for (int j = 0; j < WP_ITEMS; ++j) {
+        const uint64_t pb = pbv[j];
+        const bool valid = 32 * j < rem;
+        const bool above = valid && pb > hi;
+        const bool inwin = valid && !above && pb >= lo;
         const uint32_t ab = __ballot_sync(0xffffffffu, above);
-        if (above) {
-          ++tile_above;
-          s_aq[warp][(q_head + q_n + __popc(ab & lt)) & 63u] = pb;
-        }
+        if (lane == j) kbits = ab;
+        tile_above += (uint32_t)__popc(ab);
+        if (above) s_aq[warp][(q_head + q_n + __popc(ab & lt)) & 63u] = pb;
         q_n += __popc(ab);
         if (q_n >= 32) {  // a full warp of queued terms: one conversion each
           __syncwarp();
@@ -440,7 +444,18 @@ __global__ void __launch_bounds__(WP_BLOCK, 4) k_window_pass(const uint64_t* __r
           q_n -= 32;
         }
         if (inwin) wmask |= 1u << j;
-      } else {
+        run += __popc(__ballot_sync(0xffffffffu, inwin));
+      }
+      const uint64_t row0 = (base + (uint64_t)warp * 32 * WP_ITEMS) >> 5;
+      if (lane < WP_ITEMS && ((row0 + lane) << 5) < n) keep_bits[row0 + lane] = kbits;
+      if (lane == 0) above_c += tile_above;
+    } else {
+#pragma unroll
+      for (int j = 0; j < WP_ITEMS; ++j) {
+        const uint64_t pb = pbv[j];
+        const bool valid = 32 * j < rem;
+        const bool above = valid && pb > hi;
+        const bool inwin = valid && !above && pb >= lo;
         const u128 f = fx_from_bits(pb, &ctl->err);
         tot += f;
         if (above) {
@@ -451,16 +466,17 @@ __global__ void __launch_bounds__(WP_BLOCK, 4) k_window_pass(const uint64_t* __r
           win_m += f;
           wmask |= 1u << j;
         }
+        run += __popc(__ballot_sync(0xffffffffu, inwin));
+        // terms above the window are kept whatever the exact cut: one flag
+        // word per 32 consecutive terms (window terms kept by the cut are
+        // added later)
+        const uint32_t kb = __ballot_sync(0xffffffffu, above);
+        if (lane == 0 && 32 * j < rem) keep_bits[(e0 >> 5) + j] = kb;  // lane 0: e0 starts a 32-term row
       }
-      run += __popc(__ballot_sync(0xffffffffu, inwin));
-      // terms above the window are kept whatever the exact cut: one flag word
-      // per 32 consecutive terms (window terms kept by the cut are added later)
-      const uint32_t kb = __ballot_sync(0xffffffffu, above);
-      if (lane == 0 && 32 * j < rem) keep_bits[(e0 >> 5) + j] = kb;  // lane 0: e0 starts a 32-term row
-    }
-    above_c += tile_above;
+      above_c += tile_above;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) tile_above += __shfl_xor_sync(0xffffffffu, tile_above, o);
+      for (int o = 16; o > 0; o >>= 1) tile_above += __shfl_xor_sync(0xffffffffu, tile_above, o);
+    }
     if (lane == 0) {
       s_warp[warp] = run;
       s_above[warp] = tile_above;
