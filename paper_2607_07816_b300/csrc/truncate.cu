@@ -617,12 +617,23 @@ __global__ void k_window_tile_counts(const uint64_t* __restrict__ wp, const uint
   pdl_prologue();
   const uint64_t wn = ctl->win_n;
   const uint64_t pc = ctl->cut_pbits, kc = ctl->cut_key;
-  for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < wn;
-       j += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t pb = wp[j];
-    const uint32_t i = wi[j];
-    if (pb > pc || (pb == pc && natural_key(ctl->nat, keys[i]) <= kc)) {
-      atomicAdd(&tile_keep[i / WP_TILE], 1u);
+  const int lane = threadIdx.x & 31;
+  // warp-uniform loop: the window buffer is filled tile by tile per block,
+  // so a warp's kept terms mostly share a tile: one count atomic per tile
+  for (uint64_t b = blockIdx.x * (uint64_t)blockDim.x + (threadIdx.x & ~31u); b < wn;
+       b += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t j = b + lane;
+    bool kept = false;
+    uint32_t i = 0;
+    if (j < wn) {
+      const uint64_t pb = wp[j];
+      i = wi[j];
+      kept = pb > pc || (pb == pc && natural_key(ctl->nat, keys[i]) <= kc);
+    }
+    const uint32_t tile = kept ? i / WP_TILE : 0xffffffffu;
+    const uint32_t peers = __match_any_sync(0xffffffffu, tile);
+    if (kept) {
+      if (lane == __ffs(peers) - 1) atomicAdd(&tile_keep[tile], (uint32_t)__popc(peers));
       atomicOr(&keep_bits[i >> 5], 1u << (i & 31));
     }
   }
