@@ -874,7 +874,7 @@ sv_status sv_truncate(sv_state* s, uint64_t* kept, double* retained_fraction) {
         launch_truncate_windowed(s->prec, s->keys[s->cur], s->amps[s->cur], s->probs[s->cur], N,
                                  s->keys[alt], s->amps[alt], s->probs[alt], s->ss, s->ctl, s->st, s->peak_part,
                                  &s->peak_blocks);
-        launched(s, PH_COMPACT, 4);
+        launched(s, PH_COMPACT, 3);
       } else {
         launch_set_scale(s->ctl, s->st);
         launch_truncate_compact(s->prec, s->keys[s->cur], s->amps[s->cur], s->probs[s->cur], N,

@@ -641,6 +641,7 @@ __global__ void k_window_tile_counts(const uint64_t* __restrict__ wp, const uint
 
 // Exclusive scan of the per-tile kept counts by one block: each thread takes
 // 8 consecutive tiles per round (loads first), one block scan per round.
+// Thread 0 also sets the renormalisation scale 1/sqrt(S_c) of the cut.
 constexpr int TS_ITEMS = 8;
 __global__ void __launch_bounds__(1024) k_tile_scan(const uint32_t* __restrict__ tile_keep, uint64_t tiles,
                                                     uint64_t* __restrict__ tile_off, Ctl* ctl) {
@@ -648,7 +649,11 @@ __global__ void __launch_bounds__(1024) k_tile_scan(const uint32_t* __restrict__
   __shared__ uint64_t wsum[32];
   __shared__ uint64_t s_carry;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (threadIdx.x == 0) s_carry = 0;
+  if (threadIdx.x == 0) {
+    s_carry = 0;
+    const double sc = fx_to_double(make_u128(ctl->cut_mass_hi, ctl->cut_mass_lo));
+    ctl->scale = __ddiv_rn(1.0, __dsqrt_rn(sc));
+  }
   __syncthreads();
   for (uint64_t b0 = 0; b0 < tiles; b0 += 1024 * TS_ITEMS) {
     const uint64_t t0 = b0 + (uint64_t)threadIdx.x * TS_ITEMS;
@@ -1146,7 +1151,6 @@ void launch_truncate_windowed(int prec, const uint64_t* keys, const void* amps, 
                               uint32_t* peak_blocks) {
   (void)probs;  // the keep flags replace the probabilities here
   const uint64_t tiles = window_tiles(n);
-  launch_pdl(k_set_scale, 1, 1, 0, st, ctl);
   launch_pdl(k_window_tile_counts, 148 * 4, 256, 0, st, ss.win_p, keys, ss.win_i, ctl, ss.tile_keep, ss.keep_bits);
   launch_pdl(k_tile_scan, 1, 1024, 0, st, ss.tile_keep, tiles, ss.tile_off, ctl);
   uint64_t grid = tiles < PEAK_PARTS ? tiles : PEAK_PARTS;
