@@ -41,8 +41,14 @@ __device__ __forceinline__ void f32_split_norm(float x, uint32_t* m, int* e) {
 }
 
 // Exact float -> double by bit manipulation (no conversion instruction).
+// Normal floats (the usual case) move their exponent from bias 127 to 1023
+// and their significand up by 29 bits in one add and one shift; zeros and
+// subnormals take the general path below.
 __device__ __forceinline__ double f32_to_f64_bits(float x) {
   const uint32_t b = __float_as_uint(x);
+  if (((b >> 23) & 0xffu) != 0u && ((b >> 23) & 0xffu) != 0xffu)
+    return __longlong_as_double((long long)(((uint64_t)(b & 0x80000000u) << 32) |
+                                            (((uint64_t)(b & 0x7fffffffu) + (896ull << 23)) << 29)));
   const uint64_t sign = (uint64_t)(b >> 31) << 63;
   uint32_t m;
   int e;
