@@ -656,6 +656,28 @@ __global__ void __launch_bounds__(256) k_segsel_finish(const uint64_t* __restric
     __syncthreads();
     if (st.done) break;
     const int bits = (int)st.bits;
+    if (st.bin_count == 1) {
+      // one term left under the prefix: it is the cut, the terms before it
+      // are those counted so far (or the target is never reached)
+      for (uint32_t i = tid; i < nb; i += blockDim.x) {
+        if (!z_matches(bhi[i], blo[i], st.prefix_hi, st.prefix_lo, bits)) continue;
+        const uint64_t cc = st.before_count + 1;
+        if (cc < st.target) {
+          st.done = 2;
+          continue;
+        }
+        const uint64_t pbits = ~bhi[i];
+        const u128 sc = make_u128(st.before_mass_hi, st.before_mass_lo) + fx_from_bits(pbits, err);
+        st.cut_pbits = pbits;
+        st.cut_key = blo[i];
+        st.cut_count = cc;
+        st.cut_mass_hi = (uint64_t)(sc >> 64);
+        st.cut_mass_lo = (uint64_t)sc;
+        st.done = 1;
+      }
+      __syncthreads();
+      if (st.done) break;
+    }
     int D, shift;
     sel_digit(bits, &D, &shift);
     for (int b = tid; b < SS_BINS; b += blockDim.x) {
