@@ -67,6 +67,7 @@ __global__ void __launch_bounds__(256) k_store_tables(const GateTables t, GateTa
   if (blockIdx.x == 0 && threadIdx.x < 16) r.part_hist[threadIdx.x] = 0u;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     r.ctl->tile_counter[0] = 0;
+    r.ctl->tile_counter[1] = 0;
     for (int i = 0; i < 4; ++i) r.ctl->count[i] = 0;
     r.ctl->total_mass_hi = r.ctl->total_mass_lo = 0;
   }

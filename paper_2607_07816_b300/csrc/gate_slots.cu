@@ -305,7 +305,12 @@ __global__ void __launch_bounds__(AS_BLOCK) k_gate_apply_slots(
   // truncation's window pass then needs no per-term mass for a top-K cut)
   constexpr bool MASS = sizeof(Real) == 8;
   u128 tot = 0;
-  for (uint64_t wb = (uint64_t)blockIdx.x * AS_WARPS + warp; wb * gc < G; wb += (uint64_t)gridDim.x * AS_WARPS) {
+  // batches are taken from a counter (ctl->tile_counter[1], cleared with the
+  // gate's tables): warps whose groups have more members take fewer batches
+  uint64_t wb = 0;
+  if (lane == 0) wb = atomicAdd((unsigned long long*)&ctl->tile_counter[1], 1ull);
+  wb = __shfl_sync(0xffffffffu, wb, 0);
+  for (; wb * gc < G;) {
     // group j = 32 k + lane of the batch; all group loads first
     uint32_t s[GPL], c[GPL], pos[GPL], h[GPL], gmv[GPL];
     uint64_t ob[GPL];
@@ -450,6 +455,8 @@ __global__ void __launch_bounds__(AS_BLOCK) k_gate_apply_slots(
       zeros += (uint32_t)__popc(__ballot_sync(0xffffffffu, z));
     }
     __syncwarp();
+    if (lane == 0) wb = atomicAdd((unsigned long long*)&ctl->tile_counter[1], 1ull);
+    wb = __shfl_sync(0xffffffffu, wb, 0);
   }
   if (lane == 0 && zeros) atomicAdd((unsigned long long*)&ctl->count[3], (unsigned long long)zeros);
   if (MASS) {

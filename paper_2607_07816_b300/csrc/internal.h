@@ -77,7 +77,7 @@ struct GateTables {
 };
 
 // Per-gate counters cleared by the table upload of a gate on the global path
-// (one launch instead of a memset per counter): ctl->tile_counter[0],
+// (one launch instead of a memset per counter): ctl->tile_counter[0..1],
 // ctl->count[0..3], the total mass, the 16 partition totals of the
 // regrouping and the group scan's look-back words.  ctl == nullptr: none.
 struct GateReset {
@@ -164,7 +164,8 @@ uint64_t group_scan_lookback_words(uint64_t n);
 // precomputed position; exact zeros are written as zero and counted in
 // ctl->count[3] (to be removed by launch_drop_zero_terms).  complex128 also
 // sums the candidates' exact fixed-point total mass into ctl->total_mass.
-// ctl->count[3] and the total mass must be zero on entry (GateReset).
+// ctl->count[3], the total mass and ctl->tile_counter[1] (the batch counter)
+// must be zero on entry (GateReset).
 void launch_gate_apply_slots(int prec, const uint64_t* sk, const uint32_t* sidx, uint64_t n, const uint32_t* heads,
                              const uint32_t* gmask, const uint64_t* ooff, const void* amps_in, const GateParams& gp,
                              uint64_t* keys_out, void* amps_out, uint64_t* probs_out, Ctl* ctl, cudaStream_t st);
