@@ -235,14 +235,15 @@ void launch_group_scan(const uint64_t* sk, uint64_t n, const GateParams& gp, uin
 
 // A warp takes a batch of 32 * gpl groups.  Larger batches leave fewer
 // rounds whose lanes run chains of different lengths; smaller ones leave
-// room for more warps per SM (measured best: gpl = 4 for complex64 and 2
-// for complex128, which is bound by the FP64 pipe, while 32 * gpl * 2^m
-// stays at most 512).  A batch holds at most 32 * gpl * 2^m members and
-// output slots.
+// room for more warps per SM and, with batches taken from a counter, balance
+// better (measured at m = 2: gpl = 2 for both precisions, against 4 and 1
+// for complex64 and 1 for complex128, which is bound by the FP64 pipe; the
+// batch halves again above m = 2).  A batch holds at most 32 * gpl * 2^m
+// members and output slots.
 constexpr int AS_WARPS = 8, AS_BLOCK = AS_WARPS * 32;
 
 __host__ __device__ __forceinline__ int slots_gpl(int prec, int m) {
-  return prec == 0 ? (m <= 3 ? 2 : 1) : (m <= 2 ? 4 : (m == 3 ? 2 : 1));
+  return prec == 0 ? (m <= 3 ? 2 : 1) : (m <= 2 ? 2 : 1);
 }
 
 // Per-warp shared layout of a batch of GC = 32 * gpl groups and MC = GC * 2^m
