@@ -487,7 +487,7 @@ void launch_gate_apply_slots(int prec, const uint64_t* sk, const uint32_t* sidx,
       if (per_sm < 1) per_sm = 1;                                                                             \
     }                                                                                                         \
     if (grid > 148ull * per_sm) grid = 148ull * per_sm;                                                       \
-    /* an ordinary launch: scheduled early behind the group scan, the mat-vec ran slower (measured) */        \
+    /* ordinary launch: scheduled early behind the group scan it ran slower with static batches, no faster now */ \
     k_gate_apply_slots<R, GPLV><<<(unsigned)grid, AS_BLOCK, smem, st>>>(sk, sidx, heads, gmask, ooff,           \
                                                                         (const C2*)amps_in, gp, keys_out,        \
                                                                         (C2*)amps_out, probs_out, ctl);          \
