@@ -191,6 +191,12 @@ def test_pipelined_peak_readout_matches_oracle_gate_by_gate(sv, oracle_mod):
     with pytest.raises(sv.SVError) as e:
         g.peak_wait(tickets[-1] + 1)
     assert e.value.status == sv.SV_E_ARG
+    # the handle stays usable, and an emptied state has no peak to enqueue
+    assert g.peak_wait(g.peak_async()) == expected[-1]
+    g.load(np.zeros(0, dtype=np.uint64), np.zeros(0))
+    with pytest.raises(sv.SVError) as e:
+        g.peak_async()
+    assert e.value.status == sv.SV_E_STATE
 
 
 def test_complex64_close_to_complex128(sv, oracle_mod):
