@@ -363,3 +363,166 @@ def test_golden_closed_forms(oracle_mod):
         psi = dense_run(case["n"], gates)
         for k in range(1 << case["n"]):
             assert abs(psi[k] - want.get(k, 0.0)) < 1e-15, case["name"]
+
+
+# ------------------------------------------------------------ complex64 form
+def rn32(x: Fraction) -> float:
+    """Round an exact rational to the nearest binary32 value (ties to even,
+    gradual underflow), returned as the (exactly equal) double."""
+    if x == 0:
+        return 0.0
+    sign = -1.0 if x < 0 else 1.0
+    a = abs(x)
+    e = a.numerator.bit_length() - a.denominator.bit_length()
+    if Fraction(2) ** e > a:
+        e -= 1
+    q = max(e - 23, -149)                  # quantum: 24-bit significand, subnormals below 2^-126
+    scaled = a / Fraction(2) ** q
+    n = scaled.numerator // scaled.denominator
+    rem = scaled - n
+    if rem > Fraction(1, 2) or (rem == Fraction(1, 2) and n % 2 == 1):
+        n += 1
+    v = Fraction(n) * Fraction(2) ** q
+    assert v < Fraction(2) ** 128, "binary32 overflow"
+    return sign * float(v)
+
+
+def test_rn32_agrees_with_numpy_on_doubles():
+    # a double rounds to binary32 once, so numpy's conversion is the reference here
+    rng = np.random.default_rng(31)
+    vals = list(rng.standard_normal(300) * 10.0 ** rng.uniform(-40, 30, size=300))
+    vals += [1.0 + 2.0 ** -24, 1.0 + 3 * 2.0 ** -24, 2.0 ** -149 * 1.5, 2.0 ** -150, 2.0 ** -127 * 3]
+    for v in vals:
+        assert rn32(Fraction(v)) == float(np.float32(v)), v
+
+
+def _float_state(rng, n, count, ties):
+    keys, amps = C.random_state(n, count, rng, ties=ties)
+    return keys, amps.astype(np.complex64).astype(np.complex128)
+
+
+def brute_apply_c64(keys, amps, qubits, u):
+    """One gate in the complex64 form by brute force with exact rationals:
+    per output, an accumulator from zero over the present inputs in
+    ascending local index, each step one complex multiply-accumulate whose
+    four real fused multiply-adds are evaluated exactly and rounded to
+    binary32 (U rounded to binary32 first); exact zeros dropped."""
+    m = len(qubits)
+    d = 1 << m
+    qmask = sum(1 << q for q in qubits)
+    groups = {}
+    for k, a in zip(keys.tolist(), amps):
+        r = sum(((k >> q) & 1) << t for t, q in enumerate(qubits))
+        groups.setdefault(k & ~qmask, {})[r] = a
+    uf = [[(Fraction(rn32(Fraction(float(u[ro, ri].real)))), Fraction(rn32(Fraction(float(u[ro, ri].imag)))))
+           for ri in range(d)] for ro in range(d)]
+    out = {}
+    for rest, mem in groups.items():
+        for ro in range(d):
+            re = im = Fraction(0)
+            for ri in sorted(mem):
+                ur, ui = uf[ro][ri]
+                ar, ai = Fraction(float(mem[ri].real)), Fraction(float(mem[ri].imag))
+                re = Fraction(rn32(ur * ar + re))
+                re = Fraction(rn32(-ui * ai + re))
+                im = Fraction(rn32(ur * ai + im))
+                im = Fraction(rn32(ui * ar + im))
+            if re == 0 and im == 0:
+                continue
+            key = rest | sum(((ro >> t) & 1) << q for t, q in enumerate(qubits))
+            out[key] = complex(float(re), float(im))
+    return out
+
+
+@pytest.mark.parametrize("case", range(6))
+def test_complex64_apply_matches_exact_float_brute_force(oracle_mod, case):
+    rng = np.random.default_rng(3100 + case)
+    n = 7
+    keys, amps = _float_state(rng, n, int(rng.integers(5, 60)), ties=False)
+    o = oracle_mod.Oracle(n, prec=oracle_mod.C64)
+    o.load(keys, amps)
+    for step in range(3):
+        m = int(rng.integers(1, 5))
+        q, u = C.random_gate(n, m, rng, str(rng.choice(["haar", "mcx"])))
+        k0, a0, _ = o.export()
+        want = brute_apply_c64(k0, a0, q, u)
+        o.apply_gate(q, u)
+        k1, a1, _ = o.export()
+        got = {int(k): a for k, a in zip(k1, a1)}
+        assert got.keys() == want.keys(), (case, step)
+        for k in want:
+            assert got[k] == want[k], (case, step, k)
+
+
+@pytest.mark.parametrize("case", range(40))
+def test_complex64_truncation_matches_brute_force(oracle_mod, case):
+    """The complex64 branch of the Sec. III rule: probabilities of the widened
+    components, the same exact masses, and each kept component rescaled as
+    float(double(x) * s)."""
+    rng = np.random.default_rng(2000 + case)
+    n = int(rng.integers(3, 9))
+    count = int(rng.integers(1, min(60, 1 << n) + 1))
+    keys, amps = _float_state(rng, n, count, ties=True)
+    K = int(rng.integers(1, count + 3))
+    p = float(rng.choice([1.0, 0.5, 0.9, 0.99, 0.3, 1e-9, rng.random()]))
+    o = oracle_mod.Oracle(n, K, p, prec=oracle_mod.C64)
+    o.load(keys, amps)
+    kept, f = o.truncate()
+    want, c, wf = brute_truncate(keys, amps, K, p, prec=1)
+    assert kept == c == len(want)
+    assert f == wf
+    k2, a2, _ = o.export()
+    got = {int(k): a for k, a in zip(k2, a2)}
+    assert got.keys() == want.keys()
+    for k in got:
+        assert got[k] == want[k]
+        assert float(np.float32(got[k].real)) == got[k].real
+
+
+def test_complex64_p_cut_lands_exactly_on_prefix_sum(oracle_mod):
+    keys = np.array([5, 9, 2, 7, 11], dtype=np.uint64)
+    amps = np.array([0.5 + 0.5j, 0.5, 0.25 + 0.25j, -0.25 + 0.25j, 0.1 + 0.2j]).astype(np.complex64)
+    amps = amps.astype(np.complex128)
+    for p in [0.5, 0.75, 0.875, 0.999, 1e-300]:
+        for K in [1, 2, 100]:
+            o = oracle_mod.Oracle(4, K, p, prec=oracle_mod.C64)
+            o.load(keys, amps)
+            kept, f = o.truncate()
+            want, c, wf = brute_truncate(keys, amps, K, p, prec=1)
+            assert (kept, f) == (c, wf), (p, K)
+            k2, a2, _ = o.export()
+            assert {int(k): a for k, a in zip(k2, a2)} == want
+
+
+# ------------------------------------------------------------ peak tie-break
+@pytest.mark.parametrize("prec", [0, 1])
+def test_peak_breaks_exact_ties_by_smallest_key(oracle_mod, prec):
+    """Sec. V readout in canonical order: among terms of equal largest
+    probability the smallest key wins, also when smaller keys of lower
+    probability come first in key order and when the tied amplitudes differ
+    (a, -a, i a and conj(a) have the same probability)."""
+    rng = np.random.default_rng(4000 + prec)
+    for trial in range(30):
+        n = 12
+        count = int(rng.integers(4, 200))
+        keys = rng.choice(1 << n, size=count, replace=False).astype(np.uint64)
+        amps = (rng.standard_normal(count) + 1j * rng.standard_normal(count)) * 0.05
+        top = complex(0.6, 0.3) if trial % 2 else complex(0.7, 0.0)
+        ties = int(rng.integers(2, min(6, count) + 1))
+        # the tied terms sit at the larger keys: lower-probability terms come first in key order
+        order = np.argsort(keys)
+        tied = order[-ties:]
+        variants = [top, -top, 1j * top, top.conjugate(), -1j * top.conjugate()]
+        for j, i in enumerate(tied):
+            amps[i] = variants[j % len(variants)]
+        if prec == 1:
+            amps = amps.astype(np.complex64).astype(np.complex128)
+        probs = [rn(Fraction(float(a.real)) ** 2 + Fraction(rn(Fraction(float(a.imag)) ** 2))) for a in amps]
+        pmax = max(probs)
+        want_key = min(int(k) for k, pr in zip(keys, probs) if pr == pmax)
+        assert sum(pr == pmax for pr in probs) >= 2
+        o = oracle_mod.Oracle(n, prec=prec)
+        o.load(keys, amps)
+        assert o.peak() == (want_key, pmax), trial
+        k0, _, p0 = o.export()
+        assert (int(k0[0]), p0[0]) == (want_key, pmax)
