@@ -74,7 +74,10 @@ typedef struct {
 sv_status sv_create(int n, uint64_t K, double p, sv_state** out);
 
 /* As sv_create with an amplitude precision (sv_prec), a cudaStream_t (NULL =
- * legacy default stream) and an allocator (NULL = cudaMalloc). */
+ * legacy default stream) and an allocator (NULL = cudaMalloc).  The first
+ * handle created on a device sets the kernels' shared-memory limits there
+ * (once per device; SV_E_CUDA if that fails).  A handle's calls must run
+ * with the device it was created on current. */
 sv_status sv_create_ex(int n, uint64_t K, double p, int prec, void* cuda_stream,
                        const sv_allocator* alloc, sv_state** out);
 
@@ -170,6 +173,15 @@ sv_status sv_last_stats(const sv_state* s, sv_stats* out);
 #define SV_NUM_PHASES 10
 sv_status sv_set_timing(sv_state* s, int enable);
 sv_status sv_phase_times(const sv_state* s, double* ms, uint64_t* launches);
+
+/* FP64 pipe throughput on the current device (benchmarking hook): one
+ * launch of blocks_per_sm (1..32) blocks per SM, 256 threads each, every
+ * thread running 8 independent fused multiply-add chains of `iters` steps
+ * (no memory traffic), timed with CUDA events on the legacy default stream
+ * after a shorter warm-up launch.  *tflops receives 2 flops per fma over the
+ * elapsed time, *ms (nullable) the time.  SV_E_ARG for iters == 0 or a
+ * blocks_per_sm outside 1..32. */
+sv_status sv_probe_fp64(uint64_t iters, int blocks_per_sm, double* tflops, double* ms);
 
 /* Gate application variant for the handle's next gates.  0 (default)
  * group-first -- bring every partner group together with the gate bits at

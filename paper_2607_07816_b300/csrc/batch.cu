@@ -11,6 +11,7 @@
 // The arithmetic per group and the cut per segment are those of the single
 // state path, so each segment's result is the one it would get alone.
 #include "internal.h"
+#include "launch.cuh"
 #include "tile.cuh"
 #include "batch.h"
 #include "c64_exact.cuh"
@@ -783,20 +784,19 @@ __global__ void __launch_bounds__(256) k_segsel_finish(const uint64_t* __restric
 
 // Kernel attributes (dynamic shared memory) set once, outside any stream
 // capture.
-void batch_prepare() {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_segsel_finish, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(2 * sizeof(uint64_t) * SF_CAP));
-    attr_set = true;
-  }
-  sort_prepare();
+cudaError_t batch_prepare() {
+  static DeviceOnce once;
+  cudaError_t e = once.run([] {
+    return cudaFuncSetAttribute(k_segsel_finish, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(2 * sizeof(uint64_t) * SF_CAP));
+  });
+  return e == cudaSuccess ? sort_prepare() : e;
 }
 
 void launch_segsel_finish(const uint64_t* g_buf, const uint32_t* g_bufn, const uint64_t* g_sum, SegSel* sel,
                           int slots, uint32_t* err, cudaStream_t st) {
   const size_t smem = 2 * sizeof(uint64_t) * SF_CAP;
-  batch_prepare();
+  (void)batch_prepare();  // checked at the batch's creation; a launch without it fails loudly
   k_segsel_finish<<<slots, 256, smem, st>>>(g_buf, g_bufn, g_sum, sel, err);
 }
 

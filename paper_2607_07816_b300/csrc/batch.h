@@ -53,7 +53,7 @@ struct SegSel {
   double scale;
 };
 
-void batch_prepare();  // kernel attributes, before any stream capture
+cudaError_t batch_prepare();  // kernel attributes of this device, before any stream capture
 void launch_seg_keys(const uint64_t* keys, const uint16_t* seg, uint64_t n, const SegGate* gates, int shift,
                      uint64_t* sk, uint32_t* sidx, uint32_t* hist, int passes, cudaStream_t st);
 void launch_seg_heads(const uint64_t* sk, uint64_t n, int shift, const SegGate* gates, uint32_t* heads,

@@ -344,10 +344,13 @@ sv_status svb_create(int max_slots, int prec, void* cuda_stream, const sv_alloca
   *out = nullptr;
   if (max_slots < 1 || max_slots > 1023 || (prec != SV_C128 && prec != SV_C64)) return SV_E_ARG;
   if (alloc && (!alloc->alloc || !alloc->free)) return SV_E_ARG;
+  if (batch_prepare() != cudaSuccess) {  // kernel attributes of this device, before any capture
+    cudaGetLastError();
+    return SV_E_CUDA;
+  }
   svb_state* b = new svb_state();
   b->prec = prec;
   b->st = (cudaStream_t)cuda_stream;
-  batch_prepare();
   if (!b->st) {  // a stream of its own: the legacy default stream cannot be captured into graphs
     if (cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking) != cudaSuccess) {
       cudaGetLastError();

@@ -219,11 +219,7 @@ uint64_t group_scan_lookback_words(uint64_t n) { return 2 * (n / GS_TILE + 2); }
 
 void launch_group_scan(const uint64_t* sk, uint64_t n, const GateParams& gp, uint32_t* heads, uint32_t* gmask,
                        uint64_t* ooff, uint64_t* lookback, Ctl* ctl, cudaStream_t st) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_group_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GS_SMEM);
-    attr_set = true;
-  }
+  (void)slots_prepare();  // checked at the handle's creation; a launch without it fails loudly
   const uint64_t tiles = (n + GS_TILE - 1) / GS_TILE;
   // the look-back words, ctl->tile_counter[0] and ctl->count[0..1] arrive
   // cleared (the gate's table upload clears them)
@@ -466,6 +462,42 @@ __global__ void __launch_bounds__(AS_BLOCK) k_gate_apply_slots(
   }
 }
 
+// Resident blocks per SM of the slot mat-vec, by device, precision and m
+// (set by slots_prepare).
+int g_slots_occ[DeviceOnce::kMaxDevices][2][5];
+
+template <typename R, int GPLV, typename C2>
+cudaError_t slots_setup(int dev, int prec) {
+  // the largest batch of any m that uses this variant: 32 * GPLV groups, 512 members
+  cudaError_t e = cudaFuncSetAttribute(k_gate_apply_slots<R, GPLV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(AS_WARPS * SlotsLayout<C2>::bytes(32 * GPLV, 512)));
+  for (int m = 1; m <= 4 && e == cudaSuccess; ++m) {
+    if (slots_gpl(prec, m) != GPLV) continue;
+    const uint32_t gc = 32u * GPLV, mc = gc << m;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gate_apply_slots<R, GPLV>, AS_BLOCK,
+                                                      AS_WARPS * SlotsLayout<C2>::bytes(gc, mc));
+    g_slots_occ[dev][prec][m] = per_sm;
+  }
+  return e;
+}
+
+cudaError_t slots_prepare() {
+  static DeviceOnce once;
+  return once.run([] {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_group_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GS_SMEM);
+    if (e == cudaSuccess) e = slots_setup<double, 2, double2>(dev, 0);
+    if (e == cudaSuccess) e = slots_setup<double, 1, double2>(dev, 0);
+    if (e == cudaSuccess) e = slots_setup<float, 4, float2>(dev, 1);
+    if (e == cudaSuccess) e = slots_setup<float, 2, float2>(dev, 1);
+    if (e == cudaSuccess) e = slots_setup<float, 1, float2>(dev, 1);
+    return e;
+  });
+}
+
 void launch_gate_apply_slots(int prec, const uint64_t* sk, const uint32_t* sidx, uint64_t n, const uint32_t* heads,
                              const uint32_t* gmask, const uint64_t* ooff, const void* amps_in, const GateParams& gp,
                              uint64_t* keys_out, void* amps_out, uint64_t* probs_out, Ctl* ctl, cudaStream_t st) {
@@ -476,16 +508,13 @@ void launch_gate_apply_slots(int prec, const uint64_t* sk, const uint32_t* sidx,
   if (n == 0) return;
   const uint64_t batches = (n + gc - 1) / gc;  // groups <= n
   uint64_t grid = (batches + AS_WARPS - 1) / AS_WARPS;
-  static int occ[2][5] = {};  // resident blocks per SM, by precision and m
-  int& per_sm = occ[prec ? 1 : 0][gp.m];
+  (void)slots_prepare();  // checked at the handle's creation; a launch without it fails loudly
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= DeviceOnce::kMaxDevices) dev = 0;
+  int per_sm = g_slots_occ[dev][prec ? 1 : 0][gp.m];
+  if (per_sm < 1) per_sm = 1;
 #define SV_SLOTS(R, C2, GPLV)                                                                                 \
   do {                                                                                                        \
-    if (per_sm == 0) {                                                                                        \
-      cudaFuncSetAttribute(k_gate_apply_slots<R, GPLV>, cudaFuncAttributeMaxDynamicSharedMemorySize,          \
-                           (int)(AS_WARPS * SlotsLayout<C2>::bytes(32 * GPLV, 512)));                         \
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gate_apply_slots<R, GPLV>, AS_BLOCK, smem);    \
-      if (per_sm < 1) per_sm = 1;                                                                             \
-    }                                                                                                         \
     if (grid > 148ull * per_sm) grid = 148ull * per_sm;                                                       \
     /* ordinary launch: scheduled early behind the group scan it ran slower with static batches, no faster now */ \
     k_gate_apply_slots<R, GPLV><<<(unsigned)grid, AS_BLOCK, smem, st>>>(sk, sidx, heads, gmask, ooff,           \

@@ -40,7 +40,7 @@ void launch_digit_hist(const uint64_t* k, uint64_t n, int nbits, uint32_t* hist,
 // of key >> lo.  Returns the buffer holding the result (0: kA, 1: kB).
 int radix_sort_keys(uint64_t* kA, uint64_t* kB, uint64_t n, int lo, int nbits, const SortScratch& sc,
                     cudaStream_t st, int* passes_run, cudaError_t* cerr);
-void sort_prepare();
+cudaError_t sort_prepare();
 int radix_sort_pairs(uint64_t* kA, uint32_t* vA, uint64_t* kB, uint32_t* vB, uint64_t n, int nbits,
                      const SortScratch& sc, cudaStream_t st, int* passes_run, cudaError_t* cerr);
 
@@ -128,7 +128,12 @@ __device__ __forceinline__ uint64_t to_natural(const uint64_t* nat, uint64_t x) 
 // cleared beforehand: GateReset::part_hist).
 int regroup_terms(const uint64_t* keys, uint64_t n, const GateParams& gp, uint64_t* sk[2], uint32_t* sidx[2],
                   const SortScratch& sc, cudaStream_t st, int* launches, cudaError_t* cerr);
-void regroup_prepare();
+cudaError_t regroup_prepare();
+// Kernel attributes (dynamic shared-memory limits) and launch-shape tables
+// of this device, set once per device; the handles' creation checks them.
+cudaError_t slots_prepare();
+cudaError_t local_prepare();
+cudaError_t select_prepare();
 
 // Expand-first gate application (Sec. IV-A as the paper states it): records
 // (output sort key << m | source r, source index) for every term and output,

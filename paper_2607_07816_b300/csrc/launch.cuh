@@ -12,6 +12,7 @@
 
 #include <cuda_runtime.h>
 
+#include <mutex>
 #include <utility>
 
 namespace sv {
@@ -36,5 +37,29 @@ inline cudaError_t launch_pdl(void (*kernel)(P...), dim3 grid, dim3 block, size_
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
 }
+
+// One-time host set-up per device.  A kernel's attributes (its dynamic
+// shared-memory limit) belong to that kernel on one device, so they are set
+// once for every device the library runs on: run(f) calls f the first time
+// it is called with a given device current (thread-safe; concurrent callers
+// wait for the first) and returns the error f returned there, on that call
+// and on every later one with that device.
+class DeviceOnce {
+ public:
+  static constexpr int kMaxDevices = 64;
+  template <typename F>
+  cudaError_t run(F&& f) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::call_once(flag_[dev], [&] { err_[dev] = f(); });
+    return err_[dev];
+  }
+
+ private:
+  std::once_flag flag_[kMaxDevices];
+  cudaError_t err_[kMaxDevices] = {};
+};
 
 }  // namespace sv

@@ -18,6 +18,7 @@
 // fast or faster on this GPU.
 #include "c64_exact.cuh"
 #include "internal.h"
+#include "launch.cuh"
 #include "tile.cuh"
 
 namespace sv {
@@ -350,16 +351,21 @@ __global__ void __launch_bounds__(LG_THREADS, 1) k_local_gate(
   if (lane == 0 && max_bucket) atomicMax((unsigned long long*)&ctl->count[0], (unsigned long long)max_bucket);
 }
 
+cudaError_t local_prepare() {
+  static DeviceOnce once;
+  return once.run([] {
+    cudaError_t e = cudaFuncSetAttribute(k_local_gate<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(LocalSmem<double>));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_local_gate<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)sizeof(LocalSmem<float>));
+    return e;
+  });
+}
+
 void launch_local_gate(int prec, const uint64_t* keys, const void* amps, uint64_t n, const GateParams& gp,
                        uint64_t* keys_out, void* amps_out, uint64_t* probs_out, Ctl* ctl, cudaStream_t st) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_local_gate<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sizeof(LocalSmem<double>));
-    cudaFuncSetAttribute(k_local_gate<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sizeof(LocalSmem<float>));
-    attr_set = true;
-  }
+  (void)local_prepare();  // checked at the handle's creation; a launch without it fails loudly
   cudaMemsetAsync(&ctl->tile_counter[3], 0, sizeof(uint64_t), st);
   cudaMemsetAsync(&ctl->count[0], 0, sizeof(uint64_t) * 2, st);  // largest bucket, output count
   cudaMemsetAsync(&ctl->count[3], 0, sizeof(uint64_t), st);       // exact zeros

@@ -233,15 +233,16 @@ static size_t scatter_smem(bool pairs) { return (sizeof(uint64_t) + (pairs ? siz
 
 // Kernel attributes (dynamic shared memory) set once, outside any stream
 // capture.
-void sort_prepare() {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_tile_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)scatter_smem(true));
-    cudaFuncSetAttribute(k_tile_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)scatter_smem(false));
-    attr_set = true;
-  }
+cudaError_t sort_prepare() {
+  static DeviceOnce once;
+  return once.run([] {
+    cudaError_t e = cudaFuncSetAttribute(k_tile_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)scatter_smem(true));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_tile_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)scatter_smem(false));
+    return e;
+  });
 }
 
 // The passes of one sort: digits at lo + 8p for p < ceil(nbits / 8);
@@ -252,8 +253,11 @@ static int sort_passes(uint64_t* kA, uint32_t* vA, uint64_t* kB, uint32_t* vB, u
   const int passes = (nbits + RADIX_BITS - 1) / RADIX_BITS;
   const bool pairs = vA != nullptr;
   int cur = 0, run = 0;
-  *cerr = cudaSuccess;
-  sort_prepare();
+  *cerr = sort_prepare();
+  if (*cerr != cudaSuccess) {
+    *passes_run = 0;
+    return 0;
+  }
   const uint64_t tiles = sort_tiles(n);
   if (n > 1) {
     if (tiles > sc.lookback_tiles || n > 0xffffffffull) {

@@ -388,16 +388,16 @@ static size_t merge_smem(bool pairs) {
   return (sizeof(uint64_t) + (pairs ? sizeof(uint32_t) : 0)) * (size_t)mg_pad(MG_TILE);
 }
 
-void regroup_prepare() {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_part_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)part_smem(true));
-    cudaFuncSetAttribute(k_part_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)part_smem(false));
-    cudaFuncSetAttribute(k_merge_level<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)merge_smem(true));
-    cudaFuncSetAttribute(k_merge_level<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)merge_smem(false));
-    attr_set = true;
-  }
+cudaError_t regroup_prepare() {
+  static DeviceOnce once;
+  return once.run([] {
+    const int attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e = cudaFuncSetAttribute(k_part_scatter<true>, (cudaFuncAttribute)attr, (int)part_smem(true));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_part_scatter<false>, (cudaFuncAttribute)attr, (int)part_smem(false));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_merge_level<true>, (cudaFuncAttribute)attr, (int)merge_smem(true));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_merge_level<false>, (cudaFuncAttribute)attr, (int)merge_smem(false));
+    return e;
+  });
 }
 
 int regroup_terms(const uint64_t* keys, uint64_t n, const GateParams& gp, uint64_t* sk[2], uint32_t* sidx[2],
@@ -405,9 +405,9 @@ int regroup_terms(const uint64_t* keys, uint64_t n, const GateParams& gp, uint64
   const bool pairs = gp.vbits == 0;
   const int m = gp.m, D = 1 << m;
   const uint64_t tiles = (n + RG_TILE - 1) / RG_TILE;
-  *cerr = cudaSuccess;
   *launches = 0;
-  regroup_prepare();
+  *cerr = regroup_prepare();
+  if (*cerr != cudaSuccess) return 0;
   if (n == 0) return 0;
   if (tiles > sc.lookback_tiles || n > 0xffffffffull || m < 1 || m > 4) {
     *cerr = cudaErrorInvalidValue;

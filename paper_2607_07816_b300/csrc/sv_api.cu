@@ -413,6 +413,17 @@ sv_status sv_create_ex(int n, uint64_t K, double p, int prec, void* cuda_stream,
   if (n < 1 || n > 64 || K < 1 || !(p > 0.0) || !(p <= 1.0) || (prec != SV_C128 && prec != SV_C64))
     return SV_E_ARG;
   if (alloc && (!alloc->alloc || !alloc->free)) return SV_E_ARG;
+  {  // kernel attributes of the current device (once per device)
+    cudaError_t e = sort_prepare();
+    if (e == cudaSuccess) e = regroup_prepare();
+    if (e == cudaSuccess) e = slots_prepare();
+    if (e == cudaSuccess) e = local_prepare();
+    if (e == cudaSuccess) e = select_prepare();
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return SV_E_CUDA;
+    }
+  }
   sv_state* s = new sv_state();
   s->n = n;
   s->K = K;

@@ -583,16 +583,23 @@ __global__ void k_window_decide(Ctl* ctl, int mode, uint64_t count_target, doubl
   ctl->sel_bin_count = valid ? wn : n;
 }
 
+constexpr size_t SAMPLE_SMEM = 4 * (2 * SAMPLE_N + 32 * 256) + 8 * SAMPLE_THREADS;
+
+cudaError_t select_prepare() {
+  static DeviceOnce once;
+  return once.run([] {
+    return cudaFuncSetAttribute(k_sample_window, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SAMPLE_SMEM);
+  });
+}
+
 void launch_select_window(const uint64_t* probs, const uint64_t* keys, uint64_t n, Ctl* ctl,
                           const SelectScratch& ss, int mode, uint64_t count_target, double p,
                           bool have_total, cudaStream_t st) {
   const bool light = have_total && mode == 1;
-  static bool attr_set = false;
-  const size_t smem = 4 * (2 * SAMPLE_N + 32 * 256) + 8 * SAMPLE_THREADS;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_sample_window, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr_set = true;
-  }
+  const size_t smem = SAMPLE_SMEM;
+  // the handle's creation checked the set-up on this device; without it the
+  // launch fails and the next wait reports the launch error
+  (void)select_prepare();
   launch_pdl(k_sample_window, 1, SAMPLE_THREADS, smem, st, probs, n, ctl, mode, count_target, p, light);
   uint64_t tiles = (n + WP_TILE - 1) / WP_TILE;
   uint64_t grid = tiles < 148 * 8 ? tiles : 148 * 8;

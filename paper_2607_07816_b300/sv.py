@@ -27,7 +27,8 @@ EXPORTED = ["sv_create", "sv_create_ex", "sv_destroy", "sv_apply_gate", "sv_trun
             "sv_last_stats", "sv_set_timing", "sv_phase_times", "sv_launch_count", "sv_transfer_bytes", "sv_peak_noalloc",
             "svb_create", "svb_destroy", "svb_add", "svb_remove", "svb_step", "svb_num_terms",
             "svb_retained_mass", "svb_peak", "svb_export", "svb_last_error", "svb_set_autotune",
-            "svb_autotune_stats", "svb_set_graphs", "svb_graph_stats", "sv_selftest", "sv_set_apply_variant"]
+            "svb_autotune_stats", "svb_set_graphs", "svb_graph_stats", "sv_selftest", "sv_set_apply_variant",
+            "sv_probe_fp64"]
 PHASES = ["keys", "sort", "heads", "apply", "select", "compact", "peak", "other", "window", "local"]
 
 
@@ -146,6 +147,8 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.sv_set_apply_variant.argtypes = [vp, i32]
     lib.sv_selftest.restype = i32
     lib.sv_selftest.argtypes = [i32, u64, u64, P(u64), P(u64)]
+    lib.sv_probe_fp64.restype = i32
+    lib.sv_probe_fp64.argtypes = [u64, i32, P(dbl), P(dbl)]
     lib.sv_transfer_bytes.restype = None
     lib.sv_transfer_bytes.argtypes = [P(u64), P(u64)]
     _lib = lib
@@ -297,6 +300,15 @@ def sv_peak_noalloc(prec: int, keys_ptr: int, amps_ptr: int, n: int, stream: int
     if rc != SV_OK:
         raise SVError(rc, "sv_peak_noalloc failed")
     return k.value, p.value
+
+
+def sv_probe_fp64(iters: int = 1 << 16, blocks_per_sm: int = 4):
+    """FP64 fused multiply-add throughput of the current device: (TFLOP/s, ms)."""
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    rc = load_library().sv_probe_fp64(ctypes.c_uint64(iters), blocks_per_sm, ctypes.byref(tf), ctypes.byref(ms))
+    if rc != 0:
+        raise SVError(rc, "sv_probe_fp64 failed")
+    return tf.value, ms.value
 
 
 def sv_selftest(which: int, n: int, seed: int = 1):
