@@ -6,7 +6,9 @@ device-memory budget, or a point where an allocation would stall the
 device).  It works on the caller's own device arrays with a fixed scratch
 array inside the library.  This file is collected last on purpose.  It
 checks two calls in a row against sv_peak on the same states, through the
-C ABI, with the exact comparison the other parity tests use.
+C ABI, with the exact comparison the other parity tests use, and states
+large enough for several blocks (the cross-block reduction through the
+scratch array) with exact ties between blocks against the oracle.
 """
 import ctypes
 
@@ -54,6 +56,52 @@ def test_noalloc_peak_matches_sv_peak_on_two_calls(env, prec):
         dk, da = _device_copy(torch, keys, amps, prec)
         torch.cuda.synchronize()
         got = sv.sv_peak_noalloc(prec, dk.data_ptr(), da.data_ptr(), len(keys), stream)
+        assert got == want, (call, got, want)
+
+
+def _tied_state(rng, count, tie_pos, prec):
+    """count random terms; the largest probability is shared exactly by the
+    terms at array positions tie_pos (amplitudes a, -a, conj(a), i a, ...),
+    and the smallest of their keys sits at the last of those positions."""
+    keys = np.unique(rng.integers(0, 1 << 40, size=count + count // 8, dtype=np.uint64))[:count]
+    rng.shuffle(keys)
+    amps = (rng.standard_normal(count) + 1j * rng.standard_normal(count)) * 1e-3
+    top = complex(0.375, -0.25)
+    variants = [top, -top, top.conjugate(), 1j * top]
+    tied_keys = np.sort(keys[tie_pos])[::-1]          # descending: the smallest key goes last
+    keys[tie_pos] = tied_keys
+    for j, i in enumerate(tie_pos):
+        amps[i] = variants[j % len(variants)]
+    if prec == 1:
+        amps = amps.astype(np.complex64)
+    return keys, amps.astype(np.complex128), int(tied_keys[-1])
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_noalloc_peak_across_blocks_with_ties_matches_oracle(env, oracle_mod, prec):
+    """States of 196608 to 300000 terms span 3 to 5 blocks of 65536 terms,
+    so the per-block partials go through the shared scratch array and the
+    last block's reduction.  The largest probability is tied between terms
+    in different blocks with the smallest key in the last of them.  Two
+    calls in a row on different states; each result equals the oracle's
+    peak and sv_peak's on the same terms."""
+    sv, torch = env
+    rng = np.random.default_rng(4242 + prec)
+    stream = torch.cuda.current_stream().cuda_stream
+    cases = [(300_000, [70_000, 140_001, 299_999]), (3 * 65536 + 1, [5, 65536, 3 * 65536]),
+             (3 * 65536, [65535, 131072, 196607])]
+    for call, (count, tie_pos) in enumerate(cases):
+        keys, amps, want_key = _tied_state(rng, count, tie_pos, prec)
+        o = oracle_mod.Oracle(41, prec=prec)
+        o.load(keys, amps)
+        want = o.peak()
+        assert want[0] == want_key
+        st = sv.SparseState(41, prec=prec)
+        st.load(keys, amps)
+        assert st.peak() == want
+        dk, da = _device_copy(torch, keys, amps, prec)
+        torch.cuda.synchronize()
+        got = sv.sv_peak_noalloc(prec, dk.data_ptr(), da.data_ptr(), count, stream)
         assert got == want, (call, got, want)
 
 
