@@ -153,11 +153,13 @@ typedef struct {
   uint32_t select_levels;
   double total_mass, kept_mass;
   uint32_t window_hits;
-  uint32_t pad;
+  uint32_t selects;       /* select runs of the last truncation: top-k, then p-mass only when needed */
   uint64_t window_terms;
   uint64_t local_gates;   /* gates applied bucket-locally so far (no global sort) */
   uint64_t global_gates;  /* gates that needed the global sort so far */
   uint64_t local_fallbacks; /* local attempts redone globally (bucket too large) */
+  uint64_t diag_gates;    /* gates applied in place as diagonal matrices so far */
+  uint64_t mono_gates;    /* gates applied as permutations with phases (one output per term) so far */
 } sv_stats;
 sv_status sv_last_stats(const sv_state* s, sv_stats* out);
 
@@ -169,7 +171,8 @@ sv_status sv_last_stats(const sv_state* s, sv_stats* out);
  * 5 truncation compaction, 6 peak, 7 other (readout, load), 8 truncation
  * sample window pass, 9 bucket-local gate (and bucket-size check).  ms and
  * launches (nullable) receive SV_NUM_PHASES entries: milliseconds and kernel
- * launches. */
+ * launches.  sv_phase_times waits for the handle's stream first (with timing
+ * on), so phases still in flight are included. */
 #define SV_NUM_PHASES 10
 sv_status sv_set_timing(sv_state* s, int enable);
 sv_status sv_phase_times(const sv_state* s, double* ms, uint64_t* launches);

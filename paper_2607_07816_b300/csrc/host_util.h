@@ -86,6 +86,22 @@ inline bool is_unitary(int m, const double* U) {
 }
 
 // Nearest double to a 128-bit fixed-point mass (LSB 2^-120).
+// floor(v * 2^120) of a non-negative double, exactly: the fixed point of the
+// probability masses (the device kernels convert probabilities the same
+// way).  Zero for subnormal or negative input; values of 128 and above do
+// not fit and saturate.
+inline unsigned __int128 fx_from_double(double v) {
+  uint64_t b;
+  std::memcpy(&b, &v, sizeof(b));
+  const uint32_t e = (uint32_t)(b >> 52) & 0x7ffu;
+  if (e == 0 || (b >> 63)) return 0;
+  const uint64_t mant = (b & ((1ull << 52) - 1)) | (1ull << 52);
+  const int sh = (int)e - 955;  // v * 2^120 = mant * 2^(e - 1075 + 120)
+  if (sh >= 0) return sh > 74 ? ~(unsigned __int128)0 : ((unsigned __int128)mant) << sh;
+  if (sh <= -64) return 0;
+  return (unsigned __int128)(mant >> (-sh));
+}
+
 inline double u128_to_double(uint64_t hi, uint64_t lo) {
   unsigned __int128 v = ((unsigned __int128)hi << 64) | lo;
   return std::ldexp((double)v, -120);

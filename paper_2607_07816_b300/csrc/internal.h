@@ -107,7 +107,11 @@ struct GateParams {
   uint64_t pmask;      // bucket qubits as a key mask
   int vbits;           // > 0: sort keys carry the term index in their low vbits bits (no index array)
   int qpos[4];         // bit of qubits[t] in the stored keys before the gate
+  uint64_t rmap;       // nibble r: the digit the regrouping sorts a term with gate bits r under
+                       // (identity; a monomial gate's output index instead)
 };
+
+constexpr uint64_t RMAP_IDENTITY = 0xFEDCBA9876543210ull;
 
 // Natural key of a stored key, with the nibble table of GateTables::nat
 // (256 entries, in shared or global memory).
@@ -191,6 +195,38 @@ constexpr uint64_t LOCAL_BUCKET_MAX = LOCAL_CAP - LOCAL_CHUNK;
 void launch_local_gate(int prec, const uint64_t* keys, const void* amps, uint64_t n, const GateParams& gp,
                        uint64_t* keys_out, void* amps_out, uint64_t* probs_out, Ctl* ctl, cudaStream_t st);
 // Order-preserving removal of zero-amplitude terms (count in ctl->count[2]).
+// A diagonal gate applied in place (csrc/diag.cu): ur/ui[r] = U[r][r],
+// rnz/inz bit r set when its real / imaginary part is nonzero (complex64:
+// after rounding to float), qpos[t] the stored bit of qubits[t].  The term
+// order and keys are unchanged; amps and probs are overwritten, the exact
+// total mass is added into ctl->total_mass and exact zeros are counted in
+// ctl->count[3] (both must be zero on entry).
+struct DiagParams {
+  double ur[16], ui[16];
+  uint32_t rnz, inz;
+  int m;
+  int qpos[4];
+};
+void launch_diag_apply(int prec, const uint64_t* keys, void* amps, uint64_t* probs, uint64_t n, const DiagParams& dp,
+                       Ctl* ctl, cudaStream_t st);
+
+// A monomial gate (one nonzero per row and column: permutations with
+// phases, e.g. X, CNOT, Toffoli, C3X): the regrouping sorted the terms by
+// their output key (GateParams::rmap = the gate's output index of each r),
+// so output i is sk[i]'s term times its one matrix entry.  ur/ui[r'] =
+// U[r'][r] for the r mapped to r', rnz/inz bit r' set when nonzero (after
+// rounding to float for complex64).  Writes N outputs in order, the exact
+// total mass into ctl->total_mass and the exact zeros into ctl->count[3]
+// (both zero on entry).
+struct MonoParams {
+  double ur[16], ui[16];
+  uint32_t rnz, inz;
+  int m, vbits;
+};
+void launch_mono_apply(int prec, const uint64_t* sk, const uint32_t* sidx, uint64_t n, const void* amps_in,
+                       const MonoParams& mp, uint64_t* keys_out, void* amps_out, uint64_t* probs_out, Ctl* ctl,
+                       cudaStream_t st);
+
 void launch_drop_zero_terms(int prec, const uint64_t* keys, const void* amps, const uint64_t* probs,
                             uint64_t n, uint64_t* keys_out, void* amps_out, uint64_t* probs_out,
                             uint64_t* lookback, Ctl* ctl, cudaStream_t st);

@@ -51,9 +51,11 @@ __device__ __forceinline__ uint32_t gate_index_of(uint64_t key, const int* qpos,
 
 // The gate's sort key of a stored key: the bits at the positions in rem[]
 // (the gate qubits' stored positions, in descending order) are removed, the
-// rest shifts down over them and moves up by m, and r takes the bottom.
-__device__ __forceinline__ uint64_t sort_key_of(uint64_t key, const int* qpos, const int* rem, int m) {
-  const uint32_t r = gate_index_of(key, qpos, m);
+// rest shifts down over them and moves up by m, and the digit of r (r
+// itself, or a monomial gate's output index: rmap) takes the bottom.
+__device__ __forceinline__ uint64_t sort_key_of(uint64_t key, const int* qpos, const int* rem, int m,
+                                                uint64_t rmap) {
+  const uint32_t r = (uint32_t)(rmap >> (4 * gate_index_of(key, qpos, m))) & 15u;
   uint64_t x = key;
 #pragma unroll
   for (int t = 0; t < 4; ++t)
@@ -107,7 +109,7 @@ __global__ void __launch_bounds__(RG_THREADS) k_part_counts(const uint64_t* __re
 #pragma unroll
   for (int i = 0; i < RG_ITEMS; ++i) {
     const uint64_t idx = base + i * 32;
-    const uint32_t d = idx < n ? gate_index_of(k[i], q, m) : 16u;
+    const uint32_t d = idx < n ? (uint32_t)(gp.rmap >> (4 * gate_index_of(k[i], q, m))) & 15u : 16u;
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
     if (d < 16 && lane == __ffs(peers) - 1) atomicAdd(&h[d], (uint32_t)__popc(peers));
   }
@@ -152,7 +154,7 @@ __global__ void __launch_bounds__(RG_THREADS, 3) k_part_scatter(const uint64_t* 
   for (int i = 0; i < RG_ITEMS; ++i) {
     const uint64_t idx = base + i * 32;
     const bool valid = idx < n;
-    const uint64_t s = valid ? sort_key_of(keys[idx], qpos, rem, m) : 0ull;
+    const uint64_t s = valid ? sort_key_of(keys[idx], qpos, rem, m, gp.rmap) : 0ull;
     k[i] = vb ? ((s << vb) | idx) : s;
     d[i] = valid ? (uint32_t)(s & dmask) : 16u;
   }

@@ -535,6 +535,7 @@ sv_status sv_apply_gate(sv_state* s, int m, const int* qubits, const double* U) 
   GateParams gp;
   std::memset(&gp, 0, sizeof(gp));
   gp.m = m;
+  gp.rmap = RMAP_IDENTITY;
   gp.n_mask = s->n == 64 ? ~0ull : ((1ull << s->n) - 1);
   for (int t = 0; t < m; ++t) {
     if (qubits[t] < 0 || qubits[t] >= s->n) return fail(s, SV_E_ARG, "sv_apply_gate: qubit out of range");
@@ -563,6 +564,21 @@ sv_status sv_apply_gate(sv_state* s, int m, const int* qubits, const double* U) 
       if (rz) gp.re_nz[ro] |= 1u << r;
       if (iz) gp.im_nz[ro] |= 1u << r;
     }
+  // One nonzero per row and column (a permutation with phases): every term
+  // has one output, r -> pi(r), kept in nibble r of pi.
+  bool mono = true;
+  uint64_t pi = 0;
+  uint32_t cols_seen = 0;
+  for (int ro = 0; ro < d && mono; ++ro) {
+    const uint32_t row = gp.re_nz[ro] | gp.im_nz[ro];
+    const int r = row ? __builtin_ctz(row) : 0;
+    if (__builtin_popcount(row) != 1 || ((cols_seen >> r) & 1u)) {
+      mono = false;
+    } else {
+      cols_seen |= 1u << r;
+      pi |= (uint64_t)ro << (4 * r);
+    }
+  }
   const uint64_t N = s->N;
   s->peak_ready = false;
   s->total_ready = false;
@@ -586,6 +602,55 @@ sv_status sv_apply_gate(sv_state* s, int m, const int* qubits, const double* U) 
     s->gs_lb_entries = gs_words + gs_words / 2;
   }
   const int alt = 1 - s->cur;
+  for (int b = 0; b < s->n; ++b) s->order_next[b] = s->order[b];
+  // A diagonal U maps every term to itself (Eq. 3 with no off-diagonal
+  // entries): no grouping, the amplitudes are updated in place and the
+  // state keeps its order (default variant; the others regroup as always).
+  bool diag = s->variant == 0;
+  for (int ro = 0; ro < d && diag; ++ro)
+    if ((gp.re_nz[ro] | gp.im_nz[ro]) & ~(1u << ro)) diag = false;
+  if (diag) {
+    DiagParams dp;
+    std::memset(&dp, 0, sizeof(dp));
+    dp.m = m;
+    for (int t = 0; t < m; ++t) dp.qpos[t] = s->order[gp.q[t]];
+    for (int r = 0; r < d; ++r) {
+      dp.ur[r] = U[2 * (r * d + r)];
+      dp.ui[r] = U[2 * (r * d + r) + 1];
+      dp.rnz |= gp.re_nz[r] & (1u << r);
+      dp.inz |= gp.im_nz[r] & (1u << r);
+    }
+    ++s->global_gates;
+    ++s->stats.diag_gates;
+    // clears the gate's counters (zero count, total mass); no table to store
+    launch_store_tables(*s->tab_host, s->tab_dev, 0, GateReset{s->ctl, s->hist, nullptr, 0}, s->st);
+    ph_begin(s, PH_APPLY);
+    launch_diag_apply(s->prec, s->keys[s->cur], s->amps[s->cur], s->probs[s->cur], N, dp, s->ctl, s->st);
+    ph_end(s, PH_APPLY);
+    launched(s, PH_APPLY, 2);
+    rc = sync_ctl(s, "sv_apply_gate");
+    if (rc != SV_OK) return rc;
+    if (s->ctl_host->count[3] != 0) {  // exact zeros: drop them in order
+      rc = ensure_lookback(s, N / 2048 + 16);
+      if (rc != SV_OK) return rc;
+      ph_begin(s, PH_APPLY);
+      launch_drop_zero_terms(s->prec, s->keys[s->cur], s->amps[s->cur], s->probs[s->cur], N, s->keys[alt],
+                             s->amps[alt], s->probs[alt], s->lookback, s->ctl, s->st);
+      ph_end(s, PH_APPLY);
+      launched(s, PH_APPLY, 1);
+      rc = sync_ctl(s, "sv_apply_gate");
+      if (rc != SV_OK) return rc;
+      s->cur = alt;
+      s->N = s->ctl_host->count[2];
+    }
+    s->total_ready = true;
+    ++s->gate_index;
+    s->stats.n_pre = s->N;
+    s->stats.local_gates = s->local_gates;
+    s->stats.global_gates = s->global_gates;
+    s->stats.local_fallbacks = s->local_fallbacks;
+    return SV_OK;
+  }
   // The bucket-local kernel sorts and applies inside shared memory; it is used
   // for states that fit one of its batches (measured: beyond that the sorted
   // path was as fast or faster on this GPU, without bucket bookkeeping).
@@ -676,6 +741,10 @@ sv_status sv_apply_gate(sv_state* s, int m, const int* qubits, const double* U) 
     while (vbits < 63 && (N - 1) >> vbits) ++vbits;
     gp.vbits = s->n + vbits <= 64 ? vbits : 0;
     int w = 0, run = 0;
+    // monomial gates on the default variant: the partition digit is the output
+    // index, so the merged keys come out in the output order
+    const bool mono_path = mono && s->variant == 0;
+    if (mono_path) gp.rmap = pi;
     if (s->variant == 0) {
       // the state is sorted by the previous gate's key: partition by the gate
       // bits and merge
@@ -697,19 +766,44 @@ sv_status sv_apply_gate(sv_state* s, int m, const int* qubits, const double* U) 
       if (rc != SV_OK) return rc;
     }
     s->stats.sort_passes = (uint32_t)run;
-    ph_begin(s, PH_HEADS);
-    launch_group_scan(s->sk[w], N, gp, s->heads, s->gmask, s->ooff, s->gs_lb, s->ctl, s->st);
-    ph_end(s, PH_HEADS);
-    ph_begin(s, PH_APPLY);
-    launch_gate_apply_slots(s->prec, s->sk[w], s->sidx[w], N, s->heads, s->gmask, s->ooff, s->amps[s->cur], gp,
-                            s->keys[alt], s->amps[alt], s->probs[alt], s->ctl, s->st);
-    s->total_ready = s->prec == SV_C128;  // zeros dropped below add no mass
-    ph_end(s, PH_APPLY);
-    launched(s, PH_HEADS, 1);
-    launched(s, PH_APPLY, 1);
-    rc = sync_ctl(s, "sv_apply_gate");
-    if (rc != SV_OK) return rc;
-    const uint64_t npre = s->ctl_host->count[1];
+    uint64_t npre = N;
+    if (mono_path) {
+      ++s->stats.mono_gates;
+      // the regrouping sorted the terms by output key: one output per term
+      MonoParams mp;
+      std::memset(&mp, 0, sizeof(mp));
+      mp.m = m;
+      mp.vbits = gp.vbits;
+      for (int r = 0; r < d; ++r) {
+        const int ro = (int)((pi >> (4 * r)) & 15u);
+        mp.ur[ro] = U[2 * (ro * d + r)];
+        mp.ui[ro] = U[2 * (ro * d + r) + 1];
+        mp.rnz |= ((gp.re_nz[ro] >> r) & 1u) << ro;
+        mp.inz |= ((gp.im_nz[ro] >> r) & 1u) << ro;
+      }
+      ph_begin(s, PH_APPLY);
+      launch_mono_apply(s->prec, s->sk[w], s->sidx[w], N, s->amps[s->cur], mp, s->keys[alt], s->amps[alt],
+                        s->probs[alt], s->ctl, s->st);
+      s->total_ready = true;  // zeros dropped below add no mass
+      ph_end(s, PH_APPLY);
+      launched(s, PH_APPLY, 1);
+      rc = sync_ctl(s, "sv_apply_gate");
+      if (rc != SV_OK) return rc;
+    } else {
+      ph_begin(s, PH_HEADS);
+      launch_group_scan(s->sk[w], N, gp, s->heads, s->gmask, s->ooff, s->gs_lb, s->ctl, s->st);
+      ph_end(s, PH_HEADS);
+      ph_begin(s, PH_APPLY);
+      launch_gate_apply_slots(s->prec, s->sk[w], s->sidx[w], N, s->heads, s->gmask, s->ooff, s->amps[s->cur], gp,
+                              s->keys[alt], s->amps[alt], s->probs[alt], s->ctl, s->st);
+      s->total_ready = s->prec == SV_C128;  // zeros dropped below add no mass
+      ph_end(s, PH_APPLY);
+      launched(s, PH_HEADS, 1);
+      launched(s, PH_APPLY, 1);
+      rc = sync_ctl(s, "sv_apply_gate");
+      if (rc != SV_OK) return rc;
+      npre = s->ctl_host->count[1];
+    }
     if (s->ctl_host->count[3] != 0) {  // exact cancellations: drop the zero terms in order
       rc = ensure_lookback(s, npre / 2048 + 16);
       if (rc != SV_OK) return rc;
@@ -847,6 +941,7 @@ sv_status sv_truncate(sv_state* s, uint64_t* kept, double* retained_fraction) {
   s->stats.select_levels = 0;
   s->stats.window_hits = 0;
   s->stats.window_terms = 0;
+  s->stats.selects = 0;
   s->stats.n_kept = N;
   s->stats.total_mass = s->stats.kept_mass = 0.0;
   const bool need_p = s->p < 1.0, need_k = N > s->K;
@@ -855,23 +950,40 @@ sv_status sv_truncate(sv_state* s, uint64_t* kept, double* retained_fraction) {
     uint64_t c = N;
     bool have_cut = false;
     sv_status rc;
-    if (need_p) {
-      rc = run_select(s, 0, 0, &s->stats.select_levels);
-      if (rc != SV_OK) return rc;
-      if (s->ctl_host->sel_done == 1) {
-        c = s->ctl_host->cut_count;
-        have_cut = true;
-      }
-    }
-    if (c > s->K) {
+    // c = min(c_p, K).  With more than K terms the top-k cut is found first:
+    // its kept mass S_K decides whether the p-mass cut can lie before it
+    // (c_p <= K exactly when S_K >= T, the prefix masses being monotone), so
+    // the p-mass select runs only then.
+    bool run_p = need_p;
+    if (need_k) {
       rc = run_select(s, 1, s->K, &s->stats.select_levels);
       if (rc != SV_OK) return rc;
+      ++s->stats.selects;
       if (s->ctl_host->sel_done != 1) {
         s->broken = true;
         return fail(s, SV_E_STATE, "top-k select found no cut");
       }
       c = s->ctl_host->cut_count;
       have_cut = true;
+      if (need_p) {
+        const double SNd = u128_to_double(s->ctl_host->total_mass_hi, s->ctl_host->total_mass_lo);
+        const unsigned __int128 T = fx_from_double(s->p * SNd);
+        const unsigned __int128 SK =
+            ((unsigned __int128)s->ctl_host->cut_mass_hi << 64) | s->ctl_host->cut_mass_lo;
+        run_p = SK >= T;
+      }
+    }
+    if (run_p) {
+      rc = run_select(s, 0, 0, &s->stats.select_levels);
+      if (rc != SV_OK) return rc;
+      ++s->stats.selects;
+      if (s->ctl_host->sel_done == 1) {
+        c = s->ctl_host->cut_count;
+        have_cut = true;
+      } else if (need_k) {
+        s->broken = true;
+        return fail(s, SV_E_STATE, "p-mass select found no cut below the top-k cut");
+      }
     }
     double SN = u128_to_double(s->ctl_host->total_mass_hi, s->ctl_host->total_mass_lo);
     s->stats.total_mass = SN;
@@ -1126,6 +1238,11 @@ sv_status sv_set_timing(sv_state* s, int enable) {
 
 sv_status sv_phase_times(const sv_state* s, double* ms, uint64_t* launches) {
   if (!s) return SV_E_ARG;
+  if (s->timing) {  // fold in the phases still pending on the stream (the last compaction)
+    sv_state* w = const_cast<sv_state*>(s);
+    if (cudaStreamSynchronize(w->st) == cudaSuccess) ph_collect(w);
+    cudaGetLastError();
+  }
   for (int ph = 0; ph < PH_COUNT; ++ph) {
     if (ms) ms[ph] = s->ph_ms[ph];
     if (launches) launches[ph] = s->ph_launches[ph];

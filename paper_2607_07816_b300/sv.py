@@ -53,9 +53,10 @@ class sv_stats(ctypes.Structure):
     _fields_ = [("n_in", ctypes.c_uint64), ("n_pre", ctypes.c_uint64), ("n_kept", ctypes.c_uint64),
                 ("sort_passes", ctypes.c_uint32), ("select_levels", ctypes.c_uint32),
                 ("total_mass", ctypes.c_double), ("kept_mass", ctypes.c_double),
-                ("window_hits", ctypes.c_uint32), ("pad", ctypes.c_uint32), ("window_terms", ctypes.c_uint64),
+                ("window_hits", ctypes.c_uint32), ("selects", ctypes.c_uint32), ("window_terms", ctypes.c_uint64),
                 ("local_gates", ctypes.c_uint64), ("global_gates", ctypes.c_uint64),
-                ("local_fallbacks", ctypes.c_uint64)]
+                ("local_fallbacks", ctypes.c_uint64), ("diag_gates", ctypes.c_uint64),
+                ("mono_gates", ctypes.c_uint64)]
 
 
 _lib = None

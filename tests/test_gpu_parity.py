@@ -399,3 +399,71 @@ def test_merge_grouping_with_empty_and_lopsided_runs(sv, oracle_mod, prec):
     g = sv.SparseState(n, 1 << 16, 1.0, prec=prec)
     o = oracle_mod.Oracle(n, 1 << 16, 1.0, prec=prec)
     run_both(gates, g, o)
+
+
+def _random_diagonal(m, rng, kind):
+    d = 1 << m
+    if kind == "phase":
+        return np.diag(np.exp(2j * np.pi * rng.random(d)))
+    if kind == "quarter":    # entries 1, i, -1, -i: real or imaginary part exactly zero
+        return np.diag((1j) ** rng.integers(0, 4, size=d)).astype(np.complex128)
+    return C.mat_rz(np.pi) if m == 1 else np.diag([1.0] * (d - 1) + [-1.0]).astype(np.complex128)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_diagonal_gates_in_place_match_oracle(sv, oracle_mod, prec):
+    """Diagonal gates (phases, RZ(pi), CZ-like sign flips, entries with a zero
+    real or imaginary part) update the amplitudes in place without
+    regrouping; interleaved with dense gates that regroup the state, on
+    states from a few terms up to several times the kernel's grid, with
+    truncation after every gate."""
+    rng = np.random.default_rng(880 + prec)
+    for count, n, K, p in [(5, 8, 4, 1.0), (70001, 30, 50000, 0.99), (2_500_000, 36, 2_000_000, 0.9999)]:
+        keys, amps = C.random_state(n, count, rng, ties=True)
+        g = sv.SparseState(n, K, p, prec=prec)
+        o = oracle_mod.Oracle(n, K, p, prec=prec)
+        g.load(keys, amps)
+        o.load(keys, amps)
+        gates = []
+        for step in range(6):
+            m = int(rng.integers(1, min(4, n) + 1))
+            qs = tuple(int(x) for x in rng.choice(n, size=m, replace=False))
+            gates.append((qs, _random_diagonal(m, rng, ["phase", "quarter", "sign"][step % 3])))
+            if step % 2 == 1:
+                gates.append(C.random_gate(n, 1, rng, "haar"))
+        run_both(gates, g, o, check_every=count < 100000)
+
+
+def _random_monomial(m, rng):
+    d = 1 << m
+    perm = rng.permutation(d)
+    u = np.zeros((d, d), dtype=np.complex128)
+    phases = [1.0, -1.0, 1j, -1j, np.exp(2j * np.pi * rng.random())]
+    for r in range(d):
+        u[perm[r], r] = phases[int(rng.integers(0, len(phases)))]
+    return u
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_monomial_gates_match_oracle(sv, oracle_mod, prec):
+    """Permutations with phases on m = 1..4 qubits (X, CNOT, Toffoli, C3X and
+    random ones): the regrouping sorts by the output index and one pass
+    applies the entries.  Interleaved with dense and diagonal gates, with
+    truncation after every gate, on states above the shared-memory size."""
+    rng = np.random.default_rng(890 + prec)
+    for count, n, K, p in [(5000, 20, 4000, 1.0), (300_001, 40, 250_000, 0.999)]:
+        keys, amps = C.random_state(n, count, rng, ties=True)
+        g = sv.SparseState(n, K, p, prec=prec)
+        o = oracle_mod.Oracle(n, K, p, prec=prec)
+        g.load(keys, amps)
+        o.load(keys, amps)
+        gates = []
+        for step in range(8):
+            m = 1 + step % 4
+            qs = tuple(int(x) for x in rng.choice(n, size=m, replace=False))
+            gates.append((qs, C.mat_mcx(m) if (step // 4) == 0 and m > 1 else _random_monomial(m, rng)))
+            if step % 3 == 2:
+                gates.append(C.random_gate(n, 1, rng, "haar"))
+            if step % 4 == 1:
+                gates.append(((int(rng.integers(0, n)),), C.mat_rz(float(rng.random()))))
+        run_both(gates, g, o, check_every=count < 100000)
