@@ -1,30 +1,40 @@
 #!/usr/bin/env python
-"""Benchmark: sparse-gate terms/s and HBM / FP64 roofline fraction.
+"""Benchmark: sparse-gate terms/s and the HBM / FP64 roofline fraction.
 
-Workload: the n=40 brickwork peaked circuit (8 layers of Haar SU(4) on
-neighbouring pairs, the perturbed mirror with theta ~ N(0, 0.05), X on the
-hidden string), top-K truncation to K = 2^24 terms after every gate, p = 1.
-One step = apply the next gate + truncate + read the peak, on the state
-already at K terms (the whole hot path: key transform, grouping sort, group
-mat-vec with zero drop, select, renormalising compaction, argmax).
+Workload (default, --workload mix60): the n=60 random-mix peaked circuit --
+400 gates drawn uniformly from H, CNOT, CZ, RZ(theta ~ U[0, 2 pi)), Toffoli,
+C3X and Haar-random U(8) on random qubits, the mirror with every inverse
+perturbed as U^dagger exp(-i theta G) (theta ~ N(0, 0.05)), X on a seeded
+hidden string -- with truncation to K = 2^26 terms and p = 0.9999 retained
+mass after every gate, complex128 amplitudes.
 
-value   : sum of input terms over the timed steps / device time of the steps
-          (CUDA events on the library's stream; state resident in HBM and
-          larger than L2, so no flush is needed).
-e2e     : the same metric for the whole circuit run through the C ABI from
-          the host (create, every gate with its matrix copied from host
-          memory, every truncation, the peak read back), host wall clock.
-roofline: the dominant kernel's algorithmic bytes (or FP64 flops) per launch
-          over its CUDA-event launch time, against MEASURED_PEAKS.json.
+One step = apply the next gate + truncate + read the peak (pipelined), on
+the state once it has reached K terms: the whole hot path (key transform,
+grouping, group mat-vec with zero drop, exact mass + select, renormalising
+compaction, argmax).  The circuit from |0> up to the first gate on a full
+state is run untimed, then --warmup steps, then exactly --steps steps.
 
---impl reference times the CPU oracle (test infrastructure, the only
-reference that exists for this paper) on a bounded sample of the workload.
+value    : sum of input terms over the timed steps / device time of those
+           steps (CUDA events on the library's stream; the state is resident
+           in HBM and larger than L2, so no flush is needed).
+e2e      : the same metric for the whole circuit run through the C ABI from
+           the host (create, every gate with its matrix copied from pinned
+           host memory, every truncation, the peak read back), wall clock.
+roofline : the dominant kernel phase's algorithmic bytes (or FP64 flops) per
+           launch over its CUDA-event launch time, against
+           MEASURED_PEAKS.json (HBM) or the FP64 pipe.
+c64      : the complex64 form on the same steps, and the error of the whole
+           circuit's complex64 result against the complex128 result (which
+           equals the CPU oracle bit for bit in every parity test).
+
+--impl reference times the CPU oracle (test infrastructure; the only
+reference that exists for this paper) on a bounded sample of the same
+workload.
 """
 from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -34,27 +44,60 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-N_QUBITS, K_TERMS, LAYERS, SEED = 40, 1 << 24, 8, 1002
-SM_COUNT, FP64_FMA_PER_SM_CLK = 148, 2      # B300 FP64: 2 DFMA / SM / clock (probe: 0.56 TFMA/s @ 1.94 GHz)
-WORKLOAD = "n40 brickwork Haar-SU(4) x8 + perturbed mirror + X^s, top-K 2^24 per gate, p=1"
+SM_COUNT, FP64_FMA_PER_SM_CLK = 148, 2      # B300 FP64 pipe: 2 DFMA / SM / clock (derived peak)
+WORKLOADS = {
+    "mix60": {"n": 60, "K": 1 << 26, "p": 0.9999, "seed": 1003,
+              "desc": "n60 random mix (H, CNOT, CZ, RZ, Toffoli, C3X, Haar U(8)) x400 + perturbed mirror "
+                      "(sigma 0.05) + X^s; top-K 2^26 and p=0.9999 after every gate"},
+    "brick40": {"n": 40, "K": 1 << 24, "p": 1.0, "seed": 1002,
+                "desc": "n40 brickwork Haar-SU(4) x8 + perturbed mirror + X^s, top-K 2^24 per gate, p=1"},
+}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="mix60", choices=sorted(WORKLOADS))
     ap.add_argument("--prec", default="c128", choices=["c128", "c64"])
-    ap.add_argument("--K", type=int, default=K_TERMS)
+    ap.add_argument("--K", type=int, default=0, help="override the workload's K")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-c64", action="store_true")
+    ap.add_argument("--no-whole", action="store_true", help="skip the whole-circuit legs and the c64 error report")
     ap.add_argument("--no-ring", action="store_true", help="skip the ring u3/cz (fusion) leg")
     ap.add_argument("--no-ab", action="store_true", help="skip the group-first / expand-first comparison")
-    ap.add_argument("--serve-requests", type=int, default=128,
+    ap.add_argument("--batch-circuits", type=int, default=512,
+                    help="circuits of the batched-form leg (0: skip)")
+    ap.add_argument("--serve-requests", type=int, default=256,
                     help="requests of the serving stream measured (0: skip the serving leg)")
-    return ap.parse_args()
+    a = ap.parse_args()
+    w = dict(WORKLOADS[a.workload])
+    if a.K:
+        w["K"] = a.K
+    a.wl = w
+    return a
+
+
+def make_circuit(wl, rank=0):
+    from paper_2607_07816_b300 import circuits as C
+    if wl["n"] == 60:
+        return C.mix_n60(seed=wl["seed"] + rank, K=wl["K"], p=wl["p"])
+    return C.brickwork_n40(seed=wl["seed"] + rank, layers=8, K=wl["K"], p=wl["p"])
+
+
+def gate_kind(u) -> str:
+    """diag / mono (one nonzero per row and column) / dense, from U's zero
+    pattern (the library decides the same way)."""
+    import numpy as np
+    nz = np.abs(u) > 0
+    if not (nz & ~np.eye(len(u), dtype=bool)).any():
+        return "diag"
+    if (nz.sum(0) == 1).all() and (nz.sum(1) == 1).all():
+        return "mono"
+    return "dense"
 
 
 def measured_peaks():
@@ -74,7 +117,7 @@ class ClockSampler:
     def __init__(self, device_index: int):
         self.dev = device_index
         self.proc = None
-        self.path = os.path.join("/tmp", f"sv_clocks_{os.getpid()}.csv")
+        self.path = os.path.join("/tmp", f"sv_clocks_{os.getpid()}_{device_index}.csv")
 
     def start(self):
         try:
@@ -138,171 +181,278 @@ def whole_job_rate(units_local: float, ms_local: float):
     return units / (ms / 1e3), units, ms
 
 
-# ------------------------------------------------------------------ roofline
-def phase_model(ph: str, totals: dict, prec: str, passes: int):
-    """Algorithmic bytes and FP64 flops of one phase over the timed steps.
-    S_a = amplitude bytes; per term: key 8 B, probability 8 B."""
+# ------------------------------------------------------------------ byte / flop model
+def new_totals():
+    keys = ["n_in", "n_pre", "n_kept", "steps", "select_levels", "selects", "window_hits", "window_terms",
+            "sort_bytes", "heads_bytes", "apply_bytes", "compact_bytes", "window_bytes", "fp64_apply",
+            "gates_diag", "gates_mono", "gates_dense", "cuts", "B_method", "B_strict"]
+    return {k: 0 for k in keys}
+
+
+def account_step(tot, q, kind, s1, s2, prec, n_bits):
+    """Algorithmic bytes and FP64 work of one gate + truncation, per phase.
+    Per term: key 8 B, probability 8 B, amplitude S_a (16 complex128, 8
+    complex64); the grouping keeps a 4-byte index beside each key when
+    n + log2 N exceeds 64 bits."""
     sa = 16 if prec == "c128" else 8
-    n_in, n_pre, n_kept = totals["n_in"], totals["n_pre"], totals["n_kept"]
-    if ph == "sort":     # count pass (8 B) + scatter and merge passes (read + write the packed key: 16 B)
-        return {"bytes": (8 + 16 * passes) * n_in, "flops": 0.0}
-    if ph == "keys":     # radix-sort variant only: read key, write sort key + index
-        return {"bytes": 20 * n_in, "flops": 0.0}
-    if ph == "apply":    # read grouped key + gathered amplitude per input; write key+amp+prob per candidate
-        return {"bytes": (8 + sa) * totals["n_in_apply"] + (16 + sa) * totals["n_pre_apply"],
-                "flops": totals["fp64_apply"]}
-    if ph == "window":   # one streaming pass over the probabilities (+ window keys)
-        return {"bytes": 8 * n_pre, "flops": 0.0}
-    if ph == "select":   # histogram levels over the window terms
-        return {"bytes": 16 * totals.get("window_terms", 0), "flops": 0.0}
-    if ph == "compact":  # keep bit per candidate; read kept key + amp; write kept key, amp, prob
-        return {"bytes": n_pre / 8 + (8 + sa) * n_kept + (16 + sa) * n_kept, "flops": 0.0}
-    if ph == "peak":     # after a truncation: the compaction's per-block partials
-        return {"bytes": 16 * 1184 * totals["steps"], "flops": 0.0}
-    if ph == "heads":    # read the grouped keys (group records written: not counted)
-        return {"bytes": 8 * n_in, "flops": 0.0}
-    if ph == "local":    # read key + amplitude per input; write key + amp + prob per candidate
-        return {"bytes": (8 + sa) * totals["n_in_local"] + (16 + sa) * totals["n_pre_local"],
-                "flops": totals["fp64_local"]}
-    return {"bytes": 0.0, "flops": 0.0}
+    S = 8 + sa
+    m = len(q)
+    n_in, n_pre, n_kept = s1["n_in"], s1["n_pre"], s2["n_kept"]
+    pairs = 4 if n_bits + max(1, (max(1, n_in) - 1).bit_length()) > 64 else 0
+    tot["n_in"] += n_in
+    tot["n_pre"] += n_pre
+    tot["n_kept"] += n_kept
+    tot["steps"] += 1
+    tot["select_levels"] += s2["select_levels"]
+    tot["selects"] += s2["selects"]
+    tot["window_hits"] += s2["window_hits"]
+    tot["window_terms"] += s2["window_terms"]
+    tot["gates_" + kind] += 1
+    if kind != "diag":
+        # count pass (8), scatter (read 8, write 8 + index), m merge levels (read + write)
+        tot["sort_bytes"] += n_in * (8 + 16 + pairs) + m * n_in * (16 + 2 * pairs)
+    if kind == "dense":
+        tot["heads_bytes"] += 8 * n_in
+    if kind == "diag":
+        tot["apply_bytes"] += n_in * (8 + sa) + n_in * (sa + 8)
+    else:  # grouped key (+ index) and gathered amplitude per input; key, amplitude, probability per output
+        tot["apply_bytes"] += n_in * (8 + pairs + sa) + n_pre * (16 + sa)
+    # FP64 pipe operations of the apply kernel, 2 flops each: complex128 runs
+    # 4 fused multiply-adds per (input, output) pair with a nonzero entry;
+    # every candidate's probability is a multiply + fma in FP64
+    ops = 2.0 * n_pre
+    if prec == "c128":
+        ops += 4.0 * n_in * ((1 << m) if kind == "dense" else 1)
+    tot["fp64_apply"] += 2.0 * ops
+    tot["window_bytes"] += 8 * n_pre * s2["selects"]
+    cut = n_kept < n_pre
+    if cut:
+        tot["cuts"] += 1
+        tot["compact_bytes"] += n_pre / 8 + (8 + sa) * n_kept + (16 + sa) * n_kept
+    # gate-level model (SURVEY-style B_method): group 2 S N_in, mat-vec S (N_in + N_pre),
+    # select 8 N_pre and compaction S (N_pre + N_kept) when a cut is made
+    b = 2 * S * n_in + S * (n_in + n_pre)
+    if cut:
+        b += 8 * n_pre + S * (n_pre + n_kept)
+    tot["B_method"] += b
+    tot["B_strict"] += S * (n_in + n_kept)
 
 
-def dense_dfma_per_gate(m: int, n_in: int) -> float:
-    # every input term meets 2^m outputs, 4 fused multiply-adds each, plus
-    # the probability (2 ops) of every candidate (counted by the caller)
-    return n_in * (1 << m) * 4.0
+def phase_bytes(ph, tot):
+    return {"sort": tot["sort_bytes"], "heads": tot["heads_bytes"], "apply": tot["apply_bytes"],
+            "window": tot["window_bytes"], "select": 16 * tot["window_terms"],
+            "compact": tot["compact_bytes"], "peak": 16 * 1184 * tot["steps"]}.get(ph, 0.0)
+
+
+def fp64_derived_tflops(sm_mhz):
+    return SM_COUNT * FP64_FMA_PER_SM_CLK * 2 * sm_mhz * 1e6 / 1e12
+
+
+def roofline(res, prec, peaks, fp64_probe):
+    # the phase times come from the instrumented steps: their own gates' totals
+    tot, phases = res["phase_totals"], res["phases"]
+    dom = max((p for p in phases if p != "other"), key=lambda p: phases[p][0])
+    ms, launches = phases[dom]
+    per_launch_s = ms / 1e3 / max(1, launches)
+    bytes_per_launch = phase_bytes(dom, tot) / max(1, launches)
+    gbs = bytes_per_launch / per_launch_s / 1e9
+    hbm_frac = gbs / peaks["hbm_gbs"]
+    out = {"kernel": dom, "bound": "hbm", "achieved": round(gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+           "frac": round(hbm_frac, 4), "traffic": traffic_for(dom, prec, bytes_per_launch),
+           "peak_src": f"{peaks['src']} copy bandwidth (MEASURED_PEAKS.json)",
+           "launch_ms": round(per_launch_s * 1e3, 4), "launches": launches,
+           "alg_bytes_per_launch": round(bytes_per_launch)}
+    if dom == "apply" and tot["fp64_apply"] > 0:
+        fp64_peak = fp64_derived_tflops(peaks["sm_max_mhz"])
+        tflops = tot["fp64_apply"] / max(1, launches) / per_launch_s / 1e12
+        if tflops / fp64_peak > hbm_frac:
+            out.update({"bound": "alu", "achieved": round(tflops, 4), "peak": round(fp64_peak, 4),
+                        "unit": "TFLOP/s", "frac": round(tflops / fp64_peak, 4),
+                        "peak_src": "FP64 pipe derived: 148 SMs x 2 DFMA/clk x 2 flop x max SM clock",
+                        "fp64_probe_tflops": fp64_probe,
+                        "frac_of_probe": round(tflops / fp64_probe, 4) if fp64_probe else None,
+                        "hbm_frac": round(hbm_frac, 4)})
+    return out
+
+
+def traffic_for(phase, prec, alg_bytes):
+    """DRAM bytes per launch of the phase's dominant kernel from the
+    committed ncu summary, when it was taken on the current kernel sources
+    (else null)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path))
+        from paper_2607_07816_b300 import build as B
+        if d.get("source_hash") != B.source_hash():
+            return None
+        ent = d["kernels"].get(f"{phase}/{prec}")
+        if not ent:
+            return None
+        return round(ent["dram_bytes_per_alg_byte"] * alg_bytes)
+    except Exception:
+        return None
 
 
 # ------------------------------------------------------------------ our arm
-def run_ours(args, rank, world):
-    import numpy as np
+def run_steps(args, rank, prec_name, dev, stream, sample_clocks):
+    """The timed steps on the state at K terms, then as many instrumented
+    steps for the per-phase breakdown."""
     import torch
-    from paper_2607_07816_b300 import circuits as C
     from paper_2607_07816_b300 import sv
-
-    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
-    torch.cuda.set_device(dev)
-    stream = torch.cuda.current_stream(dev)
-    sv.load_library()
-    peaks = measured_peaks()
-
-    def run_prec(prec_name, K, steps, warmup, sample_clocks):
-        prec = sv.SV_C128 if prec_name == "c128" else sv.SV_C64
-        circ = C.brickwork_n40(seed=SEED + rank, layers=LAYERS, K=K)
-        gates = circ.gates
-        st = sv.SparseState(circ.n, K, 1.0, prec=prec, stream=stream.cuda_stream)
-        gi = 0
-        # ramp: run until the state is at K terms
-        while gi < len(gates) and st.num_terms() < K:
-            q, u = gates[gi]
-            st.apply_gate(q, u)
-            st.truncate()
-            gi += 1
-        for _ in range(warmup):
-            q, u = gates[gi % len(gates)]
-            st.apply_gate(q, u)
-            st.truncate()
-            st.peak()
-            gi += 1
-        torch.cuda.synchronize(dev)
-        barrier()
-        totals = {"n_in": 0, "n_pre": 0, "n_kept": 0, "select_levels": 0, "steps": steps,
-                  "sort_passes": 0, "window_hits": 0, "window_terms": 0,
-                  # per gate path: the sorted path (sort + group mat-vec) or the bucket-local kernel
-                  "n_in_apply": 0, "n_pre_apply": 0, "fp64_apply": 0.0,
-                  "n_in_local": 0, "n_pre_local": 0, "fp64_local": 0.0}
-        clocks = ClockSampler(dev.index) if sample_clocks else None
-        if clocks:
-            clocks.start()
-            time.sleep(0.3)
-        l0 = sv.sv_launch_count()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize(dev)
-        loc0 = st.stats()["local_gates"]
-        pending = None
-        e0.record(stream)
-        for _ in range(steps):
-            q, u = gates[gi % len(gates)]
-            gi += 1
-            st.apply_gate(q, u)
-            st.truncate()
-            # the peak of every step, read back pipelined: its 16 bytes reach
-            # the host while the next step runs, and the statistics are
-            # gathered while the compaction and the readout are on the GPU
-            ticket = st.peak_async()
-            s1 = s2 = st.stats()
-            if pending is not None:
-                st.peak_wait(pending)
-            pending = ticket
-            path = "local" if s1["local_gates"] > loc0 else "apply"
-            loc0 = s1["local_gates"]
-            totals["n_in_" + path] += s1["n_in"]
-            totals["n_pre_" + path] += s1["n_pre"]
-            # FP64 pipe work of the mat-vec kernel, counted as 2 flops per operation:
-            # complex128 runs 4 fused multiply-adds per (input, output) pair, and
-            # every candidate's probability is a multiply + fma (complex64 runs
-            # the mat-vec in FP32, so only the probabilities are FP64)
-            fp64_ops = 2.0 * s1["n_pre"]
-            if prec == sv.SV_C128:
-                fp64_ops += dense_dfma_per_gate(len(q), s1["n_in"])
-            totals["fp64_" + path] += 2.0 * fp64_ops
-            totals["n_in"] += s1["n_in"]
-            totals["n_pre"] += s1["n_pre"]
-            totals["n_kept"] += s2["n_kept"]
-            totals["sort_passes"] += s1["sort_passes"]
-            totals["select_levels"] += s2["select_levels"]
-            totals["window_hits"] += s2["window_hits"]
-            totals["window_terms"] += s2["window_terms"]
+    wl = args.wl
+    prec = sv.SV_C128 if prec_name == "c128" else sv.SV_C64
+    circ = make_circuit(wl, rank)
+    gates = circ.gates
+    kinds = [gate_kind(u) for _, u in gates]
+    st = sv.SparseState(circ.n, wl["K"], wl["p"], prec=prec, stream=stream.cuda_stream)
+    gi = 0
+    # ramp: the circuit from |0> until the state is at K terms (the p-mass cut
+    # may keep it slightly below K: 99% counts as full)
+    while gi < len(gates) and st.num_terms() < 0.99 * wl["K"]:
+        q, u = gates[gi]
+        st.apply_gate(q, u)
+        st.truncate()
+        gi += 1
+    first_full = gi
+    for _ in range(args.warmup):
+        q, u = gates[gi % len(gates)]
+        st.apply_gate(q, u)
+        st.truncate()
+        st.peak()
+        gi += 1
+    torch.cuda.synchronize(dev)
+    barrier()
+    tot = new_totals()
+    clocks = ClockSampler(dev.index) if sample_clocks else None
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    l0 = sv.sv_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    g_start = gi
+    pending = None
+    e0.record(stream)
+    for _ in range(args.steps):
+        j = gi % len(gates)
+        q, u = gates[j]
+        gi += 1
+        st.apply_gate(q, u)
+        s1 = st.stats()
+        st.truncate()
+        # the peak of every step, read back pipelined: its 16 bytes reach the
+        # host while the next step runs
+        ticket = st.peak_async()
+        s2 = st.stats()
         if pending is not None:
             st.peak_wait(pending)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        launches = sv.sv_launch_count() - l0
-        ms = e0.elapsed_time(e1)
-        clk = clocks.stop() if clocks else None
-        barrier()
-        rate, units_all, ms = whole_job_rate(totals["n_in"], ms)
-        # the per-phase breakdown: as many more steps with CUDA events around
-        # every phase (kept out of the timed loop above: the events sit
-        # between kernels of a step and cost time of their own)
-        st.set_timing(True)
-        for _ in range(steps):
-            q, u = gates[gi % len(gates)]
-            gi += 1
-            st.apply_gate(q, u)
-            st.truncate()
-            st.peak_wait(st.peak_async())
-        torch.cuda.synchronize(dev)
-        phases = st.phase_times()
-        peak = st.peak()
-        fin = st.stats()
-        paths = {k: fin[k] for k in ("local_gates", "global_gates", "local_fallbacks")}
-        st.close()
-        return {"ms": ms, "totals": totals, "phases": phases, "launches": launches, "clocks": clk,
-                "peak": peak, "hidden": circ.hidden, "paths": paths, "rate": rate, "units_all": units_all}
+        pending = ticket
+        account_step(tot, q, kinds[j], s1, s2, prec_name, circ.n)
+    if pending is not None:
+        st.peak_wait(pending)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    launches = sv.sv_launch_count() - l0
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop() if clocks else None
+    barrier()
+    rate, units_all, ms_all = whole_job_rate(tot["n_in"], ms)
+    # per-phase breakdown: as many further steps with CUDA events around each
+    # phase (events between the kernels of a step cost time of their own)
+    st.set_timing(True)
+    ph_tot = new_totals()
+    for _ in range(args.steps):
+        j = gi % len(gates)
+        q, u = gates[j]
+        gi += 1
+        st.apply_gate(q, u)
+        s1 = st.stats()
+        st.truncate()
+        s2 = st.stats()
+        st.peak_wait(st.peak_async())
+        account_step(ph_tot, q, kinds[j], s1, s2, prec_name, circ.n)
+    torch.cuda.synchronize(dev)
+    phases = st.phase_times()
+    fin = st.stats()
+    st.close()
+    return {"ms": ms, "totals": tot, "phases": phases, "phase_totals": ph_tot, "launches": launches,
+            "clocks": clk, "rate": rate, "units_all": units_all, "first_full_gate": first_full,
+            "timed_gates": [g_start, g_start + args.steps - 1],
+            "paths": {k: fin[k] for k in ("local_gates", "global_gates", "diag_gates", "mono_gates")}}
 
-    main = run_prec(args.prec, args.K, args.steps, args.warmup, sample_clocks=True)
-    res = {"main": main}
-    if not args.no_c64 and args.prec == "c128":
-        res["c64"] = run_prec("c64", args.K, args.steps, args.warmup, sample_clocks=False)
-    if not args.no_e2e:
-        res["e2e"] = run_e2e(args, rank, dev, stream)
-    if args.serve_requests > 0:
-        res["serving"] = run_serving(args, rank, dev, stream)
-    if not args.no_ring:
-        res["ring"] = run_ring(args, dev, stream)
-    if not args.no_ab:
-        res["variant_ab"] = run_variant_ab(args, rank, dev, stream)
-    return res, peaks
+
+def run_whole(args, rank, prec_name, dev, stream):
+    """The whole circuit from |0>, every gate truncated; CUDA-event time on
+    the library's stream; the final state kept for the error report."""
+    import torch
+    from paper_2607_07816_b300 import sv
+    wl = args.wl
+    prec = sv.SV_C128 if prec_name == "c128" else sv.SV_C64
+    circ = make_circuit(wl, rank)
+    st = sv.SparseState(circ.n, wl["K"], wl["p"], prec=prec, stream=stream.cuda_stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    n_in = n_pre = 0
+    e0.record(stream)
+    for (q, u) in circ.gates:
+        st.apply_gate(q, u)
+        s1 = st.stats()
+        n_in += s1["n_in"]
+        n_pre += s1["n_pre"]
+        st.truncate()
+    key, pr = st.peak()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    F = st.retained_mass()
+    keys, amps = st.export()
+    st.close()
+    return {"ms": ms, "terms": n_in, "candidates": n_pre, "terms_per_s": n_in / (ms / 1e3),
+            "gates": len(circ.gates), "peak_key": key, "peak_prob": pr, "peak_is_hidden": key == circ.hidden,
+            "retained_mass": F, "final_terms": len(keys)}, (keys, amps)
+
+
+def error_report(ref, test, dev):
+    """complex64 final state against the complex128 one, on the GPU: max
+    |d amp| on the common keys, the symmetric difference (count and its
+    probability mass on the side that has it) and the L2 distance over the
+    union (absent = 0)."""
+    import numpy as np
+    import torch
+    k0, a0 = ref
+    k1, a1 = test
+    K0 = torch.from_numpy(k0.view(np.int64)).to(dev)
+    K1 = torch.from_numpy(k1.view(np.int64)).to(dev)
+    A0 = torch.from_numpy(np.ascontiguousarray(a0)).to(dev)
+    A1 = torch.from_numpy(np.ascontiguousarray(a1.astype(np.complex128))).to(dev)
+    s0, i0 = torch.sort(K0)
+    s1, i1 = torch.sort(K1)
+    pos = torch.searchsorted(s0, s1).clamp(max=len(s0) - 1)
+    hit1 = s0[pos] == s1                     # test keys present in ref
+    in0 = torch.zeros(len(s0), dtype=torch.bool, device=dev)
+    in0[pos[hit1]] = True
+    a0s, a1s = A0[i0], A1[i1]
+    d = (a0s[pos[hit1]] - a1s[hit1]).abs()
+    only0 = (a0s[~in0].abs() ** 2).sum().item()
+    only1 = (a1s[~hit1].abs() ** 2).sum().item()
+    l2 = float(np.sqrt((d ** 2).sum().item() + only0 + only1))
+    out = {"terms_ref": len(k0), "terms": len(k1), "common": int(hit1.sum().item()),
+           "max_abs_amp_err_common": float(d.max().item()) if d.numel() else 0.0,
+           "sym_diff_count": int((~in0).sum().item() + (~hit1).sum().item()),
+           "sym_diff_mass": only0 + only1, "union_l2": l2}
+    del K0, K1, A0, A1, s0, s1, i0, i1, pos, hit1, in0, a0s, a1s, d
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_e2e(args, rank, dev, stream):
     import numpy as np
     import torch
-    from paper_2607_07816_b300 import circuits as C
     from paper_2607_07816_b300 import sv
-
-    circ = C.brickwork_n40(seed=SEED + rank, layers=LAYERS, K=args.K)
+    wl = args.wl
+    circ = make_circuit(wl, rank)
     prec = sv.SV_C128 if args.prec == "c128" else sv.SV_C64
     # host-resident inputs: the gate matrices in pinned host memory
     pinned = [(q, torch.from_numpy(np.ascontiguousarray(u)).pin_memory().numpy()) for (q, u) in circ.gates]
@@ -310,7 +460,7 @@ def run_e2e(args, rank, dev, stream):
     barrier()
     h0, d0 = sv.sv_transfer_bytes()
     t0 = time.perf_counter()
-    st = sv.SparseState(circ.n, args.K, 1.0, prec=prec, stream=stream.cuda_stream)
+    st = sv.SparseState(circ.n, wl["K"], wl["p"], prec=prec, stream=stream.cuda_stream)
     n_in = 0
     for (q, u) in pinned:
         n_in += st.num_terms()
@@ -326,108 +476,169 @@ def run_e2e(args, rank, dev, stream):
     rate, _, _ = whole_job_rate(n_in, wall * 1e3)
     return {"value": rate, "unit": "terms/s", "h2d_bytes_per_step": int((h1 - h0) / g),
             "d2h_bytes_per_step": int((d1 - d0) / g), "wall_s": wall, "gates": g,
+            "scope": "whole circuit from |0> (every gate a step), host wall clock",
             "peak_is_hidden": bool(key == circ.hidden), "peak_prob": pr}
 
 
-def run_serving(args, rank, dev, stream):
-    """Serving form against the serial plain path on the same requests.
+def peaked_check(batched, serial, circuits, oracle_results=None):
+    """Peaks of the complex64 batched results against the serial complex128
+    results.  A circuit counts as peaked when its complex128 final state has
+    a clear top: the top probability exceeds the runner-up by more than the
+    complex64 error allows (relative gap > 1e-3) and the retained mass is
+    above 1e-6."""
+    peaked = same = 0
+    diff_peaked = []
+    for j, (b, s) in enumerate(zip(batched, serial)):
+        gap = s["gap"]
+        is_peaked = gap > 1e-3 and s["F"] > 1e-6
+        if is_peaked:
+            peaked += 1
+            if b.peak_key == s["key"]:
+                same += 1
+            else:
+                diff_peaked.append(j)
+    all_same = sum(int(b.peak_key == s["key"]) for b, s in zip(batched, serial))
+    return {"identical_peaks_all": f"{all_same}/{len(serial)}",
+            "peaked_requests": peaked, "identical_peaks_on_peaked": f"{same}/{peaked}",
+            "peaked_rule": "complex128 top-two relative probability gap > 1e-3 and retained mass > 1e-6",
+            "differing_peaked_indices": diff_peaked[:20]}
 
-    Requests: the first R of the seeded serving stream (mirrored brickwork
-    circuits, n in [16,48], forward depth in [2,10], K = 2^k with k in
-    [10,20], and a 2% share of large ones with n=56, depth 12, K=2^25).
-    serial  : each request alone on the single-state complex128 path, one
-              after the other (create, every gate + top-k, peak, destroy);
-              the service time of every request is measured.
-    batched : the continuous-batching loop on the complex64 batched form,
-              160 GB admission budget: a saturated run (all requests at t=0)
-              gives the capacity; then a Poisson stream at 80% of it gives
-              arrival-to-peak latencies.  The serial latencies at the same
-              arrival times follow from its measured service times (one
-              FIFO server)."""
+
+def serial_c128(circuits, stream, arrivals=None):
+    """The serial plain path: every circuit alone on the single-state
+    complex128 API, one after the other (waiting for each arrival when
+    arrival times are given); per circuit: service time, finish time, peak,
+    runner-up gap and retained mass."""
+    from paper_2607_07816_b300 import sv
+    out = []
+    t0 = time.perf_counter()
+    for j, c in enumerate(circuits):
+        if arrivals is not None:
+            wait = arrivals[j] - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+        ts = time.perf_counter()
+        st = sv.SparseState(c.n, c.K, 1.0, prec=sv.SV_C128, stream=stream)
+        for (q, u) in c.gates:
+            st.apply_gate(q, u)
+            st.truncate()
+        key, prob = st.peak()
+        te = time.perf_counter()
+        # the runner-up (canonical dump) for the peakedness rule: not part of
+        # the service, so its time is taken off the clock
+        _, probs = st.probs()
+        F = st.retained_mass()
+        st.close()
+        t0 += time.perf_counter() - te
+        second = float(probs[1]) if len(probs) > 1 else 0.0
+        out.append({"svc": te - ts, "finish": te - t0, "key": key, "prob": prob, "F": F,
+                    "gap": (prob - second) / prob if prob > 0 else 0.0})
+    return out
+
+
+def run_batched(args, rank, dev, stream):
+    """Config-4 leg: the seeded batch of mirrored brickwork circuits (n in
+    [16,48], depth in [2,10], K = 2^k with k in [10,20]) all present at t=0,
+    on the complex64 batched serving loop, against the serial complex128
+    plain path on the same GPU (measured)."""
+    import torch
+    from paper_2607_07816_b300 import circuits as C
+    from paper_2607_07816_b300 import serve, sv
+    R = args.batch_circuits
+    circs = C.batch_circuits(R)
+    n_max = max(c.n for c in circs)
+    s = stream.cuda_stream
+    warm = [c for c in circs if c.K <= 1 << 12][:4]
+    serial_c128(warm, s)
+    w = serve.Server(160 << 30, n_max=n_max, prec=sv.SV_C64, stream=s)
+    w.run(warm)
+    w.close()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    ser = serial_c128(circs, s)
+    serial_s = time.perf_counter() - t0
+    srv = serve.Server(160 << 30, n_max=n_max, prec=sv.SV_C64, stream=s)
+    t0 = time.perf_counter()
+    res = srv.run(circs)
+    torch.cuda.synchronize(dev)
+    batched_s = time.perf_counter() - t0
+    steps = srv.steps
+    graphs = srv.batch.graph_stats()
+    srv.close()
+    out = {"circuits": R, "prec": "c64 batched vs c128 serial", "serial_circuits_per_s": R / serial_s,
+           "batched_circuits_per_s": R / batched_s, "speedup": serial_s / batched_s, "steps": steps,
+           "serial_s": serial_s, "batched_s": batched_s, "graphs": graphs}
+    out.update(peaked_check(res, ser, circs))
+    return out
+
+
+def run_serving(args, rank, dev, stream):
+    """Config-5 leg (first R requests of the seeded serving stream: mirrored
+    brickwork circuits as in config 4 plus a 2% share of large ones, n=56,
+    depth 12, K=2^25).  batched_closed: the continuous-batching loop
+    (complex64, 160 GB budget) with all requests at t=0 gives the capacity;
+    served: Poisson arrivals at 80% of it, arrival-to-peak latency; serial:
+    the single-state complex128 path serving the same arrival stream one
+    request at a time (measured, waiting for each arrival)."""
     import numpy as np
     import torch
     from paper_2607_07816_b300 import circuits as C
     from paper_2607_07816_b300 import serve, sv
-
     R = args.serve_requests
     reqs = [C.serving_request(j) for j in range(R)]
     n_max = max(c.n for c in reqs)
-    sv_stream = stream.cuda_stream
+    s = stream.cuda_stream
     torch.cuda.synchronize(dev)
-    # warm-up of both paths on a few small requests
-    small = [c for c in reqs if c.K <= 1 << 12][:4]
-    serve.serve_serial_plain(small, prec=sv.SV_C128, stream=sv_stream)
-    w = serve.Server(160 << 30, n_max=n_max, prec=sv.SV_C64, stream=sv_stream)
-    w.run(small)
-    w.close()
-    torch.cuda.synchronize(dev)
-
-    t0 = time.perf_counter()
-    ser = serve.serve_serial_plain(reqs, prec=sv.SV_C128, stream=sv_stream)
-    torch.cuda.synchronize(dev)
-    serial_s = time.perf_counter() - t0
-    svc = np.array([x[0] for x in ser])
-
-    srv = serve.Server(160 << 30, n_max=n_max, prec=sv.SV_C64, stream=sv_stream)
+    srv = serve.Server(160 << 30, n_max=n_max, prec=sv.SV_C64, stream=s)
     t0 = time.perf_counter()
     closed = srv.run(reqs)
     torch.cuda.synchronize(dev)
     closed_s = time.perf_counter() - t0
     steps_closed, resident = srv.steps, srv.peak_resident
     srv.close()
-    fin = np.sort([r.finished for r in closed])
-    lo, hi = fin[len(fin) // 4], fin[(3 * len(fin)) // 4]
-    mid_rate = ((3 * len(fin)) // 4 - len(fin) // 4) / (hi - lo) if hi > lo else None
     capacity = R / closed_s
     rate = 0.8 * capacity
     arrivals = serve.poisson_arrivals(R, rate, 1005)
-    srv = serve.Server(160 << 30, n_max=n_max, prec=sv.SV_C64, stream=sv_stream)
+    srv = serve.Server(160 << 30, n_max=n_max, prec=sv.SV_C64, stream=s)
     t0 = time.perf_counter()
     opened = srv.run(reqs, arrivals=arrivals)
     torch.cuda.synchronize(dev)
     open_s = time.perf_counter() - t0
     srv.close()
     p50, p99 = serve.percentiles(opened)
-    s_lat = serve.fifo_latencies(arrivals, svc)
-    same_peak = sum(int(a.peak_key == b[1]) for a, b in zip(closed, ser))
-    # where the argmax differs, the two peak probabilities (complex64 batched,
-    # complex128 serial): near-equal values mean a near-tie between strings
-    differ = [(a.peak_prob, b[2]) for a, b in zip(closed, ser) if a.peak_key != b[1]]
-    rel = [abs(x - y) / max(x, y) for x, y in differ]
-    same_open = sum(int(a.peak_key == b.peak_key and a.peak_prob == b.peak_prob) for a, b in zip(opened, closed))
-    large = [j for j, c in enumerate(reqs) if c.n == 56]
-    return {
-        "requests": R, "large_requests": len(large), "budget_gb": 160, "prec": "c64 batched vs c128 serial",
-        "serial": {"circuits_per_s": R / svc.sum(), "wall_s": serial_s,
-                   "p50_s": float(np.percentile(s_lat, 50)), "p99_s": float(np.percentile(s_lat, 99)),
-                   "service_ms_p50": float(np.percentile(svc, 50) * 1e3)},
-        "batched_closed": {"circuits_per_s": capacity, "wall_s": closed_s, "steps": steps_closed,
-                           "max_resident": resident, "mid_run_circuits_per_s": mid_rate},
-        "served": {"arrival_rate": rate, "circuits_per_s": R / (max(r.finished for r in opened) - arrivals[0]),
-                   "p50_s": p50, "p99_s": p99, "wall_s": open_s},
-        "speedup_circuits_per_s": capacity / (R / svc.sum()),
-        "peaks_equal_to_serial_c128": f"{same_peak}/{R}",
-        "differing_peaks_max_rel_prob_gap": max(rel) if rel else 0.0,
-        "differing_peaks_max_prob": max((max(x, y) for x, y in differ), default=0.0),
-        "served_results_equal_to_saturated_run": f"{same_open}/{R}",
-    }
+    ser = serial_c128(reqs, s, arrivals=arrivals)
+    s_lat = np.array([x["finish"] - a for x, a in zip(ser, arrivals)])
+    serial_cps = R / sum(x["svc"] for x in ser)
+    out = {"requests": R, "large_requests": sum(int(c.n == 56) for c in reqs), "budget_gb": 160,
+           "batched_closed": {"circuits_per_s": capacity, "wall_s": closed_s, "steps": steps_closed,
+                              "max_resident": resident},
+           "served": {"arrival_rate": rate, "circuits_per_s": R / (max(r.finished for r in opened) - arrivals[0]),
+                      "p50_s": p50, "p99_s": p99, "wall_s": open_s},
+           "serial_measured": {"circuits_per_s": serial_cps, "p50_s": float(np.percentile(s_lat, 50)),
+                               "p99_s": float(np.percentile(s_lat, 99)),
+                               "note": "the same arrival stream served one request at a time (queue grows: "
+                                       "arrivals exceed the serial capacity)"},
+           "speedup_circuits_per_s": capacity / serial_cps,
+           "served_results_equal_to_saturated_run": "%d/%d" % (
+               sum(int(a.peak_key == b.peak_key and a.peak_prob == b.peak_prob) for a, b in zip(opened, closed)), R)}
+    out.update(peaked_check(closed, ser, reqs))
+    return out
 
 
 def run_variant_ab(args, rank, dev, stream, steps=8):
     """Group-first (default: grouping by partition and merge) against
     group-first with a full radix sort and against expand-first (the paper's
     formulation: one record per term and output, sorted, then summed per
-    output) on the benchmark state at K terms: the same gates, alternating
-    blocks of steps, CUDA-event time per step (gate + truncation) on the
-    library's stream."""
+    output) on the n=40 brickwork state at 2^24 terms: the same gates,
+    alternating blocks of steps, CUDA-event time per step on the library's
+    stream."""
     import torch
-    from paper_2607_07816_b300 import circuits as C
     from paper_2607_07816_b300 import sv
-
-    circ = C.brickwork_n40(seed=SEED + rank, layers=LAYERS, K=args.K)
-    st = sv.SparseState(circ.n, args.K, 1.0, prec=sv.SV_C128, stream=stream.cuda_stream)
+    wl = WORKLOADS["brick40"]
+    circ = make_circuit(wl, rank)
+    st = sv.SparseState(circ.n, wl["K"], 1.0, prec=sv.SV_C128, stream=stream.cuda_stream)
     gi = 0
-    while gi < len(circ.gates) and st.num_terms() < args.K:
+    while gi < len(circ.gates) and st.num_terms() < wl["K"]:
         q, u = circ.gates[gi]
         st.apply_gate(q, u)
         st.truncate()
@@ -449,23 +660,21 @@ def run_variant_ab(args, rank, dev, stream, steps=8):
             ms[variant].append(e0.elapsed_time(e1) / (steps // 2))
     st.close()
     g, e, r = statistics.mean(ms[0]), statistics.mean(ms[1]), statistics.mean(ms[2])
-    return {"K": args.K, "steps_each": steps, "group_first_ms_per_step": round(g, 3),
+    return {"workload": "n40 brickwork at K=2^24", "steps_each": steps, "group_first_ms_per_step": round(g, 3),
             "group_first_radix_sort_ms_per_step": round(r, 3),
             "expand_first_ms_per_step": round(e, 3), "expand_over_group": round(e / g, 3),
             "radix_over_merge_grouping": round(r / g, 3)}
 
 
 def run_ring(args, dev, stream):
-    """The ring-connected u3/cz workload shaped like the paper's example
-    (44 qubits, 93 (u3, u3, cz) blocks walking the ring, their perturbed
-    mirror, X on a seeded hidden string: about 580 instructions), run whole
-    through the single-state complex128 path as given, after reordering and
-    fusion into 2-qubit blocks (one update and truncation per block), and
-    fused into blocks of up to 4 qubits: gates or blocks, wall time, and
-    whether the peak is the hidden string."""
+    """The ring-connected u3/cz workload shaped like the paper's example (44
+    qubits, 93 (u3, u3, cz) blocks walking the ring, their perturbed mirror,
+    X on a seeded hidden string: about 580 instructions), whole, as given,
+    after reordering and fusion into 2-qubit blocks, and fused into blocks of
+    up to 4 qubits: updates, wall time, and whether the peak is the hidden
+    string."""
     import torch
     from paper_2607_07816_b300 import fusion, qasm, sv
-
     c = qasm.sharp_peak_circuit(n=44, blocks=93, K=32)
     variants = {"as_given": c.gates, "reordered_fused2": fusion.prepare(c.gates, 2),
                 "fused4": fusion.fuse(c.gates, 4)}
@@ -488,74 +697,55 @@ def run_ring(args, dev, stream):
     return out
 
 
-def roofline(main, prec, peaks):
-    tot = main["totals"]
-    phases = main["phases"]
-    dom = max((p for p in phases if p != "other"), key=lambda p: phases[p][0])
-    ms, launches = phases[dom]
-    per_launch_s = ms / 1e3 / max(1, launches)
-    passes = tot["sort_passes"] / max(1, tot["steps"])
-    model = phase_model(dom, tot, prec, passes if dom == "sort" else 1)
-    bytes_per_launch = model["bytes"] / max(1, launches)
-    gbs = bytes_per_launch / per_launch_s / 1e9
-    hbm_frac = gbs / peaks["hbm_gbs"]
-    out = {"kernel": dom, "bound": "hbm", "achieved": round(gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-           "frac": round(hbm_frac, 4), "traffic": traffic_for(dom, bytes_per_launch),
-           "peak_src": f"{peaks['src']} copy bandwidth", "launch_ms": round(per_launch_s * 1e3, 4),
-           "launches": launches}
-    if model["flops"] > 0:
-        fp64_peak = SM_COUNT * FP64_FMA_PER_SM_CLK * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
-        tflops = model["flops"] / max(1, launches) / per_launch_s / 1e12
-        if tflops / fp64_peak > hbm_frac:
-            out.update({"bound": "alu", "achieved": round(tflops, 4), "peak": round(fp64_peak, 4),
-                        "unit": "TFLOP/s", "frac": round(tflops / fp64_peak, 4),
-                        "peak_src": "FP64 pipe: 148 SMs x 2 DFMA/clk x 2 flop x max SM clock",
-                        "hbm_frac": round(hbm_frac, 4)})
-    return out
-
-
-def traffic_for(kernel, alg_bytes):
-    """DRAM bytes per launch from the committed ncu summary, when it was
-    taken on the current kernel sources (else null)."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
-    if not os.path.exists(path):
-        return None
-    try:
-        d = json.load(open(path))
-        from paper_2607_07816_b300 import build as B
-        if d.get("source_hash") != B.source_hash():
-            return None
-        ent = d["kernels"].get(kernel)
-        if not ent:
-            return None
-        return ent["dram_bytes_per_unit"] * ent["units_per_launch_full"]
-    except Exception:
-        return None
-
-
-def gate_bytes_method(tot, prec):
-    sa = 16 if prec == "c128" else 8
-    S = 8 + sa
-    b = 2 * S * tot["n_in"] + S * (tot["n_in"] + tot["n_pre"]) + 8 * tot["n_pre"] + S * (tot["n_pre"] + tot["n_kept"])
-    strict = S * (tot["n_in"] + tot["n_kept"])
-    return b, strict
+def run_ours(args, rank, world):
+    import torch
+    from paper_2607_07816_b300 import sv
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    sv.load_library()
+    res = {"main": run_steps(args, rank, args.prec, dev, stream, sample_clocks=True)}
+    res["fp64_probe_tflops"] = round(sv.sv_probe_fp64(1 << 14, 4)[0], 4)
+    if not args.no_c64 and args.prec == "c128":
+        res["c64"] = run_steps(args, rank, "c64", dev, stream, sample_clocks=False)
+    if not args.no_whole:
+        w128, f128 = run_whole(args, rank, "c128", dev, stream)
+        res["whole"] = {"c128": w128}
+        if not args.no_c64:
+            w64, f64 = run_whole(args, rank, "c64", dev, stream)
+            res["whole"]["c64"] = w64
+            res["whole"]["c64_vs_c128"] = error_report(f128, f64, dev)
+            res["whole"]["c64_vs_c128"]["peak_identical"] = w64["peak_key"] == w128["peak_key"]
+            del f64
+        del f128
+    if not args.no_e2e:
+        res["e2e"] = run_e2e(args, rank, dev, stream)
+    if args.batch_circuits > 0:
+        res["batched"] = run_batched(args, rank, dev, stream)
+    if args.serve_requests > 0:
+        res["serving"] = run_serving(args, rank, dev, stream)
+    if not args.no_ring:
+        res["ring"] = run_ring(args, dev, stream)
+    if not args.no_ab:
+        res["variant_ab"] = run_variant_ab(args, rank, dev, stream)
+    return res
 
 
 # ------------------------------------------------------------------ CPU / reference arm
-def oracle_sample(seconds: float, K_cap: int, max_gates: int = 10 ** 9):
-    """The oracle as it stands, single-threaded, on the same circuit from
-    |0...0>, gate after gate until `seconds` of CPU work have elapsed."""
+def oracle_sample(wl, seconds: float, max_gates: int = 10 ** 9):
+    """The oracle as it stands, single-threaded, on the same circuit and K
+    from |0...0>, gate after gate until `seconds` of CPU work have elapsed
+    (the first gates: the state has not reached K within the sample)."""
     import oracle
-    from paper_2607_07816_b300 import circuits as C
-    circ = C.brickwork_n40(seed=SEED, layers=LAYERS, K=K_cap)
-    o = oracle.Oracle(circ.n, K_cap, 1.0)
+    circ = make_circuit(wl)
+    o = oracle.Oracle(circ.n, wl["K"], wl["p"])
     n_in, g = 0, 0
     t0 = time.perf_counter()
     last = 0.0
     while g < min(len(circ.gates), max_gates):
-        # stop before a gate that would overrun the budget (each brickwork
-        # gate can multiply the term count by 4 until K is reached)
-        if g > 0 and time.perf_counter() - t0 + 4.5 * last > seconds:
+        # stop before a gate that would overrun the budget (a gate can
+        # multiply the term count by up to 16)
+        if g > 0 and time.perf_counter() - t0 + 8 * last > seconds:
             break
         tg = time.perf_counter()
         q, u = circ.gates[g]
@@ -567,31 +757,36 @@ def oracle_sample(seconds: float, K_cap: int, max_gates: int = 10 ** 9):
         last = time.perf_counter() - tg
     dt = time.perf_counter() - t0
     return {"value": n_in / dt, "unit": "terms/s", "cores": 1, "kind": "oracle",
-            "sample": f"{WORKLOAD.split(',')[0]}: gates 1..{g} from |0>, K capped at {K_cap}, "
-                      f"{n_in} input terms in {dt:.1f} s (single-threaded C++ std::map oracle)"}
+            "sample": f"{wl['desc']}: gates 1..{g} from |0> ({n_in} input terms, largest state "
+                      f"{o.num_terms()} terms) in {dt:.1f} s, single-threaded C++ std::map oracle"}
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return None
     import oracle  # noqa: F401  (builds the oracle if needed)
+    wl = args.wl
     per = []
-    total_terms, total_t = 0, 0.0
     for i in range(args.warmup + args.steps):
-        s = oracle_sample(seconds=1.0, K_cap=1 << 14, max_gates=40)
+        s = oracle_sample(wl, seconds=1.0)
         if i >= args.warmup:
             per.append(s)
-    vals = [p["value"] for p in per]
-    v = statistics.mean(vals)
+    v = statistics.mean(p["value"] for p in per)
     line = {"metric": "sparse-gate terms/s", "value": v, "unit": "terms/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "impl": "reference",
-            "config": {"workload": WORKLOAD, "n": N_QUBITS, "K": args.K, "p": 1.0, "prec": "c128"},
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": config_of(args, world),
             "cpu_baseline": {"value": v, "unit": "terms/s", "cores": 1, "kind": "oracle",
                              "sample": "each step: " + per[0]["sample"]},
             "e2e": {"value": v, "unit": "terms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     return line
+
+
+def config_of(args, world):
+    wl = args.wl
+    return {"workload": wl["desc"], "n": wl["n"], "K": wl["K"], "p": wl["p"], "prec": args.prec,
+            "seed": wl["seed"], "l2": "state larger than L2 (no flush needed)",
+            "parallelism": "replicas" if world > 1 else "single GPU"}
 
 
 def main():
@@ -606,57 +801,54 @@ def main():
     import torch
     if world > 1:
         torch.distributed.init_process_group("nccl")
-    res, peaks = run_ours(args, rank, world)
+    peaks = measured_peaks()
+    res = run_ours(args, rank, world)
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
         return
-    main_r = res["main"]
-    tot = main_r["totals"]
-    ms = main_r["ms"]
-    value = main_r["rate"]
-    bm, bstrict = gate_bytes_method(tot, args.prec)
+    m = res["main"]
+    tot = m["totals"]
+    ms = m["ms"]
     bw = peaks["hbm_gbs"] * 1e9
     line = {
-        "metric": "sparse-gate terms/s", "value": value, "unit": "terms/s", "n_gpus": world,
+        "metric": "sparse-gate terms/s", "value": m["rate"], "unit": "terms/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.prec == "c128" else "f32",
-        "data": "synthetic (seeded Haar brickwork mirror circuit)",
-        "config": {"workload": WORKLOAD, "n": N_QUBITS, "K": args.K, "p": 1.0, "prec": args.prec,
-                   "layers": LAYERS, "seed": SEED, "l2": "state larger than L2 (no flush needed)",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": roofline(main_r, args.prec, peaks),
-        "gate_roofline": {"B_method_frac": round(bm / (ms / 1e3) / bw, 4),
-                          "B_strict_frac": round(bstrict / (ms / 1e3) / bw, 4),
+        "data": "synthetic (seeded random-mix mirror circuit)" if args.wl["n"] == 60
+        else "synthetic (seeded Haar brickwork mirror circuit)",
+        "config": config_of(args, world),
+        "roofline": roofline(m, args.prec, peaks, res["fp64_probe_tflops"]),
+        "gate_roofline": {"B_method_frac": round(tot["B_method"] / (ms / 1e3) / bw, 4),
+                          "B_strict_frac": round(tot["B_strict"] / (ms / 1e3) / bw, 4),
                           "peak_gbs": peaks["hbm_gbs"]},
-        "phases_ms": {k: round(v[0], 3) for k, v in main_r["phases"].items()},
-        "phase_launches": {k: v[1] for k, v in main_r["phases"].items()},
-        "gpu_launches": main_r["launches"],
-        "clocks": main_r["clocks"],
-        "peak_key": main_r["peak"][0],
-        "totals": {k: (v if k.startswith("fp64") else int(v)) for k, v in tot.items()},
-        "gate_paths": main_r.get("paths"),
+        "phases_ms": {k: round(v[0], 3) for k, v in m["phases"].items()},
+        "phase_launches": {k: v[1] for k, v in m["phases"].items()},
+        "gpu_launches": m["launches"],
+        "clocks": m["clocks"],
+        "fp64_probe_tflops": res["fp64_probe_tflops"],
+        "timed_gates": m["timed_gates"], "first_full_gate": m["first_full_gate"],
+        "totals": {k: (round(v) if isinstance(v, float) else v) for k, v in tot.items()},
+        "gate_paths": m["paths"],
     }
     if "c64" in res:
         c = res["c64"]
         ct = c["totals"]
-        cb, _ = gate_bytes_method(ct, "c64")
         line["c64"] = {"value": c["rate"], "unit": "terms/s", "ms_per_step": c["ms"] / args.steps,
-                       "B_method_frac": round(cb / (c["ms"] / 1e3) / bw, 4),
-                       "roofline": roofline(c, "c64", peaks),
+                       "B_method_frac": round(ct["B_method"] / (c["ms"] / 1e3) / bw, 4),
+                       "roofline": roofline(c, "c64", peaks, res["fp64_probe_tflops"]),
                        "phases_ms": {k: round(v[0], 3) for k, v in c["phases"].items()}}
-    if "e2e" in res:
-        line["e2e"] = res["e2e"]
-    if "serving" in res:
-        line["serving"] = res["serving"]
-    if "ring" in res:
-        line["ring_u3cz"] = res["ring"]
-    if "variant_ab" in res:
-        line["apply_variant_ab"] = res["variant_ab"]
+    if "whole" in res:
+        line["whole_circuit"] = res["whole"]
+        if "c64" in line and "c64_vs_c128" in res["whole"]:
+            line["c64"]["error_vs_c128_whole_circuit"] = res["whole"]["c64_vs_c128"]
+    for key, name in (("e2e", "e2e"), ("batched", "batched"), ("serving", "serving"), ("ring", "ring_u3cz"),
+                      ("variant_ab", "apply_variant_ab")):
+        if key in res:
+            line[name] = res[key]
     if not args.no_cpu and world == 1:
-        line["cpu_baseline"] = oracle_sample(seconds=15.0, K_cap=args.K)
-        line["cpu_baseline"]["cores"] = 1
+        line["cpu_baseline"] = oracle_sample(args.wl, seconds=15.0)
     print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
