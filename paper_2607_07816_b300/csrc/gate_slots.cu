@@ -278,14 +278,20 @@ __global__ void __launch_bounds__(AS_BLOCK) k_gate_apply_slots(
   constexpr int gpl = GPL;
   typedef typename SCplx<Real>::T C2;
   extern __shared__ __align__(16) uint8_t s_dyn[];
-  __shared__ Real sU[512];
+  // U with its rows padded to d + 1 entries: the lanes of a round read
+  // U[r'][r] for different r' and mostly the same r, which the padding puts
+  // in different banks
+  __shared__ Real sU[2 * 16 * 17];
   __shared__ uint32_t s_re_nz[16], s_im_nz[16];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t lt = (1u << lane) - 1u;
   const int m = gp.m, d = 1 << m, vb = gp.vbits, shift = m + vb;
   const uint32_t gc = 32u * gpl, mc = gc << m;
   SlotsLayout<C2> w(s_dyn + (size_t)warp * SlotsLayout<C2>::bytes(gc, mc), gc, mc);
-  for (int i = tid; i < 2 * d * d; i += AS_BLOCK) sU[i] = (Real)gp.U[i];
+  for (int i = tid; i < 2 * d * d; i += AS_BLOCK) {
+    const int e = i >> 1, ro = e >> m, r = e & (d - 1);
+    sU[2 * (ro * (d + 1) + r) + (i & 1)] = (Real)gp.U[i];
+  }
   if (tid < 16) {
     s_re_nz[tid] = gp.re_nz[tid];
     s_im_nz[tid] = gp.im_nz[tid];
@@ -428,7 +434,7 @@ __global__ void __launch_bounds__(AS_BLOCK) k_gate_apply_slots(
           const int r = __ffs(cols) - 1;
           cols &= cols - 1u;
           const C2 x = w.x[mb_g + __popc(pm_g & ((1u << r) - 1u))];
-          const Real ur = sU[2 * (ro * d + r)], ui = sU[2 * (ro * d + r) + 1];
+          const Real ur = sU[2 * (ro * (d + 1) + r)], ui = sU[2 * (ro * (d + 1) + r) + 1];
           if ((rnz >> r) & 1u) {
             re = sfma(ur, x.x, re);
             im = sfma(ur, x.y, im);

@@ -334,18 +334,21 @@ __global__ void __launch_bounds__(MG_THREADS, 4) k_merge_level(const uint64_t* _
     for (int j = 0; j < MG_ITEMS; ++j) {
       const uint32_t e = (uint32_t)tid + (uint32_t)j * MG_THREADS;
       if (e < len) {
-        s_k[e] = r[j];
-        if (PAIRS) s_v[e] = rv[j];
+        s_k[mg_pad(e)] = r[j];
+        if (PAIRS) s_v[mg_pad(e)] = rv[j];
       }
     }
   }
   __syncthreads();
-  // this thread's outputs: [diag, diag + MG_ITEMS) of the block's slice
+  // this thread's outputs: [diag, diag + MG_ITEMS) of the block's slice.
+  // Both slices sit in shared memory at padded positions (one gap per 16
+  // elements): neighbouring threads read A or B at strides of about 4 or 8
+  // elements, which the padding spreads over distinct banks.
   const uint32_t diag = min((uint32_t)tid * MG_ITEMS, len);
   uint32_t lo = diag > nb ? diag - nb : 0u, hi = diag < na ? diag : na;
   while (lo < hi) {
     const uint32_t mid = (lo + hi) >> 1;
-    if (s_k[mid] <= s_k[na + diag - 1 - mid])
+    if (s_k[mg_pad(mid)] <= s_k[mg_pad(na + diag - 1 - mid)])
       lo = mid + 1;
     else
       hi = mid;
@@ -353,19 +356,23 @@ __global__ void __launch_bounds__(MG_THREADS, 4) k_merge_level(const uint64_t* _
   uint32_t pa = lo, pb = diag - lo;
   uint64_t ok[MG_ITEMS];
   uint32_t ov[MG_ITEMS];
+  uint64_t ka = pa < na ? s_k[mg_pad(pa)] : 0ull, kb = pb < nb ? s_k[mg_pad(na + pb)] : 0ull;
 #pragma unroll
   for (int j = 0; j < MG_ITEMS; ++j) {
     ok[j] = 0;
     ov[j] = 0;
     if (diag + j < len) {
-      const bool take_a = pb >= nb || (pa < na && s_k[pa] <= s_k[na + pb]);
+      const bool take_a = pb >= nb || (pa < na && ka <= kb);
       const uint32_t src = take_a ? pa : na + pb;
-      ok[j] = s_k[src];
-      if (PAIRS) ov[j] = s_v[src];
-      if (take_a)
+      ok[j] = take_a ? ka : kb;
+      if (PAIRS) ov[j] = s_v[mg_pad(src)];
+      if (take_a) {
         ++pa;
-      else
+        if (pa < na) ka = s_k[mg_pad(pa)];
+      } else {
         ++pb;
+        if (pb < nb) kb = s_k[mg_pad(na + pb)];
+      }
     }
   }
   __syncthreads();

@@ -63,7 +63,9 @@ _lib = None
 
 
 def lib_path() -> str:
-    return _build.LIB
+    """The library loaded: $SV_LIBRARY when set (another build of the same
+    sources, e.g. for A/B timing), else libsv.so in the package directory."""
+    return os.environ.get("SV_LIBRARY") or _build.LIB
 
 
 def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
@@ -71,7 +73,9 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.LIB
+    path = lib_path()
+    if path != _build.LIB and not os.path.exists(path):
+        raise OSError(f"SV_LIBRARY={path} does not exist")
     if not os.path.exists(path):
         if not build_if_missing:
             raise OSError(f"libsv.so not found at {path}")
