@@ -136,6 +136,32 @@ sv_status sv_export(sv_state* s, uint64_t* keys, double* amps, uint64_t cap, uin
  * stored; complex64 handles round each component to float. */
 sv_status sv_load(sv_state* s, const uint64_t* keys, const double* amps, uint64_t N);
 
+/* Primitives for one state held in several handles (one per GPU, each with
+ * the terms of one partition of the basis states): the truncation of
+ * Sec. III taken over the union of the handles' terms.  The canonical order
+ * is that of the composite Z = (~prob_bits, natural key) read as a 128-bit
+ * integer (ascending Z = probability descending, key ascending).
+ *
+ * sv_select_histogram: among this handle's terms whose Z agrees with
+ * (prefix_hi, prefix_lo) on its top `bits` bits (0 <= bits <= 127), the
+ * count and the exact fixed-point mass (floor(prob * 2^120) summed, as
+ * hi, lo words) per value of the next D = min(11, 128 - bits) bits of Z:
+ * counts[2048] and masses[2 * 2048] (bins >= 2^D stay zero).  Summed over
+ * the handles, the levels of a radix select find the cut.  bits = 0 gives
+ * the whole state's mass split by the top digit.  Synchronises. */
+sv_status sv_select_histogram(sv_state* s, uint64_t prefix_hi, uint64_t prefix_lo, int bits, uint32_t* counts,
+                              uint64_t* masses);
+
+/* Keep this handle's terms whose Z is at most (z_hi, z_lo), in order, scaled
+ * by 1 / sqrt(double(S_c)), and multiply the retained product by
+ * double(S_c) / double(S_N), where S_c = (sc_hi, sc_lo) and
+ * S_N = (sn_hi, sn_lo) are the kept and the total fixed-point masses of all
+ * the handles together (the rule of sv_truncate, with the cut and the
+ * masses decided across handles).  *kept (nullable) receives this handle's
+ * terms left.  SV_E_ARG for a zero mass.  Synchronises. */
+sv_status sv_cut(sv_state* s, uint64_t z_hi, uint64_t z_lo, uint64_t sc_hi, uint64_t sc_lo, uint64_t sn_hi,
+                 uint64_t sn_lo, uint64_t* kept);
+
 /* Human-readable description of the last failure on this handle (never
  * NULL; empty when there was none). */
 const char* sv_last_error(const sv_state* s);

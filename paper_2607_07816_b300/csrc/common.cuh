@@ -52,6 +52,7 @@ struct Ctl {
   uint64_t above_count;                    // terms with probability > hi
   uint64_t above_mass_hi, above_mass_lo;
   uint64_t win_mass_hi, win_mass_lo;
+  uint64_t below_mass_hi, below_mass_lo;   // terms below the window (pass with a known total, by mass)
   uint32_t use_window;                     // 1: select over the window, 0: over all terms
   uint32_t sel_gated;                      // 1: select kernels decide on the device which of them run
   uint64_t kept_check;                     // terms the last truncation wrote (checked at the next wait)

@@ -286,6 +286,10 @@ void launch_truncate_compact(int prec, const uint64_t* keys, const void* amps, c
                              uint32_t* peak_blocks);
 void launch_peak_partials(const uint64_t* part, uint32_t n, Ctl* ctl, cudaStream_t st);
 void launch_set_scale(Ctl* ctl, cudaStream_t st);
+// Select state of one histogram level over all terms (prefix of `bits` fixed
+// composite bits), and a cut at the composite (~pc, kc) with kept mass S_c.
+void launch_set_select(Ctl* ctl, uint64_t ph, uint64_t pl, uint32_t bits, cudaStream_t st);
+void launch_set_cut(Ctl* ctl, uint64_t pc, uint64_t kc, uint64_t sc_hi, uint64_t sc_lo, cudaStream_t st);
 
 // Readout.
 void launch_peak(const uint64_t* probs, const uint64_t* keys, uint64_t n, Ctl* ctl, cudaStream_t st);

@@ -877,6 +877,7 @@ sv_status run_select(sv_state* s, int mode, uint64_t count_target, uint32_t* lev
   ph_begin(s, PH_WINDOW);
   launch_select_window(s->probs[s->cur], s->keys[s->cur], N, s->ctl, s->ss, mode, count_target, s->p, s->total_ready,
                        s->st);
+  s->total_ready = true;  // the pass summed the total when it was not known: a second select reuses it
   ph_end(s, PH_WINDOW);
   launched(s, PH_WINDOW, 3);
   // Two levels and the finish are enqueued behind the window without a host
@@ -1026,6 +1027,60 @@ sv_status sv_truncate(sv_state* s, uint64_t* kept, double* retained_fraction) {
   s->stats.n_kept = s->N;
   if (kept) *kept = s->N;
   if (retained_fraction) *retained_fraction = f;
+  return SV_OK;
+}
+
+sv_status sv_select_histogram(sv_state* s, uint64_t prefix_hi, uint64_t prefix_lo, int bits, uint32_t* counts,
+                              uint64_t* masses) {
+  SV_GUARD(s);
+  if (bits < 0 || bits > 127 || !counts || !masses) return fail(s, SV_E_ARG, "sv_select_histogram: bad arguments");
+  std::memset(counts, 0, sizeof(uint32_t) * SEL_BINS);
+  std::memset(masses, 0, sizeof(uint64_t) * 2 * SEL_BINS);
+  if (s->N == 0) return SV_OK;
+  // the histogram arrays arrive cleared (the pick of every select level
+  // clears them) and are cleared again after the copy
+  launch_set_select(s->ctl, prefix_hi, prefix_lo, (uint32_t)bits, s->st);
+  launch_select_hist(s->probs[s->cur], s->keys[s->cur], s->N, s->ctl, s->ss, s->st);
+  launched(s, PH_SELECT, 2);
+  cudaError_t e = cudaMemcpyAsync(counts, s->ss.hist_count, sizeof(uint32_t) * SEL_BINS, cudaMemcpyDeviceToHost, s->st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(masses, s->ss.hist_mass, sizeof(uint64_t) * 2 * SEL_BINS, cudaMemcpyDeviceToHost, s->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->ss.hist_count, 0, sizeof(uint32_t) * SEL_BINS, s->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->ss.hist_mass, 0, sizeof(uint64_t) * 2 * SEL_BINS, s->st);
+  g_d2h += sizeof(uint32_t) * SEL_BINS + sizeof(uint64_t) * 2 * SEL_BINS;
+  sv_status rc = cuda_check(s, e, "sv_select_histogram");
+  if (rc != SV_OK) return rc;
+  return sync_ctl(s, "sv_select_histogram");
+}
+
+sv_status sv_cut(sv_state* s, uint64_t z_hi, uint64_t z_lo, uint64_t sc_hi, uint64_t sc_lo, uint64_t sn_hi,
+                 uint64_t sn_lo, uint64_t* kept) {
+  SV_GUARD(s);
+  if ((sc_hi | sc_lo) == 0 || (sn_hi | sn_lo) == 0) return fail(s, SV_E_ARG, "sv_cut: zero mass");
+  const double Sc = u128_to_double(sc_hi, sc_lo), SN = u128_to_double(sn_hi, sn_lo);
+  s->peak_ready = false;
+  s->total_ready = false;
+  const uint64_t N = s->N;
+  if (N > 0) {
+    const int alt = 1 - s->cur;
+    sv_status rc = ensure_lookback(s, (N + 1023) / 1024 + 16);
+    if (rc != SV_OK) return rc;
+    ph_begin(s, PH_COMPACT);
+    launch_set_cut(s->ctl, ~z_hi, z_lo, sc_hi, sc_lo, s->st);
+    launch_set_scale(s->ctl, s->st);
+    launch_truncate_compact(s->prec, s->keys[s->cur], s->amps[s->cur], s->probs[s->cur], N, s->keys[alt],
+                            s->amps[alt], s->probs[alt], s->lookback, s->ctl, s->st, s->peak_part, &s->peak_blocks);
+    ph_end(s, PH_COMPACT);
+    launched(s, PH_COMPACT, 3);
+    rc = sync_ctl(s, "sv_cut");
+    if (rc != SV_OK) return rc;
+    s->cur = alt;
+    s->N = s->ctl_host->count[2];
+    s->peak_ready = s->peak_blocks > 0 && s->N > 0;
+  }
+  s->F = s->F * (Sc / SN);
+  s->stats.n_kept = s->N;
+  if (kept) *kept = s->N;
   return SV_OK;
 }
 

@@ -242,7 +242,8 @@ __device__ void block_select_two(const uint32_t* a, const int* r, uint32_t* hist
 // the work: the cut found afterwards is the exact one either way.
 __global__ void __launch_bounds__(SAMPLE_THREADS) k_sample_window(const uint64_t* __restrict__ probs,
                                                                   uint64_t n, Ctl* ctl, int mode,
-                                                                  uint64_t count_target, double p, bool light) {
+                                                                  uint64_t count_target, double p,
+                                                                  bool total_known) {
   pdl_prologue();
   extern __shared__ __align__(16) uint8_t s_dyn[];
   uint32_t* a = reinterpret_cast<uint32_t*>(s_dyn);
@@ -252,8 +253,8 @@ __global__ void __launch_bounds__(SAMPLE_THREADS) k_sample_window(const uint64_t
   __shared__ uint32_t dsum[256], wtot[32];
   __shared__ int s_rank;
   const int tid = threadIdx.x;
-  if (tid < 6) (&ctl->win_n)[tid] = 0;  // win_n .. win_mass_lo, summed by the window pass
-  if (!light && tid == 0) ctl->total_mass_hi = ctl->total_mass_lo = 0;  // the pass sums the total too
+  if (tid < 8) (&ctl->win_n)[tid] = 0;  // win_n .. below_mass_lo, summed by the window pass
+  if (!total_known && tid == 0) ctl->total_mass_hi = ctl->total_mass_lo = 0;  // the pass sums the total too
   // stratified random sample: one term at a hashed offset inside each of
   // SAMPLE_N equal strata (a fixed stride would alias with the 2^m-periodic
   // layout of the candidates)
@@ -302,31 +303,49 @@ __global__ void __launch_bounds__(SAMPLE_THREADS) k_sample_window(const uint64_t
   }
   block_sort_samples(a, tmp, whist, dsum, wtot);  // 4 passes: result back in a
   {
+    // the sample rank where the sorted sample's mass first reaches p of its
+    // total: a block-wide scan of the threads' 8-value sums, then the one
+    // thread whose range holds the crossing walks its values (a steering
+    // estimate in double; the exact cut is found afterwards)
     constexpr int PER = SAMPLE_N / SAMPLE_THREADS;
-    double loc = 0.0;
-    for (int k = 0; k < PER; ++k)
-      loc += __longlong_as_double((long long)~(((uint64_t)a[tid * PER + k] << 31) | (1ull << 63)));
-    pre[tid] = loc;
+    const int lane = tid & 31, warp = tid >> 5;
+    double v[PER], loc = 0.0;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      v[k] = __longlong_as_double((long long)~(((uint64_t)a[tid * PER + k] << 31) | (1ull << 63)));
+      loc += v[k];
+    }
+    double x = loc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const double y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) pre[warp] = x;
+    if (tid == 0) s_rank = SAMPLE_N - 1;
     __syncthreads();
-    if (tid == 0) {
-      double tot = 0.0;
-      for (int t = 0; t < SAMPLE_THREADS; ++t) tot += pre[t];
-      double goal = p * tot, acc = 0.0;
-      int r = SAMPLE_N - 1;
-      for (int t = 0; t < SAMPLE_THREADS; ++t) {
-        if (acc + pre[t] >= goal) {
-          for (int k = 0; k < PER; ++k) {
-            acc += __longlong_as_double((long long)~(((uint64_t)a[t * PER + k] << 31) | (1ull << 63)));
-            if (acc >= goal) {
-              r = t * PER + k;
-              break;
-            }
-          }
+    if (warp == 0) {
+      double w = pre[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const double y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += y;
+      }
+      pre[32 + lane] = w;  // inclusive over the warps
+    }
+    __syncthreads();
+    const double total = pre[32 + 31];
+    const double goal = p * total;
+    double acc = (warp > 0 ? pre[32 + warp - 1] : 0.0) + x - loc;  // mass before this thread's values
+    if (acc < goal && acc + loc >= goal) {
+#pragma unroll
+      for (int k = 0; k < PER; ++k) {
+        acc += v[k];
+        if (acc >= goal) {
+          atomicMin(&s_rank, tid * PER + k);
           break;
         }
-        acc += pre[t];
       }
-      s_rank = r;
     }
   }
   __syncthreads();
@@ -364,8 +383,11 @@ struct WindowStage {
   uint64_t base;
 };
 
+// With SUM the flushing threads also add the masses of the terms they copy
+// (the window mass of the pass with a known total).
+template <bool SUM>
 __device__ __forceinline__ void window_flush(WindowStage& st, Ctl* ctl, uint64_t* __restrict__ wp,
-                                             uint32_t* __restrict__ wi, uint64_t cap) {
+                                             uint32_t* __restrict__ wi, uint64_t cap, u128& wsum) {
   // all threads call it; st.n is block-uniform
   const uint32_t cnt = st.n;
   if (cnt == 0) return;
@@ -374,6 +396,7 @@ __device__ __forceinline__ void window_flush(WindowStage& st, Ctl* ctl, uint64_t
   const uint64_t b = st.base;
   for (uint32_t j = threadIdx.x; j < cnt; j += WP_BLOCK) {
     const uint64_t o = b + j;
+    if (SUM) wsum += fx_from_bits(st.p[j], &ctl->err);
     if (o < cap) {
       wp[o] = st.p[j];
       wi[o] = st.i[j];
@@ -384,11 +407,20 @@ __device__ __forceinline__ void window_flush(WindowStage& st, Ctl* ctl, uint64_t
   __syncthreads();
 }
 
-// LIGHT (a top-K cut after a mat-vec that summed the total mass): no
-// per-term total; the masses of the terms above the window, about a third of
-// them, are summed from a per-warp queue of their probabilities, so the
-// 128-bit conversions run on full warps of above-window terms only.
-template <bool LIGHT>
+// MODE (how the exact masses are summed):
+//   WP_FULL  every term converted: the total, above-window and window masses;
+//   WP_ABOVE a top-K cut with the total already known (summed by the gate):
+//            only the masses above the window, from a per-warp queue of their
+//            probabilities, so the 128-bit conversions run on full warps of
+//            above-window terms only;
+//   WP_BELOW a p-mass cut with the total known: the window and below-window
+//            masses (the window terms converted while they are written out,
+//            the others through the queue); the mass above the window is the
+//            total minus those two, formed exactly by the decision kernel.
+//            At p near 1 the window sits in the light tail, so few terms are
+//            converted.
+constexpr int WP_FULL = 0, WP_ABOVE = 1, WP_BELOW = 2;
+template <int MODE>
 __global__ void __launch_bounds__(WP_BLOCK, 4) k_window_pass(const uint64_t* __restrict__ probs,
                                                           uint64_t n, Ctl* ctl, uint64_t* __restrict__ wp,
                                                           uint32_t* __restrict__ wi,
@@ -401,12 +433,13 @@ __global__ void __launch_bounds__(WP_BLOCK, 4) k_window_pass(const uint64_t* __r
   __shared__ uint32_t s_acc;
   __shared__ uint64_t s_direct;
   __shared__ WindowStage st;
-  __shared__ uint64_t s_aq[LIGHT ? WP_BLOCK / 32 : 1][64];  // per-warp ring of above-window probabilities
+  constexpr bool QUEUE = MODE != WP_FULL;
+  __shared__ uint64_t s_aq[QUEUE ? WP_BLOCK / 32 : 1][64];  // per-warp ring of probabilities to convert
   const uint64_t hi = ctl->win_hi, lo = ctl->win_lo;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt = (1u << lane) - 1u;
   if (threadIdx.x == 0) st.n = 0;
-  u128 tot = 0, above_m = 0, win_m = 0;
+  u128 tot = 0, above_m = 0, win_m = 0;  // WP_BELOW: above_m holds the mass below the window
   uint64_t above_c = 0;
   uint32_t q_head = 0, q_n = 0;  // warp-uniform ring state
   const uint64_t tiles = (n + L::TILE - 1) / L::TILE;
@@ -419,7 +452,7 @@ __global__ void __launch_bounds__(WP_BLOCK, 4) k_window_pass(const uint64_t* __r
 #pragma unroll
     for (int j = 0; j < WP_ITEMS; ++j) pbv[j] = 32 * j < rem ? probs[e0 + 32 * j] : 0ull;  // all loads first
     uint32_t wmask = 0, run = 0, tile_above = 0;
-    if (LIGHT) {
+    if (QUEUE) {
       // tile_above and run are warp-wide counts (the same in every lane);
       // lane j keeps item j's keep-flag word (one flag per term above the
       // window: kept whatever the exact cut; window terms kept by the cut are
@@ -431,11 +464,13 @@ __global__ void __launch_bounds__(WP_BLOCK, 4) k_window_pass(const uint64_t* __r
         const bool valid = 32 * j < rem;
         const bool above = valid && pb > hi;
         const bool inwin = valid && !above && pb >= lo;
+        const bool queued = MODE == WP_ABOVE ? above : (valid && !above && !inwin);
         const uint32_t ab = __ballot_sync(0xffffffffu, above);
+        const uint32_t qb = MODE == WP_ABOVE ? ab : __ballot_sync(0xffffffffu, queued);
         if (lane == j) kbits = ab;
         tile_above += (uint32_t)__popc(ab);
-        if (above) s_aq[warp][(q_head + q_n + __popc(ab & lt)) & 63u] = pb;
-        q_n += __popc(ab);
+        if (queued) s_aq[warp][(q_head + q_n + __popc(qb & lt)) & 63u] = pb;
+        q_n += __popc(qb);
         if (q_n >= 32) {  // a full warp of queued terms: one conversion each
           __syncwarp();
           above_m += fx_from_bits(s_aq[warp][(q_head + lane) & 63u], &ctl->err);
@@ -498,7 +533,7 @@ __global__ void __launch_bounds__(WP_BLOCK, 4) k_window_pass(const uint64_t* __r
     const uint32_t acc = s_acc;
     if (acc == 0) continue;  // block-uniform
     const bool direct = acc > WP_STAGE;
-    if (!direct && st.n + acc > WP_STAGE) window_flush(st, ctl, wp, wi, cap);
+    if (!direct && st.n + acc > WP_STAGE) window_flush<MODE == WP_BELOW>(st, ctl, wp, wi, cap, win_m);
     const uint32_t sbase = st.n;
     uint32_t wrun = 0;  // window positions: the same ballots again, in item order
 #pragma unroll
@@ -510,6 +545,7 @@ __global__ void __launch_bounds__(WP_BLOCK, 4) k_window_pass(const uint64_t* __r
       if (inwin) {
         const uint64_t i = e0 + 32 * j;
         if (direct) {
+          if (MODE == WP_BELOW) win_m += fx_from_bits(pbv[j], &ctl->err);
           const uint64_t o = s_direct + wpos;
           if (o < cap) {
             wp[o] = pbv[j];
@@ -525,8 +561,8 @@ __global__ void __launch_bounds__(WP_BLOCK, 4) k_window_pass(const uint64_t* __r
     if (!direct && threadIdx.x == 0) st.n = sbase + acc;
     __syncthreads();
   }
-  window_flush(st, ctl, wp, wi, cap);
-  if (LIGHT) {  // the queue's rest
+  window_flush<MODE == WP_BELOW>(st, ctl, wp, wi, cap, win_m);
+  if (QUEUE) {  // the queue's rest
     __syncwarp();
     if ((uint32_t)lane < q_n) above_m += fx_from_bits(s_aq[warp][(q_head + lane) & 63u], &ctl->err);
   }
@@ -536,8 +572,11 @@ __global__ void __launch_bounds__(WP_BLOCK, 4) k_window_pass(const uint64_t* __r
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) above_c += __shfl_xor_sync(0xffffffffu, (unsigned long long)above_c, o);
   if (lane == 0) {
-    if (!LIGHT) atomic_add_u128(&ctl->total_mass_hi, &ctl->total_mass_lo, tot);
-    atomic_add_u128(&ctl->above_mass_hi, &ctl->above_mass_lo, above_m);
+    if (MODE == WP_FULL) atomic_add_u128(&ctl->total_mass_hi, &ctl->total_mass_lo, tot);
+    if (MODE == WP_BELOW)
+      atomic_add_u128(&ctl->below_mass_hi, &ctl->below_mass_lo, above_m);
+    else
+      atomic_add_u128(&ctl->above_mass_hi, &ctl->above_mass_lo, above_m);
     atomic_add_u128(&ctl->win_mass_hi, &ctl->win_mass_lo, win_m);
     atomicAdd((unsigned long long*)&ctl->above_count, (unsigned long long)above_c);
   }
@@ -545,9 +584,16 @@ __global__ void __launch_bounds__(WP_BLOCK, 4) k_window_pass(const uint64_t* __r
 
 // One thread: choose between the window and the full list and set up the
 // select state (target from the exact total mass).
-__global__ void k_window_decide(Ctl* ctl, int mode, uint64_t count_target, double p, uint64_t cap, uint64_t n) {
+__global__ void k_window_decide(Ctl* ctl, int mode, uint64_t count_target, double p, uint64_t cap, uint64_t n,
+                                int pass_mode) {
   pdl_prologue();
   const u128 total = make_u128(ctl->total_mass_hi, ctl->total_mass_lo);
+  if (pass_mode == WP_BELOW) {  // the mass above the window: the total less the window and below it
+    const u128 am = total - make_u128(ctl->win_mass_hi, ctl->win_mass_lo) -
+                    make_u128(ctl->below_mass_hi, ctl->below_mass_lo);
+    ctl->above_mass_hi = (uint64_t)(am >> 64);
+    ctl->above_mass_lo = (uint64_t)am;
+  }
   u128 target;
   if (mode == 0) {
     double T = __dmul_rn(p, fx_to_double(total));
@@ -595,22 +641,27 @@ cudaError_t select_prepare() {
 void launch_select_window(const uint64_t* probs, const uint64_t* keys, uint64_t n, Ctl* ctl,
                           const SelectScratch& ss, int mode, uint64_t count_target, double p,
                           bool have_total, cudaStream_t st) {
-  const bool light = have_total && mode == 1;
+  // with the total known (summed by the gate, or by the pass of an earlier
+  // select on the same terms) the pass converts only the smaller side
+  const int pmode = !have_total ? WP_FULL : (mode == 1 ? WP_ABOVE : WP_BELOW);
   const size_t smem = SAMPLE_SMEM;
   // the handle's creation checked the set-up on this device; without it the
   // launch fails and the next wait reports the launch error
   (void)select_prepare();
-  launch_pdl(k_sample_window, 1, SAMPLE_THREADS, smem, st, probs, n, ctl, mode, count_target, p, light);
+  launch_pdl(k_sample_window, 1, SAMPLE_THREADS, smem, st, probs, n, ctl, mode, count_target, p, have_total);
   uint64_t tiles = (n + WP_TILE - 1) / WP_TILE;
   uint64_t grid = tiles < 148 * 8 ? tiles : 148 * 8;
   if (grid == 0) grid = 1;
-  if (light)
-    launch_pdl(k_window_pass<true>, (unsigned)grid, WP_BLOCK, 0, st, probs, n, ctl, ss.win_p, ss.win_i, ss.win_cap,
-               ss.tile_keep, ss.keep_bits);
+  if (pmode == WP_ABOVE)
+    launch_pdl(k_window_pass<WP_ABOVE>, (unsigned)grid, WP_BLOCK, 0, st, probs, n, ctl, ss.win_p, ss.win_i,
+               ss.win_cap, ss.tile_keep, ss.keep_bits);
+  else if (pmode == WP_BELOW)
+    launch_pdl(k_window_pass<WP_BELOW>, (unsigned)grid, WP_BLOCK, 0, st, probs, n, ctl, ss.win_p, ss.win_i,
+               ss.win_cap, ss.tile_keep, ss.keep_bits);
   else
-    launch_pdl(k_window_pass<false>, (unsigned)grid, WP_BLOCK, 0, st, probs, n, ctl, ss.win_p, ss.win_i, ss.win_cap,
-               ss.tile_keep, ss.keep_bits);
-  launch_pdl(k_window_decide, 1, 1, 0, st, ctl, mode, count_target, p, ss.win_cap, n);
+    launch_pdl(k_window_pass<WP_FULL>, (unsigned)grid, WP_BLOCK, 0, st, probs, n, ctl, ss.win_p, ss.win_i,
+               ss.win_cap, ss.tile_keep, ss.keep_bits);
+  launch_pdl(k_window_decide, 1, 1, 0, st, ctl, mode, count_target, p, ss.win_cap, n, pmode);
 }
 
 uint64_t window_tiles(uint64_t n) { return (n + WP_TILE - 1) / WP_TILE; }
@@ -1023,6 +1074,35 @@ __global__ void k_set_scale(Ctl* ctl) {
 }
 
 void launch_set_scale(Ctl* ctl, cudaStream_t st) { launch_pdl(k_set_scale, 1, 1, 0, st, ctl); }
+
+// Select state for one histogram level over all terms (no window, not gated).
+__global__ void k_set_select(Ctl* ctl, uint64_t ph, uint64_t pl, uint32_t bits) {
+  pdl_prologue();
+  ctl->sel_prefix_hi = ph;
+  ctl->sel_prefix_lo = pl;
+  ctl->sel_bits = bits;
+  ctl->sel_done = 0;
+  ctl->sel_gated = 0;
+  ctl->use_window = 0;
+}
+
+void launch_set_select(Ctl* ctl, uint64_t ph, uint64_t pl, uint32_t bits, cudaStream_t st) {
+  launch_pdl(k_set_select, 1, 1, 0, st, ctl, ph, pl, bits);
+}
+
+// A cut given from outside: keep the terms not after the composite
+// (~pc, kc) in canonical order; S_c = (sc_hi, sc_lo).
+__global__ void k_set_cut(Ctl* ctl, uint64_t pc, uint64_t kc, uint64_t sc_hi, uint64_t sc_lo) {
+  pdl_prologue();
+  ctl->cut_pbits = pc;
+  ctl->cut_key = kc;
+  ctl->cut_mass_hi = sc_hi;
+  ctl->cut_mass_lo = sc_lo;
+}
+
+void launch_set_cut(Ctl* ctl, uint64_t pc, uint64_t kc, uint64_t sc_hi, uint64_t sc_lo, cudaStream_t st) {
+  launch_pdl(k_set_cut, 1, 1, 0, st, ctl, pc, kc, sc_hi, sc_lo);
+}
 
 constexpr int TC_BLOCK = 256, TC_ITEMS = 8;
 

@@ -28,7 +28,7 @@ EXPORTED = ["sv_create", "sv_create_ex", "sv_destroy", "sv_apply_gate", "sv_trun
             "svb_create", "svb_destroy", "svb_add", "svb_remove", "svb_step", "svb_num_terms",
             "svb_retained_mass", "svb_peak", "svb_export", "svb_last_error", "svb_set_autotune",
             "svb_autotune_stats", "svb_set_graphs", "svb_graph_stats", "sv_selftest", "sv_set_apply_variant",
-            "sv_probe_fp64"]
+            "sv_probe_fp64", "sv_select_histogram", "sv_cut"]
 PHASES = ["keys", "sort", "heads", "apply", "select", "compact", "peak", "other", "window", "local"]
 
 
@@ -154,6 +154,10 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.sv_selftest.argtypes = [i32, u64, u64, P(u64), P(u64)]
     lib.sv_probe_fp64.restype = i32
     lib.sv_probe_fp64.argtypes = [u64, i32, P(dbl), P(dbl)]
+    lib.sv_select_histogram.restype = i32
+    lib.sv_select_histogram.argtypes = [vp, u64, u64, i32, vp, vp]
+    lib.sv_cut.restype = i32
+    lib.sv_cut.argtypes = [vp, u64, u64, u64, u64, u64, u64, P(u64)]
     lib.sv_transfer_bytes.restype = None
     lib.sv_transfer_bytes.argtypes = [P(u64), P(u64)]
     _lib = lib
@@ -307,6 +311,35 @@ def sv_peak_noalloc(prec: int, keys_ptr: int, amps_ptr: int, n: int, stream: int
     return k.value, p.value
 
 
+SEL_BINS = 2048
+_M64 = (1 << 64) - 1
+
+
+def sv_select_histogram(h: int, prefix: int, bits: int):
+    """Counts (uint32[2048]) and exact fixed-point masses (Python ints, in
+    units of 2^-120) per value of the next digit of the composite
+    Z = (~prob_bits, natural key) among the terms whose top `bits` bits of Z
+    equal those of `prefix` (a 128-bit int)."""
+    counts = np.zeros(SEL_BINS, dtype=np.uint32)
+    masses = np.zeros(2 * SEL_BINS, dtype=np.uint64)
+    _check(h, load_library().sv_select_histogram(ctypes.c_void_p(h), ctypes.c_uint64(prefix >> 64),
+                                                 ctypes.c_uint64(prefix & _M64), int(bits),
+                                                 counts.ctypes.data, masses.ctypes.data))
+    hi, lo = masses[0::2], masses[1::2]
+    return counts, [(int(a) << 64) | int(b) for a, b in zip(hi, lo)]
+
+
+def sv_cut(h: int, z: int, S_c: int, S_N: int) -> int:
+    """Keep the terms with composite Z <= z, renormalised by the kept mass
+    S_c of all the handles together; S_N is their total mass (both exact
+    fixed-point ints).  Returns this handle's term count."""
+    kept = ctypes.c_uint64()
+    _check(h, load_library().sv_cut(ctypes.c_void_p(h), ctypes.c_uint64(z >> 64), ctypes.c_uint64(z & _M64),
+                                    ctypes.c_uint64(S_c >> 64), ctypes.c_uint64(S_c & _M64),
+                                    ctypes.c_uint64(S_N >> 64), ctypes.c_uint64(S_N & _M64), ctypes.byref(kept)))
+    return kept.value
+
+
 def sv_probe_fp64(iters: int = 1 << 16, blocks_per_sm: int = 4):
     """FP64 fused multiply-add throughput of the current device: (TFLOP/s, ms)."""
     tf, ms = ctypes.c_double(), ctypes.c_double()
@@ -398,6 +431,12 @@ class SparseState:
 
     def phase_times(self) -> dict:
         return sv_phase_times(self.h)
+
+    def select_histogram(self, prefix: int, bits: int):
+        return sv_select_histogram(self.h, prefix, bits)
+
+    def cut(self, z: int, S_c: int, S_N: int) -> int:
+        return sv_cut(self.h, z, S_c, S_N)
 
     def run(self, gates, truncate: bool = True):
         for (q, u) in gates:
