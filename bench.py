@@ -333,6 +333,9 @@ def run_steps(args, rank, prec_name, dev, stream, sample_clocks):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize(dev)
     g_start = gi
+    # checkpoint (untimed): the per-phase pass below replays the same gates
+    ck_keys, ck_amps = st.export()
+    torch.cuda.synchronize(dev)
     pending = None
     e0.record(stream)
     for _ in range(args.steps):
@@ -359,8 +362,12 @@ def run_steps(args, rank, prec_name, dev, stream, sample_clocks):
     clk = clocks.stop() if clocks else None
     barrier()
     rate, units_all, ms_all = whole_job_rate(tot["n_in"], ms)
-    # per-phase breakdown: as many further steps with CUDA events around each
-    # phase (events between the kernels of a step cost time of their own)
+    # per-phase breakdown: the same gates again from the checkpoint, with CUDA
+    # events around each phase (events between the kernels of a step cost
+    # time of their own, so they stay out of the timed loop)
+    st.load(ck_keys, ck_amps)
+    del ck_keys, ck_amps
+    gi = g_start
     st.set_timing(True)
     ph_tot = new_totals()
     for _ in range(args.steps):
@@ -377,7 +384,9 @@ def run_steps(args, rank, prec_name, dev, stream, sample_clocks):
     phases = st.phase_times()
     fin = st.stats()
     st.close()
+    phase_sum = sum(v[0] for v in phases.values())
     return {"ms": ms, "totals": tot, "phases": phases, "phase_totals": ph_tot, "launches": launches,
+            "phase_sum_ms": phase_sum,
             "clocks": clk, "rate": rate, "units_all": units_all, "first_full_gate": first_full,
             "timed_gates": [g_start, g_start + args.steps - 1],
             "paths": {k: fin[k] for k in ("local_gates", "global_gates", "diag_gates", "mono_gates")}}
@@ -825,6 +834,9 @@ def main():
                           "peak_gbs": peaks["hbm_gbs"]},
         "phases_ms": {k: round(v[0], 3) for k, v in m["phases"].items()},
         "phase_launches": {k: v[1] for k, v in m["phases"].items()},
+        "phases_note": "the timed steps' gates replayed from a checkpoint with CUDA events around each phase; "
+                       "the timed loop minus the phase sum is host orchestration and launch gaps",
+        "phase_sum_ms": round(m["phase_sum_ms"], 3),
         "gpu_launches": m["launches"],
         "clocks": m["clocks"],
         "fp64_probe_tflops": res["fp64_probe_tflops"],
