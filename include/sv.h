@@ -81,6 +81,17 @@ sv_status sv_create(int n, uint64_t K, double p, sv_state** out);
 sv_status sv_create_ex(int n, uint64_t K, double p, int prec, void* cuda_stream,
                        const sv_allocator* alloc, sv_state** out);
 
+/* Size the handle's device buffers for states of up to `terms` terms and
+ * the candidates of any gate on them (16 per term), so that later gates and
+ * truncations allocate nothing (buffers otherwise grow, by doubling, when a
+ * gate first needs more room; each growth allocates device memory, which
+ * costs milliseconds per gigabyte).  Buffers never shrink.  About
+ * terms * (16 * 2 * (16 + S) + 40) bytes with S the amplitude size (16 for
+ * complex128, 8 for complex64).  SV_E_NOMEM when the device memory is not
+ * there (the handle stays usable), SV_E_ARG above 2^32 - 1 terms.
+ * Synchronises. */
+sv_status sv_reserve(sv_state* s, uint64_t terms);
+
 /* Free the handle and its device memory.  Accepts NULL. */
 sv_status sv_destroy(sv_state* s);
 

@@ -257,6 +257,16 @@ sv_status ensure_state_cap(sv_state* s, uint64_t need) {
   return rc;
 }
 
+sv_status ensure_gs_lb(sv_state* s, uint64_t words) {
+  if (words <= s->gs_lb_entries) return SV_OK;
+  dev_free(s, s->gs_lb);
+  s->gs_lb_entries = 0;
+  s->gs_lb = (uint64_t*)dev_alloc(s, (words + words / 2) * sizeof(uint64_t));
+  if (!s->gs_lb) return fail(s, SV_E_NOMEM, "group scan look-back allocation failed");
+  s->gs_lb_entries = words + words / 2;
+  return SV_OK;
+}
+
 sv_status ensure_sort_cap(sv_state* s, uint64_t need) {
   if (need > s->sort_cap) {
     uint64_t cap = s->sort_cap * 2 > need ? s->sort_cap * 2 : need;
@@ -594,13 +604,8 @@ sv_status sv_apply_gate(sv_state* s, int m, const int* qubits, const double* U) 
   if (rc == SV_OK) rc = ensure_sort_cap(s, N);
   if (rc != SV_OK) return rc;
   const uint64_t gs_words = group_scan_lookback_words(N);  // the group scan's two look-backs
-  if (gs_words > s->gs_lb_entries) {
-    dev_free(s, s->gs_lb);
-    s->gs_lb_entries = 0;
-    s->gs_lb = (uint64_t*)dev_alloc(s, (gs_words + gs_words / 2) * sizeof(uint64_t));
-    if (!s->gs_lb) return fail(s, SV_E_NOMEM, "group scan look-back allocation failed");
-    s->gs_lb_entries = gs_words + gs_words / 2;
-  }
+  rc = ensure_gs_lb(s, gs_words);
+  if (rc != SV_OK) return rc;
   const int alt = 1 - s->cur;
   for (int b = 0; b < s->n; ++b) s->order_next[b] = s->order[b];
   // A diagonal U maps every term to itself (Eq. 3 with no off-diagonal
@@ -1265,6 +1270,20 @@ sv_status sv_last_stats(const sv_state* s, sv_stats* out) {
   if (!s || !out) return SV_E_ARG;
   *out = s->stats;
   return SV_OK;
+}
+
+sv_status sv_reserve(sv_state* s, uint64_t terms) {
+  SV_GUARD(s);
+  if (terms > MAX_TERMS) return fail(s, SV_E_ARG, "sv_reserve: more terms than 32-bit term indices allow");
+  if (terms == 0) return SV_OK;
+  const uint64_t cand = terms << 4;  // a 4-qubit gate gives each term at most 16 candidates
+  sv_status rc = ensure_state_cap(s, cand);
+  if (rc == SV_OK) rc = ensure_sort_cap(s, terms);
+  if (rc == SV_OK) rc = ensure_gs_lb(s, group_scan_lookback_words(terms));
+  if (rc == SV_OK) rc = ensure_window_cap(s, cand);
+  if (rc == SV_OK) rc = ensure_lookback(s, (cand + 1023) / 1024 + 16);
+  if (rc == SV_OK) rc = cuda_check(s, cudaStreamSynchronize(s->st), "sv_reserve");
+  return rc;
 }
 
 sv_status sv_set_apply_variant(sv_state* s, int variant) {

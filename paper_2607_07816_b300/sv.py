@@ -28,7 +28,7 @@ EXPORTED = ["sv_create", "sv_create_ex", "sv_destroy", "sv_apply_gate", "sv_trun
             "svb_create", "svb_destroy", "svb_add", "svb_remove", "svb_step", "svb_num_terms",
             "svb_retained_mass", "svb_peak", "svb_export", "svb_last_error", "svb_set_autotune",
             "svb_autotune_stats", "svb_set_graphs", "svb_graph_stats", "sv_selftest", "sv_set_apply_variant",
-            "sv_probe_fp64", "sv_select_histogram", "sv_cut"]
+            "sv_probe_fp64", "sv_select_histogram", "sv_cut", "sv_reserve"]
 PHASES = ["keys", "sort", "heads", "apply", "select", "compact", "peak", "other", "window", "local"]
 
 
@@ -156,6 +156,8 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.sv_probe_fp64.argtypes = [u64, i32, P(dbl), P(dbl)]
     lib.sv_select_histogram.restype = i32
     lib.sv_select_histogram.argtypes = [vp, u64, u64, i32, vp, vp]
+    lib.sv_reserve.restype = i32
+    lib.sv_reserve.argtypes = [vp, u64]
     lib.sv_cut.restype = i32
     lib.sv_cut.argtypes = [vp, u64, u64, u64, u64, u64, u64, P(u64)]
     lib.sv_transfer_bytes.restype = None
@@ -329,6 +331,11 @@ def sv_select_histogram(h: int, prefix: int, bits: int):
     return counts, [(int(a) << 64) | int(b) for a, b in zip(hi, lo)]
 
 
+def sv_reserve(h: int, terms: int) -> None:
+    """Size the handle's device buffers for states of up to `terms` terms."""
+    _check(h, load_library().sv_reserve(ctypes.c_void_p(h), ctypes.c_uint64(int(terms))))
+
+
 def sv_cut(h: int, z: int, S_c: int, S_N: int) -> int:
     """Keep the terms with composite Z <= z, renormalised by the kept mass
     S_c of all the handles together; S_N is their total mass (both exact
@@ -431,6 +438,11 @@ class SparseState:
 
     def phase_times(self) -> dict:
         return sv_phase_times(self.h)
+
+    def reserve(self, terms: int) -> None:
+        """Size the device buffers for states of up to `terms` terms (no
+        allocation in later gates and truncations)."""
+        sv_reserve(self.h, terms)
 
     def select_histogram(self, prefix: int, bits: int):
         return sv_select_histogram(self.h, prefix, bits)

@@ -467,3 +467,28 @@ def test_monomial_gates_match_oracle(sv, oracle_mod, prec):
             if step % 4 == 1:
                 gates.append(((int(rng.integers(0, n)),), C.mat_rz(float(rng.random()))))
         run_both(gates, g, o, check_every=count < 100000)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_reserved_handle_allocates_nothing_and_matches(sv, oracle_mod, prec):
+    """sv_reserve sizes every buffer up front: the gates and truncations that
+    follow take no device memory (free memory unchanged), and the results are
+    the oracle's, as on a handle that grows its buffers on demand."""
+    import torch
+    c = C.random_mix_circuit(30, 40, seed=17 + prec, sigma=0.05, K=1 << 14, p=0.999)
+    g = sv.SparseState(c.n, c.K, c.p, prec=prec)
+    g.reserve(c.K)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    o = oracle_mod.Oracle(c.n, c.K, c.p, prec=prec)
+    run_both(c.gates, g, o, check_every=False)
+    torch.cuda.synchronize()
+    # exports allocate a staging buffer and free it again; the gates none
+    assert torch.cuda.mem_get_info()[0] >= free0 - (2 << 20)
+    h = sv.SparseState(c.n, c.K, c.p, prec=prec)
+    h.run(c.gates)
+    hk, ha = h.export()
+    gk, ga = g.export()
+    assert np.array_equal(hk, gk) and np.array_equal(ha, ga)
+    with pytest.raises(sv.SVError):
+        g.reserve(1 << 40)
