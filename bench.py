@@ -244,6 +244,18 @@ def phase_bytes(ph, tot):
             "compact": tot["compact_bytes"], "peak": 16 * 1184 * tot["steps"]}.get(ph, 0.0)
 
 
+def attainable_ms(tot, bw_gbs, fp64_tflops):
+    """The steps' time if every phase ran at its own roof: the larger of its
+    algorithmic bytes over the HBM bandwidth and its FP64 work over the
+    measured FP64 rate (the gate's mat-vec; the compaction's rescale and
+    probability: 4 FP64 operations per kept term), summed over the phases."""
+    bw, f = bw_gbs * 1e9, fp64_tflops * 1e12
+    t = max(tot["apply_bytes"] / bw, tot["fp64_apply"] / f)
+    t += max(tot["compact_bytes"] / bw, 8.0 * tot["n_kept"] / f)
+    t += (tot["sort_bytes"] + tot["heads_bytes"] + tot["window_bytes"] + 16 * tot["window_terms"]) / bw
+    return 1e3 * t
+
+
 def fp64_derived_tflops(sm_mhz):
     return SM_COUNT * FP64_FMA_PER_SM_CLK * 2 * sm_mhz * 1e6 / 1e12
 
@@ -834,7 +846,12 @@ def main():
         "roofline": roofline(m, args.prec, peaks, res["fp64_probe_tflops"]),
         "gate_roofline": {"B_method_frac": round(tot["B_method"] / (ms / 1e3) / bw, 4),
                           "B_strict_frac": round(tot["B_strict"] / (ms / 1e3) / bw, 4),
-                          "peak_gbs": peaks["hbm_gbs"]},
+                          "peak_gbs": peaks["hbm_gbs"],
+                          "attainable_ms": round(attainable_ms(tot, peaks["hbm_gbs"], res["fp64_probe_tflops"]), 3),
+                          "frac_of_attainable": round(attainable_ms(tot, peaks["hbm_gbs"], res["fp64_probe_tflops"]) / ms, 4),
+                          "B_method_frac_at_attainable": round(
+                              tot["B_method"] / (attainable_ms(tot, peaks["hbm_gbs"], res["fp64_probe_tflops"]) / 1e3) / bw, 4),
+                          "note": "attainable: each phase at the larger of bytes / HBM and FP64 work / the FP64 probe"},
         "phases_ms": {k: round(v[0], 3) for k, v in m["phases"].items()},
         "phase_launches": {k: v[1] for k, v in m["phases"].items()},
         "phases_note": "the timed steps' gates replayed from a checkpoint with CUDA events around each phase; "
@@ -852,6 +869,8 @@ def main():
         ct = c["totals"]
         line["c64"] = {"value": c["rate"], "unit": "terms/s", "ms_per_step": c["ms"] / args.steps,
                        "B_method_frac": round(ct["B_method"] / (c["ms"] / 1e3) / bw, 4),
+                       "frac_of_attainable": round(attainable_ms(ct, peaks["hbm_gbs"], res["fp64_probe_tflops"])
+                                                   / c["ms"], 4),
                        "roofline": roofline(c, "c64", peaks, res["fp64_probe_tflops"]),
                        "phases_ms": {k: round(v[0], 3) for k, v in c["phases"].items()}}
     if "whole" in res:
