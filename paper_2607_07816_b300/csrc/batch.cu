@@ -147,6 +147,15 @@ __global__ void __launch_bounds__(SA_BLOCK) k_seg_apply(
   typedef typename SCplx<Real>::T C2;
   constexpr int TILE_G = SA_BLOCK * GPT;
   constexpr int WARPS = SA_BLOCK / 32;
+  constexpr int NOUT = SA_BLOCK * GPT * MAXD;  // most outputs of one tile
+  // a tile's outputs are staged in shared memory and written back coalesced
+  // (a thread's outputs are consecutive, so direct stores of neighbouring
+  // threads fall 2^m apart)
+  extern __shared__ __align__(16) uint8_t s_dyn[];
+  uint64_t* s_ok = reinterpret_cast<uint64_t*>(s_dyn);
+  uint64_t* s_op = s_ok + NOUT;
+  C2* s_oa = reinterpret_cast<C2*>(s_op + NOUT);
+  uint16_t* s_os = reinterpret_cast<uint16_t*>(s_oa + NOUT);
   __shared__ uint32_t s_warp[WARPS];
   __shared__ uint64_t s_base;
   __shared__ uint32_t s_total;
@@ -259,7 +268,7 @@ __global__ void __launch_bounds__(SA_BLOCK) k_seg_apply(
       }
     }
     __syncthreads();
-    uint64_t o = s_base + s_warp[warp] + (x - cnt);
+    uint32_t o = s_warp[warp] + (x - cnt);  // position within the tile's outputs
 #pragma unroll
     for (int j = 0; j < GPT; ++j) {
       if (!keep[j]) continue;
@@ -269,19 +278,54 @@ __global__ void __launch_bounds__(SA_BLOCK) k_seg_apply(
 #pragma unroll
       for (int ro = 0; ro < MAXD; ++ro) {
         if (!((keep[j] >> ro) & 1u)) continue;
-        keys_out[o] = rest[j] | seg_deposit_r((uint32_t)ro, q, mj[j]);
+        s_ok[o] = rest[j] | seg_deposit_r((uint32_t)ro, q, mj[j]);
         C2 y;
         y.x = yr[j][ro];
         y.y = yi[j][ro];
-        amps_out[o] = y;
-        probs_out[o] = amp_prob_bits(yr[j][ro], yi[j][ro]);
-        seg_out[o] = sgj[j];
+        s_oa[o] = y;
+        s_op[o] = amp_prob_bits(yr[j][ro], yi[j][ro]);
+        s_os[o] = sgj[j];
         ++o;
       }
+    }
+    __syncthreads();
+    const uint64_t base = s_base;
+    for (uint32_t i = tid; i < s_total; i += SA_BLOCK) {
+      keys_out[base + i] = s_ok[i];
+      amps_out[base + i] = s_oa[i];
+      probs_out[base + i] = s_op[i];
+      seg_out[base + i] = s_os[i];
     }
     if (tile == tiles - 1 && tid == 0) ctl->count[1] = s_base + s_total;
     __syncthreads();
   }
+}
+
+// Shared staging of one tile's outputs: key, probability, amplitude, slot.
+template <typename C2>
+constexpr size_t seg_apply_smem(int maxd, int gpt) {
+  return (size_t)SA_BLOCK * gpt * maxd * (8 + 8 + sizeof(C2) + 2);
+}
+
+template <typename Real, int MAXD, int GPT>
+cudaError_t seg_apply_attr() {
+  typedef typename SCplx<Real>::T C2;
+  return cudaFuncSetAttribute(k_seg_apply<Real, MAXD, GPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)seg_apply_smem<C2>(MAXD, GPT));
+}
+
+template <typename Real>
+cudaError_t seg_apply_attrs() {
+  cudaError_t e = seg_apply_attr<Real, 2, 1>();
+  if (e == cudaSuccess) e = seg_apply_attr<Real, 2, 2>();
+  if (e == cudaSuccess) e = seg_apply_attr<Real, 2, 4>();
+  if (e == cudaSuccess) e = seg_apply_attr<Real, 4, 1>();
+  if (e == cudaSuccess) e = seg_apply_attr<Real, 4, 2>();
+  if (e == cudaSuccess) e = seg_apply_attr<Real, 4, 4>();
+  if (e == cudaSuccess) e = seg_apply_attr<Real, 8, 1>();
+  if (e == cudaSuccess) e = seg_apply_attr<Real, 8, 2>();
+  if (e == cudaSuccess) e = seg_apply_attr<Real, 16, 1>();
+  return e;
 }
 
 template <typename Real>
@@ -293,8 +337,8 @@ void seg_apply_dispatch(int mmax, int gpt, unsigned grid, cudaStream_t st, const
   const C2* ai = (const C2*)amps_in;
   C2* ao = (C2*)amps_out;
 #define SV_SEG_APPLY(MAXD, GPT)                                                                         \
-  k_seg_apply<Real, MAXD, GPT><<<grid, SA_BLOCK, 0, st>>>(sk, sidx, n, heads, ai, shift, gates, keys_out, ao, \
-                                                          probs_out, seg_out, lookback, max_tiles, ctl)
+  k_seg_apply<Real, MAXD, GPT><<<grid, SA_BLOCK, seg_apply_smem<C2>(MAXD, GPT), st>>>(                    \
+      sk, sidx, n, heads, ai, shift, gates, keys_out, ao, probs_out, seg_out, lookback, max_tiles, ctl)
   if (mmax <= 1) {
     if (gpt == 1) SV_SEG_APPLY(2, 1);
     else if (gpt == 2) SV_SEG_APPLY(2, 2);
@@ -787,8 +831,11 @@ __global__ void __launch_bounds__(256) k_segsel_finish(const uint64_t* __restric
 cudaError_t batch_prepare() {
   static DeviceOnce once;
   cudaError_t e = once.run([] {
-    return cudaFuncSetAttribute(k_segsel_finish, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(2 * sizeof(uint64_t) * SF_CAP));
+    cudaError_t r = cudaFuncSetAttribute(k_segsel_finish, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(2 * sizeof(uint64_t) * SF_CAP));
+    if (r == cudaSuccess) r = seg_apply_attrs<double>();
+    if (r == cudaSuccess) r = seg_apply_attrs<float>();
+    return r;
   });
   return e == cudaSuccess ? sort_prepare() : e;
 }
