@@ -20,55 +20,84 @@
 namespace sv {
 
 // ---------------------------------------------------------------- keys
+// The nibble tables of each slot's sort order for this step (one block per
+// slot): fwd[k][v] = the sort-key bits of natural bits 4k.. given by v,
+// inv[k][v] = the natural bits of sort-key bits 4k.. given by v.
+__global__ void __launch_bounds__(256) k_seg_tables(const SegGate* __restrict__ gates,
+                                                    uint64_t* __restrict__ tables) {
+  __shared__ int8_t s_nat[64];  // sort-key bit -> qubit
+  const SegGate& gt = gates[blockIdx.x];
+  uint64_t* fwd = tables + (uint64_t)blockIdx.x * SEG_TABLE_WORDS;
+  uint64_t* inv = fwd + 256;
+  if (threadIdx.x < 64) s_nat[threadIdx.x] = -1;
+  __syncthreads();
+  if (gt.m < 0) return;  // removed or free slot: no tables needed
+  if (threadIdx.x < 64) {
+    const int p = gt.pos[threadIdx.x];
+    if (p < 64) s_nat[p] = (int8_t)threadIdx.x;
+  }
+  __syncthreads();
+  const int k = threadIdx.x >> 4, v = threadIdx.x & 15;
+  uint64_t f = 0, g = 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    if ((v >> j) & 1) {
+      const int b = 4 * k + j;
+      if (gt.pos[b] < 64) f |= 1ull << gt.pos[b];
+      if (s_nat[b] >= 0) g |= 1ull << s_nat[b];
+    }
+  fwd[threadIdx.x] = f;
+  inv[threadIdx.x] = g;
+}
+
+void launch_seg_tables(const SegGate* gates, int slots, uint64_t* tables, cudaStream_t st) {
+  if (slots > 0) k_seg_tables<<<slots, 256, 0, st>>>(gates, tables);
+}
+
+__device__ __forceinline__ uint64_t nibble_map(const uint64_t* __restrict__ t, uint64_t x) {
+  uint64_t y = 0;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) y |= t[16 * k + ((x >> (4 * k)) & 15u)];
+  return y;
+}
+
+// Sort key of every term: (segment rank, the key in its slot's sort order),
+// all ones for a term of a removed segment (left out of the grouping).
 __global__ void __launch_bounds__(256) k_seg_keys(const uint64_t* __restrict__ keys,
                                                   const uint16_t* __restrict__ seg, uint64_t n,
-                                                  const SegGate* __restrict__ gates, int shift,
-                                                  uint64_t* __restrict__ sk, uint32_t* __restrict__ sidx,
-                                                  uint32_t* __restrict__ hist, int passes) {
-  __shared__ uint32_t sh[MAX_PASSES][RADIX];
-  for (int i = threadIdx.x; i < MAX_PASSES * RADIX; i += blockDim.x) (&sh[0][0])[i] = 0;
-  __syncthreads();
+                                                  const SegGate* __restrict__ gates,
+                                                  const uint64_t* __restrict__ tables, int shift,
+                                                  uint64_t* __restrict__ sk) {
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
        i += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t sg = seg[i];
-    uint64_t s;
-    if (gates[sg].m < 0) {
-      s = ~0ull;  // term of a removed segment: sorts last and is cut off
-    } else {
-      const SegGate& gt = gates[sg];
-      const uint64_t k = keys[i];
-      s = ((uint64_t)sg << shift) | (squeeze_out(k, gt.qs, gt.m) << gt.m) | seg_gather_r(k, gt.q, gt.m);
-    }
+    uint64_t s = ~0ull;
+    if (gates[sg].m >= 0)
+      s = ((uint64_t)gates[sg].rank << shift) | nibble_map(tables + (uint64_t)sg * SEG_TABLE_WORDS, keys[i]);
     sk[i] = s;
-    sidx[i] = (uint32_t)i;
-    for (int p = 0; p < passes; ++p) atomicAdd(&sh[p][(s >> (RADIX_BITS * p)) & (RADIX - 1)], 1u);
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < passes * RADIX; i += blockDim.x) {
-    const uint32_t c = (&sh[0][0])[i];
-    if (c) atomicAdd(&hist[i], c);
   }
 }
 
-void launch_seg_keys(const uint64_t* keys, const uint16_t* seg, uint64_t n, const SegGate* gates, int shift,
-                     uint64_t* sk, uint32_t* sidx, uint32_t* hist, int passes, cudaStream_t st) {
-  cudaMemsetAsync(hist, 0, sizeof(uint32_t) * MAX_PASSES * RADIX, st);
+void launch_seg_keys(const uint64_t* keys, const uint16_t* seg, uint64_t n, const SegGate* gates,
+                     const uint64_t* tables, int shift, uint64_t* sk, cudaStream_t st) {
   if (n == 0) return;
   uint64_t blocks = (n + 255) / 256;
   if (blocks > 148 * 8) blocks = 148 * 8;
-  k_seg_keys<<<(unsigned)blocks, 256, 0, st>>>(keys, seg, n, gates, shift, sk, sidx, hist, passes);
+  k_seg_keys<<<(unsigned)blocks, 256, 0, st>>>(keys, seg, n, gates, tables, shift, sk);
 }
 
 // ---------------------------------------------------------------- heads
 constexpr int SH_BLOCK = 256, SH_ITEMS = 16;
 
-__device__ __forceinline__ uint64_t seg_group_key(uint64_t s, int shift, const SegGate* gates) {
-  const uint32_t sg = (uint32_t)(s >> shift);
-  return s >> gates[sg].m;  // the segment id stays in the top bits
+__device__ __forceinline__ uint64_t seg_group_key(uint64_t s, int shift, const SegGate* gates,
+                                                  const uint16_t* rank_slot) {
+  const uint32_t sg = rank_slot[(uint32_t)(s >> shift)];
+  return s >> gates[sg].m;  // the segment rank stays in the top bits
 }
 
 __global__ void __launch_bounds__(SH_BLOCK) k_seg_heads(const uint64_t* __restrict__ sk, uint64_t n, int shift,
                                                         const SegGate* __restrict__ gates,
+                                                        const uint16_t* __restrict__ rank_slot,
                                                         uint32_t* __restrict__ heads, uint64_t* lookback,
                                                         Ctl* ctl) {
   typedef TileLayout<SH_BLOCK, SH_ITEMS> L;
@@ -90,7 +119,7 @@ __global__ void __launch_bounds__(SH_BLOCK) k_seg_heads(const uint64_t* __restri
       if (i < n) {
         const uint64_t a = sk[i];
         f = i == 0 || (a >> shift) != (sk[i - 1] >> shift) ||
-            seg_group_key(a, shift, gates) != seg_group_key(sk[i - 1], shift, gates);
+            seg_group_key(a, shift, gates, rank_slot) != seg_group_key(sk[i - 1], shift, gates, rank_slot);
       }
       flag[j] = f;
     }
@@ -103,7 +132,8 @@ __global__ void __launch_bounds__(SH_BLOCK) k_seg_heads(const uint64_t* __restri
   }
 }
 
-void launch_seg_heads(const uint64_t* sk, uint64_t n, int shift, const SegGate* gates, uint32_t* heads,
+void launch_seg_heads(const uint64_t* sk, uint64_t n, int shift, const SegGate* gates, const uint16_t* rank_slot,
+                      uint32_t* heads,
                       uint64_t* lookback, Ctl* ctl, cudaStream_t st) {
   const uint64_t tiles = (n + SH_BLOCK * SH_ITEMS - 1) / (SH_BLOCK * SH_ITEMS);
   cudaMemsetAsync(lookback, 0, sizeof(uint64_t) * (tiles + 1), st);
@@ -111,7 +141,7 @@ void launch_seg_heads(const uint64_t* sk, uint64_t n, int shift, const SegGate* 
   cudaMemsetAsync(&ctl->count[0], 0, sizeof(uint64_t), st);
   if (n == 0) return;
   const uint64_t grid = tiles < 148 * 4 ? tiles : 148 * 4;
-  k_seg_heads<<<(unsigned)grid, SH_BLOCK, 0, st>>>(sk, n, shift, gates, heads, lookback, ctl);
+  k_seg_heads<<<(unsigned)grid, SH_BLOCK, 0, st>>>(sk, n, shift, gates, rank_slot, heads, lookback, ctl);
 }
 
 // ---------------------------------------------------------------- apply
@@ -141,7 +171,8 @@ template <typename Real, int MAXD, int GPT>
 __global__ void __launch_bounds__(SA_BLOCK) k_seg_apply(
     const uint64_t* __restrict__ sk, const uint32_t* __restrict__ sidx, uint64_t n,
     const uint32_t* __restrict__ heads, const typename SCplx<Real>::T* __restrict__ amps_in, int shift,
-    const SegGate* __restrict__ gates, uint64_t* __restrict__ keys_out,
+    const SegGate* __restrict__ gates, const uint16_t* __restrict__ rank_slot, const uint64_t* __restrict__ tables,
+    uint64_t* __restrict__ keys_out,
     typename SCplx<Real>::T* __restrict__ amps_out, uint64_t* __restrict__ probs_out,
     uint16_t* __restrict__ seg_out, uint64_t* lookback, uint64_t max_tiles, Ctl* ctl) {
   typedef typename SCplx<Real>::T C2;
@@ -210,7 +241,7 @@ __global__ void __launch_bounds__(SA_BLOCK) k_seg_apply(
       const uint64_t h = hb[j];
       const uint64_t e = hb[j + 1];
       const uint64_t s0 = s0v[j];
-      const uint32_t sg = (uint32_t)(s0 >> shift);
+      const uint32_t sg = rank_slot[(uint32_t)(s0 >> shift)];
       const SegGate& gt = gates[sg];
       const int m = gt.m;
       const int d = 1 << m;
@@ -238,7 +269,9 @@ __global__ void __launch_bounds__(SA_BLOCK) k_seg_apply(
         if (ro < d && !(yr[j][ro] == (Real)0 && yi[j][ro] == (Real)0)) keep[j] |= 1u << ro;
       for (int t = 0; t < m; ++t) qpack[j] |= (uint32_t)gt.q[t] << (8 * t);
       mj[j] = m;
-      rest[j] = spread_in((s0 & low_mask(shift)) >> m, gt.qs, m);
+      // the group's natural key without the gate bits: its sort key with the
+      // bottom m bits cleared, mapped back through the slot's inverse table
+      rest[j] = nibble_map(tables + (uint64_t)sg * SEG_TABLE_WORDS + 256, (s0 & low_mask(shift)) >> m << m);
       sgj[j] = (uint16_t)sg;
       cnt += __popc(keep[j]);
     }
@@ -331,14 +364,17 @@ cudaError_t seg_apply_attrs() {
 template <typename Real>
 void seg_apply_dispatch(int mmax, int gpt, unsigned grid, cudaStream_t st, const uint64_t* sk, const uint32_t* sidx,
                         uint64_t n, const uint32_t* heads, const void* amps_in, int shift, const SegGate* gates,
-                        uint64_t* keys_out, void* amps_out, uint64_t* probs_out, uint16_t* seg_out,
+                        const uint16_t* rank_slot, const uint64_t* tables, uint64_t* keys_out, void* amps_out,
+                        uint64_t* probs_out,
+                        uint16_t* seg_out,
                         uint64_t* lookback, uint64_t max_tiles, Ctl* ctl) {
   typedef typename SCplx<Real>::T C2;
   const C2* ai = (const C2*)amps_in;
   C2* ao = (C2*)amps_out;
 #define SV_SEG_APPLY(MAXD, GPT)                                                                         \
   k_seg_apply<Real, MAXD, GPT><<<grid, SA_BLOCK, seg_apply_smem<C2>(MAXD, GPT), st>>>(                    \
-      sk, sidx, n, heads, ai, shift, gates, keys_out, ao, probs_out, seg_out, lookback, max_tiles, ctl)
+      sk, sidx, n, heads, ai, shift, gates, rank_slot, tables, keys_out, ao, probs_out, seg_out, lookback,   \
+      max_tiles, ctl)
   if (mmax <= 1) {
     if (gpt == 1) SV_SEG_APPLY(2, 1);
     else if (gpt == 2) SV_SEG_APPLY(2, 2);
@@ -362,9 +398,10 @@ int seg_apply_configs(int mmax) { return mmax <= 2 ? 3 : (mmax == 3 ? 2 : 1); }
 // max_tiles bounds the look-back buffer: at least groups / 256 + 1, the tile
 // count of one group per thread.
 void launch_seg_apply(int prec, const uint64_t* sk, const uint32_t* sidx, uint64_t n, const uint32_t* heads,
-                      const void* amps_in, int shift, int mmax, const SegGate* gates, uint64_t* keys_out,
-                      void* amps_out, uint64_t* probs_out, uint16_t* seg_out, uint64_t* lookback, Ctl* ctl,
-                      uint64_t max_tiles, int cfg, cudaStream_t st) {
+                      const void* amps_in, int shift, int mmax, const SegGate* gates, const uint16_t* rank_slot,
+                      const uint64_t* tables, uint64_t* keys_out, void* amps_out, uint64_t* probs_out,
+                      uint16_t* seg_out,
+                      uint64_t* lookback, Ctl* ctl, uint64_t max_tiles, int cfg, cudaStream_t st) {
   cudaMemsetAsync(lookback, 0, sizeof(uint64_t) * (max_tiles + 1), st);
   cudaMemsetAsync(&ctl->tile_counter[1], 0, sizeof(uint64_t), st);
   cudaMemsetAsync(&ctl->count[1], 0, sizeof(uint64_t), st);
@@ -373,11 +410,11 @@ void launch_seg_apply(int prec, const uint64_t* sk, const uint32_t* sidx, uint64
   const int gpt = 1 << (cfg < ncfg ? cfg : ncfg - 1);
   const uint64_t grid = max_tiles < 148 * 4 ? (max_tiles ? max_tiles : 1) : 148 * 4;
   if (prec == 0)
-    seg_apply_dispatch<double>(mmax, gpt, (unsigned)grid, st, sk, sidx, n, heads, amps_in, shift, gates, keys_out,
-                               amps_out, probs_out, seg_out, lookback, max_tiles, ctl);
+    seg_apply_dispatch<double>(mmax, gpt, (unsigned)grid, st, sk, sidx, n, heads, amps_in, shift, gates, rank_slot,
+                               tables, keys_out, amps_out, probs_out, seg_out, lookback, max_tiles, ctl);
   else
-    seg_apply_dispatch<float>(mmax, gpt, (unsigned)grid, st, sk, sidx, n, heads, amps_in, shift, gates, keys_out,
-                              amps_out, probs_out, seg_out, lookback, max_tiles, ctl);
+    seg_apply_dispatch<float>(mmax, gpt, (unsigned)grid, st, sk, sidx, n, heads, amps_in, shift, gates, rank_slot,
+                              tables, keys_out, amps_out, probs_out, seg_out, lookback, max_tiles, ctl);
 }
 
 // ---------------------------------------------------------------- segment bounds
@@ -837,7 +874,8 @@ cudaError_t batch_prepare() {
     if (r == cudaSuccess) r = seg_apply_attrs<float>();
     return r;
   });
-  return e == cudaSuccess ? sort_prepare() : e;
+  if (e == cudaSuccess) e = sort_prepare();
+  return e == cudaSuccess ? regroup_prepare() : e;  // the step groups with the partition and merge kernels
 }
 
 void launch_segsel_finish(const uint64_t* g_buf, const uint32_t* g_bufn, const uint64_t* g_sum, SegSel* sel,

@@ -6,10 +6,19 @@
 namespace sv {
 
 // Gate of one segment for one step.  m == 0 is the identity (each term its
-// own group); m < 0 marks a removed segment whose terms are dropped.  The
-// sort key of a term is (segment, key with the gate bits taken out, r): the
-// gate bits are squeezed out at the ascending positions qs and r gathers
-// bit q[t] of the key into bit t.
+// own group); m < 0 marks a removed segment whose terms are dropped.
+//
+// Segments are contiguous in the buffer, in the order of their ranks (new
+// circuits are appended at the end); the sort key's segment field is the
+// rank, and rank_slot maps it back to the slot.
+//
+// Keys stay natural (qubit i = bit i), but each segment is kept sorted by a
+// sort order of its own that evolves as in the single-state path: a gate's
+// sort key puts its qubits at the bottom (qubits[t] at bit t) and keeps the
+// other qubits in the order of the previous sort key.  pos[b] is the bit of
+// qubit b in this step's sort key.  Because the segment is sorted by the
+// previous order, its terms with equal gate bits are already in the new
+// order, so the batch is grouped by a stable partition and merges.
 struct SegGate {
   uint64_t K;  // top-k limit of the slot (0: slot not in use)
   int m;
@@ -17,8 +26,15 @@ struct SegGate {
   int qs[4];  // the same qubits ascending
   uint32_t re_nz[16];
   uint32_t im_nz[16];
+  uint32_t rank;  // the segment's place in the buffer (the sort key's segment field)
+  uint8_t pos[64];
   double U[512];
 };
+
+// Per-slot nibble tables of this step's sort order: fwd maps a natural key
+// to its sort key, inv a sort key back to the natural key (16 x 16 words
+// each, fwd first).
+constexpr int SEG_TABLE_WORDS = 2 * 16 * 16;
 
 __device__ __forceinline__ uint32_t seg_gather_r(uint64_t key, const int* q, int m) {
   uint32_t r = 0;
@@ -54,9 +70,11 @@ struct SegSel {
 };
 
 cudaError_t batch_prepare();  // kernel attributes of this device, before any stream capture
-void launch_seg_keys(const uint64_t* keys, const uint16_t* seg, uint64_t n, const SegGate* gates, int shift,
-                     uint64_t* sk, uint32_t* sidx, uint32_t* hist, int passes, cudaStream_t st);
-void launch_seg_heads(const uint64_t* sk, uint64_t n, int shift, const SegGate* gates, uint32_t* heads,
+void launch_seg_tables(const SegGate* gates, int slots, uint64_t* tables, cudaStream_t st);
+void launch_seg_keys(const uint64_t* keys, const uint16_t* seg, uint64_t n, const SegGate* gates,
+                     const uint64_t* tables, int shift, uint64_t* sk, cudaStream_t st);
+void launch_seg_heads(const uint64_t* sk, uint64_t n, int shift, const SegGate* gates, const uint16_t* rank_slot,
+                      uint32_t* heads,
                       uint64_t* lookback, Ctl* ctl, cudaStream_t st);
 // Launch shapes that the batched step tunes (every shape gives the same
 // result): the mat-vec's groups per thread, the select scan's and the
@@ -65,7 +83,8 @@ int seg_apply_configs(int mmax);
 constexpr int SEGSEL_CONFIGS = 3;
 constexpr int SEGTRUNC_CONFIGS = 2;
 void launch_seg_apply(int prec, const uint64_t* sk, const uint32_t* sidx, uint64_t n, const uint32_t* heads,
-                      const void* amps_in, int shift, int mmax, const SegGate* gates, uint64_t* keys_out,
+                      const void* amps_in, int shift, int mmax, const SegGate* gates, const uint16_t* rank_slot,
+                      const uint64_t* tables, uint64_t* keys_out,
                       void* amps_out, uint64_t* probs_out, uint16_t* seg_out, uint64_t* lookback, Ctl* ctl,
                       uint64_t max_tiles, int cfg, cudaStream_t st);
 // Sizes marked n_dev are read on the device (a term count written by an

@@ -25,6 +25,7 @@ struct Slot {
   uint64_t count = 0;   // terms of this segment
   uint64_t offset = 0;  // first term in the current buffers
   double F = 1.0;
+  uint8_t order[64];    // bit of qubit b in the sort order the segment is sorted by
 };
 
 }  // namespace
@@ -57,6 +58,9 @@ struct svb_state {
 
   SegGate* gates_dev = nullptr;
   SegGate* gates_host = nullptr;
+  uint64_t* tables_dev = nullptr;  // [max_slots][SEG_TABLE_WORDS] per-slot sort-order tables
+  uint16_t* rank_slot_dev = nullptr;   // [max_slots] slot of each segment rank (buffer order)
+  uint16_t* rank_slot_host = nullptr;
   SegSel* sel_dev = nullptr;
   SegSel* sel_host = nullptr;
   uint32_t* sel_cnt = nullptr;
@@ -371,18 +375,23 @@ sv_status svb_create(int max_slots, int prec, void* cuda_stream, const sv_alloca
   b->tile_counter = (uint64_t*)b_alloc(b, 256);
   b->ctl = (Ctl*)b_alloc(b, sizeof(Ctl));
   b->gates_dev = (SegGate*)b_alloc(b, sizeof(SegGate) * max_slots);
+  b->tables_dev = (uint64_t*)b_alloc(b, sizeof(uint64_t) * SEG_TABLE_WORDS * max_slots);
+  b->rank_slot_dev = (uint16_t*)b_alloc(b, sizeof(uint16_t) * max_slots);
   b->sel_dev = (SegSel*)b_alloc(b, sizeof(SegSel) * max_slots);
   b->sel_cnt = (uint32_t*)b_alloc(b, sizeof(uint32_t) * SEL_BINS * max_slots);
   b->sel_mass = (uint64_t*)b_alloc(b, sizeof(uint64_t) * 4 * max_slots);
   b->sel_buf = (uint64_t*)b_alloc(b, sizeof(uint64_t) * 2 * SEGSEL_CAP * max_slots);
   b->sel_bufn = (uint32_t*)b_alloc(b, sizeof(uint32_t) * max_slots);
   b->bounds_dev = (uint64_t*)b_alloc(b, sizeof(uint64_t) * 2 * max_slots);
-  if (!b->hist || !b->tile_counter || !b->ctl || !b->gates_dev || !b->sel_dev || !b->sel_cnt || !b->sel_mass ||
+  if (!b->hist || !b->tile_counter || !b->ctl || !b->gates_dev || !b->tables_dev || !b->rank_slot_dev ||
+      !b->sel_dev || !b->sel_cnt ||
+      !b->sel_mass ||
       !b->sel_buf || !b->sel_bufn || !b->bounds_dev)
     rc = SV_E_NOMEM;
   if (rc == SV_OK && (cudaMallocHost(&b->hist_host, sizeof(uint32_t) * MAX_PASSES * RADIX) != cudaSuccess ||
                       cudaMallocHost(&b->ctl_host, sizeof(Ctl)) != cudaSuccess ||
                       cudaMallocHost(&b->gates_host, sizeof(SegGate) * max_slots) != cudaSuccess ||
+                      cudaMallocHost(&b->rank_slot_host, sizeof(uint16_t) * max_slots) != cudaSuccess ||
                       cudaMallocHost(&b->sel_host, sizeof(SegSel) * max_slots) != cudaSuccess ||
                       cudaMallocHost(&b->bounds_host, sizeof(uint64_t) * 2 * max_slots) != cudaSuccess))
     rc = SV_E_CUDA;
@@ -418,6 +427,8 @@ sv_status svb_destroy(svb_state* b) {
   b_free(b, b->tile_counter);
   b_free(b, b->ctl);
   b_free(b, b->gates_dev);
+  b_free(b, b->tables_dev);
+  b_free(b, b->rank_slot_dev);
   b_free(b, b->sel_dev);
   b_free(b, b->sel_cnt);
   b_free(b, b->sel_mass);
@@ -432,6 +443,7 @@ sv_status svb_destroy(svb_state* b) {
   if (b->hist_host) cudaFreeHost(b->hist_host);
   if (b->ctl_host) cudaFreeHost(b->ctl_host);
   if (b->gates_host) cudaFreeHost(b->gates_host);
+  if (b->rank_slot_host) cudaFreeHost(b->rank_slot_host);
   if (b->sel_host) cudaFreeHost(b->sel_host);
   if (b->bounds_host) cudaFreeHost(b->bounds_host);
   delete b;
@@ -470,6 +482,7 @@ sv_status svb_add(svb_state* b, int n, uint64_t K, double p, int* slot) {
   sl.count = 1;
   sl.offset = b->N;
   sl.F = 1.0;
+  for (int q = 0; q < 64; ++q) sl.order[q] = (uint8_t)q;  // sorted by the natural key at first
   b->N += 1;
   *slot = s;
   return SV_OK;
@@ -528,7 +541,8 @@ sv_status svb_step(svb_state* b, const svb_gate* gates, int count) {
     // a slot can exceed its K after this step only if its count times the
     // gate's expansion does
     if ((sl.count << (listed[s] >= 0 ? gates[listed[s]].m : 0)) > sl.K) may_truncate = true;
-    if (listed[s] < 0) {
+    for (int q = 0; q < 64; ++q) gt.pos[q] = q < sl.n ? sl.order[q] : 64;
+    if (listed[s] < 0) {  // identity: the slot keeps its order
       gt.m = 0;
       gt.re_nz[0] = 1;
       gt.U[0] = 1.0;
@@ -536,6 +550,21 @@ sv_status svb_step(svb_state* b, const svb_gate* gates, int count) {
     }
     const svb_gate& g = gates[listed[s]];
     gt.m = g.m;
+    {  // the gate's sort order: its qubits at the bottom, the others in their present order
+      int by_pos[64];
+      for (int p = 0; p < 64; ++p) by_pos[p] = -1;
+      for (int q = 0; q < sl.n; ++q) by_pos[sl.order[q]] = q;
+      bool in_gate[64] = {};
+      for (int t = 0; t < g.m; ++t) {
+        in_gate[g.qubits[t]] = true;
+        gt.pos[g.qubits[t]] = (uint8_t)t;
+      }
+      int next = g.m;
+      for (int p = 0; p < 64; ++p) {
+        const int q = by_pos[p];
+        if (q >= 0 && !in_gate[q]) gt.pos[q] = (uint8_t)next++;
+      }
+    }
     mmax = g.m > mmax ? g.m : mmax;
     const int d = 1 << g.m;
     for (int t = 0; t < g.m; ++t) gt.q[t] = g.qubits[t];
@@ -551,6 +580,16 @@ sv_status svb_step(svb_state* b, const svb_gate* gates, int count) {
       }
     for (int t = 0; t < g.m; ++t) gt.qs[t] = g.qubits[t];
     std::sort(gt.qs, gt.qs + g.m);
+  }
+  {  // segment ranks: the used slots in buffer order (new circuits were appended at the end)
+    std::vector<std::pair<uint64_t, int>> used;
+    for (int s = 0; s < top; ++s)
+      if (b->slots[s].state == SLOT_USED) used.push_back({b->slots[s].offset, s});
+    std::sort(used.begin(), used.end());
+    for (size_t r = 0; r < used.size(); ++r) {
+      b->gates_host[used[r].second].rank = (uint32_t)r;
+      b->rank_slot_host[r] = (uint16_t)used[r].second;
+    }
   }
   ++b->steps;
   const uint64_t N = b->N;
@@ -577,7 +616,6 @@ sv_status svb_step(svb_state* b, const svb_gate* gates, int count) {
   // replayed as a CUDA graph once its shapes are settled); the host waits
   // after each: to confirm every segment's cut is resolved, and for the new
   // counts.
-  const int passes = (nbits + RADIX_BITS - 1) / RADIX_BITS;
   const int alt = 1 - b->cur;
   uint64_t* start_dev = b->bounds_dev;
   uint64_t* end_dev = b->bounds_dev + b->max_slots;
@@ -597,22 +635,32 @@ sv_status svb_step(svb_state* b, const svb_gate* gates, int count) {
                                     (uint64_t)may_truncate};
   rc = run_part(b, settled, key_a, [&]() -> sv_status {
     cudaMemcpyAsync(b->gates_dev, b->gates_host, sizeof(SegGate) * top, cudaMemcpyHostToDevice, b->st);
-    launch_seg_keys(b->keys[b->cur], b->seg[b->cur], N, b->gates_dev, shift, b->sk[0], b->sidx[0], b->hist, passes,
-                    b->st);
+    cudaMemcpyAsync(b->rank_slot_dev, b->rank_slot_host, sizeof(uint16_t) * top, cudaMemcpyHostToDevice, b->st);
+    // grouping: every segment is sorted by its previous order, so the terms
+    // with equal low M bits of the new sort key are already sorted by it: a
+    // stable partition by those bits and M merge levels sort the batch
+    launch_seg_tables(b->gates_dev, top, b->tables_dev, b->st);
+    launch_seg_keys(b->keys[b->cur], b->seg[b->cur], N, b->gates_dev, b->tables_dev, shift, b->sk[1], b->st);
+    cudaMemsetAsync(b->hist, 0, sizeof(uint32_t) * 16, b->st);  // the partition's run totals
     SortScratch sc;
     sc.hist = b->hist;
-    sc.hist_host = nullptr;  // every pass runs (no read-back of the digit counts)
+    sc.hist_host = nullptr;
     sc.lookback = b->lookback;
     sc.lookback_tiles = b->lb_entries / RADIX;
     sc.tile_counter = b->tile_counter;
     sc.err = &b->ctl->err;
+    GateParams gp;
+    std::memset(&gp, 0, sizeof(gp));
+    gp.m = mmax > 1 ? mmax : 1;
+    gp.direct = 1;
     cudaError_t ce;
-    int run = 0;
-    const int w = radix_sort_pairs(b->sk[0], b->sidx[0], b->sk[1], b->sidx[1], N, nbits, sc, b->st, &run, &ce);
-    if (ce != cudaSuccess) return b_cuda(b, ce, "svb_step sort");
-    launch_seg_heads(b->sk[w], nkeep, shift, b->gates_dev, b->heads, b->lookback, b->ctl, b->st);
+    int nl = 0;
+    const int w = regroup_terms(b->sk[1], N, gp, b->sk, b->sidx, sc, b->st, &nl, &ce);
+    if (ce != cudaSuccess) return b_cuda(b, ce, "svb_step grouping");
+    launch_seg_heads(b->sk[w], nkeep, shift, b->gates_dev, b->rank_slot_dev, b->heads, b->lookback, b->ctl, b->st);
     if (timing) cudaEventRecord(b->tev[TK_APPLY][0], b->st);
     launch_seg_apply(b->prec, b->sk[w], b->sidx[w], nkeep, b->heads, b->amps[b->cur], shift, mmax, b->gates_dev,
+                     b->rank_slot_dev, b->tables_dev,
                      b->keys[alt], b->amps[alt], b->probs[alt], b->seg[alt], b->lookback, b->ctl, apply_tiles,
                      cfg_apply, b->st);
     if (timing) cudaEventRecord(b->tev[TK_APPLY][1], b->st);
@@ -701,6 +749,8 @@ sv_status svb_step(svb_state* b, const svb_gate* gates, int count) {
   for (int s = 0; s < b->max_slots; ++s) {
     Slot& sl = b->slots[s];
     if (sl.state != SLOT_USED) continue;
+    if (s < top)  // the segment is now sorted by this step's order
+      for (int q = 0; q < sl.n; ++q) sl.order[q] = b->gates_host[s].pos[q];
     if (s < top) {
       const uint64_t a = b->bounds_host[s], e = b->bounds_host[b->max_slots + s];
       sl.offset = a;

@@ -109,6 +109,8 @@ struct GateParams {
   int qpos[4];         // bit of qubits[t] in the stored keys before the gate
   uint64_t rmap;       // nibble r: the digit the regrouping sorts a term with gate bits r under
                        // (identity; a monomial gate's output index instead)
+  int direct;          // 1: the keys given to the regrouping are already sort keys (digit = low m
+                       // bits; a key of all ones is left out), as in the batched form
 };
 
 constexpr uint64_t RMAP_IDENTITY = 0xFEDCBA9876543210ull;

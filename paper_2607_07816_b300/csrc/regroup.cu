@@ -109,7 +109,13 @@ __global__ void __launch_bounds__(RG_THREADS) k_part_counts(const uint64_t* __re
 #pragma unroll
   for (int i = 0; i < RG_ITEMS; ++i) {
     const uint64_t idx = base + i * 32;
-    const uint32_t d = idx < n ? (uint32_t)(gp.rmap >> (4 * gate_index_of(k[i], q, m))) & 15u : 16u;
+    uint32_t d = 16u;
+    if (idx < n) {
+      if (gp.direct)
+        d = k[i] == ~0ull ? 16u : (uint32_t)k[i] & ((1u << m) - 1u);
+      else
+        d = (uint32_t)(gp.rmap >> (4 * gate_index_of(k[i], q, m))) & 15u;
+    }
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
     if (d < 16 && lane == __ffs(peers) - 1) atomicAdd(&h[d], (uint32_t)__popc(peers));
   }
@@ -138,6 +144,7 @@ __global__ void __launch_bounds__(RG_THREADS, 3) k_part_scatter(const uint64_t* 
   __shared__ uint32_t s_whist[RG_WARPS][16];
   __shared__ uint32_t s_local[16];
   __shared__ uint32_t s_out[16];
+  __shared__ uint32_t s_staged;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int m = gp.m, D = 1 << m, vb = gp.vbits;
   const uint32_t dmask = (uint32_t)D - 1u;
@@ -153,8 +160,12 @@ __global__ void __launch_bounds__(RG_THREADS, 3) k_part_scatter(const uint64_t* 
 #pragma unroll
   for (int i = 0; i < RG_ITEMS; ++i) {
     const uint64_t idx = base + i * 32;
-    const bool valid = idx < n;
-    const uint64_t s = valid ? sort_key_of(keys[idx], qpos, rem, m, gp.rmap) : 0ull;
+    bool valid = idx < n;
+    uint64_t s = 0ull;
+    if (valid) {
+      s = gp.direct ? keys[idx] : sort_key_of(keys[idx], qpos, rem, m, gp.rmap);
+      valid = !(gp.direct && s == ~0ull);  // a dropped term (batched form) is left out
+    }
     k[i] = vb ? ((s << vb) | idx) : s;
     d[i] = valid ? (uint32_t)(s & dmask) : 16u;
   }
@@ -189,6 +200,7 @@ __global__ void __launch_bounds__(RG_THREADS, 3) k_part_scatter(const uint64_t* 
       if (lane >= o) x += y;
     }
     if (lane < D) s_local[lane] = x - cnt;
+    if (lane == D - 1) s_staged = x;  // terms of the tile that were staged
   }
   __syncthreads();
 #pragma unroll
@@ -200,7 +212,7 @@ __global__ void __launch_bounds__(RG_THREADS, 3) k_part_scatter(const uint64_t* 
     }
   }
   __syncthreads();
-  const uint32_t tile_n = (uint32_t)(n - t * RG_TILE < (uint64_t)RG_TILE ? n - t * RG_TILE : (uint64_t)RG_TILE);
+  const uint32_t tile_n = s_staged;
   for (uint32_t j = tid; j < tile_n; j += RG_THREADS) {
     const uint64_t key = s_keys[j];
     const uint32_t dd = (uint32_t)(key >> vb) & dmask;
