@@ -69,10 +69,16 @@ def parse():
     ap.add_argument("--no-whole", action="store_true", help="skip the whole-circuit legs and the c64 error report")
     ap.add_argument("--no-ring", action="store_true", help="skip the ring u3/cz (fusion) leg")
     ap.add_argument("--no-ab", action="store_true", help="skip the group-first / expand-first comparison")
+    ap.add_argument("--no-reserve", action="store_true",
+                    help="let the buffers grow on demand instead of sizing them for K up front (profiling "
+                         "runs: the device then holds about what the state needs)")
     ap.add_argument("--batch-circuits", type=int, default=512,
                     help="circuits of the batched-form leg (0: skip)")
     ap.add_argument("--serve-requests", type=int, default=256,
                     help="requests of the serving stream measured (0: skip the serving leg)")
+    ap.add_argument("--requests-log", default="",
+                    help="write one JSON line per request of the batched and serving legs to "
+                         "<prefix>_batched.jsonl / <prefix>_serving.jsonl")
     a = ap.parse_args()
     w = dict(WORKLOADS[a.workload])
     if a.K:
@@ -319,7 +325,8 @@ def run_steps(args, rank, prec_name, dev, stream, sample_clocks):
     gates = circ.gates
     kinds = [gate_kind(u) for _, u in gates]
     st = sv.SparseState(circ.n, wl["K"], wl["p"], prec=prec, stream=stream.cuda_stream)
-    st.reserve(wl["K"])  # every buffer sized for K-term states: no allocation inside the steps
+    if not args.no_reserve:
+        st.reserve(wl["K"])  # every buffer sized for K-term states: no allocation inside the steps
     gi = 0
     # ramp: the circuit from |0> until the state is at K terms (the p-mass cut
     # may keep it slightly below K: 99% counts as full)
@@ -350,6 +357,8 @@ def run_steps(args, rank, prec_name, dev, stream, sample_clocks):
     ck_keys, ck_amps = st.export()
     torch.cuda.synchronize(dev)
     pending = None
+    # an NVTX range names the timed steps (a profiler can select their launches)
+    torch.cuda.nvtx.range_push("timed")
     e0.record(stream)
     for _ in range(args.steps):
         j = gi % len(gates)
@@ -369,6 +378,7 @@ def run_steps(args, rank, prec_name, dev, stream, sample_clocks):
     if pending is not None:
         st.peak_wait(pending)
     e1.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize(dev)
     launches = sv.sv_launch_count() - l0
     ms = e0.elapsed_time(e1)
@@ -504,35 +514,97 @@ def run_e2e(args, rank, dev, stream):
             "peak_is_hidden": bool(key == circ.hidden), "peak_prob": pr}
 
 
-def peaked_check(batched, serial, circuits, oracle_results=None):
+AMP_TOL_C64 = 2e-6  # amplitude error allowed to the complex64 form on a peaked request
+
+
+def is_peaked(s) -> bool:
+    """A request's complex128 final state has a clear top: the top
+    probability exceeds the runner-up by more than the complex64 error
+    allows (relative gap > 1e-3) and the retained mass is above 1e-6."""
+    return s["gap"] > 1e-3 and s["F"] > 1e-6
+
+
+def amp_error(keys_a, amps_a, keys_b, amps_b):
+    """max |a - b| over the keys both states hold, and the count and
+    probability mass (in b) of the keys only one of them holds."""
+    import numpy as np
+    common, ia, ib = np.intersect1d(keys_a, keys_b, assume_unique=True, return_indices=True)
+    err = float(np.max(np.abs(amps_a[ia].astype(np.complex128) - amps_b[ib]))) if len(common) else 0.0
+    only_b = np.ones(len(keys_b), dtype=bool)
+    only_b[ib] = False
+    return err, len(keys_a) + len(keys_b) - 2 * len(common), float(np.sum(np.abs(amps_b[only_b]) ** 2))
+
+
+def peaked_check(batched, serial, circuits, checked=None):
     """Peaks of the complex64 batched results against the serial complex128
-    results.  A circuit counts as peaked when its complex128 final state has
-    a clear top: the top probability exceeds the runner-up by more than the
-    complex64 error allows (relative gap > 1e-3) and the retained mass is
-    above 1e-6."""
+    results, over all requests and over the peaked ones (is_peaked).  With
+    `checked` (complex64 results holding the final states of the peaked
+    requests) the amplitudes of every peaked request are compared with the
+    complex128 state on the common keys as well."""
     peaked = same = 0
     diff_peaked = []
+    errs = []
     for j, (b, s) in enumerate(zip(batched, serial)):
-        gap = s["gap"]
-        is_peaked = gap > 1e-3 and s["F"] > 1e-6
-        if is_peaked:
+        if is_peaked(s):
             peaked += 1
             if b.peak_key == s["key"]:
                 same += 1
             else:
                 diff_peaked.append(j)
+            if checked is not None and checked[j] is not None and checked[j].keys is not None and "keys" in s:
+                errs.append((j,) + amp_error(checked[j].keys, checked[j].amps, s["keys"], s["amps"]))
     all_same = sum(int(b.peak_key == s["key"]) for b, s in zip(batched, serial))
-    return {"identical_peaks_all": f"{all_same}/{len(serial)}",
-            "peaked_requests": peaked, "identical_peaks_on_peaked": f"{same}/{peaked}",
-            "peaked_rule": "complex128 top-two relative probability gap > 1e-3 and retained mass > 1e-6",
-            "differing_peaked_indices": diff_peaked[:20]}
+    out = {"identical_peaks_all": f"{all_same}/{len(serial)}",
+           "peaked_requests": peaked, "identical_peaks_on_peaked": f"{same}/{peaked}",
+           "peaked_rule": "complex128 top-two relative probability gap > 1e-3 and retained mass > 1e-6",
+           "differing_peaked_indices": diff_peaked[:20]}
+    if errs:
+        e = [x[1] for x in errs]
+        over = [x[0] for x in errs if x[1] > AMP_TOL_C64]
+        out["amp_check_on_peaked"] = {
+            "requests": len(errs), "max_abs_amp_err": max(e), "median_abs_amp_err": statistics.median(e),
+            "within_tol": f"{len(errs) - len(over)}/{len(errs)}", "tol": AMP_TOL_C64,
+            "over_tol_indices": over[:20],
+            "max_sym_diff_count": max(x[2] for x in errs), "max_sym_diff_mass": max(x[3] for x in errs),
+            "scope": "complex64 batched final state vs complex128 serial, on the keys both hold"}
+    return out
 
 
-def serial_c128(circuits, stream, arrivals=None):
+def request_table(circuits, batched, serial):
+    """Per request: size, the complex64 batched result (peak probability,
+    retained mass) and the complex128 serial one."""
+    rows = []
+    for j, (c, b, s) in enumerate(zip(circuits, batched, serial)):
+        rows.append({"j": j, "n": c.n, "K": c.K, "gates": len(c.gates), "peaked": is_peaked(s),
+                     "c64_peak_prob": b.peak_prob, "c64_retained_mass": b.retained_mass,
+                     "c128_peak_prob": s["prob"], "c128_retained_mass": s["F"],
+                     "same_peak": bool(b.peak_key == s["key"])})
+    return rows
+
+
+def quantiles(v):
+    import numpy as np
+    v = np.asarray(v, dtype=float)
+    return {"min": float(v.min()), "p50": float(np.median(v)), "max": float(v.max())} if len(v) else None
+
+
+def request_summary(rows, path=None):
+    if path:
+        with open(path, "w") as f:
+            for r in rows:
+                f.write(json.dumps(r) + "\n")
+    return {"c64_retained_mass": quantiles([r["c64_retained_mass"] for r in rows]),
+            "c64_peak_prob": quantiles([r["c64_peak_prob"] for r in rows]),
+            "c64_peak_prob_on_peaked": quantiles([r["c64_peak_prob"] for r in rows if r["peaked"]]),
+            "log": path}
+
+
+def serial_c128(circuits, stream, arrivals=None, keep_peaked=False):
     """The serial plain path: every circuit alone on the single-state
     complex128 API, one after the other (waiting for each arrival when
     arrival times are given); per circuit: service time, finish time, peak,
-    runner-up gap and retained mass."""
+    runner-up gap and retained mass (with keep_peaked, also the final state
+    of every peaked request, read off the clock)."""
     from paper_2607_07816_b300 import sv
     out = []
     t0 = time.perf_counter()
@@ -552,12 +624,27 @@ def serial_c128(circuits, stream, arrivals=None):
         # the service, so its time is taken off the clock
         _, probs = st.probs()
         F = st.retained_mass()
+        second = float(probs[1]) if len(probs) > 1 else 0.0
+        rec = {"key": key, "prob": prob, "F": F, "gap": (prob - second) / prob if prob > 0 else 0.0}
+        if keep_peaked and is_peaked(rec):
+            rec["keys"], rec["amps"] = st.export()
         st.close()
         t0 += time.perf_counter() - te
-        second = float(probs[1]) if len(probs) > 1 else 0.0
-        out.append({"svc": te - ts, "finish": te - t0, "key": key, "prob": prob, "F": F,
-                    "gap": (prob - second) / prob if prob > 0 else 0.0})
+        rec.update({"svc": te - ts, "finish": te - t0})
+        out.append(rec)
     return out
+
+
+def peaked_states_c64(circuits, serial, n_max, stream):
+    """The complex64 batched final states of the peaked requests (an
+    untimed run of the same serving loop)."""
+    from paper_2607_07816_b300 import serve, sv
+    want = [j for j, s in enumerate(serial) if is_peaked(s)]
+    srv = serve.Server(160 << 30, n_max=n_max, prec=sv.SV_C64, stream=stream)
+    try:
+        return srv.run(circuits, export=want)
+    finally:
+        srv.close()
 
 
 def run_batched(args, rank, dev, stream):
@@ -579,7 +666,7 @@ def run_batched(args, rank, dev, stream):
     w.close()
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    ser = serial_c128(circs, s)
+    ser = serial_c128(circs, s, keep_peaked=True)  # the peaked states are read off the clock
     serial_s = time.perf_counter() - t0
     srv = serve.Server(160 << 30, n_max=n_max, prec=sv.SV_C64, stream=s)
     t0 = time.perf_counter()
@@ -592,7 +679,9 @@ def run_batched(args, rank, dev, stream):
     out = {"circuits": R, "prec": "c64 batched vs c128 serial", "serial_circuits_per_s": R / serial_s,
            "batched_circuits_per_s": R / batched_s, "speedup": serial_s / batched_s, "steps": steps,
            "serial_s": serial_s, "batched_s": batched_s, "graphs": graphs}
-    out.update(peaked_check(res, ser, circs))
+    out.update(peaked_check(res, ser, circs, peaked_states_c64(circs, ser, n_max, s)))
+    log = args.requests_log + "_batched.jsonl" if args.requests_log else None
+    out["per_request"] = request_summary(request_table(circs, res, ser), log)
     return out
 
 
@@ -630,7 +719,7 @@ def run_serving(args, rank, dev, stream):
     open_s = time.perf_counter() - t0
     srv.close()
     p50, p99 = serve.percentiles(opened)
-    ser = serial_c128(reqs, s, arrivals=arrivals)
+    ser = serial_c128(reqs, s, arrivals=arrivals, keep_peaked=True)
     s_lat = np.array([x["finish"] - a for x, a in zip(ser, arrivals)])
     serial_cps = R / sum(x["svc"] for x in ser)
     out = {"requests": R, "large_requests": sum(int(c.n == 56) for c in reqs), "budget_gb": 160,
@@ -645,7 +734,9 @@ def run_serving(args, rank, dev, stream):
            "speedup_circuits_per_s": capacity / serial_cps,
            "served_results_equal_to_saturated_run": "%d/%d" % (
                sum(int(a.peak_key == b.peak_key and a.peak_prob == b.peak_prob) for a, b in zip(opened, closed)), R)}
-    out.update(peaked_check(closed, ser, reqs))
+    out.update(peaked_check(closed, ser, reqs, peaked_states_c64(reqs, ser, n_max, s)))
+    log = args.requests_log + "_serving.jsonl" if args.requests_log else None
+    out["per_request"] = request_summary(request_table(reqs, closed, ser), log)
     return out
 
 

@@ -108,14 +108,20 @@ class Server:
         run).  A request is admitted, in arrival order, once it has arrived,
         a slot is free and its footprint fits the budget (one request is
         always admitted into an empty batch).  With export the final state of
-        each circuit is returned as well.  max_steps stops the loop after that
-        many steps (unfinished requests then have no Result).
+        each circuit is returned as well (export may also be a collection of
+        request indices: only those are exported).  max_steps stops the loop
+        after that many steps (unfinished requests then have no Result).
 
         Each admitted circuit's gates are converted once into the library's
         gate layout; the gate table of a step is then gathered with array
         indexing from the concatenated tables of the resident circuits
         (rebuilt only when residents change)."""
         n = len(circuits)
+        if isinstance(export, bool):
+            wants = (lambda j: export)  # noqa: E731
+        else:
+            chosen = set(int(j) for j in export)
+            wants = chosen.__contains__
         arrivals = np.zeros(n) if arrivals is None else np.asarray(arrivals, dtype=float)
         if clock is None:
             t0 = time.perf_counter()
@@ -145,7 +151,7 @@ class Server:
                     key, prob = st.peak()
                     f = st.retained_mass()
                     ks = am = None
-                    if export:
+                    if wants(j):
                         ks, am = st.export()
                 finally:
                     st.close()
@@ -234,7 +240,7 @@ class Server:
                     key, prob = self.batch.peak(slot)
                     f = self.batch.retained_mass(slot)
                     ks = am = None
-                    if export:
+                    if wants(j):
                         ks, am = self.batch.export(slot)
                     self.batch.remove(slot)
                     retiring += 1

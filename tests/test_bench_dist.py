@@ -59,3 +59,33 @@ def test_single_process_reduce_is_identity():
     assert bench.dist_reduce([3, 4.5], "max") == [3.0, 4.5]
     rate, units, ms = bench.whole_job_rate(500.0, 250.0)
     assert (rate, units, ms) == (2000.0, 500.0, 250.0)
+
+
+def test_amp_error_and_peaked_check():
+    """The complex64-vs-complex128 comparison of the serving legs: amplitude
+    error on the common keys, the keys held by one side only, and the peak
+    counts restricted to the peaked requests."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    ka = np.array([1, 5, 9], dtype=np.uint64)
+    aa = np.array([0.6, 0.8j, 1e-3], dtype=np.complex64)
+    kb = np.array([9, 1, 7, 5], dtype=np.uint64)
+    ab = np.array([1e-3, 0.6 + 1e-6, 0.01, 0.8j], dtype=np.complex128)
+    err, nd, mass = bench.amp_error(ka, aa, kb, ab)
+    assert err == pytest.approx(1e-6, rel=0.2, abs=3e-8)  # float32 rounding of 0.6 is ~2e-8
+    assert nd == 1 and mass == pytest.approx(1e-4)
+
+    class R:
+        def __init__(self, key, keys=None, amps=None):
+            self.peak_key, self.keys, self.amps = key, keys, amps
+
+    serial = [{"key": 1, "gap": 0.5, "F": 0.9, "keys": kb, "amps": ab},  # peaked
+              {"key": 2, "gap": 1e-5, "F": 0.9},                          # no clear top
+              {"key": 3, "gap": 0.5, "F": 1e-9}]                          # mass too small
+    batched = [R(1), R(4), R(3)]
+    chk = [R(1, ka, aa), None, None]
+    out = bench.peaked_check(batched, serial, [None] * 3, chk)
+    assert out["peaked_requests"] == 1 and out["identical_peaks_on_peaked"] == "1/1"
+    assert out["identical_peaks_all"] == "2/3"
+    assert out["amp_check_on_peaked"]["within_tol"] == "1/1"
