@@ -88,4 +88,6 @@ def test_amp_error_and_peaked_check():
     out = bench.peaked_check(batched, serial, [None] * 3, chk)
     assert out["peaked_requests"] == 1 and out["identical_peaks_on_peaked"] == "1/1"
     assert out["identical_peaks_all"] == "2/3"
-    assert out["amp_check_on_peaked"]["within_tol"] == "1/1"
+    chk_out = out["amp_check_on_peaked"]
+    assert chk_out["different_kept_set"]["within_tol"] == "1/1"  # key 7 is held by one side only
+    assert chk_out["same_kept_set"] == {"requests": 0}
