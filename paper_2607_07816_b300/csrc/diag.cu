@@ -39,6 +39,49 @@ struct DCplx<float> {
   __device__ static float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 };
 
+// x times an entry that is +-1 or +-i, with the fused chain of the general
+// path: each product is exact and the chain adds it to +0, so the result is
+// a component of x, negated or not, with -0 turned into +0.  Taken with
+// integer operations (the FP64 pipe is the scarce unit of the complex128
+// path).
+__device__ __forceinline__ double unit_part(double v, bool neg) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(v) ^ ((unsigned long long)neg << 63);
+  if ((b << 1) == 0ull) b = 0ull;
+  return __longlong_as_double((long long)b);
+}
+__device__ __forceinline__ float unit_part(float v, bool neg) {
+  uint32_t b = __float_as_uint(v) ^ ((uint32_t)neg << 31);
+  if ((b << 1) == 0u) b = 0u;
+  return __uint_as_float(b);
+}
+
+// y = u x for one entry u = (ur, ui) with nonzero components rz / iz; unit:
+// u is one of +-1, +-i (neg: its nonzero component is -1).
+template <typename Real>
+__device__ __forceinline__ void entry_times(Real ur, Real ui, bool rz, bool iz, bool unit, bool neg, Real xr, Real xi,
+                                            Real& re, Real& im) {
+  re = (Real)0;
+  im = (Real)0;
+  if (unit) {
+    if (rz) {  // u = s: (s xr, s xi)
+      re = unit_part(xr, neg);
+      im = unit_part(xi, neg);
+    } else {  // u = s i: (-s xi, s xr)
+      re = unit_part(xi, !neg);
+      im = unit_part(xr, neg);
+    }
+    return;
+  }
+  if (rz) {
+    re = DCplx<Real>::fma(ur, xr, re);
+    im = DCplx<Real>::fma(ur, xi, im);
+  }
+  if (iz) {
+    re = DCplx<Real>::fma(-ui, xi, re);
+    im = DCplx<Real>::fma(ui, xr, im);
+  }
+}
+
 template <typename Real>
 __global__ void __launch_bounds__(DG_BLOCK) k_diag_apply(const uint64_t* __restrict__ keys,
                                                         typename DCplx<Real>::T* __restrict__ amps,
@@ -75,16 +118,9 @@ __global__ void __launch_bounds__(DG_BLOCK) k_diag_apply(const uint64_t* __restr
 #pragma unroll
       for (int t = 0; t < 4; ++t)
         if (t < m) r |= (uint32_t)((k[j] >> dp.qpos[t]) & 1ull) << t;
-      const Real ur = s_ur[r], ui = s_ui[r];
-      Real re = (Real)0, im = (Real)0;
-      if ((dp.rnz >> r) & 1u) {
-        re = DCplx<Real>::fma(ur, x[j].x, re);
-        im = DCplx<Real>::fma(ur, x[j].y, im);
-      }
-      if ((dp.inz >> r) & 1u) {
-        re = DCplx<Real>::fma(-ui, x[j].y, re);
-        im = DCplx<Real>::fma(ui, x[j].x, im);
-      }
+      Real re, im;
+      entry_times(s_ur[r], s_ui[r], (dp.rnz >> r) & 1u, (dp.inz >> r) & 1u, (dp.unit >> r) & 1u, (dp.uneg >> r) & 1u,
+                  x[j].x, x[j].y, re, im);
       C2 y;
       y.x = re;
       y.y = im;
@@ -155,16 +191,9 @@ __global__ void __launch_bounds__(DG_BLOCK) k_mono_apply(const uint64_t* __restr
       if (i >= n) continue;
       const uint64_t key = v[j] >> vb;  // the output's stored key: rest above, r' at the bottom
       const uint32_t ro = (uint32_t)key & dmask;
-      const Real ur = s_ur[ro], ui = s_ui[ro];
-      Real re = (Real)0, im = (Real)0;
-      if ((mp.rnz >> ro) & 1u) {
-        re = DCplx<Real>::fma(ur, x[j].x, re);
-        im = DCplx<Real>::fma(ur, x[j].y, im);
-      }
-      if ((mp.inz >> ro) & 1u) {
-        re = DCplx<Real>::fma(-ui, x[j].y, re);
-        im = DCplx<Real>::fma(ui, x[j].x, im);
-      }
+      Real re, im;
+      entry_times(s_ur[ro], s_ui[ro], (mp.rnz >> ro) & 1u, (mp.inz >> ro) & 1u, (mp.unit >> ro) & 1u,
+                  (mp.uneg >> ro) & 1u, x[j].x, x[j].y, re, im);
       C2 y;
       y.x = re;
       y.y = im;

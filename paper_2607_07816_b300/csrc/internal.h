@@ -206,6 +206,7 @@ void launch_local_gate(int prec, const uint64_t* keys, const void* amps, uint64_
 struct DiagParams {
   double ur[16], ui[16];
   uint32_t rnz, inz;
+  uint32_t unit, uneg;  // bit r: entry r is +-1 or +-i; its nonzero component is -1
   int m;
   int qpos[4];
 };
@@ -223,6 +224,7 @@ void launch_diag_apply(int prec, const uint64_t* keys, void* amps, uint64_t* pro
 struct MonoParams {
   double ur[16], ui[16];
   uint32_t rnz, inz;
+  uint32_t unit, uneg;  // as in DiagParams, by output index r'
   int m, vbits;
 };
 void launch_mono_apply(int prec, const uint64_t* sk, const uint32_t* sidx, uint64_t n, const void* amps_in,

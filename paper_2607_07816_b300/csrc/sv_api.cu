@@ -539,6 +539,22 @@ sv_status sv_destroy(sv_state* s) {
   return SV_OK;
 }
 
+// Entries (ur[r], ui[r]) that are +-1 or +-i, given which components are
+// nonzero (rnz / inz bit r): their products are taken without the FP64 pipe
+// (unit), neg when the nonzero component is -1.
+static void unit_entries(const double* ur, const double* ui, uint32_t rnz, uint32_t inz, int d, uint32_t* unit,
+                         uint32_t* uneg) {
+  *unit = *uneg = 0;
+  for (int r = 0; r < d; ++r) {
+    const bool rz = (rnz >> r) & 1u, iz = (inz >> r) & 1u;
+    const double v = rz ? ur[r] : ui[r];
+    if (rz != iz && (v == 1.0 || v == -1.0)) {
+      *unit |= 1u << r;
+      if (v < 0) *uneg |= 1u << r;
+    }
+  }
+}
+
 sv_status sv_apply_gate(sv_state* s, int m, const int* qubits, const double* U) {
   SV_GUARD(s);
   if (m < 1 || m > 4 || !qubits || !U) return fail(s, SV_E_ARG, "sv_apply_gate: bad m or null pointer");
@@ -625,6 +641,7 @@ sv_status sv_apply_gate(sv_state* s, int m, const int* qubits, const double* U) 
       dp.rnz |= gp.re_nz[r] & (1u << r);
       dp.inz |= gp.im_nz[r] & (1u << r);
     }
+    unit_entries(dp.ur, dp.ui, dp.rnz, dp.inz, d, &dp.unit, &dp.uneg);
     ++s->global_gates;
     ++s->stats.diag_gates;
     // clears the gate's counters (zero count, total mass); no table to store
@@ -786,6 +803,7 @@ sv_status sv_apply_gate(sv_state* s, int m, const int* qubits, const double* U) 
         mp.rnz |= ((gp.re_nz[ro] >> r) & 1u) << ro;
         mp.inz |= ((gp.im_nz[ro] >> r) & 1u) << ro;
       }
+      unit_entries(mp.ur, mp.ui, mp.rnz, mp.inz, d, &mp.unit, &mp.uneg);
       ph_begin(s, PH_APPLY);
       launch_mono_apply(s->prec, s->sk[w], s->sidx[w], N, s->amps[s->cur], mp, s->keys[alt], s->amps[alt],
                         s->probs[alt], s->ctl, s->st);
