@@ -28,9 +28,11 @@ __device__ __forceinline__ uint64_t natural_key(const uint64_t* nat, uint64_t k)
 // The list is the window buffer when the window pass set use_window, else
 // all terms: the choice and the list length are read on the device, so the
 // select can be enqueued before the window is known.  Block b scans a
-// contiguous chunk of at least 8192 terms (each block flushes up to
+// contiguous chunk of at least SH_CHUNK terms (each block flushes up to
 // 3 * SEL_BINS global atomics, so blocks get a large share each).
-__global__ void __launch_bounds__(256) k_select_hist(const uint64_t* __restrict__ probs,
+constexpr int SH_UNROLL = 8;
+constexpr uint64_t SH_CHUNK = 4096;
+__global__ void __launch_bounds__(256, 4) k_select_hist(const uint64_t* __restrict__ probs,
                                                      const uint64_t* __restrict__ keys, uint64_t n,
                                                      const uint64_t* __restrict__ wp, const uint32_t* __restrict__ wi,
                                                      Ctl* ctl, uint32_t* __restrict__ g_cnt,
@@ -45,7 +47,7 @@ __global__ void __launch_bounds__(256) k_select_hist(const uint64_t* __restrict_
   const uint64_t* nat = ctl->nat;
   const uint64_t nn = win ? ctl->win_n : n;
   uint64_t chunk = (nn + gridDim.x - 1) / gridDim.x;
-  if (chunk < 8192) chunk = 8192;
+  if (chunk < SH_CHUNK) chunk = SH_CHUNK;
   const uint64_t c0 = blockIdx.x * chunk;
   if (c0 >= nn) return;
   const uint64_t c1 = c0 + chunk < nn ? c0 + chunk : nn;
@@ -60,14 +62,33 @@ __global__ void __launch_bounds__(256) k_select_hist(const uint64_t* __restrict_
   }
   __syncthreads();
   BinCache cache;
-  for (uint64_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
-    const uint64_t pb = P[i];
-    const uint64_t hi = ~pb;
-    if (bits <= 64 && bits > 0 && ((hi ^ ph) >> (64 - bits)) != 0) continue;
-    // the stored key (made natural) only where a tie on the probability needs it
-    const uint64_t lo = need_lo ? natural_key(nat, keys[win ? (uint64_t)wi[i] : i]) : 0ull;
-    if (bits > 64 && !z_matches(hi, lo, ph, pl, bits)) continue;
-    hist_add(z_digit(hi, lo, shift, D), pb, s_cnt, s_mass, &ctl->err, cache);
+  // SH_UNROLL terms per thread at a time, their loads issued together (the
+  // bins' sums are exact integers, so the order of the additions is free)
+  for (uint64_t i0 = c0 + threadIdx.x; i0 < c1; i0 += (uint64_t)SH_UNROLL * blockDim.x) {
+    uint64_t pbv[SH_UNROLL], lov[SH_UNROLL];
+#pragma unroll
+    for (int u = 0; u < SH_UNROLL; ++u) {
+      const uint64_t i = i0 + (uint64_t)u * blockDim.x;
+      pbv[u] = i < c1 ? P[i] : 0ull;
+    }
+    if (need_lo) {  // the stored key (made natural) only where a tie on the probability needs it
+#pragma unroll
+      for (int u = 0; u < SH_UNROLL; ++u) {
+        const uint64_t i = i0 + (uint64_t)u * blockDim.x;
+        lov[u] = i < c1 ? keys[win ? (uint64_t)wi[i] : i] : 0ull;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < SH_UNROLL; ++u) {
+      const uint64_t i = i0 + (uint64_t)u * blockDim.x;
+      if (i >= c1) continue;
+      const uint64_t pb = pbv[u];
+      const uint64_t hi = ~pb;
+      if (bits <= 64 && bits > 0 && ((hi ^ ph) >> (64 - bits)) != 0) continue;
+      const uint64_t lo = need_lo ? natural_key(nat, lov[u]) : 0ull;
+      if (bits > 64 && !z_matches(hi, lo, ph, pl, bits)) continue;
+      hist_add(z_digit(hi, lo, shift, D), pb, s_cnt, s_mass, &ctl->err, cache);
+    }
   }
   bin_cache_flush(cache, s_cnt, s_mass);
   __syncthreads();
@@ -84,8 +105,8 @@ __global__ void __launch_bounds__(256) k_select_hist(const uint64_t* __restrict_
 void launch_select_hist(const uint64_t* probs, const uint64_t* keys, uint64_t n, Ctl* ctl,
                         const SelectScratch& ss, cudaStream_t st) {
   if (n == 0) return;
-  uint64_t blocks = (n + 8191) / 8192;
-  if (blocks > 148 * 4) blocks = 148 * 4;
+  uint64_t blocks = (n + SH_CHUNK - 1) / SH_CHUNK;
+  if (blocks > 148 * 4) blocks = 148 * 4;  // four resident per SM (40 KB of bins each)
   launch_pdl(k_select_hist, (unsigned)blocks, 256, 0, st, probs, keys, n, ss.win_p, ss.win_i, ctl, ss.hist_count,
              ss.hist_mass);
 }
@@ -631,10 +652,14 @@ __global__ void k_window_decide(Ctl* ctl, int mode, uint64_t count_target, doubl
 
 constexpr size_t SAMPLE_SMEM = 4 * (2 * SAMPLE_N + 32 * 256) + 8 * SAMPLE_THREADS;
 
+static cudaError_t finish_attr();
+
 cudaError_t select_prepare() {
   static DeviceOnce once;
   return once.run([] {
-    return cudaFuncSetAttribute(k_sample_window, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SAMPLE_SMEM);
+    cudaError_t e = cudaFuncSetAttribute(k_sample_window, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)SAMPLE_SMEM);
+    return e == cudaSuccess ? finish_attr() : e;
   });
 }
 
@@ -920,71 +945,117 @@ void launch_select_compact(const uint64_t* probs, const uint64_t* keys, uint64_t
   launch_pdl(k_select_compact, (unsigned)blocks, 256, 0, st, probs, keys, n, ss.win_p, ss.win_i, ctl, ss.buf);
 }
 
+// The chosen bin's terms (at most FINISH_CAP, gathered by k_select_compact)
+// are sorted in shared memory by Z (a bitonic network over the next power of
+// two, padded with the largest Z), their exact masses prefix-summed in that
+// order, and the cut is the first of them where the running count or mass
+// (after the terms before the bin) reaches the target -- the same term the
+// radix levels would isolate, found without further levels (ties on the
+// probability, common in states with equal-magnitude amplitudes, cost no
+// extra passes).
+constexpr size_t FINISH_SMEM = sizeof(uint64_t) * 2 * FINISH_CAP;
+
 __global__ void __launch_bounds__(PICK_THREADS) k_select_finish(Ctl* ctl, const uint64_t* buf,
                                                                 double p) {
   pdl_prologue();
-  __shared__ uint32_t s_cnt[SEL_BINS];
-  __shared__ uint64_t s_mass[2 * SEL_BINS];
+  (void)p;
+  extern __shared__ __align__(16) uint8_t s_dyn[];
+  uint64_t* zh = reinterpret_cast<uint64_t*>(s_dyn);
+  uint64_t* zl = zh + FINISH_CAP;
+  __shared__ u128 w_m[PICK_THREADS / 32];
+  __shared__ uint32_t s_first;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const bool gated = ctl->sel_gated != 0;
+  const bool done = ctl->sel_done != 0;
   const uint64_t bin0 = ctl->sel_bin_count;
   uint64_t nb = ctl->compact_n;
   __syncthreads();
-  if (threadIdx.x == 0) {  // the gated run ends here; the next gather starts from an empty buffer
+  if (tid == 0) {  // the gated run ends here; the next gather starts from an empty buffer
     ctl->sel_gated = 0;
     ctl->compact_n = 0;
   }
-  if (gated && bin0 > (uint64_t)FINISH_CAP) return;
+  if (done || (gated && bin0 > (uint64_t)FINISH_CAP)) return;
   if (nb > FINISH_CAP) nb = FINISH_CAP;
-  for (int it = 0; it < 128; ++it) {
-    __syncthreads();
-    if (ctl->sel_done) break;
-    const int bits = (int)ctl->sel_bits;
-    const uint64_t ph = ctl->sel_prefix_hi, pl = ctl->sel_prefix_lo;
-    if (ctl->sel_bin_count == 1) {
-      // one term left under the prefix: it is the cut, and the terms before
-      // it in canonical order are the ones counted so far
-      for (uint64_t i = threadIdx.x; i < nb; i += blockDim.x) {
-        const uint64_t hi = buf[2 * i], lo = buf[2 * i + 1];
-        if (!z_matches(hi, lo, ph, pl, bits)) continue;
-        const uint64_t pbits = ~hi;
-        const u128 sc = make_u128(ctl->sel_before_mass_hi, ctl->sel_before_mass_lo) + fx_from_bits(pbits, &ctl->err);
-        const uint64_t cc = ctl->sel_before_count + 1;
-        const u128 target = make_u128(ctl->sel_target_hi, ctl->sel_target_lo);
-        if (!(ctl->sel_mode == 1 ? (u128)cc >= target : sc >= target)) {
-          ctl->sel_done = 2;  // the target is never reached: no cut
-          continue;
+  uint32_t n2 = 1;
+  while (n2 < nb) n2 <<= 1;
+  for (uint32_t i = tid; i < n2; i += PICK_THREADS) {
+    const bool real = i < nb;
+    zh[i] = real ? buf[2 * i] : ~0ull;
+    zl[i] = real ? buf[2 * i + 1] : ~0ull;
+  }
+  __syncthreads();
+  for (uint32_t k = 2; k <= n2; k <<= 1) {
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t t = tid; t < n2 / 2; t += PICK_THREADS) {
+        const uint32_t i = 2 * t - (t & (j - 1));  // bit j of i clear; its partner is i + j
+        const uint32_t l = i + j;
+        const uint64_t ah = zh[i], al = zl[i], bh = zh[l], bl = zl[l];
+        const bool gt = ah > bh || (ah == bh && al > bl);
+        if (gt == ((i & k) == 0)) {  // ascending where bit k of i is clear
+          zh[i] = bh;
+          zl[i] = bl;
+          zh[l] = ah;
+          zl[l] = al;
         }
-        ctl->cut_pbits = pbits;
-        ctl->cut_key = lo;
-        ctl->cut_count = cc;
-        ctl->cut_mass_hi = (uint64_t)(sc >> 64);
-        ctl->cut_mass_lo = (uint64_t)sc;
-        ctl->sel_done = 1;
       }
       __syncthreads();
-      if (ctl->sel_done) break;
     }
-    int D, shift;
-    sel_digit(bits, &D, &shift);
-    for (int i = threadIdx.x; i < SEL_BINS; i += blockDim.x) {
-      s_cnt[i] = 0;
-      s_mass[2 * i] = s_mass[2 * i + 1] = 0;
+  }
+  // each thread a contiguous run of the sorted terms: exact masses scanned
+  const uint32_t per = (n2 + PICK_THREADS - 1) / PICK_THREADS;
+  const uint32_t b0 = (uint32_t)tid * per;
+  u128 my = 0;
+  for (uint32_t i = b0; i < b0 + per && i < nb; ++i) my += fx_from_bits(~zh[i], &ctl->err);
+  u128 x = my;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const u128 y = shfl_up_u128(x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) w_m[warp] = x;
+  if (tid == 0) s_first = 0xffffffffu;
+  __syncthreads();
+  u128 base = 0;
+  for (int w = 0; w < warp; ++w) base += w_m[w];
+  const uint32_t mode = ctl->sel_mode;
+  const u128 target = make_u128(ctl->sel_target_hi, ctl->sel_target_lo);
+  const uint64_t before_c = ctl->sel_before_count;
+  const u128 before_m = make_u128(ctl->sel_before_mass_hi, ctl->sel_before_mass_lo) + base + x - my;
+  {
+    u128 cm = before_m;
+    for (uint32_t i = b0; i < b0 + per && i < nb; ++i) {
+      cm += fx_from_bits(~zh[i], &ctl->err);
+      if (mode == 1 ? (u128)(before_c + i + 1) >= target : cm >= target) {
+        atomicMin(&s_first, i);
+        break;
+      }
     }
-    __syncthreads();
-    BinCache cache;
-    for (uint64_t i = threadIdx.x; i < nb; i += blockDim.x) {
-      const uint64_t hi = buf[2 * i], lo = buf[2 * i + 1];
-      if (!z_matches(hi, lo, ph, pl, bits)) continue;
-      hist_add(z_digit(hi, lo, shift, D), ~hi, s_cnt, s_mass, &ctl->err, cache);
-    }
-    bin_cache_flush(cache, s_cnt, s_mass);
-    __syncthreads();
-    block_pick(s_cnt, s_mass, ctl, p);
+  }
+  __syncthreads();
+  const uint32_t first = s_first;
+  if (first == 0xffffffffu) {
+    if (tid == 0) ctl->sel_done = 2;  // the target is never reached: no cut
+    return;
+  }
+  if (first >= b0 && first < b0 + per) {
+    u128 sc = before_m;
+    for (uint32_t i = b0; i <= first; ++i) sc += fx_from_bits(~zh[i], &ctl->err);
+    ctl->cut_pbits = ~zh[first];
+    ctl->cut_key = zl[first];
+    ctl->cut_count = before_c + first + 1;
+    ctl->cut_mass_hi = (uint64_t)(sc >> 64);
+    ctl->cut_mass_lo = (uint64_t)sc;
+    ctl->sel_done = 1;
   }
 }
 
+static cudaError_t finish_attr() {
+  return cudaFuncSetAttribute(k_select_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FINISH_SMEM);
+}
+
 void launch_select_finish(Ctl* ctl, const SelectScratch& ss, double p, cudaStream_t st) {
-  launch_pdl(k_select_finish, 1, PICK_THREADS, 0, st, ctl, ss.buf, p);
+  (void)select_prepare();  // checked at the handle's creation
+  launch_pdl(k_select_finish, 1, PICK_THREADS, FINISH_SMEM, st, ctl, ss.buf, p);
 }
 
 // ---------------------------------------------------------------- peak partials
