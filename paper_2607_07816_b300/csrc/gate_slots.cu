@@ -269,8 +269,11 @@ struct SlotsLayout {
   }
 };
 
+// complex128 at four blocks per SM (64 registers); complex64 without a
+// minimum (0: the compiler's own register choice, 40-48, which measured
+// fastest for the float kernel)
 template <typename Real, int GPL>
-__global__ void __launch_bounds__(AS_BLOCK, 4) k_gate_apply_slots(
+__global__ void __launch_bounds__(AS_BLOCK, sizeof(Real) == 8 ? 4 : 0) k_gate_apply_slots(
     const uint64_t* __restrict__ sk, const uint32_t* __restrict__ sidx, const uint32_t* __restrict__ heads,
     const uint32_t* __restrict__ gmask, const uint64_t* __restrict__ ooff,
     const typename SCplx<Real>::T* __restrict__ amps_in, const GateParams gp, uint64_t* __restrict__ keys_out,
@@ -308,6 +311,7 @@ __global__ void __launch_bounds__(AS_BLOCK, 4) k_gate_apply_slots(
   // the integer pipe while the FP64 pipe does the multiply-adds (the
   // truncation's window pass then needs no per-term mass for a top-K cut)
   constexpr bool MASS = sizeof(Real) == 8;
+  constexpr bool COALESCED = sizeof(Real) == 8;
   u128 tot = 0;
   // batches are taken from a counter (ctl->tile_counter[1], cleared with the
   // gate's tables): warps whose groups have more members take fewer batches
@@ -345,39 +349,50 @@ __global__ void __launch_bounds__(AS_BLOCK, 4) k_gate_apply_slots(
       mrun += __shfl_sync(0xffffffffu, mx, 31);
       ng += (uint32_t)__popc(__ballot_sync(0xffffffffu, s[k] != 0));
     }
-    // The batch's groups are consecutive in the grouped order, so their
-    // members are the mrun terms from the first group's head on, member t of
-    // group j at mb[j] + t: all lanes load them together (coalesced keys or
-    // indices, then the amplitude gathers, AS_UNROLL of each in flight).
-    // Each group's first key gives its rest.
+    // Each group's first key gives its rest.  complex128: the batch's groups
+    // are consecutive in the grouped order, so their members are the mrun
+    // terms from the first group's head on, member t of group j at mb[j] + t:
+    // all lanes load them together (coalesced keys or indices, then the
+    // amplitude gathers, AS_UNROLL of each in flight).  complex64 (measured
+    // faster at its higher occupancy): each lane loads its groups' members.
     uint64_t rest[GPL];
 #pragma unroll
     for (int k = 0; k < GPL; ++k) rest[k] = s[k] ? sk[h[k]] : 0ull;
-    const uint64_t e0 = __shfl_sync(0xffffffffu, (uint64_t)h[0], 0);  // head of group wb * gc (< G)
-    for (uint32_t i0 = 0; i0 < mrun; i0 += 32u * AS_UNROLL) {
-      uint64_t src[AS_UNROLL];
+    if (COALESCED) {
+      const uint64_t e0 = __shfl_sync(0xffffffffu, (uint64_t)h[0], 0);  // head of group wb * gc (< G)
+      for (uint32_t i0 = 0; i0 < mrun; i0 += 32u * AS_UNROLL) {
+        uint64_t src[AS_UNROLL];
 #pragma unroll
-      for (int u = 0; u < AS_UNROLL; ++u) {
-        const uint32_t i = i0 + 32u * u + lane;
-        src[u] = 0;
-        if (i < mrun) src[u] = vb ? (sk[e0 + i] & imask) : (uint64_t)sidx[e0 + i];
+        for (int u = 0; u < AS_UNROLL; ++u) {
+          const uint32_t i = i0 + 32u * u + lane;
+          src[u] = 0;
+          if (i < mrun) src[u] = vb ? (sk[e0 + i] & imask) : (uint64_t)sidx[e0 + i];
+        }
+        C2 xv[AS_UNROLL];
+#pragma unroll
+        for (int u = 0; u < AS_UNROLL; ++u)
+          if (i0 + 32u * u + lane < mrun) xv[u] = amps_in[src[u]];
+#pragma unroll
+        for (int u = 0; u < AS_UNROLL; ++u)
+          if (i0 + 32u * u + lane < mrun) w.x[i0 + 32u * u + lane] = xv[u];
       }
-      C2 xv[AS_UNROLL];
-#pragma unroll
-      for (int u = 0; u < AS_UNROLL; ++u)
-        if (i0 + 32u * u + lane < mrun) xv[u] = amps_in[src[u]];
-#pragma unroll
-      for (int u = 0; u < AS_UNROLL; ++u)
-        if (i0 + 32u * u + lane < mrun) w.x[i0 + 32u * u + lane] = xv[u];
     }
 #pragma unroll
     for (int k = 0; k < GPL; ++k) {
       if (!s[k]) continue;
+      const uint64_t v0 = rest[k];
+      if (!COALESCED) {
+        w.x[mb[k]] = amps_in[vb ? (v0 & imask) : (uint64_t)sidx[h[k]]];
+        for (uint32_t t = 1; t < s[k]; ++t) {
+          const uint64_t v = sk[h[k] + t];
+          w.x[mb[k] + t] = amps_in[vb ? (v & imask) : (uint64_t)sidx[h[k] + t]];
+        }
+      }
       const uint32_t j = 32u * k + lane;
       w.pmom[j] = gmv[k];
       w.mb[j] = (uint16_t)mb[k];
       w.ob[j] = ob[k];
-      w.rest[j] = rest[k] >> shift;
+      w.rest[j] = v0 >> shift;
     }
     // order the groups by member count (ballots per count), then give each
     // ordered position its first slot (scan of the output counts)

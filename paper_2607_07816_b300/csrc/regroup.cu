@@ -128,23 +128,21 @@ __global__ void __launch_bounds__(RG_THREADS) k_part_counts(const uint64_t* __re
 }
 
 // Stable scatter of the new sort keys into the runs: a tile ranks its terms
-// per warp and local index, stages them in shared memory in run order and
-// writes each run's slice at off[r * tiles + t].
-// Three blocks per SM (40 registers, a few bytes spilled): more tiles in
-// flight than two blocks at 63 registers (measured).
+// per warp and local index and each thread writes its terms straight to
+// their places in the runs (the tile's slice of run r starts at
+// off[r * tiles + t]; measured faster than staging the tile in shared memory
+// in run order first).
+// Four blocks per SM (32 registers, a few bytes spilled; no shared staging
+// buffer any more): more tiles in flight than three at 40 registers
+// (measured).
 template <bool PAIRS>
-__global__ void __launch_bounds__(RG_THREADS, 3) k_part_scatter(const uint64_t* __restrict__ keys, uint64_t n,
+__global__ void __launch_bounds__(RG_THREADS, 4) k_part_scatter(const uint64_t* __restrict__ keys, uint64_t n,
                                                              const GateParams gp, uint64_t tiles,
                                                              const uint32_t* __restrict__ off,
                                                              uint64_t* __restrict__ sk, uint32_t* __restrict__ sidx) {
   pdl_prologue();
-  extern __shared__ __align__(16) uint8_t s_dyn[];
-  uint64_t* s_keys = reinterpret_cast<uint64_t*>(s_dyn);
-  uint32_t* s_vals = reinterpret_cast<uint32_t*>(s_dyn + sizeof(uint64_t) * RG_TILE);
   __shared__ uint32_t s_whist[RG_WARPS][16];
-  __shared__ uint32_t s_local[16];
   __shared__ uint32_t s_out[16];
-  __shared__ uint32_t s_staged;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int m = gp.m, D = 1 << m, vb = gp.vbits;
   const uint32_t dmask = (uint32_t)D - 1u;
@@ -184,41 +182,22 @@ __global__ void __launch_bounds__(RG_THREADS, 3) k_part_scatter(const uint64_t* 
     __syncwarp();
   }
   __syncthreads();
-  if (warp == 0) {  // per run: offsets of the warps within the run, then the runs' offsets in the tile
+  if (warp == 0 && lane < D) {  // per run: offsets of the warps within the tile's slice of the run
     uint32_t cnt = 0;
-    if (lane < D) {
-      for (int w = 0; w < RG_WARPS; ++w) {
-        const uint32_t c = s_whist[w][lane];
-        s_whist[w][lane] = cnt;
-        cnt += c;
-      }
+    for (int w = 0; w < RG_WARPS; ++w) {
+      const uint32_t c = s_whist[w][lane];
+      s_whist[w][lane] = cnt;
+      cnt += c;
     }
-    uint32_t x = cnt;
-#pragma unroll
-    for (int o = 1; o < 16; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    if (lane < D) s_local[lane] = x - cnt;
-    if (lane == D - 1) s_staged = x;  // terms of the tile that were staged
   }
   __syncthreads();
 #pragma unroll
   for (int i = 0; i < RG_ITEMS; ++i) {
     if (d[i] < 16) {
-      const uint32_t pos = s_local[d[i]] + s_whist[warp][d[i]] + rank[i];
-      s_keys[pos] = k[i];
-      if (PAIRS) s_vals[pos] = (uint32_t)(base + i * 32);
+      const uint64_t o = (uint64_t)s_out[d[i]] + s_whist[warp][d[i]] + rank[i];
+      sk[o] = k[i];
+      if (PAIRS) sidx[o] = (uint32_t)(base + i * 32);
     }
-  }
-  __syncthreads();
-  const uint32_t tile_n = s_staged;
-  for (uint32_t j = tid; j < tile_n; j += RG_THREADS) {
-    const uint64_t key = s_keys[j];
-    const uint32_t dd = (uint32_t)(key >> vb) & dmask;
-    const uint64_t o = (uint64_t)s_out[dd] + (j - s_local[dd]);
-    sk[o] = key;
-    if (PAIRS) sidx[o] = s_vals[j];
   }
 }
 
@@ -404,7 +383,6 @@ __global__ void __launch_bounds__(MG_THREADS, 4) k_merge_level(const uint64_t* _
   }
 }
 
-static size_t part_smem(bool pairs) { return (sizeof(uint64_t) + (pairs ? sizeof(uint32_t) : 0)) * RG_TILE; }
 static size_t merge_smem(bool pairs) {
   return (sizeof(uint64_t) + (pairs ? sizeof(uint32_t) : 0)) * (size_t)mg_pad(MG_TILE);
 }
@@ -413,9 +391,7 @@ cudaError_t regroup_prepare() {
   static DeviceOnce once;
   return once.run([] {
     const int attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    cudaError_t e = cudaFuncSetAttribute(k_part_scatter<true>, (cudaFuncAttribute)attr, (int)part_smem(true));
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_part_scatter<false>, (cudaFuncAttribute)attr, (int)part_smem(false));
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_merge_level<true>, (cudaFuncAttribute)attr, (int)merge_smem(true));
+    cudaError_t e = cudaFuncSetAttribute(k_merge_level<true>, (cudaFuncAttribute)attr, (int)merge_smem(true));
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_merge_level<false>, (cudaFuncAttribute)attr, (int)merge_smem(false));
     return e;
   });
@@ -440,10 +416,10 @@ int regroup_terms(const uint64_t* keys, uint64_t n, const GateParams& gp, uint64
   launch_pdl(k_part_counts, (unsigned)tiles, RG_THREADS, 0, st, keys, n, gp, tiles, cnt, sc.hist);
   launch_tile_offsets(cnt, sc.hist, tiles, D, off, st);
   if (pairs)
-    launch_pdl(k_part_scatter<true>, (unsigned)tiles, RG_THREADS, part_smem(true), st, keys, n, gp, tiles, off,
+    launch_pdl(k_part_scatter<true>, (unsigned)tiles, RG_THREADS, 0, st, keys, n, gp, tiles, off,
                sk[0], sidx[0]);
   else
-    launch_pdl(k_part_scatter<false>, (unsigned)tiles, RG_THREADS, part_smem(false), st, keys, n, gp, tiles, off,
+    launch_pdl(k_part_scatter<false>, (unsigned)tiles, RG_THREADS, 0, st, keys, n, gp, tiles, off,
                sk[0], nullptr);
   *launches = 3;
   int cur = 0;
