@@ -49,22 +49,34 @@ __device__ __forceinline__ uint32_t gate_index_of(uint64_t key, const int* qpos,
   return r;
 }
 
-// The gate's sort key of a stored key: the bits at the positions in rem[]
-// (the gate qubits' stored positions, in descending order) are removed, the
-// rest shifts down over them and moves up by m, and the digit of r (r
-// itself, or a monomial gate's output index: rmap) takes the bottom.
-__device__ __forceinline__ uint64_t sort_key_of(uint64_t key, const int* qpos, const int* rem, int m,
-                                                uint64_t rmap) {
-  const uint32_t r = (uint32_t)(rmap >> (4 * gate_index_of(key, qpos, m))) & 15u;
-  uint64_t x = key;
+// The gate's sort key of a stored key: the bits at the gate qubits' stored
+// positions rem[] (descending) are removed, the rest closes up and moves up
+// by m, and the digit of r (r itself, or a monomial gate's output index:
+// rmap) takes the bottom.  Written with masks: seg[i] holds the bits between
+// the i-th and the (i+1)-th removed position (seg[0] those above all of them,
+// seg[m] those below all); a bit of seg[i] has m - i removed positions below
+// it, so it moves up by i.
+__device__ __forceinline__ void segment_masks(const int* rem, int m, uint64_t* seg) {
 #pragma unroll
-  for (int t = 0; t < 4; ++t)
-    if (t < m) {
-      const int p = rem[t];
-      const uint64_t low = x & ((1ull << p) - 1ull);
-      x = ((x >> p) >> 1 << p) | low;
-    }
-  return (x << m) | r;
+  for (int i = 0; i <= 4; ++i) {
+    seg[i] = 0;
+    if (i > m) continue;
+    const int hb = i == 0 ? 64 : rem[i - 1];  // bits below hb ...
+    const int lb = i == m ? -1 : rem[i];      // ... and above lb
+    const uint64_t upper = hb >= 64 ? ~0ull : ((1ull << hb) - 1ull);
+    const uint64_t lower = lb + 1 >= 64 ? ~0ull : ((1ull << (lb + 1)) - 1ull);
+    seg[i] = upper & ~lower;
+  }
+}
+
+__device__ __forceinline__ uint64_t sort_key_masked(uint64_t key, const int* qpos, const uint64_t* seg, int m,
+                                                    uint64_t rmap) {
+  const uint32_t r = (uint32_t)(rmap >> (4 * gate_index_of(key, qpos, m))) & 15u;
+  uint64_t x = key & seg[0];
+#pragma unroll
+  for (int i = 1; i <= 4; ++i)
+    if (i <= m) x |= (key & seg[i]) << i;
+  return x | r;
 }
 
 __device__ __forceinline__ void gate_positions(const GateParams& gp, int* qpos, int* rem) {
@@ -148,6 +160,8 @@ __global__ void __launch_bounds__(RG_THREADS, 4) k_part_scatter(const uint64_t* 
   const uint32_t dmask = (uint32_t)D - 1u;
   int qpos[4], rem[4];
   gate_positions(gp, qpos, rem);
+  __shared__ uint64_t s_seg[5];  // read by all lanes alike (broadcast), kept out of the registers
+  if (tid == 0) segment_masks(rem, m, s_seg);
   for (int i = tid; i < RG_WARPS * 16; i += RG_THREADS) (&s_whist[0][0])[i] = 0;
   const uint64_t t = blockIdx.x;
   if (tid < D) s_out[tid] = off[(uint64_t)tid * tiles + t];
@@ -161,7 +175,7 @@ __global__ void __launch_bounds__(RG_THREADS, 4) k_part_scatter(const uint64_t* 
     bool valid = idx < n;
     uint64_t s = 0ull;
     if (valid) {
-      s = gp.direct ? keys[idx] : sort_key_of(keys[idx], qpos, rem, m, gp.rmap);
+      s = gp.direct ? keys[idx] : sort_key_masked(keys[idx], qpos, s_seg, m, gp.rmap);
       valid = !(gp.direct && s == ~0ull);  // a dropped term (batched form) is left out
     }
     k[i] = vb ? ((s << vb) | idx) : s;
