@@ -314,6 +314,24 @@ sv_status svb_autotune_stats(const svb_state* b, uint64_t* trials, uint64_t* cla
 sv_status svb_set_graphs(svb_state* b, int on);
 /* Graphs captured and graph launches so far. */
 sv_status svb_graph_stats(const svb_state* b, uint64_t* captures, uint64_t* launches);
+/* One launch per step (off by default): the whole step (sort keys, grouping,
+ * group heads, mat-vec, per-slot top-k select to the exact cut,
+ * renormalising compaction) runs as one persistent cooperative kernel whose
+ * blocks pass grid-wide barriers between the phases, with every size read
+ * on the device; with graphs on, the gate-table upload, the launch and the
+ * read-back are one graph, captured when the step's table size, widest gate
+ * and buffers recur and replayed after that, and the host waits once per
+ * step.  Off: the step's separate kernels (two parts, a host wait after
+ * each, autotuned launch shapes).  Results are the same either way. */
+sv_status svb_set_layer_kernel(svb_state* b, int on);
+/* Benchmarking hook: milliseconds spent in each phase of the one-launch
+ * step, summed over the handle's steps, as timed by the kernel's first block
+ * from one grid barrier to the next (setup, sort keys, partition counts,
+ * partition offsets, partition scatter, merge splits, merge levels, group
+ * heads, mat-vec, select state, first pick, select scans, picks, finishes,
+ * scales, compaction).  Writes min(cap, *count) values; *count = the number
+ * of phases. */
+sv_status svb_layer_phase_times(const svb_state* b, double* ms, int cap, int* count);
 
 /* Peak readout that allocates nothing.  The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc where they need

@@ -16,6 +16,7 @@
 #include "batch.h"
 #include "c64_exact.cuh"
 #include "select.cuh"
+#include "regroup.cuh"
 
 namespace sv {
 
@@ -23,18 +24,22 @@ namespace sv {
 // The nibble tables of each slot's sort order for this step (one block per
 // slot): fwd[k][v] = the sort-key bits of natural bits 4k.. given by v,
 // inv[k][v] = the natural bits of sort-key bits 4k.. given by v.
-__global__ void __launch_bounds__(256) k_seg_tables(const SegGate* __restrict__ gates,
-                                                    uint64_t* __restrict__ tables) {
-  __shared__ int8_t s_nat[64];  // sort-key bit -> qubit
-  const SegGate& gt = gates[blockIdx.x];
-  uint64_t* fwd = tables + (uint64_t)blockIdx.x * SEG_TABLE_WORDS;
+struct SegTablesSmem {
+  int8_t nat[64];  // sort-key bit -> qubit
+};
+
+// The tables of one slot; blockDim.x == 256 (one thread per table word).
+__device__ __forceinline__ void seg_tables_slot(const SegGate* __restrict__ gates, uint64_t* __restrict__ tables,
+                                                uint32_t slot, SegTablesSmem& s) {
+  const SegGate& gt = gates[slot];
+  uint64_t* fwd = tables + (uint64_t)slot * SEG_TABLE_WORDS;
   uint64_t* inv = fwd + 256;
-  if (threadIdx.x < 64) s_nat[threadIdx.x] = -1;
+  if (threadIdx.x < 64) s.nat[threadIdx.x] = -1;
   __syncthreads();
   if (gt.m < 0) return;  // removed or free slot: no tables needed
   if (threadIdx.x < 64) {
     const int p = gt.pos[threadIdx.x];
-    if (p < 64) s_nat[p] = (int8_t)threadIdx.x;
+    if (p < 64) s.nat[p] = (int8_t)threadIdx.x;
   }
   __syncthreads();
   const int k = threadIdx.x >> 4, v = threadIdx.x & 15;
@@ -44,10 +49,16 @@ __global__ void __launch_bounds__(256) k_seg_tables(const SegGate* __restrict__ 
     if ((v >> j) & 1) {
       const int b = 4 * k + j;
       if (gt.pos[b] < 64) f |= 1ull << gt.pos[b];
-      if (s_nat[b] >= 0) g |= 1ull << s_nat[b];
+      if (s.nat[b] >= 0) g |= 1ull << s.nat[b];
     }
   fwd[threadIdx.x] = f;
   inv[threadIdx.x] = g;
+}
+
+__global__ void __launch_bounds__(256) k_seg_tables(const SegGate* __restrict__ gates,
+                                                    uint64_t* __restrict__ tables) {
+  __shared__ SegTablesSmem s;
+  seg_tables_slot(gates, tables, blockIdx.x, s);
 }
 
 void launch_seg_tables(const SegGate* gates, int slots, uint64_t* tables, cudaStream_t st) {
@@ -63,19 +74,26 @@ __device__ __forceinline__ uint64_t nibble_map(const uint64_t* __restrict__ t, u
 
 // Sort key of every term: (segment rank, the key in its slot's sort order),
 // all ones for a term of a removed segment (left out of the grouping).
-__global__ void __launch_bounds__(256) k_seg_keys(const uint64_t* __restrict__ keys,
-                                                  const uint16_t* __restrict__ seg, uint64_t n,
-                                                  const SegGate* __restrict__ gates,
-                                                  const uint64_t* __restrict__ tables, int shift,
-                                                  uint64_t* __restrict__ sk) {
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
-       i += (uint64_t)gridDim.x * blockDim.x) {
+__device__ __forceinline__ void seg_keys_range(const uint64_t* __restrict__ keys, const uint16_t* __restrict__ seg,
+                                               uint64_t n, const SegGate* __restrict__ gates,
+                                               const uint64_t* __restrict__ tables, int shift,
+                                               uint64_t* __restrict__ sk, uint64_t first, uint64_t stride) {
+  for (uint64_t i = first; i < n; i += stride) {
     const uint32_t sg = seg[i];
     uint64_t s = ~0ull;
     if (gates[sg].m >= 0)
       s = ((uint64_t)gates[sg].rank << shift) | nibble_map(tables + (uint64_t)sg * SEG_TABLE_WORDS, keys[i]);
     sk[i] = s;
   }
+}
+
+__global__ void __launch_bounds__(256) k_seg_keys(const uint64_t* __restrict__ keys,
+                                                  const uint16_t* __restrict__ seg, uint64_t n,
+                                                  const SegGate* __restrict__ gates,
+                                                  const uint64_t* __restrict__ tables, int shift,
+                                                  uint64_t* __restrict__ sk) {
+  seg_keys_range(keys, seg, n, gates, tables, shift, sk, blockIdx.x * (uint64_t)blockDim.x + threadIdx.x,
+                 (uint64_t)gridDim.x * blockDim.x);
 }
 
 void launch_seg_keys(const uint64_t* keys, const uint16_t* seg, uint64_t n, const SegGate* gates,
@@ -95,19 +113,24 @@ __device__ __forceinline__ uint64_t seg_group_key(uint64_t s, int shift, const S
   return s >> gates[sg].m;  // the segment rank stays in the top bits
 }
 
-__global__ void __launch_bounds__(SH_BLOCK) k_seg_heads(const uint64_t* __restrict__ sk, uint64_t n, int shift,
-                                                        const SegGate* __restrict__ gates,
-                                                        const uint16_t* __restrict__ rank_slot,
-                                                        uint32_t* __restrict__ heads, uint64_t* lookback,
-                                                        Ctl* ctl) {
+struct SegHeadsSmem {
+  CompactShared<SH_BLOCK> cs;
+  uint64_t tile;
+};
+
+// Group heads of the grouped sort keys, tiles taken from
+// ctl->tile_counter[0] until none is left; the group count lands in
+// ctl->count[0].
+__device__ __forceinline__ void seg_heads_run(const uint64_t* __restrict__ sk, uint64_t n, int shift,
+                                              const SegGate* __restrict__ gates,
+                                              const uint16_t* __restrict__ rank_slot, uint32_t* __restrict__ heads,
+                                              uint64_t* lookback, Ctl* ctl, SegHeadsSmem& s) {
   typedef TileLayout<SH_BLOCK, SH_ITEMS> L;
-  __shared__ CompactShared<SH_BLOCK> cs;
-  __shared__ uint64_t s_tile;
   const uint64_t tiles = (n + L::TILE - 1) / L::TILE;
   while (true) {
-    if (threadIdx.x == 0) s_tile = atomicAdd((unsigned long long*)&ctl->tile_counter[0], 1ull);
+    if (threadIdx.x == 0) s.tile = atomicAdd((unsigned long long*)&ctl->tile_counter[0], 1ull);
     __syncthreads();
-    const uint64_t tile = s_tile;
+    const uint64_t tile = s.tile;
     if (tile >= tiles) break;
     const uint64_t base = tile * L::TILE;
     bool flag[SH_ITEMS];
@@ -123,13 +146,22 @@ __global__ void __launch_bounds__(SH_BLOCK) k_seg_heads(const uint64_t* __restri
       }
       flag[j] = f;
     }
-    tile_compact<SH_BLOCK, SH_ITEMS>(flag, pos, cs, lookback, tile, &ctl->err);
+    tile_compact<SH_BLOCK, SH_ITEMS>(flag, pos, s.cs, lookback, tile, &ctl->err);
 #pragma unroll
     for (int j = 0; j < SH_ITEMS; ++j)
-      if (flag[j]) heads[cs.tile_base_out + pos[j]] = (uint32_t)L::index(base, j);
-    if (tile == tiles - 1 && threadIdx.x == 0) ctl->count[0] = cs.tile_base_out + cs.tile_total;
+      if (flag[j]) heads[s.cs.tile_base_out + pos[j]] = (uint32_t)L::index(base, j);
+    if (tile == tiles - 1 && threadIdx.x == 0) ctl->count[0] = s.cs.tile_base_out + s.cs.tile_total;
     __syncthreads();
   }
+}
+
+__global__ void __launch_bounds__(SH_BLOCK) k_seg_heads(const uint64_t* __restrict__ sk, uint64_t n, int shift,
+                                                        const SegGate* __restrict__ gates,
+                                                        const uint16_t* __restrict__ rank_slot,
+                                                        uint32_t* __restrict__ heads, uint64_t* lookback,
+                                                        Ctl* ctl) {
+  __shared__ SegHeadsSmem s;
+  seg_heads_run(sk, n, shift, gates, rank_slot, heads, lookback, ctl, s);
 }
 
 void launch_seg_heads(const uint64_t* sk, uint64_t n, int shift, const SegGate* gates, const uint16_t* rank_slot,
@@ -142,6 +174,22 @@ void launch_seg_heads(const uint64_t* sk, uint64_t n, int shift, const SegGate* 
   if (n == 0) return;
   const uint64_t grid = tiles < 148 * 4 ? tiles : 148 * 4;
   k_seg_heads<<<(unsigned)grid, SH_BLOCK, 0, st>>>(sk, n, shift, gates, rank_slot, heads, lookback, ctl);
+}
+
+// ---------------------------------------------------------------- segment bounds
+// Where each slot's terms start and end in an output list, recorded while
+// the list is written: output i of a tile of `total` outputs written from
+// position base, whose slots are sl[0..total).  Slot changes inside the tile
+// are marked at once; the tile's first and last outputs may continue a slot
+// from the neighbouring tiles, so their marks take the minimum (start) and
+// maximum (end).  start must arrive all ones and end zero; a slot with no
+// outputs keeps them.
+__device__ __forceinline__ void seg_bound_marks(const uint16_t* sl, uint32_t i, uint32_t total, uint64_t base,
+                                                uint64_t* __restrict__ start, uint64_t* __restrict__ end) {
+  if (!start) return;
+  const uint16_t s = sl[i];
+  if (i == 0 || sl[i - 1] != s) atomicMin((unsigned long long*)&start[s], (unsigned long long)(base + i));
+  if (i + 1 == total || sl[i + 1] != s) atomicMax((unsigned long long*)&end[s], (unsigned long long)(base + i + 1));
 }
 
 // ---------------------------------------------------------------- apply
@@ -166,15 +214,41 @@ constexpr int SA_BLOCK = 256;
 // registers (the single-state order, U rounded to the amplitude precision,
 // products with a zero U component skipped).  Nonzero outputs are placed in
 // (group, r') order: a block scan of the per-thread counts and a decoupled
-// look-back over tiles give each thread its output range.
+// look-back over tiles give each thread its output range.  With hist1 the
+// write-back also counts every output in its slot's histogram of the
+// select's first digit (the select's first level then needs no scan).
+struct SegApplySmem {
+  uint32_t warp[SA_BLOCK / 32];
+  uint64_t base;
+  uint32_t total;
+  uint64_t tile;
+  uint32_t hslot;   // slot whose first-digit counts hcnt holds (~0: none)
+  uint32_t* hcnt;   // [SEL_BINS] in shared memory
+};
+
+// Add the block's first-digit counts of slot sm.hslot to the slot's global
+// histogram and clear them (all threads call it).
+__device__ __forceinline__ void seg_hist1_flush(SegApplySmem& sm, uint32_t* __restrict__ hist1) {
+  const uint32_t sl = sm.hslot;
+  if (sl != 0xffffffffu)
+    for (int b = threadIdx.x; b < SEL_BINS; b += SA_BLOCK) {
+      const uint32_t c = sm.hcnt[b];
+      if (c) {
+        atomicAdd(&hist1[(uint64_t)sl * SEL_BINS + b], c);
+        sm.hcnt[b] = 0;
+      }
+    }
+}
+
 template <typename Real, int MAXD, int GPT>
-__global__ void __launch_bounds__(SA_BLOCK) k_seg_apply(
+__device__ __forceinline__ void seg_apply_run(
     const uint64_t* __restrict__ sk, const uint32_t* __restrict__ sidx, uint64_t n,
     const uint32_t* __restrict__ heads, const typename SCplx<Real>::T* __restrict__ amps_in, int shift,
     const SegGate* __restrict__ gates, const uint16_t* __restrict__ rank_slot, const uint64_t* __restrict__ tables,
     uint64_t* __restrict__ keys_out,
     typename SCplx<Real>::T* __restrict__ amps_out, uint64_t* __restrict__ probs_out,
-    uint16_t* __restrict__ seg_out, uint64_t* lookback, uint64_t max_tiles, Ctl* ctl) {
+    uint16_t* __restrict__ seg_out, uint32_t* __restrict__ hist1, uint64_t* __restrict__ start,
+    uint64_t* __restrict__ end, uint64_t* lookback, uint64_t max_tiles, Ctl* ctl, SegApplySmem& sm, uint8_t* s_dyn) {
   typedef typename SCplx<Real>::T C2;
   constexpr int TILE_G = SA_BLOCK * GPT;
   constexpr int WARPS = SA_BLOCK / 32;
@@ -182,26 +256,25 @@ __global__ void __launch_bounds__(SA_BLOCK) k_seg_apply(
   // a tile's outputs are staged in shared memory and written back coalesced
   // (a thread's outputs are consecutive, so direct stores of neighbouring
   // threads fall 2^m apart)
-  extern __shared__ __align__(16) uint8_t s_dyn[];
   uint64_t* s_ok = reinterpret_cast<uint64_t*>(s_dyn);
   uint64_t* s_op = s_ok + NOUT;
   C2* s_oa = reinterpret_cast<C2*>(s_op + NOUT);
   uint16_t* s_os = reinterpret_cast<uint16_t*>(s_oa + NOUT);
-  __shared__ uint32_t s_warp[WARPS];
-  __shared__ uint64_t s_base;
-  __shared__ uint32_t s_total;
-  __shared__ uint64_t s_tile;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint64_t G = ctl->count[0];
   const uint64_t tiles = (G + TILE_G - 1) / TILE_G;
   if (tiles > max_tiles) {  // the look-back buffer was sized for fewer tiles
-    if (blockIdx.x == 0 && tid == 0) atomicOr(&ctl->err, ERR_INVARIANT);
+    if (tid == 0) atomicOr(&ctl->err, ERR_INVARIANT);
     return;
   }
+  if (hist1) {
+    for (int b = tid; b < SEL_BINS; b += SA_BLOCK) sm.hcnt[b] = 0;
+    if (tid == 0) sm.hslot = 0xffffffffu;
+  }
   while (true) {
-    if (tid == 0) s_tile = atomicAdd((unsigned long long*)&ctl->tile_counter[1], 1ull);
+    if (tid == 0) sm.tile = atomicAdd((unsigned long long*)&ctl->tile_counter[1], 1ull);
     __syncthreads();
-    const uint64_t tile = s_tile;
+    const uint64_t tile = sm.tile;
     if (tile >= tiles) break;
     const uint64_t g0 = tile * TILE_G + (uint64_t)tid * GPT;
     Real yr[GPT][MAXD], yi[GPT][MAXD];
@@ -282,26 +355,26 @@ __global__ void __launch_bounds__(SA_BLOCK) k_seg_apply(
       const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
       if (lane >= o) x += y;
     }
-    if (lane == 31) s_warp[warp] = x;
+    if (lane == 31) sm.warp[warp] = x;
     __syncthreads();
     if (warp == 0) {
-      const uint32_t v = lane < WARPS ? s_warp[lane] : 0u;
+      const uint32_t v = lane < WARPS ? sm.warp[lane] : 0u;
       uint32_t w = v;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
         if (lane >= o) w += y;
       }
-      if (lane < WARPS) s_warp[lane] = w - v;
+      if (lane < WARPS) sm.warp[lane] = w - v;
       const uint32_t total = __shfl_sync(0xffffffffu, w, 31);
       const uint64_t base = lookback_exclusive_warp(lookback, tile, total, &ctl->err);
       if (lane == 0) {
-        s_total = total;
-        s_base = base;
+        sm.total = total;
+        sm.base = base;
       }
     }
     __syncthreads();
-    uint32_t o = s_warp[warp] + (x - cnt);  // position within the tile's outputs
+    uint32_t o = sm.warp[warp] + (x - cnt);  // position within the tile's outputs
 #pragma unroll
     for (int j = 0; j < GPT; ++j) {
       if (!keep[j]) continue;
@@ -322,21 +395,64 @@ __global__ void __launch_bounds__(SA_BLOCK) k_seg_apply(
       }
     }
     __syncthreads();
-    const uint64_t base = s_base;
-    for (uint32_t i = tid; i < s_total; i += SA_BLOCK) {
-      keys_out[base + i] = s_ok[i];
-      amps_out[base + i] = s_oa[i];
-      probs_out[base + i] = s_op[i];
-      seg_out[base + i] = s_os[i];
+    const uint64_t base = sm.base;
+    if (hist1 && sm.total > 0 && s_os[0] != sm.hslot) {
+      // the block's counts follow the slot of its tiles' first outputs: a
+      // change of slot flushes them (tiles come in increasing order)
+      seg_hist1_flush(sm, hist1);
+      __syncthreads();
+      if (tid == 0) sm.hslot = s_os[0];
+      __syncthreads();
     }
-    if (tile == tiles - 1 && tid == 0) ctl->count[1] = s_base + s_total;
+    for (uint32_t i0 = 0; i0 < sm.total; i0 += SA_BLOCK) {
+      const uint32_t i = i0 + (uint32_t)tid;
+      uint32_t hk = 0xffffffffu;
+      if (i < sm.total) {
+        keys_out[base + i] = s_ok[i];
+        amps_out[base + i] = s_oa[i];
+        probs_out[base + i] = s_op[i];
+        seg_out[base + i] = s_os[i];
+        hk = ((uint32_t)s_os[i] << SEL_BITS) | sel_first_digit(s_op[i]);
+        seg_bound_marks(s_os, i, sm.total, base, start, end);
+      }
+      if (hist1) {  // the select's first digit per slot (lanes of one slot and digit add once)
+        const uint32_t peers = __match_any_sync(0xffffffffu, hk);
+        if (hk != 0xffffffffu && lane == __ffs(peers) - 1) {
+          const uint32_t sl = hk >> SEL_BITS, dg = hk & (SEL_BINS - 1);
+          if (sl == sm.hslot)
+            atomicAdd(&sm.hcnt[dg], (uint32_t)__popc(peers));
+          else  // a tile that reaches into the next slot
+            atomicAdd(&hist1[(uint64_t)sl * SEL_BINS + dg], (uint32_t)__popc(peers));
+        }
+      }
+    }
+    if (tile == tiles - 1 && tid == 0) ctl->count[1] = sm.base + sm.total;
     __syncthreads();
   }
+  if (hist1) seg_hist1_flush(sm, hist1);
+}
+
+template <typename Real, int MAXD, int GPT>
+__global__ void __launch_bounds__(SA_BLOCK) k_seg_apply(
+    const uint64_t* __restrict__ sk, const uint32_t* __restrict__ sidx, uint64_t n,
+    const uint32_t* __restrict__ heads, const typename SCplx<Real>::T* __restrict__ amps_in, int shift,
+    const SegGate* __restrict__ gates, const uint16_t* __restrict__ rank_slot, const uint64_t* __restrict__ tables,
+    uint64_t* __restrict__ keys_out,
+    typename SCplx<Real>::T* __restrict__ amps_out, uint64_t* __restrict__ probs_out,
+    uint16_t* __restrict__ seg_out, uint32_t* __restrict__ hist1, uint64_t* __restrict__ start,
+    uint64_t* __restrict__ end, uint64_t* lookback, uint64_t max_tiles, Ctl* ctl) {
+  extern __shared__ __align__(16) uint8_t s_dyn[];
+  __shared__ SegApplySmem sm;
+  __shared__ uint32_t s_hcnt[SEL_BINS];
+  if (threadIdx.x == 0) sm.hcnt = s_hcnt;
+  __syncthreads();
+  seg_apply_run<Real, MAXD, GPT>(sk, sidx, n, heads, amps_in, shift, gates, rank_slot, tables, keys_out, amps_out,
+                                 probs_out, seg_out, hist1, start, end, lookback, max_tiles, ctl, sm, s_dyn);
 }
 
 // Shared staging of one tile's outputs: key, probability, amplitude, slot.
 template <typename C2>
-constexpr size_t seg_apply_smem(int maxd, int gpt) {
+__host__ __device__ constexpr size_t seg_apply_smem(int maxd, int gpt) {
   return (size_t)SA_BLOCK * gpt * maxd * (8 + 8 + sizeof(C2) + 2);
 }
 
@@ -366,15 +482,15 @@ void seg_apply_dispatch(int mmax, int gpt, unsigned grid, cudaStream_t st, const
                         uint64_t n, const uint32_t* heads, const void* amps_in, int shift, const SegGate* gates,
                         const uint16_t* rank_slot, const uint64_t* tables, uint64_t* keys_out, void* amps_out,
                         uint64_t* probs_out,
-                        uint16_t* seg_out,
+                        uint16_t* seg_out, uint32_t* hist1, uint64_t* start, uint64_t* end,
                         uint64_t* lookback, uint64_t max_tiles, Ctl* ctl) {
   typedef typename SCplx<Real>::T C2;
   const C2* ai = (const C2*)amps_in;
   C2* ao = (C2*)amps_out;
 #define SV_SEG_APPLY(MAXD, GPT)                                                                         \
   k_seg_apply<Real, MAXD, GPT><<<grid, SA_BLOCK, seg_apply_smem<C2>(MAXD, GPT), st>>>(                    \
-      sk, sidx, n, heads, ai, shift, gates, rank_slot, tables, keys_out, ao, probs_out, seg_out, lookback,   \
-      max_tiles, ctl)
+      sk, sidx, n, heads, ai, shift, gates, rank_slot, tables, keys_out, ao, probs_out, seg_out, hist1, start,  \
+      end, lookback, max_tiles, ctl)
   if (mmax <= 1) {
     if (gpt == 1) SV_SEG_APPLY(2, 1);
     else if (gpt == 2) SV_SEG_APPLY(2, 2);
@@ -400,7 +516,7 @@ int seg_apply_configs(int mmax) { return mmax <= 2 ? 3 : (mmax == 3 ? 2 : 1); }
 void launch_seg_apply(int prec, const uint64_t* sk, const uint32_t* sidx, uint64_t n, const uint32_t* heads,
                       const void* amps_in, int shift, int mmax, const SegGate* gates, const uint16_t* rank_slot,
                       const uint64_t* tables, uint64_t* keys_out, void* amps_out, uint64_t* probs_out,
-                      uint16_t* seg_out,
+                      uint16_t* seg_out, uint32_t* hist1, uint64_t* start, uint64_t* end,
                       uint64_t* lookback, Ctl* ctl, uint64_t max_tiles, int cfg, cudaStream_t st) {
   cudaMemsetAsync(lookback, 0, sizeof(uint64_t) * (max_tiles + 1), st);
   cudaMemsetAsync(&ctl->tile_counter[1], 0, sizeof(uint64_t), st);
@@ -411,30 +527,11 @@ void launch_seg_apply(int prec, const uint64_t* sk, const uint32_t* sidx, uint64
   const uint64_t grid = max_tiles < 148 * 4 ? (max_tiles ? max_tiles : 1) : 148 * 4;
   if (prec == 0)
     seg_apply_dispatch<double>(mmax, gpt, (unsigned)grid, st, sk, sidx, n, heads, amps_in, shift, gates, rank_slot,
-                               tables, keys_out, amps_out, probs_out, seg_out, lookback, max_tiles, ctl);
+                               tables, keys_out, amps_out, probs_out, seg_out, hist1, start, end, lookback, max_tiles, ctl);
   else
     seg_apply_dispatch<float>(mmax, gpt, (unsigned)grid, st, sk, sidx, n, heads, amps_in, shift, gates, rank_slot,
-                              tables, keys_out, amps_out, probs_out, seg_out, lookback, max_tiles, ctl);
-}
-
-// ---------------------------------------------------------------- segment bounds
-// Segments are contiguous: record where each one starts and ends.
-__global__ void k_seg_bounds(const uint16_t* __restrict__ seg, const uint64_t* __restrict__ n_dev,
-                             uint64_t* __restrict__ start, uint64_t* __restrict__ end) {
-  const uint64_t n = *n_dev;
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
-       i += (uint64_t)gridDim.x * blockDim.x) {
-    const uint16_t s = seg[i];
-    if (i == 0 || seg[i - 1] != s) start[s] = i;
-    if (i + 1 == n || seg[i + 1] != s) end[s] = i + 1;
-  }
-}
-
-void launch_seg_bounds(const uint16_t* seg, const uint64_t* n_dev, uint64_t* start, uint64_t* end, int slots,
-                       cudaStream_t st) {
-  cudaMemsetAsync(start, 0, sizeof(uint64_t) * slots, st);
-  cudaMemsetAsync(end, 0, sizeof(uint64_t) * slots, st);
-  k_seg_bounds<<<148 * 8, 256, 0, st>>>(seg, n_dev, start, end);
+                              tables, keys_out, amps_out, probs_out, seg_out, hist1, start, end, lookback, max_tiles,
+                              ctl);
 }
 
 // ---------------------------------------------------------------- segmented select
@@ -465,32 +562,37 @@ __device__ __forceinline__ bool z_before_prefix(uint64_t hi, uint64_t lo, uint64
 }
 
 
-__global__ void __launch_bounds__(SS_BLOCK) k_segsel_hist(const uint64_t* __restrict__ probs,
+struct SegHistSmem {
+  uint32_t cnt[SS_BINS];
+  u128 part[2][SS_BLOCK / 32];
+  uint32_t seg;
+};
+
+// One level's scan by block `cta` of `ncta`: a contiguous chunk of the terms.
+__device__ __forceinline__ void segsel_hist_chunk(const uint64_t* __restrict__ probs,
                                                           const uint64_t* __restrict__ keys,
                                                           const uint16_t* __restrict__ seg,
                                                           const uint64_t* __restrict__ n_dev,
                                                           const SegSel* __restrict__ sel,
                                                           uint32_t* __restrict__ g_cnt, uint64_t* __restrict__ g_sum,
                                                           uint64_t* __restrict__ g_buf, uint32_t* __restrict__ g_bufn,
-                                                          uint32_t* err) {
-  __shared__ uint32_t s_cnt[SS_BINS];
-  __shared__ u128 s_part[2][SS_BLOCK / 32];
-  __shared__ uint32_t s_seg;
+                                                          uint32_t* err, uint32_t cta, uint32_t ncta,
+                                                          SegHistSmem& sm) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // one contiguous chunk per block, whole multiples of a block's sweep
   const uint64_t n = *n_dev;
   const uint64_t sweep = (uint64_t)SS_BLOCK * SS_ILP;
-  uint64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  uint64_t chunk = (n + ncta - 1) / ncta;
   chunk = (chunk + sweep - 1) / sweep * sweep;
   if (chunk < 4 * sweep) chunk = 4 * sweep;
-  const uint64_t c0 = blockIdx.x * chunk;
+  const uint64_t c0 = cta * chunk;
   if (c0 >= n) return;
   const uint64_t c1 = c0 + chunk < n ? c0 + chunk : n;
   uint64_t i0 = c0;
   while (i0 < c1) {
-    if (tid == 0) s_seg = seg[i0];
+    if (tid == 0) sm.seg = seg[i0];
     __syncthreads();
-    const uint32_t sg = s_seg;
+    const uint32_t sg = sm.seg;
     const SegSel& st = sel[sg];
     const bool collect = seg_collects(st);
     const bool count = st.active && !st.done && !collect;
@@ -509,7 +611,7 @@ __global__ void __launch_bounds__(SS_BLOCK) k_segsel_hist(const uint64_t* __rest
       i1 = lo;
     }
     if (count) {
-      for (int b = tid; b < SS_BINS; b += SS_BLOCK) s_cnt[b] = 0;
+      for (int b = tid; b < SS_BINS; b += SS_BLOCK) sm.cnt[b] = 0;
       __syncthreads();
       const bool need_lo = bits > 64 || sh < 64;
       for (uint64_t b0 = i0; b0 < i1; b0 += (uint64_t)SS_BLOCK * SS_ILP) {
@@ -530,16 +632,16 @@ __global__ void __launch_bounds__(SS_BLOCK) k_segsel_hist(const uint64_t* __rest
             // first level: the digit is the exponent, shared by most lanes
             const uint32_t dg = act ? z_digit(hi, lo, sh, D) : 0xffffffffu;
             const uint32_t peers = __match_any_sync(0xffffffffu, dg);
-            if (act && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&s_cnt[dg], (uint32_t)__popc(peers));
+            if (act && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&sm.cnt[dg], (uint32_t)__popc(peers));
           } else if (act) {
-            atomicAdd(&s_cnt[z_digit(hi, lo, sh, D)], 1u);
+            atomicAdd(&sm.cnt[z_digit(hi, lo, sh, D)], 1u);
           }
         }
       }
       __syncthreads();
       uint32_t* gc = g_cnt + (uint64_t)sg * SS_BINS;
       for (int b = tid; b < (1 << D); b += SS_BLOCK)
-        if (s_cnt[b]) atomicAdd(&gc[b], s_cnt[b]);
+        if (sm.cnt[b]) atomicAdd(&gc[b], sm.cnt[b]);
     } else if (collect) {
       uint64_t* buf = g_buf + (uint64_t)sg * 2 * SF_CAP;
       u128 tot = 0, above = 0;
@@ -578,15 +680,15 @@ __global__ void __launch_bounds__(SS_BLOCK) k_segsel_hist(const uint64_t* __rest
       tot = warp_sum_u128(tot);
       above = warp_sum_u128(above);
       if (lane == 0) {
-        s_part[0][warp] = tot;
-        s_part[1][warp] = above;
+        sm.part[0][warp] = tot;
+        sm.part[1][warp] = above;
       }
       __syncthreads();
       if (tid == 0) {
         u128 t = 0, a = 0;
         for (int w = 0; w < SS_BLOCK / 32; ++w) {
-          t += s_part[0][w];
-          a += s_part[1][w];
+          t += sm.part[0][w];
+          a += sm.part[1][w];
         }
         if (t) atomic_add_u128(&g_sum[4 * sg], &g_sum[4 * sg + 1], t);
         if (a) atomic_add_u128(&g_sum[4 * sg + 2], &g_sum[4 * sg + 3], a);
@@ -597,13 +699,30 @@ __global__ void __launch_bounds__(SS_BLOCK) k_segsel_hist(const uint64_t* __rest
   }
 }
 
+__global__ void __launch_bounds__(SS_BLOCK) k_segsel_hist(const uint64_t* __restrict__ probs,
+                                                          const uint64_t* __restrict__ keys,
+                                                          const uint16_t* __restrict__ seg,
+                                                          const uint64_t* __restrict__ n_dev,
+                                                          const SegSel* __restrict__ sel,
+                                                          uint32_t* __restrict__ g_cnt, uint64_t* __restrict__ g_sum,
+                                                          uint64_t* __restrict__ g_buf, uint32_t* __restrict__ g_bufn,
+                                                          uint32_t* err) {
+  __shared__ SegHistSmem sm;
+  segsel_hist_chunk(probs, keys, seg, n_dev, sel, g_cnt, g_sum, g_buf, g_bufn, err, blockIdx.x, gridDim.x, sm);
+}
+
 // One block per counting segment: pick the bin holding the target rank.
-__global__ void __launch_bounds__(256) k_segsel_pick(SegSel* __restrict__ sel, const uint32_t* __restrict__ g_cnt) {
-  __shared__ uint64_t w_c[8];
-  __shared__ uint32_t s_first;
-  SegSel& st = sel[blockIdx.x];
+struct SegPickSmem {
+  uint64_t w_c[8];
+  uint32_t first;
+};
+
+// Slot `slot` (blockDim.x == 256).
+__device__ __forceinline__ void segsel_pick_slot(SegSel* __restrict__ sel, const uint32_t* __restrict__ g_cnt,
+                                                 uint32_t slot, SegPickSmem& sm) {
+  SegSel& st = sel[slot];
   if (!st.active || st.done || seg_collects(st)) return;
-  const uint32_t* cnt = g_cnt + (uint64_t)blockIdx.x * SS_BINS;
+  const uint32_t* cnt = g_cnt + (uint64_t)slot * SS_BINS;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int bits = (int)st.bits;
   int D, shift;
@@ -619,11 +738,11 @@ __global__ void __launch_bounds__(256) k_segsel_pick(SegSel* __restrict__ sel, c
     const uint64_t yc = __shfl_up_sync(0xffffffffu, (unsigned long long)xc, o);
     if (lane >= o) xc += yc;
   }
-  if (lane == 31) w_c[warp] = xc;
-  if (tid == 0) s_first = 0xffffffffu;
+  if (lane == 31) sm.w_c[warp] = xc;
+  if (tid == 0) sm.first = 0xffffffffu;
   __syncthreads();
   uint64_t base_c = 0;
-  for (int w = 0; w < warp; ++w) base_c += w_c[w];
+  for (int w = 0; w < warp; ++w) base_c += sm.w_c[w];
   const uint64_t excl_c = base_c + xc - my_c;
   const uint64_t target = st.target;
   const uint64_t before_c = st.before_count;
@@ -633,13 +752,13 @@ __global__ void __launch_bounds__(256) k_segsel_pick(SegSel* __restrict__ sel, c
       const uint32_t c = cnt[b];
       cc += c;
       if (c > 0 && cc >= target) {
-        atomicMin(&s_first, (uint32_t)b);
+        atomicMin(&sm.first, (uint32_t)b);
         break;
       }
     }
   }
   __syncthreads();
-  const uint32_t first = s_first;
+  const uint32_t first = sm.first;
   if (first == 0xffffffffu) {
     if (tid == 0) st.done = 2;  // fewer terms than the target: not reached for an active segment
     return;
@@ -657,6 +776,11 @@ __global__ void __launch_bounds__(256) k_segsel_pick(SegSel* __restrict__ sel, c
   }
 }
 
+__global__ void __launch_bounds__(256) k_segsel_pick(SegSel* __restrict__ sel, const uint32_t* __restrict__ g_cnt) {
+  __shared__ SegPickSmem sm;
+  segsel_pick_slot(sel, g_cnt, blockIdx.x, sm);
+}
+
 // cfg picks the scan's blocks per SM: 2, 4 or 8.
 void launch_segsel_level(const uint64_t* probs, const uint64_t* keys, const uint16_t* seg, const uint64_t* n_dev,
                          SegSel* sel, int slots, uint32_t* g_cnt, uint64_t* g_sum, uint64_t* g_buf, uint32_t* g_bufn,
@@ -669,12 +793,15 @@ void launch_segsel_level(const uint64_t* probs, const uint64_t* keys, const uint
   k_segsel_pick<<<slots, 256, 0, st>>>(sel, g_cnt);
 }
 
+void launch_segsel_pick(SegSel* sel, int slots, const uint32_t* g_cnt, cudaStream_t st) {
+  k_segsel_pick<<<slots, 256, 0, st>>>(sel, g_cnt);
+}
+
 // Select state of every slot for this step: a slot in use with more terms
 // than its K is truncated to its top K (Sec. III).
-__global__ void k_segsel_init(SegSel* __restrict__ sel, const SegGate* __restrict__ gates,
-                              const uint64_t* __restrict__ start, const uint64_t* __restrict__ end, int slots) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= slots) return;
+__device__ __forceinline__ void segsel_init_slot(SegSel* __restrict__ sel, const SegGate* __restrict__ gates,
+                                                 const uint64_t* __restrict__ start, const uint64_t* __restrict__ end,
+                                                 int s) {
   SegSel st;
   memset(&st, 0, sizeof(SegSel));
   const uint64_t count = end[s] > start[s] ? end[s] - start[s] : 0;
@@ -689,6 +816,13 @@ __global__ void k_segsel_init(SegSel* __restrict__ sel, const SegGate* __restric
   sel[s] = st;
 }
 
+__global__ void k_segsel_init(SegSel* __restrict__ sel, const SegGate* __restrict__ gates,
+                              const uint64_t* __restrict__ start, const uint64_t* __restrict__ end, int slots) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= slots) return;
+  segsel_init_slot(sel, gates, start, end, s);
+}
+
 void launch_segsel_init(SegSel* sel, const SegGate* gates, const uint64_t* start, const uint64_t* end, int slots,
                         cudaStream_t st) {
   k_segsel_init<<<(slots + 127) / 128, 128, 0, st>>>(sel, gates, start, end, slots);
@@ -696,42 +830,49 @@ void launch_segsel_init(SegSel* sel, const SegGate* gates, const uint64_t* start
 
 // Finish: one block per segment collected in this level's scan resolves the
 // cut among the copied terms, level after level inside shared memory.
-__global__ void __launch_bounds__(256) k_segsel_finish(const uint64_t* __restrict__ g_buf,
-                                                       const uint32_t* __restrict__ g_bufn,
-                                                       const uint64_t* __restrict__ g_sum, SegSel* sel,
-                                                       uint32_t* err) {
-  extern __shared__ __align__(16) uint8_t s_dyn[];
-  uint64_t* bhi = reinterpret_cast<uint64_t*>(s_dyn);
-  uint64_t* blo = bhi + SF_CAP;
-  __shared__ uint32_t s_cnt[SS_BINS];
-  __shared__ uint64_t s_mass[2 * SS_BINS];
-  __shared__ uint64_t w_c[8];
-  __shared__ u128 w_m[8];
-  __shared__ uint32_t s_first;
-  __shared__ SegSel st;  // the segment's select state, updated here and written back once
+struct SegFinishSmem {
+  uint32_t cnt[SS_BINS];
+  uint64_t mass[2 * SS_BINS];
+  uint64_t w_c[8];
+  u128 w_m[8];
+  uint32_t first;
+  SegSel st;  // the segment's select state, updated here and written back once
+};
+
+// Slot `slot` (blockDim.x == 256).  With STAGE the copied terms are first
+// staged in shared memory (stage: 2 * SF_CAP words); without, every level
+// reads them from the copy buffer in global memory (a few KB, L2-resident).
+template <bool STAGE>
+__device__ __forceinline__ void segsel_finish_slot(const uint64_t* __restrict__ g_buf,
+                                                   const uint32_t* __restrict__ g_bufn,
+                                                   const uint64_t* __restrict__ g_sum, SegSel* sel, uint32_t* err,
+                                                   uint32_t slot, SegFinishSmem& sm, uint64_t* stage) {
+  SegSel& st = sm.st;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) {
-    st = sel[blockIdx.x];
+    st = sel[slot];
   }
   __syncthreads();
   // only segments whose terms this level's scan copied (a collected bin is
   // never empty; a segment that entered collect mode in this level's pick
   // has nothing copied yet and waits for the next scan)
-  const uint32_t copied = g_bufn[blockIdx.x];
+  const uint32_t copied = g_bufn[slot];
   if (!st.active || st.done || copied == 0) return;
   const uint32_t nb = copied < SF_CAP ? copied : SF_CAP;
   if (tid == 0) {
-    st.total_mass_hi = g_sum[4 * blockIdx.x];
-    st.total_mass_lo = g_sum[4 * blockIdx.x + 1];
-    st.before_mass_hi = g_sum[4 * blockIdx.x + 2];
-    st.before_mass_lo = g_sum[4 * blockIdx.x + 3];
+    st.total_mass_hi = g_sum[4 * slot];
+    st.total_mass_lo = g_sum[4 * slot + 1];
+    st.before_mass_hi = g_sum[4 * slot + 2];
+    st.before_mass_lo = g_sum[4 * slot + 3];
   }
-  {
-    const uint64_t* buf = g_buf + (uint64_t)blockIdx.x * 2 * SF_CAP;
+  const uint64_t* buf = g_buf + (uint64_t)slot * 2 * SF_CAP;
+  const uint64_t* bz = buf;  // term i: (bz[2 i], bz[2 i + 1]) = (hi, lo)
+  if (STAGE) {
     for (uint32_t i = tid; i < nb; i += blockDim.x) {
-      bhi[i] = buf[2 * i];
-      blo[i] = buf[2 * i + 1];
+      stage[2 * i] = buf[2 * i];
+      stage[2 * i + 1] = buf[2 * i + 1];
     }
+    bz = stage;
   }
   __syncthreads();
   for (int it = 0; it < 128; ++it) {
@@ -742,16 +883,16 @@ __global__ void __launch_bounds__(256) k_segsel_finish(const uint64_t* __restric
       // one term left under the prefix: it is the cut, the terms before it
       // are those counted so far (or the target is never reached)
       for (uint32_t i = tid; i < nb; i += blockDim.x) {
-        if (!z_matches(bhi[i], blo[i], st.prefix_hi, st.prefix_lo, bits)) continue;
+        if (!z_matches(bz[2 * i], bz[2 * i + 1], st.prefix_hi, st.prefix_lo, bits)) continue;
         const uint64_t cc = st.before_count + 1;
         if (cc < st.target) {
           st.done = 2;
           continue;
         }
-        const uint64_t pbits = ~bhi[i];
+        const uint64_t pbits = ~bz[2 * i];
         const u128 sc = make_u128(st.before_mass_hi, st.before_mass_lo) + fx_from_bits(pbits, err);
         st.cut_pbits = pbits;
-        st.cut_key = blo[i];
+        st.cut_key = bz[2 * i + 1];
         st.cut_count = cc;
         st.cut_mass_hi = (uint64_t)(sc >> 64);
         st.cut_mass_lo = (uint64_t)sc;
@@ -763,16 +904,16 @@ __global__ void __launch_bounds__(256) k_segsel_finish(const uint64_t* __restric
     int D, shift;
     sel_digit(bits, &D, &shift);
     for (int b = tid; b < SS_BINS; b += blockDim.x) {
-      s_cnt[b] = 0;
-      s_mass[2 * b] = s_mass[2 * b + 1] = 0;
+      sm.cnt[b] = 0;
+      sm.mass[2 * b] = sm.mass[2 * b + 1] = 0;
     }
-    if (tid == 0) s_first = 0xffffffffu;
+    if (tid == 0) sm.first = 0xffffffffu;
     __syncthreads();
     for (uint32_t i = tid; i < nb; i += blockDim.x) {
-      if (!z_matches(bhi[i], blo[i], st.prefix_hi, st.prefix_lo, bits)) continue;
-      const uint32_t dg = (uint32_t)(make_u128(bhi[i], blo[i]) >> shift) & ((1u << D) - 1u);
-      atomicAdd(&s_cnt[dg], 1u);
-      atomic_add_u128(&s_mass[2 * dg], &s_mass[2 * dg + 1], fx_from_bits(~bhi[i], err));
+      if (!z_matches(bz[2 * i], bz[2 * i + 1], st.prefix_hi, st.prefix_lo, bits)) continue;
+      const uint32_t dg = (uint32_t)(make_u128(bz[2 * i], bz[2 * i + 1]) >> shift) & ((1u << D) - 1u);
+      atomicAdd(&sm.cnt[dg], 1u);
+      atomic_add_u128(&sm.mass[2 * dg], &sm.mass[2 * dg + 1], fx_from_bits(~bz[2 * i], err));
     }
     __syncthreads();
     const int nbins = 1 << D;
@@ -781,8 +922,8 @@ __global__ void __launch_bounds__(256) k_segsel_finish(const uint64_t* __restric
     uint64_t my_c = 0;
     u128 my_m = 0;
     for (int b = b0; b < b0 + per && b < nbins; ++b) {
-      my_c += s_cnt[b];
-      my_m += make_u128(s_mass[2 * b], s_mass[2 * b + 1]);
+      my_c += sm.cnt[b];
+      my_m += make_u128(sm.mass[2 * b], sm.mass[2 * b + 1]);
     }
     uint64_t xc = my_c;
     u128 xm = my_m;
@@ -797,15 +938,15 @@ __global__ void __launch_bounds__(256) k_segsel_finish(const uint64_t* __restric
       }
     }
     if (lane == 31) {
-      w_c[warp] = xc;
-      w_m[warp] = xm;
+      sm.w_c[warp] = xc;
+      sm.w_m[warp] = xm;
     }
     __syncthreads();
     uint64_t base_c = 0;
     u128 base_m = 0;
     for (int w = 0; w < warp; ++w) {
-      base_c += w_c[w];
-      base_m += w_m[w];
+      base_c += sm.w_c[w];
+      base_m += sm.w_m[w];
     }
     const uint64_t excl_c = base_c + xc - my_c;
     const u128 excl_m = base_m + xm - my_m;
@@ -815,16 +956,16 @@ __global__ void __launch_bounds__(256) k_segsel_finish(const uint64_t* __restric
     {
       uint64_t cc = before_c + excl_c;
       for (int b = b0; b < b0 + per && b < nbins; ++b) {
-        const uint32_t c = s_cnt[b];
+        const uint32_t c = sm.cnt[b];
         cc += c;
         if (c > 0 && cc >= target) {
-          atomicMin(&s_first, (uint32_t)b);
+          atomicMin(&sm.first, (uint32_t)b);
           break;
         }
       }
     }
     __syncthreads();
-    const uint32_t first = s_first;
+    const uint32_t first = sm.first;
     if (first == 0xffffffffu) {
       if (tid == 0) st.done = 2;
       __syncthreads();
@@ -834,8 +975,8 @@ __global__ void __launch_bounds__(256) k_segsel_finish(const uint64_t* __restric
       uint64_t bc = before_c + excl_c;
       u128 bm = before_m + excl_m;
       for (int b = b0; b < (int)first; ++b) {
-        bc += s_cnt[b];
-        bm += make_u128(s_mass[2 * b], s_mass[2 * b + 1]);
+        bc += sm.cnt[b];
+        bm += make_u128(sm.mass[2 * b], sm.mass[2 * b + 1]);
       }
       u128 prefix = make_u128(st.prefix_hi, st.prefix_lo);
       prefix |= ((u128)first) << shift;
@@ -846,7 +987,7 @@ __global__ void __launch_bounds__(256) k_segsel_finish(const uint64_t* __restric
       st.before_count = bc;
       st.before_mass_hi = (uint64_t)(bm >> 64);
       st.before_mass_lo = (uint64_t)bm;
-      st.bin_count = s_cnt[first];
+      st.bin_count = sm.cnt[first];
       if (nbits == 128) {
         const uint64_t pbits = ~(uint64_t)(prefix >> 64);
         const u128 sc = bm + fx_from_bits(pbits, err);
@@ -860,8 +1001,19 @@ __global__ void __launch_bounds__(256) k_segsel_finish(const uint64_t* __restric
     }
   }
   __syncthreads();
-  if (tid == 0) sel[blockIdx.x] = st;
+  if (tid == 0) sel[slot] = st;
 }
+
+__global__ void __launch_bounds__(256) k_segsel_finish(const uint64_t* __restrict__ g_buf,
+                                                       const uint32_t* __restrict__ g_bufn,
+                                                       const uint64_t* __restrict__ g_sum, SegSel* sel,
+                                                       uint32_t* err) {
+  extern __shared__ __align__(16) uint64_t s_stage[];
+  __shared__ SegFinishSmem sm;
+  segsel_finish_slot<true>(g_buf, g_bufn, g_sum, sel, err, blockIdx.x, sm, s_stage);
+}
+
+cudaError_t layer_attrs();
 
 // Kernel attributes (dynamic shared memory) set once, outside any stream
 // capture.
@@ -872,6 +1024,7 @@ cudaError_t batch_prepare() {
                                          (int)(2 * sizeof(uint64_t) * SF_CAP));
     if (r == cudaSuccess) r = seg_apply_attrs<double>();
     if (r == cudaSuccess) r = seg_apply_attrs<float>();
+    if (r == cudaSuccess) r = layer_attrs();
     return r;
   });
   if (e == cudaSuccess) e = sort_prepare();
@@ -886,11 +1039,14 @@ void launch_segsel_finish(const uint64_t* g_buf, const uint32_t* g_bufn, const u
 }
 
 // Renormalisation scale of every segment that found a cut.
+__device__ __forceinline__ void segsel_scale_slot(SegSel& st) {
+  if (st.active && st.done == 1) st.scale = __ddiv_rn(1.0, __dsqrt_rn(fx_to_double(make_u128(st.cut_mass_hi, st.cut_mass_lo))));
+}
+
 __global__ void k_segsel_scale(SegSel* sel, int slots) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= slots) return;
-  SegSel& st = sel[s];
-  if (st.active && st.done == 1) st.scale = __ddiv_rn(1.0, __dsqrt_rn(fx_to_double(make_u128(st.cut_mass_hi, st.cut_mass_lo))));
+  segsel_scale_slot(sel[s]);
 }
 
 void launch_segsel_scale(SegSel* sel, int slots, cudaStream_t st) {
@@ -902,26 +1058,33 @@ constexpr int SC_BLOCK = 256, SC_ITEMS = 8;
 
 // Keep, in each segment with a cut, the terms not after its cut (scaled);
 // other segments keep everything unchanged.
+struct SegTruncSmem {
+  CompactShared<SC_BLOCK> cs;
+  uint64_t tile;
+  uint16_t list[SC_BLOCK * SC_ITEMS];
+  uint16_t slots[SC_BLOCK * SC_ITEMS];  // slot of each kept term (segment bounds)
+};
+
+// Tiles taken from ctl->tile_counter[2] until none is left; the kept count
+// lands in ctl->count[2].
 template <typename C2>
-__global__ void __launch_bounds__(SC_BLOCK, 4) k_seg_truncate(
+__device__ __forceinline__ void seg_truncate_run(
     const uint64_t* __restrict__ keys, const C2* __restrict__ amps, const uint64_t* __restrict__ probs,
     const uint16_t* __restrict__ seg, const uint64_t* __restrict__ n_dev, uint64_t n_max,
     const SegSel* __restrict__ sel, uint64_t* __restrict__ keys_out, C2* __restrict__ amps_out,
-    uint64_t* __restrict__ probs_out, uint16_t* __restrict__ seg_out, uint64_t* lookback, Ctl* ctl) {
+    uint16_t* __restrict__ seg_out, uint64_t* __restrict__ start, uint64_t* __restrict__ end, uint64_t* lookback,
+    Ctl* ctl, SegTruncSmem& sm) {
   typedef TileLayout<SC_BLOCK, SC_ITEMS> L;
-  __shared__ CompactShared<SC_BLOCK> cs;
-  __shared__ uint64_t s_tile;
-  __shared__ uint16_t s_list[SC_BLOCK * SC_ITEMS];
   const uint64_t n = *n_dev;
   if (n > n_max) {  // the look-back buffer was sized for n_max terms
-    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&ctl->err, ERR_INVARIANT);
+    if (threadIdx.x == 0) atomicOr(&ctl->err, ERR_INVARIANT);
     return;
   }
   const uint64_t tiles = (n + L::TILE - 1) / L::TILE;
   while (true) {
-    if (threadIdx.x == 0) s_tile = atomicAdd((unsigned long long*)&ctl->tile_counter[2], 1ull);
+    if (threadIdx.x == 0) sm.tile = atomicAdd((unsigned long long*)&ctl->tile_counter[2], 1ull);
     __syncthreads();
-    const uint64_t tile = s_tile;
+    const uint64_t tile = sm.tile;
     if (tile >= tiles) break;
     const uint64_t base = tile * L::TILE;
     bool flag[SC_ITEMS];
@@ -957,18 +1120,18 @@ __global__ void __launch_bounds__(SC_BLOCK, 4) k_seg_truncate(
       }
       flag[j] = f;
     }
-    tile_compact<SC_BLOCK, SC_ITEMS>(flag, pos, cs, lookback, tile, &ctl->err);
+    tile_compact<SC_BLOCK, SC_ITEMS>(flag, pos, sm.cs, lookback, tile, &ctl->err);
     // list the kept terms, then process the list densely (all lanes busy,
     // contiguous writes)
 #pragma unroll
     for (int j = 0; j < SC_ITEMS; ++j)
-      if (flag[j]) s_list[pos[j]] = (uint16_t)(L::index(base, j) - base);
+      if (flag[j]) sm.list[pos[j]] = (uint16_t)(L::index(base, j) - base);
     __syncthreads();
     last = -1;
-    const uint32_t kept = cs.tile_total;
-    const uint64_t ob = cs.tile_base_out;
+    const uint32_t kept = sm.cs.tile_total;
+    const uint64_t ob = sm.cs.tile_base_out;
     for (uint32_t t = threadIdx.x; t < kept; t += SC_BLOCK) {
-      const uint64_t i = base + s_list[t];
+      const uint64_t i = base + sm.list[t];
       const uint16_t sg = seg[i];
       if ((int)sg != last) {
         last = sg;
@@ -977,27 +1140,37 @@ __global__ void __launch_bounds__(SC_BLOCK, 4) k_seg_truncate(
         scale = st.scale;
       }
       C2 a = amps[i];
-      uint64_t pb;
-      if (cut_on) {
-        a = amp_scaled(a, scale);
-        pb = amp_prob_bits(a);
-      } else {
-        pb = probs[i];
-      }
+      if (cut_on) a = amp_scaled(a, scale);
       keys_out[ob + t] = keys[i];
       amps_out[ob + t] = a;
-      probs_out[ob + t] = pb;
       seg_out[ob + t] = sg;
+      sm.slots[t] = sg;
     }
-    if (tile == tiles - 1 && threadIdx.x == 0) ctl->count[2] = cs.tile_base_out + cs.tile_total;
+    if (start) {
+      __syncthreads();
+      for (uint32_t t = threadIdx.x; t < kept; t += SC_BLOCK) seg_bound_marks(sm.slots, t, kept, ob, start, end);
+    }
+    if (tile == tiles - 1 && threadIdx.x == 0) ctl->count[2] = sm.cs.tile_base_out + sm.cs.tile_total;
     __syncthreads();
   }
 }
 
+template <typename C2>
+__global__ void __launch_bounds__(SC_BLOCK, 4) k_seg_truncate(
+    const uint64_t* __restrict__ keys, const C2* __restrict__ amps, const uint64_t* __restrict__ probs,
+    const uint16_t* __restrict__ seg, const uint64_t* __restrict__ n_dev, uint64_t n_max,
+    const SegSel* __restrict__ sel, uint64_t* __restrict__ keys_out, C2* __restrict__ amps_out,
+    uint16_t* __restrict__ seg_out, uint64_t* __restrict__ start, uint64_t* __restrict__ end, uint64_t* lookback,
+    Ctl* ctl) {
+  __shared__ SegTruncSmem sm;
+  seg_truncate_run<C2>(keys, amps, probs, seg, n_dev, n_max, sel, keys_out, amps_out, seg_out, start, end, lookback,
+                       ctl, sm);
+}
+
 void launch_seg_truncate(int prec, const uint64_t* keys, const void* amps, const uint64_t* probs, const uint16_t* seg,
                          const uint64_t* n_dev, uint64_t n_max, const SegSel* sel, uint64_t* keys_out,
-                         void* amps_out, uint64_t* probs_out, uint16_t* seg_out, uint64_t* lookback, Ctl* ctl,
-                         int cfg, cudaStream_t st) {
+                         void* amps_out, uint16_t* seg_out, uint64_t* start, uint64_t* end, uint64_t* lookback,
+                         Ctl* ctl, int cfg, cudaStream_t st) {
   const uint64_t tiles = (n_max + SC_BLOCK * SC_ITEMS - 1) / (SC_BLOCK * SC_ITEMS);
   cudaMemsetAsync(lookback, 0, sizeof(uint64_t) * (tiles + 1), st);
   cudaMemsetAsync(&ctl->tile_counter[2], 0, sizeof(uint64_t), st);
@@ -1008,12 +1181,364 @@ void launch_seg_truncate(int prec, const uint64_t* keys, const void* amps, const
   const uint64_t grid = tiles < 148 * per_sm ? tiles : 148 * per_sm;
   if (prec == 0)
     k_seg_truncate<double2><<<(unsigned)grid, SC_BLOCK, 0, st>>>(keys, (const double2*)amps, probs, seg, n_dev, n_max,
-                                                                 sel, keys_out, (double2*)amps_out, probs_out,
-                                                                 seg_out, lookback, ctl);
+                                                                 sel, keys_out, (double2*)amps_out, seg_out,
+                                                                 start, end, lookback, ctl);
   else
     k_seg_truncate<float2><<<(unsigned)grid, SC_BLOCK, 0, st>>>(keys, (const float2*)amps, probs, seg, n_dev, n_max,
-                                                                sel, keys_out, (float2*)amps_out, probs_out, seg_out,
-                                                                lookback, ctl);
+                                                                sel, keys_out, (float2*)amps_out, seg_out,
+                                                                start, end, lookback, ctl);
+}
+
+// ---------------------------------------------------------------- one launch per layer
+// The whole step of the batched form as one persistent kernel: a grid of
+// co-resident blocks (cooperative launch) runs the phases of the step one
+// after another, with a grid-wide barrier between phases, and every size
+// is read on the device (the term counts of the previous phase), so the
+// launch and the copies around it are captured once in a CUDA graph and
+// replayed for every later step of the same shape.  The phases are the
+// bodies of the standalone kernels above and of the regrouping kernels,
+// with 256-thread blocks: the sort keys; the stable partition by the gate
+// bits and the merge levels; group heads; the mat-vec (which also counts the
+// select's first digit per slot); segment bounds; the per-slot top-k select
+// level after level until every cut is found; the renormalisation scales;
+// the compaction and the new bounds.
+
+constexpr int LAYER_THREADS = 256;
+constexpr int LAYER_ITEMS = RG_TILE / LAYER_THREADS;  // partition and merge items per thread
+constexpr int LAYER_LEVELS = 16;                       // select levels before a cut counts as unresolved
+constexpr int LAYER_GPT = 1;                           // mat-vec groups per thread
+constexpr size_t LAYER_HDR = (sizeof(SegApplySmem) > sizeof(MergeHdr) ? sizeof(SegApplySmem) : sizeof(MergeHdr)) /
+                                 128 * 128 + 128;
+
+// Spin limit of the grid barrier (polls with back-off up to 1 us: a few
+// seconds); a block that gives up records ERR_TIMEOUT and the layer stops.
+constexpr uint32_t LAYER_SPIN_LIMIT = 1u << 22;
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid-wide barrier of the layer kernel (all threads of every block call
+// it).  The last block to arrive reads the error word (every error recorded
+// before the barrier is visible to it) and publishes the next generation
+// with a stop bit, so all blocks leave the barrier with the same decision.
+// Returns true when the layer must stop.
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// The first block charges the time since the last barrier to `phase`.
+__device__ __forceinline__ void layer_phase_mark(LayerCtl* lc, int phase) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const uint64_t now = global_ns();
+    lc->phase_ns[phase] += now - lc->t_last;
+    lc->t_last = now;
+  }
+}
+
+__device__ __forceinline__ bool layer_sync(LayerCtl* lc, uint32_t nblocks, uint32_t* err, int phase) {
+  __syncthreads();
+  int stop = 0;
+  if (threadIdx.x == 0) {
+    const uint32_t g0 = ld_acquire_u32(&lc->bar_gen) & 0x7fffffffu;
+    __threadfence();
+    const uint32_t arrived = atomicAdd(&lc->bar_count, 1u) + 1u;
+    __threadfence();
+    if (arrived == nblocks) {
+      const uint32_t e = ld_acquire_u32(err);
+      atomicExch(&lc->bar_count, 0u);
+      __threadfence();
+      st_release_u32(&lc->bar_gen, ((g0 + 1u) & 0x7fffffffu) | (e ? 0x80000000u : 0u));
+      stop = e != 0;
+    } else {
+      uint32_t spins = 0, ns = 32;
+      while (true) {
+        const uint32_t g = ld_acquire_u32(&lc->bar_gen);
+        if ((g & 0x7fffffffu) != g0) {
+          stop = (int)(g >> 31);
+          break;
+        }
+        if (++spins > LAYER_SPIN_LIMIT) {
+          atomicOr(err, ERR_TIMEOUT);
+          stop = 1;
+          break;
+        }
+        __nanosleep(ns);
+        if (ns < 1024) ns <<= 1;
+      }
+    }
+    __threadfence();
+  }
+  layer_phase_mark(lc, phase);
+  return __syncthreads_or(stop) != 0;
+}
+
+template <typename T>
+__device__ __forceinline__ T& smem_as(uint8_t* p) {
+  return *reinterpret_cast<T*>(p);
+}
+
+template <typename Real, int MAXD>
+__global__ void __launch_bounds__(LAYER_THREADS, MAXD <= 4 ? 4 : (MAXD == 8 ? 2 : 1)) k_seg_layer(const LayerParams P) {
+  typedef typename SCplx<Real>::T C2;
+  extern __shared__ __align__(16) uint8_t smem[];
+  uint8_t* const dyn = smem + LAYER_HDR;  // a phase's staging area, after its shared variables
+  const uint32_t cta = blockIdx.x, ncta = gridDim.x;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const uint64_t gtid = (uint64_t)cta * LAYER_THREADS + tid, gstride = (uint64_t)ncta * LAYER_THREADS;
+  const LayerStep S = *P.step;
+  const uint64_t N = S.N, nkeep = S.nkeep;
+  const int shift = S.shift, top = S.top, m = S.m, D = 1 << m;
+  Ctl* ctl = P.ctl;
+  uint32_t* err = &ctl->err;
+  LayerCtl* lc = P.lc;
+  uint64_t* lb_heads = P.lb;
+  uint64_t* lb_apply = lb_heads + P.lb_heads_words;
+  uint64_t* lb_trunc = lb_apply + P.lb_apply_words;
+
+  // clear this layer's counters, look-backs and select histograms; tables
+  for (uint64_t i = gtid; i < P.lb_heads_words + P.lb_apply_words + P.lb_trunc_words; i += gstride) P.lb[i] = 0;
+  for (uint64_t i = gtid; i < (uint64_t)top * SEL_BINS; i += gstride) P.sel_cnt[0][i] = P.sel_cnt[1][i] = 0;
+  for (uint64_t i = gtid; i < (uint64_t)top; i += gstride) {
+    P.sel_bufn[0][i] = P.sel_bufn[1][i] = 0;
+    P.start[i] = P.start_tr[i] = ~0ull;
+    P.end[i] = P.end_tr[i] = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) P.sel_mass[0][4 * i + j] = P.sel_mass[1][4 * i + j] = 0;
+  }
+  if (gtid < 16) P.hist16[gtid] = 0;
+  if (gtid == 0) {
+    for (int j = 0; j < 3; ++j) {
+      ctl->tile_counter[j] = 0;
+      ctl->count[j] = 0;
+    }
+    lc->truncated = 0;
+    lc->unresolved = 0;
+    lc->n_out = 0;
+  }
+  if (cta == 0 && tid < LP_COUNT) lc->phase_ns[tid] = 0;
+  if (cta == 0 && tid == 0) lc->t_last = global_ns();
+  for (uint32_t vb = cta; vb < (uint32_t)top; vb += ncta) {
+    seg_tables_slot(P.gates, P.tables, vb, smem_as<SegTablesSmem>(smem));
+    __syncthreads();
+  }
+  if (layer_sync(lc, ncta, err, LP_SETUP)) return;
+
+  // sort keys, then the grouping: partition by the gate bits, m merge levels
+  seg_keys_range(P.keys_in, P.seg_in, N, P.gates, P.tables, shift, P.sk[1], gtid, gstride);
+  if (layer_sync(lc, ncta, err, LP_KEYS)) return;
+  GateParams gp;
+  memset(&gp, 0, sizeof(gp));
+  gp.m = m;
+  gp.direct = 1;
+  const uint64_t tiles = (N + RG_TILE - 1) / RG_TILE;
+  uint32_t* cnt = P.part;
+  uint32_t* off = cnt + (uint64_t)D * tiles;
+  for (uint64_t t = cta; t < tiles; t += ncta) {
+    part_counts_tile<LAYER_THREADS, LAYER_ITEMS>(P.sk[1], N, gp, tiles, cnt, P.hist16, t,
+                                                 smem_as<PartCountsSmem>(smem));
+    __syncthreads();
+  }
+  if (layer_sync(lc, ncta, err, LP_COUNTS)) return;
+  for (uint32_t d = cta; d < (uint32_t)D; d += ncta) {
+    tile_offsets_digit<LAYER_THREADS>(cnt, P.hist16, tiles, off, (int)d, smem_as<TileOffsetsSmem<LAYER_THREADS>>(smem));
+    __syncthreads();
+  }
+  if (layer_sync(lc, ncta, err, LP_OFFSETS)) return;
+  for (uint64_t t = cta; t < tiles; t += ncta) {
+    part_scatter_tile<LAYER_THREADS, LAYER_ITEMS, true>(P.sk[1], N, gp, tiles, off, P.sk[0], P.sidx[0], t,
+                                                        smem_as<PartScatterSmem<LAYER_THREADS>>(smem));
+    __syncthreads();
+  }
+  if (layer_sync(lc, ncta, err, LP_SCATTER)) return;
+  int cur = 0;
+  const uint32_t mblocks = (uint32_t)((N + MG_TILE - 1) / MG_TILE) + (uint32_t)D;
+  uint32_t* splits = cnt;  // the partition's counts are no longer needed
+  for (int level = 1; level <= m; ++level) {
+    for (uint64_t w = gtid >> 5; w < mblocks; w += gstride >> 5)
+      merge_split_warp(P.sk[cur], P.hist16, D, level, (uint32_t)w, splits, lane);
+    if (layer_sync(lc, ncta, err, LP_SPLITS)) return;
+    for (uint32_t b = cta; b < mblocks; b += ncta) {
+      merge_tile<LAYER_THREADS, LAYER_ITEMS, true>(P.sk[cur], P.sidx[cur], P.sk[1 - cur], P.sidx[1 - cur],
+                                                   P.hist16, D, level, splits, b, smem_as<MergeHdr>(smem), dyn);
+      __syncthreads();
+    }
+    if (layer_sync(lc, ncta, err, LP_MERGE)) return;
+    cur ^= 1;
+  }
+
+  // group heads, then the mat-vec (counting the select's first digit)
+  seg_heads_run(P.sk[cur], nkeep, shift, P.gates, P.rank_slot, P.heads, lb_heads, ctl, smem_as<SegHeadsSmem>(smem));
+  if (layer_sync(lc, ncta, err, LP_HEADS)) return;
+  if (tid == 0) smem_as<SegApplySmem>(smem).hcnt = reinterpret_cast<uint32_t*>(dyn + seg_apply_smem<C2>(MAXD, LAYER_GPT));
+  __syncthreads();
+  seg_apply_run<Real, MAXD, LAYER_GPT>(P.sk[cur], P.sidx[cur], nkeep, P.heads, (const C2*)P.amps_in, shift, P.gates,
+                                       P.rank_slot, P.tables, P.keys_mv, (C2*)P.amps_mv, P.probs_mv, P.seg_mv,
+                                       P.sel_cnt[0], P.start, P.end, lb_apply, P.lb_apply_words - 1, ctl,
+                                       smem_as<SegApplySmem>(smem), dyn);
+  if (layer_sync(lc, ncta, err, LP_APPLY)) return;
+
+  // per-slot top-k: bounds, select state, the first level's pick, then
+  // scan / pick / finish levels until every active slot's cut is found
+  for (uint64_t s = gtid; s < (uint64_t)top; s += gstride) segsel_init_slot(P.sel, P.gates, P.start, P.end, (int)s);
+  if (layer_sync(lc, ncta, err, LP_INIT)) return;
+  for (uint32_t vb = cta; vb < (uint32_t)top; vb += ncta) {
+    segsel_pick_slot(P.sel, P.sel_cnt[0], vb, smem_as<SegPickSmem>(smem));
+    __syncthreads();
+  }
+  if (layer_sync(lc, ncta, err, LP_PICK1)) return;
+  int par = 1;
+  bool pending = true;
+  for (int level = 0; level < LAYER_LEVELS && pending; ++level) {
+    // the other parity's histograms were read by the previous level: clear them for the next
+    for (uint64_t i = gtid; i < (uint64_t)top * SEL_BINS; i += gstride) P.sel_cnt[1 - par][i] = 0;
+    for (uint64_t i = gtid; i < (uint64_t)top; i += gstride) {
+      P.sel_bufn[1 - par][i] = 0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) P.sel_mass[1 - par][4 * i + j] = 0;
+    }
+    segsel_hist_chunk(P.probs_mv, P.keys_mv, P.seg_mv, &ctl->count[1], P.sel, P.sel_cnt[par], P.sel_mass[par],
+                      P.sel_buf, P.sel_bufn[par], err, cta, ncta, smem_as<SegHistSmem>(smem));
+    if (layer_sync(lc, ncta, err, LP_HIST)) return;
+    for (uint32_t vb = cta; vb < (uint32_t)top; vb += ncta) {
+      segsel_pick_slot(P.sel, P.sel_cnt[par], vb, smem_as<SegPickSmem>(smem));
+      __syncthreads();
+    }
+    if (layer_sync(lc, ncta, err, LP_PICK)) return;
+    for (uint32_t vb = cta; vb < (uint32_t)top; vb += ncta) {
+      segsel_finish_slot<false>(P.sel_buf, P.sel_bufn[par], P.sel_mass[par], P.sel, err, vb,
+                                smem_as<SegFinishSmem>(smem), nullptr);
+      __syncthreads();
+    }
+    if (layer_sync(lc, ncta, err, LP_FINISH)) return;
+    bool open = false;  // every block reads the same select states
+    for (int s = tid; s < top; s += LAYER_THREADS) open |= P.sel[s].active && !P.sel[s].done;
+    pending = __syncthreads_or(open) != 0;
+    par ^= 1;
+  }
+  if (pending) {
+    if (gtid == 0) lc->unresolved = 1;
+    return;
+  }
+  for (uint64_t s = gtid; s < (uint64_t)top; s += gstride) segsel_scale_slot(P.sel[s]);
+  bool cut = false;
+  for (int s = tid; s < top; s += LAYER_THREADS) cut |= P.sel[s].active && P.sel[s].done == 1;
+  const bool any_cut = __syncthreads_or(cut) != 0;
+  if (layer_sync(lc, ncta, err, LP_SCALE)) return;
+  if (!any_cut) {
+    if (gtid == 0) lc->n_out = ctl->count[1];
+    return;
+  }
+
+  // compaction of the cut slots, then their new bounds (a slot keeps at
+  // least one term, so every bound written by the mat-vec is overwritten)
+  const uint64_t n_max = (P.lb_trunc_words - 1) * (uint64_t)(SC_BLOCK * SC_ITEMS);
+  seg_truncate_run<C2>(P.keys_mv, (const C2*)P.amps_mv, P.probs_mv, P.seg_mv, &ctl->count[1], n_max, P.sel,
+                       P.keys_tr, (C2*)P.amps_tr, P.seg_tr, P.start_tr, P.end_tr, lb_trunc, ctl,
+                       smem_as<SegTruncSmem>(smem));
+  if (layer_sync(lc, ncta, err, LP_TRUNC)) return;
+  if (gtid == 0) {
+    lc->truncated = 1;
+    lc->n_out = ctl->count[2];
+  }
+}
+
+template <typename Real, int MAXD>
+constexpr size_t layer_smem() {
+  typedef typename SCplx<Real>::T C2;
+  size_t a = seg_apply_smem<C2>(MAXD, LAYER_GPT) + sizeof(uint32_t) * SEL_BINS, b = merge_smem_bytes(true),
+         c = sizeof(SegFinishSmem);
+  size_t x = a > b ? a : b;
+  return LAYER_HDR + (x > c ? x : c);
+}
+
+template <typename Real, int MAXD>
+cudaError_t layer_attr() {
+  return cudaFuncSetAttribute(k_seg_layer<Real, MAXD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)layer_smem<Real, MAXD>());
+}
+
+template <typename Real, int MAXD>
+cudaError_t layer_launch(const LayerParams& P, unsigned grid, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = LAYER_THREADS;
+  cfg.dynamicSmemBytes = layer_smem<Real, MAXD>();
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_seg_layer<Real, MAXD>, P);
+}
+
+template <typename Real, int MAXD>
+cudaError_t layer_blocks(int* per_sm) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_seg_layer<Real, MAXD>, LAYER_THREADS,
+                                                       layer_smem<Real, MAXD>());
+}
+
+static int layer_maxd(int m) { return m <= 1 ? 2 : (1 << m); }
+
+cudaError_t seg_layer_grid(int prec, int m, int sms, unsigned* grid) {
+  int per = 0;
+  const int d = layer_maxd(m);
+  cudaError_t e;
+  if (prec == 0)
+    e = d == 2 ? layer_blocks<double, 2>(&per) : d == 4 ? layer_blocks<double, 4>(&per)
+        : d == 8 ? layer_blocks<double, 8>(&per) : layer_blocks<double, 16>(&per);
+  else
+    e = d == 2 ? layer_blocks<float, 2>(&per) : d == 4 ? layer_blocks<float, 4>(&per)
+        : d == 8 ? layer_blocks<float, 8>(&per) : layer_blocks<float, 16>(&per);
+  if (e != cudaSuccess) return e;
+  if (per < 1) return cudaErrorInvalidConfiguration;
+  *grid = (unsigned)(per * sms);
+  return cudaSuccess;
+}
+
+cudaError_t launch_seg_layer(int prec, int m, const LayerParams& P, unsigned grid, cudaStream_t st) {
+  const int d = layer_maxd(m);
+  if (prec == 0)
+    return d == 2 ? layer_launch<double, 2>(P, grid, st) : d == 4 ? layer_launch<double, 4>(P, grid, st)
+           : d == 8 ? layer_launch<double, 8>(P, grid, st) : layer_launch<double, 16>(P, grid, st);
+  return d == 2 ? layer_launch<float, 2>(P, grid, st) : d == 4 ? layer_launch<float, 4>(P, grid, st)
+         : d == 8 ? layer_launch<float, 8>(P, grid, st) : layer_launch<float, 16>(P, grid, st);
+}
+
+cudaError_t layer_attrs() {
+  cudaError_t e = layer_attr<double, 2>();
+  if (e == cudaSuccess) e = layer_attr<double, 4>();
+  if (e == cudaSuccess) e = layer_attr<double, 8>();
+  if (e == cudaSuccess) e = layer_attr<double, 16>();
+  if (e == cudaSuccess) e = layer_attr<float, 2>();
+  if (e == cudaSuccess) e = layer_attr<float, 4>();
+  if (e == cudaSuccess) e = layer_attr<float, 8>();
+  if (e == cudaSuccess) e = layer_attr<float, 16>();
+  return e;
+}
+
+// ---------------------------------------------------------------- readout
+template <typename C2>
+__global__ void k_seg_probs(const C2* __restrict__ amps, uint64_t n, uint64_t* __restrict__ probs) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    probs[i] = amp_prob_bits(amps[i]);
+}
+
+void launch_seg_probs(int prec, const void* amps, uint64_t n, uint64_t* probs, cudaStream_t st) {
+  if (n == 0) return;
+  const uint64_t blocks = (n + 255) / 256;
+  const unsigned grid = (unsigned)(blocks < 148 * 8 ? blocks : 148 * 8);
+  if (prec == 0) k_seg_probs<double2><<<grid, 256, 0, st>>>((const double2*)amps, n, probs);
+  else k_seg_probs<float2><<<grid, 256, 0, st>>>((const float2*)amps, n, probs);
 }
 
 // ---------------------------------------------------------------- new terms

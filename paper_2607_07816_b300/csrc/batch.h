@@ -69,6 +69,78 @@ struct SegSel {
   double scale;
 };
 
+// ---------------------------------------------------------------- one launch per layer
+// Per-step scalars of the layer kernel, uploaded with the gate table (so a
+// captured launch reads the current step's values).
+struct LayerStep {
+  uint64_t N;      // terms in the state (removed slots' terms included)
+  uint64_t nkeep;  // terms of the slots that stay
+  int shift;       // bit of the segment rank in the sort key
+  int top;         // slots in the gate table
+  int m;           // grouping width: the widest gate of the step, at least 1
+  int pad;
+};
+
+// Phases of the layer kernel, as timed by its first block (the time from
+// one grid barrier to the next: the slowest block's work plus the barrier).
+enum LayerPhase {
+  LP_SETUP, LP_KEYS, LP_COUNTS, LP_OFFSETS, LP_SCATTER, LP_SPLITS, LP_MERGE, LP_HEADS, LP_APPLY, LP_INIT,
+  LP_PICK1, LP_HIST, LP_PICK, LP_FINISH, LP_SCALE, LP_TRUNC, LP_COUNT
+};
+
+// Control words of the layer kernel (zeroed when the handle is created).
+struct LayerCtl {
+  uint32_t bar_count, bar_gen;  // grid barrier
+  uint32_t truncated;           // 1: the step's state is in the truncation buffers
+  uint32_t unresolved;          // 1: a slot's cut was not found within LAYER_LEVELS select levels
+  uint64_t n_out;               // terms after the step
+  uint64_t t_last;              // global timer at the last barrier (first block)
+  uint64_t phase_ns[LP_COUNT];  // this step's time per phase
+};
+
+// Buffers of one layer launch.  The state moves from the input buffers to
+// the mat-vec buffers and, when a slot is cut, to the truncation buffers
+// (the input buffers again: the input is dead once the mat-vec has run).
+struct LayerParams {
+  const LayerStep* step;
+  LayerCtl* lc;
+  Ctl* ctl;
+  const uint64_t* keys_in;
+  const uint16_t* seg_in;
+  const void* amps_in;
+  uint64_t* keys_mv;
+  void* amps_mv;
+  uint64_t* probs_mv;
+  uint16_t* seg_mv;
+  uint64_t* keys_tr;
+  void* amps_tr;
+  uint16_t* seg_tr;
+  uint64_t* sk[2];
+  uint32_t* sidx[2];
+  uint32_t* heads;
+  uint32_t* hist16;
+  uint32_t* part;  // partition counts and offsets (2 * 16 * tiles words), then merge splits
+  uint64_t* lb;    // look-back words: heads, mat-vec and compaction regions in turn
+  uint64_t lb_heads_words, lb_apply_words, lb_trunc_words;
+  const SegGate* gates;
+  const uint16_t* rank_slot;
+  uint64_t* tables;
+  SegSel* sel;
+  uint32_t* sel_cnt[2];   // [slots][SEL_BINS] each (two parities: one level reads, the next clears)
+  uint64_t* sel_mass[2];  // [slots][4] each
+  uint64_t* sel_buf;
+  uint32_t* sel_bufn[2];  // [slots] each
+  uint64_t* start;  // slot bounds in the mat-vec output (start all ones for a slot with no terms)
+  uint64_t* end;
+  uint64_t* start_tr;  // slot bounds after the compaction
+  uint64_t* end_tr;
+};
+
+// Blocks of one cooperative layer launch on this device (all co-resident).
+cudaError_t seg_layer_grid(int prec, int m, int sms, unsigned* grid);
+// Enqueue the layer kernel (cooperative launch of `grid` blocks).
+cudaError_t launch_seg_layer(int prec, int m, const LayerParams& P, unsigned grid, cudaStream_t st);
+
 cudaError_t batch_prepare();  // kernel attributes of this device, before any stream capture
 void launch_seg_tables(const SegGate* gates, int slots, uint64_t* tables, cudaStream_t st);
 void launch_seg_keys(const uint64_t* keys, const uint16_t* seg, uint64_t n, const SegGate* gates,
@@ -85,25 +157,30 @@ constexpr int SEGTRUNC_CONFIGS = 2;
 void launch_seg_apply(int prec, const uint64_t* sk, const uint32_t* sidx, uint64_t n, const uint32_t* heads,
                       const void* amps_in, int shift, int mmax, const SegGate* gates, const uint16_t* rank_slot,
                       const uint64_t* tables, uint64_t* keys_out,
-                      void* amps_out, uint64_t* probs_out, uint16_t* seg_out, uint64_t* lookback, Ctl* ctl,
-                      uint64_t max_tiles, int cfg, cudaStream_t st);
+                      void* amps_out, uint64_t* probs_out, uint16_t* seg_out, uint32_t* hist1, uint64_t* start,
+                      uint64_t* end, uint64_t* lookback, Ctl* ctl, uint64_t max_tiles, int cfg, cudaStream_t st);
 // Sizes marked n_dev are read on the device (a term count written by an
 // earlier kernel on the stream); launches are sized for at most n_max terms.
-void launch_seg_bounds(const uint16_t* seg, const uint64_t* n_dev, uint64_t* start, uint64_t* end, int slots,
-                       cudaStream_t st);
 void launch_segsel_init(SegSel* sel, const SegGate* gates, const uint64_t* start, const uint64_t* end, int slots,
                         cudaStream_t st);
 constexpr int SEGSEL_CAP = 4096;  // terms per segment copied for the finish kernel
 void launch_segsel_level(const uint64_t* probs, const uint64_t* keys, const uint16_t* seg, const uint64_t* n_dev,
                          SegSel* sel, int slots, uint32_t* g_cnt, uint64_t* g_sum, uint64_t* g_buf, uint32_t* g_bufn,
                          uint32_t* err, int cfg, cudaStream_t st);
+// The first level's pick from the histogram the mat-vec counted (hist1).
+void launch_segsel_pick(SegSel* sel, int slots, const uint32_t* g_cnt, cudaStream_t st);
 void launch_segsel_finish(const uint64_t* g_buf, const uint32_t* g_bufn, const uint64_t* g_sum, SegSel* sel,
                           int slots, uint32_t* err, cudaStream_t st);
 void launch_segsel_scale(SegSel* sel, int slots, cudaStream_t st);
+// The compaction writes keys, amplitudes and slots; the probabilities of
+// the kept terms are not written (the next mat-vec computes its own, and a
+// readout first recomputes them with launch_seg_probs).
 void launch_seg_truncate(int prec, const uint64_t* keys, const void* amps, const uint64_t* probs, const uint16_t* seg,
                          const uint64_t* n_dev, uint64_t n_max, const SegSel* sel, uint64_t* keys_out,
-                         void* amps_out, uint64_t* probs_out, uint16_t* seg_out, uint64_t* lookback, Ctl* ctl,
-                         int cfg, cudaStream_t st);
+                         void* amps_out, uint16_t* seg_out, uint64_t* start, uint64_t* end, uint64_t* lookback,
+                         Ctl* ctl, int cfg, cudaStream_t st);
+// probs[i] = the probability bits of amplitude i (its own precision's formula).
+void launch_seg_probs(int prec, const void* amps, uint64_t n, uint64_t* probs, cudaStream_t st);
 void launch_seg_append(uint64_t* keys, void* amps, uint64_t* probs, uint16_t* seg, uint64_t at, int slot, int prec,
                        cudaStream_t st);
 

@@ -5,6 +5,7 @@
 #include <array>
 #include <cstdio>
 #include <map>
+#include <set>
 #include <string>
 #include <vector>
 
@@ -67,7 +68,7 @@ struct svb_state {
   uint64_t* sel_mass = nullptr;  // [max_slots][4]: total and before-bin mass (u128 each) of the collect scan
   uint64_t* sel_buf = nullptr;   // [max_slots][SEGSEL_CAP] (hi, lo) copies of a segment's cut bin
   uint32_t* sel_bufn = nullptr;
-  uint64_t* bounds_dev = nullptr;   // [2][max_slots] start, end
+  uint64_t* bounds_dev = nullptr;   // [4][max_slots]: start, end of the mat-vec output; start, end after a cut
   uint64_t* bounds_host = nullptr;
   Ctl* ctl = nullptr;
   Ctl* ctl_host = nullptr;
@@ -94,7 +95,27 @@ struct svb_state {
   bool own_stream = false;
   bool graphs_on = true;
   uint64_t gen = 0;
+  // the layer kernel: every step one persistent cooperative launch (with
+  // the gate-table upload and the readback, one graph replay)
+  bool layer_on = false;
+  int sms = 0;
+  unsigned layer_grid[5] = {};  // blocks per launch by grouping width m (0: not queried yet)
+  LayerStep* step_dev = nullptr;
+  LayerStep* step_host = nullptr;
+  LayerCtl* lc_dev = nullptr;
+  LayerCtl* lc_host = nullptr;
+  uint32_t* sel_cnt2 = nullptr;   // second parity of the select histograms
+  uint64_t* sel_mass2 = nullptr;
+  uint32_t* sel_bufn2 = nullptr;
+  uint32_t* layer_part = nullptr;  // partition counts and offsets, merge splits
+  uint64_t layer_part_words = 0;
+  uint64_t* layer_lb = nullptr;    // look-backs of the heads, the mat-vec and the compaction
+  uint64_t layer_lb_heads = 0, layer_lb_apply = 0, layer_lb_trunc = 0;
+  uint64_t layer_launches = 0;
+  double layer_ms[LP_COUNT] = {};  // time per phase of the layer kernel, summed over the steps
+
   std::map<std::array<uint64_t, 12>, cudaGraphExec_t> graphs;
+  std::set<std::array<uint64_t, 12>> seen_keys;  // keys enqueued once without a graph
   uint64_t graph_launches = 0, graph_captures = 0;
 };
 
@@ -226,6 +247,36 @@ sv_status b_sort_cap(svb_state* b, uint64_t need) {
   return b_lookback(b, sort_tiles(need) * RADIX + 16);
 }
 
+// Scratch of the layer kernel for N terms in (nkeep of them in slots that
+// stay) and gates of up to 2^mmax outputs per group.
+sv_status b_layer_cap(svb_state* b, uint64_t N, uint64_t nkeep, int mmax) {
+  const uint64_t tiles = N / 4096 + 2;
+  const uint64_t part = 2 * 16 * tiles + 64;
+  if (part > b->layer_part_words) {
+    const uint64_t want = part + part / 2;
+    uint32_t* p = (uint32_t*)b_alloc(b, want * 4);
+    if (!p) return b_fail(b, SV_E_NOMEM, "layer scratch allocation failed");
+    b_free(b, b->layer_part);
+    b->layer_part = p;
+    b->layer_part_words = want;
+    ++b->gen;
+  }
+  const uint64_t heads = nkeep / 4096 + 2, apply = nkeep / 256 + 2, trunc = (nkeep << mmax) / 2048 + 2;
+  if (heads > b->layer_lb_heads || apply > b->layer_lb_apply || trunc > b->layer_lb_trunc) {
+    const uint64_t h = std::max(heads + heads / 2, b->layer_lb_heads), a = std::max(apply + apply / 2, b->layer_lb_apply),
+                   t = std::max(trunc + trunc / 2, b->layer_lb_trunc);
+    uint64_t* p = (uint64_t*)b_alloc(b, (h + a + t) * 8);
+    if (!p) return b_fail(b, SV_E_NOMEM, "layer look-back allocation failed");
+    b_free(b, b->layer_lb);
+    b->layer_lb = p;
+    b->layer_lb_heads = h;
+    b->layer_lb_apply = a;
+    b->layer_lb_trunc = t;
+    ++b->gen;
+  }
+  return SV_OK;
+}
+
 enum TuneKernel { TK_APPLY = 0, TK_SELECT = 1, TK_TRUNC = 2 };
 
 uint64_t tune_key(int kernel, int prec, int mmax, uint64_t n) {
@@ -268,13 +319,22 @@ void drop_graphs(svb_state* b) {
 }
 
 // Enqueue one part of a step: replay its graph when one was captured under
-// the same key, else capture it now (the first time) or, with graphs off or
-// unavailable, enqueue the launches directly.
+// the same key, capture it when the key comes a second time, else (a key
+// seen once, or graphs off or unavailable) enqueue the launches directly.
+// Keys that never repeat (term counts change while states grow and
+// circuits retire) so cost no capture and instantiation.
 template <typename F>
 sv_status run_part(svb_state* b, bool use_graph, const std::array<uint64_t, 12>& key, F&& enqueue) {
   if (!(use_graph && b->graphs_on)) return enqueue();
   auto it = b->graphs.find(key);
   if (it == b->graphs.end()) {
+    if (b->seen_keys.insert(key).second) {
+      if (b->seen_keys.size() > 4096) {
+        b->seen_keys.clear();
+        b->seen_keys.insert(key);
+      }
+      return enqueue();
+    }
     if (b->graphs.size() >= 64) drop_graphs(b);
     if (cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
       cudaGetLastError();
@@ -288,8 +348,8 @@ sv_status run_part(svb_state* b, bool use_graph, const std::array<uint64_t, 12>&
     if (rc != SV_OK || e != cudaSuccess || cudaGraphInstantiate(&x, g, 0) != cudaSuccess) {
       if (g) cudaGraphDestroy(g);
       cudaGetLastError();
-      b->graphs_on = false;  // run this and later steps without graphs
-      return rc != SV_OK ? rc : enqueue();
+      b->graphs_on = false;  // run this and later steps without graphs (nothing captured has run)
+      return enqueue();
     }
     cudaGraphDestroy(g);
     it = b->graphs.emplace(key, x).first;
@@ -339,6 +399,254 @@ void tune_record(svb_state* b, uint64_t key, int shapes, int shape, float ms) {
 
 }  // namespace
 
+// The step as separate kernels (two enqueued parts, each replayed as a CUDA
+// graph once its shapes are settled, and a host wait after each).
+static sv_status step_kernels(svb_state* b, int top, uint64_t N, uint64_t nkeep, int shift, int nbits, int mmax,
+                       bool may_truncate, bool& truncated) {
+  sv_status rc = SV_OK;
+  const uint64_t apply_tiles = nkeep / 256 + 2;  // one group per thread: the most tiles of any shape
+  if (rc == SV_OK) rc = b_lookback(b, apply_tiles + 16);
+  if (rc != SV_OK) return rc;
+  const uint64_t n_cand = nkeep << mmax;  // the most candidates the mat-vec can emit
+  if (may_truncate) rc = b_lookback(b, std::max(apply_tiles, n_cand / 2048 + 2) + 16);
+  if (rc != SV_OK) return rc;
+  // The step is enqueued with device-side term counts in two parts (each
+  // replayed as a CUDA graph once its shapes are settled); the host waits
+  // after each: to confirm every segment's cut is resolved, and for the new
+  // counts.
+  const int alt = 1 - b->cur;
+  uint64_t* start_dev = b->bounds_dev;
+  uint64_t* end_dev = b->bounds_dev + b->max_slots;
+  uint64_t* start_tr = b->bounds_dev + 2 * b->max_slots;
+  uint64_t* end_tr = b->bounds_dev + 3 * b->max_slots;
+  const uint64_t key_apply = tune_key(TK_APPLY, b->prec, mmax, nkeep);
+  const uint64_t key_sel = tune_key(TK_SELECT, b->prec, mmax, n_cand);
+  const uint64_t key_trunc = tune_key(TK_TRUNC, b->prec, mmax, n_cand);
+  const int n_apply = seg_apply_configs(mmax);
+  const int cfg_apply = tune_pick(b, key_apply, n_apply, mmax == 2 ? 1 : 0);
+  const int cfg_sel = may_truncate ? tune_pick(b, key_sel, SEGSEL_CONFIGS, 1) : -1;
+  const int cfg_trunc = may_truncate ? tune_pick(b, key_trunc, SEGTRUNC_CONFIGS, 1) : -1;
+  const bool settled = tune_settled(b, key_apply, n_apply) &&
+                       (!may_truncate || (tune_settled(b, key_sel, SEGSEL_CONFIGS) &&
+                                          tune_settled(b, key_trunc, SEGTRUNC_CONFIGS)));
+  const bool timing = b->autotune && !settled;  // events only while shapes are explored
+  std::array<uint64_t, 12> key_a = {0, N, nkeep, (uint64_t)top, (uint64_t)shift, (uint64_t)nbits, (uint64_t)mmax,
+                                    (uint64_t)cfg_apply, (uint64_t)(cfg_sel + 1), (uint64_t)b->cur, b->gen,
+                                    (uint64_t)may_truncate};
+  rc = run_part(b, settled, key_a, [&]() -> sv_status {
+    cudaMemcpyAsync(b->gates_dev, b->gates_host, sizeof(SegGate) * top, cudaMemcpyHostToDevice, b->st);
+    cudaMemcpyAsync(b->rank_slot_dev, b->rank_slot_host, sizeof(uint16_t) * top, cudaMemcpyHostToDevice, b->st);
+    // grouping: every segment is sorted by its previous order, so the terms
+    // with equal low M bits of the new sort key are already sorted by it: a
+    // stable partition by those bits and M merge levels sort the batch
+    launch_seg_tables(b->gates_dev, top, b->tables_dev, b->st);
+    launch_seg_keys(b->keys[b->cur], b->seg[b->cur], N, b->gates_dev, b->tables_dev, shift, b->sk[1], b->st);
+    cudaMemsetAsync(b->hist, 0, sizeof(uint32_t) * 16, b->st);  // the partition's run totals
+    SortScratch sc;
+    sc.hist = b->hist;
+    sc.hist_host = nullptr;
+    sc.lookback = b->lookback;
+    sc.lookback_tiles = b->lb_entries / RADIX;
+    sc.tile_counter = b->tile_counter;
+    sc.err = &b->ctl->err;
+    GateParams gp;
+    std::memset(&gp, 0, sizeof(gp));
+    gp.m = mmax > 1 ? mmax : 1;
+    gp.direct = 1;
+    cudaError_t ce;
+    int nl = 0;
+    const int w = regroup_terms(b->sk[1], N, gp, b->sk, b->sidx, sc, b->st, &nl, &ce);
+    if (ce != cudaSuccess) return b_cuda(b, ce, "svb_step grouping");
+    launch_seg_heads(b->sk[w], nkeep, shift, b->gates_dev, b->rank_slot_dev, b->heads, b->lookback, b->ctl, b->st);
+    // the mat-vec counts the select's first digit per slot when a cut may
+    // follow, and records where each slot's outputs start and end
+    if (may_truncate) cudaMemsetAsync(b->sel_cnt, 0, sizeof(uint32_t) * SEL_BINS * top, b->st);
+    cudaMemsetAsync(start_dev, 0xff, sizeof(uint64_t) * b->max_slots, b->st);
+    cudaMemsetAsync(end_dev, 0, sizeof(uint64_t) * b->max_slots, b->st);
+    if (timing) cudaEventRecord(b->tev[TK_APPLY][0], b->st);
+    launch_seg_apply(b->prec, b->sk[w], b->sidx[w], nkeep, b->heads, b->amps[b->cur], shift, mmax, b->gates_dev,
+                     b->rank_slot_dev, b->tables_dev,
+                     b->keys[alt], b->amps[alt], b->probs[alt], b->seg[alt], may_truncate ? b->sel_cnt : nullptr,
+                     start_dev, end_dev, b->lookback, b->ctl, apply_tiles, cfg_apply, b->st);
+    if (timing) cudaEventRecord(b->tev[TK_APPLY][1], b->st);
+    if (may_truncate) {
+      // per-segment top-k: three levels normally resolve every cut
+      // (exponent bin, top mantissa bin, the copied bin); the first one's
+      // histogram came with the mat-vec, so two scans follow its pick
+      launch_segsel_init(b->sel_dev, b->gates_dev, start_dev, end_dev, top, b->st);
+      if (timing) cudaEventRecord(b->tev[TK_SELECT][0], b->st);
+      launch_segsel_pick(b->sel_dev, top, b->sel_cnt, b->st);
+      for (int level = 1; level < 3; ++level) {
+        launch_segsel_level(b->probs[alt], b->keys[alt], b->seg[alt], &b->ctl->count[1], b->sel_dev, top, b->sel_cnt,
+                            b->sel_mass, b->sel_buf, b->sel_bufn, &b->ctl->err, cfg_sel, b->st);
+        launch_segsel_finish(b->sel_buf, b->sel_bufn, b->sel_mass, b->sel_dev, top, &b->ctl->err, b->st);
+      }
+      if (timing) cudaEventRecord(b->tev[TK_SELECT][1], b->st);
+      cudaMemcpyAsync(b->sel_host, b->sel_dev, sizeof(SegSel) * top, cudaMemcpyDeviceToHost, b->st);
+    } else {
+      cudaMemcpyAsync(b->bounds_host, b->bounds_dev, sizeof(uint64_t) * 4 * b->max_slots, cudaMemcpyDeviceToHost,
+                      b->st);
+    }
+    cudaMemcpyAsync(b->ctl_host, b->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, b->st);
+    return SV_OK;
+  });
+  if (rc != SV_OK) return rc;
+  rc = b_wait(b, "svb_step");
+  if (rc != SV_OK) return rc;
+  for (int s = 0; s < b->max_slots; ++s)
+    if (b->slots[s].state == SLOT_REMOVING) b->slots[s] = Slot();
+  b->cur = alt;
+  if (may_truncate) {
+    // rarely a cut needs more levels (long runs of equal probabilities)
+    bool all_done = false;
+    for (int extra = 0;; ++extra) {
+      all_done = true;
+      for (int s = 0; s < top; ++s)
+        if (b->sel_host[s].active && !b->sel_host[s].done) all_done = false;
+      if (all_done || extra >= 13) break;
+      launch_segsel_level(b->probs[b->cur], b->keys[b->cur], b->seg[b->cur], &b->ctl->count[1], b->sel_dev, top,
+                          b->sel_cnt, b->sel_mass, b->sel_buf, b->sel_bufn, &b->ctl->err, cfg_sel, b->st);
+      launch_segsel_finish(b->sel_buf, b->sel_bufn, b->sel_mass, b->sel_dev, top, &b->ctl->err, b->st);
+      cudaMemcpyAsync(b->sel_host, b->sel_dev, sizeof(SegSel) * top, cudaMemcpyDeviceToHost, b->st);
+      rc = b_sync_ctl(b, "svb_step select");
+      if (rc != SV_OK) return rc;
+    }
+    if (!all_done) {
+      b->broken = true;
+      return b_fail(b, SV_E_STATE, "svb_step: segmented select did not resolve");
+    }
+    for (int s = 0; s < top; ++s)
+      if (b->sel_host[s].active && b->sel_host[s].done == 1) truncated = true;
+    const int alt2 = 1 - b->cur;
+    std::array<uint64_t, 12> key_b = {1, N, nkeep, (uint64_t)top, n_cand, (uint64_t)truncated, (uint64_t)mmax,
+                                      (uint64_t)cfg_trunc, 0, (uint64_t)b->cur, b->gen, 0};
+    rc = run_part(b, settled, key_b, [&]() -> sv_status {
+      if (truncated) {
+        launch_segsel_scale(b->sel_dev, top, b->st);
+        cudaMemsetAsync(start_tr, 0xff, sizeof(uint64_t) * b->max_slots, b->st);
+        cudaMemsetAsync(end_tr, 0, sizeof(uint64_t) * b->max_slots, b->st);
+        if (timing) cudaEventRecord(b->tev[TK_TRUNC][0], b->st);
+        launch_seg_truncate(b->prec, b->keys[b->cur], b->amps[b->cur], b->probs[b->cur], b->seg[b->cur],
+                            &b->ctl->count[1], n_cand, b->sel_dev, b->keys[alt2], b->amps[alt2], b->seg[alt2],
+                            start_tr, end_tr, b->lookback, b->ctl, cfg_trunc, b->st);
+        if (timing) cudaEventRecord(b->tev[TK_TRUNC][1], b->st);
+      }
+      cudaMemcpyAsync(b->bounds_host, b->bounds_dev, sizeof(uint64_t) * 4 * b->max_slots, cudaMemcpyDeviceToHost,
+                      b->st);
+      cudaMemcpyAsync(b->ctl_host, b->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, b->st);
+      return SV_OK;
+    });
+    if (rc != SV_OK) return rc;
+    rc = b_wait(b, "svb_step truncate");
+    if (rc != SV_OK) return rc;
+    if (truncated) b->cur = alt2;
+  }
+  b->N = truncated ? b->ctl_host->count[2] : b->ctl_host->count[1];
+  if (timing) {  // the stream is idle: every recorded interval is complete
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, b->tev[TK_APPLY][0], b->tev[TK_APPLY][1]) == cudaSuccess)
+      tune_record(b, key_apply, n_apply, cfg_apply, ms);
+    if (cfg_sel >= 0 && cudaEventElapsedTime(&ms, b->tev[TK_SELECT][0], b->tev[TK_SELECT][1]) == cudaSuccess)
+      tune_record(b, key_sel, SEGSEL_CONFIGS, cfg_sel, ms);
+    if (truncated && cudaEventElapsedTime(&ms, b->tev[TK_TRUNC][0], b->tev[TK_TRUNC][1]) == cudaSuccess)
+      tune_record(b, key_trunc, SEGTRUNC_CONFIGS, cfg_trunc, ms);
+    cudaGetLastError();
+  }
+  return SV_OK;
+}
+
+// The step as one persistent launch of the layer kernel (one graph replay:
+// the table upload, the launch and the readback), one host wait.
+static sv_status step_layer(svb_state* b, int top, uint64_t N, uint64_t nkeep, int shift, int mmax, bool& truncated) {
+  const int m = mmax > 1 ? mmax : 1;
+  sv_status rc = b_layer_cap(b, N, nkeep, m);
+  if (rc != SV_OK) return rc;
+  if (!b->layer_grid[m]) {
+    unsigned g = 0;
+    rc = b_cuda(b, seg_layer_grid(b->prec, m, b->sms, &g), "svb_step layer occupancy");
+    if (rc != SV_OK) return rc;
+    b->layer_grid[m] = g;
+  }
+  const unsigned grid = b->layer_grid[m];
+  b->step_host->N = N;
+  b->step_host->nkeep = nkeep;
+  b->step_host->shift = shift;
+  b->step_host->top = top;
+  b->step_host->m = m;
+  b->step_host->pad = 0;
+  const int cur = b->cur, alt = 1 - cur;
+  LayerParams P;
+  std::memset(&P, 0, sizeof(P));
+  P.step = b->step_dev;
+  P.lc = b->lc_dev;
+  P.ctl = b->ctl;
+  P.keys_in = b->keys[cur];
+  P.seg_in = b->seg[cur];
+  P.amps_in = b->amps[cur];
+  P.keys_mv = b->keys[alt];
+  P.amps_mv = b->amps[alt];
+  P.probs_mv = b->probs[alt];
+  P.seg_mv = b->seg[alt];
+  P.keys_tr = b->keys[cur];
+  P.amps_tr = b->amps[cur];
+  P.seg_tr = b->seg[cur];
+  for (int i = 0; i < 2; ++i) {
+    P.sk[i] = b->sk[i];
+    P.sidx[i] = b->sidx[i];
+  }
+  P.heads = b->heads;
+  P.hist16 = b->hist;
+  P.part = b->layer_part;
+  P.lb = b->layer_lb;
+  P.lb_heads_words = b->layer_lb_heads;
+  P.lb_apply_words = b->layer_lb_apply;
+  P.lb_trunc_words = b->layer_lb_trunc;
+  P.gates = b->gates_dev;
+  P.rank_slot = b->rank_slot_dev;
+  P.tables = b->tables_dev;
+  P.sel = b->sel_dev;
+  P.sel_cnt[0] = b->sel_cnt;
+  P.sel_cnt[1] = b->sel_cnt2;
+  P.sel_mass[0] = b->sel_mass;
+  P.sel_mass[1] = b->sel_mass2;
+  P.sel_buf = b->sel_buf;
+  P.sel_bufn[0] = b->sel_bufn;
+  P.sel_bufn[1] = b->sel_bufn2;
+  P.start = b->bounds_dev;
+  P.end = b->bounds_dev + b->max_slots;
+  P.start_tr = b->bounds_dev + 2 * b->max_slots;
+  P.end_tr = b->bounds_dev + 3 * b->max_slots;
+  const std::array<uint64_t, 12> key = {2, (uint64_t)top, (uint64_t)m, (uint64_t)cur, b->gen, grid, 0, 0, 0, 0, 0, 0};
+  rc = run_part(b, true, key, [&]() -> sv_status {
+    cudaMemcpyAsync(b->gates_dev, b->gates_host, sizeof(SegGate) * top, cudaMemcpyHostToDevice, b->st);
+    cudaMemcpyAsync(b->rank_slot_dev, b->rank_slot_host, sizeof(uint16_t) * top, cudaMemcpyHostToDevice, b->st);
+    cudaMemcpyAsync(b->step_dev, b->step_host, sizeof(LayerStep), cudaMemcpyHostToDevice, b->st);
+    const cudaError_t e = launch_seg_layer(b->prec, m, P, grid, b->st);
+    if (e != cudaSuccess) return b_cuda(b, e, "svb_step layer launch");
+    cudaMemcpyAsync(b->ctl_host, b->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, b->st);
+    cudaMemcpyAsync(b->lc_host, b->lc_dev, sizeof(LayerCtl), cudaMemcpyDeviceToHost, b->st);
+    cudaMemcpyAsync(b->bounds_host, b->bounds_dev, sizeof(uint64_t) * 4 * b->max_slots, cudaMemcpyDeviceToHost,
+                    b->st);
+    cudaMemcpyAsync(b->sel_host, b->sel_dev, sizeof(SegSel) * top, cudaMemcpyDeviceToHost, b->st);
+    return SV_OK;
+  });
+  if (rc != SV_OK) return rc;
+  rc = b_wait(b, "svb_step");
+  if (rc != SV_OK) return rc;
+  ++b->layer_launches;
+  for (int i = 0; i < LP_COUNT; ++i) b->layer_ms[i] += 1e-6 * (double)b->lc_host->phase_ns[i];
+  if (b->lc_host->unresolved) {
+    b->broken = true;
+    return b_fail(b, SV_E_STATE, "svb_step: segmented select did not resolve");
+  }
+  for (int s = 0; s < b->max_slots; ++s)
+    if (b->slots[s].state == SLOT_REMOVING) b->slots[s] = Slot();
+  truncated = b->lc_host->truncated != 0;
+  if (!truncated) b->cur = alt;
+  b->N = b->lc_host->n_out;
+  return SV_OK;
+}
+
 extern "C" {
 
 sv_status svb_destroy(svb_state* b);
@@ -382,7 +690,13 @@ sv_status svb_create(int max_slots, int prec, void* cuda_stream, const sv_alloca
   b->sel_mass = (uint64_t*)b_alloc(b, sizeof(uint64_t) * 4 * max_slots);
   b->sel_buf = (uint64_t*)b_alloc(b, sizeof(uint64_t) * 2 * SEGSEL_CAP * max_slots);
   b->sel_bufn = (uint32_t*)b_alloc(b, sizeof(uint32_t) * max_slots);
-  b->bounds_dev = (uint64_t*)b_alloc(b, sizeof(uint64_t) * 2 * max_slots);
+  b->bounds_dev = (uint64_t*)b_alloc(b, sizeof(uint64_t) * 4 * max_slots);
+  b->sel_cnt2 = (uint32_t*)b_alloc(b, sizeof(uint32_t) * SEL_BINS * max_slots);
+  b->sel_mass2 = (uint64_t*)b_alloc(b, sizeof(uint64_t) * 4 * max_slots);
+  b->sel_bufn2 = (uint32_t*)b_alloc(b, sizeof(uint32_t) * max_slots);
+  b->step_dev = (LayerStep*)b_alloc(b, sizeof(LayerStep));
+  b->lc_dev = (LayerCtl*)b_alloc(b, sizeof(LayerCtl));
+  if (!b->sel_cnt2 || !b->sel_mass2 || !b->sel_bufn2 || !b->step_dev || !b->lc_dev) rc = SV_E_NOMEM;
   if (!b->hist || !b->tile_counter || !b->ctl || !b->gates_dev || !b->tables_dev || !b->rank_slot_dev ||
       !b->sel_dev || !b->sel_cnt ||
       !b->sel_mass ||
@@ -393,14 +707,24 @@ sv_status svb_create(int max_slots, int prec, void* cuda_stream, const sv_alloca
                       cudaMallocHost(&b->gates_host, sizeof(SegGate) * max_slots) != cudaSuccess ||
                       cudaMallocHost(&b->rank_slot_host, sizeof(uint16_t) * max_slots) != cudaSuccess ||
                       cudaMallocHost(&b->sel_host, sizeof(SegSel) * max_slots) != cudaSuccess ||
-                      cudaMallocHost(&b->bounds_host, sizeof(uint64_t) * 2 * max_slots) != cudaSuccess))
+                      cudaMallocHost(&b->bounds_host, sizeof(uint64_t) * 4 * max_slots) != cudaSuccess ||
+                      cudaMallocHost(&b->step_host, sizeof(LayerStep)) != cudaSuccess ||
+                      cudaMallocHost(&b->lc_host, sizeof(LayerCtl)) != cudaSuccess))
     rc = SV_E_CUDA;
+  if (rc == SV_OK) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      rc = SV_E_CUDA;
+  }
   for (int k = 0; k < 3 && rc == SV_OK; ++k)
     for (int j = 0; j < 2 && rc == SV_OK; ++j)
       if (cudaEventCreate(&b->tev[k][j]) != cudaSuccess) rc = SV_E_CUDA;
   if (rc == SV_OK) rc = b_state_cap(b, 4096);
   if (rc == SV_OK) rc = b_sort_cap(b, 4096);
   if (rc == SV_OK) rc = b_cuda(b, cudaMemsetAsync(b->ctl, 0, sizeof(Ctl), b->st), "svb_create");
+  if (rc == SV_OK) rc = b_cuda(b, cudaMemsetAsync(b->lc_dev, 0, sizeof(LayerCtl), b->st), "svb_create");
+  if (rc == SV_OK) rc = b_cuda(b, cudaStreamSynchronize(b->st), "svb_create");
   if (rc != SV_OK) {
     svb_destroy(b);
     return rc;
@@ -435,6 +759,13 @@ sv_status svb_destroy(svb_state* b) {
   b_free(b, b->sel_buf);
   b_free(b, b->sel_bufn);
   b_free(b, b->bounds_dev);
+  b_free(b, b->sel_cnt2);
+  b_free(b, b->sel_mass2);
+  b_free(b, b->sel_bufn2);
+  b_free(b, b->step_dev);
+  b_free(b, b->lc_dev);
+  b_free(b, b->layer_part);
+  b_free(b, b->layer_lb);
   for (int k = 0; k < 3; ++k)
     for (int j = 0; j < 2; ++j)
       if (b->tev[k][j]) cudaEventDestroy(b->tev[k][j]);
@@ -446,6 +777,8 @@ sv_status svb_destroy(svb_state* b) {
   if (b->rank_slot_host) cudaFreeHost(b->rank_slot_host);
   if (b->sel_host) cudaFreeHost(b->sel_host);
   if (b->bounds_host) cudaFreeHost(b->bounds_host);
+  if (b->step_host) cudaFreeHost(b->step_host);
+  if (b->lc_host) cudaFreeHost(b->lc_host);
   delete b;
   return SV_OK;
 }
@@ -606,154 +939,20 @@ sv_status svb_step(svb_state* b, const svb_gate* gates, int count) {
   const int nbits = shift + segbits;
   sv_status rc = b_state_cap(b, nkeep << mmax > N ? nkeep << mmax : N);
   if (rc == SV_OK) rc = b_sort_cap(b, N);
-  const uint64_t apply_tiles = nkeep / 256 + 2;  // one group per thread: the most tiles of any shape
-  if (rc == SV_OK) rc = b_lookback(b, apply_tiles + 16);
   if (rc != SV_OK) return rc;
-  const uint64_t n_cand = nkeep << mmax;  // the most candidates the mat-vec can emit
-  if (may_truncate) rc = b_lookback(b, std::max(apply_tiles, n_cand / 2048 + 2) + 16);
-  if (rc != SV_OK) return rc;
-  // The step is enqueued with device-side term counts in two parts (each
-  // replayed as a CUDA graph once its shapes are settled); the host waits
-  // after each: to confirm every segment's cut is resolved, and for the new
-  // counts.
-  const int alt = 1 - b->cur;
-  uint64_t* start_dev = b->bounds_dev;
-  uint64_t* end_dev = b->bounds_dev + b->max_slots;
-  const uint64_t key_apply = tune_key(TK_APPLY, b->prec, mmax, nkeep);
-  const uint64_t key_sel = tune_key(TK_SELECT, b->prec, mmax, n_cand);
-  const uint64_t key_trunc = tune_key(TK_TRUNC, b->prec, mmax, n_cand);
-  const int n_apply = seg_apply_configs(mmax);
-  const int cfg_apply = tune_pick(b, key_apply, n_apply, mmax == 2 ? 1 : 0);
-  const int cfg_sel = may_truncate ? tune_pick(b, key_sel, SEGSEL_CONFIGS, 1) : -1;
-  const int cfg_trunc = may_truncate ? tune_pick(b, key_trunc, SEGTRUNC_CONFIGS, 1) : -1;
-  const bool settled = tune_settled(b, key_apply, n_apply) &&
-                       (!may_truncate || (tune_settled(b, key_sel, SEGSEL_CONFIGS) &&
-                                          tune_settled(b, key_trunc, SEGTRUNC_CONFIGS)));
-  const bool timing = b->autotune && !settled;  // events only while shapes are explored
-  std::array<uint64_t, 12> key_a = {0, N, nkeep, (uint64_t)top, (uint64_t)shift, (uint64_t)nbits, (uint64_t)mmax,
-                                    (uint64_t)cfg_apply, (uint64_t)(cfg_sel + 1), (uint64_t)b->cur, b->gen,
-                                    (uint64_t)may_truncate};
-  rc = run_part(b, settled, key_a, [&]() -> sv_status {
-    cudaMemcpyAsync(b->gates_dev, b->gates_host, sizeof(SegGate) * top, cudaMemcpyHostToDevice, b->st);
-    cudaMemcpyAsync(b->rank_slot_dev, b->rank_slot_host, sizeof(uint16_t) * top, cudaMemcpyHostToDevice, b->st);
-    // grouping: every segment is sorted by its previous order, so the terms
-    // with equal low M bits of the new sort key are already sorted by it: a
-    // stable partition by those bits and M merge levels sort the batch
-    launch_seg_tables(b->gates_dev, top, b->tables_dev, b->st);
-    launch_seg_keys(b->keys[b->cur], b->seg[b->cur], N, b->gates_dev, b->tables_dev, shift, b->sk[1], b->st);
-    cudaMemsetAsync(b->hist, 0, sizeof(uint32_t) * 16, b->st);  // the partition's run totals
-    SortScratch sc;
-    sc.hist = b->hist;
-    sc.hist_host = nullptr;
-    sc.lookback = b->lookback;
-    sc.lookback_tiles = b->lb_entries / RADIX;
-    sc.tile_counter = b->tile_counter;
-    sc.err = &b->ctl->err;
-    GateParams gp;
-    std::memset(&gp, 0, sizeof(gp));
-    gp.m = mmax > 1 ? mmax : 1;
-    gp.direct = 1;
-    cudaError_t ce;
-    int nl = 0;
-    const int w = regroup_terms(b->sk[1], N, gp, b->sk, b->sidx, sc, b->st, &nl, &ce);
-    if (ce != cudaSuccess) return b_cuda(b, ce, "svb_step grouping");
-    launch_seg_heads(b->sk[w], nkeep, shift, b->gates_dev, b->rank_slot_dev, b->heads, b->lookback, b->ctl, b->st);
-    if (timing) cudaEventRecord(b->tev[TK_APPLY][0], b->st);
-    launch_seg_apply(b->prec, b->sk[w], b->sidx[w], nkeep, b->heads, b->amps[b->cur], shift, mmax, b->gates_dev,
-                     b->rank_slot_dev, b->tables_dev,
-                     b->keys[alt], b->amps[alt], b->probs[alt], b->seg[alt], b->lookback, b->ctl, apply_tiles,
-                     cfg_apply, b->st);
-    if (timing) cudaEventRecord(b->tev[TK_APPLY][1], b->st);
-    launch_seg_bounds(b->seg[alt], &b->ctl->count[1], start_dev, end_dev, top, b->st);
-    if (may_truncate) {
-      // per-segment top-k: three levels normally resolve every cut
-      // (exponent bin, top mantissa bin, the copied bin)
-      launch_segsel_init(b->sel_dev, b->gates_dev, start_dev, end_dev, top, b->st);
-      if (timing) cudaEventRecord(b->tev[TK_SELECT][0], b->st);
-      for (int level = 0; level < 3; ++level) {
-        launch_segsel_level(b->probs[alt], b->keys[alt], b->seg[alt], &b->ctl->count[1], b->sel_dev, top, b->sel_cnt,
-                            b->sel_mass, b->sel_buf, b->sel_bufn, &b->ctl->err, cfg_sel, b->st);
-        launch_segsel_finish(b->sel_buf, b->sel_bufn, b->sel_mass, b->sel_dev, top, &b->ctl->err, b->st);
-      }
-      if (timing) cudaEventRecord(b->tev[TK_SELECT][1], b->st);
-      cudaMemcpyAsync(b->sel_host, b->sel_dev, sizeof(SegSel) * top, cudaMemcpyDeviceToHost, b->st);
-    } else {
-      cudaMemcpyAsync(b->bounds_host, b->bounds_dev, sizeof(uint64_t) * 2 * b->max_slots, cudaMemcpyDeviceToHost,
-                      b->st);
-    }
-    cudaMemcpyAsync(b->ctl_host, b->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, b->st);
-    return SV_OK;
-  });
-  if (rc != SV_OK) return rc;
-  rc = b_wait(b, "svb_step");
-  if (rc != SV_OK) return rc;
-  for (int s = 0; s < b->max_slots; ++s)
-    if (b->slots[s].state == SLOT_REMOVING) b->slots[s] = Slot();
-  b->cur = alt;
   bool truncated = false;
-  if (may_truncate) {
-    // rarely a cut needs more levels (long runs of equal probabilities)
-    bool all_done = false;
-    for (int extra = 0;; ++extra) {
-      all_done = true;
-      for (int s = 0; s < top; ++s)
-        if (b->sel_host[s].active && !b->sel_host[s].done) all_done = false;
-      if (all_done || extra >= 13) break;
-      launch_segsel_level(b->probs[b->cur], b->keys[b->cur], b->seg[b->cur], &b->ctl->count[1], b->sel_dev, top,
-                          b->sel_cnt, b->sel_mass, b->sel_buf, b->sel_bufn, &b->ctl->err, cfg_sel, b->st);
-      launch_segsel_finish(b->sel_buf, b->sel_bufn, b->sel_mass, b->sel_dev, top, &b->ctl->err, b->st);
-      cudaMemcpyAsync(b->sel_host, b->sel_dev, sizeof(SegSel) * top, cudaMemcpyDeviceToHost, b->st);
-      rc = b_sync_ctl(b, "svb_step select");
-      if (rc != SV_OK) return rc;
-    }
-    if (!all_done) {
-      b->broken = true;
-      return b_fail(b, SV_E_STATE, "svb_step: segmented select did not resolve");
-    }
-    for (int s = 0; s < top; ++s)
-      if (b->sel_host[s].active && b->sel_host[s].done == 1) truncated = true;
-    const int alt2 = 1 - b->cur;
-    std::array<uint64_t, 12> key_b = {1, N, nkeep, (uint64_t)top, n_cand, (uint64_t)truncated, (uint64_t)mmax,
-                                      (uint64_t)cfg_trunc, 0, (uint64_t)b->cur, b->gen, 0};
-    rc = run_part(b, settled, key_b, [&]() -> sv_status {
-      if (truncated) {
-        launch_segsel_scale(b->sel_dev, top, b->st);
-        if (timing) cudaEventRecord(b->tev[TK_TRUNC][0], b->st);
-        launch_seg_truncate(b->prec, b->keys[b->cur], b->amps[b->cur], b->probs[b->cur], b->seg[b->cur],
-                            &b->ctl->count[1], n_cand, b->sel_dev, b->keys[alt2], b->amps[alt2], b->probs[alt2],
-                            b->seg[alt2], b->lookback, b->ctl, cfg_trunc, b->st);
-        if (timing) cudaEventRecord(b->tev[TK_TRUNC][1], b->st);
-        launch_seg_bounds(b->seg[alt2], &b->ctl->count[2], start_dev, end_dev, top, b->st);
-      }
-      cudaMemcpyAsync(b->bounds_host, b->bounds_dev, sizeof(uint64_t) * 2 * b->max_slots, cudaMemcpyDeviceToHost,
-                      b->st);
-      cudaMemcpyAsync(b->ctl_host, b->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, b->st);
-      return SV_OK;
-    });
-    if (rc != SV_OK) return rc;
-    rc = b_wait(b, "svb_step truncate");
-    if (rc != SV_OK) return rc;
-    if (truncated) b->cur = alt2;
-  }
-  b->N = truncated ? b->ctl_host->count[2] : b->ctl_host->count[1];
-  if (timing) {  // the stream is idle: every recorded interval is complete
-    float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, b->tev[TK_APPLY][0], b->tev[TK_APPLY][1]) == cudaSuccess)
-      tune_record(b, key_apply, n_apply, cfg_apply, ms);
-    if (cfg_sel >= 0 && cudaEventElapsedTime(&ms, b->tev[TK_SELECT][0], b->tev[TK_SELECT][1]) == cudaSuccess)
-      tune_record(b, key_sel, SEGSEL_CONFIGS, cfg_sel, ms);
-    if (truncated && cudaEventElapsedTime(&ms, b->tev[TK_TRUNC][0], b->tev[TK_TRUNC][1]) == cudaSuccess)
-      tune_record(b, key_trunc, SEGTRUNC_CONFIGS, cfg_trunc, ms);
-    cudaGetLastError();
-  }
+  rc = b->layer_on ? step_layer(b, top, N, nkeep, shift, mmax, truncated)
+                   : step_kernels(b, top, N, nkeep, shift, nbits, mmax, may_truncate, truncated);
+  if (rc != SV_OK) return rc;
   for (int s = 0; s < b->max_slots; ++s) {
     Slot& sl = b->slots[s];
     if (sl.state != SLOT_USED) continue;
     if (s < top)  // the segment is now sorted by this step's order
       for (int q = 0; q < sl.n; ++q) sl.order[q] = b->gates_host[s].pos[q];
     if (s < top) {
-      const uint64_t a = b->bounds_host[s], e = b->bounds_host[b->max_slots + s];
-      sl.offset = a;
+      const uint64_t* bh = b->bounds_host + (truncated ? 2 * b->max_slots : 0);  // the state's bounds
+      const uint64_t a = bh[s], e = bh[b->max_slots + s];
+      sl.offset = e > a ? a : 0;  // a slot with no terms keeps start all ones
       sl.count = e > a ? e - a : 0;
     }
     if (truncated && s < top) {
@@ -771,6 +970,19 @@ sv_status svb_step(svb_state* b, const svb_gate* gates, int count) {
 sv_status svb_set_autotune(svb_state* b, int on) {
   SVB_GUARD(b);
   b->autotune = on != 0;
+  return SV_OK;
+}
+
+sv_status svb_set_layer_kernel(svb_state* b, int on) {
+  SVB_GUARD(b);
+  b->layer_on = on != 0;
+  return SV_OK;
+}
+
+sv_status svb_layer_phase_times(const svb_state* b, double* ms, int cap, int* count) {
+  if (!b || !count || (cap > 0 && !ms)) return SV_E_ARG;
+  *count = LP_COUNT;
+  for (int i = 0; i < cap && i < LP_COUNT; ++i) ms[i] = b->layer_ms[i];
   return SV_OK;
 }
 
@@ -825,6 +1037,9 @@ sv_status svb_peak(svb_state* b, int slot, uint64_t* key, double* prob) {
     return b_fail(b, SV_E_ARG, "svb_peak: slot not in use");
   const Slot& sl = b->slots[slot];
   if (sl.count == 0) return b_fail(b, SV_E_STATE, "svb_peak: empty segment");
+  // a truncation leaves no probabilities behind: recompute the segment's
+  launch_seg_probs(b->prec, (const char*)b->amps[b->cur] + sl.offset * b->amp_bytes, sl.count,
+                   b->probs[b->cur] + sl.offset, b->st);
   launch_peak(b->probs[b->cur] + sl.offset, b->keys[b->cur] + sl.offset, sl.count, b->ctl, b->st);
   sv_status rc = b_sync_ctl(b, "svb_peak");
   if (rc != SV_OK) return rc;
@@ -846,6 +1061,8 @@ sv_status svb_export(svb_state* b, int slot, uint64_t* keys, double* amps, uint6
   if (rc != SV_OK) return rc;
   double* tmp = (double*)b_alloc(b, w * 16);
   if (!tmp) return b_fail(b, SV_E_NOMEM, "svb_export: staging allocation failed");
+  launch_seg_probs(b->prec, (const char*)b->amps[b->cur] + sl.offset * b->amp_bytes, w,
+                   b->probs[b->cur] + sl.offset, b->st);
   launch_iota(b->sidx[0], w, b->st);
   launch_gather_terms(b->prec, b->sidx[0], w, b->keys[b->cur] + sl.offset,
                       (const char*)b->amps[b->cur] + sl.offset * b->amp_bytes, b->probs[b->cur] + sl.offset,

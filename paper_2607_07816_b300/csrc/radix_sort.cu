@@ -14,6 +14,7 @@
 // memory in digit order and writes each digit run at its scanned offset.
 #include "internal.h"
 #include "launch.cuh"
+#include "regroup.cuh"
 
 namespace sv {
 
@@ -88,46 +89,8 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_tile_offsets(const uint32_t* _
                                                                const uint32_t* __restrict__ hist, uint64_t tiles,
                                                                uint32_t* __restrict__ off) {
   pdl_prologue();
-  __shared__ uint32_t wsum[SCAN_THREADS / 32];
-  __shared__ uint32_t s_carry;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int d = blockIdx.x;
-  if (tid == 0) {
-    uint32_t b = 0;
-    for (int e = 0; e < d; ++e) b += hist[e];
-    s_carry = b;
-  }
-  __syncthreads();
-  const uint32_t* row = cnt + (uint64_t)d * tiles;
-  uint32_t* orow = off + (uint64_t)d * tiles;
-  for (uint64_t c0 = 0; c0 < tiles; c0 += SCAN_THREADS) {
-    const uint64_t t = c0 + tid;
-    const uint32_t v = t < tiles ? row[t] : 0u;
-    uint32_t x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    if (lane == 31) wsum[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-      const uint32_t w = wsum[lane];
-      uint32_t z = w;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, z, o);
-        if (lane >= o) z += y;
-      }
-      wsum[lane] = z - w;  // exclusive over warps
-    }
-    __syncthreads();
-    const uint32_t carry = s_carry;
-    if (t < tiles) orow[t] = carry + wsum[warp] + x - v;
-    __syncthreads();
-    if (tid == SCAN_THREADS - 1) s_carry = carry + wsum[warp] + x;
-    __syncthreads();
-  }
+  __shared__ TileOffsetsSmem<SCAN_THREADS> s;
+  tile_offsets_digit<SCAN_THREADS>(cnt, hist, tiles, off, blockIdx.x, s);
 }
 
 void launch_tile_offsets(const uint32_t* cnt, const uint32_t* hist, uint64_t tiles, int digits, uint32_t* off,

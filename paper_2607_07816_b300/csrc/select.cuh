@@ -45,6 +45,12 @@ __device__ __forceinline__ uint32_t z_digit(uint64_t hi, uint64_t lo, int shift,
   return (uint32_t)(z >> shift) & ((1u << D) - 1u);
 }
 
+// Digit of the first level (one bit fixed: the top bit of ~prob_bits, set
+// for every non-negative probability) from a probability's bits.
+__device__ __forceinline__ uint32_t sel_first_digit(uint64_t prob_bits) {
+  return (uint32_t)(~prob_bits >> (63 - SEL_BITS)) & (SEL_BINS - 1u);
+}
+
 // Histogram adds with one bin's pending (count, exact fixed-point mass)
 // held in each thread's registers: a thread touches the shared histogram only
 // when its element falls into another bin than its last one.  A level whose

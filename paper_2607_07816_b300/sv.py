@@ -27,7 +27,7 @@ EXPORTED = ["sv_create", "sv_create_ex", "sv_destroy", "sv_apply_gate", "sv_trun
             "sv_last_stats", "sv_set_timing", "sv_phase_times", "sv_launch_count", "sv_transfer_bytes", "sv_peak_noalloc",
             "svb_create", "svb_destroy", "svb_add", "svb_remove", "svb_step", "svb_num_terms",
             "svb_retained_mass", "svb_peak", "svb_export", "svb_last_error", "svb_set_autotune",
-            "svb_autotune_stats", "svb_set_graphs", "svb_graph_stats", "sv_selftest", "sv_set_apply_variant",
+            "svb_autotune_stats", "svb_set_graphs", "svb_graph_stats", "svb_set_layer_kernel", "svb_layer_phase_times", "sv_selftest", "sv_set_apply_variant",
             "sv_probe_fp64", "sv_select_histogram", "sv_cut", "sv_reserve"]
 PHASES = ["keys", "sort", "heads", "apply", "select", "compact", "peak", "other", "window", "local"]
 
@@ -144,6 +144,10 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.svb_autotune_stats.argtypes = [vp, P(u64), P(u64), P(u64)]
     lib.svb_set_graphs.restype = i32
     lib.svb_set_graphs.argtypes = [vp, i32]
+    lib.svb_set_layer_kernel.restype = i32
+    lib.svb_set_layer_kernel.argtypes = [vp, i32]
+    lib.svb_layer_phase_times.restype = i32
+    lib.svb_layer_phase_times.argtypes = [vp, P(dbl), i32, P(i32)]
     lib.svb_graph_stats.restype = i32
     lib.svb_graph_stats.argtypes = [vp, P(u64), P(u64)]
     lib.sv_peak_noalloc.restype = i32
@@ -571,6 +575,23 @@ def svb_set_graphs(h: int, on: bool) -> None:
     _bcheck(h, load_library().svb_set_graphs(ctypes.c_void_p(h), 1 if on else 0))
 
 
+def svb_set_layer_kernel(h: int, on: bool) -> None:
+    _bcheck(h, load_library().svb_set_layer_kernel(ctypes.c_void_p(h), 1 if on else 0))
+
+
+LAYER_PHASES = ["setup", "keys", "counts", "offsets", "scatter", "splits", "merge", "heads", "apply",
+                "init", "pick1", "hist", "pick", "finish", "scale", "trunc"]
+
+
+def svb_layer_phase_times(h: int):
+    """Milliseconds per phase of the one-launch step, summed over the steps."""
+    lib = load_library()
+    arr = (ctypes.c_double * len(LAYER_PHASES))()
+    cnt = ctypes.c_int()
+    _bcheck(h, lib.svb_layer_phase_times(ctypes.c_void_p(h), arr, len(LAYER_PHASES), ctypes.byref(cnt)))
+    return dict(zip(LAYER_PHASES, [float(x) for x in arr[:cnt.value]]))
+
+
 def svb_graph_stats(h: int):
     c, n = ctypes.c_uint64(), ctypes.c_uint64()
     _bcheck(h, load_library().svb_graph_stats(ctypes.c_void_p(h), ctypes.byref(c), ctypes.byref(n)))
@@ -637,3 +658,9 @@ class Batch:
 
     def graph_stats(self):
         return svb_graph_stats(self.h)
+
+    def set_layer_kernel(self, on: bool) -> None:
+        svb_set_layer_kernel(self.h, on)
+
+    def layer_phase_times(self):
+        return svb_layer_phase_times(self.h)

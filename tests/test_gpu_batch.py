@@ -44,11 +44,15 @@ def _circuits(rng, count):
     return out
 
 
+@pytest.mark.parametrize("layer", [True, False], ids=["one_launch", "kernels"])
 @pytest.mark.parametrize("prec", [0, 1])
-def test_batch_matches_oracle_per_circuit(sv, oracle_mod, prec):
+def test_batch_matches_oracle_per_circuit(sv, oracle_mod, prec, layer):
+    """Both forms of the step (the persistent one-launch layer kernel and the
+    separate kernels) against the oracle, circuit by circuit."""
     rng = np.random.default_rng(31 + prec)
     circs = _circuits(rng, 10)
     b = sv.Batch(16, prec=prec)
+    b.set_layer_kernel(layer)
     slots = [b.add(c.n, c.K) for c in circs]
     orcs = [oracle_mod.Oracle(c.n, c.K, 1.0, prec=prec) for c in circs]
     pos = [0] * len(circs)
@@ -151,10 +155,11 @@ def test_batch_sort_key_bit_bound(sv):
     b.close()
 
 
-def _run_batch(sv, circs, tune, graphs, reps=1):
+def _run_batch(sv, circs, tune, graphs, reps=1, layer=False):
     b = sv.Batch(16, prec=1)
     b.set_autotune(tune)
     b.set_graphs(graphs)
+    b.set_layer_kernel(layer)
     slots = [b.add(c.n, c.K) for c in circs]
     longest = max(len(c.gates) for c in circs)
     for _ in range(reps):
@@ -195,3 +200,19 @@ def test_graph_replay_gives_identical_results(sv):
     _same(direct, graphed)
     tuned, (tstats, gstats2) = _run_batch(sv, circs, tune=True, graphs=True)
     _same(direct, tuned)
+
+
+def test_layer_kernel_graphs_and_separate_kernels_agree(sv):
+    """The one-launch step, direct and replayed from its graph, equals the
+    separate kernels bit for bit; steps of circuits held at their K replay
+    the captured launch."""
+    rng = np.random.default_rng(73)
+    circs = [C.brickwork_circuit(24, 3, seed=int(rng.integers(1 << 30)), sigma=0.05, K=256, p=1.0)
+             for _ in range(6)]
+    kernels, _ = _run_batch(sv, circs, tune=False, graphs=False, layer=False)
+    direct, (_, g0) = _run_batch(sv, circs, tune=False, graphs=False, layer=True)
+    graphed, (_, g1) = _run_batch(sv, circs, tune=False, graphs=True, layer=True)
+    assert g0["launches"] == 0
+    assert g1["captures"] >= 1 and g1["launches"] > 2 * g1["captures"]
+    _same(kernels, direct)
+    _same(kernels, graphed)

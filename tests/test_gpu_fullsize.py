@@ -103,13 +103,16 @@ def test_hadamard_ties_at_the_cut_on_4e6_candidates(sv, oracle_mod, prec):
         assert n_pre == 1 << 22
 
 
+@pytest.mark.parametrize("layer", [True, False], ids=["one_launch", "kernels"])
 @pytest.mark.parametrize("prec", [0, 1])
-def test_batched_circuits_with_large_cut_bins(sv, oracle_mod, prec):
+def test_batched_circuits_with_large_cut_bins(sv, oracle_mod, prec, layer):
     """Batched circuits at K = 2^16 and 2^18 on 48 qubits: their first
     select levels see cut bins of far more than 4096 terms.  Each slot
-    equals its circuit run alone on the oracle."""
+    equals its circuit run alone on the oracle, with the step as one launch
+    and as separate kernels."""
     circs = [C.brickwork_circuit(48, 1, seed=77 + j, sigma=0.05, K=1 << k, p=1.0) for j, k in enumerate((16, 18))]
     b = sv.Batch(4, prec=prec)
+    b.set_layer_kernel(layer)
     slots = [b.add(c.n, c.K) for c in circs]
     orcs = [oracle_mod.Oracle(c.n, c.K, 1.0, prec=prec) for c in circs]
     length = max(len(c.gates) for c in circs)
