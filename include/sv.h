@@ -291,6 +291,17 @@ sv_status svb_num_terms(svb_state* b, int slot, uint64_t* N);
 sv_status svb_retained_mass(svb_state* b, int slot, double* F);
 /* Most probable basis state of the slot in canonical order (Sec. V). */
 sv_status svb_peak(svb_state* b, int slot, uint64_t* key, double* prob);
+/* Pipelined readout of a slot: svb_peak_async enqueues the computation of
+ * the slot's most probable basis state (as svb_peak) and its retained mass
+ * on the handle's stream behind the steps enqueued so far, and returns a
+ * ticket at once; svb_peak_wait(ticket) waits for that readout only and
+ * returns its results (F may be NULL).  The slot may be removed right after
+ * svb_peak_async.  At most 1024 readouts can be outstanding (SV_E_STATE
+ * beyond); each ticket is collected once.  With one launch per step the
+ * steps themselves do not wait either, so a serving loop can enqueue the
+ * next step before it collects the readouts of the last one. */
+sv_status svb_peak_async(svb_state* b, int slot, uint64_t* ticket);
+sv_status svb_peak_wait(svb_state* b, uint64_t ticket, uint64_t* key, double* prob, double* F);
 /* The slot's keys and amplitudes (interleaved re, im doubles) in storage
  * order, min(cap, N) of them; *count = N. */
 sv_status svb_export(svb_state* b, int slot, uint64_t* keys, double* amps, uint64_t cap, uint64_t* count);
@@ -318,11 +329,16 @@ sv_status svb_graph_stats(const svb_state* b, uint64_t* captures, uint64_t* laun
  * group heads, mat-vec, per-slot top-k select to the exact cut,
  * renormalising compaction) runs as one persistent cooperative kernel whose
  * blocks pass grid-wide barriers between the phases, with every size read
- * on the device; with graphs on, the gate-table upload, the launch and the
- * read-back are one graph, captured when the step's table size, widest gate
- * and buffers recur and replayed after that, and the host waits once per
- * step.  Off: the step's separate kernels (two parts, a host wait after
- * each, autotuned launch shapes).  Results are the same either way. */
+ * on the device.  With graphs on, the gate-table upload and the launch are
+ * one graph, captured when the step's table size, widest gate and buffers
+ * recur and replayed after that.  The device then keeps the state's term
+ * count, slot ranges and retained masses, svb_step and svb_add return
+ * without waiting, and the calls that report on a slot (svb_num_terms,
+ * svb_retained_mass, svb_peak, svb_export) wait for the steps enqueued
+ * before them; device errors of a step are returned by the next call that
+ * waits.  Off: the step's separate kernels (two parts, a host wait after
+ * each, autotuned launch shapes).  Results are the same either way.  Only
+ * an empty batch changes mode (SV_E_STATE otherwise). */
 sv_status svb_set_layer_kernel(svb_state* b, int on);
 /* Benchmarking hook: milliseconds spent in each phase of the one-launch
  * step, summed over the handle's steps, as timed by the kernel's first block
@@ -331,7 +347,7 @@ sv_status svb_set_layer_kernel(svb_state* b, int on);
  * heads, mat-vec, select state, first pick, select scans, picks, finishes,
  * scales, compaction).  Writes min(cap, *count) values; *count = the number
  * of phases. */
-sv_status svb_layer_phase_times(const svb_state* b, double* ms, int cap, int* count);
+sv_status svb_layer_phase_times(svb_state* b, double* ms, int cap, int* count);
 
 /* Peak readout that allocates nothing.  The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc where they need

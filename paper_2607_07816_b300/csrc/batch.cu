@@ -1295,11 +1295,20 @@ __global__ void __launch_bounds__(LAYER_THREADS, MAXD <= 4 ? 4 : (MAXD == 8 ? 2 
   const int tid = threadIdx.x, lane = tid & 31;
   const uint64_t gtid = (uint64_t)cta * LAYER_THREADS + tid, gstride = (uint64_t)ncta * LAYER_THREADS;
   const LayerStep S = *P.step;
-  const uint64_t N = S.N, nkeep = S.nkeep;
   const int shift = S.shift, top = S.top, m = S.m, D = 1 << m;
   Ctl* ctl = P.ctl;
   uint32_t* err = &ctl->err;
   LayerCtl* lc = P.lc;
+  // the state's buffer set and term count (rewritten only at the very end)
+  const int cin = (int)lc->cur, cmv = 1 - cin;
+  const uint64_t N = lc->n_cur;
+  const uint64_t* keys_in = P.keys[cin];
+  const uint16_t* seg_in = P.seg[cin];
+  const C2* amps_in = (const C2*)P.amps[cin];
+  uint64_t* keys_mv = P.keys[cmv];
+  C2* amps_mv = (C2*)P.amps[cmv];
+  uint64_t* probs_mv = P.probs[cmv];
+  uint16_t* seg_mv = P.seg[cmv];
   uint64_t* lb_heads = P.lb;
   uint64_t* lb_apply = lb_heads + P.lb_heads_words;
   uint64_t* lb_trunc = lb_apply + P.lb_apply_words;
@@ -1322,10 +1331,8 @@ __global__ void __launch_bounds__(LAYER_THREADS, MAXD <= 4 ? 4 : (MAXD == 8 ? 2 
     }
     lc->truncated = 0;
     lc->unresolved = 0;
-    lc->n_out = 0;
   }
-  if (cta == 0 && tid < LP_COUNT) lc->phase_ns[tid] = 0;
-  if (cta == 0 && tid == 0) lc->t_last = global_ns();
+  if (cta == 0 && tid == 0) lc->t_last = global_ns();  // phase times add up over the steps
   for (uint32_t vb = cta; vb < (uint32_t)top; vb += ncta) {
     seg_tables_slot(P.gates, P.tables, vb, smem_as<SegTablesSmem>(smem));
     __syncthreads();
@@ -1333,7 +1340,7 @@ __global__ void __launch_bounds__(LAYER_THREADS, MAXD <= 4 ? 4 : (MAXD == 8 ? 2 
   if (layer_sync(lc, ncta, err, LP_SETUP)) return;
 
   // sort keys, then the grouping: partition by the gate bits, m merge levels
-  seg_keys_range(P.keys_in, P.seg_in, N, P.gates, P.tables, shift, P.sk[1], gtid, gstride);
+  seg_keys_range(keys_in, seg_in, N, P.gates, P.tables, shift, P.sk[1], gtid, gstride);
   if (layer_sync(lc, ncta, err, LP_KEYS)) return;
   GateParams gp;
   memset(&gp, 0, sizeof(gp));
@@ -1348,6 +1355,8 @@ __global__ void __launch_bounds__(LAYER_THREADS, MAXD <= 4 ? 4 : (MAXD == 8 ? 2 
     __syncthreads();
   }
   if (layer_sync(lc, ncta, err, LP_COUNTS)) return;
+  uint64_t nkeep = 0;  // terms of the slots that stay (a removed slot's terms are left out)
+  for (int d = 0; d < D; ++d) nkeep += P.hist16[d];
   for (uint32_t d = cta; d < (uint32_t)D; d += ncta) {
     tile_offsets_digit<LAYER_THREADS>(cnt, P.hist16, tiles, off, (int)d, smem_as<TileOffsetsSmem<LAYER_THREADS>>(smem));
     __syncthreads();
@@ -1380,8 +1389,8 @@ __global__ void __launch_bounds__(LAYER_THREADS, MAXD <= 4 ? 4 : (MAXD == 8 ? 2 
   if (layer_sync(lc, ncta, err, LP_HEADS)) return;
   if (tid == 0) smem_as<SegApplySmem>(smem).hcnt = reinterpret_cast<uint32_t*>(dyn + seg_apply_smem<C2>(MAXD, LAYER_GPT));
   __syncthreads();
-  seg_apply_run<Real, MAXD, LAYER_GPT>(P.sk[cur], P.sidx[cur], nkeep, P.heads, (const C2*)P.amps_in, shift, P.gates,
-                                       P.rank_slot, P.tables, P.keys_mv, (C2*)P.amps_mv, P.probs_mv, P.seg_mv,
+  seg_apply_run<Real, MAXD, LAYER_GPT>(P.sk[cur], P.sidx[cur], nkeep, P.heads, amps_in, shift, P.gates,
+                                       P.rank_slot, P.tables, keys_mv, amps_mv, probs_mv, seg_mv,
                                        P.sel_cnt[0], P.start, P.end, lb_apply, P.lb_apply_words - 1, ctl,
                                        smem_as<SegApplySmem>(smem), dyn);
   if (layer_sync(lc, ncta, err, LP_APPLY)) return;
@@ -1405,7 +1414,7 @@ __global__ void __launch_bounds__(LAYER_THREADS, MAXD <= 4 ? 4 : (MAXD == 8 ? 2 
 #pragma unroll
       for (int j = 0; j < 4; ++j) P.sel_mass[1 - par][4 * i + j] = 0;
     }
-    segsel_hist_chunk(P.probs_mv, P.keys_mv, P.seg_mv, &ctl->count[1], P.sel, P.sel_cnt[par], P.sel_mass[par],
+    segsel_hist_chunk(probs_mv, keys_mv, seg_mv, &ctl->count[1], P.sel, P.sel_cnt[par], P.sel_mass[par],
                       P.sel_buf, P.sel_bufn[par], err, cta, ncta, smem_as<SegHistSmem>(smem));
     if (layer_sync(lc, ncta, err, LP_HIST)) return;
     for (uint32_t vb = cta; vb < (uint32_t)top; vb += ncta) {
@@ -1425,29 +1434,42 @@ __global__ void __launch_bounds__(LAYER_THREADS, MAXD <= 4 ? 4 : (MAXD == 8 ? 2 
     par ^= 1;
   }
   if (pending) {
-    if (gtid == 0) lc->unresolved = 1;
+    if (gtid == 0) {
+      lc->unresolved = 1;
+      atomicOr(err, ERR_INVARIANT);
+    }
     return;
   }
-  for (uint64_t s = gtid; s < (uint64_t)top; s += gstride) segsel_scale_slot(P.sel[s]);
+  for (uint64_t s = gtid; s < (uint64_t)top; s += gstride) {
+    SegSel& st = P.sel[s];
+    segsel_scale_slot(st);
+    if (st.active && st.done == 1)  // retained mass F *= S_c / S_N (Sec. III)
+      P.F[s] = __dmul_rn(P.F[s], __ddiv_rn(fx_to_double(make_u128(st.cut_mass_hi, st.cut_mass_lo)),
+                                           fx_to_double(make_u128(st.total_mass_hi, st.total_mass_lo))));
+  }
   bool cut = false;
   for (int s = tid; s < top; s += LAYER_THREADS) cut |= P.sel[s].active && P.sel[s].done == 1;
   const bool any_cut = __syncthreads_or(cut) != 0;
   if (layer_sync(lc, ncta, err, LP_SCALE)) return;
   if (!any_cut) {
-    if (gtid == 0) lc->n_out = ctl->count[1];
+    if (gtid == 0) {
+      lc->cur = (uint32_t)cmv;
+      lc->n_cur = ctl->count[1];
+    }
     return;
   }
 
   // compaction of the cut slots, then their new bounds (a slot keeps at
   // least one term, so every bound written by the mat-vec is overwritten)
   const uint64_t n_max = (P.lb_trunc_words - 1) * (uint64_t)(SC_BLOCK * SC_ITEMS);
-  seg_truncate_run<C2>(P.keys_mv, (const C2*)P.amps_mv, P.probs_mv, P.seg_mv, &ctl->count[1], n_max, P.sel,
-                       P.keys_tr, (C2*)P.amps_tr, P.seg_tr, P.start_tr, P.end_tr, lb_trunc, ctl,
+  seg_truncate_run<C2>(keys_mv, amps_mv, probs_mv, seg_mv, &ctl->count[1], n_max, P.sel, P.keys[cin],
+                       (C2*)P.amps[cin], P.seg[cin], P.start_tr, P.end_tr, lb_trunc, ctl,
                        smem_as<SegTruncSmem>(smem));
   if (layer_sync(lc, ncta, err, LP_TRUNC)) return;
   if (gtid == 0) {
     lc->truncated = 1;
-    lc->n_out = ctl->count[2];
+    lc->cur = (uint32_t)cin;
+    lc->n_cur = ctl->count[2];
   }
 }
 
@@ -1539,6 +1561,146 @@ void launch_seg_probs(int prec, const void* amps, uint64_t n, uint64_t* probs, c
   const unsigned grid = (unsigned)(blocks < 148 * 8 ? blocks : 148 * 8);
   if (prec == 0) k_seg_probs<double2><<<grid, 256, 0, st>>>((const double2*)amps, n, probs);
   else k_seg_probs<float2><<<grid, 256, 0, st>>>((const float2*)amps, n, probs);
+}
+
+// ---------------------------------------------------------------- layer bookkeeping
+__global__ void k_seg_append_layer(uint64_t* k0, uint64_t* k1, void* a0, void* a1, uint64_t* p0, uint64_t* p1,
+                                   uint16_t* s0, uint16_t* s1, LayerCtl* lc, uint64_t* bounds, int max_slots,
+                                   double* F, int slot, int prec) {
+  const int cur = (int)lc->cur;
+  const uint64_t at = lc->n_cur;
+  uint64_t* keys = cur ? k1 : k0;
+  void* amps = cur ? a1 : a0;
+  uint64_t* probs = cur ? p1 : p0;
+  uint16_t* seg = cur ? s1 : s0;
+  keys[at] = 0;
+  if (prec == 0) reinterpret_cast<double2*>(amps)[at] = make_double2(1.0, 0.0);
+  else reinterpret_cast<float2*>(amps)[at] = make_float2(1.0f, 0.0f);
+  probs[at] = 0x3ff0000000000000ull;
+  seg[at] = (uint16_t)slot;
+  const int pair = lc->truncated ? 2 : 0;  // the pair of bounds the last step left
+  bounds[(uint64_t)pair * max_slots + slot] = at;
+  bounds[(uint64_t)(pair + 1) * max_slots + slot] = at + 1;
+  F[slot] = 1.0;
+  lc->n_cur = at + 1;
+}
+
+void launch_seg_append_layer(uint64_t* const keys[2], void* const amps[2], uint64_t* const probs[2],
+                             uint16_t* const seg[2], LayerCtl* lc, uint64_t* bounds, int max_slots, double* F,
+                             int slot, int prec, cudaStream_t st) {
+  k_seg_append_layer<<<1, 1, 0, st>>>(keys[0], keys[1], amps[0], amps[1], probs[0], probs[1], seg[0], seg[1], lc,
+                                      bounds, max_slots, F, slot, prec);
+}
+
+// Peak of one slot: per block the canonical best (larger probability bits,
+// then the smaller key) over a grid-stride share of the slot's range, then
+// one block reduces the partials.
+__device__ __forceinline__ bool peak_better(uint64_t pa, uint64_t ka, uint64_t pb, uint64_t kb) {
+  return pa > pb || (pa == pb && ka < kb);
+}
+
+__device__ __forceinline__ void block_best(uint64_t& p, uint64_t& k, uint64_t* sp, uint64_t* sk) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const uint64_t op = __shfl_xor_sync(0xffffffffu, (unsigned long long)p, o);
+    const uint64_t ok = __shfl_xor_sync(0xffffffffu, (unsigned long long)k, o);
+    if (peak_better(op, ok, p, k)) {
+      p = op;
+      k = ok;
+    }
+  }
+  if (lane == 0) {
+    sp[warp] = p;
+    sk[warp] = k;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    p = lane < (int)(blockDim.x >> 5) ? sp[lane] : 0ull;
+    k = lane < (int)(blockDim.x >> 5) ? sk[lane] : ~0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const uint64_t op = __shfl_xor_sync(0xffffffffu, (unsigned long long)p, o);
+      const uint64_t ok = __shfl_xor_sync(0xffffffffu, (unsigned long long)k, o);
+      if (peak_better(op, ok, p, k)) {
+        p = op;
+        k = ok;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void seg_peak_range(const LayerCtl* lc, const uint64_t* bounds, int max_slots, int slot,
+                                               int dev_range, uint64_t off, uint64_t count, int cur, uint64_t* a,
+                                               uint64_t* e, int* c) {
+  if (dev_range) {
+    const int pair = lc->truncated ? 2 : 0;
+    *a = bounds[(uint64_t)pair * max_slots + slot];
+    *e = bounds[(uint64_t)(pair + 1) * max_slots + slot];
+    *c = (int)lc->cur;
+  } else {
+    *a = off;
+    *e = off + count;
+    *c = cur;
+  }
+}
+
+template <typename C2>
+__global__ void __launch_bounds__(256) k_seg_peak_part(const uint64_t* k0, const uint64_t* k1, const C2* a0,
+                                                       const C2* a1, int dev_range, const LayerCtl* lc,
+                                                       const uint64_t* bounds, int max_slots, int slot, uint64_t off,
+                                                       uint64_t count, int cur, uint64_t* part) {
+  __shared__ uint64_t sp[8], sk[8];
+  uint64_t a, e;
+  int c;
+  seg_peak_range(lc, bounds, max_slots, slot, dev_range, off, count, cur, &a, &e, &c);
+  const uint64_t* keys = c ? k1 : k0;
+  const C2* amps = c ? a1 : a0;
+  uint64_t bp = 0, bk = ~0ull;
+  for (uint64_t i = a + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < e; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t p = amp_prob_bits(amps[i]), k = keys[i];
+    if (peak_better(p, k, bp, bk)) {
+      bp = p;
+      bk = k;
+    }
+  }
+  block_best(bp, bk, sp, sk);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = bp;
+    part[2 * blockIdx.x + 1] = bk;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_seg_peak_final(const uint64_t* part, int nparts, int dev_range,
+                                                        const double* F, int slot, double F_host, uint64_t* out) {
+  __shared__ uint64_t sp[8], sk[8];
+  uint64_t bp = 0, bk = ~0ull;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x)
+    if (peak_better(part[2 * i], part[2 * i + 1], bp, bk)) {
+      bp = part[2 * i];
+      bk = part[2 * i + 1];
+    }
+  block_best(bp, bk, sp, sk);
+  if (threadIdx.x == 0) {
+    out[0] = bk;
+    out[1] = bp;
+    const double f = dev_range ? F[slot] : F_host;
+    out[2] = (uint64_t)__double_as_longlong(f);
+  }
+}
+
+void launch_seg_peak(uint64_t* const keys[2], void* const amps[2], int prec, int dev_range, const LayerCtl* lc,
+                     const uint64_t* bounds, int max_slots, const double* F, int slot, uint64_t off, uint64_t count,
+                     int cur, double F_host, uint64_t* part, uint64_t* out, cudaStream_t st) {
+  if (prec == 0)
+    k_seg_peak_part<double2><<<PEAK_SEG_BLOCKS, 256, 0, st>>>(keys[0], keys[1], (const double2*)amps[0],
+                                                             (const double2*)amps[1], dev_range, lc, bounds,
+                                                             max_slots, slot, off, count, cur, part);
+  else
+    k_seg_peak_part<float2><<<PEAK_SEG_BLOCKS, 256, 0, st>>>(keys[0], keys[1], (const float2*)amps[0],
+                                                            (const float2*)amps[1], dev_range, lc, bounds, max_slots,
+                                                            slot, off, count, cur, part);
+  k_seg_peak_final<<<1, 256, 0, st>>>(part, PEAK_SEG_BLOCKS, dev_range, F, slot, F_host, out);
 }
 
 // ---------------------------------------------------------------- new terms

@@ -73,11 +73,9 @@ struct SegSel {
 // Per-step scalars of the layer kernel, uploaded with the gate table (so a
 // captured launch reads the current step's values).
 struct LayerStep {
-  uint64_t N;      // terms in the state (removed slots' terms included)
-  uint64_t nkeep;  // terms of the slots that stay
-  int shift;       // bit of the segment rank in the sort key
-  int top;         // slots in the gate table
-  int m;           // grouping width: the widest gate of the step, at least 1
+  int shift;  // bit of the segment rank in the sort key
+  int top;    // slots in the gate table
+  int m;      // grouping width: the widest gate of the step, at least 1
   int pad;
 };
 
@@ -89,13 +87,19 @@ enum LayerPhase {
 };
 
 // Control words of the layer kernel (zeroed when the handle is created).
+// With one launch per step the device holds the state's bookkeeping: which
+// of the two buffer sets holds the state, its term count, the slot bounds
+// (in bounds[0..1] after a step without a cut, bounds[2..3] after one) and
+// every slot's retained mass; the host reads them when it needs them.
 struct LayerCtl {
   uint32_t bar_count, bar_gen;  // grid barrier
-  uint32_t truncated;           // 1: the step's state is in the truncation buffers
+  uint32_t truncated;           // 1: the last step cut a slot (its bounds are the second pair)
   uint32_t unresolved;          // 1: a slot's cut was not found within LAYER_LEVELS select levels
-  uint64_t n_out;               // terms after the step
+  uint32_t cur;                 // buffer set holding the state
+  uint32_t pad;
+  uint64_t n_cur;               // terms in the state
   uint64_t t_last;              // global timer at the last barrier (first block)
-  uint64_t phase_ns[LP_COUNT];  // this step's time per phase
+  uint64_t phase_ns[LP_COUNT];  // time per phase, summed over the steps
 };
 
 // Buffers of one layer launch.  The state moves from the input buffers to
@@ -105,16 +109,11 @@ struct LayerParams {
   const LayerStep* step;
   LayerCtl* lc;
   Ctl* ctl;
-  const uint64_t* keys_in;
-  const uint16_t* seg_in;
-  const void* amps_in;
-  uint64_t* keys_mv;
-  void* amps_mv;
-  uint64_t* probs_mv;
-  uint16_t* seg_mv;
-  uint64_t* keys_tr;
-  void* amps_tr;
-  uint16_t* seg_tr;
+  uint64_t* keys[2];  // the two buffer sets: the state in lc->cur, the mat-vec output in the other,
+  void* amps[2];      // a compaction back into lc->cur
+  uint64_t* probs[2];
+  uint16_t* seg[2];
+  double* F;          // [slots] retained mass of every slot
   uint64_t* sk[2];
   uint32_t* sidx[2];
   uint32_t* heads;
@@ -135,6 +134,21 @@ struct LayerParams {
   uint64_t* start_tr;  // slot bounds after the compaction
   uint64_t* end_tr;
 };
+
+// Append the state |0> of a new slot at the end of the device-held state
+// (layer bookkeeping: lc->n_cur grows by one, the slot's bounds and retained
+// mass are set).
+void launch_seg_append_layer(uint64_t* const keys[2], void* const amps[2], uint64_t* const probs[2],
+                             uint16_t* const seg[2], LayerCtl* lc, uint64_t* bounds, int max_slots, double* F,
+                             int slot, int prec, cudaStream_t st);
+// Peak of one slot (canonical order over its amplitudes' probabilities) into
+// out = {key, probability bits, retained mass bits}: with dev_range the
+// slot's range, buffer set and mass come from the layer bookkeeping, else
+// from (off, count, cur) and F_host.  part: [PEAK_SEG_BLOCKS][2] scratch.
+constexpr int PEAK_SEG_BLOCKS = 148 * 2;
+void launch_seg_peak(uint64_t* const keys[2], void* const amps[2], int prec, int dev_range, const LayerCtl* lc,
+                     const uint64_t* bounds, int max_slots, const double* F, int slot, uint64_t off, uint64_t count,
+                     int cur, double F_host, uint64_t* part, uint64_t* out, cudaStream_t st);
 
 // Blocks of one cooperative layer launch on this device (all co-resident).
 cudaError_t seg_layer_grid(int prec, int m, int sms, unsigned* grid);

@@ -26,8 +26,13 @@ struct Slot {
   uint64_t count = 0;   // terms of this segment
   uint64_t offset = 0;  // first term in the current buffers
   double F = 1.0;
-  uint8_t order[64];    // bit of qubit b in the sort order the segment is sorted by
+  uint64_t count_ub = 0;  // upper bound of count while steps are in flight (one launch per step)
+  uint64_t seq = 0;       // order of admission = order of the segments in the buffers
+  uint8_t order[64];      // bit of qubit b in the sort order the segment is sorted by
 };
+
+// Peak readouts in flight (svb_peak_async): ring of result slots.
+constexpr int PEAK_RING = 1024;
 
 }  // namespace
 
@@ -112,7 +117,24 @@ struct svb_state {
   uint64_t* layer_lb = nullptr;    // look-backs of the heads, the mat-vec and the compaction
   uint64_t layer_lb_heads = 0, layer_lb_apply = 0, layer_lb_trunc = 0;
   uint64_t layer_launches = 0;
-  double layer_ms[LP_COUNT] = {};  // time per phase of the layer kernel, summed over the steps
+  // With one launch per step the steps run asynchronously: the device holds
+  // the state's buffer set, term count, slot bounds and retained masses, the
+  // host keeps upper bounds of the slot counts and reads the rest back
+  // (b_settle) only when a call needs it.  The gate tables alternate between
+  // two pinned buffer sets (tparity), each reused once the step that read it
+  // has completed (upload_ev).
+  bool pending = false;
+  int tparity = 0;
+  cudaEvent_t upload_ev[2] = {};
+  double* F_dev = nullptr;     // [max_slots]
+  double* F_mirror = nullptr;  // pinned [max_slots]
+  uint64_t next_seq = 0;
+  uint64_t* peak_part = nullptr;   // [PEAK_SEG_BLOCKS][2]
+  uint64_t* ring_dev = nullptr;    // [PEAK_RING][4]
+  uint64_t* ring_host = nullptr;   // pinned [PEAK_RING][4]: key, probability bits, mass bits, error bits
+  cudaEvent_t ring_ev[PEAK_RING] = {};
+  uint64_t ring_ticket[PEAK_RING] = {};  // ticket + 1 held by each ring slot (0: free)
+  uint64_t next_ticket = 0;
 
   std::map<std::array<uint64_t, 12>, cudaGraphExec_t> graphs;
   std::set<std::array<uint64_t, 12>> seen_keys;  // keys enqueued once without a graph
@@ -120,6 +142,8 @@ struct svb_state {
 };
 
 namespace {
+
+sv_status b_settle(svb_state* b);
 
 void* b_alloc(svb_state* b, size_t bytes) {
   if (bytes == 0) bytes = 256;
@@ -181,6 +205,10 @@ sv_status b_lookback(svb_state* b, uint64_t entries) {
 // Buffers for `need` terms; the current contents are preserved.
 sv_status b_state_cap(svb_state* b, uint64_t need) {
   if (need <= b->cap) return SV_OK;
+  if (b->pending) {  // the copy below needs the exact state, and steps in flight use the old buffers
+    sv_status rs = b_settle(b);
+    if (rs != SV_OK) return rs;
+  }
   uint64_t cap = b->cap * 2 > need ? b->cap * 2 : need;
   if (cap < 4096) cap = 4096;
   uint64_t* k[2];
@@ -222,6 +250,8 @@ sv_status b_state_cap(svb_state* b, uint64_t need) {
   b->cur = 0;
   b->cap = cap;
   ++b->gen;
+  if (rc == SV_OK && b->layer_on)  // the device bookkeeping follows the copy into buffer set 0
+    rc = b_cuda(b, cudaMemsetAsync(&b->lc_dev->cur, 0, sizeof(uint32_t), b->st), "batch state growth");
   return rc;
 }
 
@@ -249,6 +279,12 @@ sv_status b_sort_cap(svb_state* b, uint64_t need) {
 
 // Scratch of the layer kernel for N terms in (nkeep of them in slots that
 // stay) and gates of up to 2^mmax outputs per group.
+// Whether that scratch must grow first.
+bool layer_grows(const svb_state* b, uint64_t N, uint64_t nkeep, int mmax) {
+  return 2 * 16 * (N / 4096 + 2) + 64 > b->layer_part_words || nkeep / 4096 + 2 > b->layer_lb_heads ||
+         nkeep / 256 + 2 > b->layer_lb_apply || (nkeep << mmax) / 2048 + 2 > b->layer_lb_trunc;
+}
+
 sv_status b_layer_cap(svb_state* b, uint64_t N, uint64_t nkeep, int mmax) {
   const uint64_t tiles = N / 4096 + 2;
   const uint64_t part = 2 * 16 * tiles + 64;
@@ -377,6 +413,38 @@ sv_status b_wait(svb_state* b, const char* where) {
     b->broken = true;
     return b_fail(b, SV_E_STATE, std::string(where) + ": device state error");
   }
+  return SV_OK;
+}
+
+// Bring the host's view of the state up to date after asynchronous steps:
+// wait for the stream, read the device bookkeeping (buffer set, term count,
+// slot bounds, retained masses, error bits) and set every slot's offset,
+// count and mass from it.
+sv_status b_settle(svb_state* b) {
+  if (!b->pending) return SV_OK;
+  cudaMemcpyAsync(b->lc_host, b->lc_dev, sizeof(LayerCtl), cudaMemcpyDeviceToHost, b->st);
+  cudaMemcpyAsync(b->ctl_host, b->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, b->st);
+  cudaMemcpyAsync(b->bounds_host, b->bounds_dev, sizeof(uint64_t) * 4 * b->max_slots, cudaMemcpyDeviceToHost, b->st);
+  cudaMemcpyAsync(b->F_mirror, b->F_dev, sizeof(double) * b->max_slots, cudaMemcpyDeviceToHost, b->st);
+  sv_status rc = b_wait(b, "batch readback");
+  if (rc != SV_OK) return rc;
+  if (b->lc_host->unresolved) {
+    b->broken = true;
+    return b_fail(b, SV_E_STATE, "svb_step: segmented select did not resolve");
+  }
+  b->cur = (int)b->lc_host->cur;
+  b->N = b->lc_host->n_cur;
+  const uint64_t* bh = b->bounds_host + (b->lc_host->truncated ? 2 * b->max_slots : 0);
+  for (int s = 0; s < b->max_slots; ++s) {
+    Slot& sl = b->slots[s];
+    if (sl.state == SLOT_FREE) continue;
+    const uint64_t a = bh[s], e = bh[b->max_slots + s];
+    sl.offset = e > a ? a : 0;  // a slot with no terms keeps start all ones
+    sl.count = e > a ? e - a : 0;
+    sl.count_ub = sl.count;
+    sl.F = b->F_mirror[s];
+  }
+  b->pending = false;
   return SV_OK;
 }
 
@@ -555,9 +623,10 @@ static sv_status step_kernels(svb_state* b, int top, uint64_t N, uint64_t nkeep,
   return SV_OK;
 }
 
-// The step as one persistent launch of the layer kernel (one graph replay:
-// the table upload, the launch and the readback), one host wait.
-static sv_status step_layer(svb_state* b, int top, uint64_t N, uint64_t nkeep, int shift, int mmax, bool& truncated) {
+// The step as one persistent launch of the layer kernel: the gate-table
+// upload, the launch (one graph replay once the shape recurs) and no wait;
+// the term counts stay on the device.
+static sv_status step_layer(svb_state* b, int par, int top, uint64_t N, uint64_t nkeep, int shift, int mmax) {
   const int m = mmax > 1 ? mmax : 1;
   sv_status rc = b_layer_cap(b, N, nkeep, m);
   if (rc != SV_OK) return rc;
@@ -568,32 +637,27 @@ static sv_status step_layer(svb_state* b, int top, uint64_t N, uint64_t nkeep, i
     b->layer_grid[m] = g;
   }
   const unsigned grid = b->layer_grid[m];
-  b->step_host->N = N;
-  b->step_host->nkeep = nkeep;
-  b->step_host->shift = shift;
-  b->step_host->top = top;
-  b->step_host->m = m;
-  b->step_host->pad = 0;
-  const int cur = b->cur, alt = 1 - cur;
+  LayerStep* sh = b->step_host + par;
+  sh->shift = shift;
+  sh->top = top;
+  sh->m = m;
+  sh->pad = 0;
+  SegGate* gh = b->gates_host + (size_t)par * b->max_slots;
+  uint16_t* rh = b->rank_slot_host + (size_t)par * b->max_slots;
   LayerParams P;
   std::memset(&P, 0, sizeof(P));
   P.step = b->step_dev;
   P.lc = b->lc_dev;
   P.ctl = b->ctl;
-  P.keys_in = b->keys[cur];
-  P.seg_in = b->seg[cur];
-  P.amps_in = b->amps[cur];
-  P.keys_mv = b->keys[alt];
-  P.amps_mv = b->amps[alt];
-  P.probs_mv = b->probs[alt];
-  P.seg_mv = b->seg[alt];
-  P.keys_tr = b->keys[cur];
-  P.amps_tr = b->amps[cur];
-  P.seg_tr = b->seg[cur];
   for (int i = 0; i < 2; ++i) {
+    P.keys[i] = b->keys[i];
+    P.amps[i] = b->amps[i];
+    P.probs[i] = b->probs[i];
+    P.seg[i] = b->seg[i];
     P.sk[i] = b->sk[i];
     P.sidx[i] = b->sidx[i];
   }
+  P.F = b->F_dev;
   P.heads = b->heads;
   P.hist16 = b->hist;
   P.part = b->layer_part;
@@ -616,34 +680,20 @@ static sv_status step_layer(svb_state* b, int top, uint64_t N, uint64_t nkeep, i
   P.end = b->bounds_dev + b->max_slots;
   P.start_tr = b->bounds_dev + 2 * b->max_slots;
   P.end_tr = b->bounds_dev + 3 * b->max_slots;
-  const std::array<uint64_t, 12> key = {2, (uint64_t)top, (uint64_t)m, (uint64_t)cur, b->gen, grid, 0, 0, 0, 0, 0, 0};
+  const std::array<uint64_t, 12> key = {2, (uint64_t)top, (uint64_t)m, (uint64_t)par, b->gen, grid, 0, 0, 0, 0, 0, 0};
   rc = run_part(b, true, key, [&]() -> sv_status {
-    cudaMemcpyAsync(b->gates_dev, b->gates_host, sizeof(SegGate) * top, cudaMemcpyHostToDevice, b->st);
-    cudaMemcpyAsync(b->rank_slot_dev, b->rank_slot_host, sizeof(uint16_t) * top, cudaMemcpyHostToDevice, b->st);
-    cudaMemcpyAsync(b->step_dev, b->step_host, sizeof(LayerStep), cudaMemcpyHostToDevice, b->st);
+    cudaMemcpyAsync(b->gates_dev, gh, sizeof(SegGate) * top, cudaMemcpyHostToDevice, b->st);
+    cudaMemcpyAsync(b->rank_slot_dev, rh, sizeof(uint16_t) * top, cudaMemcpyHostToDevice, b->st);
+    cudaMemcpyAsync(b->step_dev, sh, sizeof(LayerStep), cudaMemcpyHostToDevice, b->st);
     const cudaError_t e = launch_seg_layer(b->prec, m, P, grid, b->st);
     if (e != cudaSuccess) return b_cuda(b, e, "svb_step layer launch");
-    cudaMemcpyAsync(b->ctl_host, b->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, b->st);
-    cudaMemcpyAsync(b->lc_host, b->lc_dev, sizeof(LayerCtl), cudaMemcpyDeviceToHost, b->st);
-    cudaMemcpyAsync(b->bounds_host, b->bounds_dev, sizeof(uint64_t) * 4 * b->max_slots, cudaMemcpyDeviceToHost,
-                    b->st);
-    cudaMemcpyAsync(b->sel_host, b->sel_dev, sizeof(SegSel) * top, cudaMemcpyDeviceToHost, b->st);
     return SV_OK;
   });
   if (rc != SV_OK) return rc;
-  rc = b_wait(b, "svb_step");
+  rc = b_cuda(b, cudaEventRecord(b->upload_ev[par], b->st), "svb_step");
   if (rc != SV_OK) return rc;
+  b->pending = true;
   ++b->layer_launches;
-  for (int i = 0; i < LP_COUNT; ++i) b->layer_ms[i] += 1e-6 * (double)b->lc_host->phase_ns[i];
-  if (b->lc_host->unresolved) {
-    b->broken = true;
-    return b_fail(b, SV_E_STATE, "svb_step: segmented select did not resolve");
-  }
-  for (int s = 0; s < b->max_slots; ++s)
-    if (b->slots[s].state == SLOT_REMOVING) b->slots[s] = Slot();
-  truncated = b->lc_host->truncated != 0;
-  if (!truncated) b->cur = alt;
-  b->N = b->lc_host->n_out;
   return SV_OK;
 }
 
@@ -696,7 +746,12 @@ sv_status svb_create(int max_slots, int prec, void* cuda_stream, const sv_alloca
   b->sel_bufn2 = (uint32_t*)b_alloc(b, sizeof(uint32_t) * max_slots);
   b->step_dev = (LayerStep*)b_alloc(b, sizeof(LayerStep));
   b->lc_dev = (LayerCtl*)b_alloc(b, sizeof(LayerCtl));
-  if (!b->sel_cnt2 || !b->sel_mass2 || !b->sel_bufn2 || !b->step_dev || !b->lc_dev) rc = SV_E_NOMEM;
+  b->F_dev = (double*)b_alloc(b, sizeof(double) * max_slots);
+  b->peak_part = (uint64_t*)b_alloc(b, sizeof(uint64_t) * 2 * PEAK_SEG_BLOCKS);
+  b->ring_dev = (uint64_t*)b_alloc(b, sizeof(uint64_t) * 4 * PEAK_RING);
+  if (!b->sel_cnt2 || !b->sel_mass2 || !b->sel_bufn2 || !b->step_dev || !b->lc_dev || !b->F_dev || !b->peak_part ||
+      !b->ring_dev)
+    rc = SV_E_NOMEM;
   if (!b->hist || !b->tile_counter || !b->ctl || !b->gates_dev || !b->tables_dev || !b->rank_slot_dev ||
       !b->sel_dev || !b->sel_cnt ||
       !b->sel_mass ||
@@ -704,13 +759,19 @@ sv_status svb_create(int max_slots, int prec, void* cuda_stream, const sv_alloca
     rc = SV_E_NOMEM;
   if (rc == SV_OK && (cudaMallocHost(&b->hist_host, sizeof(uint32_t) * MAX_PASSES * RADIX) != cudaSuccess ||
                       cudaMallocHost(&b->ctl_host, sizeof(Ctl)) != cudaSuccess ||
-                      cudaMallocHost(&b->gates_host, sizeof(SegGate) * max_slots) != cudaSuccess ||
-                      cudaMallocHost(&b->rank_slot_host, sizeof(uint16_t) * max_slots) != cudaSuccess ||
+                      cudaMallocHost(&b->gates_host, sizeof(SegGate) * 2 * max_slots) != cudaSuccess ||
+                      cudaMallocHost(&b->rank_slot_host, sizeof(uint16_t) * 2 * max_slots) != cudaSuccess ||
                       cudaMallocHost(&b->sel_host, sizeof(SegSel) * max_slots) != cudaSuccess ||
                       cudaMallocHost(&b->bounds_host, sizeof(uint64_t) * 4 * max_slots) != cudaSuccess ||
-                      cudaMallocHost(&b->step_host, sizeof(LayerStep)) != cudaSuccess ||
-                      cudaMallocHost(&b->lc_host, sizeof(LayerCtl)) != cudaSuccess))
+                      cudaMallocHost(&b->step_host, sizeof(LayerStep) * 2) != cudaSuccess ||
+                      cudaMallocHost(&b->lc_host, sizeof(LayerCtl)) != cudaSuccess ||
+                      cudaMallocHost(&b->F_mirror, sizeof(double) * max_slots) != cudaSuccess ||
+                      cudaMallocHost(&b->ring_host, sizeof(uint64_t) * 4 * PEAK_RING) != cudaSuccess))
     rc = SV_E_CUDA;
+  for (int j = 0; j < 2 && rc == SV_OK; ++j)
+    if (cudaEventCreateWithFlags(&b->upload_ev[j], cudaEventDisableTiming) != cudaSuccess) rc = SV_E_CUDA;
+  for (int j = 0; j < PEAK_RING && rc == SV_OK; ++j)
+    if (cudaEventCreateWithFlags(&b->ring_ev[j], cudaEventDisableTiming) != cudaSuccess) rc = SV_E_CUDA;
   if (rc == SV_OK) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -724,6 +785,7 @@ sv_status svb_create(int max_slots, int prec, void* cuda_stream, const sv_alloca
   if (rc == SV_OK) rc = b_sort_cap(b, 4096);
   if (rc == SV_OK) rc = b_cuda(b, cudaMemsetAsync(b->ctl, 0, sizeof(Ctl), b->st), "svb_create");
   if (rc == SV_OK) rc = b_cuda(b, cudaMemsetAsync(b->lc_dev, 0, sizeof(LayerCtl), b->st), "svb_create");
+  if (rc == SV_OK) std::memset(b->lc_host, 0, sizeof(LayerCtl));
   if (rc == SV_OK) rc = b_cuda(b, cudaStreamSynchronize(b->st), "svb_create");
   if (rc != SV_OK) {
     svb_destroy(b);
@@ -766,6 +828,13 @@ sv_status svb_destroy(svb_state* b) {
   b_free(b, b->lc_dev);
   b_free(b, b->layer_part);
   b_free(b, b->layer_lb);
+  b_free(b, b->F_dev);
+  b_free(b, b->peak_part);
+  b_free(b, b->ring_dev);
+  for (int j = 0; j < 2; ++j)
+    if (b->upload_ev[j]) cudaEventDestroy(b->upload_ev[j]);
+  for (int j = 0; j < PEAK_RING; ++j)
+    if (b->ring_ev[j]) cudaEventDestroy(b->ring_ev[j]);
   for (int k = 0; k < 3; ++k)
     for (int j = 0; j < 2; ++j)
       if (b->tev[k][j]) cudaEventDestroy(b->tev[k][j]);
@@ -779,6 +848,8 @@ sv_status svb_destroy(svb_state* b) {
   if (b->bounds_host) cudaFreeHost(b->bounds_host);
   if (b->step_host) cudaFreeHost(b->step_host);
   if (b->lc_host) cudaFreeHost(b->lc_host);
+  if (b->F_mirror) cudaFreeHost(b->F_mirror);
+  if (b->ring_host) cudaFreeHost(b->ring_host);
   delete b;
   return SV_OK;
 }
@@ -803,20 +874,34 @@ sv_status svb_add(svb_state* b, int n, uint64_t K, double p, int* slot) {
   while ((1 << segbits) <= top) ++segbits;
   if (maxn + segbits > 64)
     return b_fail(b, SV_E_ARG, "svb_add: the largest n plus the slot-index bits exceed the 64-bit sort key");
-  sv_status rc = b_state_cap(b, b->N + 1);
-  if (rc != SV_OK) return rc;
-  launch_seg_append(b->keys[b->cur], b->amps[b->cur], b->probs[b->cur], b->seg[b->cur], b->N, s, b->prec, b->st);
-  rc = b_cuda(b, cudaGetLastError(), "svb_add");
-  if (rc != SV_OK) return rc;
   Slot& sl = b->slots[s];
+  if (b->layer_on) {  // appended at the end of the device-held state, no wait
+    uint64_t total = 0;
+    for (const Slot& o : b->slots) total += o.state == SLOT_FREE ? 0 : o.count_ub;
+    sv_status rc = b_state_cap(b, total + 1);
+    if (rc != SV_OK) return rc;
+    launch_seg_append_layer(b->keys, b->amps, b->probs, b->seg, b->lc_dev, b->bounds_dev, b->max_slots, b->F_dev, s,
+                            b->prec, b->st);
+    rc = b_cuda(b, cudaGetLastError(), "svb_add");
+    if (rc != SV_OK) return rc;
+    b->pending = true;
+  } else {
+    sv_status rc = b_state_cap(b, b->N + 1);
+    if (rc != SV_OK) return rc;
+    launch_seg_append(b->keys[b->cur], b->amps[b->cur], b->probs[b->cur], b->seg[b->cur], b->N, s, b->prec, b->st);
+    rc = b_cuda(b, cudaGetLastError(), "svb_add");
+    if (rc != SV_OK) return rc;
+    sl.offset = b->N;
+    b->N += 1;
+  }
   sl.state = SLOT_USED;
   sl.n = n;
   sl.K = K;
   sl.count = 1;
-  sl.offset = b->N;
+  sl.count_ub = 1;
+  sl.seq = b->next_seq++;
   sl.F = 1.0;
   for (int q = 0; q < 64; ++q) sl.order[q] = (uint8_t)q;  // sorted by the natural key at first
-  b->N += 1;
   *slot = s;
   return SV_OK;
 }
@@ -850,30 +935,44 @@ sv_status svb_step(svb_state* b, const svb_gate* gates, int count) {
     if (!is_unitary(g.m, g.U)) return b_fail(b, SV_E_NOT_UNITARY, "svb_step: U is not unitary within 1e-10");
     listed[g.slot] = i;
   }
+  const bool layer = b->layer_on;
+  // the gate table: with one launch per step the two pinned table sets
+  // alternate, and a set is rewritten once the step that read it is done
+  const int par = layer ? b->tparity : 0;
+  if (layer) {
+    sv_status rc = b_cuda(b, cudaEventSynchronize(b->upload_ev[par]), "svb_step table reuse");
+    if (rc != SV_OK) return rc;
+  }
+  SegGate* gh = b->gates_host + (size_t)par * b->max_slots;
+  uint16_t* rh = b->rank_slot_host + (size_t)par * b->max_slots;
   int top = 0, maxn = 1, mmax = 0;
-  uint64_t removed = 0;
+  uint64_t removed = 0, total = 0, cand = 0;
   bool may_truncate = false;
   for (int s = 0; s < b->max_slots; ++s) {
     const Slot& sl = b->slots[s];
-    SegGate& gt = b->gates_host[s];
+    SegGate& gt = gh[s];
+    const uint64_t cnt = layer ? sl.count_ub : sl.count;  // the host's exact count, or its bound
     if (sl.state == SLOT_FREE) {
       gt.m = -1;
       gt.K = 0;
       continue;
     }
     top = s + 1;
+    total += cnt;
     if (sl.state == SLOT_REMOVING) {
       gt.m = -1;
       gt.K = 0;
-      removed += sl.count;
+      removed += cnt;
       continue;
     }
+    const int gm = listed[s] >= 0 ? gates[listed[s]].m : 0;
+    cand += cnt << gm;
     maxn = sl.n > maxn ? sl.n : maxn;
     std::memset(&gt, 0, sizeof(SegGate));
     gt.K = sl.K;
     // a slot can exceed its K after this step only if its count times the
     // gate's expansion does
-    if ((sl.count << (listed[s] >= 0 ? gates[listed[s]].m : 0)) > sl.K) may_truncate = true;
+    if ((cnt << gm) > sl.K) may_truncate = true;
     for (int q = 0; q < 64; ++q) gt.pos[q] = q < sl.n ? sl.order[q] : 64;
     if (listed[s] < 0) {  // identity: the slot keeps its order
       gt.m = 0;
@@ -914,22 +1013,22 @@ sv_status svb_step(svb_state* b, const svb_gate* gates, int count) {
     for (int t = 0; t < g.m; ++t) gt.qs[t] = g.qubits[t];
     std::sort(gt.qs, gt.qs + g.m);
   }
-  {  // segment ranks: the used slots in buffer order (new circuits were appended at the end)
+  {  // segment ranks: the used slots in buffer order, which is their order of admission
     std::vector<std::pair<uint64_t, int>> used;
     for (int s = 0; s < top; ++s)
-      if (b->slots[s].state == SLOT_USED) used.push_back({b->slots[s].offset, s});
+      if (b->slots[s].state == SLOT_USED) used.push_back({b->slots[s].seq, s});
     std::sort(used.begin(), used.end());
     for (size_t r = 0; r < used.size(); ++r) {
-      b->gates_host[used[r].second].rank = (uint32_t)r;
-      b->rank_slot_host[r] = (uint16_t)used[r].second;
+      gh[used[r].second].rank = (uint32_t)r;
+      rh[r] = (uint16_t)used[r].second;
     }
   }
   ++b->steps;
-  const uint64_t N = b->N;
+  const uint64_t N = layer ? total : b->N;
   if (N == 0 || top == 0) {
     for (int s = 0; s < b->max_slots; ++s)
       if (b->slots[s].state == SLOT_REMOVING) b->slots[s] = Slot();
-    b->N = 0;
+    if (!layer) b->N = 0;
     return SV_OK;
   }
   const uint64_t nkeep = N - removed;
@@ -937,18 +1036,40 @@ sv_status svb_step(svb_state* b, const svb_gate* gates, int count) {
   while ((1 << segbits) <= top) ++segbits;  // every real sort key is below the drop marker
   const int shift = maxn;
   const int nbits = shift + segbits;
-  sv_status rc = b_state_cap(b, nkeep << mmax > N ? nkeep << mmax : N);
+  const uint64_t need = layer ? (cand > N ? cand : N) : (nkeep << mmax > N ? nkeep << mmax : N);
+  sv_status rc = SV_OK;
+  if (layer && b->pending && (need > b->cap || N > b->sort_cap || layer_grows(b, N, nkeep, mmax > 1 ? mmax : 1)))
+    rc = b_settle(b);  // buffers in use by steps in flight are replaced only after those steps
+  if (rc == SV_OK) rc = b_state_cap(b, need);
   if (rc == SV_OK) rc = b_sort_cap(b, N);
   if (rc != SV_OK) return rc;
+  if (layer) {
+    rc = step_layer(b, par, top, N, nkeep, shift, mmax);
+    if (rc != SV_OK) return rc;
+    for (int s = 0; s < b->max_slots; ++s) {
+      Slot& sl = b->slots[s];
+      if (sl.state == SLOT_REMOVING) {
+        sl = Slot();  // its terms are dropped by the step just enqueued
+        continue;
+      }
+      if (sl.state != SLOT_USED || s >= top) continue;
+      for (int q = 0; q < sl.n; ++q) sl.order[q] = gh[s].pos[q];
+      if (listed[s] >= 0) {  // the count after the gate's expansion and the top-k cut
+        const uint64_t grown = sl.count_ub << gates[listed[s]].m;
+        sl.count_ub = grown < sl.K ? grown : sl.K;
+      }
+    }
+    b->tparity ^= 1;
+    return SV_OK;
+  }
   bool truncated = false;
-  rc = b->layer_on ? step_layer(b, top, N, nkeep, shift, mmax, truncated)
-                   : step_kernels(b, top, N, nkeep, shift, nbits, mmax, may_truncate, truncated);
+  rc = step_kernels(b, top, N, nkeep, shift, nbits, mmax, may_truncate, truncated);
   if (rc != SV_OK) return rc;
   for (int s = 0; s < b->max_slots; ++s) {
     Slot& sl = b->slots[s];
     if (sl.state != SLOT_USED) continue;
     if (s < top)  // the segment is now sorted by this step's order
-      for (int q = 0; q < sl.n; ++q) sl.order[q] = b->gates_host[s].pos[q];
+      for (int q = 0; q < sl.n; ++q) sl.order[q] = gh[s].pos[q];
     if (s < top) {
       const uint64_t* bh = b->bounds_host + (truncated ? 2 * b->max_slots : 0);  // the state's bounds
       const uint64_t a = bh[s], e = bh[b->max_slots + s];
@@ -975,14 +1096,30 @@ sv_status svb_set_autotune(svb_state* b, int on) {
 
 sv_status svb_set_layer_kernel(svb_state* b, int on) {
   SVB_GUARD(b);
+  if ((on != 0) == b->layer_on) return SV_OK;
+  for (const Slot& sl : b->slots)
+    if (sl.state != SLOT_FREE) return b_fail(b, SV_E_STATE, "svb_set_layer_kernel: the batch must be empty");
+  sv_status rc = b_settle(b);
+  if (rc != SV_OK) return rc;
+  if (on) {  // the device takes over the bookkeeping of the (empty) state
+    b->lc_host->cur = (uint32_t)b->cur;
+    b->lc_host->n_cur = b->N;
+    rc = b_cuda(b, cudaMemcpyAsync(b->lc_dev, b->lc_host, sizeof(LayerCtl), cudaMemcpyHostToDevice, b->st),
+                "svb_set_layer_kernel");
+    if (rc == SV_OK) rc = b_cuda(b, cudaStreamSynchronize(b->st), "svb_set_layer_kernel");
+    if (rc != SV_OK) return rc;
+  }
   b->layer_on = on != 0;
   return SV_OK;
 }
 
-sv_status svb_layer_phase_times(const svb_state* b, double* ms, int cap, int* count) {
-  if (!b || !count || (cap > 0 && !ms)) return SV_E_ARG;
+sv_status svb_layer_phase_times(svb_state* b, double* ms, int cap, int* count) {
+  SVB_GUARD(b);
+  if (!count || (cap > 0 && !ms)) return b_fail(b, SV_E_ARG, "svb_layer_phase_times: bad arguments");
+  sv_status rc = b_settle(b);
+  if (rc != SV_OK) return rc;
   *count = LP_COUNT;
-  for (int i = 0; i < cap && i < LP_COUNT; ++i) ms[i] = b->layer_ms[i];
+  for (int i = 0; i < cap && i < LP_COUNT; ++i) ms[i] = 1e-6 * (double)b->lc_host->phase_ns[i];
   return SV_OK;
 }
 
@@ -1019,6 +1156,10 @@ sv_status svb_num_terms(svb_state* b, int slot, uint64_t* N) {
   SVB_GUARD(b);
   if (!N || slot < 0 || slot >= b->max_slots || b->slots[slot].state != SLOT_USED)
     return b_fail(b, SV_E_ARG, "svb_num_terms: slot not in use");
+  {
+    const sv_status rs = b_settle(b);  // after asynchronous steps: the slot's current range and mass
+    if (rs != SV_OK) return rs;
+  }
   *N = b->slots[slot].count;
   return SV_OK;
 }
@@ -1027,6 +1168,10 @@ sv_status svb_retained_mass(svb_state* b, int slot, double* F) {
   SVB_GUARD(b);
   if (!F || slot < 0 || slot >= b->max_slots || b->slots[slot].state != SLOT_USED)
     return b_fail(b, SV_E_ARG, "svb_retained_mass: slot not in use");
+  {
+    const sv_status rs = b_settle(b);  // after asynchronous steps: the slot's current range and mass
+    if (rs != SV_OK) return rs;
+  }
   *F = b->slots[slot].F;
   return SV_OK;
 }
@@ -1035,6 +1180,10 @@ sv_status svb_peak(svb_state* b, int slot, uint64_t* key, double* prob) {
   SVB_GUARD(b);
   if (!key || !prob || slot < 0 || slot >= b->max_slots || b->slots[slot].state != SLOT_USED)
     return b_fail(b, SV_E_ARG, "svb_peak: slot not in use");
+  {
+    const sv_status rs = b_settle(b);  // after asynchronous steps: the slot's current range and mass
+    if (rs != SV_OK) return rs;
+  }
   const Slot& sl = b->slots[slot];
   if (sl.count == 0) return b_fail(b, SV_E_STATE, "svb_peak: empty segment");
   // a truncation leaves no probabilities behind: recompute the segment's
@@ -1049,10 +1198,55 @@ sv_status svb_peak(svb_state* b, int slot, uint64_t* key, double* prob) {
   return SV_OK;
 }
 
+sv_status svb_peak_async(svb_state* b, int slot, uint64_t* ticket) {
+  SVB_GUARD(b);
+  if (!ticket || slot < 0 || slot >= b->max_slots || b->slots[slot].state != SLOT_USED)
+    return b_fail(b, SV_E_ARG, "svb_peak_async: slot not in use");
+  const uint64_t t = b->next_ticket;
+  const int r = (int)(t % PEAK_RING);
+  if (b->ring_ticket[r]) return b_fail(b, SV_E_STATE, "svb_peak_async: too many readouts not yet collected");
+  const Slot& sl = b->slots[slot];
+  uint64_t* out = b->ring_dev + 4 * r;
+  launch_seg_peak(b->keys, b->amps, b->prec, b->layer_on ? 1 : 0, b->lc_dev, b->bounds_dev, b->max_slots, b->F_dev,
+                  slot, sl.offset, sl.count, b->cur, sl.F, b->peak_part, out, b->st);
+  cudaMemcpyAsync(out + 3, &b->ctl->err, sizeof(uint32_t), cudaMemcpyDeviceToDevice, b->st);
+  cudaMemcpyAsync(b->ring_host + 4 * r, out, sizeof(uint64_t) * 4, cudaMemcpyDeviceToHost, b->st);
+  sv_status rc = b_cuda(b, cudaEventRecord(b->ring_ev[r], b->st), "svb_peak_async");
+  if (rc != SV_OK) return rc;
+  b->ring_ticket[r] = t + 1;
+  b->next_ticket = t + 1;
+  *ticket = t;
+  return SV_OK;
+}
+
+sv_status svb_peak_wait(svb_state* b, uint64_t ticket, uint64_t* key, double* prob, double* F) {
+  SVB_GUARD(b);
+  const int r = (int)(ticket % PEAK_RING);
+  if (!key || !prob || b->ring_ticket[r] != ticket + 1)
+    return b_fail(b, SV_E_ARG, "svb_peak_wait: not a readout in flight");
+  sv_status rc = b_cuda(b, cudaEventSynchronize(b->ring_ev[r]), "svb_peak_wait");
+  if (rc != SV_OK) return rc;
+  b->ring_ticket[r] = 0;
+  const uint64_t* h = b->ring_host + 4 * r;
+  const uint32_t err = (uint32_t)h[3];
+  if (err) {
+    b->broken = true;
+    return b_fail(b, (err & ERR_TIMEOUT) ? SV_E_TIMEOUT : SV_E_STATE, "svb_peak_wait: device state error");
+  }
+  *key = h[0];
+  std::memcpy(prob, &h[1], 8);
+  if (F) std::memcpy(F, &h[2], 8);
+  return SV_OK;
+}
+
 sv_status svb_export(svb_state* b, int slot, uint64_t* keys, double* amps, uint64_t cap, uint64_t* count) {
   SVB_GUARD(b);
   if (!count || slot < 0 || slot >= b->max_slots || b->slots[slot].state != SLOT_USED)
     return b_fail(b, SV_E_ARG, "svb_export: slot not in use");
+  {
+    const sv_status rs = b_settle(b);  // after asynchronous steps: the slot's current range and mass
+    if (rs != SV_OK) return rs;
+  }
   const Slot& sl = b->slots[slot];
   *count = sl.count;
   const uint64_t w = cap < sl.count ? cap : sl.count;

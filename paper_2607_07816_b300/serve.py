@@ -85,11 +85,14 @@ class Server:
     on a stream from solo_stream() (an object with a cuda_stream handle)."""
 
     def __init__(self, budget_bytes: int, max_slots: int = 512, n_max: int = 54, prec: int = sv.SV_C64,
-                 stream: int = 0, batch=None, solo_min_terms: int = 1 << 22, solo_stream=None):
+                 stream: int = 0, batch=None, solo_min_terms: int = 1 << 22, solo_stream=None,
+                 one_launch: Optional[bool] = None):
         self.budget = int(budget_bytes)
         self.max_slots = slot_limit(n_max, max_slots)
         self.prec = prec
         self.batch = batch if batch is not None else sv.Batch(self.max_slots, prec=prec, stream=stream)
+        if one_launch is not None:  # each step one persistent launch (steps then run ahead of the host)
+            self.batch.set_layer_kernel(one_launch)
         self.solo_min_terms = int(solo_min_terms)
         self.solo_stream = solo_stream if solo_stream is not None else _new_stream
         self.steps = 0
@@ -139,6 +142,17 @@ class Server:
         solo_finished: List = []  # (request index, Result or exception) from the solo threads
         solo_threads: List[threading.Thread] = []
         solo_running = 0
+        inflight: List = []  # (request index, readout ticket, admission time) of retired slots
+
+        def collect() -> int:
+            """Results of the readouts enqueued so far (waits for each)."""
+            got = 0
+            for j, ticket, admitted in inflight:
+                key, prob, f = self.batch.peak_wait(ticket)
+                results[j] = Result(j, key, prob, f, float(arrivals[j]), admitted, clock())
+                got += 1
+            inflight.clear()
+            return got
 
         def solo(j: int, c, admitted: float) -> None:
             try:
@@ -201,6 +215,9 @@ class Server:
                 self.peak_resident = max(self.peak_resident, len(live) + solo_running)
                 self.peak_bytes = max(self.peak_bytes, used)
                 if not live:
+                    if inflight:
+                        done += collect()
+                        continue
                     if retiring:  # an empty step frees the retired slots
                         self.batch.step([])
                         retiring = 0
@@ -234,20 +251,24 @@ class Server:
                 self.steps += 1
                 retiring = 0
                 pos += 1
+                # the readouts of the slots retired after the previous step
+                # complete while this step runs
+                done += collect()
                 for k in np.nonzero(pos == counts)[0]:
                     slot = int(slots[k])
                     j, _, admitted, _ = live[slot]
-                    key, prob = self.batch.peak(slot)
-                    f = self.batch.retained_mass(slot)
-                    ks = am = None
-                    if wants(j):
+                    if wants(j):  # read at once, with the final state
+                        key, prob = self.batch.peak(slot)
+                        f = self.batch.retained_mass(slot)
                         ks, am = self.batch.export(slot)
+                        results[j] = Result(j, key, prob, f, float(arrivals[j]), admitted, clock(), ks, am)
+                        done += 1
+                    else:  # pipelined: collected after the next step is enqueued
+                        inflight.append((j, self.batch.peak_async(slot), admitted))
                     self.batch.remove(slot)
                     retiring += 1
                     del live[slot]
                     used -= footprint(circuits[j])
-                    results[j] = Result(j, key, prob, f, float(arrivals[j]), admitted, clock(), ks, am)
-                    done += 1
                     dirty = True
                 if dirty:  # retirements: save the positions before a slot can be reused
                     for k, sl in enumerate(slots):

@@ -27,7 +27,8 @@ EXPORTED = ["sv_create", "sv_create_ex", "sv_destroy", "sv_apply_gate", "sv_trun
             "sv_last_stats", "sv_set_timing", "sv_phase_times", "sv_launch_count", "sv_transfer_bytes", "sv_peak_noalloc",
             "svb_create", "svb_destroy", "svb_add", "svb_remove", "svb_step", "svb_num_terms",
             "svb_retained_mass", "svb_peak", "svb_export", "svb_last_error", "svb_set_autotune",
-            "svb_autotune_stats", "svb_set_graphs", "svb_graph_stats", "svb_set_layer_kernel", "svb_layer_phase_times", "sv_selftest", "sv_set_apply_variant",
+            "svb_autotune_stats", "svb_set_graphs", "svb_graph_stats", "svb_set_layer_kernel", "svb_layer_phase_times", "svb_peak_async", "svb_peak_wait",
+            "sv_selftest", "sv_set_apply_variant",
             "sv_probe_fp64", "sv_select_histogram", "sv_cut", "sv_reserve"]
 PHASES = ["keys", "sort", "heads", "apply", "select", "compact", "peak", "other", "window", "local"]
 
@@ -148,6 +149,10 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.svb_set_layer_kernel.argtypes = [vp, i32]
     lib.svb_layer_phase_times.restype = i32
     lib.svb_layer_phase_times.argtypes = [vp, P(dbl), i32, P(i32)]
+    lib.svb_peak_async.restype = i32
+    lib.svb_peak_async.argtypes = [vp, i32, P(u64)]
+    lib.svb_peak_wait.restype = i32
+    lib.svb_peak_wait.argtypes = [vp, u64, P(u64), P(dbl), P(dbl)]
     lib.svb_graph_stats.restype = i32
     lib.svb_graph_stats.argtypes = [vp, P(u64), P(u64)]
     lib.sv_peak_noalloc.restype = i32
@@ -579,6 +584,20 @@ def svb_set_layer_kernel(h: int, on: bool) -> None:
     _bcheck(h, load_library().svb_set_layer_kernel(ctypes.c_void_p(h), 1 if on else 0))
 
 
+def svb_peak_async(h: int, slot: int) -> int:
+    t = ctypes.c_uint64()
+    _bcheck(h, load_library().svb_peak_async(ctypes.c_void_p(h), slot, ctypes.byref(t)))
+    return t.value
+
+
+def svb_peak_wait(h: int, ticket: int):
+    """(key, probability, retained mass) of a readout from svb_peak_async."""
+    k, p, f = ctypes.c_uint64(), ctypes.c_double(), ctypes.c_double()
+    _bcheck(h, load_library().svb_peak_wait(ctypes.c_void_p(h), ctypes.c_uint64(ticket), ctypes.byref(k),
+                                            ctypes.byref(p), ctypes.byref(f)))
+    return k.value, p.value, f.value
+
+
 LAYER_PHASES = ["setup", "keys", "counts", "offsets", "scatter", "splits", "merge", "heads", "apply",
                 "init", "pick1", "hist", "pick", "finish", "scale", "trunc"]
 
@@ -664,3 +683,9 @@ class Batch:
 
     def layer_phase_times(self):
         return svb_layer_phase_times(self.h)
+
+    def peak_async(self, slot: int) -> int:
+        return svb_peak_async(self.h, slot)
+
+    def peak_wait(self, ticket: int):
+        return svb_peak_wait(self.h, ticket)

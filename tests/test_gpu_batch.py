@@ -82,10 +82,12 @@ def test_batch_matches_oracle_per_circuit(sv, oracle_mod, prec, layer):
     b.close()
 
 
-def test_batch_slot_reuse_and_late_arrivals(sv, oracle_mod):
+@pytest.mark.parametrize("layer", [True, False], ids=["one_launch", "kernels"])
+def test_batch_slot_reuse_and_late_arrivals(sv, oracle_mod, layer):
     rng = np.random.default_rng(7)
     circs = _circuits(rng, 8)
     b = sv.Batch(4, prec=1)
+    b.set_layer_kernel(layer)
     live = {}  # slot -> (circuit index, position, oracle)
     queue = list(range(len(circs)))
     finished = 0
@@ -112,6 +114,47 @@ def test_batch_slot_reuse_and_late_arrivals(sv, oracle_mod):
                 del live[s]
                 finished += 1
         b.step([])  # frees the retired slots for the next arrivals
+    b.close()
+
+
+@pytest.mark.parametrize("layer", [True, False], ids=["one_launch", "kernels"])
+def test_pipelined_readout_after_removal(sv, oracle_mod, layer):
+    """Slots retired with svb_peak_async and removed at once, their readouts
+    collected after later steps (and adds into the freed slots) have been
+    enqueued: each gives the oracle's peak and retained mass."""
+    rng = np.random.default_rng(19)
+    circs = _circuits(rng, 9)
+    b = sv.Batch(3, prec=0)
+    b.set_layer_kernel(layer)
+    live, queue, tickets, want = {}, list(range(len(circs))), [], {}
+    while queue or live:
+        while queue and len(live) < 3:
+            j = queue.pop(0)
+            s = b.add(circs[j].n, circs[j].K)
+            live[s] = [j, 0, oracle_mod.Oracle(circs[j].n, circs[j].K, 1.0, prec=0)]
+        gates = []
+        for s, (j, p, o) in live.items():
+            q, u = circs[j].gates[p]
+            gates.append((s, q, u))
+            o.apply_gate(q, u)
+            o.truncate()
+            live[s][1] += 1
+        b.step(gates)
+        for s in list(live):
+            j, p, o = live[s]
+            if p == len(circs[j].gates):
+                tickets.append((j, b.peak_async(s)))
+                want[j] = (o.peak(), o.retained_mass())
+                b.remove(s)
+                del live[s]
+        b.step([])
+    assert len(tickets) == len(circs)
+    for j, t in tickets:
+        key, prob, f = b.peak_wait(t)
+        assert (key, prob) == want[j][0], f"circuit {j}"
+        assert f == want[j][1], f"circuit {j}"
+    with pytest.raises(sv.SVError):
+        b.peak_wait(tickets[0][1])  # collected once
     b.close()
 
 

@@ -38,17 +38,24 @@ def _as_dict(keys, amps):
 
 
 @pytest.mark.parametrize("prec", [1, 0])
-def test_alone_vs_mix(serve, oracle_mod, prec):
+@pytest.mark.parametrize("one_launch", [True, False], ids=["one_launch", "kernels"])
+def test_alone_vs_mix(serve, oracle_mod, prec, one_launch):
     circs = _requests(14, 900 + prec)
     # arrivals in steps: later requests arrive while earlier ones are resident
     arrivals = [0, 0, 1, 3, 4, 4, 7, 9, 12, 12, 15, 20, 22, 30]
     budget = 3 * max(serve.footprint(c) for c in circs)
-    srv = serve.Server(budget, max_slots=6, prec=prec)
+    srv = serve.Server(budget, max_slots=6, prec=prec, one_launch=one_launch)
     mix = srv.run(circs, arrivals=arrivals, clock=lambda: srv.steps, export=True)
     assert srv.peak_bytes <= budget and srv.peak_resident >= 2
     srv.close()
+    # the same stream with pipelined readouts (no export): the same results
+    srv = serve.Server(budget, max_slots=6, prec=prec, one_launch=one_launch)
+    piped = srv.run(circs, arrivals=arrivals, clock=lambda: srv.steps)
+    srv.close()
+    for m, q in zip(mix, piped):
+        assert (m.peak_key, m.peak_prob, m.retained_mass) == (q.peak_key, q.peak_prob, q.retained_mass)
     for j, c in enumerate(circs):
-        one = serve.Server(1 << 40, max_slots=1, prec=prec)
+        one = serve.Server(1 << 40, max_slots=1, prec=prec, one_launch=one_launch)
         alone = one.run([c], export=True)[0]
         one.close()
         m = mix[j]
