@@ -670,24 +670,38 @@ def run_batched(args, rank, dev, stream):
     s = stream.cuda_stream
     warm = [c for c in circs if c.K <= 1 << 12][:4]
     serial_c128(warm, s)
-    w = serve.Server(160 << 30, n_max=n_max, prec=sv.SV_C64, stream=s)
-    w.run(warm)
-    w.close()
+    for one_launch in (True, False):
+        w = serve.Server(160 << 30, n_max=n_max, prec=sv.SV_C64, stream=s, one_launch=one_launch)
+        w.run(warm)
+        w.close()
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     ser = serial_c128(circs, s, keep_peaked=True)  # the peaked states are read off the clock
     serial_s = time.perf_counter() - t0
-    srv = serve.Server(160 << 30, n_max=n_max, prec=sv.SV_C64, stream=s)
-    t0 = time.perf_counter()
-    res = srv.run(circs)
-    torch.cuda.synchronize(dev)
-    batched_s = time.perf_counter() - t0
-    steps = srv.steps
-    graphs = srv.batch.graph_stats()
-    srv.close()
+    # the step as one persistent launch (the default) and as separate kernels
+    forms, res = {}, None
+    for name, one_launch in (("one_launch", True), ("kernels", False)):
+        srv = serve.Server(160 << 30, n_max=n_max, prec=sv.SV_C64, stream=s, one_launch=one_launch)
+        t0 = time.perf_counter()
+        got = srv.run(circs)
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - t0
+        forms[name] = {"circuits_per_s": R / wall, "wall_s": wall, "steps": srv.steps,
+                       "graphs": srv.batch.graph_stats()}
+        if one_launch:
+            forms[name]["phases_ms"] = {k: round(v, 2) for k, v in srv.batch.layer_phase_times().items()}
+            res = got
+        else:
+            forms[name]["results_equal_to_one_launch"] = "%d/%d" % (
+                sum(int((a.peak_key, a.peak_prob, a.retained_mass) == (b.peak_key, b.peak_prob, b.retained_mass))
+                    for a, b in zip(res, got)), R)
+        srv.close()
+    batched_s = forms["one_launch"]["wall_s"]
     out = {"circuits": R, "prec": "c64 batched vs c128 serial", "serial_circuits_per_s": R / serial_s,
-           "batched_circuits_per_s": R / batched_s, "speedup": serial_s / batched_s, "steps": steps,
-           "serial_s": serial_s, "batched_s": batched_s, "graphs": graphs}
+           "batched_circuits_per_s": R / batched_s, "speedup": serial_s / batched_s,
+           "form": "one persistent launch per step (graph replay, no host wait)",
+           "steps": forms["one_launch"]["steps"], "serial_s": serial_s, "batched_s": batched_s, "forms": forms,
+           "kernels_speedup": serial_s / forms["kernels"]["wall_s"]}
     out.update(peaked_check(res, ser, circs, peaked_states_c64(circs, ser, n_max, s)))
     log = args.requests_log + "_batched.jsonl" if args.requests_log else None
     out["per_request"] = request_summary(request_table(circs, res, ser), log)

@@ -325,7 +325,7 @@ sv_status svb_autotune_stats(const svb_state* b, uint64_t* trials, uint64_t* cla
 sv_status svb_set_graphs(svb_state* b, int on);
 /* Graphs captured and graph launches so far. */
 sv_status svb_graph_stats(const svb_state* b, uint64_t* captures, uint64_t* launches);
-/* One launch per step (off by default): the whole step (sort keys, grouping,
+/* One launch per step (on by default): the whole step (sort keys, grouping,
  * group heads, mat-vec, per-slot top-k select to the exact cut,
  * renormalising compaction) runs as one persistent cooperative kernel whose
  * blocks pass grid-wide barriers between the phases, with every size read

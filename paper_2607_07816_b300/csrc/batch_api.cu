@@ -102,7 +102,7 @@ struct svb_state {
   uint64_t gen = 0;
   // the layer kernel: every step one persistent cooperative launch (with
   // the gate-table upload and the readback, one graph replay)
-  bool layer_on = false;
+  bool layer_on = true;
   int sms = 0;
   unsigned layer_grid[5] = {};  // blocks per launch by grouping width m (0: not queried yet)
   LayerStep* step_dev = nullptr;
