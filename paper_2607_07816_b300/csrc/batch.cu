@@ -1548,21 +1548,6 @@ cudaError_t layer_attrs() {
   return e;
 }
 
-// ---------------------------------------------------------------- readout
-template <typename C2>
-__global__ void k_seg_probs(const C2* __restrict__ amps, uint64_t n, uint64_t* __restrict__ probs) {
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
-    probs[i] = amp_prob_bits(amps[i]);
-}
-
-void launch_seg_probs(int prec, const void* amps, uint64_t n, uint64_t* probs, cudaStream_t st) {
-  if (n == 0) return;
-  const uint64_t blocks = (n + 255) / 256;
-  const unsigned grid = (unsigned)(blocks < 148 * 8 ? blocks : 148 * 8);
-  if (prec == 0) k_seg_probs<double2><<<grid, 256, 0, st>>>((const double2*)amps, n, probs);
-  else k_seg_probs<float2><<<grid, 256, 0, st>>>((const float2*)amps, n, probs);
-}
-
 // ---------------------------------------------------------------- layer bookkeeping
 __global__ void k_seg_append_layer(uint64_t* k0, uint64_t* k1, void* a0, void* a1, uint64_t* p0, uint64_t* p1,
                                    uint16_t* s0, uint16_t* s1, LayerCtl* lc, uint64_t* bounds, int max_slots,

@@ -188,13 +188,11 @@ void launch_segsel_finish(const uint64_t* g_buf, const uint32_t* g_bufn, const u
 void launch_segsel_scale(SegSel* sel, int slots, cudaStream_t st);
 // The compaction writes keys, amplitudes and slots; the probabilities of
 // the kept terms are not written (the next mat-vec computes its own, and a
-// readout first recomputes them with launch_seg_probs).
+// readout first recomputes them with launch_amp_probs).
 void launch_seg_truncate(int prec, const uint64_t* keys, const void* amps, const uint64_t* probs, const uint16_t* seg,
                          const uint64_t* n_dev, uint64_t n_max, const SegSel* sel, uint64_t* keys_out,
                          void* amps_out, uint16_t* seg_out, uint64_t* start, uint64_t* end, uint64_t* lookback,
                          Ctl* ctl, int cfg, cudaStream_t st);
-// probs[i] = the probability bits of amplitude i (its own precision's formula).
-void launch_seg_probs(int prec, const void* amps, uint64_t n, uint64_t* probs, cudaStream_t st);
 void launch_seg_append(uint64_t* keys, void* amps, uint64_t* probs, uint16_t* seg, uint64_t at, int slot, int prec,
                        cudaStream_t st);
 

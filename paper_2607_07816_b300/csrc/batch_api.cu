@@ -1187,7 +1187,7 @@ sv_status svb_peak(svb_state* b, int slot, uint64_t* key, double* prob) {
   const Slot& sl = b->slots[slot];
   if (sl.count == 0) return b_fail(b, SV_E_STATE, "svb_peak: empty segment");
   // a truncation leaves no probabilities behind: recompute the segment's
-  launch_seg_probs(b->prec, (const char*)b->amps[b->cur] + sl.offset * b->amp_bytes, sl.count,
+  launch_amp_probs(b->prec, (const char*)b->amps[b->cur] + sl.offset * b->amp_bytes, sl.count,
                    b->probs[b->cur] + sl.offset, b->st);
   launch_peak(b->probs[b->cur] + sl.offset, b->keys[b->cur] + sl.offset, sl.count, b->ctl, b->st);
   sv_status rc = b_sync_ctl(b, "svb_peak");
@@ -1255,7 +1255,7 @@ sv_status svb_export(svb_state* b, int slot, uint64_t* keys, double* amps, uint6
   if (rc != SV_OK) return rc;
   double* tmp = (double*)b_alloc(b, w * 16);
   if (!tmp) return b_fail(b, SV_E_NOMEM, "svb_export: staging allocation failed");
-  launch_seg_probs(b->prec, (const char*)b->amps[b->cur] + sl.offset * b->amp_bytes, w,
+  launch_amp_probs(b->prec, (const char*)b->amps[b->cur] + sl.offset * b->amp_bytes, w,
                    b->probs[b->cur] + sl.offset, b->st);
   launch_iota(b->sidx[0], w, b->st);
   launch_gather_terms(b->prec, b->sidx[0], w, b->keys[b->cur] + sl.offset,

@@ -57,6 +57,8 @@ struct Ctl {
   uint32_t sel_gated;                      // 1: select kernels decide on the device which of them run
   uint64_t kept_check;                     // terms the last truncation wrote (checked at the next wait)
   const uint64_t* nat;                     // natural-key table of the stored keys (null: keys are natural)
+  uint64_t pmax_bits;                      // largest probability (bits) the window pass saw
+  double peak_thr;                         // |component| below which a rescaled kept term cannot be the peak
 };
 
 __device__ __forceinline__ uint64_t ld_acquire(const uint64_t* p) {

@@ -260,12 +260,16 @@ uint64_t window_tiles(uint64_t n);
 // ctl->count[2]) and the lookback-free renormalising compaction.
 // The compactions leave each block's canonical best kept term in
 // peak_part[2b], peak_part[2b + 1] (probability bits, key) for blocks
-// b < *peak_blocks <= PEAK_PARTS; launch_peak_partials reduces them.
+// b < *peak_blocks <= PEAK_PARTS; launch_peak_partials reduces them.  They
+// write keys and rescaled amplitudes only: the kept terms' new
+// probabilities are computed where a term can be its block's peak, and a
+// caller that needs them all afterwards recomputes them (launch_amp_probs).
 constexpr uint32_t PEAK_PARTS = 148 * 8;
 void launch_truncate_windowed(int prec, const uint64_t* keys, const void* amps, const uint64_t* probs,
-                              uint64_t n, uint64_t* keys_out, void* amps_out, uint64_t* probs_out,
-                              const SelectScratch& ss, Ctl* ctl, cudaStream_t st, uint64_t* peak_part,
-                              uint32_t* peak_blocks);
+                              uint64_t n, uint64_t* keys_out, void* amps_out, const SelectScratch& ss, Ctl* ctl,
+                              cudaStream_t st, uint64_t* peak_part, uint32_t* peak_blocks);
+// probs[i] = the probability bits of amplitude i (its precision's formula).
+void launch_amp_probs(int prec, const void* amps, uint64_t n, uint64_t* probs, cudaStream_t st);
 
 // Sample-estimated window, one streaming pass (exact total mass, count and
 // mass above the window, window terms gathered) and the choice of the list
@@ -285,9 +289,8 @@ void launch_select_finish(Ctl* ctl, const SelectScratch& ss, double p, cudaStrea
 // Keep the terms not after the cut in canonical order, scale them by
 // ctl->scale and recompute their probabilities; count in ctl->count[2].
 void launch_truncate_compact(int prec, const uint64_t* keys, const void* amps, const uint64_t* probs,
-                             uint64_t n, uint64_t* keys_out, void* amps_out, uint64_t* probs_out,
-                             uint64_t* lookback, Ctl* ctl, cudaStream_t st, uint64_t* peak_part,
-                             uint32_t* peak_blocks);
+                             uint64_t n, uint64_t* keys_out, void* amps_out, uint64_t* lookback, Ctl* ctl,
+                             cudaStream_t st, uint64_t* peak_part, uint32_t* peak_blocks);
 void launch_peak_partials(const uint64_t* part, uint32_t n, Ctl* ctl, cudaStream_t st);
 void launch_set_scale(Ctl* ctl, cudaStream_t st);
 // Select state of one histogram level over all terms (prefix of `bits` fixed

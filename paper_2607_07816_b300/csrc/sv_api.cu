@@ -87,6 +87,7 @@ struct sv_state {
   uint64_t* peak_part = nullptr;
   uint32_t peak_blocks = 0;
   bool peak_ready = false;
+  bool probs_valid = true;  // probs[cur] holds every term's probability (a compaction leaves them stale)
   // pipelined peak readouts: results copied into a ring of pinned slots,
   // each with the event that marks its copy done
   static constexpr uint32_t PEAK_RING = 8;
@@ -342,10 +343,21 @@ sv_status sort_keys(sv_state* s, uint64_t n, int lo, int nbits, int* which, int*
   return cuda_check(s, e, "radix sort");
 }
 
+// The state's probabilities, recomputed from its amplitudes when a
+// compaction left them stale (the compactions rescale the kept terms but
+// compute new probabilities only for the peak candidates).
+void ensure_probs(sv_state* s) {
+  if (s->probs_valid) return;
+  launch_amp_probs(s->prec, s->amps[s->cur], s->N, s->probs[s->cur], s->st);
+  launched(s, PH_OTHER, 1);
+  s->probs_valid = true;
+}
+
 // Canonical order (probability descending, key ascending) of the current
 // state: the permutation ends in sidx[*which].
 sv_status canonical_perm(sv_state* s, int* which) {
   uint64_t N = s->N;
+  ensure_probs(s);
   sv_status rc = ensure_sort_cap(s, N);
   if (rc != SV_OK) return rc;
   launch_iota(s->sidx[0], N, s->st);
@@ -666,6 +678,7 @@ sv_status sv_apply_gate(sv_state* s, int m, const int* qubits, const double* U) 
       s->N = s->ctl_host->count[2];
     }
     s->total_ready = true;
+    s->probs_valid = true;  // the diagonal kernel rewrote every probability
     ++s->gate_index;
     s->stats.n_pre = s->N;
     s->stats.local_gates = s->local_gates;
@@ -844,6 +857,7 @@ sv_status sv_apply_gate(sv_state* s, int m, const int* qubits, const double* U) 
     }
   }
   ++s->gate_index;
+  s->probs_valid = true;  // every gate path writes all its outputs' probabilities
   for (int b = 0; b < s->n; ++b) s->order[b] = s->order_next[b];
   s->stats.n_pre = s->N;
   s->stats.local_gates = s->local_gates;
@@ -895,6 +909,7 @@ sv_status ensure_window_cap(sv_state* s, uint64_t N) {
 // in s->ctl_host.
 sv_status run_select(sv_state* s, int mode, uint64_t count_target, uint32_t* levels) {
   const uint64_t N = s->N;
+  ensure_probs(s);
   sv_status rc = ensure_window_cap(s, N);
   if (rc != SV_OK) return rc;
   ph_begin(s, PH_WINDOW);
@@ -1019,13 +1034,12 @@ sv_status sv_truncate(sv_state* s, uint64_t* kept, double* retained_fraction) {
       ph_begin(s, PH_COMPACT);
       if (s->ctl_host->use_window) {
         launch_truncate_windowed(s->prec, s->keys[s->cur], s->amps[s->cur], s->probs[s->cur], N,
-                                 s->keys[alt], s->amps[alt], s->probs[alt], s->ss, s->ctl, s->st, s->peak_part,
-                                 &s->peak_blocks);
+                                 s->keys[alt], s->amps[alt], s->ss, s->ctl, s->st, s->peak_part, &s->peak_blocks);
         launched(s, PH_COMPACT, 3);
       } else {
         launch_set_scale(s->ctl, s->st);
         launch_truncate_compact(s->prec, s->keys[s->cur], s->amps[s->cur], s->probs[s->cur], N,
-                                s->keys[alt], s->amps[alt], s->probs[alt], s->lookback, s->ctl, s->st, s->peak_part,
+                                s->keys[alt], s->amps[alt], s->lookback, s->ctl, s->st, s->peak_part,
                                 &s->peak_blocks);
         launched(s, PH_COMPACT, 2);
       }
@@ -1043,6 +1057,7 @@ sv_status sv_truncate(sv_state* s, uint64_t* kept, double* retained_fraction) {
       f = Sc / SN;
       s->F = s->F * f;
       s->cur = alt;
+      s->probs_valid = false;
       s->N = c;
       s->stats.kept_mass = Sc;
     }
@@ -1062,6 +1077,7 @@ sv_status sv_select_histogram(sv_state* s, uint64_t prefix_hi, uint64_t prefix_l
   if (s->N == 0) return SV_OK;
   // the histogram arrays arrive cleared (the pick of every select level
   // clears them) and are cleared again after the copy
+  ensure_probs(s);
   launch_set_select(s->ctl, prefix_hi, prefix_lo, (uint32_t)bits, s->st);
   launch_select_hist(s->probs[s->cur], s->keys[s->cur], s->N, s->ctl, s->ss, s->st);
   launched(s, PH_SELECT, 2);
@@ -1089,10 +1105,11 @@ sv_status sv_cut(sv_state* s, uint64_t z_hi, uint64_t z_lo, uint64_t sc_hi, uint
     sv_status rc = ensure_lookback(s, (N + 1023) / 1024 + 16);
     if (rc != SV_OK) return rc;
     ph_begin(s, PH_COMPACT);
+    ensure_probs(s);
     launch_set_cut(s->ctl, ~z_hi, z_lo, sc_hi, sc_lo, s->st);
     launch_set_scale(s->ctl, s->st);
     launch_truncate_compact(s->prec, s->keys[s->cur], s->amps[s->cur], s->probs[s->cur], N, s->keys[alt],
-                            s->amps[alt], s->probs[alt], s->lookback, s->ctl, s->st, s->peak_part, &s->peak_blocks);
+                            s->amps[alt], s->lookback, s->ctl, s->st, s->peak_part, &s->peak_blocks);
     ph_end(s, PH_COMPACT);
     launched(s, PH_COMPACT, 3);
     rc = sync_ctl(s, "sv_cut");
@@ -1100,6 +1117,7 @@ sv_status sv_cut(sv_state* s, uint64_t z_hi, uint64_t z_lo, uint64_t sc_hi, uint
     s->cur = alt;
     s->N = s->ctl_host->count[2];
     s->peak_ready = s->peak_blocks > 0 && s->N > 0;
+    s->probs_valid = false;
   }
   s->F = s->F * (Sc / SN);
   s->stats.n_kept = s->N;
@@ -1114,6 +1132,7 @@ void enqueue_peak(sv_state* s) {
     launch_peak_partials(s->peak_part, s->peak_blocks, s->ctl, s->st);
     launched(s, PH_PEAK, 1);
   } else {
+    ensure_probs(s);
     launch_peak(s->probs[s->cur], s->keys[s->cur], s->N, s->ctl, s->st);
     launched(s, PH_PEAK, 2);
   }
@@ -1248,6 +1267,7 @@ sv_status sv_load(sv_state* s, const uint64_t* keys, const double* amps, uint64_
   if (rc != SV_OK) return rc;
   if (N == 0) {
     s->N = 0;
+    s->probs_valid = true;
     return SV_OK;
   }
   double* tmp = (double*)dev_alloc(s, N * 16);
@@ -1273,6 +1293,7 @@ sv_status sv_load(sv_state* s, const uint64_t* keys, const double* amps, uint64_
   if (s->ctl_host->count[3] != 0) return fail(s, SV_E_ARG, "sv_load: duplicate keys");
   s->cur = alt;
   s->N = s->ctl_host->count[2];
+  s->probs_valid = true;  // written by the load's compaction
   for (int b = 0; b < 64; ++b) s->order[b] = b;  // sorted by key, stored as natural keys
   rc = upload_nat(s);
   if (rc != SV_OK) return rc;

@@ -275,6 +275,7 @@ __global__ void __launch_bounds__(SAMPLE_THREADS) k_sample_window(const uint64_t
   __shared__ int s_rank;
   const int tid = threadIdx.x;
   if (tid < 8) (&ctl->win_n)[tid] = 0;  // win_n .. below_mass_lo, summed by the window pass
+  if (tid == 8) ctl->pmax_bits = 0;     // the largest probability, taken by the window pass
   if (!total_known && tid == 0) ctl->total_mass_hi = ctl->total_mass_lo = 0;  // the pass sums the total too
   // stratified random sample: one term at a hashed offset inside each of
   // SAMPLE_N equal strata (a fixed stride would alias with the 2^m-periodic
@@ -461,7 +462,7 @@ __global__ void __launch_bounds__(WP_BLOCK, 4) k_window_pass(const uint64_t* __r
   const uint32_t lt = (1u << lane) - 1u;
   if (threadIdx.x == 0) st.n = 0;
   u128 tot = 0, above_m = 0, win_m = 0;  // WP_BELOW: above_m holds the mass below the window
-  uint64_t above_c = 0;
+  uint64_t above_c = 0, pmax = 0;
   uint32_t q_head = 0, q_n = 0;  // warp-uniform ring state
   const uint64_t tiles = (n + L::TILE - 1) / L::TILE;
   for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
@@ -472,6 +473,8 @@ __global__ void __launch_bounds__(WP_BLOCK, 4) k_window_pass(const uint64_t* __r
     uint64_t pbv[WP_ITEMS];
 #pragma unroll
     for (int j = 0; j < WP_ITEMS; ++j) pbv[j] = 32 * j < rem ? probs[e0 + 32 * j] : 0ull;  // all loads first
+#pragma unroll
+    for (int j = 0; j < WP_ITEMS; ++j) pmax = pbv[j] > pmax ? pbv[j] : pmax;  // (absent terms read as 0)
     uint32_t wmask = 0, run = 0, tile_above = 0;
     if (QUEUE) {
       // tile_above and run are warp-wide counts (the same in every lane);
@@ -591,8 +594,13 @@ __global__ void __launch_bounds__(WP_BLOCK, 4) k_window_pass(const uint64_t* __r
   above_m = warp_sum_u128(above_m);
   win_m = warp_sum_u128(win_m);
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) above_c += __shfl_xor_sync(0xffffffffu, (unsigned long long)above_c, o);
+  for (int o = 16; o > 0; o >>= 1) {
+    above_c += __shfl_xor_sync(0xffffffffu, (unsigned long long)above_c, o);
+    const uint64_t x = __shfl_xor_sync(0xffffffffu, (unsigned long long)pmax, o);
+    pmax = x > pmax ? x : pmax;
+  }
   if (lane == 0) {
+    if (pmax) atomicMax((unsigned long long*)&ctl->pmax_bits, (unsigned long long)pmax);
     if (MODE == WP_FULL) atomic_add_u128(&ctl->total_mass_hi, &ctl->total_mass_lo, tot);
     if (MODE == WP_BELOW)
       atomic_add_u128(&ctl->below_mass_hi, &ctl->below_mass_lo, above_m);
@@ -735,7 +743,15 @@ __global__ void __launch_bounds__(1024) k_tile_scan(const uint32_t* __restrict__
   if (threadIdx.x == 0) {
     s_carry = 0;
     const double sc = fx_to_double(make_u128(ctl->cut_mass_hi, ctl->cut_mass_lo));
-    ctl->scale = __ddiv_rn(1.0, __dsqrt_rn(sc));
+    const double scale = __ddiv_rn(1.0, __dsqrt_rn(sc));
+    ctl->scale = scale;
+    // the largest probability is always kept; after the rescale it is about
+    // pmax s^2, and a kept term whose larger |component| x' has
+    // 2 x'^2 (1 + eps) below that cannot be the peak (eps covers the
+    // roundings of both precisions' rescale and probability: 2^-20 for the
+    // complex64 float rescale, far above them)
+    const double pmax = __longlong_as_double((long long)ctl->pmax_bits);
+    ctl->peak_thr = __dmul_rn(__dmul_rn(__dsqrt_rn(__dmul_rn(pmax, 0.5)), scale), 1.0 - 0x1p-20);
   }
   __syncthreads();
   for (uint64_t b0 = 0; b0 < tiles; b0 += 1024 * TS_ITEMS) {
@@ -1088,6 +1104,29 @@ struct PeakRun {
   __device__ __forceinline__ uint64_t natural(const uint64_t* nat) const { return any ? natural_key(nat, k) : ~0ull; }
 };
 
+// The windowed compaction rescales every kept term but needs the new
+// probability only of terms that can be the peak: with the largest
+// probability pmax (always kept) taken by the window pass, a term whose
+// larger |component| after the rescale lies below peak_thr (about
+// sqrt(pmax / 2) s, see k_tile_scan) is less probable than that term.  The
+// test is one integer compare on the component bits, so whole warps skip
+// the FP64 work together (the threshold is the same in every lane).
+__device__ __forceinline__ uint64_t peak_abs_bits(double2 a) {
+  const uint64_t x = (uint64_t)__double_as_longlong(a.x) & 0x7fffffffffffffffull;
+  const uint64_t y = (uint64_t)__double_as_longlong(a.y) & 0x7fffffffffffffffull;
+  return x > y ? x : y;
+}
+__device__ __forceinline__ uint64_t peak_abs_bits(float2 a) {
+  const uint32_t x = __float_as_uint(a.x) & 0x7fffffffu, y = __float_as_uint(a.y) & 0x7fffffffu;
+  return x > y ? x : y;
+}
+// peak_thr as bits of the amplitude's precision (rounded down for float).
+template <typename C2>
+__device__ __forceinline__ uint64_t peak_thr_bits(double t) {
+  if (sizeof(C2) == sizeof(double2)) return (uint64_t)__double_as_longlong(t);
+  return (uint64_t)__float_as_uint(__double2float_rd(t));
+}
+
 // Block-wide best of (bp, bk) into out[0] (probability bits), out[1] (key);
 // all threads must call it.
 __device__ void block_peak_write(uint64_t bp, uint64_t bk, uint64_t* out) {
@@ -1184,8 +1223,8 @@ constexpr int TC_BLOCK = 256, TC_ITEMS = 8;
 template <typename C2>
 __global__ void __launch_bounds__(TC_BLOCK) k_truncate_compact(
     const uint64_t* __restrict__ keys, const C2* __restrict__ amps, const uint64_t* __restrict__ probs,
-    uint64_t n, uint64_t* __restrict__ keys_out, C2* __restrict__ amps_out,
-    uint64_t* __restrict__ probs_out, uint64_t* lookback, Ctl* ctl, uint64_t* __restrict__ peak_part) {
+    uint64_t n, uint64_t* __restrict__ keys_out, C2* __restrict__ amps_out, uint64_t* lookback, Ctl* ctl,
+    uint64_t* __restrict__ peak_part) {
   typedef TileLayout<TC_BLOCK, TC_ITEMS> L;
   PeakRun best;
   __shared__ CompactShared<TC_BLOCK> cs;
@@ -1218,11 +1257,10 @@ __global__ void __launch_bounds__(TC_BLOCK) k_truncate_compact(
         const uint64_t i = L::index(base, j);
         const uint64_t o = cs.tile_base_out + pos[j];
         const C2 a = amp_scaled(amps[i], s);
-        const uint64_t k = keys[i], pb = amp_prob_bits(a);
+        const uint64_t k = keys[i];
         keys_out[o] = k;
         amps_out[o] = a;
-        probs_out[o] = pb;
-        best.take(pb, k, ctl->nat);
+        best.take(amp_prob_bits(a), k, ctl->nat);
       }
     }
     if (tile == tiles - 1 && threadIdx.x == 0) ctl->count[2] = cs.tile_base_out + cs.tile_total;
@@ -1240,13 +1278,14 @@ template <typename C2>
 __global__ void __launch_bounds__(WP_BLOCK) k_truncate_write(
     const uint64_t* __restrict__ keys, const C2* __restrict__ amps, const uint32_t* __restrict__ keep_bits,
     uint64_t n, const uint64_t* __restrict__ tile_off, uint64_t* __restrict__ keys_out,
-    C2* __restrict__ amps_out, uint64_t* __restrict__ probs_out, const Ctl* ctl, uint64_t* __restrict__ peak_part) {
+    C2* __restrict__ amps_out, const Ctl* ctl, uint64_t* __restrict__ peak_part) {
   pdl_prologue();
   typedef TileLayout<WP_BLOCK, WP_ITEMS> L;
   __shared__ CompactShared<WP_BLOCK> cs;
   __shared__ uint16_t s_list[WP_TILE];
   PeakRun best;
   const double s = ctl->scale;
+  const uint64_t thr = peak_thr_bits<C2>(ctl->peak_thr);
   const uint64_t* nat = ctl->nat;
   const int lane = threadIdx.x & 31;
   const uint64_t tiles = (n + L::TILE - 1) / L::TILE;
@@ -1290,11 +1329,9 @@ __global__ void __launch_bounds__(WP_BLOCK) k_truncate_write(
         const uint32_t t = t0 + u * WP_BLOCK;
         if (t < kept) {
           const C2 y = amp_scaled(a[u], s);
-          const uint64_t pb = amp_prob_bits(y);
           keys_out[ob + t] = k[u];
           amps_out[ob + t] = y;
-          probs_out[ob + t] = pb;
-          best.take(pb, k[u], nat);
+          if (peak_abs_bits(y) >= thr) best.take(amp_prob_bits(y), k[u], nat);
         }
       }
     }
@@ -1304,8 +1341,7 @@ __global__ void __launch_bounds__(WP_BLOCK) k_truncate_write(
 }
 
 void launch_truncate_windowed(int prec, const uint64_t* keys, const void* amps, const uint64_t* probs,
-                              uint64_t n, uint64_t* keys_out, void* amps_out, uint64_t* probs_out,
-                              const SelectScratch& ss, Ctl* ctl, cudaStream_t st, uint64_t* peak_part,
+                              uint64_t n, uint64_t* keys_out, void* amps_out, const SelectScratch& ss, Ctl* ctl, cudaStream_t st, uint64_t* peak_part,
                               uint32_t* peak_blocks) {
   (void)probs;  // the keep flags replace the probabilities here
   const uint64_t tiles = window_tiles(n);
@@ -1316,15 +1352,14 @@ void launch_truncate_windowed(int prec, const uint64_t* keys, const void* amps, 
   *peak_blocks = (uint32_t)grid;
   if (prec == 0)
     launch_pdl(k_truncate_write<double2>, (unsigned)grid, WP_BLOCK, 0, st, keys, (const double2*)amps, ss.keep_bits,
-               n, ss.tile_off, keys_out, (double2*)amps_out, probs_out, ctl, peak_part);
+               n, ss.tile_off, keys_out, (double2*)amps_out, ctl, peak_part);
   else
     launch_pdl(k_truncate_write<float2>, (unsigned)grid, WP_BLOCK, 0, st, keys, (const float2*)amps, ss.keep_bits,
-               n, ss.tile_off, keys_out, (float2*)amps_out, probs_out, ctl, peak_part);
+               n, ss.tile_off, keys_out, (float2*)amps_out, ctl, peak_part);
 }
 
 void launch_truncate_compact(int prec, const uint64_t* keys, const void* amps, const uint64_t* probs,
-                             uint64_t n, uint64_t* keys_out, void* amps_out, uint64_t* probs_out,
-                             uint64_t* lookback, Ctl* ctl, cudaStream_t st, uint64_t* peak_part,
+                             uint64_t n, uint64_t* keys_out, void* amps_out, uint64_t* lookback, Ctl* ctl, cudaStream_t st, uint64_t* peak_part,
                              uint32_t* peak_blocks) {
   uint64_t tiles = (n + TC_BLOCK * TC_ITEMS - 1) / (TC_BLOCK * TC_ITEMS);
   cudaMemsetAsync(lookback, 0, sizeof(uint64_t) * (tiles + 1), st);
@@ -1336,10 +1371,25 @@ void launch_truncate_compact(int prec, const uint64_t* keys, const void* amps, c
   *peak_blocks = (uint32_t)grid;
   if (prec == 0)
     k_truncate_compact<double2><<<(unsigned)grid, TC_BLOCK, 0, st>>>(
-        keys, (const double2*)amps, probs, n, keys_out, (double2*)amps_out, probs_out, lookback, ctl, peak_part);
+        keys, (const double2*)amps, probs, n, keys_out, (double2*)amps_out, lookback, ctl, peak_part);
   else
     k_truncate_compact<float2><<<(unsigned)grid, TC_BLOCK, 0, st>>>(
-        keys, (const float2*)amps, probs, n, keys_out, (float2*)amps_out, probs_out, lookback, ctl, peak_part);
+        keys, (const float2*)amps, probs, n, keys_out, (float2*)amps_out, lookback, ctl, peak_part);
+}
+
+// ---------------------------------------------------------------- probabilities
+template <typename C2>
+__global__ void k_amp_probs(const C2* __restrict__ amps, uint64_t n, uint64_t* __restrict__ probs) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    probs[i] = amp_prob_bits(amps[i]);
+}
+
+void launch_amp_probs(int prec, const void* amps, uint64_t n, uint64_t* probs, cudaStream_t st) {
+  if (n == 0) return;
+  const uint64_t blocks = (n + 255) / 256;
+  const unsigned grid = (unsigned)(blocks < 148 * 8 ? blocks : 148 * 8);
+  if (prec == 0) k_amp_probs<double2><<<grid, 256, 0, st>>>((const double2*)amps, n, probs);
+  else k_amp_probs<float2><<<grid, 256, 0, st>>>((const float2*)amps, n, probs);
 }
 
 // ---------------------------------------------------------------- peak
