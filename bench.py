@@ -234,7 +234,9 @@ def account_step(tot, q, kind, s1, s2, prec, n_bits):
     cut = n_kept < n_pre
     if cut:
         tot["cuts"] += 1
-        tot["compact_bytes"] += n_pre / 8 + (8 + sa) * n_kept + (16 + sa) * n_kept
+        # keep flags, the kept terms' keys and amplitudes read and written
+        # (the compaction writes no probabilities)
+        tot["compact_bytes"] += n_pre / 8 + 2 * (8 + sa) * n_kept
     # gate-level model (SURVEY-style B_method): group 2 S N_in, mat-vec S (N_in + N_pre),
     # select 8 N_pre and compaction S (N_pre + N_kept) when a cut is made
     b = 2 * S * n_in + S * (n_in + n_pre)
@@ -253,11 +255,11 @@ def phase_bytes(ph, tot):
 def attainable_ms(tot, bw_gbs, fp64_tflops):
     """The steps' time if every phase ran at its own roof: the larger of its
     algorithmic bytes over the HBM bandwidth and its FP64 work over the
-    measured FP64 rate (the gate's mat-vec; the compaction's rescale and
-    probability: 4 FP64 operations per kept term), summed over the phases."""
+    measured FP64 rate (the gate's mat-vec; the compaction's rescale: 2 FP64
+    multiplies per kept term), summed over the phases."""
     bw, f = bw_gbs * 1e9, fp64_tflops * 1e12
     t = max(tot["apply_bytes"] / bw, tot["fp64_apply"] / f)
-    t += max(tot["compact_bytes"] / bw, 8.0 * tot["n_kept"] / f)
+    t += max(tot["compact_bytes"] / bw, 4.0 * tot["n_kept"] / f)
     t += (tot["sort_bytes"] + tot["heads_bytes"] + tot["window_bytes"] + 16 * tot["window_terms"]) / bw
     return 1e3 * t
 

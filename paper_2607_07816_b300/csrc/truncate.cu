@@ -473,8 +473,13 @@ __global__ void __launch_bounds__(WP_BLOCK, 4) k_window_pass(const uint64_t* __r
     uint64_t pbv[WP_ITEMS];
 #pragma unroll
     for (int j = 0; j < WP_ITEMS; ++j) pbv[j] = 32 * j < rem ? probs[e0 + 32 * j] : 0ull;  // all loads first
+    // the largest probability: with a top-K window (the cut inside it, so
+    // the maximum is above it or in it) from the queued above-window terms
+    // and the window terms only, else from every term (absent ones read 0)
+    if (MODE != WP_ABOVE) {
 #pragma unroll
-    for (int j = 0; j < WP_ITEMS; ++j) pmax = pbv[j] > pmax ? pbv[j] : pmax;  // (absent terms read as 0)
+      for (int j = 0; j < WP_ITEMS; ++j) pmax = pbv[j] > pmax ? pbv[j] : pmax;
+    }
     uint32_t wmask = 0, run = 0, tile_above = 0;
     if (QUEUE) {
       // tile_above and run are warp-wide counts (the same in every lane);
@@ -497,7 +502,9 @@ __global__ void __launch_bounds__(WP_BLOCK, 4) k_window_pass(const uint64_t* __r
         q_n += __popc(qb);
         if (q_n >= 32) {  // a full warp of queued terms: one conversion each
           __syncwarp();
-          above_m += fx_from_bits(s_aq[warp][(q_head + lane) & 63u], &ctl->err);
+          const uint64_t qp = s_aq[warp][(q_head + lane) & 63u];
+          above_m += fx_from_bits(qp, &ctl->err);
+          if (MODE == WP_ABOVE) pmax = qp > pmax ? qp : pmax;
           __syncwarp();
           q_head = (q_head + 32) & 63u;
           q_n -= 32;
@@ -568,6 +575,7 @@ __global__ void __launch_bounds__(WP_BLOCK, 4) k_window_pass(const uint64_t* __r
       wrun += __popc(b);
       if (inwin) {
         const uint64_t i = e0 + 32 * j;
+        if (MODE == WP_ABOVE) pmax = pbv[j] > pmax ? pbv[j] : pmax;
         if (direct) {
           if (MODE == WP_BELOW) win_m += fx_from_bits(pbv[j], &ctl->err);
           const uint64_t o = s_direct + wpos;
@@ -588,7 +596,11 @@ __global__ void __launch_bounds__(WP_BLOCK, 4) k_window_pass(const uint64_t* __r
   window_flush<MODE == WP_BELOW>(st, ctl, wp, wi, cap, win_m);
   if (QUEUE) {  // the queue's rest
     __syncwarp();
-    if ((uint32_t)lane < q_n) above_m += fx_from_bits(s_aq[warp][(q_head + lane) & 63u], &ctl->err);
+    if ((uint32_t)lane < q_n) {
+      const uint64_t qp = s_aq[warp][(q_head + lane) & 63u];
+      above_m += fx_from_bits(qp, &ctl->err);
+      if (MODE == WP_ABOVE) pmax = qp > pmax ? qp : pmax;
+    }
   }
   tot = warp_sum_u128(tot);
   above_m = warp_sum_u128(above_m);
