@@ -335,19 +335,26 @@ def main(argv=None) -> None:
     ap.add_argument("--prec", choices=["c64", "c128"], default="c64")
     ap.add_argument("--budget-gb", type=float, default=160.0)
     ap.add_argument("--max-steps", type=int, default=None)
+    ap.add_argument("--form", choices=["one_launch", "kernels"], default="one_launch",
+                    help="the batched step as one persistent launch, or as separate kernels")
+    ap.add_argument("--no-autotune", action="store_true", help="fixed launch shapes (separate kernels)")
     a = ap.parse_args(argv)
     reqs = [C.serving_request(j, seed=a.seed, large_frac=a.large_frac, k_range=(a.k_min, a.k_max))
             for j in range(a.requests)]
     arrivals = poisson_arrivals(len(reqs), a.rate, a.seed) if a.rate > 0 else None
     srv = Server(int(a.budget_gb * (1 << 30)), n_max=max(c.n for c in reqs),
-                 prec=sv.SV_C64 if a.prec == "c64" else sv.SV_C128)
+                 prec=sv.SV_C64 if a.prec == "c64" else sv.SV_C128, one_launch=a.form == "one_launch")
+    if a.no_autotune:
+        srv.batch.set_autotune(False)
     t0 = time.perf_counter()
     res = srv.run(reqs, arrivals=arrivals, max_steps=a.max_steps)
     wall = time.perf_counter() - t0
     fin = [r for r in res if r is not None]
     out = {"requests": len(reqs), "finished": len(fin), "steps": srv.steps, "wall_s": wall,
            "circuits_per_s": len(fin) / wall if wall > 0 else None, "max_resident": srv.peak_resident,
-           "graphs": srv.batch.graph_stats(), "autotune": srv.batch.autotune_stats()}
+           "graphs": srv.batch.graph_stats(), "autotune": srv.batch.autotune_stats(), "form": a.form}
+    if a.form == "one_launch":
+        out["layer_phases_ms"] = {k: round(v, 3) for k, v in srv.batch.layer_phase_times().items()}
     if fin:
         lat = np.array([r.latency for r in fin])
         out.update({"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99))})
