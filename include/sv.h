@@ -308,10 +308,13 @@ sv_status svb_export(svb_state* b, int slot, uint64_t* keys, double* amps, uint6
 const char* svb_last_error(const svb_state* b);
 /* Autotuning of the step's launch shapes (on by default): for every class of
  * step (kernel, precision, widest gate of the step, floor(log2) of the term
- * count) each candidate shape of the group mat-vec (groups per thread), the
- * select scan and the compaction (blocks per SM) is timed twice on live steps
- * with CUDA events, then the fastest is kept.  Every shape computes the same
- * result.  Off: fixed default shapes. */
+ * count) each candidate shape is timed twice on live steps with CUDA events,
+ * then the fastest is kept: with one launch per step, the layer kernel's
+ * blocks per SM (the most that fit, or one or two fewer; a launch's time is
+ * read once the step after next reuses its table set, so tuning adds no
+ * wait); with separate kernels, the group mat-vec's groups per thread and the
+ * select scan's and the compaction's blocks per SM.  Every shape computes the
+ * same result.  Off: fixed default shapes. */
 sv_status svb_set_autotune(svb_state* b, int on);
 /* Timed trials so far, step classes seen, and classes whose every shape has
  * been timed (the tuner has settled them). */

@@ -104,7 +104,13 @@ struct svb_state {
   // the gate-table upload and the readback, one graph replay)
   bool layer_on = true;
   int sms = 0;
-  unsigned layer_grid[5] = {};  // blocks per launch by grouping width m (0: not queried yet)
+  int layer_per_sm[5] = {};     // most co-resident blocks per SM by grouping width m (0: not queried yet)
+  // autotuning of the layer kernel's blocks per SM: a step's launch is timed
+  // with events that are read when its table set is reused (two steps on)
+  cudaEvent_t lev[2][2] = {};
+  uint64_t lev_key[2] = {};
+  int lev_cfg[2] = {}, lev_shapes[2] = {};
+  bool lev_pending[2] = {};
   LayerStep* step_dev = nullptr;
   LayerStep* step_host = nullptr;
   LayerCtl* lc_dev = nullptr;
@@ -313,7 +319,7 @@ sv_status b_layer_cap(svb_state* b, uint64_t N, uint64_t nkeep, int mmax) {
   return SV_OK;
 }
 
-enum TuneKernel { TK_APPLY = 0, TK_SELECT = 1, TK_TRUNC = 2 };
+enum TuneKernel { TK_APPLY = 0, TK_SELECT = 1, TK_TRUNC = 2, TK_LAYER = 3 };
 
 uint64_t tune_key(int kernel, int prec, int mmax, uint64_t n) {
   const int sclass = n ? 63 - __builtin_clzll(n) : 0;
@@ -630,13 +636,20 @@ static sv_status step_layer(svb_state* b, int par, int top, uint64_t N, uint64_t
   const int m = mmax > 1 ? mmax : 1;
   sv_status rc = b_layer_cap(b, N, nkeep, m);
   if (rc != SV_OK) return rc;
-  if (!b->layer_grid[m]) {
+  if (!b->layer_per_sm[m]) {
     unsigned g = 0;
     rc = b_cuda(b, seg_layer_grid(b->prec, m, b->sms, &g), "svb_step layer occupancy");
     if (rc != SV_OK) return rc;
-    b->layer_grid[m] = g;
+    b->layer_per_sm[m] = (int)(g / (unsigned)b->sms);
   }
-  const unsigned grid = b->layer_grid[m];
+  // blocks per SM: the most that fit, or one or two fewer (more shared
+  // memory and cache per block), chosen by timing live steps of each class
+  const int most = b->layer_per_sm[m];
+  const int shapes = most < 3 ? most : 3;
+  const uint64_t tkey = tune_key(TK_LAYER, b->prec, m, N);
+  const int cfg = tune_pick(b, tkey, shapes, 0);
+  const bool timing = b->autotune && !tune_settled(b, tkey, shapes);
+  const unsigned grid = (unsigned)((most - cfg) * b->sms);
   LayerStep* sh = b->step_host + par;
   sh->shift = shift;
   sh->top = top;
@@ -681,6 +694,7 @@ static sv_status step_layer(svb_state* b, int par, int top, uint64_t N, uint64_t
   P.start_tr = b->bounds_dev + 2 * b->max_slots;
   P.end_tr = b->bounds_dev + 3 * b->max_slots;
   const std::array<uint64_t, 12> key = {2, (uint64_t)top, (uint64_t)m, (uint64_t)par, b->gen, grid, 0, 0, 0, 0, 0, 0};
+  if (timing) cudaEventRecord(b->lev[par][0], b->st);
   rc = run_part(b, true, key, [&]() -> sv_status {
     cudaMemcpyAsync(b->gates_dev, gh, sizeof(SegGate) * top, cudaMemcpyHostToDevice, b->st);
     cudaMemcpyAsync(b->rank_slot_dev, rh, sizeof(uint16_t) * top, cudaMemcpyHostToDevice, b->st);
@@ -690,6 +704,13 @@ static sv_status step_layer(svb_state* b, int par, int top, uint64_t N, uint64_t
     return SV_OK;
   });
   if (rc != SV_OK) return rc;
+  if (timing) {
+    cudaEventRecord(b->lev[par][1], b->st);
+    b->lev_key[par] = tkey;
+    b->lev_cfg[par] = cfg;
+    b->lev_shapes[par] = shapes;
+    b->lev_pending[par] = true;
+  }
   rc = b_cuda(b, cudaEventRecord(b->upload_ev[par], b->st), "svb_step");
   if (rc != SV_OK) return rc;
   b->pending = true;
@@ -769,7 +790,9 @@ sv_status svb_create(int max_slots, int prec, void* cuda_stream, const sv_alloca
                       cudaMallocHost(&b->ring_host, sizeof(uint64_t) * 4 * PEAK_RING) != cudaSuccess))
     rc = SV_E_CUDA;
   for (int j = 0; j < 2 && rc == SV_OK; ++j)
-    if (cudaEventCreateWithFlags(&b->upload_ev[j], cudaEventDisableTiming) != cudaSuccess) rc = SV_E_CUDA;
+    if (cudaEventCreateWithFlags(&b->upload_ev[j], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreate(&b->lev[j][0]) != cudaSuccess || cudaEventCreate(&b->lev[j][1]) != cudaSuccess)
+      rc = SV_E_CUDA;
   for (int j = 0; j < PEAK_RING && rc == SV_OK; ++j)
     if (cudaEventCreateWithFlags(&b->ring_ev[j], cudaEventDisableTiming) != cudaSuccess) rc = SV_E_CUDA;
   if (rc == SV_OK) {
@@ -831,8 +854,11 @@ sv_status svb_destroy(svb_state* b) {
   b_free(b, b->F_dev);
   b_free(b, b->peak_part);
   b_free(b, b->ring_dev);
-  for (int j = 0; j < 2; ++j)
+  for (int j = 0; j < 2; ++j) {
     if (b->upload_ev[j]) cudaEventDestroy(b->upload_ev[j]);
+    for (int k = 0; k < 2; ++k)
+      if (b->lev[j][k]) cudaEventDestroy(b->lev[j][k]);
+  }
   for (int j = 0; j < PEAK_RING; ++j)
     if (b->ring_ev[j]) cudaEventDestroy(b->ring_ev[j]);
   for (int k = 0; k < 3; ++k)
@@ -942,6 +968,13 @@ sv_status svb_step(svb_state* b, const svb_gate* gates, int count) {
   if (layer) {
     sv_status rc = b_cuda(b, cudaEventSynchronize(b->upload_ev[par]), "svb_step table reuse");
     if (rc != SV_OK) return rc;
+    if (b->lev_pending[par]) {  // that step (two steps back) is done: its launch time is known
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, b->lev[par][0], b->lev[par][1]) == cudaSuccess)
+        tune_record(b, b->lev_key[par], b->lev_shapes[par], b->lev_cfg[par], ms);
+      cudaGetLastError();
+      b->lev_pending[par] = false;
+    }
   }
   SegGate* gh = b->gates_host + (size_t)par * b->max_slots;
   uint16_t* rh = b->rank_slot_host + (size_t)par * b->max_slots;

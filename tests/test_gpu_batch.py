@@ -229,6 +229,10 @@ def test_autotuned_shapes_give_identical_results(sv):
     assert tstats["trials"] == 0
     assert tstats2["trials"] > 0 and tstats2["classes"] > 0
     _same(fixed, tuned)
+    # the one-launch step tunes its blocks per SM (timings read two steps on)
+    layer, (tstats3, _) = _run_batch(sv, circs, tune=True, graphs=True, layer=True)
+    assert tstats3["trials"] > 0 and tstats3["classes"] > 0
+    _same(fixed, layer)
 
 
 def test_graph_replay_gives_identical_results(sv):
