@@ -310,9 +310,9 @@ const char* svb_last_error(const svb_state* b);
  * step (kernel, precision, widest gate of the step, floor(log2) of the term
  * count) each candidate shape is timed twice on live steps with CUDA events,
  * then the fastest is kept: with one launch per step, the layer kernel's
- * blocks per SM (the most that fit, or one or two fewer; a launch's time is
- * read once the step after next reuses its table set, so tuning adds no
- * wait); with separate kernels, the group mat-vec's groups per thread and the
+ * blocks per SM (the most that fit, or one fewer; classes by the term count
+ * in factors of 4; a launch's time is read once the step after next reuses
+ * its table set, so tuning adds no wait); with separate kernels, the group mat-vec's groups per thread and the
  * select scan's and the compaction's blocks per SM.  Every shape computes the
  * same result.  Off: fixed default shapes. */
 sv_status svb_set_autotune(svb_state* b, int on);

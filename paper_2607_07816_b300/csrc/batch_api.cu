@@ -642,11 +642,12 @@ static sv_status step_layer(svb_state* b, int par, int top, uint64_t N, uint64_t
     if (rc != SV_OK) return rc;
     b->layer_per_sm[m] = (int)(g / (unsigned)b->sms);
   }
-  // blocks per SM: the most that fit, or one or two fewer (more shared
-  // memory and cache per block), chosen by timing live steps of each class
+  // blocks per SM: the most that fit, or one fewer (more shared memory and
+  // cache per block), chosen by timing live steps of each class (term
+  // counts by factors of 4: few classes, so little of a run goes to trials)
   const int most = b->layer_per_sm[m];
-  const int shapes = most < 3 ? most : 3;
-  const uint64_t tkey = tune_key(TK_LAYER, b->prec, m, N);
+  const int shapes = most < 2 ? most : 2;
+  const uint64_t tkey = tune_key(TK_LAYER, b->prec, m, N ? 1ull << ((63 - __builtin_clzll(N)) & ~1) : 0);
   const int cfg = tune_pick(b, tkey, shapes, 0);
   const bool timing = b->autotune && !tune_settled(b, tkey, shapes);
   const unsigned grid = (unsigned)((most - cfg) * b->sms);
