@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def declared_symbols():
     text = open(os.path.join(ROOT, "include", "sv.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(sv_[a-z_0-9]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(svb?_[a-z_0-9]+)\s*\(", text)))
 
 
 @pytest.fixture(scope="module")
@@ -25,7 +25,8 @@ def test_header_declares_the_boundary():
     syms = declared_symbols()
     for name in ["sv_create", "sv_create_ex", "sv_destroy", "sv_apply_gate", "sv_truncate",
                  "sv_peak", "sv_probs", "sv_num_terms", "sv_retained_mass", "sv_export", "sv_load",
-                 "sv_last_error"]:
+                 "sv_last_error", "svb_create", "svb_add", "svb_step", "svb_peak", "svb_peak_async",
+                 "svb_peak_wait", "svb_set_layer_kernel"]:
         assert name in syms
 
 
