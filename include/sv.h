@@ -256,7 +256,11 @@ void sv_transfer_bytes(uint64_t* h2d, uint64_t* d2h);
  * grouping sort, one mat-vec pass and one segmented select per step; each
  * slot's result is the one the single-state path gives for the same gates.
  * Gate conventions are those of sv_apply_gate.  Calls enqueue on the
- * handle's stream and synchronise before returning.
+ * handle's stream.  With one launch per step (the default, see
+ * svb_set_layer_kernel) svb_step and svb_add return without waiting for
+ * the device and svb_peak_async / svb_peak_wait read results pipelined;
+ * the calls that report on a slot wait for the work enqueued before them.
+ * With separate kernels every call synchronises before returning.
  * ------------------------------------------------------------------- */
 typedef struct svb_state svb_state;
 typedef struct {

@@ -1087,10 +1087,9 @@ void launch_select_finish(Ctl* ctl, const SelectScratch& ss, double p, cudaStrea
 }
 
 // ---------------------------------------------------------------- peak partials
-// The compactions write every kept term's final probability, so they also
-// keep each block's canonical best term (probability bits larger, then key
-// smaller): the peak readout after a truncation reduces these partials
-// instead of reading the state again.
+// The compactions keep each block's canonical best kept term (probability
+// bits larger, then key smaller), so the peak readout after a truncation
+// reduces these partials instead of reading the state again.
 __device__ __forceinline__ void peak_take(uint64_t& bp, uint64_t& bk, uint64_t p, uint64_t k) {
   if (p > bp || (p == bp && k < bk)) {
     bp = p;
