@@ -244,7 +244,7 @@ template <typename Real, int MAXD, int GPT>
 __device__ __forceinline__ void seg_apply_run(
     const uint64_t* __restrict__ sk, const uint32_t* __restrict__ sidx, uint64_t n,
     const uint32_t* __restrict__ heads, const typename SCplx<Real>::T* __restrict__ amps_in, int shift,
-    const SegGate* __restrict__ gates, const uint16_t* __restrict__ rank_slot, const uint64_t* __restrict__ tables,
+    const SegGate* __restrict__ gates, const uint16_t* __restrict__ rank_slot, const uint64_t* __restrict__ keys_in,
     uint64_t* __restrict__ keys_out,
     typename SCplx<Real>::T* __restrict__ amps_out, uint64_t* __restrict__ probs_out,
     uint16_t* __restrict__ seg_out, uint32_t* __restrict__ hist1, uint64_t* __restrict__ start,
@@ -286,7 +286,7 @@ __device__ __forceinline__ void seg_apply_run(
     // the loads of the GPT groups are issued together, level by level
     // (heads, first sort key and index, first amplitude): most groups of a
     // truncated state have a single member
-    uint64_t hb[GPT + 1], s0v[GPT];
+    uint64_t hb[GPT + 1], s0v[GPT], k0v[GPT];
     C2 x0v[GPT];
 #pragma unroll
     for (int j = 0; j <= GPT; ++j) {
@@ -299,6 +299,7 @@ __device__ __forceinline__ void seg_apply_run(
       s0v[j] = ok ? sk[hb[j]] : 0ull;
       const uint32_t ix = ok ? sidx[hb[j]] : 0u;
       x0v[j] = ok ? amps_in[ix] : C2();
+      k0v[j] = ok ? keys_in[ix] : 0ull;  // the head member's natural key
     }
 #pragma unroll
     for (int j = 0; j < GPT; ++j) {
@@ -340,11 +341,15 @@ __device__ __forceinline__ void seg_apply_run(
 #pragma unroll
       for (int ro = 0; ro < MAXD; ++ro)
         if (ro < d && !(yr[j][ro] == (Real)0 && yi[j][ro] == (Real)0)) keep[j] |= 1u << ro;
-      for (int t = 0; t < m; ++t) qpack[j] |= (uint32_t)gt.q[t] << (8 * t);
+      uint64_t qmask = 0;
+      for (int t = 0; t < m; ++t) {
+        qpack[j] |= (uint32_t)gt.q[t] << (8 * t);
+        qmask |= 1ull << gt.q[t];
+      }
       mj[j] = m;
-      // the group's natural key without the gate bits: its sort key with the
-      // bottom m bits cleared, mapped back through the slot's inverse table
-      rest[j] = nibble_map(tables + (uint64_t)sg * SEG_TABLE_WORDS + 256, (s0 & low_mask(shift)) >> m << m);
+      // the group's natural key without the gate bits: any member's natural
+      // key (the batched state keeps natural keys) with the gate bits cleared
+      rest[j] = k0v[j] & ~qmask;
       sgj[j] = (uint16_t)sg;
       cnt += __popc(keep[j]);
     }
@@ -436,7 +441,7 @@ template <typename Real, int MAXD, int GPT>
 __global__ void __launch_bounds__(SA_BLOCK) k_seg_apply(
     const uint64_t* __restrict__ sk, const uint32_t* __restrict__ sidx, uint64_t n,
     const uint32_t* __restrict__ heads, const typename SCplx<Real>::T* __restrict__ amps_in, int shift,
-    const SegGate* __restrict__ gates, const uint16_t* __restrict__ rank_slot, const uint64_t* __restrict__ tables,
+    const SegGate* __restrict__ gates, const uint16_t* __restrict__ rank_slot, const uint64_t* __restrict__ keys_in,
     uint64_t* __restrict__ keys_out,
     typename SCplx<Real>::T* __restrict__ amps_out, uint64_t* __restrict__ probs_out,
     uint16_t* __restrict__ seg_out, uint32_t* __restrict__ hist1, uint64_t* __restrict__ start,
@@ -446,7 +451,7 @@ __global__ void __launch_bounds__(SA_BLOCK) k_seg_apply(
   __shared__ uint32_t s_hcnt[SEL_BINS];
   if (threadIdx.x == 0) sm.hcnt = s_hcnt;
   __syncthreads();
-  seg_apply_run<Real, MAXD, GPT>(sk, sidx, n, heads, amps_in, shift, gates, rank_slot, tables, keys_out, amps_out,
+  seg_apply_run<Real, MAXD, GPT>(sk, sidx, n, heads, amps_in, shift, gates, rank_slot, keys_in, keys_out, amps_out,
                                  probs_out, seg_out, hist1, start, end, lookback, max_tiles, ctl, sm, s_dyn);
 }
 
@@ -480,7 +485,7 @@ cudaError_t seg_apply_attrs() {
 template <typename Real>
 void seg_apply_dispatch(int mmax, int gpt, unsigned grid, cudaStream_t st, const uint64_t* sk, const uint32_t* sidx,
                         uint64_t n, const uint32_t* heads, const void* amps_in, int shift, const SegGate* gates,
-                        const uint16_t* rank_slot, const uint64_t* tables, uint64_t* keys_out, void* amps_out,
+                        const uint16_t* rank_slot, const uint64_t* keys_in, uint64_t* keys_out, void* amps_out,
                         uint64_t* probs_out,
                         uint16_t* seg_out, uint32_t* hist1, uint64_t* start, uint64_t* end,
                         uint64_t* lookback, uint64_t max_tiles, Ctl* ctl) {
@@ -489,7 +494,7 @@ void seg_apply_dispatch(int mmax, int gpt, unsigned grid, cudaStream_t st, const
   C2* ao = (C2*)amps_out;
 #define SV_SEG_APPLY(MAXD, GPT)                                                                         \
   k_seg_apply<Real, MAXD, GPT><<<grid, SA_BLOCK, seg_apply_smem<C2>(MAXD, GPT), st>>>(                    \
-      sk, sidx, n, heads, ai, shift, gates, rank_slot, tables, keys_out, ao, probs_out, seg_out, hist1, start,  \
+      sk, sidx, n, heads, ai, shift, gates, rank_slot, keys_in, keys_out, ao, probs_out, seg_out, hist1, start, \
       end, lookback, max_tiles, ctl)
   if (mmax <= 1) {
     if (gpt == 1) SV_SEG_APPLY(2, 1);
@@ -515,7 +520,7 @@ int seg_apply_configs(int mmax) { return mmax <= 2 ? 3 : (mmax == 3 ? 2 : 1); }
 // count of one group per thread.
 void launch_seg_apply(int prec, const uint64_t* sk, const uint32_t* sidx, uint64_t n, const uint32_t* heads,
                       const void* amps_in, int shift, int mmax, const SegGate* gates, const uint16_t* rank_slot,
-                      const uint64_t* tables, uint64_t* keys_out, void* amps_out, uint64_t* probs_out,
+                      const uint64_t* keys_in, uint64_t* keys_out, void* amps_out, uint64_t* probs_out,
                       uint16_t* seg_out, uint32_t* hist1, uint64_t* start, uint64_t* end,
                       uint64_t* lookback, Ctl* ctl, uint64_t max_tiles, int cfg, cudaStream_t st) {
   cudaMemsetAsync(lookback, 0, sizeof(uint64_t) * (max_tiles + 1), st);
@@ -527,10 +532,11 @@ void launch_seg_apply(int prec, const uint64_t* sk, const uint32_t* sidx, uint64
   const uint64_t grid = max_tiles < 148 * 4 ? (max_tiles ? max_tiles : 1) : 148 * 4;
   if (prec == 0)
     seg_apply_dispatch<double>(mmax, gpt, (unsigned)grid, st, sk, sidx, n, heads, amps_in, shift, gates, rank_slot,
-                               tables, keys_out, amps_out, probs_out, seg_out, hist1, start, end, lookback, max_tiles, ctl);
+                               keys_in, keys_out, amps_out, probs_out, seg_out, hist1, start, end, lookback, max_tiles,
+                               ctl);
   else
     seg_apply_dispatch<float>(mmax, gpt, (unsigned)grid, st, sk, sidx, n, heads, amps_in, shift, gates, rank_slot,
-                              tables, keys_out, amps_out, probs_out, seg_out, hist1, start, end, lookback, max_tiles,
+                              keys_in, keys_out, amps_out, probs_out, seg_out, hist1, start, end, lookback, max_tiles,
                               ctl);
 }
 
@@ -1390,7 +1396,7 @@ __global__ void __launch_bounds__(LAYER_THREADS, MAXD <= 4 ? 4 : (MAXD == 8 ? 2 
   if (tid == 0) smem_as<SegApplySmem>(smem).hcnt = reinterpret_cast<uint32_t*>(dyn + seg_apply_smem<C2>(MAXD, LAYER_GPT));
   __syncthreads();
   seg_apply_run<Real, MAXD, LAYER_GPT>(P.sk[cur], P.sidx[cur], nkeep, P.heads, amps_in, shift, P.gates,
-                                       P.rank_slot, P.tables, keys_mv, amps_mv, probs_mv, seg_mv,
+                                       P.rank_slot, keys_in, keys_mv, amps_mv, probs_mv, seg_mv,
                                        P.sel_cnt[0], P.start, P.end, lb_apply, P.lb_apply_words - 1, ctl,
                                        smem_as<SegApplySmem>(smem), dyn);
   if (layer_sync(lc, ncta, err, LP_APPLY)) return;

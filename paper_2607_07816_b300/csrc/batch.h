@@ -170,7 +170,7 @@ constexpr int SEGSEL_CONFIGS = 3;
 constexpr int SEGTRUNC_CONFIGS = 2;
 void launch_seg_apply(int prec, const uint64_t* sk, const uint32_t* sidx, uint64_t n, const uint32_t* heads,
                       const void* amps_in, int shift, int mmax, const SegGate* gates, const uint16_t* rank_slot,
-                      const uint64_t* tables, uint64_t* keys_out,
+                      const uint64_t* keys_in, uint64_t* keys_out,
                       void* amps_out, uint64_t* probs_out, uint16_t* seg_out, uint32_t* hist1, uint64_t* start,
                       uint64_t* end, uint64_t* lookback, Ctl* ctl, uint64_t max_tiles, int cfg, cudaStream_t st);
 // Sizes marked n_dev are read on the device (a term count written by an

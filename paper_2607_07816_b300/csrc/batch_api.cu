@@ -539,7 +539,7 @@ static sv_status step_kernels(svb_state* b, int top, uint64_t N, uint64_t nkeep,
     cudaMemsetAsync(end_dev, 0, sizeof(uint64_t) * b->max_slots, b->st);
     if (timing) cudaEventRecord(b->tev[TK_APPLY][0], b->st);
     launch_seg_apply(b->prec, b->sk[w], b->sidx[w], nkeep, b->heads, b->amps[b->cur], shift, mmax, b->gates_dev,
-                     b->rank_slot_dev, b->tables_dev,
+                     b->rank_slot_dev, b->keys[b->cur],
                      b->keys[alt], b->amps[alt], b->probs[alt], b->seg[alt], may_truncate ? b->sel_cnt : nullptr,
                      start_dev, end_dev, b->lookback, b->ctl, apply_tiles, cfg_apply, b->st);
     if (timing) cudaEventRecord(b->tev[TK_APPLY][1], b->st);
