@@ -237,7 +237,7 @@ def account_step(tot, q, kind, s1, s2, prec, n_bits):
         # keep flags, the kept terms' keys and amplitudes read and written
         # (the compaction writes no probabilities)
         tot["compact_bytes"] += n_pre / 8 + 2 * (8 + sa) * n_kept
-    # gate-level model (SURVEY-style B_method): group 2 S N_in, mat-vec S (N_in + N_pre),
+    # gate-level byte model B_method: group 2 S N_in, mat-vec S (N_in + N_pre),
     # select 8 N_pre and compaction S (N_pre + N_kept) when a cut is made
     b = 2 * S * n_in + S * (n_in + n_pre)
     if cut:

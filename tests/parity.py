@@ -1,5 +1,9 @@
 """Comparison helpers: CUDA path (through the C ABI) against the oracle."""
+import functools
+
 import numpy as np
+
+from paper_2607_07816_b300 import circuits as C
 
 
 def assert_states_equal(gpu, orc, exact=True, atol=0.0, what=""):
@@ -35,3 +39,18 @@ def run_both(gates, gpu, orc, truncate=True, check_every=True, exact=True, atol=
     assert_states_equal(gpu, orc, exact=exact, atol=atol, what="final")
     assert gpu.peak() == orc.peak()
     assert gpu.retained_mass() == orc.retained_mass()
+
+
+@functools.lru_cache(maxsize=None)
+def batched_sample(count=8, max_log2_k=11, max_gates=200):
+    """The first `count` circuits of the 512-circuit batched workload (seed
+    1004; circuit j depends on j alone, so the first 160 are those of the
+    full list) with K <= 2^max_log2_k and at most max_gates gates (small enough
+    for the oracle to finish in a few seconds)."""
+    out = []
+    for j, c in enumerate(C.batch_circuits(count=160)):
+        if c.K <= (1 << max_log2_k) and len(c.gates) <= max_gates:
+            out.append((j, c))
+            if len(out) == count:
+                break
+    return out

@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 
 from paper_2607_07816_b300 import circuits as C
+from tests.parity import batched_sample
 
 pytestmark = pytest.mark.gpu
 
@@ -263,3 +264,39 @@ def test_layer_kernel_graphs_and_separate_kernels_agree(sv):
     assert g1["captures"] >= 1 and g1["launches"] > 2 * g1["captures"]
     _same(kernels, direct)
     _same(kernels, graphed)
+
+
+@pytest.mark.parametrize("layer", [True, False], ids=["one_launch", "kernels"])
+def test_complex64_batch_against_complex128_oracle(sv, oracle_mod, layer):
+    """Circuits of the 512-circuit batched workload, advanced together in
+    complex64: each slot equals the complex64 oracle exactly and stays within
+    2e-6 per amplitude of the complex128 oracle, with the same kept terms and
+    the same peak string."""
+    sample = batched_sample()
+    circs = [c for _, c in sample]
+    b = sv.Batch(len(circs), prec=1)
+    b.set_layer_kernel(layer)
+    slots = [b.add(c.n, c.K) for c in circs]
+    o64 = [oracle_mod.Oracle(c.n, c.K, 1.0, prec=1) for c in circs]
+    o128 = [oracle_mod.Oracle(c.n, c.K, 1.0, prec=0) for c in circs]
+    for t in range(max(len(c.gates) for c in circs)):
+        gates = []
+        for s, c, x, y in zip(slots, circs, o64, o128):
+            if t < len(c.gates):
+                q, u = c.gates[t]
+                gates.append((s, q, u))
+                for o in (x, y):
+                    o.apply_gate(q, u)
+                    o.truncate()
+        b.step(gates)
+    for (j, c), s, x, y in zip(sample, slots, o64, o128):
+        what = f"circuit {j} (n={c.n}, K={c.K})"
+        _check_slot(b, s, x, what)
+        gk, ga = b.export(s)
+        wk, wa, _ = y.export()
+        g, w = _as_dict(gk, ga), _as_dict(wk, wa)
+        assert g.keys() == w.keys(), what
+        d = max(abs(g[k] - w[k]) for k in w)
+        assert d <= 2e-6, f"{what}: max |d amp| {d:.3e}"
+        assert b.peak(s)[0] == y.peak()[0], what
+    b.close()
